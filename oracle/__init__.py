@@ -1,0 +1,300 @@
+"""FP64 CPU oracle for the WNNC hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It is written from the paper alone and
+shares no code with the CUDA path; it loads a small C library
+(``wnnc_oracle.c``, built into ``oracle/_build/``) that holds the O(N^2) sums,
+the treecode and the iteration, all in double precision.
+
+Units.  ``direct`` works on whatever coordinates it is given.  The ``eval_*``
+and ``iterate`` functions mirror the library's boundary: points and normals in
+the caller's units, the smoothing width ``w`` in the normalised units of
+Sec. 5.1.1 (the cloud scaled into [-1,1]^3 with a 1/11 margin, by s), and
+results converted back (mu scales like area, s^2; the gradient of F like 1/length, s;
+A^T s like s^2 so that <A mu, v> = <mu, A^T v> holds in caller units).
+
+Parity status of each function (pins live in tests/test_oracle_pins.py):
+  direct A, G, A^T   pinned (closed forms on spheres, F(centre)=1, FD of A = -G,
+                     adjointness, symmetry, scaling and rotation invariance)
+  tree A, G, A^T     pinned (theta->0 limit equals direct, error decreases with
+                     theta, exact adjointness of the rep_mode-1 pair, Alg. 4
+                     per-target criterion holds for every far use)
+  iterate            pinned (first-iteration closed form on a sphere, energy
+                     decrease of the exact line search, P_co = 100% on a sphere,
+                     the zero-init / no-grad-step behaviour of Sec. 6.1.4)
+  knn                pinned (against sorting all distances)
+  mlp                pinned (finite differences)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from ctypes import POINTER, c_double, c_int, c_int64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wnnc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+OP_A, OP_G, OP_AT = 0, 1, 2
+GROUP_SIZE = 32
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, -O2, OpenMP, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-std=c11", _SRC, "-o", _LIB_PATH, "-lm"])
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        d, i64, P = c_double, c_int64, POINTER
+        L.or_num_threads.restype = c_int
+        L.or_normalize.argtypes = [c_void_p, i64, c_void_p, c_void_p, c_void_p]
+        L.or_direct.argtypes = [c_int, c_void_p, i64, c_void_p, c_void_p, i64, d, d, c_void_p, c_void_p]
+        L.or_tree_build.argtypes = [c_void_p, i64, c_int, c_int, c_int, d]
+        L.or_tree_build.restype = c_void_p
+        L.or_tree_free.argtypes = [c_void_p]
+        L.or_tree_nnodes.argtypes = [c_void_p]
+        L.or_tree_nnodes.restype = i64
+        L.or_tree_nodes.argtypes = [c_void_p] + [c_void_p] * 5
+        L.or_tree_perm.argtypes = [c_void_p, c_void_p]
+        L.or_tree_boxes.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        L.or_tree_counts.argtypes = [c_void_p, c_void_p]
+        L.or_tree_lists.argtypes = [c_void_p] + [c_void_p] * 4
+        L.or_tree_apply.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p]
+        L.or_tree_apply_at.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, i64, c_void_p, c_void_p]
+        L.or_schedule_width.argtypes = [c_int, c_int, d, d]
+        L.or_schedule_width.restype = d
+        L.or_iterate.argtypes = [c_void_p, c_void_p, i64, c_void_p, c_int, c_int, c_int, d, d, c_int,
+                                 c_int, c_void_p, c_int, c_int, c_void_p]
+        L.or_knn.argtypes = [c_void_p, i64, c_int, c_void_p, c_void_p]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(c_void_p) if a is not None else None
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
+# ---------------------------------------------------------------------------
+# Normalisation (Sec. 5.1.1)
+# ---------------------------------------------------------------------------
+
+def normalize(points):
+    """(xn, center, scale): xn = (x - center) * scale, in float64."""
+    pts = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+    n = pts.shape[0]
+    xn = np.empty((n, 3))
+    c = np.empty(3)
+    s = np.empty(1)
+    lib().or_normalize(_p(pts), n, _p(xn), _p(c), _p(s))
+    return xn, c, float(s[0])
+
+
+def apply_normalization(q, center, scale):
+    """Map caller-unit query points into normalised units (same formula)."""
+    q = np.asarray(q, dtype=np.float32).astype(np.float64).reshape(-1, 3)
+    return (q - center) * scale
+
+
+# ---------------------------------------------------------------------------
+# Direct O(N*M) sums (the plain definitions of A, G, A^T)
+# ---------------------------------------------------------------------------
+
+def direct(op: int, x, nu, w: float, y=None, amb_tol: float = 0.0):
+    """Direct sum of operator ``op`` with sources x, attribute nu, targets y
+    (default: the sources).  Returns (out, amb); amb is None unless amb_tol>0."""
+    x = _f64(x, (-1, 3))
+    y = x if y is None else _f64(y, (-1, 3))
+    ns, nt = x.shape[0], y.shape[0]
+    nu = _f64(nu, (ns, 3) if op != OP_AT else (ns,))
+    out = np.zeros(nt) if op == OP_A else np.zeros((nt, 3))
+    amb = np.zeros(nt) if amb_tol > 0 else None
+    lib().or_direct(op, _p(x), ns, _p(nu), _p(y), nt, float(w), float(amb_tol), _p(out), _p(amb))
+    return out, amb
+
+
+# ---------------------------------------------------------------------------
+# Treecode
+# ---------------------------------------------------------------------------
+
+class Tree:
+    """Source octree + on-surface target groups over normalised points xn."""
+
+    def __init__(self, xn, theta: float, leaf_size: int = 32, max_depth: int = 15,
+                 group_size: int = GROUP_SIZE):
+        self.xn = _f64(xn, (-1, 3))
+        self.n = self.xn.shape[0]
+        self.theta = float(theta)
+        self._h = lib().or_tree_build(_p(self.xn), self.n, leaf_size, group_size, max_depth, self.theta)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().or_tree_free(self._h)
+            self._h = None
+
+    def apply(self, op: int, nu, w: float, rep_mode: int = 1):
+        nu = _f64(nu, (self.n, 3) if op != OP_AT else (self.n,))
+        out = np.zeros(self.n) if op == OP_A else np.zeros((self.n, 3))
+        lib().or_tree_apply(self._h, op, rep_mode, float(w), _p(nu), _p(out))
+        return out
+
+    def apply_at(self, op: int, nu, qn, w: float, rep_mode: int = 1):
+        nu = _f64(nu, (self.n, 3))
+        qn = _f64(qn, (-1, 3))
+        m = qn.shape[0]
+        out = np.zeros(m) if op == OP_A else np.zeros((m, 3))
+        pairs = np.zeros(2, np.int64)
+        lib().or_tree_apply_at(self._h, op, rep_mode, float(w), _p(nu), _p(qn), m, _p(out), _p(pairs))
+        return out, pairs
+
+    def counts(self):
+        """(far list entries, near list entries, far pairs, near pairs)."""
+        c = np.zeros(4, np.int64)
+        lib().or_tree_counts(self._h, _p(c))
+        return tuple(int(v) for v in c)
+
+    def nodes(self):
+        m = lib().or_tree_nnodes(self._h)
+        start = np.zeros(m, np.int64); count = np.zeros(m, np.int64)
+        depth = np.zeros(m, np.int32); nchild = np.zeros(m, np.int32); parent = np.zeros(m, np.int64)
+        lib().or_tree_nodes(self._h, _p(start), _p(count), _p(depth), _p(nchild), _p(parent))
+        lo = np.zeros((m, 3)); hi = np.zeros((m, 3)); cent = np.zeros((m, 3))
+        lib().or_tree_boxes(self._h, _p(lo), _p(hi), _p(cent))
+        return dict(start=start, count=count, depth=depth, nchild=nchild, parent=parent,
+                    lo=lo, hi=hi, cent=cent)
+
+    def perm(self):
+        p = np.zeros(self.n, np.int64)
+        lib().or_tree_perm(self._h, _p(p))
+        return p
+
+    def lists(self):
+        ng = (self.n + GROUP_SIZE - 1) // GROUP_SIZE
+        c = self.counts()
+        fo = np.zeros(ng + 1, np.int64); no = np.zeros(ng + 1, np.int64)
+        fi = np.zeros(max(c[0], 1), np.int64); ni = np.zeros(max(c[1], 1), np.int64)
+        lib().or_tree_lists(self._h, _p(fo), _p(fi), _p(no), _p(ni))
+        return fo, fi[:c[0]], no, ni[:c[1]]
+
+
+# ---------------------------------------------------------------------------
+# Boundary-shaped entry points (caller units, like the library's C ABI)
+# ---------------------------------------------------------------------------
+
+def _setup(points, theta, leaf_size, max_depth):
+    xn, c, s = normalize(points)
+    tree = Tree(xn, theta, leaf_size, max_depth) if theta > 0 else None
+    return xn, c, s, tree
+
+
+def eval_op(op: int, points, nu, w: float, theta: float = 0.0, leaf_size: int = 32,
+            max_depth: int = 15, rep_mode: int = 1, amb_tol: float = 0.0):
+    """One operator at the input points, caller units in and out.
+
+    op A: nu = mu (N,3) -> F (N,);  op G: nu = mu -> grad F = -G (N,3);
+    op AT: nu = s (N,) -> A^T s (N,3).  theta = 0 uses the direct sums."""
+    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth)
+    nu = np.asarray(nu, dtype=np.float64)
+    nun = nu * (s * s) if op != OP_AT else nu
+    amb = None
+    if tree is None:
+        out, amb = direct(op, xn, nun, w, amb_tol=amb_tol)
+    else:
+        out = tree.apply(op, nun, w, rep_mode)
+    if op == OP_G:
+        out = -out * s          # grad F in caller units
+    elif op == OP_AT:
+        out = out * (s * s)
+    return out, amb
+
+
+def eval_at(op: int, points, mu, queries, w: float, theta: float = 0.0, leaf_size: int = 32,
+            max_depth: int = 15, rep_mode: int = 1):
+    """A (F) or grad F at off-surface query points (caller units)."""
+    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth)
+    qn = apply_normalization(queries, c, s)
+    mun = np.asarray(mu, dtype=np.float64) * (s * s)
+    if tree is None:
+        out, _ = direct(op, xn, mun, w, y=qn)
+    else:
+        out, _ = tree.apply_at(op, mun, qn, w, rep_mode)
+    return -out * s if op == OP_G else out
+
+
+def iterate(points, mu0=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0.016,
+            theta: float = 0.0, leaf_size: int = 32, max_depth: int = 15, rep_mode: int = 1,
+            first_iter: int = 1, last_iter: int | None = None, rescale: int = 0, area=None,
+            use_grad: bool = True, use_wnnc: bool = True):
+    """Alg. 3 on the cloud; returns (mu in caller units, stats[iter] = (w, E, alpha, |r|^2))."""
+    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth)
+    n = xn.shape[0]
+    mu = np.zeros((n, 3)) if mu0 is None else np.array(mu0, dtype=np.float64).reshape(n, 3) * (s * s)
+    last = n_iter if last_iter is None else last_iter
+    stats = np.zeros((max(last - first_iter + 1, 0), 4))
+    ar = None if area is None else np.ascontiguousarray(np.asarray(area, np.float64) * (s * s))
+    lib().or_iterate(tree._h if tree is not None else None, _p(xn), n, _p(mu), n_iter, first_iter,
+                     last, float(w1), float(w2), rep_mode, rescale, _p(ar), int(use_grad),
+                     int(use_wnnc), _p(stats))
+    return mu / (s * s), stats
+
+
+def schedule_width(i: int, n_iter: int, w1: float, w2: float) -> float:
+    return lib().or_schedule_width(i, n_iter, w1, w2)
+
+
+def knn(x, k: int = 16):
+    """Exhaustive k nearest neighbours (excluding the point itself)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    idx = np.zeros((n, k), np.int64)
+    d2 = np.zeros((n, k))
+    lib().or_knn(_p(x), n, k, _p(idx), _p(d2))
+    return idx, d2
+
+
+# ---------------------------------------------------------------------------
+# Metrics (Sec. 5.1.3)
+# ---------------------------------------------------------------------------
+
+def unit(v):
+    v = np.asarray(v, dtype=np.float64)
+    nrm = np.linalg.norm(v, axis=1, keepdims=True)
+    return np.divide(v, nrm, out=np.zeros_like(v), where=nrm > 0)
+
+
+def ae_pcd(n_gt, n_rec, valid=None):
+    """AE_pcd = mean (1 - n_gt . n_rec) / 2 over valid points."""
+    d = (unit(n_gt) * unit(n_rec)).sum(1)
+    if valid is not None:
+        d = d[valid]
+    return float(np.mean((1.0 - d) / 2.0))
+
+
+def p_co(n_gt, n_rec, valid=None):
+    """P_co = fraction of points with n_gt . n_rec > 0."""
+    d = (np.asarray(n_gt, np.float64) * np.asarray(n_rec, np.float64)).sum(1)
+    if valid is not None:
+        d = d[valid]
+    return float(np.mean(d > 0))

@@ -1,0 +1,706 @@
+/*
+ * wnnc_oracle.c -- plain FP64 CPU oracle for the WNNC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package's smoke() check and
+ * the benchmark's CPU-baseline leg may load this library.  It shares no code
+ * with the CUDA path (no headers, no helpers, no constants).
+ *
+ * What it computes (all in double precision, one OpenMP loop over targets
+ * where the loop has no cross-target accumulation):
+ *
+ *  - or_normalize: the input normalisation of Sec. 5.1.1 (points scaled into
+ *    [-1,1]^3 with a margin of 1/11).
+ *  - or_direct: the plain O(N*M) sums of the three operators of Sec. 4.4,
+ *      A(mu)_y   = sum_j gradPhi(y - x_j) . mu_j            (Eq. 4, Eq. 7)
+ *      G(mu)_y   = -sum_j HPhi(y - x_j) mu_j               (Eq. 9, Eq. 10)
+ *      AT(s)_y   = sum_i s_i gradPhi(x_i - y)              (Sec. 4.4, A^T)
+ *    with gradPhi(y) = -y/(4 pi |y|^3) (Thm. 1) and
+ *    HPhi(y) = -I/(4 pi |y|^3) + 3 y y^T/(4 pi |y|^5) (Eq. 9), every term set
+ *    to zero when |y - x| < w (Sec. 4.3, operators A_w, G_w).
+ *  - or_tree_*: the treecode approximation of Sec. 4.4 / Alg. 4: an octree
+ *    over the sources that stops splitting at leaf_size points or depth D,
+ *    node representatives (Eq. 11/12), and far / recurse / leaf-direct
+ *    decisions.  Targets are evaluated in groups of consecutive Morton-sorted
+ *    targets; a node is used as a far source for a whole group when the gap
+ *    between the group's bounding box and the node's bounding box exceeds
+ *    c * width(node), c = 1/theta.  Because both the target and the
+ *    representative lie in those boxes, every far use also satisfies the
+ *    per-target test of Alg. 4 (|x_i - x_B| > c * width(B)).
+ *  - or_iterate: Alg. 3 (width schedule, grad step of Alg. 2, WNNC update,
+ *    rescale), on either the direct sums or a tree.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+enum { OP_A = 0, OP_G = 1, OP_AT = 2 };
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Normalisation (Sec. 5.1.1): centre the bounding box, scale the largest    */
+/* half-extent to 10/11.                                                     */
+/* ------------------------------------------------------------------------ */
+void or_normalize(const float* pts, int64_t n, double* xn, double* center, double* scale) {
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = n > 0 ? (double)pts[k] : 0.0;
+        hi[k] = lo[k];
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            double v = (double)pts[3 * i + k];
+            if (v < lo[k]) lo[k] = v;
+            if (v > hi[k]) hi[k] = v;
+        }
+    double hmax = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        center[k] = (lo[k] + hi[k]) * 0.5;
+        double h = (hi[k] - lo[k]) * 0.5;
+        if (h > hmax) hmax = h;
+    }
+    double s = hmax > 0.0 ? (10.0 / 11.0) / hmax : 1.0;
+    *scale = s;
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k)
+            xn[3 * i + k] = ((double)pts[3 * i + k] - center[k]) * s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pair terms.  d = y - x (target minus source).                              */
+/* ------------------------------------------------------------------------ */
+
+/* gradPhi(y - x) . mu  =  -(d . mu) / (4 pi r^3) */
+static inline double term_A(const double d[3], double r2, const double* mu) {
+    double r = sqrt(r2);
+    return -(d[0] * mu[0] + d[1] * mu[1] + d[2] * mu[2]) / (4.0 * OR_PI * r2 * r);
+}
+
+/* -HPhi(d) mu = mu/(4 pi r^3) - 3 d (d.mu)/(4 pi r^5) */
+static inline void term_G(const double d[3], double r2, const double* mu, double out[3]) {
+    double r = sqrt(r2);
+    double r3 = r2 * r, r5 = r3 * r2;
+    double dm = d[0] * mu[0] + d[1] * mu[1] + d[2] * mu[2];
+    for (int k = 0; k < 3; ++k)
+        out[k] = mu[k] / (4.0 * OR_PI * r3) - 3.0 * d[k] * dm / (4.0 * OR_PI * r5);
+}
+
+/* s * gradPhi(x - y) = s * d / (4 pi r^3), d = y - x */
+static inline void term_AT(const double d[3], double r2, double s, double out[3]) {
+    double r = sqrt(r2);
+    for (int k = 0; k < 3; ++k) out[k] = s * d[k] / (4.0 * OR_PI * r2 * r);
+}
+
+/* Cut-off of Sec. 4.3: a term counts iff |y - x| >= w; coincident points
+ * never count (this is the self term, and the only exclusion when w = 0). */
+static inline int keep_pair(double r2, double w2) { return r2 > 0.0 && r2 >= w2; }
+
+/* A pair is "cut-off ambiguous" when r^2 lies within amb_tol*w^2 of w^2: a
+ * single-precision evaluation may take the other side of the test. */
+static inline int ambiguous(double r2, double w2, double amb_tol) {
+    return w2 > 0.0 && fabs(r2 - w2) <= amb_tol * w2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct sums: targets y (nt x 3), sources x (ns x 3).                       */
+/* nu: mu (ns x 3) for A and G, s (ns) for AT.                                */
+/* out: nt for A, nt x 3 for G and AT.  amb (optional): per target, the sum   */
+/* of |term| over cut-off-ambiguous pairs (the largest change a flipped       */
+/* cut-off decision can make).                                               */
+/* ------------------------------------------------------------------------ */
+void or_direct(int op, const double* xs, int64_t ns, const double* nu,
+               const double* yt, int64_t nt, double w, double amb_tol,
+               double* out, double* amb) {
+    const double w2 = w * w;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        double acc[3] = {0, 0, 0}, ab = 0.0;
+        for (int64_t j = 0; j < ns; ++j) {
+            double d[3] = {yt[3 * t] - xs[3 * j], yt[3 * t + 1] - xs[3 * j + 1],
+                           yt[3 * t + 2] - xs[3 * j + 2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 > 0.0)) continue;
+            int amb_p = amb && ambiguous(r2, w2, amb_tol);
+            if (!keep_pair(r2, w2) && !amb_p) continue;
+            double v[3] = {0, 0, 0};
+            if (op == OP_A) v[0] = term_A(d, r2, nu + 3 * j);
+            else if (op == OP_G) term_G(d, r2, nu + 3 * j, v);
+            else term_AT(d, r2, nu[j], v);
+            if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            if (keep_pair(r2, w2))
+                for (int k = 0; k < 3; ++k) acc[k] += v[k];
+        }
+        if (op == OP_A) out[t] = acc[0];
+        else for (int k = 0; k < 3; ++k) out[3 * t + k] = acc[k];
+        if (amb) amb[t] = ab;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Octree (Sec. 4.4): cells are the dyadic cubes of the root cube [-1,1]^3;  */
+/* a cell at depth d has width 2/2^d.  A node is split into its non-empty    */
+/* child cells while it holds more than leaf_size points and d < max_depth.  */
+/* Points are ordered by a 45-bit Morton key (15 bits per axis, x the most   */
+/* significant bit of each 3-bit digit), ties broken by input index.         */
+/* ------------------------------------------------------------------------ */
+
+static int64_t quant15(double v) {
+    double q = floor((v + 1.0) * 16384.0);
+    if (q < 0.0) q = 0.0;
+    if (q > 32767.0) q = 32767.0;
+    return (int64_t)q;
+}
+
+static uint64_t morton45(const double* x) {
+    int64_t q[3] = {quant15(x[0]), quant15(x[1]), quant15(x[2])};
+    uint64_t key = 0;
+    for (int b = 14; b >= 0; --b) {
+        uint64_t digit = (uint64_t)(((q[0] >> b) & 1) << 2 | ((q[1] >> b) & 1) << 1 | ((q[2] >> b) & 1));
+        key = (key << 3) | digit;
+    }
+    return key;
+}
+
+typedef struct { uint64_t key; int64_t idx; } keyidx;
+
+static int cmp_keyidx(const void* a, const void* b) {
+    const keyidx* p = (const keyidx*)a;
+    const keyidx* q = (const keyidx*)b;
+    if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    return (p->idx > q->idx) - (p->idx < q->idx);
+}
+
+/* Sorted order of a point set: perm[k] = input index of the k-th point. */
+static void morton_order(const double* x, int64_t n, int64_t* perm, uint64_t* keys) {
+    keyidx* ki = (keyidx*)malloc(sizeof(keyidx) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) { ki[i].key = morton45(x + 3 * i); ki[i].idx = i; }
+    qsort(ki, (size_t)n, sizeof(keyidx), cmp_keyidx);
+    for (int64_t i = 0; i < n; ++i) { perm[i] = ki[i].idx; if (keys) keys[i] = ki[i].key; }
+    free(ki);
+}
+
+typedef struct {
+    int64_t n, nnodes, cap;
+    int leaf_size, max_depth;
+    double* x;          /* sources, normalised, sorted order (n x 3) */
+    int64_t* perm;      /* sorted position -> input index */
+    uint64_t* key;
+    int64_t *start, *count, *parent, *child0;
+    int *depth, *nchild;
+    double *lo, *hi, *cent;   /* tight bounding box and point centroid per node */
+} or_octree;
+
+static int64_t new_node(or_octree* t) {
+    if (t->nnodes == t->cap) {
+        t->cap = t->cap ? 2 * t->cap : 1024;
+        t->start = realloc(t->start, sizeof(int64_t) * t->cap);
+        t->count = realloc(t->count, sizeof(int64_t) * t->cap);
+        t->parent = realloc(t->parent, sizeof(int64_t) * t->cap);
+        t->child0 = realloc(t->child0, sizeof(int64_t) * t->cap);
+        t->depth = realloc(t->depth, sizeof(int) * t->cap);
+        t->nchild = realloc(t->nchild, sizeof(int) * t->cap);
+    }
+    return t->nnodes++;
+}
+
+/* Breadth-first construction so that the children of a node are consecutive. */
+static void build_octree(or_octree* t) {
+    int64_t root = new_node(t);
+    t->start[root] = 0; t->count[root] = t->n; t->parent[root] = -1;
+    t->depth[root] = 0; t->nchild[root] = 0; t->child0[root] = -1;
+    for (int64_t b = 0; b < t->nnodes; ++b) {
+        if (t->count[b] <= t->leaf_size || t->depth[b] >= t->max_depth) continue;
+        int d = t->depth[b];
+        int shift = 3 * (14 - d);      /* digit of the child level d+1 */
+        int64_t s = t->start[b], e = s + t->count[b];
+        int64_t first = -1; int nc = 0;
+        int64_t i = s;
+        while (i < e) {
+            uint64_t dig = (t->key[i] >> shift) & 7u;
+            int64_t j = i;
+            while (j < e && ((t->key[j] >> shift) & 7u) == dig) ++j;
+            int64_t c = new_node(t);
+            if (first < 0) first = c;
+            t->start[c] = i; t->count[c] = j - i; t->parent[c] = b;
+            t->depth[c] = d + 1; t->nchild[c] = 0; t->child0[c] = -1;
+            ++nc;
+            i = j;
+        }
+        t->child0[b] = first; t->nchild[b] = nc;
+    }
+    int64_t m = t->nnodes;
+    t->lo = malloc(sizeof(double) * 3 * m);
+    t->hi = malloc(sizeof(double) * 3 * m);
+    t->cent = malloc(sizeof(double) * 3 * m);
+    for (int64_t b = 0; b < m; ++b) {
+        double sum[3] = {0, 0, 0};
+        for (int k = 0; k < 3; ++k) { t->lo[3 * b + k] = INFINITY; t->hi[3 * b + k] = -INFINITY; }
+        for (int64_t i = t->start[b]; i < t->start[b] + t->count[b]; ++i)
+            for (int k = 0; k < 3; ++k) {
+                double v = t->x[3 * i + k];
+                if (v < t->lo[3 * b + k]) t->lo[3 * b + k] = v;
+                if (v > t->hi[3 * b + k]) t->hi[3 * b + k] = v;
+                sum[k] += v;
+            }
+        for (int k = 0; k < 3; ++k) t->cent[3 * b + k] = sum[k] / (double)t->count[b];
+    }
+}
+
+/* Target groups: consecutive runs of group_size Morton-sorted targets, with
+ * their interaction lists against the source octree. */
+typedef struct {
+    int64_t m, ngroups;
+    int group_size;
+    double* y;           /* targets, normalised, sorted (m x 3) */
+    int64_t* perm;       /* sorted position -> input index */
+    double *glo, *ghi;   /* group bounding boxes */
+    int64_t *far_off, *far_id, *near_off, *near_id;   /* CSR lists per group */
+    int64_t far_pairs, near_pairs;
+} or_targets;
+
+typedef struct { int64_t *v; int64_t n, cap; } ivec;
+static void ivec_push(ivec* a, int64_t x) {
+    if (a->n == a->cap) { a->cap = a->cap ? 2 * a->cap : 64; a->v = realloc(a->v, sizeof(int64_t) * a->cap); }
+    a->v[a->n++] = x;
+}
+
+/* Far test for a target group box (glo, ghi) against node b: the gap between
+ * the boxes, squared, must exceed (c * width(b))^2.  Evaluated as written, in
+ * double precision, without fused multiply-adds. */
+static int is_far(const or_octree* t, int64_t b, const double* glo, const double* ghi, double c) {
+    if (!(c < INFINITY)) return 0;
+    double g[3];
+    for (int k = 0; k < 3; ++k) {
+        double a = t->lo[3 * b + k] - ghi[k];
+        double e = glo[k] - t->hi[3 * b + k];
+        double m = a > e ? a : e;
+        g[k] = m > 0.0 ? m : 0.0;
+    }
+    double gx = g[0] * g[0], gy = g[1] * g[1], gz = g[2] * g[2];
+    double d2 = (gx + gy) + gz;
+    double width = ldexp(2.0, -t->depth[b]);
+    double cw = c * width;
+    return d2 > cw * cw;
+}
+
+static void traverse(const or_octree* t, int64_t b, const double* glo, const double* ghi, double c,
+                     ivec* far, ivec* near) {
+    if (is_far(t, b, glo, ghi, c)) { ivec_push(far, b); return; }
+    if (t->nchild[b] == 0) { ivec_push(near, b); return; }
+    for (int q = 0; q < t->nchild[b]; ++q) traverse(t, t->child0[b] + q, glo, ghi, c, far, near);
+}
+
+static void build_targets(or_targets* T, const or_octree* t, const double* yn, int64_t m,
+                          int group_size, double theta) {
+    T->m = m; T->group_size = group_size;
+    T->perm = malloc(sizeof(int64_t) * (m > 0 ? m : 1));
+    morton_order(yn, m, T->perm, NULL);
+    T->y = malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
+    for (int64_t i = 0; i < m; ++i)
+        for (int k = 0; k < 3; ++k) T->y[3 * i + k] = yn[3 * T->perm[i] + k];
+    int64_t ng = (m + group_size - 1) / group_size;
+    T->ngroups = ng;
+    T->glo = malloc(sizeof(double) * 3 * (ng > 0 ? ng : 1));
+    T->ghi = malloc(sizeof(double) * 3 * (ng > 0 ? ng : 1));
+    double c = theta > 0.0 ? 1.0 / theta : INFINITY;
+    ivec* fars = calloc((size_t)(ng > 0 ? ng : 1), sizeof(ivec));
+    ivec* nears = calloc((size_t)(ng > 0 ? ng : 1), sizeof(ivec));
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t g = 0; g < ng; ++g) {
+        int64_t s = g * group_size, e = s + group_size < m ? s + group_size : m;
+        for (int k = 0; k < 3; ++k) { T->glo[3 * g + k] = INFINITY; T->ghi[3 * g + k] = -INFINITY; }
+        for (int64_t i = s; i < e; ++i)
+            for (int k = 0; k < 3; ++k) {
+                double v = T->y[3 * i + k];
+                if (v < T->glo[3 * g + k]) T->glo[3 * g + k] = v;
+                if (v > T->ghi[3 * g + k]) T->ghi[3 * g + k] = v;
+            }
+        if (t->n > 0) traverse(t, 0, T->glo + 3 * g, T->ghi + 3 * g, c, &fars[g], &nears[g]);
+    }
+    T->far_off = malloc(sizeof(int64_t) * (ng + 1));
+    T->near_off = malloc(sizeof(int64_t) * (ng + 1));
+    T->far_off[0] = T->near_off[0] = 0;
+    for (int64_t g = 0; g < ng; ++g) {
+        T->far_off[g + 1] = T->far_off[g] + fars[g].n;
+        T->near_off[g + 1] = T->near_off[g] + nears[g].n;
+    }
+    T->far_id = malloc(sizeof(int64_t) * (T->far_off[ng] > 0 ? T->far_off[ng] : 1));
+    T->near_id = malloc(sizeof(int64_t) * (T->near_off[ng] > 0 ? T->near_off[ng] : 1));
+    T->far_pairs = T->near_pairs = 0;
+    for (int64_t g = 0; g < ng; ++g) {
+        int64_t gs = g * group_size, ge = gs + group_size < m ? gs + group_size : m;
+        memcpy(T->far_id + T->far_off[g], fars[g].v, sizeof(int64_t) * fars[g].n);
+        memcpy(T->near_id + T->near_off[g], nears[g].v, sizeof(int64_t) * nears[g].n);
+        T->far_pairs += (ge - gs) * fars[g].n;
+        for (int64_t q = 0; q < nears[g].n; ++q) T->near_pairs += (ge - gs) * t->count[nears[g].v[q]];
+        free(fars[g].v); free(nears[g].v);
+    }
+    free(fars); free(nears);
+}
+
+static void free_targets(or_targets* T) {
+    free(T->y); free(T->perm); free(T->glo); free(T->ghi);
+    free(T->far_off); free(T->far_id); free(T->near_off); free(T->near_id);
+}
+
+/* The public tree handle: sources with their octree, and the sources
+ * themselves as the on-surface target set. */
+typedef struct {
+    or_octree src;
+    or_targets self;
+    double theta;
+} or_tree;
+
+or_tree* or_tree_build(const double* xn, int64_t n, int leaf_size, int group_size, int max_depth,
+                       double theta) {
+    or_tree* T = calloc(1, sizeof(or_tree));
+    or_octree* t = &T->src;
+    t->n = n; t->leaf_size = leaf_size; t->max_depth = max_depth;
+    t->perm = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    t->key = malloc(sizeof(uint64_t) * (n > 0 ? n : 1));
+    morton_order(xn, n, t->perm, t->key);
+    t->x = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) t->x[3 * i + k] = xn[3 * t->perm[i] + k];
+    if (n > 0) build_octree(t);
+    T->theta = theta;
+    build_targets(&T->self, t, xn, n, group_size, theta);
+    return T;
+}
+
+void or_tree_free(or_tree* T) {
+    if (!T) return;
+    or_octree* t = &T->src;
+    free(t->x); free(t->perm); free(t->key); free(t->start); free(t->count); free(t->parent);
+    free(t->child0); free(t->depth); free(t->nchild); free(t->lo); free(t->hi); free(t->cent);
+    free_targets(&T->self);
+    free(T);
+}
+
+/* Structure queries (for the structural pins and for comparing list sizes). */
+int64_t or_tree_nnodes(const or_tree* T) { return T->src.nnodes; }
+void or_tree_nodes(const or_tree* T, int64_t* start, int64_t* count, int* depth, int* nchild,
+                   int64_t* parent) {
+    const or_octree* t = &T->src;
+    for (int64_t b = 0; b < t->nnodes; ++b) {
+        start[b] = t->start[b]; count[b] = t->count[b]; depth[b] = t->depth[b];
+        nchild[b] = t->nchild[b]; parent[b] = t->parent[b];
+    }
+}
+void or_tree_perm(const or_tree* T, int64_t* perm) { memcpy(perm, T->src.perm, sizeof(int64_t) * T->src.n); }
+void or_tree_boxes(const or_tree* T, double* lo, double* hi, double* cent) {
+    const or_octree* t = &T->src;
+    memcpy(lo, t->lo, sizeof(double) * 3 * t->nnodes);
+    memcpy(hi, t->hi, sizeof(double) * 3 * t->nnodes);
+    memcpy(cent, t->cent, sizeof(double) * 3 * t->nnodes);
+}
+/* far / near list sizes and pair counts of the on-surface target set */
+void or_tree_counts(const or_tree* T, int64_t* out4) {
+    out4[0] = T->self.far_off[T->self.ngroups];
+    out4[1] = T->self.near_off[T->self.ngroups];
+    out4[2] = T->self.far_pairs;
+    out4[3] = T->self.near_pairs;
+}
+void or_tree_lists(const or_tree* T, int64_t* far_off, int64_t* far_id, int64_t* near_off, int64_t* near_id) {
+    const or_targets* S = &T->self;
+    memcpy(far_off, S->far_off, sizeof(int64_t) * (S->ngroups + 1));
+    memcpy(near_off, S->near_off, sizeof(int64_t) * (S->ngroups + 1));
+    memcpy(far_id, S->far_id, sizeof(int64_t) * S->far_off[S->ngroups]);
+    memcpy(near_id, S->near_id, sizeof(int64_t) * S->near_off[S->ngroups]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Node representatives (Eq. 11, Eq. 12).                                    */
+/*  rep_mode 0 (as in the paper): x_B = sum |nu_i| x_i / sum |nu_j|          */
+/*  rep_mode 1: x_B = plain centroid of the node's points (independent of    */
+/*              nu, which makes the tree operator linear in nu).             */
+/*  If sum |nu_j| = 0 the plain centroid is used (nu_B = 0 then anyway).     */
+/*  nu_B = sum nu_i.  nu has dim 3 (mu) or 1 (s); nu is in sorted order.     */
+/* ------------------------------------------------------------------------ */
+static void node_reps(const or_octree* t, const double* nu, int dim, int rep_mode,
+                      double* rep, double* nuB) {
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t b = 0; b < t->nnodes; ++b) {
+        double sw = 0.0, sx[3] = {0, 0, 0}, sn[3] = {0, 0, 0};
+        for (int64_t i = t->start[b]; i < t->start[b] + t->count[b]; ++i) {
+            double a = 0.0;
+            for (int k = 0; k < dim; ++k) { sn[k] += nu[dim * i + k]; a += nu[dim * i + k] * nu[dim * i + k]; }
+            a = sqrt(a);
+            sw += a;
+            for (int k = 0; k < 3; ++k) sx[k] += a * t->x[3 * i + k];
+        }
+        for (int k = 0; k < 3; ++k)
+            rep[3 * b + k] = (rep_mode == 0 && sw > 0.0) ? sx[k] / sw : t->cent[3 * b + k];
+        for (int k = 0; k < dim; ++k) nuB[dim * b + k] = sn[k];
+    }
+}
+
+/* Gather-form treecode for targets T against the source octree:
+ *   op A : out (m)    = sum_far gradPhi(y - x_B) . mu_B + sum_near gradPhi(y - x_j) . mu_j
+ *   op G : out (m x 3) = sum_far -HPhi(y - x_B) mu_B  + sum_near -HPhi(y - x_j) mu_j
+ *   op AT (rep_mode 0 only, the s-representative treecode of Sec. 4.4):
+ *          out (m x 3) = sum_far s_B gradPhi(x_B - y) + sum_near s_i gradPhi(x_i - y)
+ * nu_sorted: source attribute in sorted source order.  out: sorted target order.
+ */
+static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep_mode, double w,
+                        const double* nu_sorted, double* out_sorted) {
+    int dim = (op == OP_AT) ? 1 : 3;
+    double* rep = malloc(sizeof(double) * 3 * (t->nnodes > 0 ? t->nnodes : 1));
+    double* nuB = malloc(sizeof(double) * dim * (t->nnodes > 0 ? t->nnodes : 1));
+    node_reps(t, nu_sorted, dim, rep_mode, rep, nuB);
+    const double w2 = w * w;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t g = 0; g < T->ngroups; ++g) {
+        int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
+        for (int64_t i = s; i < e; ++i) {
+            const double* y = T->y + 3 * i;
+            double acc[3] = {0, 0, 0};
+            for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
+                int64_t b = T->far_id[q];
+                double d[3] = {y[0] - rep[3 * b], y[1] - rep[3 * b + 1], y[2] - rep[3 * b + 2]};
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!keep_pair(r2, w2)) continue;
+                double v[3] = {0, 0, 0};
+                if (op == OP_A) v[0] = term_A(d, r2, nuB + 3 * b);
+                else if (op == OP_G) term_G(d, r2, nuB + 3 * b, v);
+                else term_AT(d, r2, nuB[b], v);
+                for (int k = 0; k < 3; ++k) acc[k] += v[k];
+            }
+            for (int64_t q = T->near_off[g]; q < T->near_off[g + 1]; ++q) {
+                int64_t b = T->near_id[q];
+                for (int64_t j = t->start[b]; j < t->start[b] + t->count[b]; ++j) {
+                    const double* x = t->x + 3 * j;
+                    double d[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (!keep_pair(r2, w2)) continue;
+                    double v[3] = {0, 0, 0};
+                    if (op == OP_A) v[0] = term_A(d, r2, nu_sorted + 3 * j);
+                    else if (op == OP_G) term_G(d, r2, nu_sorted + 3 * j, v);
+                    else term_AT(d, r2, nu_sorted[j], v);
+                    for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                }
+            }
+            if (op == OP_A) out_sorted[i] = acc[0];
+            else for (int k = 0; k < 3; ++k) out_sorted[3 * i + k] = acc[k];
+        }
+    }
+    free(rep); free(nuB);
+}
+
+/* Exact transpose of the rep_mode-1 tree operator A (targets = sources):
+ *   A_tree(mu)_i = sum_{B far for g(i)} gradPhi(x_i - x_B) . sum_{j in B} mu_j
+ *                + sum_{L near for g(i)} sum_{j in L} gradPhi(x_i - x_j) . mu_j
+ * so
+ *   (A_tree^T s)_j = sum_{B containing j} V_B
+ *                  + sum_{(g, L): L near for g, j in L} sum_{i in g} s_i gradPhi(x_i - x_j),
+ *   V_B = sum_{g: B far for g} sum_{i in g} s_i gradPhi(x_i - x_B).
+ * The node sums and the leaf sums are gathered through the transposed lists so
+ * that each output is a sum in a fixed order (groups ascending, then i). */
+static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w,
+                               const double* s_sorted, double* out_sorted) {
+    int64_t nn = t->nnodes, ng = T->ngroups;
+    const double w2 = w * w;
+    /* transposed lists: node -> groups using it (far), leaf -> groups using it (near) */
+    int64_t* fcnt = calloc((size_t)nn + 1, sizeof(int64_t));
+    int64_t* ncnt = calloc((size_t)nn + 1, sizeof(int64_t));
+    for (int64_t q = 0; q < T->far_off[ng]; ++q) fcnt[T->far_id[q] + 1]++;
+    for (int64_t q = 0; q < T->near_off[ng]; ++q) ncnt[T->near_id[q] + 1]++;
+    for (int64_t b = 0; b < nn; ++b) { fcnt[b + 1] += fcnt[b]; ncnt[b + 1] += ncnt[b]; }
+    int64_t* fg = malloc(sizeof(int64_t) * (fcnt[nn] > 0 ? fcnt[nn] : 1));
+    int64_t* ngp = malloc(sizeof(int64_t) * (ncnt[nn] > 0 ? ncnt[nn] : 1));
+    int64_t* fpos = malloc(sizeof(int64_t) * (nn > 0 ? nn : 1));
+    int64_t* npos = malloc(sizeof(int64_t) * (nn > 0 ? nn : 1));
+    memcpy(fpos, fcnt, sizeof(int64_t) * nn);
+    memcpy(npos, ncnt, sizeof(int64_t) * nn);
+    for (int64_t g = 0; g < ng; ++g) {
+        for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) fg[fpos[T->far_id[q]]++] = g;
+        for (int64_t q = T->near_off[g]; q < T->near_off[g + 1]; ++q) ngp[npos[T->near_id[q]]++] = g;
+    }
+    double* V = calloc((size_t)(nn > 0 ? nn : 1) * 3, sizeof(double));
+    const double* rep = t->cent;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < nn; ++b) {
+        double acc[3] = {0, 0, 0};
+        for (int64_t q = fcnt[b]; q < fcnt[b + 1]; ++q) {
+            int64_t g = fg[q];
+            int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
+            for (int64_t i = s; i < e; ++i) {
+                /* s_i gradPhi(x_i - x_B) = s_i (x_B - x_i) / (4 pi r^3) */
+                double d[3] = {rep[3 * b] - T->y[3 * i], rep[3 * b + 1] - T->y[3 * i + 1],
+                               rep[3 * b + 2] - T->y[3 * i + 2]};
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!keep_pair(r2, w2)) continue;
+                double v[3];
+                term_AT(d, r2, s_sorted[i], v);
+                for (int k = 0; k < 3; ++k) acc[k] += v[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) V[3 * b + k] = acc[k];
+    }
+    /* near part, per source leaf, then add the far sums of all nodes containing j */
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < nn; ++b) {
+        if (t->nchild[b] != 0) continue;
+        for (int64_t j = t->start[b]; j < t->start[b] + t->count[b]; ++j) {
+            const double* x = t->x + 3 * j;
+            double acc[3] = {0, 0, 0};
+            for (int64_t q = ncnt[b]; q < ncnt[b + 1]; ++q) {
+                int64_t g = ngp[q];
+                int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
+                for (int64_t i = s; i < e; ++i) {
+                    double d[3] = {x[0] - T->y[3 * i], x[1] - T->y[3 * i + 1], x[2] - T->y[3 * i + 2]};
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (!keep_pair(r2, w2)) continue;
+                    double v[3];
+                    term_AT(d, r2, s_sorted[i], v);
+                    for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                }
+            }
+            double far[3] = {0, 0, 0};
+            for (int64_t a = b; a >= 0; a = t->parent[a])
+                for (int k = 0; k < 3; ++k) far[k] += V[3 * a + k];
+            for (int k = 0; k < 3; ++k) out_sorted[3 * j + k] = acc[k] + far[k];
+        }
+    }
+    free(fcnt); free(ncnt); free(fg); free(ngp); free(fpos); free(npos); free(V);
+}
+
+/* On-surface application of an operator.  nu and out are in input order,
+ * normalised units.  For op AT, rep_mode 1 gives the exact transpose of the
+ * rep_mode-1 A, rep_mode 0 the paper's s-representative treecode. */
+void or_tree_apply(const or_tree* T, int op, int rep_mode, double w, const double* nu, double* out) {
+    const or_octree* t = &T->src;
+    int64_t n = t->n;
+    int din = (op == OP_AT) ? 1 : 3, dout = (op == OP_A) ? 1 : 3;
+    double* nus = malloc(sizeof(double) * din * (n > 0 ? n : 1));
+    double* outs = malloc(sizeof(double) * dout * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < din; ++k) nus[din * i + k] = nu[din * t->perm[i] + k];
+    if (op == OP_AT && rep_mode == 1) tree_adjoint_exact(t, &T->self, w, nus, outs);
+    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs);
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < dout; ++k) out[dout * T->self.perm[i] + k] = outs[dout * i + k];
+    free(nus); free(outs);
+}
+
+/* Off-surface targets (op A or G): the targets are grouped and listed
+ * against the source octree exactly like the on-surface set. */
+void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const double* nu,
+                      const double* qn, int64_t m, double* out, int64_t* pairs2) {
+    const or_octree* t = &T->src;
+    or_targets Q;
+    memset(&Q, 0, sizeof(Q));
+    build_targets(&Q, t, qn, m, T->self.group_size, T->theta);
+    int64_t n = t->n;
+    int dout = (op == OP_A) ? 1 : 3;
+    double* nus = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double* outs = malloc(sizeof(double) * dout * (m > 0 ? m : 1));
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) nus[3 * i + k] = nu[3 * t->perm[i] + k];
+    tree_gather(t, &Q, op, rep_mode, w, nus, outs);
+    for (int64_t i = 0; i < m; ++i)
+        for (int k = 0; k < dout; ++k) out[dout * Q.perm[i] + k] = outs[dout * i + k];
+    if (pairs2) { pairs2[0] = Q.far_pairs; pairs2[1] = Q.near_pairs; }
+    free(nus); free(outs);
+    free_targets(&Q);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 3: n iterations of grad step (Alg. 2) + WNNC update + rescale, with  */
+/* the linear width schedule w = w2 (n-i)/(n-1) + w1 (i-1)/(n-1).            */
+/*   T == NULL: the operators are the direct sums over xn.                   */
+/*   mu (n x 3, input order, normalised units) is updated in place.          */
+/*   rescale 0: mu_i <- muhat_i |mu_i| / |muhat_i|  (Alg. 3)                 */
+/*   rescale 1: mu_i <- muhat_i sigma_i / |muhat_i|  (Eq. 14, needs area)    */
+/*   use_grad / use_wnnc switch the two halves off for the ablations of      */
+/*   Sec. 5.5.2 / Sec. 6.1.4.                                                */
+/*   stats (optional, per iteration): w, E = |A mu - b|^2 before the step,   */
+/*   alpha, |r|^2.                                                           */
+/* ------------------------------------------------------------------------ */
+static void apply_op(const or_tree* T, const double* xn, int64_t n, int op, int rep_mode, double w,
+                     const double* nu, double* out) {
+    if (T) or_tree_apply(T, op, rep_mode, w, nu, out);
+    else or_direct(op, xn, n, nu, xn, n, w, 0.0, out, NULL);
+}
+
+double or_schedule_width(int i, int n_iter, double w1, double w2) {
+    if (n_iter <= 1) return w1;
+    return w2 * (double)(n_iter - i) / (double)(n_iter - 1) + w1 * (double)(i - 1) / (double)(n_iter - 1);
+}
+
+void or_iterate(const or_tree* T, const double* xn, int64_t n, double* mu, int n_iter, int first_iter,
+                int last_iter, double w1, double w2, int rep_mode, int rescale, const double* area,
+                int use_grad, int use_wnnc, double* stats) {
+    double* a = malloc(sizeof(double) * (n > 0 ? n : 1));
+    double* s = malloc(sizeof(double) * (n > 0 ? n : 1));
+    double* r = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double* q = malloc(sizeof(double) * (n > 0 ? n : 1));
+    double* muhat = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    for (int it = first_iter; it <= last_iter; ++it) {
+        double w = or_schedule_width(it, n_iter, w1, w2);
+        double E = 0.0, rr = 0.0, qq = 0.0, alpha = 0.0;
+        if (use_grad) {
+            /* Alg. 2:  r = A^T b - A^T A mu = A^T (b - A mu);  alpha = r.r / |A r|^2;  mu += alpha r */
+            apply_op(T, xn, n, OP_A, rep_mode, w, mu, a);
+            for (int64_t i = 0; i < n; ++i) { s[i] = 0.5 - a[i]; E += s[i] * s[i]; }
+            apply_op(T, xn, n, OP_AT, rep_mode, w, s, r);
+            for (int64_t i = 0; i < 3 * n; ++i) rr += r[i] * r[i];
+            apply_op(T, xn, n, OP_A, rep_mode, w, r, q);
+            for (int64_t i = 0; i < n; ++i) qq += q[i] * q[i];
+            alpha = qq > 0.0 ? rr / qq : 0.0;
+            for (int64_t i = 0; i < 3 * n; ++i) mu[i] += alpha * r[i];
+        }
+        if (use_wnnc) {
+            /* WNNC update muhat = G_w(mu), then rescale */
+            apply_op(T, xn, n, OP_G, rep_mode, w, mu, muhat);
+            for (int64_t i = 0; i < n; ++i) {
+                double hn = sqrt(muhat[3 * i] * muhat[3 * i] + muhat[3 * i + 1] * muhat[3 * i + 1] +
+                                 muhat[3 * i + 2] * muhat[3 * i + 2]);
+                if (!(hn > 0.0)) continue;
+                double len;
+                if (rescale == 1 && area) len = area[i];
+                else len = sqrt(mu[3 * i] * mu[3 * i] + mu[3 * i + 1] * mu[3 * i + 1] + mu[3 * i + 2] * mu[3 * i + 2]);
+                for (int k = 0; k < 3; ++k) mu[3 * i + k] = muhat[3 * i + k] * len / hn;
+            }
+        }
+        if (stats) {
+            double* st = stats + 4 * (it - first_iter);
+            st[0] = w; st[1] = E; st[2] = alpha; st[3] = rr;
+        }
+    }
+    free(a); free(s); free(r); free(q); free(muhat);
+}
+
+/* ------------------------------------------------------------------------ */
+/* k nearest neighbours by exhaustive search (ties by index), excluding the  */
+/* point itself.  out: n x k indices, dist2: n x k squared distances.        */
+/* ------------------------------------------------------------------------ */
+void or_knn(const double* x, int64_t n, int k, int64_t* out, double* dist2) {
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t* idx = out + (int64_t)k * i;
+        double* dd = dist2 + (int64_t)k * i;
+        int cnt = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (cnt == k && !(r2 < dd[k - 1])) continue;
+            int p = cnt < k ? cnt++ : k - 1;
+            while (p > 0 && dd[p - 1] > r2) { dd[p] = dd[p - 1]; idx[p] = idx[p - 1]; --p; }
+            dd[p] = r2; idx[p] = j;
+        }
+    }
+}
