@@ -1,0 +1,221 @@
+/*
+ * wnnc.h -- C ABI of the B300 (sm_103a) WNNC treecode library.
+ *
+ * The library evaluates, on one GPU, the three linear operators of the
+ * Winding-Number-Normal-Consistency normal-orientation method
+ * (Lin, Shi, Liu, "Fast and Globally Consistent Normal Orientation based on
+ * the Winding Number Normal Consistency", Sec. 4):
+ *
+ *   A(mu)_i  = sum_j gradPhi(x_i - x_j) . mu_j         winding number F(x_i; mu)  (Eq. 4, Eq. 7)
+ *   G(mu)_i  = -sum_j HPhi(x_i - x_j) mu_j              = -grad F(x_i; mu)          (Eq. 9, Eq. 10)
+ *   A^T(s)_j = sum_i s_i gradPhi(x_i - x_j)             adjoint of A (Sec. 4.4)
+ *
+ *   gradPhi(y) = -y / (4 pi |y|^3)                        (Thm. 1)
+ *   HPhi(y)    = -I/(4 pi |y|^3) + 3 y y^T / (4 pi |y|^5) (Eq. 9)
+ *
+ * with every pair term set to zero when |x_i - x_j| < w (smoothing width,
+ * Sec. 4.3), accelerated by a treecode over an octree of the points
+ * (Sec. 4.4, Eq. 11-12, Alg. 4), and the iteration of Alg. 3 (width
+ * schedule, gradient step of Alg. 2, WNNC update, rescale).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers marked "device" are CUDA device pointers; "host" are host
+ *    pointers.  Arrays of points/normals are row-major float32 [n][3]
+ *    (a contiguous torch tensor of shape (n, 3)), in the caller's input order.
+ *  - The caller owns every input and output buffer.  The library owns only
+ *    wnnc_tree objects (and the device memory inside them).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Evaluation and iteration calls are asynchronous on that stream; build
+ *    and free synchronise with it.  Calls that use the same tree must not run
+ *    concurrently (they share the tree's work buffers).
+ *  - Units: positions and normals are in the caller's units.  The tree
+ *    normalises the cloud into [-1,1]^3 with a 1/11 margin (Sec. 5.1.1):
+ *    x' = (x - c) * s.  The smoothing width w is given in those normalised
+ *    units, as in the paper.  mu scales like area (mu' = s^2 mu); results are
+ *    returned in caller units (F is dimensionless, grad F scales by s,
+ *    A^T v by s^2, so that <A mu, v> = <mu, A^T v> in caller units).
+ *  - Errors: every call returns a wnnc_status.  Argument and launch errors
+ *    are reported at once.  Conditions detected on the device (a non-finite
+ *    step length in the iteration) are latched in the tree and returned by
+ *    wnnc_sync_status.  wnnc_last_error() returns a thread-local text for the
+ *    last failure.  No exception crosses this boundary.
+ */
+#ifndef WNNC_H
+#define WNNC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wnnc_tree wnnc_tree;
+
+typedef enum {
+    WNNC_OK = 0,
+    WNNC_EINVAL = 1,      /* bad argument (NULL pointer, n < 1, w < 0, theta < 0, ...) */
+    WNNC_ENOMEM = 2,      /* device or host allocation failed */
+    WNNC_ECUDA = 3,       /* a CUDA runtime call failed */
+    WNNC_ENONFINITE = 4,  /* the iteration produced a non-finite step length */
+    WNNC_ECAPACITY = 5,   /* a traversal stack or list capacity was exceeded */
+    WNNC_ETIMEOUT = 6     /* reserved: a bounded device wait gave up */
+} wnnc_status;
+
+/* Tree parameters (Sec. 5.1.1 defaults: D = 15, c = 2 i.e. theta = 0.5). */
+typedef struct {
+    int max_depth;     /* maximum octree depth D, root = depth 0; 1..15 (default 15) */
+    int leaf_size;     /* a node is split while it holds more than this many points
+                          (the paper splits down to 1 point); 1..1024 (default 32) */
+    float theta;       /* opening parameter, 1/c of Alg. 4; 0 = exact direct sums (default 0.5) */
+    int rep_mode;      /* node representative (Eq. 11): 1 = point centroid, which makes the
+                          tree operator linear so that A^T is its exact transpose (default);
+                          0 = |nu|-weighted centroid as in the paper (A^T is then the paper's
+                          s-representative treecode, not an exact transpose) */
+    int moments_fp64;  /* 1 = accumulate node moments in double precision (default 0) */
+} wnnc_tree_params;
+
+/* Iteration parameters (Alg. 3; Sec. 5.1.1 defaults n = 40, w1 = 0.002, w2 = 0.016). */
+typedef struct {
+    int n_iter;        /* n of the width schedule w_i = w2 (n-i)/(n-1) + w1 (i-1)/(n-1) */
+    int first_iter;    /* first i to run (1 = from the start; >1 resumes a saved run) */
+    int last_iter;     /* last i to run (0 = n_iter) */
+    float w1, w2;      /* final and initial smoothing widths, normalised units */
+    int init;          /* 0 = start from mu = 0 (the paper); 1 = start from mu_inout */
+    int rescale;       /* 0 = |mu_i| kept across the WNNC update (Alg. 3);
+                          1 = |mu_i| set to the given area sigma_i (Eq. 14) */
+    int use_grad;      /* 1 = gradient step of Alg. 2 (default); 0 = skip it (ablation) */
+    int use_wnnc;      /* 1 = WNNC update + rescale (default); 0 = skip it (ablation) */
+} wnnc_iter_params;
+
+/* Fill p with the defaults listed above.  Returns WNNC_EINVAL if p is NULL. */
+wnnc_status wnnc_tree_params_default(wnnc_tree_params* p);
+wnnc_status wnnc_iter_params_default(wnnc_iter_params* p);
+
+/*
+ * Build the octree (Sec. 4.4: split until leaf_size points or depth D),
+ * node boxes and centroids, and the interaction lists of the points as
+ * targets (Alg. 4's far / recurse / leaf-direct decisions, taken once per
+ * group of 32 Morton-consecutive targets against its bounding box).
+ *   pts    device, float32 [n][3], caller units; read during the call only.
+ *   n      number of points, >= 1.
+ *   params host, may be NULL for the defaults.
+ *   out    host; receives the new tree (NULL on failure).
+ * Synchronises with `stream`.  Errors: WNNC_EINVAL, WNNC_ENOMEM, WNNC_ECUDA,
+ * WNNC_ECAPACITY.
+ */
+wnnc_status wnnc_build_tree(const float* pts, int64_t n, const wnnc_tree_params* params,
+                            void* stream, wnnc_tree** out);
+
+/* Release a tree and its device memory (synchronises with the device). NULL is a no-op. */
+wnnc_status wnnc_tree_free(wnnc_tree* tree);
+
+/*
+ * F(x_i; mu) = A_w(mu)_i at every input point (Eq. 7 with the cut-off of Sec. 4.3).
+ *   mu  device, float32 [n][3], caller units (oriented area elements).
+ *   w   smoothing width (normalised units), >= 0; w = 0 only drops coincident pairs.
+ *   out device, float32 [n].
+ */
+wnnc_status wnnc_eval_w(const wnnc_tree* tree, const float* mu, float w, float* out, void* stream);
+
+/*
+ * grad F(x_i; mu) = -G_w(mu)_i at every input point (Eq. 8-10).
+ *   mu  device, float32 [n][3];  out device, float32 [n][3] (caller units).
+ */
+wnnc_status wnnc_eval_grad(const wnnc_tree* tree, const float* mu, float w, float* out, void* stream);
+
+/*
+ * A_w^T(s) at every input point (Sec. 4.4; the backward of F with respect to mu).
+ *   s   device, float32 [n];  out device, float32 [n][3] (caller units).
+ * With rep_mode 1 this is the exact transpose of wnnc_eval_w's operator.
+ */
+wnnc_status wnnc_eval_adjoint(const wnnc_tree* tree, const float* s, float w, float* out, void* stream);
+
+/*
+ * F(q_k; mu) (grad = 0) or grad F(q_k; mu) (grad = 1) at m query points that
+ * need not be input points (Thm. 1: 1 inside, 0 outside, 1/2 on the surface).
+ *   q   device, float32 [m][3], caller units;  m >= 1.
+ *   out device, float32 [m] (grad = 0) or [m][3] (grad = 1).
+ * Builds the queries' interaction lists (allocates) and synchronises with `stream`.
+ */
+wnnc_status wnnc_eval_at(const wnnc_tree* tree, const float* mu, const float* q, int64_t m,
+                         float w, int grad, float* out, void* stream);
+
+/*
+ * Run iterations first_iter..last_iter of Alg. 3 on the tree's points.
+ *   mu_inout device, float32 [n][3], caller units: the initial field when
+ *            init = 1 (ignored when init = 0), the result on return.
+ *   area     device, float32 [n] (caller units) for rescale = 1, else NULL.
+ *   params   host; NULL for the defaults.
+ *   stats    device, float32 [last-first+1][4] or NULL: per iteration the width
+ *            w_i, the energy E = |A mu - b|^2 before the step (Eq. 6, b = 1/2),
+ *            the step length alpha and |r|^2 (Alg. 2), in normalised units.
+ * Asynchronous; a non-finite alpha is latched (WNNC_ENONFINITE).
+ */
+wnnc_status wnnc_iterate(wnnc_tree* tree, float* mu_inout, const float* area,
+                         const wnnc_iter_params* params, void* stream, float* stats);
+
+/* Interaction counts of one on-surface operator evaluation: far (target, node)
+ * pairs and near (target, source) pairs, cut-off ones included.  host out. */
+wnnc_status wnnc_get_stats(const wnnc_tree* tree, int64_t* far_pairs, int64_t* near_pairs);
+
+/*
+ * Sizes of the tree (host out, any may be NULL): points, nodes, leaves,
+ * target groups, far-list entries, merged near ranges, transposed near entries,
+ * maximum depth reached.
+ */
+wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, int64_t* nleaves,
+                           int64_t* ngroups, int64_t* far_entries, int64_t* near_ranges,
+                           int64_t* tnear_entries, int* depth);
+
+/*
+ * Copy the tree's structure to host buffers (any may be NULL), for checking
+ * against an independent construction:
+ *   perm        int64 [n]        sorted position -> input index
+ *   node_start  int32 [nnodes]   first sorted point of each node (breadth-first order)
+ *   node_count  int32 [nnodes]
+ *   node_depth  int32 [nnodes]
+ *   node_nchild int32 [nnodes]   0 for leaves
+ *   far_off     int32 [ngroups+1], far_id int32 [far_entries]  per group, ascending node id
+ *   near_off    int32 [ngroups+1], near_rng int32 [near_ranges][2]  merged [start,end) ranges
+ *   center_scale float64 [4]     normalisation centre c (3) and scale s
+ */
+wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node_start,
+                             int32_t* node_count, int32_t* node_depth, int32_t* node_nchild,
+                             int32_t* far_off, int32_t* far_id, int32_t* near_off,
+                             int32_t* near_rng, double* center_scale);
+
+/*
+ * Kernel timing (not in the paper; the tracing facility of this library).
+ * When enabled, every kernel launch of the evaluation and iteration calls is
+ * bracketed by CUDA events on the launching stream and attributed to one of
+ * the classes below.  wnnc_profile_read synchronises with those events and
+ * returns, per class, the number of launches and their summed device time in
+ * milliseconds since the last reset (host out, arrays of WNNC_PROF_CLASSES
+ * entries, either may be NULL).  Enabling adds two event records per launch.
+ */
+enum {
+    WNNC_PROF_MOMENTS = 0,   /* bottom-up node moments (Eq. 11, Eq. 12) */
+    WNNC_PROF_A = 1,         /* treecode sum of A (Eq. 7, Alg. 4) */
+    WNNC_PROF_ADJ_FAR = 2,   /* adjoint: far (target group, node) sums */
+    WNNC_PROF_ADJ_NODE = 3,  /* adjoint: per-node reduction */
+    WNNC_PROF_ADJ_NEAR = 4,  /* adjoint: near sums + push-down of node sums */
+    WNNC_PROF_G = 5,         /* treecode sum of G + rescale (Eq. 10, Alg. 3) */
+    WNNC_PROF_SMALL = 6,     /* permutations, step length, axpy */
+    WNNC_PROF_CLASSES = 7
+};
+wnnc_status wnnc_profile_enable(wnnc_tree* tree, int enable);
+wnnc_status wnnc_profile_read(wnnc_tree* tree, int64_t* launches, double* total_ms);
+wnnc_status wnnc_profile_reset(wnnc_tree* tree);
+
+/* Wait for the stream and return (and clear) any condition latched on the device. */
+wnnc_status wnnc_sync_status(wnnc_tree* tree, void* stream);
+
+/* Thread-local description of the last failed call ("" if none). */
+const char* wnnc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WNNC_H */

@@ -73,7 +73,7 @@ def lib():
         L.or_tree_boxes.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
         L.or_tree_counts.argtypes = [c_void_p, c_void_p]
         L.or_tree_lists.argtypes = [c_void_p] + [c_void_p] * 4
-        L.or_tree_apply.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p]
+        L.or_tree_apply.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, d, c_void_p]
         L.or_tree_apply_at.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, i64, c_void_p, c_void_p]
         L.or_schedule_width.argtypes = [c_int, c_int, d, d]
         L.or_schedule_width.restype = d
@@ -154,11 +154,13 @@ class Tree:
             lib().or_tree_free(self._h)
             self._h = None
 
-    def apply(self, op: int, nu, w: float, rep_mode: int = 1):
+    def apply(self, op: int, nu, w: float, rep_mode: int = 1, amb_tol: float = 0.0):
+        """Tree operator on the points; with amb_tol > 0 returns (out, amb)."""
         nu = _f64(nu, (self.n, 3) if op != OP_AT else (self.n,))
         out = np.zeros(self.n) if op == OP_A else np.zeros((self.n, 3))
-        lib().or_tree_apply(self._h, op, rep_mode, float(w), _p(nu), _p(out))
-        return out
+        amb = np.zeros(self.n) if amb_tol > 0 else None
+        lib().or_tree_apply(self._h, op, rep_mode, float(w), _p(nu), _p(out), float(amb_tol), _p(amb))
+        return (out, amb) if amb_tol > 0 else out
 
     def apply_at(self, op: int, nu, qn, w: float, rep_mode: int = 1):
         nu = _f64(nu, (self.n, 3))
@@ -221,12 +223,16 @@ def eval_op(op: int, points, nu, w: float, theta: float = 0.0, leaf_size: int = 
     amb = None
     if tree is None:
         out, amb = direct(op, xn, nun, w, amb_tol=amb_tol)
+    elif amb_tol > 0:
+        out, amb = tree.apply(op, nun, w, rep_mode, amb_tol=amb_tol)
     else:
         out = tree.apply(op, nun, w, rep_mode)
     if op == OP_G:
         out = -out * s          # grad F in caller units
+        amb = None if amb is None else amb * s
     elif op == OP_AT:
         out = out * (s * s)
+        amb = None if amb is None else amb * (s * s)
     return out, amb
 
 

@@ -455,7 +455,7 @@ static void node_reps(const or_octree* t, const double* nu, int dim, int rep_mod
  * nu_sorted: source attribute in sorted source order.  out: sorted target order.
  */
 static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep_mode, double w,
-                        const double* nu_sorted, double* out_sorted) {
+                        const double* nu_sorted, double* out_sorted, double amb_tol, double* amb_sorted) {
     int dim = (op == OP_AT) ? 1 : 3;
     double* rep = malloc(sizeof(double) * 3 * (t->nnodes > 0 ? t->nnodes : 1));
     double* nuB = malloc(sizeof(double) * dim * (t->nnodes > 0 ? t->nnodes : 1));
@@ -466,17 +466,20 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
         int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
         for (int64_t i = s; i < e; ++i) {
             const double* y = T->y + 3 * i;
-            double acc[3] = {0, 0, 0};
+            double acc[3] = {0, 0, 0}, ab = 0.0;
             for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
                 int64_t b = T->far_id[q];
                 double d[3] = {y[0] - rep[3 * b], y[1] - rep[3 * b + 1], y[2] - rep[3 * b + 2]};
                 double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                if (!keep_pair(r2, w2)) continue;
+                int amb_p = amb_sorted && r2 > 0.0 && ambiguous(r2, w2, amb_tol);
+                if (!keep_pair(r2, w2) && !amb_p) continue;
                 double v[3] = {0, 0, 0};
                 if (op == OP_A) v[0] = term_A(d, r2, nuB + 3 * b);
                 else if (op == OP_G) term_G(d, r2, nuB + 3 * b, v);
                 else term_AT(d, r2, nuB[b], v);
-                for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                if (keep_pair(r2, w2))
+                    for (int k = 0; k < 3; ++k) acc[k] += v[k];
             }
             for (int64_t q = T->near_off[g]; q < T->near_off[g + 1]; ++q) {
                 int64_t b = T->near_id[q];
@@ -484,16 +487,20 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
                     const double* x = t->x + 3 * j;
                     double d[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
                     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (!keep_pair(r2, w2)) continue;
+                    int amb_p = amb_sorted && r2 > 0.0 && ambiguous(r2, w2, amb_tol);
+                    if (!keep_pair(r2, w2) && !amb_p) continue;
                     double v[3] = {0, 0, 0};
                     if (op == OP_A) v[0] = term_A(d, r2, nu_sorted + 3 * j);
                     else if (op == OP_G) term_G(d, r2, nu_sorted + 3 * j, v);
                     else term_AT(d, r2, nu_sorted[j], v);
-                    for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                    if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                    if (keep_pair(r2, w2))
+                        for (int k = 0; k < 3; ++k) acc[k] += v[k];
                 }
             }
             if (op == OP_A) out_sorted[i] = acc[0];
             else for (int k = 0; k < 3; ++k) out_sorted[3 * i + k] = acc[k];
+            if (amb_sorted) amb_sorted[i] = ab;
         }
     }
     free(rep); free(nuB);
@@ -509,7 +516,8 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
  * The node sums and the leaf sums are gathered through the transposed lists so
  * that each output is a sum in a fixed order (groups ascending, then i). */
 static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w,
-                               const double* s_sorted, double* out_sorted) {
+                               const double* s_sorted, double* out_sorted, double amb_tol,
+                               double* amb_sorted) {
     int64_t nn = t->nnodes, ng = T->ngroups;
     const double w2 = w * w;
     /* transposed lists: node -> groups using it (far), leaf -> groups using it (near) */
@@ -529,10 +537,11 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         for (int64_t q = T->near_off[g]; q < T->near_off[g + 1]; ++q) ngp[npos[T->near_id[q]]++] = g;
     }
     double* V = calloc((size_t)(nn > 0 ? nn : 1) * 3, sizeof(double));
+    double* VA = calloc((size_t)(nn > 0 ? nn : 1), sizeof(double));
     const double* rep = t->cent;
     #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t b = 0; b < nn; ++b) {
-        double acc[3] = {0, 0, 0};
+        double acc[3] = {0, 0, 0}, ab = 0.0;
         for (int64_t q = fcnt[b]; q < fcnt[b + 1]; ++q) {
             int64_t g = fg[q];
             int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
@@ -541,13 +550,17 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                 double d[3] = {rep[3 * b] - T->y[3 * i], rep[3 * b + 1] - T->y[3 * i + 1],
                                rep[3 * b + 2] - T->y[3 * i + 2]};
                 double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                if (!keep_pair(r2, w2)) continue;
+                int amb_p = amb_sorted && r2 > 0.0 && ambiguous(r2, w2, amb_tol);
+                if (!keep_pair(r2, w2) && !amb_p) continue;
                 double v[3];
                 term_AT(d, r2, s_sorted[i], v);
-                for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                if (keep_pair(r2, w2))
+                    for (int k = 0; k < 3; ++k) acc[k] += v[k];
             }
         }
         for (int k = 0; k < 3; ++k) V[3 * b + k] = acc[k];
+        VA[b] = ab;
     }
     /* near part, per source leaf, then add the far sums of all nodes containing j */
     #pragma omp parallel for schedule(dynamic, 16)
@@ -555,44 +568,54 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         if (t->nchild[b] != 0) continue;
         for (int64_t j = t->start[b]; j < t->start[b] + t->count[b]; ++j) {
             const double* x = t->x + 3 * j;
-            double acc[3] = {0, 0, 0};
+            double acc[3] = {0, 0, 0}, ab = 0.0;
             for (int64_t q = ncnt[b]; q < ncnt[b + 1]; ++q) {
                 int64_t g = ngp[q];
                 int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
                 for (int64_t i = s; i < e; ++i) {
                     double d[3] = {x[0] - T->y[3 * i], x[1] - T->y[3 * i + 1], x[2] - T->y[3 * i + 2]};
                     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (!keep_pair(r2, w2)) continue;
+                    int amb_p = amb_sorted && r2 > 0.0 && ambiguous(r2, w2, amb_tol);
+                    if (!keep_pair(r2, w2) && !amb_p) continue;
                     double v[3];
                     term_AT(d, r2, s_sorted[i], v);
-                    for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                    if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                    if (keep_pair(r2, w2))
+                        for (int k = 0; k < 3; ++k) acc[k] += v[k];
                 }
             }
             double far[3] = {0, 0, 0};
-            for (int64_t a = b; a >= 0; a = t->parent[a])
+            for (int64_t a = b; a >= 0; a = t->parent[a]) {
                 for (int k = 0; k < 3; ++k) far[k] += V[3 * a + k];
+                ab += VA[a];
+            }
             for (int k = 0; k < 3; ++k) out_sorted[3 * j + k] = acc[k] + far[k];
+            if (amb_sorted) amb_sorted[j] = ab;
         }
     }
-    free(fcnt); free(ncnt); free(fg); free(ngp); free(fpos); free(npos); free(V);
+    free(fcnt); free(ncnt); free(fg); free(ngp); free(fpos); free(npos); free(V); free(VA);
 }
 
 /* On-surface application of an operator.  nu and out are in input order,
  * normalised units.  For op AT, rep_mode 1 gives the exact transpose of the
  * rep_mode-1 A, rep_mode 0 the paper's s-representative treecode. */
-void or_tree_apply(const or_tree* T, int op, int rep_mode, double w, const double* nu, double* out) {
+void or_tree_apply(const or_tree* T, int op, int rep_mode, double w, const double* nu, double* out,
+                   double amb_tol, double* amb) {
     const or_octree* t = &T->src;
     int64_t n = t->n;
     int din = (op == OP_AT) ? 1 : 3, dout = (op == OP_A) ? 1 : 3;
     double* nus = malloc(sizeof(double) * din * (n > 0 ? n : 1));
     double* outs = malloc(sizeof(double) * dout * (n > 0 ? n : 1));
+    double* ambs = amb ? malloc(sizeof(double) * (n > 0 ? n : 1)) : NULL;
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < din; ++k) nus[din * i + k] = nu[din * t->perm[i] + k];
-    if (op == OP_AT && rep_mode == 1) tree_adjoint_exact(t, &T->self, w, nus, outs);
-    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs);
-    for (int64_t i = 0; i < n; ++i)
+    if (op == OP_AT && rep_mode == 1) tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs);
+    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs);
+    for (int64_t i = 0; i < n; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * T->self.perm[i] + k] = outs[dout * i + k];
-    free(nus); free(outs);
+        if (amb) amb[T->self.perm[i]] = ambs[i];
+    }
+    free(nus); free(outs); free(ambs);
 }
 
 /* Off-surface targets (op A or G): the targets are grouped and listed
@@ -609,7 +632,7 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
     double* outs = malloc(sizeof(double) * dout * (m > 0 ? m : 1));
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) nus[3 * i + k] = nu[3 * t->perm[i] + k];
-    tree_gather(t, &Q, op, rep_mode, w, nus, outs);
+    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL);
     for (int64_t i = 0; i < m; ++i)
         for (int k = 0; k < dout; ++k) out[dout * Q.perm[i] + k] = outs[dout * i + k];
     if (pairs2) { pairs2[0] = Q.far_pairs; pairs2[1] = Q.near_pairs; }
@@ -631,7 +654,7 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
 /* ------------------------------------------------------------------------ */
 static void apply_op(const or_tree* T, const double* xn, int64_t n, int op, int rep_mode, double w,
                      const double* nu, double* out) {
-    if (T) or_tree_apply(T, op, rep_mode, w, nu, out);
+    if (T) or_tree_apply(T, op, rep_mode, w, nu, out, 0.0, NULL);
     else or_direct(op, xn, n, nu, xn, n, w, 0.0, out, NULL);
 }
 

@@ -1,0 +1,288 @@
+"""B300-native WNNC treecode: Python binding of the C ABI in ``include/wnnc.h``.
+
+This module only marshals arguments: every step of the computation runs in the
+CUDA kernels of ``libwnnc.so`` (built in-tree by ``paper_2405_16634_b300.build``).
+PyTorch supplies device memory and the current CUDA stream.  There is no CPU
+fallback: loading fails loudly if the library is missing, and every call
+raises ``WnncError`` when the library returns a non-OK status.
+
+Operators (Sec. 4 of the paper; w in normalised units, everything else in the
+caller's units):
+
+* ``Tree.eval_w(mu, w)``        F(x_i; mu) = A_w(mu)_i          (Eq. 7)
+* ``Tree.eval_grad(mu, w)``     grad F(x_i; mu) = -G_w(mu)_i    (Eq. 8-10)
+* ``Tree.eval_adjoint(s, w)``   A_w^T(s)                         (Sec. 4.4)
+* ``Tree.eval_at(mu, q, w)``    F (or grad F) at query points
+* ``Tree.iterate(...)``         Alg. 3 with the gradient step of Alg. 2
+* ``winding_number(tree, mu, w)`` differentiable F(mu) whose backward is A^T.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, c_double, c_float, c_int, c_int64, c_void_p
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libwnnc.so")
+
+__all__ = ["Tree", "TreeParams", "IterParams", "WnncError", "winding_number", "WindingNumber",
+           "lib", "LIB_PATH", "PROF_CLASSES"]
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ECAPACITY",
+          6: "ETIMEOUT"}
+PROF_CLASSES = ["moments", "A", "adj_far", "adj_node", "adj_near", "G", "small"]
+
+
+class WnncError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"wnnc status {status}: {msg}")
+        self.status = status
+
+
+class TreeParams(Structure):
+    _fields_ = [("max_depth", c_int), ("leaf_size", c_int), ("theta", c_float),
+                ("rep_mode", c_int), ("moments_fp64", c_int)]
+
+
+class IterParams(Structure):
+    _fields_ = [("n_iter", c_int), ("first_iter", c_int), ("last_iter", c_int),
+                ("w1", c_float), ("w2", c_float), ("init", c_int), ("rescale", c_int),
+                ("use_grad", c_int), ("use_wnnc", c_int)]
+
+
+_lib = None
+
+
+def build_if_needed() -> str:
+    """Compile libwnnc.so if it is missing or older than its sources (nvcc, no GPU needed)."""
+    from . import build as _build
+    return _build.build()
+
+
+def lib():
+    """Load libwnnc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2405_16634_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    L.wnnc_tree_params_default.argtypes = [POINTER(TreeParams)]
+    L.wnnc_iter_params_default.argtypes = [POINTER(IterParams)]
+    L.wnnc_build_tree.argtypes = [P, c_int64, POINTER(TreeParams), P, POINTER(c_void_p)]
+    L.wnnc_tree_free.argtypes = [P]
+    L.wnnc_eval_w.argtypes = [P, P, c_float, P, P]
+    L.wnnc_eval_grad.argtypes = [P, P, c_float, P, P]
+    L.wnnc_eval_adjoint.argtypes = [P, P, c_float, P, P]
+    L.wnnc_eval_at.argtypes = [P, P, P, c_int64, c_float, c_int, P, P]
+    L.wnnc_iterate.argtypes = [P, P, P, POINTER(IterParams), P, P]
+    L.wnnc_get_stats.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
+    L.wnnc_tree_info.argtypes = [P] + [POINTER(c_int64)] * 7 + [POINTER(c_int)]
+    L.wnnc_tree_export.argtypes = [P] + [P] * 10
+    L.wnnc_profile_enable.argtypes = [P, c_int]
+    L.wnnc_profile_read.argtypes = [P, P, P]
+    L.wnnc_profile_reset.argtypes = [P]
+    L.wnnc_sync_status.argtypes = [P, P]
+    L.wnnc_last_error.restype = ctypes.c_char_p
+    for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
+                 "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
+                 "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_tree_info",
+                 "wnnc_tree_export", "wnnc_profile_enable", "wnnc_profile_read",
+                 "wnnc_profile_reset", "wnnc_sync_status"):
+        getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().wnnc_last_error().decode(errors="replace")
+        raise WnncError(status, f"{STATUS.get(status, '?')}: {msg}")
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _dev_f32(t, shape, device) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
+    t = t.to(device=device, dtype=torch.float32).contiguous()
+    if tuple(t.shape) != tuple(shape):
+        t = t.reshape(shape)
+    return t
+
+
+def default_tree_params() -> TreeParams:
+    p = TreeParams()
+    _check(lib().wnnc_tree_params_default(ctypes.byref(p)))
+    return p
+
+
+def default_iter_params() -> IterParams:
+    p = IterParams()
+    _check(lib().wnnc_iter_params_default(ctypes.byref(p)))
+    return p
+
+
+class Tree:
+    """Octree, node data and interaction lists of a point cloud on one GPU."""
+
+    def __init__(self, points, theta: float = 0.5, leaf_size: int = 32, max_depth: int = 15,
+                 rep_mode: int = 1, moments_fp64: bool = False):
+        pts = points if isinstance(points, torch.Tensor) else torch.as_tensor(points)
+        self.device = pts.device if pts.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        pts = _dev_f32(pts, (-1, 3), self.device)
+        self.n = pts.shape[0]
+        p = default_tree_params()
+        p.max_depth, p.leaf_size, p.theta = int(max_depth), int(leaf_size), float(theta)
+        p.rep_mode, p.moments_fp64 = int(rep_mode), int(bool(moments_fp64))
+        self.params = p
+        h = c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().wnnc_build_tree(pts.data_ptr(), self.n, ctypes.byref(p),
+                                         _stream_ptr(self.device), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().wnnc_tree_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- operators -----------------------------------------------------------
+    def eval_w(self, mu, w: float, out: torch.Tensor | None = None) -> torch.Tensor:
+        mu = _dev_f32(mu, (self.n, 3), self.device)
+        out = torch.empty(self.n, device=self.device, dtype=torch.float32) if out is None else out
+        _check(lib().wnnc_eval_w(self._h, mu.data_ptr(), float(w), out.data_ptr(),
+                                 _stream_ptr(self.device)))
+        return out
+
+    def eval_grad(self, mu, w: float, out: torch.Tensor | None = None) -> torch.Tensor:
+        mu = _dev_f32(mu, (self.n, 3), self.device)
+        out = torch.empty(self.n, 3, device=self.device, dtype=torch.float32) if out is None else out
+        _check(lib().wnnc_eval_grad(self._h, mu.data_ptr(), float(w), out.data_ptr(),
+                                    _stream_ptr(self.device)))
+        return out
+
+    def eval_adjoint(self, s, w: float, out: torch.Tensor | None = None) -> torch.Tensor:
+        s = _dev_f32(s, (self.n,), self.device)
+        out = torch.empty(self.n, 3, device=self.device, dtype=torch.float32) if out is None else out
+        _check(lib().wnnc_eval_adjoint(self._h, s.data_ptr(), float(w), out.data_ptr(),
+                                       _stream_ptr(self.device)))
+        return out
+
+    def eval_at(self, mu, q, w: float, grad: bool = False) -> torch.Tensor:
+        mu = _dev_f32(mu, (self.n, 3), self.device)
+        q = _dev_f32(q, (-1, 3), self.device)
+        m = q.shape[0]
+        out = torch.empty((m, 3) if grad else (m,), device=self.device, dtype=torch.float32)
+        _check(lib().wnnc_eval_at(self._h, mu.data_ptr(), q.data_ptr(), m, float(w), int(grad),
+                                  out.data_ptr(), _stream_ptr(self.device)))
+        return out
+
+    def iterate(self, mu=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0.016,
+                first_iter: int = 1, last_iter: int = 0, area=None, rescale: int = 0,
+                use_grad: bool = True, use_wnnc: bool = True, stats: bool = False, out=None):
+        """Alg. 3.  mu None = zero init; returns mu (and per-iteration stats)."""
+        p = default_iter_params()
+        p.n_iter, p.first_iter, p.last_iter = int(n_iter), int(first_iter), int(last_iter)
+        p.w1, p.w2 = float(w1), float(w2)
+        p.init = 0 if mu is None else 1
+        p.rescale, p.use_grad, p.use_wnnc = int(rescale), int(bool(use_grad)), int(bool(use_wnnc))
+        if out is not None:
+            mu_t = out
+            if mu is not None:
+                mu_t.copy_(_dev_f32(mu, (self.n, 3), self.device))
+        elif mu is None:
+            mu_t = torch.zeros(self.n, 3, device=self.device, dtype=torch.float32)
+        else:
+            mu_t = _dev_f32(mu, (self.n, 3), self.device).clone()
+        ar = None if area is None else _dev_f32(area, (self.n,), self.device)
+        last = last_iter if last_iter > 0 else n_iter
+        st = torch.zeros(max(last - first_iter + 1, 1), 4, device=self.device, dtype=torch.float32) \
+            if stats else None
+        _check(lib().wnnc_iterate(self._h, mu_t.data_ptr(), None if ar is None else ar.data_ptr(),
+                                  ctypes.byref(p), _stream_ptr(self.device),
+                                  None if st is None else st.data_ptr()))
+        return (mu_t, st) if stats else mu_t
+
+    # -- inspection ----------------------------------------------------------
+    def stats(self):
+        """(far pairs, near pairs) of one operator evaluation on the points."""
+        f, nn = c_int64(), c_int64()
+        _check(lib().wnnc_get_stats(self._h, ctypes.byref(f), ctypes.byref(nn)))
+        return f.value, nn.value
+
+    def info(self) -> dict:
+        v = [c_int64() for _ in range(7)]
+        d = c_int()
+        _check(lib().wnnc_tree_info(self._h, *[ctypes.byref(x) for x in v], ctypes.byref(d)))
+        keys = ["n", "nnodes", "nleaves", "ngroups", "far_entries", "near_ranges", "tnear_entries"]
+        out = {k: x.value for k, x in zip(keys, v)}
+        out["depth"] = d.value
+        return out
+
+    def export(self) -> dict:
+        inf = self.info()
+        n, nn, ng = inf["n"], inf["nnodes"], inf["ngroups"]
+        a = dict(perm=np.zeros(n, np.int64), node_start=np.zeros(nn, np.int32),
+                 node_count=np.zeros(nn, np.int32), node_depth=np.zeros(nn, np.int32),
+                 node_nchild=np.zeros(nn, np.int32), far_off=np.zeros(ng + 1, np.int32),
+                 far_id=np.zeros(max(inf["far_entries"], 1), np.int32),
+                 near_off=np.zeros(ng + 1, np.int32),
+                 near_rng=np.zeros((max(inf["near_ranges"], 1), 2), np.int32),
+                 center_scale=np.zeros(4, np.float64))
+        ptr = lambda x: x.ctypes.data_as(c_void_p)
+        _check(lib().wnnc_tree_export(self._h, *[ptr(a[k]) for k in (
+            "perm", "node_start", "node_count", "node_depth", "node_nchild", "far_off", "far_id",
+            "near_off", "near_rng", "center_scale")]))
+        a["far_id"] = a["far_id"][:inf["far_entries"]]
+        a["near_rng"] = a["near_rng"][:inf["near_ranges"]]
+        return a
+
+    def profile(self, enable: bool = True):
+        _check(lib().wnnc_profile_enable(self._h, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        n = len(PROF_CLASSES)
+        launches = np.zeros(n, np.int64)
+        ms = np.zeros(n, np.float64)
+        _check(lib().wnnc_profile_read(self._h, launches.ctypes.data_as(c_void_p),
+                                       ms.ctypes.data_as(c_void_p)))
+        return {k: (int(launches[i]), float(ms[i])) for i, k in enumerate(PROF_CLASSES)}
+
+    def profile_reset(self):
+        _check(lib().wnnc_profile_reset(self._h))
+
+    def sync_status(self) -> None:
+        _check(lib().wnnc_sync_status(self._h, _stream_ptr(self.device)))
+
+
+class WindingNumber(torch.autograd.Function):
+    """F(mu) = A_w(mu) at the tree's points; backward = A_w^T (Sec. 4.4).
+
+    With rep_mode 1 the backward is the exact transpose of the forward tree
+    operator, so gradients agree with finite differences of the forward."""
+
+    @staticmethod
+    def forward(ctx, mu, tree: Tree, w: float):
+        ctx.tree, ctx.w = tree, w
+        return tree.eval_w(mu.detach(), w)
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.tree.eval_adjoint(g.contiguous(), ctx.w), None, None
+
+
+def winding_number(tree: Tree, mu: torch.Tensor, w: float) -> torch.Tensor:
+    return WindingNumber.apply(mu, tree, w)

@@ -1,0 +1,317 @@
+// api.cu -- the extern "C" boundary (include/wnnc.h): argument checks, status
+// codes, thread-local error text, tree lifetime and work buffers.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace wnnc {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+[[noreturn]] void fail(wnnc_status st, const std::string& msg) { throw Error{st, msg}; }
+
+static void alloc_workspace(Tree& t) {
+    const int64_t n = t.n;
+    const int nn = t.nnodes;
+    t.mu_a = dalloc<float4>(n);
+    t.mu_b = dalloc<float4>(n);
+    t.r_s = dalloc<float4>(n);
+    t.s_s = dalloc<float>(n);
+    t.area_s = dalloc<float>(n);
+    t.mom = dalloc<float4>(nn);
+    t.mom_x = dalloc<float4>(nn);
+    t.node_rep = dalloc<float4>(nn);
+    t.contrib = dalloc<float4>(t.self.far_entries);
+    t.vnode = dalloc<float4>(nn);
+    t.arrive = dalloc<int>(nn);
+    WNNC_CUDA(cudaMemset(t.arrive, 0, sizeof(int) * nn));
+    if (t.params.moments_fp64) t.dmom = dalloc<double>(8 * (size_t)nn);
+    t.partials = dalloc<double>(3 * (size_t)t.self.ngroups);
+    t.scalars = dalloc<double>(4);
+    WNNC_CUDA(cudaMemset(t.scalars, 0, 4 * sizeof(double)));
+    t.err_flag = dalloc<int>(1);
+    WNNC_CUDA(cudaMemset(t.err_flag, 0, sizeof(int)));
+}
+
+// Read and clear the latched device error flags.
+static wnnc_status take_device_status(Tree& t, cudaStream_t s) {
+    int f = 0;
+    WNNC_CUDA(cudaMemcpyAsync(&f, t.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    if (f) {
+        WNNC_CUDA(cudaMemsetAsync(t.err_flag, 0, sizeof(int), s));
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        if (f & kErrNonFinite) {
+            set_last_error("non-finite step length in the iteration");
+            return WNNC_ENONFINITE;
+        }
+        set_last_error("device capacity exceeded");
+        return WNNC_ECAPACITY;
+    }
+    return WNNC_OK;
+}
+
+template <class F>
+static wnnc_status guarded(F&& f) {
+    try {
+        f();
+        return WNNC_OK;
+    } catch (const Error& e) {
+        set_last_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return WNNC_ENOMEM;
+    } catch (...) {
+        set_last_error("unexpected internal error");
+        return WNNC_ECUDA;
+    }
+}
+
+static void check_params(const wnnc_tree_params& p) {
+    if (p.max_depth < 1 || p.max_depth > kMaxDepth) fail(WNNC_EINVAL, "max_depth must be in [1, 15]");
+    if (p.leaf_size < 1 || p.leaf_size > 1024) fail(WNNC_EINVAL, "leaf_size must be in [1, 1024]");
+    if (!(p.theta >= 0.f) || !std::isfinite(p.theta)) fail(WNNC_EINVAL, "theta must be finite and >= 0");
+    if (p.rep_mode != 0 && p.rep_mode != 1) fail(WNNC_EINVAL, "rep_mode must be 0 or 1");
+}
+
+static void check_w(float w) {
+    if (!(w >= 0.f) || !std::isfinite(w)) fail(WNNC_EINVAL, "w must be finite and >= 0");
+}
+
+static Tree& unwrap(const wnnc_tree* h) {
+    if (!h) fail(WNNC_EINVAL, "tree is NULL");
+    return *reinterpret_cast<Tree*>(const_cast<wnnc_tree*>(h));
+}
+
+}  // namespace wnnc
+
+using namespace wnnc;
+
+extern "C" {
+
+wnnc_status wnnc_tree_params_default(wnnc_tree_params* p) {
+    if (!p) {
+        set_last_error("params is NULL");
+        return WNNC_EINVAL;
+    }
+    p->max_depth = 15;
+    p->leaf_size = 32;
+    p->theta = 0.5f;
+    p->rep_mode = 1;
+    p->moments_fp64 = 0;
+    return WNNC_OK;
+}
+
+wnnc_status wnnc_iter_params_default(wnnc_iter_params* p) {
+    if (!p) {
+        set_last_error("params is NULL");
+        return WNNC_EINVAL;
+    }
+    p->n_iter = 40;
+    p->first_iter = 1;
+    p->last_iter = 0;
+    p->w1 = 0.002f;
+    p->w2 = 0.016f;
+    p->init = 0;
+    p->rescale = 0;
+    p->use_grad = 1;
+    p->use_wnnc = 1;
+    return WNNC_OK;
+}
+
+wnnc_status wnnc_build_tree(const float* pts, int64_t n, const wnnc_tree_params* params, void* stream,
+                            wnnc_tree** out) {
+    if (out) *out = nullptr;
+    Tree* t = nullptr;
+    wnnc_status st = guarded([&] {
+        if (!out) fail(WNNC_EINVAL, "out is NULL");
+        if (!pts) fail(WNNC_EINVAL, "pts is NULL");
+        if (n < 1) fail(WNNC_EINVAL, "n must be >= 1");
+        if (n > (int64_t)INT32_MAX / 2) fail(WNNC_EINVAL, "n too large (max 2^30 points)");
+        wnnc_tree_params p;
+        wnnc_tree_params_default(&p);
+        if (params) p = *params;
+        check_params(p);
+        t = new Tree();
+        t->n = n;
+        t->params = p;
+        WNNC_CUDA(cudaGetDevice(&t->device));
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        build_tree(*t, pts, s);
+        alloc_workspace(*t);
+        WNNC_CUDA(cudaStreamSynchronize(s));
+    });
+    if (st != WNNC_OK) {
+        if (t) {
+            cudaDeviceSynchronize();
+            free_tree(*t);
+            delete t;
+        }
+        return st;
+    }
+    *out = reinterpret_cast<wnnc_tree*>(t);
+    return WNNC_OK;
+}
+
+wnnc_status wnnc_tree_free(wnnc_tree* tree) {
+    if (!tree) return WNNC_OK;
+    return guarded([&] {
+        Tree* t = reinterpret_cast<Tree*>(tree);
+        WNNC_CUDA(cudaDeviceSynchronize());
+        free_tree(*t);
+        delete t;
+    });
+}
+
+wnnc_status wnnc_eval_w(const wnnc_tree* tree, const float* mu, float w, float* out, void* stream) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (!mu || !out) fail(WNNC_EINVAL, "mu/out is NULL");
+        check_w(w);
+        eval_w(t, mu, w, out, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wnnc_status wnnc_eval_grad(const wnnc_tree* tree, const float* mu, float w, float* out, void* stream) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (!mu || !out) fail(WNNC_EINVAL, "mu/out is NULL");
+        check_w(w);
+        eval_grad(t, mu, w, out, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wnnc_status wnnc_eval_adjoint(const wnnc_tree* tree, const float* s, float w, float* out, void* stream) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (!s || !out) fail(WNNC_EINVAL, "s/out is NULL");
+        check_w(w);
+        eval_adjoint(t, s, w, out, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wnnc_status wnnc_eval_at(const wnnc_tree* tree, const float* mu, const float* q, int64_t m, float w,
+                         int grad, float* out, void* stream) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (!mu || !q || !out) fail(WNNC_EINVAL, "mu/q/out is NULL");
+        if (m < 1) fail(WNNC_EINVAL, "m must be >= 1");
+        if (m > (int64_t)INT32_MAX / 2) fail(WNNC_EINVAL, "m too large");
+        check_w(w);
+        eval_at(t, mu, q, m, w, grad, out, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wnnc_status wnnc_iterate(wnnc_tree* tree, float* mu_inout, const float* area, const wnnc_iter_params* params,
+                         void* stream, float* stats) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (!mu_inout) fail(WNNC_EINVAL, "mu_inout is NULL");
+        wnnc_iter_params p;
+        wnnc_iter_params_default(&p);
+        if (params) p = *params;
+        const int last = p.last_iter > 0 ? p.last_iter : p.n_iter;
+        if (p.n_iter < 1) fail(WNNC_EINVAL, "n_iter must be >= 1");
+        if (p.first_iter < 1 || p.first_iter > last || last > p.n_iter)
+            fail(WNNC_EINVAL, "need 1 <= first_iter <= last_iter <= n_iter");
+        check_w(p.w1);
+        check_w(p.w2);
+        if (p.init != 0 && p.init != 1) fail(WNNC_EINVAL, "init must be 0 or 1");
+        if (p.rescale != 0 && p.rescale != 1) fail(WNNC_EINVAL, "rescale must be 0 or 1");
+        if (p.rescale == 1 && !area) fail(WNNC_EINVAL, "rescale = 1 needs area");
+        iterate(t, mu_inout, area, p, static_cast<cudaStream_t>(stream), stats);
+    });
+}
+
+wnnc_status wnnc_get_stats(const wnnc_tree* tree, int64_t* far_pairs, int64_t* near_pairs) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (far_pairs) *far_pairs = t.self.far_pairs;
+        if (near_pairs) *near_pairs = t.self.near_pairs;
+    });
+}
+
+wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, int64_t* nleaves,
+                           int64_t* ngroups, int64_t* far_entries, int64_t* near_ranges,
+                           int64_t* tnear_entries, int* depth) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (n) *n = t.n;
+        if (nnodes) *nnodes = t.nnodes;
+        if (nleaves) *nleaves = t.nleaves;
+        if (ngroups) *ngroups = t.self.ngroups;
+        if (far_entries) *far_entries = t.self.far_entries;
+        if (near_ranges) *near_ranges = t.self.near_ranges;
+        if (tnear_entries) *tnear_entries = t.tnear_entries;
+        if (depth) *depth = t.depth_reached;
+    });
+}
+
+wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node_start, int32_t* node_count,
+                             int32_t* node_depth, int32_t* node_nchild, int32_t* far_off, int32_t* far_id,
+                             int32_t* near_off, int32_t* near_rng, double* center_scale) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        WNNC_CUDA(cudaDeviceSynchronize());
+        auto cp = [](void* dst, const void* src, size_t bytes) {
+            if (dst && bytes) WNNC_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+        };
+        const TargetSet& S = t.self;
+        cp(perm, S.perm, sizeof(int64_t) * t.n);
+        cp(node_start, t.node_start, sizeof(int) * t.nnodes);
+        cp(node_count, t.node_count, sizeof(int) * t.nnodes);
+        cp(node_depth, t.node_depth, sizeof(int) * t.nnodes);
+        cp(node_nchild, t.node_nchild, sizeof(int) * t.nnodes);
+        cp(far_off, S.far_off, sizeof(int) * (S.ngroups + 1));
+        cp(far_id, S.far_id, sizeof(int) * S.far_entries);
+        cp(near_off, S.near_off, sizeof(int) * (S.ngroups + 1));
+        cp(near_rng, S.near_rng, sizeof(int2) * S.near_ranges);
+        if (center_scale) {
+            for (int k = 0; k < 3; ++k) center_scale[k] = t.center[k];
+            center_scale[3] = t.scale;
+        }
+    });
+}
+
+wnnc_status wnnc_profile_enable(wnnc_tree* tree, int enable) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        t.prof.on = enable != 0;
+    });
+}
+
+wnnc_status wnnc_profile_read(wnnc_tree* tree, int64_t* launches, double* total_ms) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        t.prof.collect();
+        for (int k = 0; k < WNNC_PROF_CLASSES; ++k) {
+            if (launches) launches[k] = t.prof.launches[k];
+            if (total_ms) total_ms[k] = t.prof.ms[k];
+        }
+    });
+}
+
+wnnc_status wnnc_profile_reset(wnnc_tree* tree) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        t.prof.reset();
+    });
+}
+
+wnnc_status wnnc_sync_status(wnnc_tree* tree, void* stream) {
+    wnnc_status dev = WNNC_OK;
+    wnnc_status st = guarded([&] {
+        Tree& t = unwrap(tree);
+        dev = take_device_status(t, static_cast<cudaStream_t>(stream));
+    });
+    return st != WNNC_OK ? st : dev;
+}
+
+const char* wnnc_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

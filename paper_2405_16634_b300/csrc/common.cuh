@@ -1,0 +1,193 @@
+// common.cuh -- shared declarations of the WNNC CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/wnnc.h"
+
+namespace wnnc {
+
+constexpr int kWarp = 32;
+constexpr int kGroup = 32;          // targets per group = one warp, one target per lane
+constexpr int kKeyBits = 45;        // 15 bits per axis -> depth 15
+constexpr int kMaxDepth = 15;
+constexpr float kInv4Pi = 0.0795774715459476678f;   // 1/(4 pi)
+
+// Device-side error flags (latched per tree, read by wnnc_sync_status).
+enum : int { kErrCapacity = 1, kErrNonFinite = 2 };
+
+// Thrown internally by host orchestration code; converted to a status at the ABI.
+struct Error {
+    wnnc_status status;
+    std::string msg;
+};
+
+void set_last_error(const std::string& msg);
+[[noreturn]] void fail(wnnc_status st, const std::string& msg);
+
+#define WNNC_CUDA(call)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            ::wnnc::fail(e_ == cudaErrorMemoryAllocation ? WNNC_ENOMEM : WNNC_ECUDA,     \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+#define WNNC_LAUNCH_CHECK() WNNC_CUDA(cudaGetLastError())
+
+// Typed device allocation that throws on failure.
+template <class T>
+T* dalloc(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    WNNC_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    return static_cast<T*>(p);
+}
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Target set: targets sorted by Morton key, cut into groups of 32, with the
+// interaction lists of each group against the source octree.
+// ---------------------------------------------------------------------------
+struct TargetSet {
+    int64_t m = 0;          // number of targets
+    int ngroups = 0;
+    int64_t* perm = nullptr;      // sorted position -> input index
+    float4* pos = nullptr;        // target offset from its group origin (x,y,z,0)
+    float4* gorig = nullptr;      // group origin (dyadic, exact in fp32)
+    double* glo = nullptr;        // group bounding boxes (3 per group), build only
+    double* ghi = nullptr;
+    int* far_off = nullptr;       // [ngroups+1]
+    int* far_id = nullptr;        // node ids, ascending per group
+    int* near_off = nullptr;      // [ngroups+1]
+    int2* near_rng = nullptr;     // merged [start,end) source ranges
+    int64_t far_entries = 0, near_ranges = 0;
+    int64_t far_pairs = 0, near_pairs = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Per-launch event timing (wnnc_profile_*).
+// ---------------------------------------------------------------------------
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[WNNC_PROF_CLASSES] = {};
+    double ms[WNNC_PROF_CLASSES] = {};
+    cudaEvent_t get();
+    void collect();       // synchronise pending records and accumulate
+    void reset();
+    ~Profiler();
+};
+
+// Brackets the launches issued while it lives with two events (when on).
+struct ProfScope {
+    Profiler* p;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(Profiler* p_, int cls_, cudaStream_t s_);
+    ~ProfScope();
+};
+
+// ---------------------------------------------------------------------------
+// The tree object behind the opaque wnnc_tree handle.
+// ---------------------------------------------------------------------------
+struct Tree {
+    int64_t n = 0;
+    wnnc_tree_params params{};
+    double center[3] = {0, 0, 0};
+    double scale = 1.0;
+    int device = 0;
+
+    // sorted sources
+    uint64_t* keys = nullptr;     // Morton keys, sorted
+    double* xs = nullptr;         // normalised coordinates, sorted (n x 3), build only
+
+    // nodes, breadth-first
+    int nnodes = 0, nleaves = 0, depth_reached = 0;
+    int* node_start = nullptr;
+    int* node_count = nullptr;
+    int* node_parent = nullptr;
+    int* node_child0 = nullptr;
+    int* node_nchild = nullptr;
+    int* node_depth = nullptr;
+    int* level_off = nullptr;     // host: first node of each level, [levels+1]
+    int nlevels = 0;
+    double* node_lo = nullptr;    // tight bounding boxes (build)
+    double* node_hi = nullptr;
+    float4* node_cell = nullptr;  // cell centre (exact) + width
+    float4* node_cent = nullptr;  // point centroid - cell centre
+    int* leaf_of = nullptr;       // sorted point -> leaf node
+
+    // the points as their own targets
+    TargetSet self;
+
+    // transposed lists (adjoint, rep_mode 1)
+    int* tfar_off = nullptr;      // [nnodes+1]
+    int* tfar_ent = nullptr;      // far-entry index (position in self.far_id), grouped by node
+    int* tnear_off = nullptr;     // [ngroups+1], per source group
+    int2* tnear_ent = nullptr;    // (target group, lane mask of the source group)
+    int64_t tnear_entries = 0;
+
+    // work buffers (sized at build)
+    float4* mu_a = nullptr;       // sorted normalised mu (two buffers)
+    float4* mu_b = nullptr;
+    float4* r_s = nullptr;        // sorted residual direction r
+    float* s_s = nullptr;         // sorted scalar field (s or adjoint input)
+    float* area_s = nullptr;      // sorted areas (rescale mode 1)
+    float4* mom = nullptr;        // node moments: (nu_x, nu_y, nu_z, sum|nu|)
+    float4* mom_x = nullptr;      // node weighted offsets (rep_mode 0): sum|nu|(x-cell), -
+    float4* node_rep = nullptr;   // representative offset from cell centre, per call
+    float4* contrib = nullptr;    // per far entry contribution (adjoint)
+    float4* vnode = nullptr;      // per node far sum (adjoint)
+    int* arrive = nullptr;        // bottom-up arrival counters (zero between launches)
+    double* dmom = nullptr;       // double-precision node moments (moments_fp64), 8 per node
+    double* partials = nullptr;   // per-group partial sums (3 x ngroups)
+    double* scalars = nullptr;    // device scalars: [0]=E [1]=rr [2]=qq [3]=alpha
+    int* err_flag = nullptr;      // device error flags
+    Profiler prof;
+};
+
+// scan / sort primitives (scan_sort.cu)
+void exclusive_scan_i32(const int* in, int* out, int64_t n, cudaStream_t s);   // out[n] = total
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s);
+// off[g] = first index i with (keys[i] >> 32) >= g, for g in [0, ng]; keys sorted.
+void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s);
+
+// tree build (tree_build.cu)
+void build_tree(Tree& t, const float* pts, cudaStream_t s);
+void build_target_set(const Tree& t, TargetSet& ts, const double* yn_unsorted, int64_t m,
+                      cudaStream_t s);
+void free_target_set(TargetSet& ts);
+void free_tree(Tree& t);
+
+// operators (operators.cu)
+enum Op : int { kOpA = 0, kOpG = 1, kOpATpaper = 2 };
+void moments(Tree& t, const float4* nu_sorted_vec, const float* nu_sorted_scalar, int rep_mode,
+             cudaStream_t s);
+void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s);
+void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s);
+void eval_adjoint(Tree& t, const float* sv, float w, float* out, cudaStream_t s);
+void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int grad, float* out,
+             cudaStream_t s);
+void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params& p,
+             cudaStream_t s, float* stats);
+
+}  // namespace wnnc

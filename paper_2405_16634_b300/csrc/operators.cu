@@ -1,0 +1,841 @@
+// operators.cu -- node moments and the treecode sums of A, G and A^T.
+//
+// Pair terms (d = x_source - x_target, r = |d|, every term zero when r < w):
+//   A  : gradPhi(x_t - x_s) . mu_s = (d . mu_s) / (4 pi r^3)             (Thm. 1, Eq. 7)
+//   G  : -HPhi(x_t - x_s) mu_s = mu_s/(4 pi r^3) - 3 d (d.mu_s)/(4 pi r^5) (Eq. 9, Eq. 10)
+//   A^T: s_s gradPhi(x_s - x_t) = -s_s d / (4 pi r^3)                    (Sec. 4.4)
+// A far node B acts as one source at its representative x_B carrying
+// nu_B = sum of its points' attributes (Eq. 11, Eq. 12).
+//
+// Layout: one warp per group of 32 Morton-consecutive targets, one target per
+// lane.  Sources (a merged near range of points, or a batch of far nodes) are
+// staged 32 at a time in shared memory, shifted into the group's local frame
+// (group origin + float offset, exact frame shifts), and every lane sums over
+// them with rsqrt and FMA chains.  The 1/(4 pi) factor is applied once.
+#include <cfloat>
+#include <utility>
+
+#include "common.cuh"
+
+namespace wnnc {
+
+namespace {
+
+constexpr int kTB = 256;
+constexpr int kGatherWarps = 4;
+
+// ---------------------------------------------------------------------------
+// Node moments, bottom-up in one launch: each leaf sums its points, then the
+// last child to arrive at a parent sums the parent's children (in child
+// order, so the result does not depend on arrival order) and climbs on.
+// No thread waits for another: a thread that is not last simply returns.
+//   mom[b]   = (sum nu, sum |nu|)        (nu = mu: 3 components; nu = s: 1)
+//   momx[b]  = sum |nu| (x - cell_b)     (only for the |nu|-weighted representative)
+// ---------------------------------------------------------------------------
+template <bool SCALAR, bool WEIGHTED, class Acc>
+__global__ void k_moments(int nnodes, const int* nstart, const int* ncount, const int* nparent,
+                          const int* nchild, const int* nchild0, const float4* ncell,
+                          const float4* spos, const float4* sgorig, const float4* nu_vec,
+                          const float* nu_s, float4* mom, float4* momx, Acc* dmom, int* arrive) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes || nchild[b] != 0) return;
+    Acc m0 = 0, m1 = 0, m2 = 0, wsum = 0, x0 = 0, x1 = 0, x2 = 0;
+    const float4 cb = ncell[b];
+    for (int j = nstart[b]; j < nstart[b] + ncount[b]; ++j) {
+        float v0, v1 = 0.f, v2 = 0.f, a;
+        if (SCALAR) {
+            v0 = nu_s[j];
+            a = fabsf(v0);
+        } else {
+            float4 v = nu_vec[j];
+            v0 = v.x; v1 = v.y; v2 = v.z;
+            a = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+        }
+        m0 += v0; m1 += v1; m2 += v2; wsum += a;
+        if (WEIGHTED) {
+            float4 p = spos[j];
+            float4 go = sgorig[j >> 5];
+            x0 += (Acc)a * (Acc)((go.x - cb.x) + p.x);
+            x1 += (Acc)a * (Acc)((go.y - cb.y) + p.y);
+            x2 += (Acc)a * (Acc)((go.z - cb.z) + p.z);
+        }
+    }
+    for (;;) {
+        mom[b] = make_float4((float)m0, (float)m1, (float)m2, (float)wsum);
+        if (WEIGHTED) momx[b] = make_float4((float)x0, (float)x1, (float)x2, 0.f);
+        if (dmom) {
+            Acc* d = dmom + 8 * (int64_t)b;
+            d[0] = m0; d[1] = m1; d[2] = m2; d[3] = wsum; d[4] = x0; d[5] = x1; d[6] = x2;
+        }
+        int p = nparent[b];
+        if (p < 0) return;
+        __threadfence();
+        int old = atomicAdd(&arrive[p], 1);
+        if (old != nchild[p] - 1) return;
+        arrive[p] = 0;   // reset for the next launch; nobody else touches it now
+        __threadfence();
+        const float4 cp = ncell[p];
+        m0 = m1 = m2 = wsum = x0 = x1 = x2 = 0;
+        for (int q = 0; q < nchild[p]; ++q) {
+            int c = nchild0[p] + q;
+            Acc c0, c1, c2, cw, cx0 = 0, cx1 = 0, cx2 = 0;
+            if (dmom) {
+                const Acc* d = dmom + 8 * (int64_t)c;
+                c0 = __ldcg(d); c1 = __ldcg(d + 1); c2 = __ldcg(d + 2); cw = __ldcg(d + 3);
+                if (WEIGHTED) { cx0 = __ldcg(d + 4); cx1 = __ldcg(d + 5); cx2 = __ldcg(d + 6); }
+            } else {
+                float4 mm = __ldcg(&mom[c]);
+                c0 = mm.x; c1 = mm.y; c2 = mm.z; cw = mm.w;
+                if (WEIGHTED) {
+                    float4 xx = __ldcg(&momx[c]);
+                    cx0 = xx.x; cx1 = xx.y; cx2 = xx.z;
+                }
+            }
+            m0 += c0; m1 += c1; m2 += c2; wsum += cw;
+            if (WEIGHTED) {
+                // re-centre the child's weighted offsets on the parent's cell
+                const float4 cc = ncell[c];
+                x0 += cx0 + cw * (Acc)(cc.x - cp.x);
+                x1 += cx1 + cw * (Acc)(cc.y - cp.y);
+                x2 += cx2 + cw * (Acc)(cc.z - cp.z);
+            }
+        }
+        b = p;
+    }
+}
+
+// Representative offsets from the cell centre: |nu|-weighted centroid where
+// sum |nu| > 0, else the point centroid.
+__global__ void k_weighted_reps(int nnodes, const float4* mom, const float4* momx,
+                                const float4* cent, float4* rep) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes) return;
+    float w = mom[b].w;
+    if (w > 0.f) {
+        float4 x = momx[b];
+        rep[b] = make_float4(x.x / w, x.y / w, x.z / w, 0.f);
+    } else {
+        rep[b] = cent[b];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather kernel
+// ---------------------------------------------------------------------------
+enum Epi : int {
+    kEpiStoreW = 0,      // out[perm[i]] = F
+    kEpiStoreGrad,       // out[perm[i]] = grad F (caller units) = -G * scale
+    kEpiStoreATpaper,    // out[perm[i]] = A^T s (caller units) = acc * scale^2
+    kEpiResidual,        // s_s[i] = 1/2 - F; partial |s|^2
+    kEpiNormSq,          // partial |F|^2
+    kEpiRescale,         // mu_out[i] = Ghat |mu_i| / |Ghat| (or sigma_i / |Ghat|)
+    kEpiStoreR,          // mu_out[i] = acc / (4 pi) (sorted, normalised); partial |.|^2
+};
+
+struct GatherArgs {
+    int ngroups;
+    int64_t m;
+    const float4* tpos;
+    const float4* tgorig;
+    const int64_t* tperm;
+    const int* far_off;
+    const int* far_id;
+    const int* near_off;
+    const int2* near_rng;
+    const float4* spos;
+    const float4* sgorig;
+    const float4* sval;       // mu (x,y,z) per sorted source point
+    const float* sval_s;      // s per sorted source point (A^T, paper mode)
+    const float4* ncell;
+    const float4* nrep;
+    const float4* nmom;
+    float w2;
+    float scale;              // output unit conversion factor
+    float* out;
+    float* s_out;
+    double* partial;
+    const float4* mu_cur;     // rescale: the field before the WNNC update
+    const float* area;        // rescale mode 1
+    float4* mu_out;
+    int rescale_mode;
+};
+
+struct Acc3 {
+    float x = 0.f, y = 0.f, z = 0.f;
+};
+
+template <int OP>
+__device__ __forceinline__ void interact(const float4& t, const float4& sp, const float4& sv, float w2,
+                                         Acc3& a) {
+    float dx = sp.x - t.x, dy = sp.y - t.y, dz = sp.z - t.z;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float ir = (r2 >= w2) ? rsqrtf(r2) : 0.f;
+    if (OP == kOpA) {
+        float ir3 = ir * ir * ir;
+        float dm = fmaf(dx, sv.x, fmaf(dy, sv.y, dz * sv.z));
+        a.x = fmaf(dm, ir3, a.x);
+    } else if (OP == kOpG) {
+        float ir2 = ir * ir;
+        float ir3 = ir2 * ir;
+        float dm = fmaf(dx, sv.x, fmaf(dy, sv.y, dz * sv.z));
+        float t3 = (3.f * dm) * (ir3 * ir2);
+        a.x = fmaf(sv.x, ir3, fmaf(-dx, t3, a.x));
+        a.y = fmaf(sv.y, ir3, fmaf(-dy, t3, a.y));
+        a.z = fmaf(sv.z, ir3, fmaf(-dz, t3, a.z));
+    } else {   // paper-mode A^T: -s d / r^3
+        float q = -sv.x * (ir * ir * ir);
+        a.x = fmaf(q, dx, a.x);
+        a.y = fmaf(q, dy, a.y);
+        a.z = fmaf(q, dz, a.z);
+    }
+}
+
+template <int OP, int EPI>
+__global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs A) {
+    __shared__ float4 sp_all[kGatherWarps][32];
+    __shared__ float4 sv_all[kGatherWarps][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kGatherWarps + wl;
+    if (g >= A.ngroups) return;
+    float4* sp = sp_all[wl];
+    float4* sv = sv_all[wl];
+    const int64_t i = (int64_t)g * kGroup + lane;
+    const bool valid = i < A.m;
+    const float4 t = valid ? A.tpos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 o = A.tgorig[g];
+    Acc3 acc;
+
+    // near field: merged ranges of source points
+    for (int q = A.near_off[g]; q < A.near_off[g + 1]; ++q) {
+        const int2 r = A.near_rng[q];
+        for (int base = r.x; base < r.y; base += 32) {
+            const int cnt = min(32, r.y - base);
+            if (lane < cnt) {
+                const int j = base + lane;
+                const float4 p = A.spos[j];
+                const float4 go = A.sgorig[j >> 5];
+                sp[lane] = make_float4((go.x - o.x) + p.x, (go.y - o.y) + p.y, (go.z - o.z) + p.z, 0.f);
+                if (OP == kOpATpaper) sv[lane] = make_float4(A.sval_s[j], 0.f, 0.f, 0.f);
+                else sv[lane] = A.sval[j];
+            }
+            __syncwarp();
+#pragma unroll 4
+            for (int k = 0; k < cnt; ++k) interact<OP>(t, sp[k], sv[k], A.w2, acc);
+            __syncwarp();
+        }
+    }
+    // far field: node representatives
+    const int f1 = A.far_off[g + 1];
+    for (int base = A.far_off[g]; base < f1; base += 32) {
+        const int cnt = min(32, f1 - base);
+        if (lane < cnt) {
+            const int b = A.far_id[base + lane];
+            const float4 c = A.ncell[b];
+            const float4 rp = A.nrep[b];
+            sp[lane] = make_float4((c.x - o.x) + rp.x, (c.y - o.y) + rp.y, (c.z - o.z) + rp.z, 0.f);
+            sv[lane] = A.nmom[b];
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < cnt; ++k) interact<OP>(t, sp[k], sv[k], A.w2, acc);
+        __syncwarp();
+    }
+
+    // epilogues
+    double part = 0.0;
+    if (EPI == kEpiStoreW) {
+        if (valid) A.out[A.tperm[i]] = acc.x * kInv4Pi;
+    } else if (EPI == kEpiStoreGrad) {
+        if (valid) {
+            const float f = -kInv4Pi * A.scale;
+            const int64_t o3 = 3 * A.tperm[i];
+            A.out[o3] = acc.x * f;
+            A.out[o3 + 1] = acc.y * f;
+            A.out[o3 + 2] = acc.z * f;
+        }
+    } else if (EPI == kEpiStoreATpaper) {
+        if (valid) {
+            const float f = kInv4Pi * A.scale;
+            const int64_t o3 = 3 * A.tperm[i];
+            A.out[o3] = acc.x * f;
+            A.out[o3 + 1] = acc.y * f;
+            A.out[o3 + 2] = acc.z * f;
+        }
+    } else if (EPI == kEpiResidual) {
+        if (valid) {
+            const float sres = 0.5f - acc.x * kInv4Pi;
+            A.s_out[i] = sres;
+            part = (double)sres * (double)sres;
+        }
+    } else if (EPI == kEpiNormSq) {
+        if (valid) {
+            const float v = acc.x * kInv4Pi;
+            part = (double)v * (double)v;
+        }
+    } else if (EPI == kEpiRescale) {
+        if (valid) {
+            const float gx = acc.x * kInv4Pi, gy = acc.y * kInv4Pi, gz = acc.z * kInv4Pi;
+            const float4 mc = A.mu_cur[i];
+            const float hn = sqrtf(gx * gx + gy * gy + gz * gz);
+            float4 res = mc;
+            if (hn > 0.f) {
+                const float len = A.rescale_mode == 1 ? A.area[i] : sqrtf(mc.x * mc.x + mc.y * mc.y + mc.z * mc.z);
+                const float f = len / hn;
+                res = make_float4(gx * f, gy * f, gz * f, 0.f);
+            }
+            A.mu_out[i] = res;
+        }
+    } else if (EPI == kEpiStoreR) {
+        if (valid) {
+            const float4 v = make_float4(acc.x * kInv4Pi, acc.y * kInv4Pi, acc.z * kInv4Pi, 0.f);
+            A.mu_out[i] = v;
+            part = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
+        }
+    }
+    if (EPI == kEpiResidual || EPI == kEpiNormSq || EPI == kEpiStoreR) {
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
+        if (lane == 0) A.partial[g] = part;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exact adjoint of the rep_mode-1 tree operator A.
+//   far:  contrib[e] = sum_{i in g} s_i (x_B - x_i) / r^3 for far entry e = (g, B)
+//   node: vnode[B]   = sum of contrib over B's entries (ascending group)
+//   near: per source group, gather over (target group, lane mask) entries, then
+//         add the far sums of every node containing the point (walk to the root).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * kGatherWarps)
+k_adj_far(int ngroups, int64_t n, const float4* pos, const float4* gorig, const float* sv,
+          const int* far_off, const int* far_id, const float4* ncell, const float4* ncent, float w2,
+          float4* contrib) {
+    __shared__ float4 tp_all[kGatherWarps][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kGatherWarps + wl;
+    if (g >= ngroups) return;
+    float4* tp = tp_all[wl];
+    const int64_t i = (int64_t)g * kGroup + lane;
+    const bool valid = i < n;
+    float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    p.w = valid ? sv[i] : 0.f;
+    tp[lane] = p;
+    __syncwarp();
+    const float4 o = gorig[g];
+    const int cnt_t = (int)min((int64_t)32, n - (int64_t)g * kGroup);
+    const int f1 = far_off[g + 1];
+    for (int base = far_off[g]; base < f1; base += 32) {
+        const int e = base + lane;
+        if (e < f1) {
+            const int b = far_id[e];
+            const float4 c = ncell[b];
+            const float4 rp = ncent[b];
+            const float bx = (c.x - o.x) + rp.x, by = (c.y - o.y) + rp.y, bz = (c.z - o.z) + rp.z;
+            float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < cnt_t; ++k) {
+                const float4 ti = tp[k];
+                const float dx = bx - ti.x, dy = by - ti.y, dz = bz - ti.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ir = (r2 >= w2) ? rsqrtf(r2) : 0.f;
+                const float q = ti.w * (ir * ir * ir);
+                ax = fmaf(q, dx, ax);
+                ay = fmaf(q, dy, ay);
+                az = fmaf(q, dz, az);
+            }
+            contrib[e] = make_float4(ax, ay, az, 0.f);
+        }
+    }
+}
+
+__global__ void k_adj_node(int nnodes, const int* tfar_off, const int* tfar_ent, const float4* contrib,
+                           float4* vnode) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nnodes) return;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int q = tfar_off[b] + lane; q < tfar_off[b + 1]; q += 32) {
+        const float4 c = contrib[tfar_ent[q]];
+        ax += c.x; ay += c.y; az += c.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    if (lane == 0) vnode[b] = make_float4(ax, ay, az, 0.f);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(32 * kGatherWarps)
+k_adj_near(int ngroups, int64_t n, const float4* pos, const float4* gorig, const float* sv,
+           const int* tnear_off, const int2* tnear_ent, const int* leaf_of, const int* nparent,
+           const float4* vnode, float w2, float scale, const int64_t* perm, float* out, float4* r_out,
+           double* partial) {
+    __shared__ float4 tp_all[kGatherWarps][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gs = blockIdx.x * kGatherWarps + wl;   // source group (outputs)
+    if (gs >= ngroups) return;
+    float4* tp = tp_all[wl];
+    const int64_t j = (int64_t)gs * kGroup + lane;
+    const bool valid = j < n;
+    const float4 xj = valid ? pos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 o = gorig[gs];
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int q = tnear_off[gs]; q < tnear_off[gs + 1]; ++q) {
+        const int2 ent = tnear_ent[q];
+        const int g = ent.x;
+        const unsigned mask = (unsigned)ent.y;
+        const int64_t i = (int64_t)g * kGroup + lane;
+        const float4 og = gorig[g];
+        if (i < n) {
+            const float4 p = pos[i];
+            tp[lane] = make_float4((og.x - o.x) + p.x, (og.y - o.y) + p.y, (og.z - o.z) + p.z, sv[i]);
+        }
+        __syncwarp();
+        if ((mask >> lane) & 1u) {
+            const int cnt_t = (int)min((int64_t)32, n - (int64_t)g * kGroup);
+#pragma unroll 4
+            for (int k = 0; k < cnt_t; ++k) {
+                const float4 ti = tp[k];
+                // s_i gradPhi(x_i - x_j) = s_i (x_j - x_i) / r^3
+                const float dx = xj.x - ti.x, dy = xj.y - ti.y, dz = xj.z - ti.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ir = (r2 >= w2) ? rsqrtf(r2) : 0.f;
+                const float qq = ti.w * (ir * ir * ir);
+                ax = fmaf(qq, dx, ax);
+                ay = fmaf(qq, dy, ay);
+                az = fmaf(qq, dz, az);
+            }
+        }
+        __syncwarp();
+    }
+    double part = 0.0;
+    if (valid) {
+        // far part: every node on the path from the point's leaf to the root
+        for (int a = leaf_of[j]; a >= 0; a = nparent[a]) {
+            const float4 v = vnode[a];
+            ax += v.x; ay += v.y; az += v.z;
+        }
+        ax *= kInv4Pi; ay *= kInv4Pi; az *= kInv4Pi;
+        if (EPI == kEpiStoreATpaper) {
+            const int64_t o3 = 3 * perm[j];
+            out[o3] = ax * scale;
+            out[o3 + 1] = ay * scale;
+            out[o3 + 2] = az * scale;
+        } else {
+            r_out[j] = make_float4(ax, ay, az, 0.f);
+            part = (double)ax * ax + (double)ay * ay + (double)az * az;
+        }
+    }
+    if (EPI != kEpiStoreATpaper) {
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
+        if (lane == 0) partial[gs] = part;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Permutations / small kernels
+// ---------------------------------------------------------------------------
+__global__ void k_perm_in_vec(const float* in, const int64_t* perm, int64_t n, float f, float4* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = 3 * perm[i];
+    out[i] = make_float4(in[j] * f, in[j + 1] * f, in[j + 2] * f, 0.f);
+}
+__global__ void k_perm_in_scalar(const float* in, const int64_t* perm, int64_t n, float f, float* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[perm[i]] * f;
+}
+__global__ void k_perm_out_vec(const float4* in, const int64_t* perm, int64_t n, float f, float* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = 3 * perm[i];
+    const float4 v = in[i];
+    out[j] = v.x * f;
+    out[j + 1] = v.y * f;
+    out[j + 2] = v.z * f;
+}
+__global__ void k_normalize_queries(const float* q, int64_t m, double cx, double cy, double cz,
+                                    double s, double* qn) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    qn[3 * i] = __dmul_rn(__dsub_rn((double)q[3 * i], cx), s);
+    qn[3 * i + 1] = __dmul_rn(__dsub_rn((double)q[3 * i + 1], cy), s);
+    qn[3 * i + 2] = __dmul_rn(__dsub_rn((double)q[3 * i + 2], cz), s);
+}
+
+// Deterministic reduction of the per-group partials and the step length of
+// Alg. 2: alpha = |r|^2 / |A r|^2 (0 if |A r| = 0).  Also records the stats.
+__global__ void k_finalize_alpha(const double* pE, const double* prr, const double* pqq, int np,
+                                 double* scalars, float* stats, float w, int* err) {
+    __shared__ double sh[3][1024];
+    double e = 0, rr = 0, qq = 0;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        e += pE[k];
+        rr += prr[k];
+        qq += pqq[k];
+    }
+    sh[0][threadIdx.x] = e;
+    sh[1][threadIdx.x] = rr;
+    sh[2][threadIdx.x] = qq;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double E = sh[0][0], R = sh[1][0], Q = sh[2][0];
+        double alpha = Q > 0.0 ? R / Q : 0.0;
+        if (!isfinite(alpha)) {
+            atomicOr(err, kErrNonFinite);
+            alpha = 0.0;
+        }
+        scalars[0] = E;
+        scalars[1] = R;
+        scalars[2] = Q;
+        scalars[3] = alpha;
+        if (stats) {
+            stats[0] = w;
+            stats[1] = (float)E;
+            stats[2] = (float)alpha;
+            stats[3] = (float)R;
+        }
+    }
+}
+
+__global__ void k_axpy(const float4* mu, const float4* r, const double* scalars, int64_t n, float4* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float a = (float)scalars[3];
+    const float4 m = mu[i], d = r[i];
+    out[i] = make_float4(fmaf(a, d.x, m.x), fmaf(a, d.y, m.y), fmaf(a, d.z, m.z), 0.f);
+}
+
+__global__ void k_stats_nograd(float* stats, float w) {
+    stats[0] = w;
+    stats[1] = 0.f;
+    stats[2] = 0.f;
+    stats[3] = 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+inline float cutoff2(float w) { return fmaxf(w * w, FLT_MIN); }
+
+GatherArgs base_args(const Tree& t, const TargetSet& ts, float w) {
+    GatherArgs a{};
+    a.ngroups = ts.ngroups;
+    a.m = ts.m;
+    a.tpos = ts.pos;
+    a.tgorig = ts.gorig;
+    a.tperm = ts.perm;
+    a.far_off = ts.far_off;
+    a.far_id = ts.far_id;
+    a.near_off = ts.near_off;
+    a.near_rng = ts.near_rng;
+    a.spos = t.self.pos;
+    a.sgorig = t.self.gorig;
+    a.ncell = t.node_cell;
+    a.nrep = t.params.rep_mode == 0 ? t.node_rep : t.node_cent;
+    a.nmom = t.mom;
+    a.w2 = cutoff2(w);
+    return a;
+}
+
+template <int OP, int EPI>
+void launch_gather(Tree& t, const GatherArgs& a, cudaStream_t s) {
+    if (a.ngroups == 0) return;
+    ProfScope ps(&t.prof, OP == kOpG ? WNNC_PROF_G : (OP == kOpA ? WNNC_PROF_A : WNNC_PROF_ADJ_NEAR), s);
+    k_gather<OP, EPI><<<ceil_div(a.ngroups, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
+    WNNC_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Profiler
+// ---------------------------------------------------------------------------
+cudaEvent_t Profiler::get() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    WNNC_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void Profiler::collect() {
+    for (auto& r : recs) {
+        WNNC_CUDA(cudaEventSynchronize(r.b));
+        float ms_ = 0.f;
+        WNNC_CUDA(cudaEventElapsedTime(&ms_, r.a, r.b));
+        launches[r.cls] += 1;
+        ms[r.cls] += ms_;
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    recs.clear();
+}
+
+void Profiler::reset() {
+    collect();
+    for (int k = 0; k < WNNC_PROF_CLASSES; ++k) {
+        launches[k] = 0;
+        ms[k] = 0.0;
+    }
+}
+
+Profiler::~Profiler() {
+    for (auto& r : recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+}
+
+ProfScope::ProfScope(Profiler* p_, int cls_, cudaStream_t s_) : p(p_), cls(cls_), s(s_) {
+    if (p && p->on) {
+        a = p->get();
+        b = p->get();
+        cudaEventRecord(a, s);
+    }
+}
+
+ProfScope::~ProfScope() {
+    if (a) {
+        cudaEventRecord(b, s);
+        p->recs.push_back({cls, a, b});
+    }
+}
+
+// Moments of nu over all nodes (and the dynamic representatives in rep_mode 0).
+void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, cudaStream_t s) {
+    ProfScope ps(&t.prof, WNNC_PROF_MOMENTS, s);
+    const int grid = ceil_div(t.nnodes, kTB);
+    const bool w = rep_mode == 0;
+    const bool fp64 = t.params.moments_fp64 != 0;
+#define WNNC_MOM(SC, WE)                                                                          \
+    if (fp64)                                                                                     \
+        k_moments<SC, WE, double><<<grid, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count,       \
+            t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.gorig,    \
+            nu_vec, nu_s, t.mom, t.mom_x, t.dmom, t.arrive);                                       \
+    else                                                                                          \
+        k_moments<SC, WE, float><<<grid, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count,        \
+            t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.gorig,    \
+            nu_vec, nu_s, t.mom, t.mom_x, (float*)nullptr, t.arrive);
+    if (nu_s) {
+        if (w) { WNNC_MOM(true, true) } else { WNNC_MOM(true, false) }
+    } else {
+        if (w) { WNNC_MOM(false, true) } else { WNNC_MOM(false, false) }
+    }
+#undef WNNC_MOM
+    WNNC_LAUNCH_CHECK();
+    if (w) {
+        k_weighted_reps<<<grid, kTB, 0, s>>>(t.nnodes, t.mom, t.mom_x, t.node_cent, t.node_rep);
+        WNNC_LAUNCH_CHECK();
+    }
+}
+
+static void perm_in_vec(Tree& t, const float* in, float f, float4* out, cudaStream_t s) {
+    ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
+    k_perm_in_vec<<<ceil_div(t.n, kTB), kTB, 0, s>>>(in, t.self.perm, t.n, f, out);
+    WNNC_LAUNCH_CHECK();
+}
+
+void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
+    const float s2 = (float)(t.scale * t.scale);
+    perm_in_vec(t, mu, s2, t.mu_a, s);
+    moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
+    GatherArgs a = base_args(t, t.self, w);
+    a.sval = t.mu_a;
+    a.out = out;
+    launch_gather<kOpA, kEpiStoreW>(t, a, s);
+}
+
+void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
+    const float s2 = (float)(t.scale * t.scale);
+    perm_in_vec(t, mu, s2, t.mu_a, s);
+    moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
+    GatherArgs a = base_args(t, t.self, w);
+    a.sval = t.mu_a;
+    a.out = out;
+    a.scale = (float)t.scale;
+    launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
+}
+
+// r_sorted <- A^T(s_sorted) in normalised units (exact transpose, rep_mode 1),
+// or stores to out (caller units) when out != nullptr.
+static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, float4* r_sorted,
+                          double* partial, cudaStream_t s) {
+    const TargetSet& S = t.self;
+    const int ng = S.ngroups;
+    const float w2 = cutoff2(w);
+    if (S.far_entries > 0) {
+        {
+            ProfScope ps(&t.prof, WNNC_PROF_ADJ_FAR, s);
+            k_adj_far<<<ceil_div(ng, kGatherWarps), 32 * kGatherWarps, 0, s>>>(
+                ng, t.n, S.pos, S.gorig, s_sorted, S.far_off, S.far_id, t.node_cell, t.node_cent, w2,
+                t.contrib);
+            WNNC_LAUNCH_CHECK();
+        }
+        ProfScope ps(&t.prof, WNNC_PROF_ADJ_NODE, s);
+        k_adj_node<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(t.nnodes, t.tfar_off, t.tfar_ent,
+                                                                         t.contrib, t.vnode);
+        WNNC_LAUNCH_CHECK();
+    } else {
+        WNNC_CUDA(cudaMemsetAsync(t.vnode, 0, sizeof(float4) * t.nnodes, s));
+    }
+    const float s2 = (float)(t.scale * t.scale);
+    ProfScope ps(&t.prof, WNNC_PROF_ADJ_NEAR, s);
+    if (out) {
+        k_adj_near<kEpiStoreATpaper><<<ceil_div(ng, kGatherWarps), 32 * kGatherWarps, 0, s>>>(
+            ng, t.n, S.pos, S.gorig, s_sorted, t.tnear_off, t.tnear_ent, t.leaf_of, t.node_parent, t.vnode,
+            w2, s2, S.perm, out, nullptr, nullptr);
+    } else {
+        k_adj_near<kEpiNormSq><<<ceil_div(ng, kGatherWarps), 32 * kGatherWarps, 0, s>>>(
+            ng, t.n, S.pos, S.gorig, s_sorted, t.tnear_off, t.tnear_ent, t.leaf_of, t.node_parent, t.vnode,
+            w2, 1.f, S.perm, nullptr, r_sorted, partial);
+    }
+    WNNC_LAUNCH_CHECK();
+}
+
+void eval_adjoint(Tree& t, const float* sv, float w, float* out, cudaStream_t s) {
+    {
+        ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
+        k_perm_in_scalar<<<ceil_div(t.n, kTB), kTB, 0, s>>>(sv, t.self.perm, t.n, 1.f, t.s_s);
+        WNNC_LAUNCH_CHECK();
+    }
+    if (t.params.rep_mode == 1) {
+        adjoint_exact(t, t.s_s, w, out, nullptr, nullptr, s);
+    } else {
+        moments(t, nullptr, t.s_s, 0, s);
+        GatherArgs a = base_args(t, t.self, w);
+        a.sval_s = t.s_s;
+        a.out = out;
+        a.scale = (float)(t.scale * t.scale);
+        launch_gather<kOpATpaper, kEpiStoreATpaper>(t, a, s);
+    }
+}
+
+void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int grad, float* out,
+             cudaStream_t s) {
+    const float s2 = (float)(t.scale * t.scale);
+    double* qn = dalloc<double>(3 * m);
+    k_normalize_queries<<<ceil_div(m, kTB), kTB, 0, s>>>(q, m, t.center[0], t.center[1], t.center[2],
+                                                         t.scale, qn);
+    WNNC_LAUNCH_CHECK();
+    TargetSet Q;
+    try {
+        build_target_set(t, Q, qn, m, s);
+    } catch (...) {
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        free_target_set(Q);
+        cudaFree(qn);
+        throw;
+    }
+    cudaFree(qn);
+    perm_in_vec(t, mu, s2, t.mu_a, s);
+    moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
+    GatherArgs a = base_args(t, Q, w);
+    a.sval = t.mu_a;
+    a.out = out;
+    a.scale = (float)t.scale;
+    if (grad) launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
+    else launch_gather<kOpA, kEpiStoreW>(t, a, s);
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    free_target_set(Q);
+}
+
+// Alg. 3 with Alg. 2, in the sorted order, normalised units.
+void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params& p, cudaStream_t s,
+             float* stats) {
+    const int64_t n = t.n;
+    const int ng = t.self.ngroups;
+    const float s2 = (float)(t.scale * t.scale);
+    const int grid_n = ceil_div(n, kTB);
+    float4* mu = t.mu_a;
+    float4* mu_alt = t.mu_b;
+    if (p.init == 1) {
+        perm_in_vec(t, mu_inout, s2, mu, s);
+    } else {
+        WNNC_CUDA(cudaMemsetAsync(mu, 0, sizeof(float4) * n, s));
+    }
+    if (p.rescale == 1) {
+        ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
+        k_perm_in_scalar<<<grid_n, kTB, 0, s>>>(area, t.self.perm, n, s2, t.area_s);
+        WNNC_LAUNCH_CHECK();
+    }
+    double* pE = t.partials;
+    double* prr = t.partials + ng;
+    double* pqq = t.partials + 2 * (int64_t)ng;
+    const int last = p.last_iter > 0 ? p.last_iter : p.n_iter;
+    const int rep_mode = t.params.rep_mode;
+    for (int it = p.first_iter; it <= last; ++it) {
+        const double wd = p.n_iter <= 1 ? (double)p.w1
+                                        : (double)p.w2 * (double)(p.n_iter - it) / (double)(p.n_iter - 1) +
+                                              (double)p.w1 * (double)(it - 1) / (double)(p.n_iter - 1);
+        const float w = (float)wd;
+        float* st = stats ? stats + 4 * (int64_t)(it - p.first_iter) : nullptr;
+        if (p.use_grad) {
+            // s = b - A mu
+            moments(t, mu, nullptr, rep_mode, s);
+            GatherArgs a = base_args(t, t.self, w);
+            a.sval = mu;
+            a.s_out = t.s_s;
+            a.partial = pE;
+            launch_gather<kOpA, kEpiResidual>(t, a, s);
+            // r = A^T s
+            if (rep_mode == 1) {
+                adjoint_exact(t, t.s_s, w, nullptr, t.r_s, prr, s);
+            } else {
+                // the paper's s-representative treecode for A^T
+                moments(t, nullptr, t.s_s, 0, s);
+                GatherArgs c = base_args(t, t.self, w);
+                c.sval_s = t.s_s;
+                c.mu_out = t.r_s;
+                c.partial = prr;
+                launch_gather<kOpATpaper, kEpiStoreR>(t, c, s);
+            }
+            // |A r|^2
+            moments(t, t.r_s, nullptr, rep_mode, s);
+            GatherArgs b = base_args(t, t.self, w);
+            b.sval = t.r_s;
+            b.partial = pqq;
+            launch_gather<kOpA, kEpiNormSq>(t, b, s);
+            {
+                ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
+                k_finalize_alpha<<<1, 1024, 0, s>>>(pE, prr, pqq, ng, t.scalars, st, w, t.err_flag);
+                WNNC_LAUNCH_CHECK();
+                k_axpy<<<grid_n, kTB, 0, s>>>(mu, t.r_s, t.scalars, n, mu_alt);
+                WNNC_LAUNCH_CHECK();
+            }
+            std::swap(mu, mu_alt);
+        } else if (st) {
+            k_stats_nograd<<<1, 1, 0, s>>>(st, w);
+            WNNC_LAUNCH_CHECK();
+        }
+        if (p.use_wnnc) {
+            moments(t, mu, nullptr, rep_mode, s);
+            GatherArgs g = base_args(t, t.self, w);
+            g.sval = mu;
+            g.mu_cur = mu;
+            g.mu_out = mu_alt;
+            g.area = t.area_s;
+            g.rescale_mode = p.rescale;
+            launch_gather<kOpG, kEpiRescale>(t, g, s);
+            std::swap(mu, mu_alt);
+        }
+    }
+    ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
+    k_perm_out_vec<<<grid_n, kTB, 0, s>>>(mu, t.self.perm, n, 1.f / s2, mu_inout);
+    WNNC_LAUNCH_CHECK();
+}
+
+}  // namespace wnnc

@@ -1,0 +1,822 @@
+// tree_build.cu -- normalisation, Morton order, octree, node boxes and
+// centroids, target groups and interaction lists (forward and transposed).
+//
+// Sec. 4.4 builds an octree that stops splitting at one point or at depth D,
+// and Alg. 4 decides, per target and node, between a far (representative)
+// interaction, recursion, and a leaf direct sum.  Here the decision is taken
+// once per group of 32 Morton-consecutive targets (one warp), against the
+// group's bounding box: node B is far for the group when the gap between the
+// two bounding boxes exceeds c * width(B).  Every target and the node's
+// representative lie inside those boxes, so each far use also passes the
+// per-target test of Alg. 4.  The test is evaluated in double precision with
+// explicit round-to-nearest operations (no contraction), so that any
+// implementation of the same rule takes identical decisions.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace wnnc {
+
+namespace {
+
+constexpr int kTB = 256;
+
+// ---------------------------------------------------------------------------
+// Normalisation (Sec. 5.1.1) and Morton keys
+// ---------------------------------------------------------------------------
+
+__global__ void k_bbox_partial(const float* pts, int64_t n, double* part) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = (double)pts[3 * i + k];
+            lo[k] = fmin(lo[k], v);
+            hi[k] = fmax(hi[k], v);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    __shared__ double s[2][3][32];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) { s[0][k][warp] = lo[k]; s[1][k][warp] = hi[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fmin(lo[k], s[0][k][w]);
+                hi[k] = fmax(hi[k], s[1][k][w]);
+            }
+        for (int k = 0; k < 3; ++k) { part[6 * blockIdx.x + k] = lo[k]; part[6 * blockIdx.x + 3 + k] = hi[k]; }
+    }
+}
+
+// centre (3) and scale: centre of the bounding box, largest half-extent -> 10/11
+__global__ void k_bbox_final(const double* part, int nparts, double* cs) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nparts; ++b)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], part[6 * b + k]);
+            hi[k] = fmax(hi[k], part[6 * b + 3 + k]);
+        }
+    double hmax = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        cs[k] = __dmul_rn(__dadd_rn(lo[k], hi[k]), 0.5);
+        double h = __dmul_rn(__dsub_rn(hi[k], lo[k]), 0.5);
+        if (h > hmax) hmax = h;
+    }
+    cs[3] = hmax > 0.0 ? (10.0 / 11.0) / hmax : 1.0;
+}
+
+__device__ __forceinline__ int64_t quant15(double v) {
+    double q = floor(__dmul_rn(__dadd_rn(v, 1.0), 16384.0));
+    q = fmin(fmax(q, 0.0), 32767.0);
+    return (int64_t)q;
+}
+
+// 45-bit key, 15 bits per axis, x the high bit of each 3-bit digit.
+__device__ __forceinline__ uint64_t morton45(double x, double y, double z) {
+    int64_t q[3] = {quant15(x), quant15(y), quant15(z)};
+    uint64_t key = 0;
+#pragma unroll
+    for (int b = 14; b >= 0; --b) {
+        uint64_t dig = (uint64_t)((((q[0] >> b) & 1) << 2) | (((q[1] >> b) & 1) << 1) | ((q[2] >> b) & 1));
+        key = (key << 3) | dig;
+    }
+    return key;
+}
+
+// Normalised coordinates (double) and Morton keys of float32 caller-unit points.
+__global__ void k_normalize_keys(const float* pts, int64_t n, const double* cs, double* xn,
+                                 uint64_t* keys, uint32_t* idx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = cs[3];
+    double v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = __dmul_rn(__dsub_rn((double)pts[3 * i + k], cs[k]), s);
+        xn[3 * i + k] = v[k];
+    }
+    keys[i] = morton45(v[0], v[1], v[2]);
+    idx[i] = (uint32_t)i;
+}
+
+__global__ void k_keys_from_xn(const double* xn, int64_t n, uint64_t* keys, uint32_t* idx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = morton45(xn[3 * i], xn[3 * i + 1], xn[3 * i + 2]);
+    idx[i] = (uint32_t)i;
+}
+
+__global__ void k_gather_sorted(const double* xn, const uint32_t* idx, int64_t n, double* xs,
+                                int64_t* perm) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = idx[i];
+    perm[i] = j;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) xs[3 * i + k] = xn[3 * j + k];
+}
+
+// ---------------------------------------------------------------------------
+// Octree, level by level (breadth-first numbering, children in digit order)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int digit_at(uint64_t key, int depth_of_parent) {
+    return (int)((key >> (3 * (14 - depth_of_parent))) & 7u);
+}
+
+// First index in [s, e) whose digit (below the parent's depth) is >= c.
+__device__ __forceinline__ int first_digit_ge(const uint64_t* keys, int s, int e, int d, int c) {
+    int lo = s, hi = e;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (digit_at(keys[mid], d) < c) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_split_count(const uint64_t* keys, const int* start, const int* count, int base,
+                              int m, int depth, int leaf_size, int max_depth, int* nkids) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int b = base + i;
+    int s = start[b], c = count[b];
+    int nk = 0;
+    if (c > leaf_size && depth < max_depth) {
+        int prev = s;
+        for (int q = 1; q <= 8; ++q) {
+            int p = q < 8 ? first_digit_ge(keys, prev, s + c, depth, q) : s + c;
+            if (p > prev) ++nk;
+            prev = p;
+        }
+    }
+    nkids[i] = nk;
+}
+
+__global__ void k_split_write(const uint64_t* keys, int* start, int* count, int* parent,
+                              int* child0, int* nchild, int* ndepth, int base, int m, int depth,
+                              int next_base, const int* koff, const int* nkids) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int b = base + i;
+    int nk = nkids[i];
+    if (nk == 0) {
+        child0[b] = -1;
+        nchild[b] = 0;
+        return;
+    }
+    int c0 = next_base + koff[i];
+    child0[b] = c0;
+    nchild[b] = nk;
+    int s = start[b], e = s + count[b];
+    int prev = s, w = 0;
+    for (int q = 1; q <= 8; ++q) {
+        int p = q < 8 ? first_digit_ge(keys, prev, e, depth, q) : e;
+        if (p > prev) {
+            int c = c0 + w++;
+            start[c] = prev;
+            count[c] = p - prev;
+            parent[c] = b;
+            ndepth[c] = depth + 1;
+        }
+        prev = p;
+    }
+}
+
+// Bounding box and point sum of the nodes of one level (deepest first).
+__global__ void k_node_boxes(const double* xs, const int* start, const int* count,
+                             const int* child0, const int* nchild, int base, int m, double* lo,
+                             double* hi, double* sum) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int b = base + i;
+    double l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double sm[3] = {0, 0, 0};
+    if (nchild[b] == 0) {
+        for (int j = start[b]; j < start[b] + count[b]; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                double v = xs[3 * (int64_t)j + k];
+                l[k] = fmin(l[k], v);
+                h[k] = fmax(h[k], v);
+                sm[k] += v;
+            }
+    } else {
+        for (int q = 0; q < nchild[b]; ++q) {
+            int c = child0[b] + q;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                l[k] = fmin(l[k], lo[3 * c + k]);
+                h[k] = fmax(h[k], hi[3 * c + k]);
+                sm[k] += sum[3 * c + k];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { lo[3 * b + k] = l[k]; hi[3 * b + k] = h[k]; sum[3 * b + k] = sm[k]; }
+}
+
+// Cell centre (exact dyadic), width, centroid offset; leaf ownership of points.
+__global__ void k_node_cells(const uint64_t* keys, const int* start, const int* count,
+                             const int* ndepth, const int* nchild, const double* sum, int nn,
+                             float4* cell, float4* cent, int* leaf_of) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nn) return;
+    int d = ndepth[b];
+    uint64_t key = keys[start[b]];
+    int q[3] = {0, 0, 0};
+    for (int bit = 14; bit >= 0; --bit) {
+        int dig = (int)((key >> (3 * bit)) & 7u);
+        q[0] = (q[0] << 1) | ((dig >> 2) & 1);
+        q[1] = (q[1] << 1) | ((dig >> 1) & 1);
+        q[2] = (q[2] << 1) | (dig & 1);
+    }
+    double width = ldexp(2.0, -d);
+    double c[3];
+    for (int k = 0; k < 3; ++k) c[k] = -1.0 + ((double)(q[k] >> (15 - d)) + 0.5) * width;
+    cell[b] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)width);
+    double inv = 1.0 / (double)count[b];
+    cent[b] = make_float4((float)(sum[3 * b] * inv - c[0]), (float)(sum[3 * b + 1] * inv - c[1]),
+                          (float)(sum[3 * b + 2] * inv - c[2]), 0.f);
+    if (nchild[b] == 0)
+        for (int j = start[b]; j < start[b] + count[b]; ++j) leaf_of[j] = b;
+}
+
+// ---------------------------------------------------------------------------
+// Target groups
+// ---------------------------------------------------------------------------
+
+// warp per group: bounding box, dyadic origin (multiple of 2^-12), offsets
+__global__ void k_group_boxes(const double* ys, int64_t m, int ng, double* glo, double* ghi,
+                              float4* gorig, float4* pos) {
+    int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    int64_t i = (int64_t)g * kGroup + lane;
+    bool valid = i < m;
+    double l[3], h[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = valid ? ys[3 * i + k] : 0.0;
+        l[k] = valid ? v : INFINITY;
+        h[k] = valid ? v : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) {
+            l[k] = fmin(l[k], __shfl_xor_sync(0xffffffffu, l[k], o));
+            h[k] = fmax(h[k], __shfl_xor_sync(0xffffffffu, h[k], o));
+        }
+    }
+    double o[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = rint(0.5 * (l[k] + h[k]) * 4096.0) / 4096.0;
+    if (lane == 0) {
+        for (int k = 0; k < 3; ++k) { glo[3 * g + k] = l[k]; ghi[3 * g + k] = h[k]; }
+        gorig[g] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
+    }
+    if (valid)
+        pos[i] = make_float4((float)(ys[3 * i] - o[0]), (float)(ys[3 * i + 1] - o[1]),
+                             (float)(ys[3 * i + 2] - o[2]), 0.f);
+}
+
+// Far test of a group box against node b (see the file comment).
+__device__ __forceinline__ bool is_far(const double* nlo, const double* nhi, const int* ndepth,
+                                       int b, const double* glo, const double* ghi, double c) {
+    double gq[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double a = __dsub_rn(nlo[3 * b + k], ghi[k]);
+        double e = __dsub_rn(glo[k], nhi[3 * b + k]);
+        double mm = a > e ? a : e;
+        gq[k] = mm > 0.0 ? mm : 0.0;
+    }
+    double gx = __dmul_rn(gq[0], gq[0]), gy = __dmul_rn(gq[1], gq[1]), gz = __dmul_rn(gq[2], gq[2]);
+    double d2 = __dadd_rn(__dadd_rn(gx, gy), gz);
+    double cw = __dmul_rn(c, ldexp(2.0, -ndepth[b]));
+    return d2 > __dmul_rn(cw, cw);
+}
+
+constexpr int kTravWarps = 2;
+constexpr int kStack = 4096;
+
+// Warp-cooperative traversal of the octree for one target group.  Pass 0
+// counts far nodes and near leaves; pass 1 writes keys (group<<32 | node) for
+// far entries and (group<<32 | first point) for near leaves, unsorted within
+// the group.  Up to 32 nodes are tested at once; children of opened nodes are
+// pushed on a per-warp shared stack whose capacity is checked before a push.
+__global__ void __launch_bounds__(32 * kTravWarps)
+k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* nchild,
+           const int* child0, const int* nstart, const double* glo, const double* ghi, int ng,
+           double theta, int pass, int* far_cnt, int* near_cnt, const int* far_off,
+           const int* near_off, uint64_t* far_keys, uint64_t* near_keys, uint32_t* near_vals,
+           int* err) {
+    __shared__ int stack[kTravWarps][kStack];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kTravWarps + wl;
+    if (g >= ng) return;
+    const unsigned lt = (1u << lane) - 1u;
+    double bl[3], bh[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { bl[k] = glo[3 * g + k]; bh[k] = ghi[3 * g + k]; }
+    const double c = 1.0 / theta;
+    int* st = stack[wl];
+    if (lane == 0) st[0] = 0;
+    __syncwarp();
+    int top = 1, nfar = 0, nnear = 0;
+    const int fo = pass ? far_off[g] : 0, no = pass ? near_off[g] : 0;
+    while (top > 0) {
+        int take = min(top, 32);
+        int b = lane < take ? st[top - take + lane] : -1;
+        top -= take;
+        __syncwarp();
+        bool far = false, leaf = false, open = false;
+        if (b >= 0) {
+            far = is_far(nlo, nhi, ndepth, b, bl, bh, c);
+            if (!far) {
+                if (nchild[b] == 0) leaf = true; else open = true;
+            }
+        }
+        unsigned fm = __ballot_sync(0xffffffffu, far), lm = __ballot_sync(0xffffffffu, leaf);
+        if (pass) {
+            if (far) far_keys[fo + nfar + __popc(fm & lt)] = ((uint64_t)g << 32) | (uint32_t)b;
+            if (leaf) {
+                int p = no + nnear + __popc(lm & lt);
+                near_keys[p] = ((uint64_t)g << 32) | (uint32_t)nstart[b];
+                near_vals[p] = (uint32_t)b;
+            }
+        }
+        nfar += __popc(fm);
+        nnear += __popc(lm);
+        int nc = open ? nchild[b] : 0;
+        int inc = nc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        int total = __shfl_sync(0xffffffffu, inc, 31);
+        if (top + total > kStack) {
+            if (lane == 0) atomicOr(err, kErrCapacity);
+            break;
+        }
+        if (open) {
+            int c0 = child0[b], p = top + inc - nc;
+            for (int q = 0; q < nc; ++q) st[p + q] = c0 + q;
+        }
+        top += total;
+        __syncwarp();
+    }
+    if (!pass && lane == 0) {
+        far_cnt[g] = nfar;
+        near_cnt[g] = nnear;
+    }
+}
+
+// theta = 0: every leaf is near for every group (one merged range [0, n)).
+__global__ void k_all_near(int ng, int n, int* near_off, int2* rng) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > ng) return;
+    near_off[g] = g;
+    if (g < ng) rng[g] = make_int2(0, n);
+}
+
+__global__ void k_low32(const uint64_t* keys, int64_t n, int* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int)(uint32_t)(keys[i] & 0xffffffffu);
+}
+
+// Near leaves (sorted by group, then first point) -> merged ranges.
+// head[e] = 1 where entry e starts a range (first of its group, or not
+// contiguous with the previous leaf).
+__global__ void k_near_heads(const uint64_t* keys, const uint32_t* leaf, int64_t n,
+                             const int* ncount, int* head) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int h = 1;
+    if (e > 0 && (keys[e] >> 32) == (keys[e - 1] >> 32)) {
+        uint32_t prev = leaf[e - 1];
+        int prev_end = (int)(keys[e - 1] & 0xffffffffu) + ncount[prev];
+        if (prev_end == (int)(keys[e] & 0xffffffffu)) h = 0;
+    }
+    head[e] = h;
+}
+
+// hscan = exclusive scan of head over n+1 entries (head[n] = 1 sentinel).
+// Entry e belongs to range hscan[e+1]-1; it starts it if head[e], and ends
+// it if head[e+1].
+__global__ void k_near_ranges(const uint64_t* keys, const uint32_t* leaf, int64_t n,
+                              const int* ncount, const int* hscan, int2* rng) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int r = hscan[e + 1] - 1;
+    int s = (int)(keys[e] & 0xffffffffu);
+    if (hscan[e + 1] != hscan[e]) rng[r].x = s;
+    if (hscan[e + 2] - hscan[e + 1] == 1) rng[r].y = s + ncount[leaf[e]];
+}
+
+__global__ void k_gather_i32(const int* src, const int* idx, int n, int* dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+// Interaction pair counts: far pairs = sum_g |g| * far(g), near = sum_g |g| * sum |range|
+__global__ void k_pair_counts(int ng, int64_t m, const int* far_off, const int* near_off,
+                              const int2* rng, unsigned long long* out) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    int64_t sz = min((int64_t)kGroup, m - (int64_t)g * kGroup);
+    int64_t nf = far_off[g + 1] - far_off[g];
+    int64_t nn = 0;
+    for (int q = near_off[g]; q < near_off[g + 1]; ++q) nn += rng[q].y - rng[q].x;
+    atomicAdd(&out[0], (unsigned long long)(sz * nf));
+    atomicAdd(&out[1], (unsigned long long)(sz * nn));
+}
+
+// Transposed far lists: key (node << 32 | entry index).
+__global__ void k_tfar_keys(const int* far_id, int64_t nent, uint64_t* keys) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nent) keys[e] = ((uint64_t)(uint32_t)far_id[e] << 32) | (uint32_t)e;
+}
+
+// Transposed near entries: for each merged range of target group g, the source
+// groups it overlaps, with the mask of overlapped lanes.
+__global__ void k_tnear_count(const int2* rng, int64_t nr, int* cnt) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nr) return;
+    int2 r = rng[q];
+    cnt[q] = r.y > r.x ? (((r.y - 1) >> 5) - (r.x >> 5) + 1) : 0;
+}
+
+__global__ void k_tnear_fill(const int2* rng, const int* near_off, int ng, const int* cnt_off,
+                             uint64_t* keys, uint32_t* masks) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    for (int q = near_off[g]; q < near_off[g + 1]; ++q) {
+        int2 r = rng[q];
+        if (r.y <= r.x) continue;
+        int p = cnt_off[q];
+        for (int sg = r.x >> 5; sg <= (r.y - 1) >> 5; ++sg, ++p) {
+            int lo = max(r.x, sg * 32) - sg * 32, hi = min(r.y, sg * 32 + 32) - sg * 32;
+            uint32_t m = (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+            keys[p] = ((uint64_t)(uint32_t)sg << 32) | (uint32_t)g;
+            masks[p] = m;
+        }
+    }
+}
+
+__global__ void k_key_heads(const uint64_t* keys, int64_t n, int* head) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
+}
+
+// Equal (source group, target group) keys: OR their masks into one entry.
+__global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* masks, int64_t n,
+                              const int* head_scan, int2* ent, uint64_t* ukeys) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    if (e > 0 && keys[e] == keys[e - 1]) return;
+    uint32_t m = 0;
+    for (int64_t f = e; f < n && keys[f] == keys[e]; ++f) m |= masks[f];
+    int r = head_scan[e];
+    ent[r] = make_int2((int)(uint32_t)(keys[e] & 0xffffffffu), (int)m);
+    ukeys[r] = keys[e];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host orchestration
+// ---------------------------------------------------------------------------
+
+static int read_int(const int* dptr, cudaStream_t s) {
+    int v = 0;
+    WNNC_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    return v;
+}
+
+static int bits_for(int64_t v) {
+    int b = 0;
+    while ((int64_t(1) << b) <= v) ++b;
+    return b;
+}
+
+void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m, cudaStream_t s) {
+    ts.m = m;
+    ts.ngroups = ceil_div(m, kGroup);
+    const int ng = ts.ngroups;
+    // Morton order of the targets
+    uint64_t* keys = dalloc<uint64_t>(m);
+    uint32_t* idx = dalloc<uint32_t>(m);
+    k_keys_from_xn<<<ceil_div(m, kTB), kTB, 0, s>>>(yn, m, keys, idx);
+    WNNC_LAUNCH_CHECK();
+    radix_sort_pairs(keys, idx, m, kKeyBits, s);
+    double* ys = dalloc<double>(3 * m);
+    ts.perm = dalloc<int64_t>(m);
+    k_gather_sorted<<<ceil_div(m, kTB), kTB, 0, s>>>(yn, idx, m, ys, ts.perm);
+    WNNC_LAUNCH_CHECK();
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    cudaFree(keys);
+    cudaFree(idx);
+    // groups
+    ts.glo = dalloc<double>(3 * (size_t)ng);
+    ts.ghi = dalloc<double>(3 * (size_t)ng);
+    ts.gorig = dalloc<float4>(ng);
+    ts.pos = dalloc<float4>(m);
+    k_group_boxes<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(ys, m, ng, ts.glo, ts.ghi, ts.gorig, ts.pos);
+    WNNC_LAUNCH_CHECK();
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    cudaFree(ys);
+
+    ts.far_off = dalloc<int>(ng + 1);
+    ts.near_off = dalloc<int>(ng + 1);
+    const double theta = (double)t.params.theta;
+    if (theta <= 0.0) {
+        ts.far_entries = 0;
+        ts.far_id = dalloc<int>(1);
+        WNNC_CUDA(cudaMemsetAsync(ts.far_off, 0, sizeof(int) * (ng + 1), s));
+        ts.near_rng = dalloc<int2>(ng);
+        ts.near_ranges = ng;
+        k_all_near<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(ng, (int)t.n, ts.near_off, ts.near_rng);
+        WNNC_LAUNCH_CHECK();
+    } else {
+        int* far_cnt = dalloc<int>(ng + 1);
+        int* near_cnt = dalloc<int>(ng + 1);
+        int* leaf_off = dalloc<int>(ng + 1);
+        int* err = dalloc<int>(1);
+        WNNC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        const int tgrid = ceil_div(ng, kTravWarps);
+        k_traverse<<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_depth, t.node_nchild,
+                                                    t.node_child0, t.node_start, ts.glo, ts.ghi, ng, theta, 0,
+                                                    far_cnt, near_cnt, nullptr, nullptr, nullptr, nullptr,
+                                                    nullptr, err);
+        WNNC_LAUNCH_CHECK();
+        if (read_int(err, s)) {
+            cudaFree(far_cnt); cudaFree(near_cnt); cudaFree(leaf_off); cudaFree(err);
+            fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
+        }
+        exclusive_scan_i32(far_cnt, ts.far_off, ng, s);
+        exclusive_scan_i32(near_cnt, leaf_off, ng, s);
+        int nfar = read_int(ts.far_off + ng, s);
+        int nleafent = read_int(leaf_off + ng, s);
+        uint64_t* fkeys = dalloc<uint64_t>(nfar);
+        uint64_t* nkeys = dalloc<uint64_t>(nleafent);
+        uint32_t* nvals = dalloc<uint32_t>(nleafent);
+        k_traverse<<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_depth, t.node_nchild,
+                                                    t.node_child0, t.node_start, ts.glo, ts.ghi, ng, theta, 1,
+                                                    nullptr, nullptr, ts.far_off, leaf_off, fkeys, nkeys,
+                                                    nvals, err);
+        WNNC_LAUNCH_CHECK();
+        int gbits = bits_for(ng);
+        radix_sort_pairs(fkeys, nullptr, nfar, 32 + gbits, s);
+        radix_sort_pairs(nkeys, nvals, nleafent, 32 + gbits, s);
+        ts.far_entries = nfar;
+        ts.far_id = dalloc<int>(nfar);
+        if (nfar) {
+            k_low32<<<ceil_div(nfar, kTB), kTB, 0, s>>>(fkeys, nfar, ts.far_id);
+            WNNC_LAUNCH_CHECK();
+        }
+        // merge consecutive near leaves into ranges
+        int* head = dalloc<int>(nleafent + 2);
+        int* hscan = dalloc<int>(nleafent + 2);
+        if (nleafent) {
+            k_near_heads<<<ceil_div(nleafent, kTB), kTB, 0, s>>>(nkeys, nvals, nleafent, t.node_count, head);
+            WNNC_LAUNCH_CHECK();
+        }
+        {
+            // sentinel head[n] = 1 so that the last entry closes its range
+            int one = 1;
+            WNNC_CUDA(cudaMemcpyAsync(head + nleafent, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+            WNNC_CUDA(cudaStreamSynchronize(s));
+        }
+        exclusive_scan_i32(head, hscan, nleafent + 1, s);
+        int nr = read_int(hscan + nleafent, s);   // heads among the real entries
+        ts.near_ranges = nr;
+        ts.near_rng = dalloc<int2>(nr);
+        if (nleafent) {
+            k_near_ranges<<<ceil_div(nleafent, kTB), kTB, 0, s>>>(nkeys, nvals, nleafent, t.node_count, hscan,
+                                                                 ts.near_rng);
+            WNNC_LAUNCH_CHECK();
+        }
+        // range offsets per group = number of heads before the group's first leaf entry
+        k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(hscan, leaf_off, ng + 1, ts.near_off);
+        WNNC_LAUNCH_CHECK();
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        cudaFree(fkeys); cudaFree(nkeys); cudaFree(nvals); cudaFree(head); cudaFree(hscan);
+        cudaFree(far_cnt); cudaFree(near_cnt); cudaFree(leaf_off); cudaFree(err);
+    }
+    unsigned long long* pc = dalloc<unsigned long long>(2);
+    WNNC_CUDA(cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), s));
+    k_pair_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ng, m, ts.far_off, ts.near_off, ts.near_rng, pc);
+    WNNC_LAUNCH_CHECK();
+    unsigned long long hc[2];
+    WNNC_CUDA(cudaMemcpyAsync(hc, pc, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    cudaFree(pc);
+    ts.far_pairs = (int64_t)hc[0];
+    ts.near_pairs = (int64_t)hc[1];
+}
+
+void free_target_set(TargetSet& ts) {
+    dfree(ts.perm); dfree(ts.pos); dfree(ts.gorig); dfree(ts.glo); dfree(ts.ghi);
+    dfree(ts.far_off); dfree(ts.far_id); dfree(ts.near_off); dfree(ts.near_rng);
+}
+
+static void grow_nodes(Tree& t, int& cap, int need) {
+    if (need <= cap) return;
+    int ncap = std::max(need, 2 * cap);
+    auto grow = [&](int*& p) {
+        int* q = dalloc<int>(ncap);
+        WNNC_CUDA(cudaMemcpy(q, p, sizeof(int) * cap, cudaMemcpyDeviceToDevice));
+        cudaFree(p);
+        p = q;
+    };
+    grow(t.node_start); grow(t.node_count); grow(t.node_parent);
+    grow(t.node_child0); grow(t.node_nchild); grow(t.node_depth);
+    cap = ncap;
+}
+
+void build_tree(Tree& t, const float* pts, cudaStream_t s) {
+    const int64_t n = t.n;
+    const wnnc_tree_params& P = t.params;
+    // --- normalisation and Morton order ---
+    const int nparts = (int)std::min<int64_t>(1024, ceil_div(n, kTB));
+    double* part = dalloc<double>(6 * nparts);
+    double* cs = dalloc<double>(4);
+    k_bbox_partial<<<nparts, kTB, 0, s>>>(pts, n, part);
+    WNNC_LAUNCH_CHECK();
+    k_bbox_final<<<1, 1, 0, s>>>(part, nparts, cs);
+    WNNC_LAUNCH_CHECK();
+    double hcs[4];
+    WNNC_CUDA(cudaMemcpyAsync(hcs, cs, sizeof(hcs), cudaMemcpyDeviceToHost, s));
+    double* xn = dalloc<double>(3 * n);
+    uint32_t* idx = dalloc<uint32_t>(n);
+    t.keys = dalloc<uint64_t>(n);
+    k_normalize_keys<<<ceil_div(n, kTB), kTB, 0, s>>>(pts, n, cs, xn, t.keys, idx);
+    WNNC_LAUNCH_CHECK();
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < 3; ++k) t.center[k] = hcs[k];
+    t.scale = hcs[3];
+    radix_sort_pairs(t.keys, idx, n, kKeyBits, s);
+    t.xs = dalloc<double>(3 * n);
+    int64_t* perm_tmp = dalloc<int64_t>(n);
+    k_gather_sorted<<<ceil_div(n, kTB), kTB, 0, s>>>(xn, idx, n, t.xs, perm_tmp);
+    WNNC_LAUNCH_CHECK();
+
+    // --- octree, breadth-first by level ---
+    int cap = (int)std::min<int64_t>(INT32_MAX / 2, 2 * n + 64);
+    t.node_start = dalloc<int>(cap); t.node_count = dalloc<int>(cap); t.node_parent = dalloc<int>(cap);
+    t.node_child0 = dalloc<int>(cap); t.node_nchild = dalloc<int>(cap); t.node_depth = dalloc<int>(cap);
+    {
+        int h0 = 0, hn = (int)n, hp = -1;
+        WNNC_CUDA(cudaMemcpy(t.node_start, &h0, sizeof(int), cudaMemcpyHostToDevice));
+        WNNC_CUDA(cudaMemcpy(t.node_count, &hn, sizeof(int), cudaMemcpyHostToDevice));
+        WNNC_CUDA(cudaMemcpy(t.node_parent, &hp, sizeof(int), cudaMemcpyHostToDevice));
+        WNNC_CUDA(cudaMemcpy(t.node_depth, &h0, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    std::vector<int> level_off = {0, 1};
+    int base = 0, m = 1, depth = 0, total_nodes = 1;
+    int* nkids = dalloc<int>(n + 1);
+    int* koff = dalloc<int>(n + 2);
+    while (m > 0) {
+        k_split_count<<<ceil_div(m, kTB), kTB, 0, s>>>(t.keys, t.node_start, t.node_count, base, m, depth,
+                                                      P.leaf_size, P.max_depth, nkids);
+        WNNC_LAUNCH_CHECK();
+        exclusive_scan_i32(nkids, koff, m, s);
+        int nnext = read_int(koff + m, s);
+        grow_nodes(t, cap, total_nodes + nnext);
+        k_split_write<<<ceil_div(m, kTB), kTB, 0, s>>>(t.keys, t.node_start, t.node_count, t.node_parent,
+                                                      t.node_child0, t.node_nchild, t.node_depth, base, m,
+                                                      depth, total_nodes, koff, nkids);
+        WNNC_LAUNCH_CHECK();
+        base = total_nodes;
+        total_nodes += nnext;
+        m = nnext;
+        if (m > 0) {
+            level_off.push_back(total_nodes);
+            ++depth;
+        }
+    }
+    cudaFree(nkids);
+    cudaFree(koff);
+    t.nnodes = total_nodes;
+    t.nlevels = (int)level_off.size() - 1;
+    t.depth_reached = t.nlevels - 1;
+    t.level_off = new int[level_off.size()];
+    std::copy(level_off.begin(), level_off.end(), t.level_off);
+
+    // --- boxes and centroids, deepest level first ---
+    t.node_lo = dalloc<double>(3 * (size_t)t.nnodes);
+    t.node_hi = dalloc<double>(3 * (size_t)t.nnodes);
+    double* sum = dalloc<double>(3 * (size_t)t.nnodes);
+    for (int L = t.nlevels - 1; L >= 0; --L) {
+        int b0 = t.level_off[L], mm = t.level_off[L + 1] - b0;
+        k_node_boxes<<<ceil_div(mm, kTB), kTB, 0, s>>>(t.xs, t.node_start, t.node_count, t.node_child0,
+                                                      t.node_nchild, b0, mm, t.node_lo, t.node_hi, sum);
+        WNNC_LAUNCH_CHECK();
+    }
+    t.node_cell = dalloc<float4>(t.nnodes);
+    t.node_cent = dalloc<float4>(t.nnodes);
+    t.leaf_of = dalloc<int>(n);
+    k_node_cells<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.keys, t.node_start, t.node_count, t.node_depth,
+                                                        t.node_nchild, sum, t.nnodes, t.node_cell,
+                                                        t.node_cent, t.leaf_of);
+    WNNC_LAUNCH_CHECK();
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    cudaFree(sum);
+    {
+        std::vector<int> nc(t.nnodes);
+        WNNC_CUDA(cudaMemcpy(nc.data(), t.node_nchild, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
+        t.nleaves = (int)std::count(nc.begin(), nc.end(), 0);
+    }
+
+    // --- the points as targets: same Morton order as the sources ---
+    build_target_set(t, t.self, xn, n, s);
+    cudaFree(xn);
+    cudaFree(idx);
+    cudaFree(perm_tmp);
+    cudaFree(part);
+    cudaFree(cs);
+
+    // --- transposed lists for the adjoint ---
+    const TargetSet& S = t.self;
+    const int ng = S.ngroups;
+    t.tfar_off = dalloc<int>(t.nnodes + 1);
+    {
+        int64_t ne = S.far_entries;
+        uint64_t* k = dalloc<uint64_t>(ne);
+        if (ne) {
+            k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, k);
+            WNNC_LAUNCH_CHECK();
+        }
+        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes), s);
+        t.tfar_ent = dalloc<int>(ne);
+        if (ne) {
+            k_low32<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, t.tfar_ent);
+            WNNC_LAUNCH_CHECK();
+        }
+        segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        cudaFree(k);
+    }
+    {
+        int64_t nr = S.near_ranges;
+        int* cnt = dalloc<int>(nr + 1);
+        int* coff = dalloc<int>(nr + 2);
+        if (nr) {
+            k_tnear_count<<<ceil_div(nr, kTB), kTB, 0, s>>>(S.near_rng, nr, cnt);
+            WNNC_LAUNCH_CHECK();
+        }
+        exclusive_scan_i32(cnt, coff, nr, s);
+        int ne = read_int(coff + nr, s);
+        uint64_t* k = dalloc<uint64_t>(ne);
+        uint32_t* msk = dalloc<uint32_t>(ne);
+        k_tnear_fill<<<ceil_div(ng, kTB), kTB, 0, s>>>(S.near_rng, S.near_off, ng, coff, k, msk);
+        WNNC_LAUNCH_CHECK();
+        radix_sort_pairs(k, msk, ne, 32 + bits_for(ng), s);
+        int* head = dalloc<int>(ne + 1);
+        int* hscan = dalloc<int>(ne + 2);
+        if (ne) {
+            k_key_heads<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, head);
+            WNNC_LAUNCH_CHECK();
+        }
+        exclusive_scan_i32(head, hscan, ne, s);
+        int nu = read_int(hscan + ne, s);
+        t.tnear_entries = nu;
+        t.tnear_ent = dalloc<int2>(nu);
+        uint64_t* uk = dalloc<uint64_t>(nu);
+        if (ne) {
+            k_tnear_merge<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, msk, ne, hscan, t.tnear_ent, uk);
+            WNNC_LAUNCH_CHECK();
+        }
+        t.tnear_off = dalloc<int>(ng + 1);
+        segment_offsets_hi32(uk, nu, t.tnear_off, ng, s);
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        cudaFree(cnt); cudaFree(coff); cudaFree(k); cudaFree(msk); cudaFree(head); cudaFree(hscan);
+        cudaFree(uk);
+    }
+}
+
+void free_tree(Tree& t) {
+    dfree(t.keys); dfree(t.xs);
+    dfree(t.node_start); dfree(t.node_count); dfree(t.node_parent); dfree(t.node_child0);
+    dfree(t.node_nchild); dfree(t.node_depth); dfree(t.node_lo); dfree(t.node_hi);
+    dfree(t.node_cell); dfree(t.node_cent); dfree(t.leaf_of);
+    delete[] t.level_off;
+    t.level_off = nullptr;
+    free_target_set(t.self);
+    dfree(t.tfar_off); dfree(t.tfar_ent); dfree(t.tnear_off); dfree(t.tnear_ent);
+    dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
+    dfree(t.mom_x); dfree(t.dmom); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode); dfree(t.arrive);
+    dfree(t.partials); dfree(t.scalars); dfree(t.err_flag);
+}
+
+}  // namespace wnnc

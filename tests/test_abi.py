@@ -1,0 +1,49 @@
+"""The C-ABI library loads and exports every entry point that include/wnnc.h
+declares; argument errors are reported as status codes (no GPU needed)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "wnnc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(wnnc_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("wnnc_build_tree", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
+                     "wnnc_iterate", "wnnc_tree_free", "wnnc_get_stats", "wnnc_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2405_16634_b300 as W
+    W.build_if_needed()
+    L = W.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_defaults_and_argument_errors_without_gpu():
+    import paper_2405_16634_b300 as W
+    W.build_if_needed()
+    L = W.lib()
+    p = W.default_tree_params()
+    assert (p.max_depth, p.leaf_size, p.rep_mode, p.moments_fp64) == (15, 32, 1, 0)
+    assert abs(p.theta - 0.5) < 1e-7
+    q = W.default_iter_params()
+    assert (q.n_iter, q.first_iter, q.last_iter, q.init, q.rescale, q.use_grad, q.use_wnnc) == \
+        (40, 1, 0, 0, 0, 1, 1)
+    assert abs(q.w1 - 0.002) < 1e-9 and abs(q.w2 - 0.016) < 1e-9
+    assert L.wnnc_tree_params_default(None) == 1
+    h = ctypes.c_void_p()
+    assert L.wnnc_build_tree(None, 10, None, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert b"NULL" in L.wnnc_last_error()
+    assert L.wnnc_eval_w(None, None, ctypes.c_float(0.0), None, None) == 1
+    assert L.wnnc_tree_free(None) == 0

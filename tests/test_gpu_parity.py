@@ -1,0 +1,342 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance (FP32 kernels vs FP64 oracle): each output element may differ by
+1e-4 times the RMS of the oracle's output, plus that target's cut-off
+ambiguity budget (the terms whose pair distance lies within 1e-5 w^2 of w^2,
+where the kernel's FP32 test may fall on the other side).  Integer work
+(sort order, octree, interaction lists) must match exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import OP_A, OP_AT, OP_G
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+AMB = 1e-5
+
+
+def _wnnc():
+    import paper_2405_16634_b300 as W
+    return W
+
+
+def f32(x):
+    """theta is a float32 parameter of the library; give the oracle the same value."""
+    return float(np.float32(x))
+
+
+def check_close(gpu, ora, amb=None, tol=TOL, what=""):
+    gpu = np.asarray(gpu, np.float64)
+    ora = np.asarray(ora, np.float64)
+    rms = np.sqrt(np.mean(ora ** 2))
+    err = np.abs(gpu - ora)
+    if err.ndim == 2:
+        err = err.max(1)
+    bound = tol * rms + (0.0 if amb is None else amb * (1 + 1e-6))
+    bad = err > bound
+    assert not bad.any(), (f"{what}: {bad.sum()} outputs out of tolerance; worst err/rms = "
+                           f"{(err / rms).max():.3e}")
+    return float((err / rms).max())
+
+
+@pytest.fixture(scope="module")
+def union5k():
+    c = synth.union_cloud(5003, 77, n_tori=1, n_ellipsoids=2, noise=0.002)
+    rng = np.random.default_rng(5)
+    mu = (synth.random_unit_vectors(len(c.points), 6) * (c.area / len(c.points))).astype(np.float32)
+    s = rng.standard_normal(len(c.points)).astype(np.float32)
+    return c, mu, s
+
+
+def test_library_is_the_cuda_build():
+    W = _wnnc()
+    L = W.lib()
+    assert L._name.endswith("libwnnc.so")
+    assert torch.cuda.is_available()
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
+def test_tree_and_lists_match_oracle_exactly(theta):
+    W = _wnnc()
+    c = synth.config_cloud("union50k", n=20000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta)
+    e = t.export()
+    xn, ctr, s = oracle.normalize(c.points)
+    assert np.array_equal(e["center_scale"], np.concatenate([ctr, [s]]))
+    ot = oracle.Tree(xn, f32(theta))
+    assert np.array_equal(e["perm"], ot.perm())
+    nd = ot.nodes()
+    assert np.array_equal(e["node_start"], nd["start"])
+    assert np.array_equal(e["node_count"], nd["count"])
+    assert np.array_equal(e["node_depth"], nd["depth"])
+    assert np.array_equal(e["node_nchild"], nd["nchild"])
+    fo, fi, no, ni = ot.lists()
+    assert np.array_equal(e["far_off"], fo)
+    ng = len(fo) - 1
+    for g in range(ng):
+        assert np.array_equal(e["far_id"][fo[g]:fo[g + 1]], np.sort(fi[fo[g]:fo[g + 1]]))
+    # near: GPU merged ranges cover exactly the oracle's near leaves
+    for g in range(0, ng, 7):
+        leaves = ni[no[g]:no[g + 1]]
+        cover = np.zeros(len(c.points), bool)
+        for b in leaves:
+            cover[nd["start"][b]:nd["start"][b] + nd["count"][b]] = True
+        gcover = np.zeros(len(c.points), bool)
+        for r in e["near_rng"][e["near_off"][g]:e["near_off"][g + 1]]:
+            assert not gcover[r[0]:r[1]].any()
+            gcover[r[0]:r[1]] = True
+        assert np.array_equal(cover, gcover), g
+    far_pairs, near_pairs = t.stats()
+    oc = ot.counts()
+    assert (far_pairs, near_pairs) == (oc[2], oc[3])
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5])
+def test_operators_match_oracle(union5k, theta):
+    W = _wnnc()
+    c, mu, s = union5k
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta)
+    for w in (0.002, 0.004, 0.016):
+        F = t.eval_w(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Fo, amb = oracle.eval_op(OP_A, c.points, mu, w, theta=f32(theta), amb_tol=AMB)
+        check_close(F, Fo, amb, what=f"A theta={theta} w={w}")
+        Gr = t.eval_grad(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Go, amb = oracle.eval_op(OP_G, c.points, mu, w, theta=f32(theta), amb_tol=AMB)
+        check_close(Gr, Go, amb, what=f"grad theta={theta} w={w}")
+        T = t.eval_adjoint(torch.from_numpy(s).cuda(), w).cpu().numpy()
+        To, amb = oracle.eval_op(OP_AT, c.points, s, w, theta=f32(theta), amb_tol=AMB)
+        check_close(T, To, amb, what=f"AT theta={theta} w={w}")
+
+
+def test_paper_representatives_match_oracle(union5k):
+    """rep_mode 0: |mu|-weighted node representatives (Eq. 11) and the
+    s-representative A^T treecode, against the oracle's same-rule treecode."""
+    W = _wnnc()
+    c, mu, s = union5k
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, rep_mode=0)
+    for moments_fp64 in (False, True):
+        t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, rep_mode=0, moments_fp64=moments_fp64)
+        w = 0.004
+        F = t.eval_w(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Fo, amb = oracle.eval_op(OP_A, c.points, mu, w, theta=0.5, rep_mode=0, amb_tol=AMB)
+        check_close(F, Fo, amb, tol=3e-4, what="A rep0")
+        G = t.eval_grad(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Go, amb = oracle.eval_op(OP_G, c.points, mu, w, theta=0.5, rep_mode=0, amb_tol=AMB)
+        check_close(G, Go, amb, tol=3e-4, what="grad rep0")
+        T = t.eval_adjoint(torch.from_numpy(s).cuda(), w).cpu().numpy()
+        To, amb = oracle.eval_op(OP_AT, c.points, s, w, theta=0.5, rep_mode=0, amb_tol=AMB)
+        check_close(T, To, amb, tol=3e-4, what="AT rep0")
+
+
+def test_no_smoothing_on_separated_points():
+    """w = 0 (Alg. 1, no smoothing) drops only coincident pairs.  On a cloud
+    without near-coincident points the FP32 sums keep the 1e-4 bound."""
+    W = _wnnc()
+    c = synth.fibonacci_sphere(6000)
+    mu = synth.init_normals(6000, 9, 4 * math.pi / 6000)
+    s = np.random.default_rng(4).standard_normal(6000).astype(np.float32)
+    for theta in (0.0, 0.5):
+        t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta)
+        F = t.eval_w(torch.from_numpy(mu).cuda(), 0.0).cpu().numpy()
+        Fo, _ = oracle.eval_op(OP_A, c.points, mu, 0.0, theta=f32(theta))
+        check_close(F, Fo, what="A w=0")
+        G = t.eval_grad(torch.from_numpy(mu).cuda(), 0.0).cpu().numpy()
+        Go, _ = oracle.eval_op(OP_G, c.points, mu, 0.0, theta=f32(theta))
+        check_close(G, Go, what="grad w=0")
+        T = t.eval_adjoint(torch.from_numpy(s).cuda(), 0.0).cpu().numpy()
+        To, _ = oracle.eval_op(OP_AT, c.points, s, 0.0, theta=f32(theta))
+        check_close(T, To, what="AT w=0")
+
+
+def test_direct_sphere2k_matches_oracle():
+    """The 2,000-point sphere of the first configuration, direct sums."""
+    W = _wnnc()
+    c = synth.config_cloud("sphere2k")
+    mu = synth.init_normals(len(c.points), 1001, 4 * math.pi / len(c.points))
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.0)
+    for w in (0.002, 0.016, 0.2):
+        F = t.eval_w(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Fo, amb = oracle.eval_op(OP_A, c.points, mu, w, amb_tol=AMB)
+        check_close(F, Fo, amb, what="A")
+        Gr = t.eval_grad(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Go, amb = oracle.eval_op(OP_G, c.points, mu, w, amb_tol=AMB)
+        check_close(Gr, Go, amb, what="grad")
+
+
+def test_treecode_error_vs_direct_is_bounded_and_monotone():
+    """At production theta the tree differs from the exact sums by the
+    far-field approximation only; the error shrinks as theta -> 0."""
+    W = _wnnc()
+    c = synth.config_cloud("union50k", n=20000)
+    mu = (c.normals * (c.area / len(c.points))).astype(np.float32)
+    Fd, _ = oracle.eval_op(OP_A, c.points, mu, 0.004)
+    errs = []
+    for theta in (0.8, 0.5, 0.3):
+        t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta)
+        F = t.eval_w(torch.from_numpy(mu).cuda(), 0.004).cpu().numpy()
+        errs.append(np.linalg.norm(F - Fd) / np.linalg.norm(Fd))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] < 5e-3      # theta = 0.5 (the paper's c = 2)
+
+
+def test_exact_adjoint_identity(union5k):
+    W = _wnnc()
+    c, mu, s = union5k
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    F = t.eval_w(torch.from_numpy(mu).cuda(), 0.004).double().cpu().numpy()
+    T = t.eval_adjoint(torch.from_numpy(s).cuda(), 0.004).double().cpu().numpy()
+    lhs, rhs = (F * s).sum(), (mu.astype(np.float64) * T).sum()
+    assert abs(lhs - rhs) <= 1e-5 * np.abs(F * s).sum()
+
+
+def test_autograd_backward_is_adjoint_and_matches_fd():
+    """d<g, F(mu)>/dmu by autograd vs central differences (step 1e-3) on 64
+    random entries, on the 500,000-point configuration.  F is linear in mu
+    (rep_mode 1), so the differences are exact up to rounding."""
+    W = _wnnc()
+    c = synth.config_cloud("union500k")
+    n = len(c.points)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    nrm = np.nan_to_num(c.normals)
+    mu = torch.from_numpy((nrm * (c.area / n)).astype(np.float32)).cuda().requires_grad_(True)
+    g = torch.from_numpy(np.random.default_rng(2).standard_normal(n).astype(np.float32)).cuda()
+    w = 0.004
+    F = W.winding_number(t, mu, w)
+    (F * g).sum().backward()
+    grad = mu.grad.double().cpu().numpy()
+    gd = g.double()
+    rng = np.random.default_rng(3)
+    idx = rng.choice(n * 3, 64, replace=False)
+    h = 1e-3
+    base = mu.detach().clone()
+    fd = []
+    for k in idx:
+        p = base.clone().view(-1)
+        p[k] += h
+        Lp = (t.eval_w(p.view(n, 3), w).double() * gd).sum().item()
+        p[k] -= 2 * h
+        Lm = (t.eval_w(p.view(n, 3), w).double() * gd).sum().item()
+        fd.append((Lp - Lm) / (2 * h))
+    fd = np.array(fd)
+    ag = grad.reshape(-1)[idx]
+    assert np.abs(fd - ag).max() <= 1e-3 * np.abs(ag).max()
+    # and the backward equals the oracle's dense A^T product on a sample
+    To, _ = oracle.eval_op(OP_AT, c.points, g.cpu().numpy(), w, theta=0.5)
+    check_close(grad, To, what="autograd backward vs oracle A^T")
+
+
+def test_query_points_inside_outside():
+    """F = 1 inside, 0 outside a densely sampled sphere with outward normals (Thm. 1)."""
+    W = _wnnc()
+    c = synth.fibonacci_sphere(40000)
+    n = len(c.points)
+    mu = (c.normals * (4 * math.pi / n)).astype(np.float32)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.3)
+    qi = synth.ball_queries(300, 1, (0, 0, 0), 0.7)
+    qo = (qi / np.linalg.norm(qi, axis=1, keepdims=True) * 1.5).astype(np.float32)
+    Fi = t.eval_at(torch.from_numpy(mu).cuda(), torch.from_numpy(qi).cuda(), 0.0).cpu().numpy()
+    Fo = t.eval_at(torch.from_numpy(mu).cuda(), torch.from_numpy(qo).cuda(), 0.0).cpu().numpy()
+    assert np.abs(Fi - 1).max() < 2e-3
+    assert np.abs(Fo).max() < 2e-3
+    Fq = oracle.eval_at(OP_A, c.points, mu, qi, 0.0, theta=f32(0.3))
+    check_close(Fi, Fq, what="A at queries")
+    Gq = t.eval_at(torch.from_numpy(mu).cuda(), torch.from_numpy(qo).cuda(), 0.0, grad=True).cpu().numpy()
+    Gqo = oracle.eval_at(OP_G, c.points, mu, qo, 0.0, theta=f32(0.3))
+    check_close(Gq, Gqo, what="grad at queries")
+
+
+@pytest.mark.parametrize("n,leaf,depth", [(1, 32, 15), (2, 32, 15), (33, 32, 15), (500, 1, 15),
+                                          (3000, 32, 3), (4097, 64, 15)])
+def test_edge_sizes(n, leaf, depth):
+    """Ragged groups, single points, leaf_size 1 (the paper's octree), shallow
+    trees whose leaves hold hundreds of points."""
+    W = _wnnc()
+    c = synth.union_cloud(max(n, 4), 11, n_tori=1, n_ellipsoids=1)
+    pts = np.ascontiguousarray(c.points[:n])
+    mu = synth.init_normals(n, 3, 1e-3)
+    s = np.random.default_rng(1).standard_normal(n).astype(np.float32)
+    for theta in (0.0, 0.5):
+        t = W.Tree(torch.from_numpy(pts).cuda(), theta=theta, leaf_size=leaf, max_depth=depth)
+        F = t.eval_w(torch.from_numpy(mu).cuda(), 0.01).cpu().numpy()
+        T = t.eval_adjoint(torch.from_numpy(s).cuda(), 0.01).cpu().numpy()
+        xn, _, sc = oracle.normalize(pts)
+        if theta > 0:
+            ot = oracle.Tree(xn, f32(theta), leaf_size=leaf, max_depth=depth)
+            Fo, amb = ot.apply(OP_A, mu.astype(np.float64) * sc * sc, 0.01, amb_tol=AMB)
+            To, ambt = ot.apply(OP_AT, s, 0.01, amb_tol=AMB)
+        else:
+            Fo, amb = oracle.direct(OP_A, xn, mu.astype(np.float64) * sc * sc, 0.01, amb_tol=AMB)
+            To, ambt = oracle.direct(OP_AT, xn, s, 0.01, amb_tol=AMB)
+        if n == 1:
+            assert F[0] == 0.0 and np.all(T == 0.0)
+            continue
+        check_close(F, Fo, amb, what="A")
+        check_close(T, To * sc * sc, ambt * sc * sc, what="AT")
+
+
+def test_duplicate_points():
+    """All points coincident except one: a depth-15 leaf with many points, and
+    coincident pairs excluded even at w = 0."""
+    W = _wnnc()
+    pts = np.zeros((100, 3), np.float32)
+    pts[-1] = (1, 1, 1)
+    mu = synth.init_normals(100, 4, 1.0)
+    t = W.Tree(torch.from_numpy(pts).cuda(), theta=0.5)
+    F = t.eval_w(torch.from_numpy(mu).cuda(), 0.0).cpu().numpy()
+    Fo, _ = oracle.eval_op(OP_A, pts, mu, 0.0)
+    check_close(F, Fo, what="A duplicates")
+    assert t.info()["depth"] == 15
+
+
+def test_errors_are_reported():
+    W = _wnnc()
+    with pytest.raises(W.WnncError) as e:
+        W.Tree(torch.zeros(0, 3, device="cuda"))
+    assert e.value.status == 1
+    t = W.Tree(torch.rand(100, 3, device="cuda"))
+    with pytest.raises(W.WnncError):
+        t.eval_w(torch.zeros(100, 3, device="cuda"), -1.0)
+    with pytest.raises(W.WnncError):
+        W.Tree(torch.rand(100, 3, device="cuda"), theta=float("nan"))
+    with pytest.raises(W.WnncError):
+        t.iterate(n_iter=0)
+    t.sync_status()
+
+
+def test_units_scale_invariance():
+    """x -> k x (mu -> k^2 mu): F unchanged, grad F scales 1/k, A^T 1/k^2."""
+    W = _wnnc()
+    c = synth.union_cloud(4000, 8, n_tori=1, n_ellipsoids=1)
+    mu = synth.init_normals(4000, 2, 1e-3)
+    s = np.random.default_rng(0).standard_normal(4000).astype(np.float32)
+    k = 4.0
+    t1 = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    t2 = W.Tree(torch.from_numpy(c.points * k).cuda(), theta=0.5)
+    m1, m2 = torch.from_numpy(mu).cuda(), torch.from_numpy(mu * k * k).cuda()
+    F1, F2 = t1.eval_w(m1, 0.01).cpu().numpy(), t2.eval_w(m2, 0.01).cpu().numpy()
+    check_close(F2, F1, what="F")
+    G1, G2 = t1.eval_grad(m1, 0.01).cpu().numpy(), t2.eval_grad(m2, 0.01).cpu().numpy()
+    check_close(G2 * k, G1, what="grad")
+    T1 = t1.eval_adjoint(torch.from_numpy(s).cuda(), 0.01).cpu().numpy()
+    T2 = t2.eval_adjoint(torch.from_numpy(s).cuda(), 0.01).cpu().numpy()
+    check_close(T2 * k * k, T1, what="AT")
+
+
+def test_profiler_counts_launches():
+    W = _wnnc()
+    c = synth.union_cloud(3000, 8, n_tori=1, n_ellipsoids=1)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    t.profile(True)
+    t.iterate(n_iter=2)
+    p = t.profile_read()
+    assert p["G"][0] == 2 and p["A"][0] == 4 and p["adj_near"][0] == 2 and p["moments"][0] == 6
+    assert all(v[1] >= 0 for v in p.values())
+    t.profile_reset()
+    assert t.profile_read()["G"] == (0, 0.0)

@@ -1,0 +1,170 @@
+"""The Alg. 3 iteration: the oracle against the paper's sphere table, and the
+CUDA iteration against the oracle's iteration."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sphere_area_table.txt")
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def _paper_table():
+    vals = {}
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip() or line.startswith("stat"):
+            continue
+        k, v = line.split()
+        vals[k] = float(v)
+    return vals
+
+
+def _area_stats(mu):
+    a = np.linalg.norm(mu, axis=1)
+    return dict(min=a.min(), max=a.max(), mean=a.mean(), total=a.sum())
+
+
+@pytest.mark.slow
+def test_oracle_reproduces_paper_sphere_area_table():
+    """Oracle, icosphere-7 (163,842 points), 40 iterations, theta = 0.5."""
+    c = synth.icosphere(7)
+    mu, _ = oracle.iterate(c.points, n_iter=40, theta=0.5)
+    got, ref = _area_stats(mu), _paper_table()
+    for k in ("min", "max", "mean", "total"):
+        assert abs(got[k] / ref[k] - 1) < 0.03, (k, got[k], ref[k])
+    assert oracle.p_co(c.normals, mu) == 1.0
+
+
+def _gpu():
+    import paper_2405_16634_b300 as W
+    return W
+
+
+@pytest.mark.gpu
+def test_gpu_reproduces_paper_sphere_area_table():
+    W = _gpu()
+    c = synth.icosphere(7)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mu = t.iterate(n_iter=40).cpu().numpy().astype(np.float64)
+    got, ref = _area_stats(mu), _paper_table()
+    for k in ("min", "max", "mean", "total"):
+        assert abs(got[k] / ref[k] - 1) < 0.03, (k, got[k], ref[k])
+    assert oracle.p_co(c.normals, mu) == 1.0
+
+
+def _compare_fields(mu_g, mu_o, min_sign=0.995, min_cos=0.99):
+    ug, uo = oracle.unit(mu_g), oracle.unit(mu_o)
+    cos = (ug * uo).sum(1)
+    assert np.mean(cos > 0) >= min_sign, np.mean(cos > 0)
+    assert np.median(cos) >= min_cos, np.median(cos)
+    lg, lo = np.linalg.norm(mu_g, axis=1), np.linalg.norm(mu_o, axis=1)
+    return cos, np.median(np.abs(lg / np.maximum(lo, 1e-30) - 1))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("init", ["zero", "random"])
+def test_gpu_iteration_sphere2k_matches_oracle(init):
+    """First configuration: 2,000 sphere points, direct sums, 40 iterations."""
+    W = _gpu()
+    c = synth.config_cloud("sphere2k")
+    n = len(c.points)
+    mu0 = None if init == "zero" else synth.init_normals(n, 1001, 4 * math.pi / n)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.0)
+    mg, st = t.iterate(None if mu0 is None else torch.from_numpy(mu0).cuda(), n_iter=40, stats=True)
+    mg = mg.cpu().numpy().astype(np.float64)
+    st = st.cpu().numpy()
+    mo, so = oracle.iterate(c.points, mu0=mu0, n_iter=40)
+    cos, dlen = _compare_fields(mg, mo, min_sign=1.0, min_cos=0.9999)
+    assert dlen < 1e-3
+    assert np.allclose(st[:, 0], so[:, 0], rtol=1e-6)
+    assert np.allclose(st[:5, 1], so[:5, 1], rtol=1e-3)
+    assert np.allclose(st[:5, 2], so[:5, 2], rtol=1e-3)
+    if init == "zero":
+        assert oracle.p_co(c.normals, mg) == 1.0
+
+
+@pytest.mark.gpu
+def test_gpu_first_iteration_closed_form():
+    W = _gpu()
+    c = synth.fibonacci_sphere(40000)
+    n = len(c.points)
+    w = 0.1
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.3)
+    mu = t.iterate(n_iter=1, w1=w, w2=w).cpu().numpy().astype(np.float64)
+    xn, _, s = oracle.normalize(c.points)
+    R = np.linalg.norm(xn, axis=1).mean()
+    pred = 4 * math.pi * (R / s) ** 2 / n / (1 - w / (2 * R))
+    assert abs(np.linalg.norm(mu, axis=1).mean() / pred - 1) < 1e-2
+    assert oracle.p_co(c.normals, mu) == 1.0
+
+
+@pytest.mark.gpu
+def test_gpu_iteration_union50k_matches_oracle():
+    """Second configuration: 50,000 union points, theta = 0.5, 40 iterations."""
+    W = _gpu()
+    c = synth.config_cloud("union50k")
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mg = t.iterate(n_iter=40).cpu().numpy().astype(np.float64)
+    mo, _ = oracle.iterate(c.points, n_iter=40, theta=f32(0.5))
+    _compare_fields(mg, mo, min_sign=0.995, min_cos=0.995)
+    assert oracle.p_co(c.normals, mg) > 0.98
+    assert abs(oracle.p_co(c.normals, mg) - oracle.p_co(c.normals, mo)) < 0.005
+
+
+@pytest.mark.gpu
+def test_gpu_paper_mode_iteration_matches_oracle():
+    """rep_mode 0 (the paper's |nu|-weighted representatives and the
+    s-representative A^T) through the whole iteration."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=10000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, rep_mode=0)
+    mg = t.iterate(n_iter=10).cpu().numpy().astype(np.float64)
+    mo, _ = oracle.iterate(c.points, n_iter=10, theta=0.5, rep_mode=0)
+    _compare_fields(mg, mo, min_sign=0.995, min_cos=0.995)
+
+
+@pytest.mark.gpu
+def test_gpu_ablations_behave_as_in_the_paper():
+    """Sec. 6.1.4: without the gradient step mu stays 0; the grad step alone
+    (no WNNC update) decreases the energy monotonically at fixed width."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=10000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mu = t.iterate(n_iter=5, use_grad=False)
+    assert torch.count_nonzero(mu).item() == 0
+    _, st = t.iterate(n_iter=6, w1=0.02, w2=0.02, use_wnnc=False, stats=True)
+    E = st[:, 1].cpu().numpy()
+    assert np.all(np.diff(E) < 0)
+
+
+@pytest.mark.gpu
+def test_gpu_fixed_area_rescale():
+    """Eq. 14: with rescale = 1 every |mu_i| equals the given area."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=10000)
+    n = len(c.points)
+    area = np.full(n, c.area / n, np.float32)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mu = t.iterate(n_iter=5, area=torch.from_numpy(area).cuda(), rescale=1).cpu().numpy()
+    assert np.allclose(np.linalg.norm(mu, axis=1), area, rtol=1e-5)
+
+
+@pytest.mark.gpu
+def test_gpu_resume_equals_full_run():
+    """Checkpoint/resume: iterations 1..20 then 21..40 equal one 1..40 run."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=20000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    full = t.iterate(n_iter=40)
+    half = t.iterate(n_iter=40, last_iter=20)
+    rest = t.iterate(half, n_iter=40, first_iter=21)
+    cos = (oracle.unit(full.cpu().numpy()) * oracle.unit(rest.cpu().numpy())).sum(1)
+    assert np.min(cos) > 0.999
