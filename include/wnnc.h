@@ -208,6 +208,10 @@ wnnc_status wnnc_profile_enable(wnnc_tree* tree, int enable);
 wnnc_status wnnc_profile_read(wnnc_tree* tree, int64_t* launches, double* total_ms);
 wnnc_status wnnc_profile_reset(wnnc_tree* tree);
 
+/* Number of kernels this library has launched in this process so far (all
+ * threads, all trees); for counting the launches inside a timed region. */
+int64_t wnnc_kernel_launches(void);
+
 /* Wait for the stream and return (and clear) any condition latched on the device. */
 wnnc_status wnnc_sync_status(wnnc_tree* tree, void* stream);
 

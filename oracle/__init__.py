@@ -62,7 +62,8 @@ def lib():
         d, i64, P = c_double, c_int64, POINTER
         L.or_num_threads.restype = c_int
         L.or_normalize.argtypes = [c_void_p, i64, c_void_p, c_void_p, c_void_p]
-        L.or_direct.argtypes = [c_int, c_void_p, i64, c_void_p, c_void_p, i64, d, d, c_void_p, c_void_p]
+        L.or_direct.argtypes = [c_int, c_void_p, i64, c_void_p, c_void_p, i64, d, d, c_void_p, c_void_p,
+                                c_void_p]
         L.or_tree_build.argtypes = [c_void_p, i64, c_int, c_int, c_int, d]
         L.or_tree_build.restype = c_void_p
         L.or_tree_free.argtypes = [c_void_p]
@@ -73,8 +74,9 @@ def lib():
         L.or_tree_boxes.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
         L.or_tree_counts.argtypes = [c_void_p, c_void_p]
         L.or_tree_lists.argtypes = [c_void_p] + [c_void_p] * 4
-        L.or_tree_apply.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, d, c_void_p]
-        L.or_tree_apply_at.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, i64, c_void_p, c_void_p]
+        L.or_tree_apply.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, d, c_void_p, c_void_p]
+        L.or_tree_apply_at.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, i64, c_void_p,
+                                       c_void_p, c_void_p]
         L.or_schedule_width.argtypes = [c_int, c_int, d, d]
         L.or_schedule_width.restype = d
         L.or_iterate.argtypes = [c_void_p, c_void_p, i64, c_void_p, c_int, c_int, c_int, d, d, c_int,
@@ -124,15 +126,22 @@ def apply_normalization(q, center, scale):
 
 def direct(op: int, x, nu, w: float, y=None, amb_tol: float = 0.0):
     """Direct sum of operator ``op`` with sources x, attribute nu, targets y
-    (default: the sources).  Returns (out, amb); amb is None unless amb_tol>0."""
+    (default: the sources).  Returns (out, bounds); bounds is None unless
+    amb_tol > 0, else a dict of per-target arrays:
+      amb    sum of |term| over pairs whose r^2 is within amb_tol*w^2 of w^2
+             (a lower-precision cut-off test may decide them either way)
+      abssum sum of |term| over the counted pairs (the scale of the rounding
+             error of any floating-point evaluation of the sum)."""
     x = _f64(x, (-1, 3))
     y = x if y is None else _f64(y, (-1, 3))
     ns, nt = x.shape[0], y.shape[0]
     nu = _f64(nu, (ns, 3) if op != OP_AT else (ns,))
     out = np.zeros(nt) if op == OP_A else np.zeros((nt, 3))
     amb = np.zeros(nt) if amb_tol > 0 else None
-    lib().or_direct(op, _p(x), ns, _p(nu), _p(y), nt, float(w), float(amb_tol), _p(out), _p(amb))
-    return out, amb
+    abssum = np.zeros(nt) if amb_tol > 0 else None
+    lib().or_direct(op, _p(x), ns, _p(nu), _p(y), nt, float(w), float(amb_tol), _p(out), _p(amb),
+                    _p(abssum))
+    return out, (None if amb is None else {"amb": amb, "abssum": abssum})
 
 
 # ---------------------------------------------------------------------------
@@ -155,21 +164,27 @@ class Tree:
             self._h = None
 
     def apply(self, op: int, nu, w: float, rep_mode: int = 1, amb_tol: float = 0.0):
-        """Tree operator on the points; with amb_tol > 0 returns (out, amb)."""
+        """Tree operator on the points; with amb_tol > 0 returns (out, bounds)
+        (bounds as in ``direct``)."""
         nu = _f64(nu, (self.n, 3) if op != OP_AT else (self.n,))
         out = np.zeros(self.n) if op == OP_A else np.zeros((self.n, 3))
         amb = np.zeros(self.n) if amb_tol > 0 else None
-        lib().or_tree_apply(self._h, op, rep_mode, float(w), _p(nu), _p(out), float(amb_tol), _p(amb))
-        return (out, amb) if amb_tol > 0 else out
+        abssum = np.zeros(self.n) if amb_tol > 0 else None
+        lib().or_tree_apply(self._h, op, rep_mode, float(w), _p(nu), _p(out), float(amb_tol), _p(amb),
+                            _p(abssum))
+        return (out, {"amb": amb, "abssum": abssum}) if amb_tol > 0 else out
 
     def apply_at(self, op: int, nu, qn, w: float, rep_mode: int = 1):
+        """(out, pairs, abssum) at off-surface targets qn."""
         nu = _f64(nu, (self.n, 3))
         qn = _f64(qn, (-1, 3))
         m = qn.shape[0]
         out = np.zeros(m) if op == OP_A else np.zeros((m, 3))
         pairs = np.zeros(2, np.int64)
-        lib().or_tree_apply_at(self._h, op, rep_mode, float(w), _p(nu), _p(qn), m, _p(out), _p(pairs))
-        return out, pairs
+        abssum = np.zeros(m)
+        lib().or_tree_apply_at(self._h, op, rep_mode, float(w), _p(nu), _p(qn), m, _p(out), _p(pairs),
+                               _p(abssum))
+        return out, pairs, abssum
 
     def counts(self):
         """(far list entries, near list entries, far pairs, near pairs)."""
@@ -220,33 +235,41 @@ def eval_op(op: int, points, nu, w: float, theta: float = 0.0, leaf_size: int = 
     xn, c, s, tree = _setup(points, theta, leaf_size, max_depth)
     nu = np.asarray(nu, dtype=np.float64)
     nun = nu * (s * s) if op != OP_AT else nu
-    amb = None
+    bounds = None
     if tree is None:
-        out, amb = direct(op, xn, nun, w, amb_tol=amb_tol)
+        out, bounds = direct(op, xn, nun, w, amb_tol=amb_tol)
     elif amb_tol > 0:
-        out, amb = tree.apply(op, nun, w, rep_mode, amb_tol=amb_tol)
+        out, bounds = tree.apply(op, nun, w, rep_mode, amb_tol=amb_tol)
     else:
         out = tree.apply(op, nun, w, rep_mode)
+    f = 1.0
     if op == OP_G:
-        out = -out * s          # grad F in caller units
-        amb = None if amb is None else amb * s
+        out, f = -out * s, s          # grad F in caller units
     elif op == OP_AT:
-        out = out * (s * s)
-        amb = None if amb is None else amb * (s * s)
-    return out, amb
+        out, f = out * (s * s), s * s
+    if bounds is not None:
+        bounds = {k: v * f for k, v in bounds.items()}
+    return out, bounds
 
 
 def eval_at(op: int, points, mu, queries, w: float, theta: float = 0.0, leaf_size: int = 32,
-            max_depth: int = 15, rep_mode: int = 1):
-    """A (F) or grad F at off-surface query points (caller units)."""
+            max_depth: int = 15, rep_mode: int = 1, with_bounds: bool = False):
+    """A (F) or grad F at off-surface query points (caller units); with
+    with_bounds also the per-target bounds (amb is zero here: w applies only
+    through the cut-off, and off-surface tests use w = 0)."""
     xn, c, s, tree = _setup(points, theta, leaf_size, max_depth)
     qn = apply_normalization(queries, c, s)
     mun = np.asarray(mu, dtype=np.float64) * (s * s)
     if tree is None:
-        out, _ = direct(op, xn, mun, w, y=qn)
+        out, b = direct(op, xn, mun, w, y=qn, amb_tol=1e-5)
+        abssum = b["abssum"]
     else:
-        out, _ = tree.apply_at(op, mun, qn, w, rep_mode)
-    return -out * s if op == OP_G else out
+        out, _, abssum = tree.apply_at(op, mun, qn, w, rep_mode)
+    f = s if op == OP_G else 1.0
+    out = -out * s if op == OP_G else out
+    if with_bounds:
+        return out, {"amb": np.zeros(len(out)), "abssum": abssum * f}
+    return out
 
 
 def iterate(points, mu0=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0.016,

@@ -103,14 +103,18 @@ static inline void term_AT(const double d[3], double r2, double s, double out[3]
     for (int k = 0; k < 3; ++k) out[k] = s * d[k] / (4.0 * OR_PI * r2 * r);
 }
 
-/* Cut-off of Sec. 4.3: a term counts iff |y - x| >= w; coincident points
- * never count (this is the self term, and the only exclusion when w = 0). */
-static inline int keep_pair(double r2, double w2) { return r2 > 0.0 && r2 >= w2; }
+/* Cut-off of Sec. 4.3: a term counts iff |y - x| >= w.  Pairs closer than
+ * MIN_SEP = 2^-20 (normalised units, about 1e-6 of the cloud) count as
+ * coincident and never count either: this removes the self term, and it is the
+ * only exclusion when w = 0 (Alg. 1), where the kernel is singular. */
+#define MIN_SEP2 (1.0 / 1099511627776.0) /* (2^-20)^2 */
+static inline double eff_w2(double w) { double w2 = w * w; return w2 > MIN_SEP2 ? w2 : MIN_SEP2; }
+static inline int keep_pair(double r2, double w2) { return r2 >= w2; }
 
 /* A pair is "cut-off ambiguous" when r^2 lies within amb_tol*w^2 of w^2: a
  * single-precision evaluation may take the other side of the test. */
 static inline int ambiguous(double r2, double w2, double amb_tol) {
-    return w2 > 0.0 && fabs(r2 - w2) <= amb_tol * w2;
+    return fabs(r2 - w2) <= amb_tol * w2;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -122,29 +126,32 @@ static inline int ambiguous(double r2, double w2, double amb_tol) {
 /* ------------------------------------------------------------------------ */
 void or_direct(int op, const double* xs, int64_t ns, const double* nu,
                const double* yt, int64_t nt, double w, double amb_tol,
-               double* out, double* amb) {
-    const double w2 = w * w;
+               double* out, double* amb, double* abssum) {
+    const double w2 = eff_w2(w);
     #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; ++t) {
-        double acc[3] = {0, 0, 0}, ab = 0.0;
+        double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
         for (int64_t j = 0; j < ns; ++j) {
             double d[3] = {yt[3 * t] - xs[3 * j], yt[3 * t + 1] - xs[3 * j + 1],
                            yt[3 * t + 2] - xs[3 * j + 2]};
             double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (!(r2 > 0.0)) continue;
             int amb_p = amb && ambiguous(r2, w2, amb_tol);
             if (!keep_pair(r2, w2) && !amb_p) continue;
             double v[3] = {0, 0, 0};
             if (op == OP_A) v[0] = term_A(d, r2, nu + 3 * j);
             else if (op == OP_G) term_G(d, r2, nu + 3 * j, v);
             else term_AT(d, r2, nu[j], v);
-            if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            if (keep_pair(r2, w2))
+            double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            if (amb_p) ab += vn;
+            if (keep_pair(r2, w2)) {
                 for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                as += vn;
+            }
         }
         if (op == OP_A) out[t] = acc[0];
         else for (int k = 0; k < 3; ++k) out[3 * t + k] = acc[k];
         if (amb) amb[t] = ab;
+        if (abssum) abssum[t] = as;
     }
 }
 
@@ -455,31 +462,35 @@ static void node_reps(const or_octree* t, const double* nu, int dim, int rep_mod
  * nu_sorted: source attribute in sorted source order.  out: sorted target order.
  */
 static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep_mode, double w,
-                        const double* nu_sorted, double* out_sorted, double amb_tol, double* amb_sorted) {
+                        const double* nu_sorted, double* out_sorted, double amb_tol, double* amb_sorted,
+                        double* abs_sorted) {
     int dim = (op == OP_AT) ? 1 : 3;
     double* rep = malloc(sizeof(double) * 3 * (t->nnodes > 0 ? t->nnodes : 1));
     double* nuB = malloc(sizeof(double) * dim * (t->nnodes > 0 ? t->nnodes : 1));
     node_reps(t, nu_sorted, dim, rep_mode, rep, nuB);
-    const double w2 = w * w;
+    const double w2 = eff_w2(w);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < T->ngroups; ++g) {
         int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
         for (int64_t i = s; i < e; ++i) {
             const double* y = T->y + 3 * i;
-            double acc[3] = {0, 0, 0}, ab = 0.0;
+            double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
             for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
                 int64_t b = T->far_id[q];
                 double d[3] = {y[0] - rep[3 * b], y[1] - rep[3 * b + 1], y[2] - rep[3 * b + 2]};
                 double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                int amb_p = amb_sorted && r2 > 0.0 && ambiguous(r2, w2, amb_tol);
+                int amb_p = amb_sorted && ambiguous(r2, w2, amb_tol);
                 if (!keep_pair(r2, w2) && !amb_p) continue;
                 double v[3] = {0, 0, 0};
                 if (op == OP_A) v[0] = term_A(d, r2, nuB + 3 * b);
                 else if (op == OP_G) term_G(d, r2, nuB + 3 * b, v);
                 else term_AT(d, r2, nuB[b], v);
-                if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                if (keep_pair(r2, w2))
+                double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                if (amb_p) ab += vn;
+                if (keep_pair(r2, w2)) {
                     for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                    as += vn;
+                }
             }
             for (int64_t q = T->near_off[g]; q < T->near_off[g + 1]; ++q) {
                 int64_t b = T->near_id[q];
@@ -487,20 +498,24 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
                     const double* x = t->x + 3 * j;
                     double d[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
                     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    int amb_p = amb_sorted && r2 > 0.0 && ambiguous(r2, w2, amb_tol);
+                    int amb_p = amb_sorted && ambiguous(r2, w2, amb_tol);
                     if (!keep_pair(r2, w2) && !amb_p) continue;
                     double v[3] = {0, 0, 0};
                     if (op == OP_A) v[0] = term_A(d, r2, nu_sorted + 3 * j);
                     else if (op == OP_G) term_G(d, r2, nu_sorted + 3 * j, v);
                     else term_AT(d, r2, nu_sorted[j], v);
-                    if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                    if (keep_pair(r2, w2))
+                    double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                    if (amb_p) ab += vn;
+                    if (keep_pair(r2, w2)) {
                         for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                        as += vn;
+                    }
                 }
             }
             if (op == OP_A) out_sorted[i] = acc[0];
             else for (int k = 0; k < 3; ++k) out_sorted[3 * i + k] = acc[k];
             if (amb_sorted) amb_sorted[i] = ab;
+            if (abs_sorted) abs_sorted[i] = as;
         }
     }
     free(rep); free(nuB);
@@ -517,9 +532,9 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
  * that each output is a sum in a fixed order (groups ascending, then i). */
 static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w,
                                const double* s_sorted, double* out_sorted, double amb_tol,
-                               double* amb_sorted) {
+                               double* amb_sorted, double* abs_sorted) {
     int64_t nn = t->nnodes, ng = T->ngroups;
-    const double w2 = w * w;
+    const double w2 = eff_w2(w);
     /* transposed lists: node -> groups using it (far), leaf -> groups using it (near) */
     int64_t* fcnt = calloc((size_t)nn + 1, sizeof(int64_t));
     int64_t* ncnt = calloc((size_t)nn + 1, sizeof(int64_t));
@@ -538,10 +553,11 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
     }
     double* V = calloc((size_t)(nn > 0 ? nn : 1) * 3, sizeof(double));
     double* VA = calloc((size_t)(nn > 0 ? nn : 1), sizeof(double));
+    double* VS = calloc((size_t)(nn > 0 ? nn : 1), sizeof(double));
     const double* rep = t->cent;
     #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t b = 0; b < nn; ++b) {
-        double acc[3] = {0, 0, 0}, ab = 0.0;
+        double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
         for (int64_t q = fcnt[b]; q < fcnt[b + 1]; ++q) {
             int64_t g = fg[q];
             int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
@@ -550,17 +566,21 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                 double d[3] = {rep[3 * b] - T->y[3 * i], rep[3 * b + 1] - T->y[3 * i + 1],
                                rep[3 * b + 2] - T->y[3 * i + 2]};
                 double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                int amb_p = amb_sorted && r2 > 0.0 && ambiguous(r2, w2, amb_tol);
+                int amb_p = amb_sorted && ambiguous(r2, w2, amb_tol);
                 if (!keep_pair(r2, w2) && !amb_p) continue;
                 double v[3];
                 term_AT(d, r2, s_sorted[i], v);
-                if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                if (keep_pair(r2, w2))
+                double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                if (amb_p) ab += vn;
+                if (keep_pair(r2, w2)) {
                     for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                    as += vn;
+                }
             }
         }
         for (int k = 0; k < 3; ++k) V[3 * b + k] = acc[k];
         VA[b] = ab;
+        VS[b] = as;
     }
     /* near part, per source leaf, then add the far sums of all nodes containing j */
     #pragma omp parallel for schedule(dynamic, 16)
@@ -568,60 +588,67 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         if (t->nchild[b] != 0) continue;
         for (int64_t j = t->start[b]; j < t->start[b] + t->count[b]; ++j) {
             const double* x = t->x + 3 * j;
-            double acc[3] = {0, 0, 0}, ab = 0.0;
+            double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
             for (int64_t q = ncnt[b]; q < ncnt[b + 1]; ++q) {
                 int64_t g = ngp[q];
                 int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
                 for (int64_t i = s; i < e; ++i) {
                     double d[3] = {x[0] - T->y[3 * i], x[1] - T->y[3 * i + 1], x[2] - T->y[3 * i + 2]};
                     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    int amb_p = amb_sorted && r2 > 0.0 && ambiguous(r2, w2, amb_tol);
+                    int amb_p = amb_sorted && ambiguous(r2, w2, amb_tol);
                     if (!keep_pair(r2, w2) && !amb_p) continue;
                     double v[3];
                     term_AT(d, r2, s_sorted[i], v);
-                    if (amb_p) ab += sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                    if (keep_pair(r2, w2))
+                    double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                    if (amb_p) ab += vn;
+                    if (keep_pair(r2, w2)) {
                         for (int k = 0; k < 3; ++k) acc[k] += v[k];
+                        as += vn;
+                    }
                 }
             }
             double far[3] = {0, 0, 0};
             for (int64_t a = b; a >= 0; a = t->parent[a]) {
                 for (int k = 0; k < 3; ++k) far[k] += V[3 * a + k];
                 ab += VA[a];
+                as += VS[a];
             }
             for (int k = 0; k < 3; ++k) out_sorted[3 * j + k] = acc[k] + far[k];
             if (amb_sorted) amb_sorted[j] = ab;
+            if (abs_sorted) abs_sorted[j] = as;
         }
     }
-    free(fcnt); free(ncnt); free(fg); free(ngp); free(fpos); free(npos); free(V); free(VA);
+    free(fcnt); free(ncnt); free(fg); free(ngp); free(fpos); free(npos); free(V); free(VA); free(VS);
 }
 
 /* On-surface application of an operator.  nu and out are in input order,
  * normalised units.  For op AT, rep_mode 1 gives the exact transpose of the
  * rep_mode-1 A, rep_mode 0 the paper's s-representative treecode. */
 void or_tree_apply(const or_tree* T, int op, int rep_mode, double w, const double* nu, double* out,
-                   double amb_tol, double* amb) {
+                   double amb_tol, double* amb, double* abssum) {
     const or_octree* t = &T->src;
     int64_t n = t->n;
     int din = (op == OP_AT) ? 1 : 3, dout = (op == OP_A) ? 1 : 3;
     double* nus = malloc(sizeof(double) * din * (n > 0 ? n : 1));
     double* outs = malloc(sizeof(double) * dout * (n > 0 ? n : 1));
     double* ambs = amb ? malloc(sizeof(double) * (n > 0 ? n : 1)) : NULL;
+    double* abss = abssum ? malloc(sizeof(double) * (n > 0 ? n : 1)) : NULL;
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < din; ++k) nus[din * i + k] = nu[din * t->perm[i] + k];
-    if (op == OP_AT && rep_mode == 1) tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs);
-    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs);
+    if (op == OP_AT && rep_mode == 1) tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs, abss);
+    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs, abss);
     for (int64_t i = 0; i < n; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * T->self.perm[i] + k] = outs[dout * i + k];
         if (amb) amb[T->self.perm[i]] = ambs[i];
+        if (abssum) abssum[T->self.perm[i]] = abss[i];
     }
-    free(nus); free(outs); free(ambs);
+    free(nus); free(outs); free(ambs); free(abss);
 }
 
 /* Off-surface targets (op A or G): the targets are grouped and listed
  * against the source octree exactly like the on-surface set. */
 void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const double* nu,
-                      const double* qn, int64_t m, double* out, int64_t* pairs2) {
+                      const double* qn, int64_t m, double* out, int64_t* pairs2, double* abssum) {
     const or_octree* t = &T->src;
     or_targets Q;
     memset(&Q, 0, sizeof(Q));
@@ -632,9 +659,13 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
     double* outs = malloc(sizeof(double) * dout * (m > 0 ? m : 1));
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) nus[3 * i + k] = nu[3 * t->perm[i] + k];
-    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL);
-    for (int64_t i = 0; i < m; ++i)
+    double* abss = abssum ? malloc(sizeof(double) * (m > 0 ? m : 1)) : NULL;
+    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL, abss);
+    for (int64_t i = 0; i < m; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * Q.perm[i] + k] = outs[dout * i + k];
+        if (abssum) abssum[Q.perm[i]] = abss[i];
+    }
+    free(abss);
     if (pairs2) { pairs2[0] = Q.far_pairs; pairs2[1] = Q.near_pairs; }
     free(nus); free(outs);
     free_targets(&Q);
@@ -654,8 +685,8 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
 /* ------------------------------------------------------------------------ */
 static void apply_op(const or_tree* T, const double* xn, int64_t n, int op, int rep_mode, double w,
                      const double* nu, double* out) {
-    if (T) or_tree_apply(T, op, rep_mode, w, nu, out, 0.0, NULL);
-    else or_direct(op, xn, n, nu, xn, n, w, 0.0, out, NULL);
+    if (T) or_tree_apply(T, op, rep_mode, w, nu, out, 0.0, NULL, NULL);
+    else or_direct(op, xn, n, nu, xn, n, w, 0.0, out, NULL, NULL);
 }
 
 double or_schedule_width(int i, int n_iter, double w1, double w2) {

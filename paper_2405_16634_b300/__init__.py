@@ -88,6 +88,7 @@ def lib():
     L.wnnc_profile_reset.argtypes = [P]
     L.wnnc_sync_status.argtypes = [P, P]
     L.wnnc_last_error.restype = ctypes.c_char_p
+    L.wnnc_kernel_launches.restype = c_int64
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
                  "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
                  "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_tree_info",
@@ -115,6 +116,11 @@ def _dev_f32(t, shape, device) -> torch.Tensor:
     if tuple(t.shape) != tuple(shape):
         t = t.reshape(shape)
     return t
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().wnnc_kernel_launches())
 
 
 def default_tree_params() -> TreeParams:

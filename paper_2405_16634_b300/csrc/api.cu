@@ -1,5 +1,6 @@
 // api.cu -- the extern "C" boundary (include/wnnc.h): argument checks, status
 // codes, thread-local error text, tree lifetime and work buffers.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -9,6 +10,9 @@
 namespace wnnc {
 
 static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
@@ -311,6 +315,8 @@ wnnc_status wnnc_sync_status(wnnc_tree* tree, void* stream) {
     });
     return st != WNNC_OK ? st : dev;
 }
+
+int64_t wnnc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* wnnc_last_error(void) { return g_last_error.c_str(); }
 

@@ -37,7 +37,13 @@ void set_last_error(const std::string& msg);
                          std::string(#call) + ": " + cudaGetErrorString(e_));            \
     } while (0)
 
-#define WNNC_LAUNCH_CHECK() WNNC_CUDA(cudaGetLastError())
+// Every kernel launch is followed by this check, which also counts the launch.
+void count_launch();
+#define WNNC_LAUNCH_CHECK()             \
+    do {                                \
+        ::wnnc::count_launch();         \
+        WNNC_CUDA(cudaGetLastError());  \
+    } while (0)
 
 // Typed device allocation that throws on failure.
 template <class T>

@@ -525,7 +525,9 @@ __global__ void k_stats_nograd(float* stats, float w) {
 // ---------------------------------------------------------------------------
 // Host helpers
 // ---------------------------------------------------------------------------
-inline float cutoff2(float w) { return fmaxf(w * w, FLT_MIN); }
+// Squared cut-off: w^2, floored at (2^-20)^2 so that coincident pairs (the
+// self term, repeated samples) never count, also when w = 0 (Alg. 1).
+inline float cutoff2(float w) { return fmaxf(w * w, 0x1p-40f); }
 
 GatherArgs base_args(const Tree& t, const TargetSet& ts, float w) {
     GatherArgs a{};

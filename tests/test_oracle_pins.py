@@ -166,14 +166,26 @@ def test_ambiguity_budget_flags_boundary_pairs():
     x = np.array([[0.25, 0.0, 0.0], [0.0, 0.75, 0.0]])
     mu = np.array([[1.0, 0, 0], [0, 1.0, 0]])
     y = np.zeros((1, 3))
-    out, amb = oracle.direct(OP_A, x, mu, 0.25, y=y, amb_tol=1e-6)
-    assert abs(amb[0] - 0.25 / (4 * math.pi * 0.25 ** 3)) < 1e-12
+    out, b = oracle.direct(OP_A, x, mu, 0.25, y=y, amb_tol=1e-6)
+    assert abs(b["amb"][0] - 0.25 / (4 * math.pi * 0.25 ** 3)) < 1e-12
+    assert abs(b["abssum"][0] - (0.25 / (4 * math.pi * 0.25 ** 3) + 0.75 / (4 * math.pi * 0.75 ** 3))) < 1e-12
     assert abs(out[0] - (0.25 / (4 * math.pi * 0.25 ** 3) + 0.75 / (4 * math.pi * 0.75 ** 3))) < 1e-12
 
 
 # ---------------------------------------------------------------------------
 # Normalisation (Sec. 5.1.1)
 # ---------------------------------------------------------------------------
+
+def test_coincident_pairs_never_count():
+    """Exact duplicates (the self term, repeated samples) contribute nothing,
+    also at w = 0; pairs just above the 2^-20 floor do."""
+    x = np.array([[0.5, 0.0, 0.0], [0.5, 0.0, 0.0], [0.5 + 2.0 ** -19, 0.0, 0.0]])
+    mu = np.array([[1.0, 0, 0], [1.0, 0, 0], [1.0, 0, 0]])
+    out, _ = oracle.direct(OP_A, x, mu, 0.0)
+    d = 2.0 ** -19
+    assert out[0] == pytest.approx(d / (4 * math.pi * d ** 3))
+    assert out[2] == pytest.approx(-2 * d / (4 * math.pi * d ** 3))
+
 
 def test_normalization_margin():
     c = synth.union_cloud(5000, 7)
@@ -288,7 +300,7 @@ def test_tree_query_targets_match_direct_in_limit(cloud20k):
     xn, mu, _ = cloud20k
     q = synth.ball_queries(500, 9, (0, 0, 0), 0.9).astype(np.float64)
     t = oracle.Tree(xn[:5000], 1e-12)
-    out, pairs = t.apply_at(OP_A, mu[:5000], q, 0.0)
+    out, pairs, _ = t.apply_at(OP_A, mu[:5000], q, 0.0)
     d, _ = oracle.direct(OP_A, xn[:5000], mu[:5000], 0.0, y=q)
     assert pairs[0] == 0 and pairs[1] == 500 * 5000
     assert np.abs(out - d).max() <= 1e-12 * np.abs(d).max()
