@@ -36,10 +36,18 @@ sys.path.insert(0, ROOT)
 N_ITER = 40
 W1, W2 = 0.002, 0.016
 THETA = 0.5
+WORKLOADS = {
+    "union500k": ("union500k: 500,000 points on a union of 6 tori + 6 ellipsoids, 10x density "
+                  "modulation, 1% outliers; theta=0.5 (c=2), leaf_size=32, depth 15; 40 iterations "
+                  "w2=0.016 -> w1=0.002"),
+    "union50k": ("union50k: 50,000 points on a union of 2 tori + 2 ellipsoids, noise 0.002; "
+                 "theta=0.5, leaf_size=32, depth 15; 40 iterations w2=0.016 -> w1=0.002 "
+                 "(small case for profiling)"),
+    "union2m": ("union2m: 2,000,000 points on 24 primitives incl. thin tori (r=0.01) and "
+                "near-touching ellipsoid pairs (gap 0.005), noise 0.001; theta=0.5; 40 iterations"),
+}
 CONFIG_NAME = "union500k"
-WORKLOAD = ("union500k: 500,000 points on a union of 6 tori + 6 ellipsoids, 10x density "
-            "modulation, 1% outliers; theta=0.5 (c=2), leaf_size=32, depth 15; 40 iterations "
-            "w2=0.016 -> w1=0.002")
+WORKLOAD = WORKLOADS[CONFIG_NAME]
 # algorithmic FP32 flops per pair term (FMA = 2, rsqrt = 1; the cut-off select is not counted)
 FLOPS_A, FLOPS_AT, FLOPS_G = 18, 18, 31
 FLOPS_ITER = 2 * FLOPS_A + FLOPS_AT + FLOPS_G      # A(mu), A(r), A^T(s), G(mu) per iteration
@@ -283,7 +291,8 @@ def run_gpu(args):
     g_achieved = FLOPS_G * inter_per_op / (g_avg_ms / 1e3) / 1e12
     shares = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4) for k, v in prof.items()}
     line = {
-        "metric": "WNNC iterations/s (500k points)",
+        "metric": "WNNC iterations/s (500k points)" if CONFIG_NAME == "union500k"
+                  else f"WNNC iterations/s ({CONFIG_NAME})",
         "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -325,7 +334,11 @@ def main():
     ap.add_argument("--impl", default="wnnc", choices=["wnnc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--config", default="union500k", choices=sorted(WORKLOADS),
+                    help="workload (the default is the one the metric is quoted on)")
     args = ap.parse_args()
+    global CONFIG_NAME, WORKLOAD
+    CONFIG_NAME, WORKLOAD = args.config, WORKLOADS[args.config]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
