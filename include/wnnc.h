@@ -96,7 +96,7 @@ wnnc_status wnnc_iter_params_default(wnnc_iter_params* p);
  * Build the octree (Sec. 4.4: split until leaf_size points or depth D),
  * node boxes and centroids, and the interaction lists of the points as
  * targets (Alg. 4's far / recurse / leaf-direct decisions, taken once per
- * group of 32 Morton-consecutive targets against its bounding box).
+ * group of at most 32 Morton-consecutive targets against its bounding box).
  *   pts    device, float32 [n][3], caller units; read during the call only.
  *   n      number of points, >= 1.
  *   params host, may be NULL for the defaults.
@@ -177,13 +177,17 @@ wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, i
  *   node_depth  int32 [nnodes]
  *   node_nchild int32 [nnodes]   0 for leaves
  *   far_off     int32 [ngroups+1], far_id int32 [far_entries]  per group, ascending node id
- *   near_off    int32 [ngroups+1], near_rng int32 [near_ranges][2]  merged [start,end) ranges
+ *   near_off    int32 [ngroups+1], near_rng int32 [near_ranges][2]  [start,end) point ranges
+ *               (consecutive near leaves merged, then cut to at most 256 points)
+ *   group_off   int32 [ngroups+1]  target group g = sorted points group_off[g]..group_off[g+1]-1
+ *               (at most 32; a new group starts where consecutive points' leaves share no
+ *               ancestor within 2 levels of the deeper leaf)
  *   center_scale float64 [4]     normalisation centre c (3) and scale s
  */
 wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node_start,
                              int32_t* node_count, int32_t* node_depth, int32_t* node_nchild,
                              int32_t* far_off, int32_t* far_id, int32_t* near_off,
-                             int32_t* near_rng, double* center_scale);
+                             int32_t* near_rng, int32_t* group_off, double* center_scale);
 
 /*
  * Kernel timing (not in the paper; the tracing facility of this library).

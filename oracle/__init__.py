@@ -41,6 +41,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 OP_A, OP_G, OP_AT = 0, 1, 2
 GROUP_SIZE = 32
+GROUP_SLACK = 2     # target groups never straddle leaves without a common ancestor 2 levels up
 
 
 def build(force: bool = False) -> str:
@@ -64,7 +65,10 @@ def lib():
         L.or_normalize.argtypes = [c_void_p, i64, c_void_p, c_void_p, c_void_p]
         L.or_direct.argtypes = [c_int, c_void_p, i64, c_void_p, c_void_p, i64, d, d, c_void_p, c_void_p,
                                 c_void_p]
-        L.or_tree_build.argtypes = [c_void_p, i64, c_int, c_int, c_int, d]
+        L.or_tree_build.argtypes = [c_void_p, i64, c_int, c_int, c_int, d, c_int]
+        L.or_tree_ngroups.argtypes = [c_void_p]
+        L.or_tree_ngroups.restype = i64
+        L.or_tree_groups.argtypes = [c_void_p, c_void_p]
         L.or_tree_build.restype = c_void_p
         L.or_tree_free.argtypes = [c_void_p]
         L.or_tree_nnodes.argtypes = [c_void_p]
@@ -152,11 +156,12 @@ class Tree:
     """Source octree + on-surface target groups over normalised points xn."""
 
     def __init__(self, xn, theta: float, leaf_size: int = 32, max_depth: int = 15,
-                 group_size: int = GROUP_SIZE):
+                 group_size: int = GROUP_SIZE, group_slack: int = GROUP_SLACK):
         self.xn = _f64(xn, (-1, 3))
         self.n = self.xn.shape[0]
         self.theta = float(theta)
-        self._h = lib().or_tree_build(_p(self.xn), self.n, leaf_size, group_size, max_depth, self.theta)
+        self._h = lib().or_tree_build(_p(self.xn), self.n, leaf_size, group_size, max_depth, self.theta,
+                                      int(group_slack))
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -207,8 +212,15 @@ class Tree:
         lib().or_tree_perm(self._h, _p(p))
         return p
 
+    def groups(self):
+        """Group offsets: group g = sorted points goff[g] .. goff[g+1]-1."""
+        ng = lib().or_tree_ngroups(self._h)
+        g = np.zeros(ng + 1, np.int64)
+        lib().or_tree_groups(self._h, _p(g))
+        return g
+
     def lists(self):
-        ng = (self.n + GROUP_SIZE - 1) // GROUP_SIZE
+        ng = lib().or_tree_ngroups(self._h)
         c = self.counts()
         fo = np.zeros(ng + 1, np.int64); no = np.zeros(ng + 1, np.int64)
         fi = np.zeros(max(c[0], 1), np.int64); ni = np.zeros(max(c[1], 1), np.int64)

@@ -265,11 +265,13 @@ static void build_octree(or_octree* t) {
     }
 }
 
-/* Target groups: consecutive runs of group_size Morton-sorted targets, with
- * their interaction lists against the source octree. */
+/* Target groups: runs of at most group_size consecutive Morton-sorted
+ * targets (group g = sorted targets goff[g] .. goff[g+1]-1), with their
+ * interaction lists against the source octree. */
 typedef struct {
     int64_t m, ngroups;
     int group_size;
+    int64_t* goff;
     double* y;           /* targets, normalised, sorted (m x 3) */
     int64_t* perm;       /* sorted position -> input index */
     double *glo, *ghi;   /* group bounding boxes */
@@ -309,15 +311,63 @@ static void traverse(const or_octree* t, int64_t b, const double* glo, const dou
     for (int q = 0; q < t->nchild[b]; ++q) traverse(t, t->child0[b] + q, glo, ghi, c, far, near);
 }
 
+/* Number of leading 3-bit digits two 45-bit Morton keys share (0..15). */
+static int common_digits(uint64_t a, uint64_t b) {
+    int c = 0;
+    for (int l = 14; l >= 0; --l) {
+        if (((a >> (3 * l)) & 7u) != ((b >> (3 * l)) & 7u)) break;
+        ++c;
+    }
+    return c;
+}
+
+/* Group boundaries.  Without a tree (slack < 0): fixed runs of group_size.
+ * With the source tree (targets = sources, sorted alike): a new group also
+ * starts before sorted point k when the leaves of points k-1 and k do not
+ * share an ancestor within `slack` levels of the deeper leaf, i.e. when the
+ * keys share fewer than max(depth(leaf(k-1)), depth(leaf(k))) - slack digits.
+ * A group then never straddles a jump of the Morton curve between distant
+ * cells, which keeps its bounding box (and its interaction lists) compact. */
+static int64_t group_offsets(const or_octree* t, const uint64_t* keys, int64_t m, int group_size,
+                             int slack, int64_t* goff) {
+    int* ldepth = NULL;
+    if (slack >= 0) {
+        ldepth = malloc(sizeof(int) * (m > 0 ? m : 1));
+        for (int64_t b = 0; b < t->nnodes; ++b)
+            if (t->nchild[b] == 0)
+                for (int64_t i = t->start[b]; i < t->start[b] + t->count[b]; ++i) ldepth[i] = t->depth[b];
+    }
+    int64_t ng = 0, start = 0;
+    for (int64_t k = 0; k < m; ++k) {
+        int cut = (k == 0) || (k - start == group_size);
+        if (!cut && slack >= 0) {
+            int d = ldepth[k - 1] > ldepth[k] ? ldepth[k - 1] : ldepth[k];
+            cut = common_digits(keys[k - 1], keys[k]) < d - slack;
+        }
+        if (cut) {
+            if (goff) goff[ng] = k;
+            ++ng;
+            start = k;
+        }
+    }
+    if (goff) goff[ng] = m;
+    free(ldepth);
+    return ng;
+}
+
 static void build_targets(or_targets* T, const or_octree* t, const double* yn, int64_t m,
-                          int group_size, double theta) {
+                          int group_size, double theta, int slack) {
     T->m = m; T->group_size = group_size;
     T->perm = malloc(sizeof(int64_t) * (m > 0 ? m : 1));
-    morton_order(yn, m, T->perm, NULL);
+    uint64_t* keys = malloc(sizeof(uint64_t) * (m > 0 ? m : 1));
+    morton_order(yn, m, T->perm, keys);
     T->y = malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
     for (int64_t i = 0; i < m; ++i)
         for (int k = 0; k < 3; ++k) T->y[3 * i + k] = yn[3 * T->perm[i] + k];
-    int64_t ng = (m + group_size - 1) / group_size;
+    int64_t ng = group_offsets(t, keys, m, group_size, slack, NULL);
+    T->goff = malloc(sizeof(int64_t) * (ng + 1));
+    group_offsets(t, keys, m, group_size, slack, T->goff);
+    free(keys);
     T->ngroups = ng;
     T->glo = malloc(sizeof(double) * 3 * (ng > 0 ? ng : 1));
     T->ghi = malloc(sizeof(double) * 3 * (ng > 0 ? ng : 1));
@@ -326,7 +376,7 @@ static void build_targets(or_targets* T, const or_octree* t, const double* yn, i
     ivec* nears = calloc((size_t)(ng > 0 ? ng : 1), sizeof(ivec));
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < ng; ++g) {
-        int64_t s = g * group_size, e = s + group_size < m ? s + group_size : m;
+        int64_t s = T->goff[g], e = T->goff[g + 1];
         for (int k = 0; k < 3; ++k) { T->glo[3 * g + k] = INFINITY; T->ghi[3 * g + k] = -INFINITY; }
         for (int64_t i = s; i < e; ++i)
             for (int k = 0; k < 3; ++k) {
@@ -347,7 +397,7 @@ static void build_targets(or_targets* T, const or_octree* t, const double* yn, i
     T->near_id = malloc(sizeof(int64_t) * (T->near_off[ng] > 0 ? T->near_off[ng] : 1));
     T->far_pairs = T->near_pairs = 0;
     for (int64_t g = 0; g < ng; ++g) {
-        int64_t gs = g * group_size, ge = gs + group_size < m ? gs + group_size : m;
+        int64_t gs = T->goff[g], ge = T->goff[g + 1];
         memcpy(T->far_id + T->far_off[g], fars[g].v, sizeof(int64_t) * fars[g].n);
         memcpy(T->near_id + T->near_off[g], nears[g].v, sizeof(int64_t) * nears[g].n);
         T->far_pairs += (ge - gs) * fars[g].n;
@@ -358,7 +408,7 @@ static void build_targets(or_targets* T, const or_octree* t, const double* yn, i
 }
 
 static void free_targets(or_targets* T) {
-    free(T->y); free(T->perm); free(T->glo); free(T->ghi);
+    free(T->y); free(T->perm); free(T->glo); free(T->ghi); free(T->goff);
     free(T->far_off); free(T->far_id); free(T->near_off); free(T->near_id);
 }
 
@@ -370,8 +420,10 @@ typedef struct {
     double theta;
 } or_tree;
 
+/* group_slack: the rule of group_offsets for the points as targets (< 0:
+ * fixed runs of group_size). */
 or_tree* or_tree_build(const double* xn, int64_t n, int leaf_size, int group_size, int max_depth,
-                       double theta) {
+                       double theta, int group_slack) {
     or_tree* T = calloc(1, sizeof(or_tree));
     or_octree* t = &T->src;
     t->n = n; t->leaf_size = leaf_size; t->max_depth = max_depth;
@@ -383,7 +435,7 @@ or_tree* or_tree_build(const double* xn, int64_t n, int leaf_size, int group_siz
         for (int k = 0; k < 3; ++k) t->x[3 * i + k] = xn[3 * t->perm[i] + k];
     if (n > 0) build_octree(t);
     T->theta = theta;
-    build_targets(&T->self, t, xn, n, group_size, theta);
+    build_targets(&T->self, t, xn, n, group_size, theta, group_slack);
     return T;
 }
 
@@ -419,6 +471,10 @@ void or_tree_counts(const or_tree* T, int64_t* out4) {
     out4[1] = T->self.near_off[T->self.ngroups];
     out4[2] = T->self.far_pairs;
     out4[3] = T->self.near_pairs;
+}
+int64_t or_tree_ngroups(const or_tree* T) { return T->self.ngroups; }
+void or_tree_groups(const or_tree* T, int64_t* goff) {
+    memcpy(goff, T->self.goff, sizeof(int64_t) * (T->self.ngroups + 1));
 }
 void or_tree_lists(const or_tree* T, int64_t* far_off, int64_t* far_id, int64_t* near_off, int64_t* near_id) {
     const or_targets* S = &T->self;
@@ -471,7 +527,7 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
     const double w2 = eff_w2(w);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < T->ngroups; ++g) {
-        int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
+        int64_t s = T->goff[g], e = T->goff[g + 1];
         for (int64_t i = s; i < e; ++i) {
             const double* y = T->y + 3 * i;
             double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
@@ -560,7 +616,7 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
         for (int64_t q = fcnt[b]; q < fcnt[b + 1]; ++q) {
             int64_t g = fg[q];
-            int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
+            int64_t s = T->goff[g], e = T->goff[g + 1];
             for (int64_t i = s; i < e; ++i) {
                 /* s_i gradPhi(x_i - x_B) = s_i (x_B - x_i) / (4 pi r^3) */
                 double d[3] = {rep[3 * b] - T->y[3 * i], rep[3 * b + 1] - T->y[3 * i + 1],
@@ -591,7 +647,7 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
             double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
             for (int64_t q = ncnt[b]; q < ncnt[b + 1]; ++q) {
                 int64_t g = ngp[q];
-                int64_t s = g * T->group_size, e = s + T->group_size < T->m ? s + T->group_size : T->m;
+                int64_t s = T->goff[g], e = T->goff[g + 1];
                 for (int64_t i = s; i < e; ++i) {
                     double d[3] = {x[0] - T->y[3 * i], x[1] - T->y[3 * i + 1], x[2] - T->y[3 * i + 2]};
                     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -652,7 +708,7 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
     const or_octree* t = &T->src;
     or_targets Q;
     memset(&Q, 0, sizeof(Q));
-    build_targets(&Q, t, qn, m, T->self.group_size, T->theta);
+    build_targets(&Q, t, qn, m, T->self.group_size, T->theta, -1);
     int64_t n = t->n;
     int dout = (op == OP_A) ? 1 : 3;
     double* nus = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));

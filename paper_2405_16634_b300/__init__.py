@@ -82,7 +82,7 @@ def lib():
     L.wnnc_iterate.argtypes = [P, P, P, POINTER(IterParams), P, P]
     L.wnnc_get_stats.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
     L.wnnc_tree_info.argtypes = [P] + [POINTER(c_int64)] * 7 + [POINTER(c_int)]
-    L.wnnc_tree_export.argtypes = [P] + [P] * 10
+    L.wnnc_tree_export.argtypes = [P] + [P] * 11
     L.wnnc_profile_enable.argtypes = [P, c_int]
     L.wnnc_profile_read.argtypes = [P, P, P]
     L.wnnc_profile_reset.argtypes = [P]
@@ -247,11 +247,11 @@ class Tree:
                  far_id=np.zeros(max(inf["far_entries"], 1), np.int32),
                  near_off=np.zeros(ng + 1, np.int32),
                  near_rng=np.zeros((max(inf["near_ranges"], 1), 2), np.int32),
-                 center_scale=np.zeros(4, np.float64))
+                 group_off=np.zeros(ng + 1, np.int32), center_scale=np.zeros(4, np.float64))
         ptr = lambda x: x.ctypes.data_as(c_void_p)
         _check(lib().wnnc_tree_export(self._h, *[ptr(a[k]) for k in (
             "perm", "node_start", "node_count", "node_depth", "node_nchild", "far_off", "far_id",
-            "near_off", "near_rng", "center_scale")]))
+            "near_off", "near_rng", "group_off", "center_scale")]))
         a["far_id"] = a["far_id"][:inf["far_entries"]]
         a["near_rng"] = a["near_rng"][:inf["near_ranges"]]
         return a

@@ -1,5 +1,6 @@
 // api.cu -- the extern "C" boundary (include/wnnc.h): argument checks, status
 // codes, thread-local error text, tree lifetime and work buffers.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -34,7 +35,9 @@ static void alloc_workspace(Tree& t) {
     t.arrive = dalloc<int>(nn);
     WNNC_CUDA(cudaMemset(t.arrive, 0, sizeof(int) * nn));
     if (t.params.moments_fp64) t.dmom = dalloc<double>(8 * (size_t)nn);
-    t.partials = dalloc<double>(3 * (size_t)t.self.ngroups);
+    t.partials = dalloc<double>(3 * (size_t)std::max(t.self.ngroups, t.self.nchunks));
+    t.part_slots = std::max(t.self.work.nslots, t.adj_near_work.nslots);
+    t.part_acc = dalloc<float4>((size_t)t.part_slots * 32);
     t.scalars = dalloc<double>(4);
     WNNC_CUDA(cudaMemset(t.scalars, 0, 4 * sizeof(double)));
     t.err_flag = dalloc<int>(1);
@@ -258,7 +261,8 @@ wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, i
 
 wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node_start, int32_t* node_count,
                              int32_t* node_depth, int32_t* node_nchild, int32_t* far_off, int32_t* far_id,
-                             int32_t* near_off, int32_t* near_rng, double* center_scale) {
+                             int32_t* near_off, int32_t* near_rng, int32_t* group_off,
+                             double* center_scale) {
     return guarded([&] {
         Tree& t = unwrap(tree);
         WNNC_CUDA(cudaDeviceSynchronize());
@@ -275,6 +279,7 @@ wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node
         cp(far_id, S.far_id, sizeof(int) * S.far_entries);
         cp(near_off, S.near_off, sizeof(int) * (S.ngroups + 1));
         cp(near_rng, S.near_rng, sizeof(int2) * S.near_ranges);
+        cp(group_off, S.goff, sizeof(int) * (S.ngroups + 1));
         if (center_scale) {
             for (int k = 0; k < 3; ++k) center_scale[k] = t.center[k];
             center_scale[3] = t.scale;

@@ -62,23 +62,59 @@ void dfree(T*& p) {
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------------------
-// Target set: targets sorted by Morton key, cut into groups of 32, with the
-// interaction lists of each group against the source octree.
+// Work lists.  A warp processes one Item: a slice of one group's interaction
+// lists, at most about kItemCost lane-slots long, so that no single warp
+// carries a group whose lists are unusually long.  Items run heaviest first.
+// When a group is cut into several items, each writes its partial sums to a
+// slot of a scratch buffer and a finalize pass adds the parts in order.
+// ---------------------------------------------------------------------------
+constexpr int kItemCost = 4096;     // lane-slots per item (about)
+constexpr int kMaxRange = 256;      // near ranges are cut into pieces of at most this many points
+constexpr int kGroupSlack = 2;      // group rule: see build_target_set
+
+struct Item {
+    int g;          // target group (adjoint near sums: source chunk)
+    int q0, q1;     // near ranges [q0, q1) (adjoint near sums: transposed entries)
+    int f0, f1;     // far entries [f0, f1)
+    int pslot;      // partial-sum slot if the group is cut into several items, else -1
+    int cost;       // lane-slots
+    int pad;
+};
+
+struct WorkList {
+    Item* items = nullptr;
+    int nitems = 0;
+    int4* splits = nullptr;     // (group, first slot, number of parts, -) of cut groups
+    int nsplit = 0;
+    int nslots = 0;
+};
+void free_work(WorkList& w);
+
+// ---------------------------------------------------------------------------
+// Target set: targets sorted by Morton key and cut into groups of at most 32
+// consecutive targets (one warp, one target per lane), with the interaction
+// lists of each group against the source octree.  Coordinates are stored as
+// float offsets from the origin of their fixed 32-point chunk; each group has
+// its own origin, and both origins are dyadic so that frame shifts are exact.
 // ---------------------------------------------------------------------------
 struct TargetSet {
     int64_t m = 0;          // number of targets
     int ngroups = 0;
+    int nchunks = 0;
     int64_t* perm = nullptr;      // sorted position -> input index
-    float4* pos = nullptr;        // target offset from its group origin (x,y,z,0)
-    float4* gorig = nullptr;      // group origin (dyadic, exact in fp32)
+    float4* pos = nullptr;        // target offset from its chunk origin (x,y,z,0)
+    float4* corig = nullptr;      // chunk origins (chunk = 32 consecutive sorted targets)
+    float4* gorig = nullptr;      // group origins
+    int* goff = nullptr;          // [ngroups+1] group g = sorted targets goff[g]..goff[g+1]-1
     double* glo = nullptr;        // group bounding boxes (3 per group), build only
     double* ghi = nullptr;
     int* far_off = nullptr;       // [ngroups+1]
     int* far_id = nullptr;        // node ids, ascending per group
     int* near_off = nullptr;      // [ngroups+1]
-    int2* near_rng = nullptr;     // merged [start,end) source ranges
+    int2* near_rng = nullptr;     // merged [start,end) source ranges, at most kMaxRange long
     int64_t far_entries = 0, near_ranges = 0;
     int64_t far_pairs = 0, near_pairs = 0;
+    WorkList work;                // items of the gather kernels
 };
 
 // ---------------------------------------------------------------------------
@@ -146,9 +182,11 @@ struct Tree {
     // transposed lists (adjoint, rep_mode 1)
     int* tfar_off = nullptr;      // [nnodes+1]
     int* tfar_ent = nullptr;      // far-entry index (position in self.far_id), grouped by node
-    int* tnear_off = nullptr;     // [ngroups+1], per source group
-    int2* tnear_ent = nullptr;    // (target group, lane mask of the source group)
+    int* tnear_off = nullptr;     // [nchunks+1], per source chunk
+    int2* tnear_ent = nullptr;    // (target group, lane mask of the source chunk)
     int64_t tnear_entries = 0;
+    WorkList adj_far_work;        // items over the far lists (per target group)
+    WorkList adj_near_work;       // items over the transposed near entries (per source chunk)
 
     // work buffers (sized at build)
     float4* mu_a = nullptr;       // sorted normalised mu (two buffers)
@@ -163,7 +201,9 @@ struct Tree {
     float4* vnode = nullptr;      // per node far sum (adjoint)
     int* arrive = nullptr;        // bottom-up arrival counters (zero between launches)
     double* dmom = nullptr;       // double-precision node moments (moments_fp64), 8 per node
-    double* partials = nullptr;   // per-group partial sums (3 x ngroups)
+    double* partials = nullptr;   // per-group partial sums (3 x max(ngroups, nchunks))
+    float4* part_acc = nullptr;   // scratch: partial sums of cut groups, 32 per slot
+    int part_slots = 0;
     double* scalars = nullptr;    // device scalars: [0]=E [1]=rr [2]=qq [3]=alpha
     int* err_flag = nullptr;      // device error flags
     Profiler prof;
@@ -179,7 +219,9 @@ void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cud
 
 // tree build (tree_build.cu)
 void build_tree(Tree& t, const float* pts, cudaStream_t s);
-void build_target_set(const Tree& t, TargetSet& ts, const double* yn_unsorted, int64_t m,
+// self = the tree's own points as targets (groups cut at Morton jumps);
+// otherwise fixed 32-target groups.
+void build_target_set(const Tree& t, TargetSet& ts, const double* yn_unsorted, int64_t m, bool self,
                       cudaStream_t s);
 void free_target_set(TargetSet& ts);
 void free_tree(Tree& t);

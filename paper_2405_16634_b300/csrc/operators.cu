@@ -7,11 +7,14 @@
 // A far node B acts as one source at its representative x_B carrying
 // nu_B = sum of its points' attributes (Eq. 11, Eq. 12).
 //
-// Layout: one warp per group of 32 Morton-consecutive targets, one target per
-// lane.  Sources (a merged near range of points, or a batch of far nodes) are
-// staged 32 at a time in shared memory, shifted into the group's local frame
-// (group origin + float offset, exact frame shifts), and every lane sums over
-// them with rsqrt and FMA chains.  The 1/(4 pi) factor is applied once.
+// Layout: one warp per work item (a slice of one target group's lists, see
+// WorkList), one target per lane.  Sources (a range of points, or a batch of
+// far nodes) are staged 32 at a time in shared memory, shifted into the
+// group's frame (dyadic origins, exact shifts), and every lane sums over them
+// with rsqrt and FMA chains.  The 1/(4 pi) factor is applied once.  Groups cut
+// into several items write partial sums to scratch slots; a finalize pass adds
+// them in a fixed order (results do not depend on scheduling).
+#include <algorithm>
 #include <cfloat>
 #include <utility>
 
@@ -120,7 +123,7 @@ __global__ void k_weighted_reps(int nnodes, const float4* mom, const float4* mom
 }
 
 // ---------------------------------------------------------------------------
-// Gather kernel
+// Gather kernel (one warp per work item)
 // ---------------------------------------------------------------------------
 enum Epi : int {
     kEpiStoreW = 0,      // out[perm[i]] = F
@@ -133,17 +136,24 @@ enum Epi : int {
 };
 
 struct GatherArgs {
+    // work
+    const Item* items;
+    int nitems;
+    const int4* splits;
+    int nsplit;
+    float4* part_acc;
+    // targets
     int ngroups;
-    int64_t m;
+    const int* goff;
     const float4* tpos;
+    const float4* tcorig;
     const float4* tgorig;
     const int64_t* tperm;
-    const int* far_off;
     const int* far_id;
-    const int* near_off;
     const int2* near_rng;
+    // sources
     const float4* spos;
-    const float4* sgorig;
+    const float4* scorig;
     const float4* sval;       // mu (x,y,z) per sorted source point
     const float* sval_s;      // s per sorted source point (A^T, paper mode)
     const float4* ncell;
@@ -151,6 +161,7 @@ struct GatherArgs {
     const float4* nmom;
     float w2;
     float scale;              // output unit conversion factor
+    // epilogue buffers
     float* out;
     float* s_out;
     double* partial;
@@ -190,72 +201,22 @@ __device__ __forceinline__ void interact(const float4& t, const float4& sp, cons
     }
 }
 
-template <int OP, int EPI>
-__global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs A) {
-    __shared__ float4 sp_all[kGatherWarps][32];
-    __shared__ float4 sv_all[kGatherWarps][32];
-    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.x * kGatherWarps + wl;
-    if (g >= A.ngroups) return;
-    float4* sp = sp_all[wl];
-    float4* sv = sv_all[wl];
-    const int64_t i = (int64_t)g * kGroup + lane;
-    const bool valid = i < A.m;
-    const float4 t = valid ? A.tpos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 o = A.tgorig[g];
-    Acc3 acc;
+// Shift a point stored in chunk frame `c` into the frame with origin `o`
+// (both origins are multiples of 2^-12, so the shift is exact).
+__device__ __forceinline__ float4 shift(const float4& c, const float4& o, const float4& p) {
+    return make_float4((c.x - o.x) + p.x, (c.y - o.y) + p.y, (c.z - o.z) + p.z, 0.f);
+}
 
-    // near field: merged ranges of source points
-    for (int q = A.near_off[g]; q < A.near_off[g + 1]; ++q) {
-        const int2 r = A.near_rng[q];
-        for (int base = r.x; base < r.y; base += 32) {
-            const int cnt = min(32, r.y - base);
-            if (lane < cnt) {
-                const int j = base + lane;
-                const float4 p = A.spos[j];
-                const float4 go = A.sgorig[j >> 5];
-                sp[lane] = make_float4((go.x - o.x) + p.x, (go.y - o.y) + p.y, (go.z - o.z) + p.z, 0.f);
-                if (OP == kOpATpaper) sv[lane] = make_float4(A.sval_s[j], 0.f, 0.f, 0.f);
-                else sv[lane] = A.sval[j];
-            }
-            __syncwarp();
-#pragma unroll 4
-            for (int k = 0; k < cnt; ++k) interact<OP>(t, sp[k], sv[k], A.w2, acc);
-            __syncwarp();
-        }
-    }
-    // far field: node representatives
-    const int f1 = A.far_off[g + 1];
-    for (int base = A.far_off[g]; base < f1; base += 32) {
-        const int cnt = min(32, f1 - base);
-        if (lane < cnt) {
-            const int b = A.far_id[base + lane];
-            const float4 c = A.ncell[b];
-            const float4 rp = A.nrep[b];
-            sp[lane] = make_float4((c.x - o.x) + rp.x, (c.y - o.y) + rp.y, (c.z - o.z) + rp.z, 0.f);
-            sv[lane] = A.nmom[b];
-        }
-        __syncwarp();
-#pragma unroll 4
-        for (int k = 0; k < cnt; ++k) interact<OP>(t, sp[k], sv[k], A.w2, acc);
-        __syncwarp();
-    }
-
-    // epilogues
+// Epilogue of one group (all 32 lanes call it; lane < size holds target i).
+template <int EPI>
+__device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int64_t i, bool valid,
+                                                const Acc3& acc, int lane) {
     double part = 0.0;
     if (EPI == kEpiStoreW) {
         if (valid) A.out[A.tperm[i]] = acc.x * kInv4Pi;
-    } else if (EPI == kEpiStoreGrad) {
+    } else if (EPI == kEpiStoreGrad || EPI == kEpiStoreATpaper) {
         if (valid) {
-            const float f = -kInv4Pi * A.scale;
-            const int64_t o3 = 3 * A.tperm[i];
-            A.out[o3] = acc.x * f;
-            A.out[o3 + 1] = acc.y * f;
-            A.out[o3 + 2] = acc.z * f;
-        }
-    } else if (EPI == kEpiStoreATpaper) {
-        if (valid) {
-            const float f = kInv4Pi * A.scale;
+            const float f = (EPI == kEpiStoreGrad ? -kInv4Pi : kInv4Pi) * A.scale;
             const int64_t o3 = 3 * A.tperm[i];
             A.out[o3] = acc.x * f;
             A.out[o3 + 1] = acc.y * f;
@@ -299,51 +260,149 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs A) {
     }
 }
 
+template <int OP, int EPI>
+__global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs A) {
+    __shared__ float4 sp_all[kGatherWarps][32];
+    __shared__ float4 sv_all[kGatherWarps][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x * kGatherWarps + wl;
+    if (it >= A.nitems) return;
+    float4* sp = sp_all[wl];
+    float4* sv = sv_all[wl];
+    const Item item = A.items[it];
+    const int g = item.g;
+    const int i0 = A.goff[g];
+    const int64_t i = (int64_t)i0 + lane;
+    const bool valid = lane < A.goff[g + 1] - i0;
+    const float4 o = A.tgorig[g];
+    const float4 t = valid ? shift(A.tcorig[i >> 5], o, A.tpos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    Acc3 acc;
+
+    // near field: ranges of source points
+    for (int q = item.q0; q < item.q1; ++q) {
+        const int2 r = A.near_rng[q];
+        for (int base = r.x; base < r.y; base += 32) {
+            const int cnt = min(32, r.y - base);
+            if (lane < cnt) {
+                const int j = base + lane;
+                sp[lane] = shift(A.scorig[j >> 5], o, A.spos[j]);
+                if (OP == kOpATpaper) sv[lane] = make_float4(A.sval_s[j], 0.f, 0.f, 0.f);
+                else sv[lane] = A.sval[j];
+            }
+            __syncwarp();
+#pragma unroll 4
+            for (int k = 0; k < cnt; ++k) interact<OP>(t, sp[k], sv[k], A.w2, acc);
+            __syncwarp();
+        }
+    }
+    // far field: node representatives
+    for (int base = item.f0; base < item.f1; base += 32) {
+        const int cnt = min(32, item.f1 - base);
+        if (lane < cnt) {
+            const int b = A.far_id[base + lane];
+            sp[lane] = shift(A.ncell[b], o, A.nrep[b]);
+            sv[lane] = A.nmom[b];
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < cnt; ++k) interact<OP>(t, sp[k], sv[k], A.w2, acc);
+        __syncwarp();
+    }
+
+    if (item.pslot < 0) {
+        gather_epilogue<EPI>(A, g, i, valid, acc, lane);
+    } else {
+        A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(acc.x, acc.y, acc.z, 0.f);
+    }
+}
+
+// Groups cut into several items: add the parts in order, then the epilogue.
+template <int EPI>
+__global__ void k_gather_finalize(GatherArgs A) {
+    const int sidx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sidx >= A.nsplit) return;
+    const int4 sp = A.splits[sidx];
+    const int g = sp.x;
+    Acc3 acc;
+    for (int p = 0; p < sp.z; ++p) {
+        const float4 v = A.part_acc[(int64_t)(sp.y + p) * 32 + lane];
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+    }
+    const int i0 = A.goff[g];
+    gather_epilogue<EPI>(A, g, (int64_t)i0 + lane, lane < A.goff[g + 1] - i0, acc, lane);
+}
+
 // ---------------------------------------------------------------------------
 // Exact adjoint of the rep_mode-1 tree operator A.
 //   far:  contrib[e] = sum_{i in g} s_i (x_B - x_i) / r^3 for far entry e = (g, B)
 //   node: vnode[B]   = sum of contrib over B's entries (ascending group)
-//   near: per source group, gather over (target group, lane mask) entries, then
+//   near: per source chunk, gather over (target group, lane mask) entries, then
 //         add the far sums of every node containing the point (walk to the root).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kGatherWarps)
-k_adj_far(int ngroups, int64_t n, const float4* pos, const float4* gorig, const float* sv,
-          const int* far_off, const int* far_id, const float4* ncell, const float4* ncent, float w2,
-          float4* contrib) {
+struct AdjArgs {
+    const Item* items;
+    int nitems;
+    const int4* splits;
+    int nsplit;
+    float4* part_acc;
+    int64_t n;
+    const int* goff;
+    const float4* pos;
+    const float4* corig;
+    const float4* gorig;
+    const float* sv;
+    const int* far_id;
+    const float4* ncell;
+    const float4* ncent;
+    float4* contrib;
+    const int2* tnear_ent;
+    const int* leaf_of;
+    const int* nparent;
+    const float4* vnode;
+    float w2;
+    float scale;
+    const int64_t* perm;
+    float* out;
+    float4* r_out;
+    double* partial;
+};
+
+__global__ void __launch_bounds__(32 * kGatherWarps) k_adj_far(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.x * kGatherWarps + wl;
-    if (g >= ngroups) return;
+    const int it = blockIdx.x * kGatherWarps + wl;
+    if (it >= A.nitems) return;
     float4* tp = tp_all[wl];
-    const int64_t i = (int64_t)g * kGroup + lane;
-    const bool valid = i < n;
-    float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    p.w = valid ? sv[i] : 0.f;
+    const Item item = A.items[it];
+    const int g = item.g;
+    const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
+    const int64_t i = (int64_t)i0 + lane;
+    const float4 o = A.gorig[g];
+    float4 p = lane < cnt_t ? shift(A.corig[i >> 5], o, A.pos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    p.w = lane < cnt_t ? A.sv[i] : 0.f;
     tp[lane] = p;
     __syncwarp();
-    const float4 o = gorig[g];
-    const int cnt_t = (int)min((int64_t)32, n - (int64_t)g * kGroup);
-    const int f1 = far_off[g + 1];
-    for (int base = far_off[g]; base < f1; base += 32) {
+    for (int base = item.f0; base < item.f1; base += 32) {
         const int e = base + lane;
-        if (e < f1) {
-            const int b = far_id[e];
-            const float4 c = ncell[b];
-            const float4 rp = ncent[b];
-            const float bx = (c.x - o.x) + rp.x, by = (c.y - o.y) + rp.y, bz = (c.z - o.z) + rp.z;
+        if (e < item.f1) {
+            const int b = A.far_id[e];
+            const float4 bp = shift(A.ncell[b], o, A.ncent[b]);
             float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll 4
             for (int k = 0; k < cnt_t; ++k) {
                 const float4 ti = tp[k];
-                const float dx = bx - ti.x, dy = by - ti.y, dz = bz - ti.z;
+                const float dx = bp.x - ti.x, dy = bp.y - ti.y, dz = bp.z - ti.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ir = (r2 >= w2) ? rsqrtf(r2) : 0.f;
+                const float ir = (r2 >= A.w2) ? rsqrtf(r2) : 0.f;
                 const float q = ti.w * (ir * ir * ir);
                 ax = fmaf(q, dx, ax);
                 ay = fmaf(q, dy, ay);
                 az = fmaf(q, dz, az);
             }
-            contrib[e] = make_float4(ax, ay, az, 0.f);
+            A.contrib[e] = make_float4(ax, ay, az, 0.f);
         }
     }
 }
@@ -367,42 +426,68 @@ __global__ void k_adj_node(int nnodes, const int* tfar_off, const int* tfar_ent,
     if (lane == 0) vnode[b] = make_float4(ax, ay, az, 0.f);
 }
 
+// Epilogue of one source chunk: far part (walk to the root), 1/(4 pi), store.
 template <int EPI>
-__global__ void __launch_bounds__(32 * kGatherWarps)
-k_adj_near(int ngroups, int64_t n, const float4* pos, const float4* gorig, const float* sv,
-           const int* tnear_off, const int2* tnear_ent, const int* leaf_of, const int* nparent,
-           const float4* vnode, float w2, float scale, const int64_t* perm, float* out, float4* r_out,
-           double* partial) {
+__device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j, bool valid, float ax,
+                                             float ay, float az, int lane) {
+    double part = 0.0;
+    if (valid) {
+        for (int a = A.leaf_of[j]; a >= 0; a = A.nparent[a]) {
+            const float4 v = A.vnode[a];
+            ax += v.x; ay += v.y; az += v.z;
+        }
+        ax *= kInv4Pi; ay *= kInv4Pi; az *= kInv4Pi;
+        if (EPI == kEpiStoreATpaper) {
+            const int64_t o3 = 3 * A.perm[j];
+            A.out[o3] = ax * A.scale;
+            A.out[o3 + 1] = ay * A.scale;
+            A.out[o3 + 2] = az * A.scale;
+        } else {
+            A.r_out[j] = make_float4(ax, ay, az, 0.f);
+            part = (double)ax * ax + (double)ay * ay + (double)az * az;
+        }
+    }
+    if (EPI != kEpiStoreATpaper) {
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
+        if (lane == 0) A.partial[gs] = part;
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(32 * kGatherWarps) k_adj_near(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gs = blockIdx.x * kGatherWarps + wl;   // source group (outputs)
-    if (gs >= ngroups) return;
+    const int it = blockIdx.x * kGatherWarps + wl;
+    if (it >= A.nitems) return;
     float4* tp = tp_all[wl];
+    const Item item = A.items[it];
+    const int gs = item.g;                       // source chunk (outputs)
     const int64_t j = (int64_t)gs * kGroup + lane;
-    const bool valid = j < n;
-    const float4 xj = valid ? pos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 o = gorig[gs];
+    const bool valid = j < A.n;
+    const float4 o = A.corig[gs];
+    const float4 xj = valid ? A.pos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int q = tnear_off[gs]; q < tnear_off[gs + 1]; ++q) {
-        const int2 ent = tnear_ent[q];
+    for (int q = item.q0; q < item.q1; ++q) {
+        const int2 ent = A.tnear_ent[q];
         const int g = ent.x;
         const unsigned mask = (unsigned)ent.y;
-        const int64_t i = (int64_t)g * kGroup + lane;
-        const float4 og = gorig[g];
-        if (i < n) {
-            const float4 p = pos[i];
-            tp[lane] = make_float4((og.x - o.x) + p.x, (og.y - o.y) + p.y, (og.z - o.z) + p.z, sv[i]);
+        const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
+        if (lane < cnt_t) {
+            const int64_t i = (int64_t)i0 + lane;
+            float4 p = shift(A.corig[i >> 5], o, A.pos[i]);
+            p.w = A.sv[i];
+            tp[lane] = p;
         }
         __syncwarp();
         if ((mask >> lane) & 1u) {
-            const int cnt_t = (int)min((int64_t)32, n - (int64_t)g * kGroup);
 #pragma unroll 4
             for (int k = 0; k < cnt_t; ++k) {
                 const float4 ti = tp[k];
                 // s_i gradPhi(x_i - x_j) = s_i (x_j - x_i) / r^3
                 const float dx = xj.x - ti.x, dy = xj.y - ti.y, dz = xj.z - ti.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ir = (r2 >= w2) ? rsqrtf(r2) : 0.f;
+                const float ir = (r2 >= A.w2) ? rsqrtf(r2) : 0.f;
                 const float qq = ti.w * (ir * ir * ir);
                 ax = fmaf(qq, dx, ax);
                 ay = fmaf(qq, dy, ay);
@@ -411,29 +496,26 @@ k_adj_near(int ngroups, int64_t n, const float4* pos, const float4* gorig, const
         }
         __syncwarp();
     }
-    double part = 0.0;
-    if (valid) {
-        // far part: every node on the path from the point's leaf to the root
-        for (int a = leaf_of[j]; a >= 0; a = nparent[a]) {
-            const float4 v = vnode[a];
-            ax += v.x; ay += v.y; az += v.z;
-        }
-        ax *= kInv4Pi; ay *= kInv4Pi; az *= kInv4Pi;
-        if (EPI == kEpiStoreATpaper) {
-            const int64_t o3 = 3 * perm[j];
-            out[o3] = ax * scale;
-            out[o3 + 1] = ay * scale;
-            out[o3 + 2] = az * scale;
-        } else {
-            r_out[j] = make_float4(ax, ay, az, 0.f);
-            part = (double)ax * ax + (double)ay * ay + (double)az * az;
-        }
+    if (item.pslot < 0) {
+        adj_epilogue<EPI>(A, gs, j, valid, ax, ay, az, lane);
+    } else {
+        A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(ax, ay, az, 0.f);
     }
-    if (EPI != kEpiStoreATpaper) {
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
-        if (lane == 0) partial[gs] = part;
+}
+
+template <int EPI>
+__global__ void k_adj_near_finalize(AdjArgs A) {
+    const int sidx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sidx >= A.nsplit) return;
+    const int4 sp = A.splits[sidx];
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int p = 0; p < sp.z; ++p) {
+        const float4 v = A.part_acc[(int64_t)(sp.y + p) * 32 + lane];
+        ax += v.x; ay += v.y; az += v.z;
     }
+    const int64_t j = (int64_t)sp.x * kGroup + lane;
+    adj_epilogue<EPI>(A, sp.x, j, j < A.n, ax, ay, az, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -469,15 +551,13 @@ __global__ void k_normalize_queries(const float* q, int64_t m, double cx, double
 
 // Deterministic reduction of the per-group partials and the step length of
 // Alg. 2: alpha = |r|^2 / |A r|^2 (0 if |A r| = 0).  Also records the stats.
-__global__ void k_finalize_alpha(const double* pE, const double* prr, const double* pqq, int np,
-                                 double* scalars, float* stats, float w, int* err) {
+__global__ void k_finalize_alpha(const double* pE, int nE, const double* prr, int nrr, const double* pqq,
+                                 int nqq, double* scalars, float* stats, float w, int* err) {
     __shared__ double sh[3][1024];
     double e = 0, rr = 0, qq = 0;
-    for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        e += pE[k];
-        rr += prr[k];
-        qq += pqq[k];
-    }
+    for (int k = threadIdx.x; k < nE; k += blockDim.x) e += pE[k];
+    for (int k = threadIdx.x; k < nrr; k += blockDim.x) rr += prr[k];
+    for (int k = threadIdx.x; k < nqq; k += blockDim.x) qq += pqq[k];
     sh[0][threadIdx.x] = e;
     sh[1][threadIdx.x] = rr;
     sh[2][threadIdx.x] = qq;
@@ -529,19 +609,23 @@ __global__ void k_stats_nograd(float* stats, float w) {
 // self term, repeated samples) never count, also when w = 0 (Alg. 1).
 inline float cutoff2(float w) { return fmaxf(w * w, 0x1p-40f); }
 
-GatherArgs base_args(const Tree& t, const TargetSet& ts, float w) {
+GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_acc) {
     GatherArgs a{};
+    a.items = ts.work.items;
+    a.nitems = ts.work.nitems;
+    a.splits = ts.work.splits;
+    a.nsplit = ts.work.nsplit;
+    a.part_acc = part_acc;
     a.ngroups = ts.ngroups;
-    a.m = ts.m;
+    a.goff = ts.goff;
     a.tpos = ts.pos;
+    a.tcorig = ts.corig;
     a.tgorig = ts.gorig;
     a.tperm = ts.perm;
-    a.far_off = ts.far_off;
     a.far_id = ts.far_id;
-    a.near_off = ts.near_off;
     a.near_rng = ts.near_rng;
     a.spos = t.self.pos;
-    a.sgorig = t.self.gorig;
+    a.scorig = t.self.corig;
     a.ncell = t.node_cell;
     a.nrep = t.params.rep_mode == 0 ? t.node_rep : t.node_cent;
     a.nmom = t.mom;
@@ -551,10 +635,35 @@ GatherArgs base_args(const Tree& t, const TargetSet& ts, float w) {
 
 template <int OP, int EPI>
 void launch_gather(Tree& t, const GatherArgs& a, cudaStream_t s) {
-    if (a.ngroups == 0) return;
+    if (a.nitems == 0) return;
     ProfScope ps(&t.prof, OP == kOpG ? WNNC_PROF_G : (OP == kOpA ? WNNC_PROF_A : WNNC_PROF_ADJ_NEAR), s);
-    k_gather<OP, EPI><<<ceil_div(a.ngroups, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
+    k_gather<OP, EPI><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
     WNNC_LAUNCH_CHECK();
+    if (a.nsplit > 0) {
+        k_gather_finalize<EPI><<<ceil_div((int64_t)a.nsplit * 32, kTB), kTB, 0, s>>>(a);
+        WNNC_LAUNCH_CHECK();
+    }
+}
+
+AdjArgs adj_args(const Tree& t, float w) {
+    const TargetSet& S = t.self;
+    AdjArgs a{};
+    a.part_acc = t.part_acc;
+    a.n = t.n;
+    a.goff = S.goff;
+    a.pos = S.pos;
+    a.corig = S.corig;
+    a.gorig = S.gorig;
+    a.far_id = S.far_id;
+    a.ncell = t.node_cell;
+    a.ncent = t.node_cent;
+    a.contrib = t.contrib;
+    a.tnear_ent = t.tnear_ent;
+    a.leaf_of = t.leaf_of;
+    a.nparent = t.node_parent;
+    a.vnode = t.vnode;
+    a.w2 = cutoff2(w);
+    return a;
 }
 
 }  // namespace
@@ -651,11 +760,12 @@ static void perm_in_vec(Tree& t, const float* in, float f, float4* out, cudaStre
     WNNC_LAUNCH_CHECK();
 }
 
+
 void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     const float s2 = (float)(t.scale * t.scale);
     perm_in_vec(t, mu, s2, t.mu_a, s);
     moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
-    GatherArgs a = base_args(t, t.self, w);
+    GatherArgs a = base_args(t, t.self, w, t.part_acc);
     a.sval = t.mu_a;
     a.out = out;
     launch_gather<kOpA, kEpiStoreW>(t, a, s);
@@ -665,7 +775,7 @@ void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     const float s2 = (float)(t.scale * t.scale);
     perm_in_vec(t, mu, s2, t.mu_a, s);
     moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
-    GatherArgs a = base_args(t, t.self, w);
+    GatherArgs a = base_args(t, t.self, w, t.part_acc);
     a.sval = t.mu_a;
     a.out = out;
     a.scale = (float)t.scale;
@@ -676,15 +786,15 @@ void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
 // or stores to out (caller units) when out != nullptr.
 static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, float4* r_sorted,
                           double* partial, cudaStream_t s) {
-    const TargetSet& S = t.self;
-    const int ng = S.ngroups;
-    const float w2 = cutoff2(w);
-    if (S.far_entries > 0) {
+    AdjArgs a = adj_args(t, w);
+    a.sv = s_sorted;
+    if (t.self.far_entries > 0) {
         {
             ProfScope ps(&t.prof, WNNC_PROF_ADJ_FAR, s);
-            k_adj_far<<<ceil_div(ng, kGatherWarps), 32 * kGatherWarps, 0, s>>>(
-                ng, t.n, S.pos, S.gorig, s_sorted, S.far_off, S.far_id, t.node_cell, t.node_cent, w2,
-                t.contrib);
+            AdjArgs f = a;
+            f.items = t.adj_far_work.items;
+            f.nitems = t.adj_far_work.nitems;
+            k_adj_far<<<ceil_div(f.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(f);
             WNNC_LAUNCH_CHECK();
         }
         ProfScope ps(&t.prof, WNNC_PROF_ADJ_NODE, s);
@@ -694,18 +804,32 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
     } else {
         WNNC_CUDA(cudaMemsetAsync(t.vnode, 0, sizeof(float4) * t.nnodes, s));
     }
-    const float s2 = (float)(t.scale * t.scale);
+    a.items = t.adj_near_work.items;
+    a.nitems = t.adj_near_work.nitems;
+    a.splits = t.adj_near_work.splits;
+    a.nsplit = t.adj_near_work.nsplit;
+    a.perm = t.self.perm;
+    a.out = out;
+    a.r_out = r_sorted;
+    a.partial = partial;
+    a.scale = out ? (float)(t.scale * t.scale) : 1.f;
     ProfScope ps(&t.prof, WNNC_PROF_ADJ_NEAR, s);
+    const int grid = ceil_div(a.nitems, kGatherWarps), fgrid = ceil_div((int64_t)a.nsplit * 32, kTB);
     if (out) {
-        k_adj_near<kEpiStoreATpaper><<<ceil_div(ng, kGatherWarps), 32 * kGatherWarps, 0, s>>>(
-            ng, t.n, S.pos, S.gorig, s_sorted, t.tnear_off, t.tnear_ent, t.leaf_of, t.node_parent, t.vnode,
-            w2, s2, S.perm, out, nullptr, nullptr);
+        k_adj_near<kEpiStoreATpaper><<<grid, 32 * kGatherWarps, 0, s>>>(a);
+        WNNC_LAUNCH_CHECK();
+        if (a.nsplit) {
+            k_adj_near_finalize<kEpiStoreATpaper><<<fgrid, kTB, 0, s>>>(a);
+            WNNC_LAUNCH_CHECK();
+        }
     } else {
-        k_adj_near<kEpiNormSq><<<ceil_div(ng, kGatherWarps), 32 * kGatherWarps, 0, s>>>(
-            ng, t.n, S.pos, S.gorig, s_sorted, t.tnear_off, t.tnear_ent, t.leaf_of, t.node_parent, t.vnode,
-            w2, 1.f, S.perm, nullptr, r_sorted, partial);
+        k_adj_near<kEpiNormSq><<<grid, 32 * kGatherWarps, 0, s>>>(a);
+        WNNC_LAUNCH_CHECK();
+        if (a.nsplit) {
+            k_adj_near_finalize<kEpiNormSq><<<fgrid, kTB, 0, s>>>(a);
+            WNNC_LAUNCH_CHECK();
+        }
     }
-    WNNC_LAUNCH_CHECK();
 }
 
 void eval_adjoint(Tree& t, const float* sv, float w, float* out, cudaStream_t s) {
@@ -718,7 +842,7 @@ void eval_adjoint(Tree& t, const float* sv, float w, float* out, cudaStream_t s)
         adjoint_exact(t, t.s_s, w, out, nullptr, nullptr, s);
     } else {
         moments(t, nullptr, t.s_s, 0, s);
-        GatherArgs a = base_args(t, t.self, w);
+        GatherArgs a = base_args(t, t.self, w, t.part_acc);
         a.sval_s = t.s_s;
         a.out = out;
         a.scale = (float)(t.scale * t.scale);
@@ -734,10 +858,12 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
                                                          t.scale, qn);
     WNNC_LAUNCH_CHECK();
     TargetSet Q;
+    float4* pacc = nullptr;
     try {
-        build_target_set(t, Q, qn, m, s);
+        build_target_set(t, Q, qn, m, false, s);
+        pacc = dalloc<float4>((size_t)Q.work.nslots * 32);
     } catch (...) {
-        WNNC_CUDA(cudaStreamSynchronize(s));
+        cudaStreamSynchronize(s);
         free_target_set(Q);
         cudaFree(qn);
         throw;
@@ -745,13 +871,14 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     cudaFree(qn);
     perm_in_vec(t, mu, s2, t.mu_a, s);
     moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
-    GatherArgs a = base_args(t, Q, w);
+    GatherArgs a = base_args(t, Q, w, pacc);
     a.sval = t.mu_a;
     a.out = out;
     a.scale = (float)t.scale;
     if (grad) launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
     else launch_gather<kOpA, kEpiStoreW>(t, a, s);
     WNNC_CUDA(cudaStreamSynchronize(s));
+    cudaFree(pacc);
     free_target_set(Q);
 }
 
@@ -759,7 +886,8 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
 void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params& p, cudaStream_t s,
              float* stats) {
     const int64_t n = t.n;
-    const int ng = t.self.ngroups;
+    const TargetSet& S = t.self;
+    const int npart = std::max(S.ngroups, S.nchunks);
     const float s2 = (float)(t.scale * t.scale);
     const int grid_n = ceil_div(n, kTB);
     float4* mu = t.mu_a;
@@ -771,14 +899,15 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
     }
     if (p.rescale == 1) {
         ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
-        k_perm_in_scalar<<<grid_n, kTB, 0, s>>>(area, t.self.perm, n, s2, t.area_s);
+        k_perm_in_scalar<<<grid_n, kTB, 0, s>>>(area, S.perm, n, s2, t.area_s);
         WNNC_LAUNCH_CHECK();
     }
     double* pE = t.partials;
-    double* prr = t.partials + ng;
-    double* pqq = t.partials + 2 * (int64_t)ng;
+    double* prr = t.partials + npart;
+    double* pqq = t.partials + 2 * (int64_t)npart;
     const int last = p.last_iter > 0 ? p.last_iter : p.n_iter;
     const int rep_mode = t.params.rep_mode;
+    const int n_rr = rep_mode == 1 ? S.nchunks : S.ngroups;
     for (int it = p.first_iter; it <= last; ++it) {
         const double wd = p.n_iter <= 1 ? (double)p.w1
                                         : (double)p.w2 * (double)(p.n_iter - it) / (double)(p.n_iter - 1) +
@@ -788,7 +917,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
         if (p.use_grad) {
             // s = b - A mu
             moments(t, mu, nullptr, rep_mode, s);
-            GatherArgs a = base_args(t, t.self, w);
+            GatherArgs a = base_args(t, S, w, t.part_acc);
             a.sval = mu;
             a.s_out = t.s_s;
             a.partial = pE;
@@ -799,7 +928,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             } else {
                 // the paper's s-representative treecode for A^T
                 moments(t, nullptr, t.s_s, 0, s);
-                GatherArgs c = base_args(t, t.self, w);
+                GatherArgs c = base_args(t, S, w, t.part_acc);
                 c.sval_s = t.s_s;
                 c.mu_out = t.r_s;
                 c.partial = prr;
@@ -807,13 +936,14 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             }
             // |A r|^2
             moments(t, t.r_s, nullptr, rep_mode, s);
-            GatherArgs b = base_args(t, t.self, w);
+            GatherArgs b = base_args(t, S, w, t.part_acc);
             b.sval = t.r_s;
             b.partial = pqq;
             launch_gather<kOpA, kEpiNormSq>(t, b, s);
             {
                 ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
-                k_finalize_alpha<<<1, 1024, 0, s>>>(pE, prr, pqq, ng, t.scalars, st, w, t.err_flag);
+                k_finalize_alpha<<<1, 1024, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.scalars, st, w,
+                                                    t.err_flag);
                 WNNC_LAUNCH_CHECK();
                 k_axpy<<<grid_n, kTB, 0, s>>>(mu, t.r_s, t.scalars, n, mu_alt);
                 WNNC_LAUNCH_CHECK();
@@ -825,7 +955,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
         }
         if (p.use_wnnc) {
             moments(t, mu, nullptr, rep_mode, s);
-            GatherArgs g = base_args(t, t.self, w);
+            GatherArgs g = base_args(t, S, w, t.part_acc);
             g.sval = mu;
             g.mu_cur = mu;
             g.mu_out = mu_alt;
@@ -836,7 +966,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
         }
     }
     ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
-    k_perm_out_vec<<<grid_n, kTB, 0, s>>>(mu, t.self.perm, n, 1.f / s2, mu_inout);
+    k_perm_out_vec<<<grid_n, kTB, 0, s>>>(mu, S.perm, n, 1.f / s2, mu_inout);
     WNNC_LAUNCH_CHECK();
 }
 

@@ -253,38 +253,107 @@ __global__ void k_node_cells(const uint64_t* keys, const int* start, const int* 
 }
 
 // ---------------------------------------------------------------------------
-// Target groups
+// Target groups and coordinate frames
 // ---------------------------------------------------------------------------
 
-// warp per group: bounding box, dyadic origin (multiple of 2^-12), offsets
-__global__ void k_group_boxes(const double* ys, int64_t m, int ng, double* glo, double* ghi,
-                              float4* gorig, float4* pos) {
-    int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ double dyadic12(double v) { return rint(v * 4096.0) / 4096.0; }
+
+// Number of leading 3-bit digits two 45-bit keys share (0..15).
+__device__ __forceinline__ int common_digits(uint64_t a, uint64_t b) {
+    uint64_t x = a ^ b;
+    if (x == 0) return 15;
+    int hb = 63 - __clzll((long long)x);
+    return 14 - hb / 3;
+}
+
+// Group rule for the points as targets: a new group starts before sorted
+// point k when the leaves of k-1 and k share no ancestor within `slack`
+// levels of the deeper leaf (the keys share fewer than that many digits).
+__global__ void k_group_cuts(const uint64_t* keys, const int* leaf_of, const int* ndepth, int64_t m,
+                             int slack, int* cut) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    int c = 1;
+    if (k > 0) {
+        int d = max(ndepth[leaf_of[k - 1]], ndepth[leaf_of[k]]);
+        c = common_digits(keys[k - 1], keys[k]) < d - slack;
+    }
+    cut[k] = c;
+}
+
+// out[scan[k]] = k for every flagged k.
+__global__ void k_compact(const int* flag, const int* scan, int64_t m, int* out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m && flag[k]) out[scan[k]] = (int)k;
+}
+
+// Runs between cuts are cut again into groups of at most 32.
+__global__ void k_run_ngroups(const int* run_start, int nruns, int64_t m, int* cnt) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nruns) return;
+    int e = r + 1 < nruns ? run_start[r + 1] : (int)m;
+    cnt[r] = (e - run_start[r] + kGroup - 1) / kGroup;
+}
+
+__global__ void k_run_goff(const int* run_start, int nruns, int64_t m, const int* cnt_off, int* goff) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nruns) return;
+    int e = r + 1 < nruns ? run_start[r + 1] : (int)m;
+    int b = cnt_off[r];
+    for (int s = run_start[r], j = 0; s < e; s += kGroup, ++j) goff[b + j] = s;
+    if (r == nruns - 1) goff[cnt_off[nruns]] = (int)m;
+}
+
+__global__ void k_fixed_goff(int ng, int64_t m, int* goff) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g <= ng) goff[g] = (int)min((int64_t)g * kGroup, m);
+}
+
+// Warp per fixed chunk of 32 sorted targets: dyadic origin and float offsets.
+__global__ void k_chunk_frames(const double* ys, int64_t m, int nchunks, float4* corig, float4* pos) {
+    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
-    if (g >= ng) return;
-    int64_t i = (int64_t)g * kGroup + lane;
+    if (c >= nchunks) return;
+    int64_t i = (int64_t)c * kGroup + lane;
     bool valid = i < m;
-    double l[3], h[3];
+    double o[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         double v = valid ? ys[3 * i + k] : 0.0;
-        l[k] = valid ? v : INFINITY;
-        h[k] = valid ? v : -INFINITY;
-        for (int o = 16; o > 0; o >>= 1) {
-            l[k] = fmin(l[k], __shfl_xor_sync(0xffffffffu, l[k], o));
-            h[k] = fmax(h[k], __shfl_xor_sync(0xffffffffu, h[k], o));
+        double l = valid ? v : INFINITY, h = valid ? v : -INFINITY;
+        for (int d = 16; d > 0; d >>= 1) {
+            l = fmin(l, __shfl_xor_sync(0xffffffffu, l, d));
+            h = fmax(h, __shfl_xor_sync(0xffffffffu, h, d));
         }
+        o[k] = dyadic12(0.5 * (l + h));
     }
-    double o[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) o[k] = rint(0.5 * (l[k] + h[k]) * 4096.0) / 4096.0;
-    if (lane == 0) {
-        for (int k = 0; k < 3; ++k) { glo[3 * g + k] = l[k]; ghi[3 * g + k] = h[k]; }
-        gorig[g] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
-    }
+    if (lane == 0) corig[c] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
     if (valid)
         pos[i] = make_float4((float)(ys[3 * i] - o[0]), (float)(ys[3 * i + 1] - o[1]),
                              (float)(ys[3 * i + 2] - o[2]), 0.f);
+}
+
+// Warp per group: bounding box and dyadic origin.
+__global__ void k_group_boxes(const double* ys, const int* goff, int ng, double* glo, double* ghi,
+                              float4* gorig) {
+    int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    int64_t i = (int64_t)goff[g] + lane;
+    bool valid = i < goff[g + 1];
+    double o[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = valid ? ys[3 * i + k] : 0.0;
+        double l = valid ? v : INFINITY, h = valid ? v : -INFINITY;
+        for (int d = 16; d > 0; d >>= 1) {
+            l = fmin(l, __shfl_xor_sync(0xffffffffu, l, d));
+            h = fmax(h, __shfl_xor_sync(0xffffffffu, h, d));
+        }
+        if (lane == 0) { glo[3 * g + k] = l; ghi[3 * g + k] = h; }
+        o[k] = dyadic12(0.5 * (l + h));
+    }
+    if (lane == 0) gorig[g] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
 }
 
 // Far test of a group box against node b (see the file comment).
@@ -380,7 +449,9 @@ k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* n
     }
 }
 
-// theta = 0: every leaf is near for every group (one merged range [0, n)).
+
+// theta = 0: every leaf is near for every group (one merged range [0, n),
+// cut into pieces later).
 __global__ void k_all_near(int ng, int n, int* near_off, int2* rng) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g > ng) return;
@@ -422,17 +493,30 @@ __global__ void k_near_ranges(const uint64_t* keys, const uint32_t* leaf, int64_
     if (hscan[e + 2] - hscan[e + 1] == 1) rng[r].y = s + ncount[leaf[e]];
 }
 
+// Cut ranges longer than kMaxRange into pieces.
+__global__ void k_cap_count(const int2* rng, int64_t nr, int* cnt) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nr) cnt[q] = (rng[q].y - rng[q].x + kMaxRange - 1) / kMaxRange;
+}
+__global__ void k_cap_write(const int2* rng, int64_t nr, const int* off, int2* out) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nr) return;
+    int2 r = rng[q];
+    int p = off[q];
+    for (int s = r.x; s < r.y; s += kMaxRange) out[p++] = make_int2(s, min(s + kMaxRange, r.y));
+}
+
 __global__ void k_gather_i32(const int* src, const int* idx, int n, int* dst) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = src[idx[i]];
 }
 
 // Interaction pair counts: far pairs = sum_g |g| * far(g), near = sum_g |g| * sum |range|
-__global__ void k_pair_counts(int ng, int64_t m, const int* far_off, const int* near_off,
+__global__ void k_pair_counts(int ng, const int* goff, const int* far_off, const int* near_off,
                               const int2* rng, unsigned long long* out) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
-    int64_t sz = min((int64_t)kGroup, m - (int64_t)g * kGroup);
+    int64_t sz = goff[g + 1] - goff[g];
     int64_t nf = far_off[g + 1] - far_off[g];
     int64_t nn = 0;
     for (int q = near_off[g]; q < near_off[g + 1]; ++q) nn += rng[q].y - rng[q].x;
@@ -446,8 +530,8 @@ __global__ void k_tfar_keys(const int* far_id, int64_t nent, uint64_t* keys) {
     if (e < nent) keys[e] = ((uint64_t)(uint32_t)far_id[e] << 32) | (uint32_t)e;
 }
 
-// Transposed near entries: for each merged range of target group g, the source
-// groups it overlaps, with the mask of overlapped lanes.
+// Transposed near entries: for each near range of target group g, the source
+// chunks it overlaps, with the mask of overlapped lanes.
 __global__ void k_tnear_count(const int2* rng, int64_t nr, int* cnt) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nr) return;
@@ -477,7 +561,7 @@ __global__ void k_key_heads(const uint64_t* keys, int64_t n, int* head) {
     if (e < n) head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
 }
 
-// Equal (source group, target group) keys: OR their masks into one entry.
+// Equal (source chunk, target group) keys: OR their masks into one entry.
 __global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* masks, int64_t n,
                               const int* head_scan, int2* ent, uint64_t* ukeys) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -488,6 +572,85 @@ __global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* masks, int64
     int r = head_scan[e];
     ent[r] = make_int2((int)(uint32_t)(keys[e] & 0xffffffffu), (int)m);
     ukeys[r] = keys[e];
+}
+
+// ---------------------------------------------------------------------------
+// Work lists: each segment's lists (near units, then far entries in blocks of
+// 32) are cut greedily into items of about kItemCost lane-slots.
+//   mode 0: near units are ranges costing their length (gather kernels)
+//   mode 1: near units are transposed entries costing 32 each (adjoint near)
+//   mode 2: far entries only (adjoint far)
+// ---------------------------------------------------------------------------
+struct ItemWalk {
+    int g, q0, f0, cost, k;
+    Item* out;
+    int base, pslot_base, nparts;
+    bool partials;
+    __device__ void emit(int q1, int f1) {
+        if (out) {
+            Item it;
+            it.g = g; it.q0 = q0; it.q1 = q1; it.f0 = f0; it.f1 = f1;
+            it.pslot = (partials && nparts > 1) ? pslot_base + k : -1;
+            it.cost = cost; it.pad = 0;
+            out[base + k] = it;
+        }
+        ++k;
+        q0 = q1;
+        f0 = f1;
+        cost = 0;
+    }
+};
+
+__device__ int walk_items(int mode, int g, const int* near_off, const int2* rng, const int* far_off,
+                          Item* out, int base, int pslot_base, int nparts, bool partials) {
+    const int qb = near_off ? near_off[g] : 0, qe = near_off ? near_off[g + 1] : 0;
+    const int fb = far_off ? far_off[g] : 0, fe = far_off ? far_off[g + 1] : 0;
+    ItemWalk w{g, qb, fb, 0, 0, out, base, pslot_base, nparts, partials};
+    for (int q = qb; q < qe; ++q) {
+        int c = mode == 1 ? 32 : rng[q].y - rng[q].x;
+        if (w.cost > 0 && w.cost + c > kItemCost) w.emit(q, fb);
+        w.cost += c;
+    }
+    for (int e = fb; e < fe; e += 32) {
+        int c = min(32, fe - e);
+        if (w.cost > 0 && w.cost + c > kItemCost) w.emit(qe, e);
+        w.cost += c;
+    }
+    if (w.cost > 0 || w.k == 0) w.emit(qe, fe);
+    return w.k;
+}
+
+__global__ void k_items_count(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
+                              int* cnt, int* slots) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg) return;
+    int c = walk_items(mode, g, near_off, rng, far_off, nullptr, 0, 0, 0, false);
+    cnt[g] = c;
+    slots[g] = c > 1 ? c : 0;
+}
+
+__global__ void k_items_fill(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
+                             const int* cnt, const int* item_off, const int* slot_off, bool partials,
+                             Item* items, int4* splits, const int* split_off) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg) return;
+    walk_items(mode, g, near_off, rng, far_off, items, item_off[g], slot_off[g], cnt[g], partials);
+    if (partials && cnt[g] > 1) splits[split_off[g]] = make_int4(g, slot_off[g], cnt[g], 0);
+}
+
+__global__ void k_split_flags(const int* cnt, int nseg, int* flag) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < nseg) flag[g] = cnt[g] > 1;
+}
+
+// Heaviest first: key = (INT_MAX - cost) << 32 | item index.
+__global__ void k_item_keys(const Item* items, int n, uint64_t* keys) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keys[i] = ((uint64_t)(uint32_t)(0x7fffffff - items[i].cost) << 32) | (uint32_t)i;
+}
+__global__ void k_item_permute(const Item* in, const uint64_t* keys, int n, Item* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[(uint32_t)(keys[i] & 0xffffffffu)];
 }
 
 }  // namespace
@@ -509,11 +672,53 @@ static int bits_for(int64_t v) {
     return b;
 }
 
-void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m, cudaStream_t s) {
+void free_work(WorkList& w) {
+    dfree(w.items);
+    dfree(w.splits);
+    w.nitems = w.nsplit = w.nslots = 0;
+}
+
+// Build the work list of nseg segments (see walk_items), heaviest item first.
+static void build_work(WorkList& w, int mode, int nseg, const int* near_off, const int2* rng,
+                       const int* far_off, bool partials, cudaStream_t s) {
+    int* cnt = dalloc<int>(nseg + 1);
+    int* slots = dalloc<int>(nseg + 1);
+    int* item_off = dalloc<int>(nseg + 2);
+    int* slot_off = dalloc<int>(nseg + 2);
+    int* flag = dalloc<int>(nseg + 1);
+    int* split_off = dalloc<int>(nseg + 2);
+    k_items_count<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cnt, slots);
+    WNNC_LAUNCH_CHECK();
+    exclusive_scan_i32(cnt, item_off, nseg, s);
+    exclusive_scan_i32(slots, slot_off, nseg, s);
+    k_split_flags<<<ceil_div(nseg, kTB), kTB, 0, s>>>(cnt, nseg, flag);
+    WNNC_LAUNCH_CHECK();
+    exclusive_scan_i32(flag, split_off, nseg, s);
+    w.nitems = read_int(item_off + nseg, s);
+    w.nslots = partials ? read_int(slot_off + nseg, s) : 0;
+    w.nsplit = partials ? read_int(split_off + nseg, s) : 0;
+    Item* tmp = dalloc<Item>(w.nitems);
+    w.splits = dalloc<int4>(w.nsplit);
+    k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cnt, item_off,
+                                                    slot_off, partials, tmp, w.splits, split_off);
+    WNNC_LAUNCH_CHECK();
+    uint64_t* keys = dalloc<uint64_t>(w.nitems);
+    k_item_keys<<<ceil_div(w.nitems, kTB), kTB, 0, s>>>(tmp, w.nitems, keys);
+    WNNC_LAUNCH_CHECK();
+    radix_sort_pairs(keys, nullptr, w.nitems, 63, s);
+    w.items = dalloc<Item>(w.nitems);
+    k_item_permute<<<ceil_div(w.nitems, kTB), kTB, 0, s>>>(tmp, keys, w.nitems, w.items);
+    WNNC_LAUNCH_CHECK();
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    cudaFree(cnt); cudaFree(slots); cudaFree(item_off); cudaFree(slot_off); cudaFree(flag);
+    cudaFree(split_off); cudaFree(tmp); cudaFree(keys);
+}
+
+void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m, bool self,
+                      cudaStream_t s) {
     ts.m = m;
-    ts.ngroups = ceil_div(m, kGroup);
-    const int ng = ts.ngroups;
-    // Morton order of the targets
+    ts.nchunks = ceil_div(m, kGroup);
+    // Morton order of the targets (the same order as the sources when self)
     uint64_t* keys = dalloc<uint64_t>(m);
     uint32_t* idx = dalloc<uint32_t>(m);
     k_keys_from_xn<<<ceil_div(m, kTB), kTB, 0, s>>>(yn, m, keys, idx);
@@ -523,29 +728,62 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     ts.perm = dalloc<int64_t>(m);
     k_gather_sorted<<<ceil_div(m, kTB), kTB, 0, s>>>(yn, idx, m, ys, ts.perm);
     WNNC_LAUNCH_CHECK();
-    WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(keys);
-    cudaFree(idx);
+    // coordinate frames of the fixed chunks
+    ts.corig = dalloc<float4>(ts.nchunks);
+    ts.pos = dalloc<float4>(m);
+    k_chunk_frames<<<ceil_div((int64_t)ts.nchunks * 32, kTB), kTB, 0, s>>>(ys, m, ts.nchunks, ts.corig, ts.pos);
+    WNNC_LAUNCH_CHECK();
     // groups
+    if (self) {
+        int* cut = dalloc<int>(m + 1);
+        int* cscan = dalloc<int>(m + 2);
+        k_group_cuts<<<ceil_div(m, kTB), kTB, 0, s>>>(keys, t.leaf_of, t.node_depth, m, kGroupSlack, cut);
+        WNNC_LAUNCH_CHECK();
+        exclusive_scan_i32(cut, cscan, m, s);
+        int nruns = read_int(cscan + m, s);
+        int* run_start = dalloc<int>(nruns);
+        k_compact<<<ceil_div(m, kTB), kTB, 0, s>>>(cut, cscan, m, run_start);
+        WNNC_LAUNCH_CHECK();
+        int* rcnt = dalloc<int>(nruns + 1);
+        int* roff = dalloc<int>(nruns + 2);
+        k_run_ngroups<<<ceil_div(nruns, kTB), kTB, 0, s>>>(run_start, nruns, m, rcnt);
+        WNNC_LAUNCH_CHECK();
+        exclusive_scan_i32(rcnt, roff, nruns, s);
+        ts.ngroups = read_int(roff + nruns, s);
+        ts.goff = dalloc<int>(ts.ngroups + 1);
+        k_run_goff<<<ceil_div(nruns, kTB), kTB, 0, s>>>(run_start, nruns, m, roff, ts.goff);
+        WNNC_LAUNCH_CHECK();
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        cudaFree(cut); cudaFree(cscan); cudaFree(run_start); cudaFree(rcnt); cudaFree(roff);
+    } else {
+        ts.ngroups = ts.nchunks;
+        ts.goff = dalloc<int>(ts.ngroups + 1);
+        k_fixed_goff<<<ceil_div(ts.ngroups + 1, kTB), kTB, 0, s>>>(ts.ngroups, m, ts.goff);
+        WNNC_LAUNCH_CHECK();
+    }
+    const int ng = ts.ngroups;
     ts.glo = dalloc<double>(3 * (size_t)ng);
     ts.ghi = dalloc<double>(3 * (size_t)ng);
     ts.gorig = dalloc<float4>(ng);
-    ts.pos = dalloc<float4>(m);
-    k_group_boxes<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(ys, m, ng, ts.glo, ts.ghi, ts.gorig, ts.pos);
+    k_group_boxes<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(ys, ts.goff, ng, ts.glo, ts.ghi, ts.gorig);
     WNNC_LAUNCH_CHECK();
     WNNC_CUDA(cudaStreamSynchronize(s));
     cudaFree(ys);
+    cudaFree(keys);
+    cudaFree(idx);
 
     ts.far_off = dalloc<int>(ng + 1);
-    ts.near_off = dalloc<int>(ng + 1);
+    int* near_off0 = dalloc<int>(ng + 1);     // merged (uncut) ranges
+    int2* rng0 = nullptr;
+    int64_t nr0 = 0;
     const double theta = (double)t.params.theta;
     if (theta <= 0.0) {
         ts.far_entries = 0;
         ts.far_id = dalloc<int>(1);
         WNNC_CUDA(cudaMemsetAsync(ts.far_off, 0, sizeof(int) * (ng + 1), s));
-        ts.near_rng = dalloc<int2>(ng);
-        ts.near_ranges = ng;
-        k_all_near<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(ng, (int)t.n, ts.near_off, ts.near_rng);
+        rng0 = dalloc<int2>(ng);
+        nr0 = ng;
+        k_all_near<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(ng, (int)t.n, near_off0, rng0);
         WNNC_LAUNCH_CHECK();
     } else {
         int* far_cnt = dalloc<int>(ng + 1);
@@ -560,7 +798,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
                                                     nullptr, err);
         WNNC_LAUNCH_CHECK();
         if (read_int(err, s)) {
-            cudaFree(far_cnt); cudaFree(near_cnt); cudaFree(leaf_off); cudaFree(err);
+            cudaFree(far_cnt); cudaFree(near_cnt); cudaFree(leaf_off); cudaFree(err); cudaFree(near_off0);
             fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
         }
         exclusive_scan_i32(far_cnt, ts.far_off, ng, s);
@@ -598,24 +836,44 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             WNNC_CUDA(cudaStreamSynchronize(s));
         }
         exclusive_scan_i32(head, hscan, nleafent + 1, s);
-        int nr = read_int(hscan + nleafent, s);   // heads among the real entries
-        ts.near_ranges = nr;
-        ts.near_rng = dalloc<int2>(nr);
+        nr0 = read_int(hscan + nleafent, s);   // heads among the real entries
+        rng0 = dalloc<int2>(nr0);
         if (nleafent) {
             k_near_ranges<<<ceil_div(nleafent, kTB), kTB, 0, s>>>(nkeys, nvals, nleafent, t.node_count, hscan,
-                                                                 ts.near_rng);
+                                                                 rng0);
             WNNC_LAUNCH_CHECK();
         }
         // range offsets per group = number of heads before the group's first leaf entry
-        k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(hscan, leaf_off, ng + 1, ts.near_off);
+        k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(hscan, leaf_off, ng + 1, near_off0);
         WNNC_LAUNCH_CHECK();
         WNNC_CUDA(cudaStreamSynchronize(s));
         cudaFree(fkeys); cudaFree(nkeys); cudaFree(nvals); cudaFree(head); cudaFree(hscan);
         cudaFree(far_cnt); cudaFree(near_cnt); cudaFree(leaf_off); cudaFree(err);
     }
+    // cut ranges to at most kMaxRange points
+    {
+        int* cnt = dalloc<int>(nr0 + 1);
+        int* off = dalloc<int>(nr0 + 2);
+        if (nr0) {
+            k_cap_count<<<ceil_div(nr0, kTB), kTB, 0, s>>>(rng0, nr0, cnt);
+            WNNC_LAUNCH_CHECK();
+        }
+        exclusive_scan_i32(cnt, off, nr0, s);
+        ts.near_ranges = read_int(off + nr0, s);
+        ts.near_rng = dalloc<int2>(ts.near_ranges);
+        if (nr0) {
+            k_cap_write<<<ceil_div(nr0, kTB), kTB, 0, s>>>(rng0, nr0, off, ts.near_rng);
+            WNNC_LAUNCH_CHECK();
+        }
+        ts.near_off = dalloc<int>(ng + 1);
+        k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(off, near_off0, ng + 1, ts.near_off);
+        WNNC_LAUNCH_CHECK();
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        cudaFree(cnt); cudaFree(off); cudaFree(rng0); cudaFree(near_off0);
+    }
     unsigned long long* pc = dalloc<unsigned long long>(2);
     WNNC_CUDA(cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), s));
-    k_pair_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ng, m, ts.far_off, ts.near_off, ts.near_rng, pc);
+    k_pair_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ng, ts.goff, ts.far_off, ts.near_off, ts.near_rng, pc);
     WNNC_LAUNCH_CHECK();
     unsigned long long hc[2];
     WNNC_CUDA(cudaMemcpyAsync(hc, pc, sizeof(hc), cudaMemcpyDeviceToHost, s));
@@ -623,11 +881,13 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     cudaFree(pc);
     ts.far_pairs = (int64_t)hc[0];
     ts.near_pairs = (int64_t)hc[1];
+    build_work(ts.work, 0, ng, ts.near_off, ts.near_rng, ts.far_off, true, s);
 }
 
 void free_target_set(TargetSet& ts) {
-    dfree(ts.perm); dfree(ts.pos); dfree(ts.gorig); dfree(ts.glo); dfree(ts.ghi);
-    dfree(ts.far_off); dfree(ts.far_id); dfree(ts.near_off); dfree(ts.near_rng);
+    dfree(ts.perm); dfree(ts.pos); dfree(ts.corig); dfree(ts.gorig); dfree(ts.goff); dfree(ts.glo);
+    dfree(ts.ghi); dfree(ts.far_off); dfree(ts.far_id); dfree(ts.near_off); dfree(ts.near_rng);
+    free_work(ts.work);
 }
 
 static void grow_nodes(Tree& t, int& cap, int need) {
@@ -739,16 +999,16 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     }
 
     // --- the points as targets: same Morton order as the sources ---
-    build_target_set(t, t.self, xn, n, s);
+    build_target_set(t, t.self, xn, n, true, s);
     cudaFree(xn);
     cudaFree(idx);
     cudaFree(perm_tmp);
     cudaFree(part);
     cudaFree(cs);
 
-    // --- transposed lists for the adjoint ---
+    // --- transposed lists and work lists for the adjoint ---
     const TargetSet& S = t.self;
-    const int ng = S.ngroups;
+    const int ng = S.ngroups, nch = S.nchunks;
     t.tfar_off = dalloc<int>(t.nnodes + 1);
     {
         int64_t ne = S.far_entries;
@@ -781,7 +1041,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         uint32_t* msk = dalloc<uint32_t>(ne);
         k_tnear_fill<<<ceil_div(ng, kTB), kTB, 0, s>>>(S.near_rng, S.near_off, ng, coff, k, msk);
         WNNC_LAUNCH_CHECK();
-        radix_sort_pairs(k, msk, ne, 32 + bits_for(ng), s);
+        radix_sort_pairs(k, msk, ne, 32 + bits_for(nch), s);
         int* head = dalloc<int>(ne + 1);
         int* hscan = dalloc<int>(ne + 2);
         if (ne) {
@@ -797,12 +1057,14 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             k_tnear_merge<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, msk, ne, hscan, t.tnear_ent, uk);
             WNNC_LAUNCH_CHECK();
         }
-        t.tnear_off = dalloc<int>(ng + 1);
-        segment_offsets_hi32(uk, nu, t.tnear_off, ng, s);
+        t.tnear_off = dalloc<int>(nch + 1);
+        segment_offsets_hi32(uk, nu, t.tnear_off, nch, s);
         WNNC_CUDA(cudaStreamSynchronize(s));
         cudaFree(cnt); cudaFree(coff); cudaFree(k); cudaFree(msk); cudaFree(head); cudaFree(hscan);
         cudaFree(uk);
     }
+    build_work(t.adj_far_work, 2, ng, nullptr, nullptr, S.far_off, false, s);
+    build_work(t.adj_near_work, 1, nch, t.tnear_off, nullptr, nullptr, true, s);
 }
 
 void free_tree(Tree& t) {
@@ -814,9 +1076,11 @@ void free_tree(Tree& t) {
     t.level_off = nullptr;
     free_target_set(t.self);
     dfree(t.tfar_off); dfree(t.tfar_ent); dfree(t.tnear_off); dfree(t.tnear_ent);
+    free_work(t.adj_far_work);
+    free_work(t.adj_near_work);
     dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
     dfree(t.mom_x); dfree(t.dmom); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode); dfree(t.arrive);
-    dfree(t.partials); dfree(t.scalars); dfree(t.err_flag);
+    dfree(t.partials); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
 
 }  // namespace wnnc

@@ -90,8 +90,12 @@ def test_tree_and_lists_match_oracle_exactly(theta):
     assert np.array_equal(e["node_count"], nd["count"])
     assert np.array_equal(e["node_depth"], nd["depth"])
     assert np.array_equal(e["node_nchild"], nd["nchild"])
+    assert np.array_equal(e["group_off"], ot.groups())
     fo, fi, no, ni = ot.lists()
     assert np.array_equal(e["far_off"], fo)
+    assert np.all(np.diff(e["group_off"]) <= 32) and np.all(np.diff(e["group_off"]) >= 1)
+    r = e["near_rng"]
+    assert np.all(r[:, 1] - r[:, 0] <= 256) and np.all(r[:, 1] > r[:, 0])
     ng = len(fo) - 1
     for g in range(ng):
         assert np.array_equal(e["far_id"][fo[g]:fo[g + 1]], np.sort(fi[fo[g]:fo[g + 1]]))

@@ -242,19 +242,50 @@ def test_tree_lists_partition_sources_and_satisfy_alg4(cloud20k):
     t = oracle.Tree(xn, theta)
     nd = t.nodes()
     fo, fi, no, ni = t.lists()
+    go = t.groups()
     xs = xn[t.perm()]
     n = len(xn)
+    assert go[0] == 0 and go[-1] == n and np.all(np.diff(go) >= 1) and np.all(np.diff(go) <= 32)
     for g in range(0, len(fo) - 1, 37):
         cover = np.zeros(n, np.int32)
         for b in fi[fo[g]:fo[g + 1]]:
             cover[nd["start"][b]:nd["start"][b] + nd["count"][b]] += 1
-            ti = xs[g * 32:min(g * 32 + 32, n)]
+            ti = xs[go[g]:go[g + 1]]
             dist = np.linalg.norm(ti - nd["cent"][b], axis=1)
             assert np.all(dist > (1 / theta) * 2.0 ** (1 - nd["depth"][b]))
         for b in ni[no[g]:no[g + 1]]:
             assert nd["nchild"][b] == 0
             cover[nd["start"][b]:nd["start"][b] + nd["count"][b]] += 1
         assert np.all(cover == 1)
+
+
+def test_groups_never_straddle_distant_leaves(cloud20k):
+    """Target groups are runs of at most 32 sorted points that end where two
+    consecutive points' leaves share no ancestor within 2 levels; with a
+    negative slack they are plain runs of 32."""
+    xn = cloud20k[0]
+    t = oracle.Tree(xn, 0.5)
+    nd = t.nodes()
+    go = t.groups()
+    leaves = np.where(nd["nchild"] == 0)[0]
+    leaf_of = np.zeros(len(xn), np.int64)
+    for b in leaves:
+        leaf_of[nd["start"][b]:nd["start"][b] + nd["count"][b]] = b
+    # ancestors of every node
+    def ancestors(b):
+        out = []
+        while b >= 0:
+            out.append(b)
+            b = nd["parent"][b]
+        return out
+    for g in range(len(go) - 1):
+        for k in range(go[g] + 1, go[g + 1]):
+            a, b = leaf_of[k - 1], leaf_of[k]
+            d = max(nd["depth"][a], nd["depth"][b])
+            common = set(ancestors(a)) & set(ancestors(b))
+            assert max(nd["depth"][c] for c in common) >= d - 2
+    fixed = oracle.Tree(xn, 0.5, group_slack=-1).groups()
+    assert np.array_equal(fixed, np.minimum(np.arange(len(fixed)) * 32, len(xn)))
 
 
 def test_tree_limit_equals_direct(cloud20k):
