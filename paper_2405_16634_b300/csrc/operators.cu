@@ -38,7 +38,7 @@ constexpr int kGatherWarps = 4;
 template <bool SCALAR, bool WEIGHTED, class Acc>
 __global__ void k_moments(int nnodes, const int* nstart, const int* ncount, const int* nparent,
                           const int* nchild, const int* nchild0, const float4* ncell,
-                          const float4* spos, const float4* sgorig, const float4* nu_vec,
+                          const float4* spos, const float4* scorig, const float4* nu_vec,
                           const float* nu_s, float4* mom, float4* momx, Acc* dmom, int* arrive) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnodes || nchild[b] != 0) return;
@@ -57,7 +57,7 @@ __global__ void k_moments(int nnodes, const int* nstart, const int* ncount, cons
         m0 += v0; m1 += v1; m2 += v2; wsum += a;
         if (WEIGHTED) {
             float4 p = spos[j];
-            float4 go = sgorig[j >> 5];
+            float4 go = scorig[j >> 5];   // the point's chunk frame
             x0 += (Acc)a * (Acc)((go.x - cb.x) + p.x);
             x1 += (Acc)a * (Acc)((go.y - cb.y) + p.y);
             x2 += (Acc)a * (Acc)((go.z - cb.z) + p.z);
@@ -735,11 +735,11 @@ void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, cud
 #define WNNC_MOM(SC, WE)                                                                          \
     if (fp64)                                                                                     \
         k_moments<SC, WE, double><<<grid, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count,       \
-            t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.gorig,    \
+            t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.corig,    \
             nu_vec, nu_s, t.mom, t.mom_x, t.dmom, t.arrive);                                       \
     else                                                                                          \
         k_moments<SC, WE, float><<<grid, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count,        \
-            t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.gorig,    \
+            t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.corig,    \
             nu_vec, nu_s, t.mom, t.mom_x, (float*)nullptr, t.arrive);
     if (nu_s) {
         if (w) { WNNC_MOM(true, true) } else { WNNC_MOM(true, false) }
