@@ -216,6 +216,27 @@ wnnc_status wnnc_profile_reset(wnnc_tree* tree);
  * threads, all trees); for counting the launches inside a timed region. */
 int64_t wnnc_kernel_launches(void);
 
+/*
+ * F(q_k; mu) at m query points by direct summation over all n points, with no
+ * tree and no device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc (a host application
+ * that owns all device memory through its own pool, a plugin sandbox, or a
+ * latency-critical path where an allocation that may synchronise the device is
+ * not acceptable).  Results equal wnnc_eval_at on a tree built with theta = 0
+ * from the same points (same normalisation, cut-off and units).
+ *   pts device, float32 [n][3]; mu device, float32 [n][3]; q device, float32 [m][3]
+ *   out device, float32 [m];  w smoothing width (normalised units), >= 0
+ *   n   at most 32768 points (larger n returns WNNC_EINVAL with a message).
+ * Scratch lives in a fixed array of about 1 MiB inside the library's device
+ * image (held by every GPU that loads the library until the process exits).
+ * The first call on a device looks up that array's device address; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array: calls whose kernels may overlap on the GPU (different streams
+ * without ordering) race, so order them.  Asynchronous on `stream`.
+ */
+wnnc_status wnnc_eval_w_direct_noalloc(const float* pts, int64_t n, const float* mu, const float* q,
+                                       int64_t m, float w, float* out, void* stream);
+
 /* Wait for the stream and return (and clear) any condition latched on the device. */
 wnnc_status wnnc_sync_status(wnnc_tree* tree, void* stream);
 
