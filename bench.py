@@ -52,6 +52,9 @@ WORKLOAD = WORKLOADS[CONFIG_NAME]
 FLOPS_A, FLOPS_AT, FLOPS_G = 18, 18, 31
 FLOPS_ITER = 2 * FLOPS_A + FLOPS_AT + FLOPS_G      # A(mu), A(r), A^T(s), G(mu) per iteration
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
+# DRAM bytes (read + write) of one launch of the G kernel on union500k, from ncu
+# (profiles/union500k_treecode_kernels.md); None once the kernel has changed.
+G_TRAFFIC_BYTES = 81.493504e6 + 4.47744e6
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
@@ -308,7 +311,12 @@ def run_gpu(args):
         "tree": info,
         "roofline": {"kernel": "k_gather<G, rescale> (treecode sum of G + rescale)",
                      "bound": "alu", "achieved": g_achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": g_achieved / peak, "traffic": None,
+                     "frac": g_achieved / peak,
+                     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
+                     # kernel (ncu, profiles/union500k_treecode_kernels.md); only valid for
+                     # the default workload and the kernel version that was profiled
+                     "traffic": G_TRAFFIC_BYTES if CONFIG_NAME == "union500k" else None,
+                     "traffic_unit": "bytes",
                      "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 "
                                     f"x {max_mhz:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
                      "avg_launch_ms": g_avg_ms, "launches": g_launch,
