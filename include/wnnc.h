@@ -6,16 +6,16 @@
  * (Lin, Shi, Liu, "Fast and Globally Consistent Normal Orientation based on
  * the Winding Number Normal Consistency", Sec. 4):
  *
- *   A(mu)_i  = sum_j gradPhi(x_i - x_j) . mu_j         winding number F(x_i; mu)  (Eq. 4, Eq. 7)
+ *   A(mu)_i  = sum_j gradPhi(x_i - x_j) . mu_j         winding number F(x_i; mu)  (Eq. 5, Eq. 6)
  *   G(mu)_i  = -sum_j HPhi(x_i - x_j) mu_j              = -grad F(x_i; mu)          (Eq. 9, Eq. 10)
- *   A^T(s)_j = sum_i s_i gradPhi(x_i - x_j)             adjoint of A (Sec. 4.4)
+ *   A^T(s)_j = sum_i s_i gradPhi(x_i - x_j)             adjoint of A (Sec. 4.5)
  *
  *   gradPhi(y) = -y / (4 pi |y|^3)                        (Thm. 1)
  *   HPhi(y)    = -I/(4 pi |y|^3) + 3 y y^T / (4 pi |y|^5) (Eq. 9)
  *
  * with every pair term set to zero when |x_i - x_j| < w (smoothing width,
- * Sec. 4.3), accelerated by a treecode over an octree of the points
- * (Sec. 4.4, Eq. 11-12, Alg. 4), and the iteration of Alg. 3 (width
+ * Sec. 4.4), accelerated by a treecode over an octree of the points
+ * (Sec. 4.5, Eq. 13-14, Alg. 4), and the iteration of Alg. 3 (width
  * schedule, gradient step of Alg. 2, WNNC update, rescale).
  *
  * Conventions shared by every entry point
@@ -68,7 +68,7 @@ typedef struct {
     int leaf_size;     /* a node is split while it holds more than this many points
                           (the paper splits down to 1 point); 1..1024 (default 32) */
     float theta;       /* opening parameter, 1/c of Alg. 4; 0 = exact direct sums (default 0.5) */
-    int rep_mode;      /* node representative (Eq. 11): 1 = point centroid, which makes the
+    int rep_mode;      /* node representative (Eq. 13): 1 = point centroid, which makes the
                           tree operator linear so that A^T is its exact transpose (default);
                           0 = |nu|-weighted centroid as in the paper (A^T is then the paper's
                           s-representative treecode, not an exact transpose) */
@@ -83,7 +83,7 @@ typedef struct {
     float w1, w2;      /* final and initial smoothing widths, normalised units */
     int init;          /* 0 = start from mu = 0 (the paper); 1 = start from mu_inout */
     int rescale;       /* 0 = |mu_i| kept across the WNNC update (Alg. 3);
-                          1 = |mu_i| set to the given area sigma_i (Eq. 14) */
+                          1 = |mu_i| set to the given area sigma_i (Eq. 19) */
     int use_grad;      /* 1 = gradient step of Alg. 2 (default); 0 = skip it (ablation) */
     int use_wnnc;      /* 1 = WNNC update + rescale (default); 0 = skip it (ablation) */
 } wnnc_iter_params;
@@ -93,7 +93,7 @@ wnnc_status wnnc_tree_params_default(wnnc_tree_params* p);
 wnnc_status wnnc_iter_params_default(wnnc_iter_params* p);
 
 /*
- * Build the octree (Sec. 4.4: split until leaf_size points or depth D),
+ * Build the octree (Sec. 4.5: split until leaf_size points or depth D),
  * node boxes and centroids, and the interaction lists of the points as
  * targets (Alg. 4's far / recurse / leaf-direct decisions, taken once per
  * group of at most 32 Morton-consecutive targets against its bounding box).
@@ -111,7 +111,7 @@ wnnc_status wnnc_build_tree(const float* pts, int64_t n, const wnnc_tree_params*
 wnnc_status wnnc_tree_free(wnnc_tree* tree);
 
 /*
- * F(x_i; mu) = A_w(mu)_i at every input point (Eq. 7 with the cut-off of Sec. 4.3).
+ * F(x_i; mu) = A_w(mu)_i at every input point (Eq. 5 with the cut-off of Sec. 4.4).
  *   mu  device, float32 [n][3], caller units (oriented area elements).
  *   w   smoothing width (normalised units), >= 0; w = 0 only drops coincident pairs.
  *   out device, float32 [n].
@@ -125,7 +125,7 @@ wnnc_status wnnc_eval_w(const wnnc_tree* tree, const float* mu, float w, float* 
 wnnc_status wnnc_eval_grad(const wnnc_tree* tree, const float* mu, float w, float* out, void* stream);
 
 /*
- * A_w^T(s) at every input point (Sec. 4.4; the backward of F with respect to mu).
+ * A_w^T(s) at every input point (Sec. 4.5; the backward of F with respect to mu).
  *   s   device, float32 [n];  out device, float32 [n][3] (caller units).
  * With rep_mode 1 this is the exact transpose of wnnc_eval_w's operator.
  */
@@ -148,7 +148,7 @@ wnnc_status wnnc_eval_at(const wnnc_tree* tree, const float* mu, const float* q,
  *   area     device, float32 [n] (caller units) for rescale = 1, else NULL.
  *   params   host; NULL for the defaults.
  *   stats    device, float32 [last-first+1][4] or NULL: per iteration the width
- *            w_i, the energy E = |A mu - b|^2 before the step (Eq. 6, b = 1/2),
+ *            w_i, the energy E = |A mu - b|^2 before the step (Eq. 12, b = 1/2),
  *            the step length alpha and |r|^2 (Alg. 2), in normalised units.
  * Asynchronous; a non-finite alpha is latched (WNNC_ENONFINITE).
  */
@@ -199,8 +199,8 @@ wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node
  * entries, either may be NULL).  Enabling adds two event records per launch.
  */
 enum {
-    WNNC_PROF_MOMENTS = 0,   /* bottom-up node moments (Eq. 11, Eq. 12) */
-    WNNC_PROF_A = 1,         /* treecode sum of A (Eq. 7, Alg. 4) */
+    WNNC_PROF_MOMENTS = 0,   /* bottom-up node moments (Eq. 13, Eq. 14) */
+    WNNC_PROF_A = 1,         /* treecode sum of A (Eq. 5, Alg. 4) */
     WNNC_PROF_ADJ_FAR = 2,   /* adjoint: far (target group, node) sums */
     WNNC_PROF_ADJ_NODE = 3,  /* adjoint: per-node reduction */
     WNNC_PROF_ADJ_NEAR = 4,  /* adjoint: near sums + push-down of node sums */

@@ -21,7 +21,7 @@ Parity status of each function (pins live in tests/test_oracle_pins.py):
                      per-target criterion holds for every far use)
   iterate            pinned (first-iteration closed form on a sphere, energy
                      decrease of the exact line search, P_co = 100% on a sphere,
-                     the zero-init / no-grad-step behaviour of Sec. 6.1.4)
+                     the zero-init / no-grad-step behaviour of Sec. 6.1.3)
   knn                pinned (against sorting all distances)
   mlp                pinned (finite differences)
 """
@@ -316,7 +316,7 @@ def knn(x, k: int = 16):
 
 
 # ---------------------------------------------------------------------------
-# Metrics (Sec. 5.1.3)
+# Metrics (Sec. 5.1.4)
 # ---------------------------------------------------------------------------
 
 def unit(v):

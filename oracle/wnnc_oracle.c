@@ -10,16 +10,16 @@
  *
  *  - or_normalize: the input normalisation of Sec. 5.1.1 (points scaled into
  *    [-1,1]^3 with a margin of 1/11).
- *  - or_direct: the plain O(N*M) sums of the three operators of Sec. 4.4,
- *      A(mu)_y   = sum_j gradPhi(y - x_j) . mu_j            (Eq. 4, Eq. 7)
+ *  - or_direct: the plain O(N*M) sums of the three operators of Sec. 4.5,
+ *      A(mu)_y   = sum_j gradPhi(y - x_j) . mu_j            (Eq. 5, Eq. 6)
  *      G(mu)_y   = -sum_j HPhi(y - x_j) mu_j               (Eq. 9, Eq. 10)
- *      AT(s)_y   = sum_i s_i gradPhi(x_i - y)              (Sec. 4.4, A^T)
+ *      AT(s)_y   = sum_i s_i gradPhi(x_i - y)              (Sec. 4.5, A^T)
  *    with gradPhi(y) = -y/(4 pi |y|^3) (Thm. 1) and
  *    HPhi(y) = -I/(4 pi |y|^3) + 3 y y^T/(4 pi |y|^5) (Eq. 9), every term set
- *    to zero when |y - x| < w (Sec. 4.3, operators A_w, G_w).
- *  - or_tree_*: the treecode approximation of Sec. 4.4 / Alg. 4: an octree
+ *    to zero when |y - x| < w (Sec. 4.4, operators A_w, G_w).
+ *  - or_tree_*: the treecode approximation of Sec. 4.5 / Alg. 4: an octree
  *    over the sources that stops splitting at leaf_size points or depth D,
- *    node representatives (Eq. 11/12), and far / recurse / leaf-direct
+ *    node representatives (Eq. 13/14), and far / recurse / leaf-direct
  *    decisions.  Targets are evaluated in groups of consecutive Morton-sorted
  *    targets; a node is used as a far source for a whole group when the gap
  *    between the group's bounding box and the node's bounding box exceeds
@@ -103,7 +103,7 @@ static inline void term_AT(const double d[3], double r2, double s, double out[3]
     for (int k = 0; k < 3; ++k) out[k] = s * d[k] / (4.0 * OR_PI * r2 * r);
 }
 
-/* Cut-off of Sec. 4.3: a term counts iff |y - x| >= w.  Pairs closer than
+/* Cut-off of Sec. 4.4: a term counts iff |y - x| >= w.  Pairs closer than
  * MIN_SEP = 2^-20 (normalised units, about 1e-6 of the cloud) count as
  * coincident and never count either: this removes the self term, and it is the
  * only exclusion when w = 0 (Alg. 1), where the kernel is singular. */
@@ -156,7 +156,7 @@ void or_direct(int op, const double* xs, int64_t ns, const double* nu,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Octree (Sec. 4.4): cells are the dyadic cubes of the root cube [-1,1]^3;  */
+/* Octree (Sec. 4.5): cells are the dyadic cubes of the root cube [-1,1]^3;  */
 /* a cell at depth d has width 2/2^d.  A node is split into its non-empty    */
 /* child cells while it holds more than leaf_size points and d < max_depth.  */
 /* Points are ordered by a 45-bit Morton key (15 bits per axis, x the most   */
@@ -485,7 +485,7 @@ void or_tree_lists(const or_tree* T, int64_t* far_off, int64_t* far_id, int64_t*
 }
 
 /* ------------------------------------------------------------------------ */
-/* Node representatives (Eq. 11, Eq. 12).                                    */
+/* Node representatives (Eq. 13, Eq. 14).                                    */
 /*  rep_mode 0 (as in the paper): x_B = sum |nu_i| x_i / sum |nu_j|          */
 /*  rep_mode 1: x_B = plain centroid of the node's points (independent of    */
 /*              nu, which makes the tree operator linear in nu).             */
@@ -513,7 +513,7 @@ static void node_reps(const or_octree* t, const double* nu, int dim, int rep_mod
 /* Gather-form treecode for targets T against the source octree:
  *   op A : out (m)    = sum_far gradPhi(y - x_B) . mu_B + sum_near gradPhi(y - x_j) . mu_j
  *   op G : out (m x 3) = sum_far -HPhi(y - x_B) mu_B  + sum_near -HPhi(y - x_j) mu_j
- *   op AT (rep_mode 0 only, the s-representative treecode of Sec. 4.4):
+ *   op AT (rep_mode 0 only, the s-representative treecode of Sec. 4.5):
  *          out (m x 3) = sum_far s_B gradPhi(x_B - y) + sum_near s_i gradPhi(x_i - y)
  * nu_sorted: source attribute in sorted source order.  out: sorted target order.
  */
@@ -733,9 +733,9 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
 /*   T == NULL: the operators are the direct sums over xn.                   */
 /*   mu (n x 3, input order, normalised units) is updated in place.          */
 /*   rescale 0: mu_i <- muhat_i |mu_i| / |muhat_i|  (Alg. 3)                 */
-/*   rescale 1: mu_i <- muhat_i sigma_i / |muhat_i|  (Eq. 14, needs area)    */
+/*   rescale 1: mu_i <- muhat_i sigma_i / |muhat_i|  (Eq. 19, needs area)    */
 /*   use_grad / use_wnnc switch the two halves off for the ablations of      */
-/*   Sec. 5.5.2 / Sec. 6.1.4.                                                */
+/*   Sec. 5.5.2 / Sec. 6.1.3.                                                */
 /*   stats (optional, per iteration): w, E = |A mu - b|^2 before the step,   */
 /*   alpha, |r|^2.                                                           */
 /* ------------------------------------------------------------------------ */

@@ -9,9 +9,9 @@ raises ``WnncError`` when the library returns a non-OK status.
 Operators (Sec. 4 of the paper; w in normalised units, everything else in the
 caller's units):
 
-* ``Tree.eval_w(mu, w)``        F(x_i; mu) = A_w(mu)_i          (Eq. 7)
+* ``Tree.eval_w(mu, w)``        F(x_i; mu) = A_w(mu)_i          (Eq. 5)
 * ``Tree.eval_grad(mu, w)``     grad F(x_i; mu) = -G_w(mu)_i    (Eq. 8-10)
-* ``Tree.eval_adjoint(s, w)``   A_w^T(s)                         (Sec. 4.4)
+* ``Tree.eval_adjoint(s, w)``   A_w^T(s)                         (Sec. 4.5)
 * ``Tree.eval_at(mu, q, w)``    F (or grad F) at query points
 * ``Tree.iterate(...)``         Alg. 3 with the gradient step of Alg. 2
 * ``winding_number(tree, mu, w)`` differentiable F(mu) whose backward is A^T.
@@ -275,7 +275,7 @@ class Tree:
 
 
 class WindingNumber(torch.autograd.Function):
-    """F(mu) = A_w(mu) at the tree's points; backward = A_w^T (Sec. 4.4).
+    """F(mu) = A_w(mu) at the tree's points; backward = A_w^T (Sec. 4.5).
 
     With rep_mode 1 the backward is the exact transpose of the forward tree
     operator, so gradients agree with finite differences of the forward."""

@@ -1,11 +1,11 @@
 // operators.cu -- node moments and the treecode sums of A, G and A^T.
 //
 // Pair terms (d = x_source - x_target, r = |d|, every term zero when r < w):
-//   A  : gradPhi(x_t - x_s) . mu_s = (d . mu_s) / (4 pi r^3)             (Thm. 1, Eq. 7)
+//   A  : gradPhi(x_t - x_s) . mu_s = (d . mu_s) / (4 pi r^3)             (Thm. 1, Eq. 5)
 //   G  : -HPhi(x_t - x_s) mu_s = mu_s/(4 pi r^3) - 3 d (d.mu_s)/(4 pi r^5) (Eq. 9, Eq. 10)
-//   A^T: s_s gradPhi(x_s - x_t) = -s_s d / (4 pi r^3)                    (Sec. 4.4)
+//   A^T: s_s gradPhi(x_s - x_t) = -s_s d / (4 pi r^3)                    (Sec. 4.5)
 // A far node B acts as one source at its representative x_B carrying
-// nu_B = sum of its points' attributes (Eq. 11, Eq. 12).
+// nu_B = sum of its points' attributes (Eq. 13, Eq. 14).
 //
 // Layout: one warp per work item (a slice of one target group's lists, see
 // WorkList), one target per lane.  Sources (a range of points, or a batch of

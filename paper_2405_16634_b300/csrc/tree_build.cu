@@ -1,7 +1,7 @@
 // tree_build.cu -- normalisation, Morton order, octree, node boxes and
 // centroids, target groups and interaction lists (forward and transposed).
 //
-// Sec. 4.4 builds an octree that stops splitting at one point or at depth D,
+// Sec. 4.5 builds an octree that stops splitting at one point or at depth D,
 // and Alg. 4 decides, per target and node, between a far (representative)
 // interaction, recursion, and a leaf direct sum.  Here the decision is taken
 // once per group of 32 Morton-consecutive targets (one warp), against the

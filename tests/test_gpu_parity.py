@@ -133,7 +133,7 @@ def test_operators_match_oracle(union5k, theta):
 
 
 def test_paper_representatives_match_oracle(union5k):
-    """rep_mode 0: |mu|-weighted node representatives (Eq. 11) and the
+    """rep_mode 0: |mu|-weighted node representatives (Eq. 13) and the
     s-representative A^T treecode, against the oracle's same-rule treecode."""
     W = _wnnc()
     c, mu, s = union5k

@@ -134,7 +134,7 @@ def test_gpu_paper_mode_iteration_matches_oracle():
 
 @pytest.mark.gpu
 def test_gpu_ablations_behave_as_in_the_paper():
-    """Sec. 6.1.4: without the gradient step mu stays 0; the grad step alone
+    """Sec. 6.1.3: without the gradient step mu stays 0; the grad step alone
     (no WNNC update) decreases the energy monotonically at fixed width."""
     W = _gpu()
     c = synth.config_cloud("union50k", n=10000)
@@ -148,7 +148,7 @@ def test_gpu_ablations_behave_as_in_the_paper():
 
 @pytest.mark.gpu
 def test_gpu_fixed_area_rescale():
-    """Eq. 14: with rescale = 1 every |mu_i| equals the given area."""
+    """Eq. 19: with rescale = 1 every |mu_i| equals the given area."""
     W = _gpu()
     c = synth.config_cloud("union50k", n=10000)
     n = len(c.points)

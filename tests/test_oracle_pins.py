@@ -390,7 +390,7 @@ def test_grad_steps_decrease_energy_and_alpha_is_line_minimum():
 
 
 def test_zero_init_without_grad_step_stays_zero():
-    """Sec. 6.1.4: without the gradient step, mu stays at 0."""
+    """Sec. 6.1.3: without the gradient step, mu stays at 0."""
     c = synth.config_cloud("union50k", n=2000)
     mu, _ = oracle.iterate(c.points, n_iter=5, use_grad=False)
     assert np.all(mu == 0.0)
