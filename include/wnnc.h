@@ -212,6 +212,64 @@ wnnc_status wnnc_profile_enable(wnnc_tree* tree, int enable);
 wnnc_status wnnc_profile_read(wnnc_tree* tree, int64_t* launches, double* total_ms);
 wnnc_status wnnc_profile_reset(wnnc_tree* tree);
 
+/* ------------------------------------------------------------------------ */
+/* Learned warm start (not in the paper).  A point-patch MLP maps the 16      */
+/* nearest neighbours of a point (offsets divided by the 16th neighbour's     */
+/* distance, nearest first, 48 values) through 128-128-128 ReLU layers to an  */
+/* oriented normal; it is trained on the method's own converged normals and   */
+/* starts the iteration (init = 1) on the tail of the width schedule.         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * k = 16 nearest neighbours of every tree point (the point itself excluded)
+ * and its patch features.  Exact neighbours (FP32 distances in local frames).
+ *   idx  device, int32 [n][16] (input indices, nearest first) or NULL
+ *   feat device, float32 [n][48]: (x_j - x_i) / |x_j16 - x_i| for the 16
+ *        neighbours j1..j16 in order, or NULL.  Synchronises with `stream`.
+ */
+wnnc_status wnnc_knn16(const wnnc_tree* tree, int32_t* idx, float* feat, void* stream);
+
+typedef struct wnnc_mlp wnnc_mlp;
+enum { WNNC_MLP_PARAMS = 39683 };   /* 48*128+128 + 2*(128*128+128) + 128*3+3 */
+
+/*
+ * Parameter layout (FP32, flat): W1 [128][48], b1 [128], W2 [128][128], b2,
+ * W3 [128][128], b3, W4 [3][128], b4 [3].  Weights are rounded to BF16 when
+ * read; products accumulate in FP32.  max_batch bounds the rows of one
+ * gradient or training call (forward calls of any size are processed in
+ * max_batch chunks).  The MLP owns its work buffers (allocated here).
+ */
+wnnc_status wnnc_mlp_create(int64_t max_batch, wnnc_mlp** out);
+wnnc_status wnnc_mlp_free(wnnc_mlp* mlp);
+/* Copy parameters in (device [WNNC_MLP_PARAMS]); resets the Adam state. */
+wnnc_status wnnc_mlp_set_params(wnnc_mlp* mlp, const float* params, void* stream);
+wnnc_status wnnc_mlp_get_params(const wnnc_mlp* mlp, float* params, void* stream);
+/* y [B][3] = network(x [B][48]) (device pointers). */
+wnnc_status wnnc_mlp_forward(wnnc_mlp* mlp, const float* x, int64_t B, float* y, void* stream);
+/*
+ * Training loss per row, with c = (y/|y|).label: mode 0 (default) 1 - c,
+ * mode 1 1 - c^2 (indifferent to the sign of y).  Other modes: WNNC_EINVAL.
+ */
+wnnc_status wnnc_mlp_set_loss(wnnc_mlp* mlp, int mode);
+/*
+ * Gradient of the mean loss over B <= max_batch rows with
+ * respect to the parameters.  grad device [WNNC_MLP_PARAMS] or NULL (kept
+ * inside for the next train step); loss device [1] or NULL.
+ */
+wnnc_status wnnc_mlp_grad(wnnc_mlp* mlp, const float* x, const float* label, int64_t B, float* grad,
+                          float* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the gradient of (x, label). */
+wnnc_status wnnc_mlp_train_step(wnnc_mlp* mlp, const float* x, const float* label, int64_t B, float lr,
+                                float* loss, void* stream);
+/*
+ * Warm-start field: mu_i = L_i * dir_i / |dir_i|, negated where
+ * dir_i . ref_i < 0 (ref: the field after one iteration of the method, or
+ * NULL for no sign correction), with L_i = area if area > 0, else |ref_i|.
+ * dir, ref, mu device float32 [n][3].
+ */
+wnnc_status wnnc_warm_init(const float* dir, const float* ref, int64_t n, float area, float* mu,
+                           void* stream);
+
 /* Number of kernels this library has launched in this process so far (all
  * threads, all trees); for counting the launches inside a timed region. */
 int64_t wnnc_kernel_launches(void);

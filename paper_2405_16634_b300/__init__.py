@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libwnnc.so")
 
 __all__ = ["Tree", "TreeParams", "IterParams", "WnncError", "winding_number", "WindingNumber",
-           "lib", "LIB_PATH", "PROF_CLASSES"]
+           "lib", "LIB_PATH", "PROF_CLASSES", "knn16", "Mlp", "MLP_PARAMS", "warm_init"]
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ECAPACITY",
           6: "ETIMEOUT"}
@@ -87,13 +87,25 @@ def lib():
     L.wnnc_profile_read.argtypes = [P, P, P]
     L.wnnc_profile_reset.argtypes = [P]
     L.wnnc_sync_status.argtypes = [P, P]
+    L.wnnc_knn16.argtypes = [P, P, P, P]
+    L.wnnc_mlp_create.argtypes = [c_int64, POINTER(c_void_p)]
+    L.wnnc_mlp_free.argtypes = [P]
+    L.wnnc_mlp_set_params.argtypes = [P, P, P]
+    L.wnnc_mlp_get_params.argtypes = [P, P, P]
+    L.wnnc_mlp_forward.argtypes = [P, P, c_int64, P, P]
+    L.wnnc_mlp_set_loss.argtypes = [P, c_int]
+    L.wnnc_mlp_grad.argtypes = [P, P, P, c_int64, P, P, P]
+    L.wnnc_mlp_train_step.argtypes = [P, P, P, c_int64, c_float, P, P]
+    L.wnnc_warm_init.argtypes = [P, P, c_int64, c_float, P, P]
     L.wnnc_last_error.restype = ctypes.c_char_p
     L.wnnc_kernel_launches.restype = c_int64
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
                  "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
                  "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_tree_info",
                  "wnnc_tree_export", "wnnc_profile_enable", "wnnc_profile_read",
-                 "wnnc_profile_reset", "wnnc_sync_status"):
+                 "wnnc_profile_reset", "wnnc_sync_status", "wnnc_knn16", "wnnc_mlp_create",
+                 "wnnc_mlp_free", "wnnc_mlp_set_params", "wnnc_mlp_get_params", "wnnc_mlp_forward",
+                 "wnnc_mlp_set_loss", "wnnc_mlp_grad", "wnnc_mlp_train_step", "wnnc_warm_init"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -272,6 +284,88 @@ class Tree:
 
     def sync_status(self) -> None:
         _check(lib().wnnc_sync_status(self._h, _stream_ptr(self.device)))
+
+
+def knn16(tree: Tree):
+    """(idx [n][16] int32 input indices, feat [n][48] float32) of the tree's points."""
+    idx = torch.empty(tree.n, 16, device=tree.device, dtype=torch.int32)
+    feat = torch.empty(tree.n, 48, device=tree.device, dtype=torch.float32)
+    _check(lib().wnnc_knn16(tree._h, idx.data_ptr(), feat.data_ptr(), _stream_ptr(tree.device)))
+    return idx, feat
+
+
+MLP_PARAMS = 39683
+
+
+class Mlp:
+    """The warm-start point-patch MLP (48 -> 128 -> 128 -> 128 -> 3, BF16 weights)."""
+
+    def __init__(self, max_batch: int = 65536, params=None, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.max_batch = int(max_batch)
+        h = c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().wnnc_mlp_create(self.max_batch, ctypes.byref(h)))
+        self._h = h
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().wnnc_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = _dev_f32(params, (MLP_PARAMS,), self.device)
+        _check(lib().wnnc_mlp_set_params(self._h, p.data_ptr(), _stream_ptr(self.device)))
+        torch.cuda.current_stream(self.device).synchronize()
+
+    def get_params(self) -> torch.Tensor:
+        p = torch.empty(MLP_PARAMS, device=self.device, dtype=torch.float32)
+        _check(lib().wnnc_mlp_get_params(self._h, p.data_ptr(), _stream_ptr(self.device)))
+        return p
+
+    def forward(self, x) -> torch.Tensor:
+        x = _dev_f32(x, (-1, 48), self.device)
+        y = torch.empty(x.shape[0], 3, device=self.device, dtype=torch.float32)
+        _check(lib().wnnc_mlp_forward(self._h, x.data_ptr(), x.shape[0], y.data_ptr(), _stream_ptr(self.device)))
+        return y
+
+    def set_loss(self, mode: int):
+        """0: 1 - c (signed, default); 1: 1 - c^2 (sign-free); c = (y/|y|).label."""
+        _check(lib().wnnc_mlp_set_loss(self._h, int(mode)))
+
+    def grad(self, x, label):
+        x = _dev_f32(x, (-1, 48), self.device)
+        label = _dev_f32(label, (x.shape[0], 3), self.device)
+        g = torch.empty(MLP_PARAMS, device=self.device, dtype=torch.float32)
+        loss = torch.empty(1, device=self.device, dtype=torch.float32)
+        _check(lib().wnnc_mlp_grad(self._h, x.data_ptr(), label.data_ptr(), x.shape[0], g.data_ptr(),
+                                   loss.data_ptr(), _stream_ptr(self.device)))
+        return g, loss
+
+    def train_step(self, x, label, lr: float) -> torch.Tensor:
+        loss = torch.empty(1, device=self.device, dtype=torch.float32)
+        _check(lib().wnnc_mlp_train_step(self._h, x.data_ptr(), label.data_ptr(), x.shape[0], float(lr),
+                                         loss.data_ptr(), _stream_ptr(self.device)))
+        return loss
+
+
+def warm_init(direction, reference, area: float) -> torch.Tensor:
+    """mu = area * dir/|dir|, flipped where dir . reference < 0 (reference may be None)."""
+    d = direction.contiguous()
+    n = d.shape[0]
+    mu = torch.empty_like(d)
+    ref = None if reference is None else reference.contiguous()
+    _check(lib().wnnc_warm_init(d.data_ptr(), None if ref is None else ref.data_ptr(), n, float(area),
+                                mu.data_ptr(), _stream_ptr(d.device)))
+    return mu
 
 
 class WindingNumber(torch.autograd.Function):

@@ -321,6 +321,122 @@ wnnc_status wnnc_sync_status(wnnc_tree* tree, void* stream) {
     return st != WNNC_OK ? st : dev;
 }
 
+wnnc_status wnnc_knn16(const wnnc_tree* tree, int32_t* idx, float* feat, void* stream) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        knn16(t, idx, feat, static_cast<cudaStream_t>(stream));
+    });
+}
+
+static Mlp& unwrap_mlp(const wnnc_mlp* h) {
+    if (!h) fail(WNNC_EINVAL, "mlp is NULL");
+    return *reinterpret_cast<Mlp*>(const_cast<wnnc_mlp*>(h));
+}
+
+wnnc_status wnnc_mlp_create(int64_t max_batch, wnnc_mlp** out) {
+    if (out) *out = nullptr;
+    Mlp* m = nullptr;
+    wnnc_status st = guarded([&] {
+        if (!out) fail(WNNC_EINVAL, "out is NULL");
+        if (max_batch < 1 || max_batch > (int64_t)1 << 26) fail(WNNC_EINVAL, "max_batch must be in [1, 2^26]");
+        m = new Mlp();
+        mlp_alloc(*m, max_batch);
+    });
+    if (st != WNNC_OK) {
+        if (m) {
+            mlp_free(*m);
+            delete m;
+        }
+        return st;
+    }
+    *out = reinterpret_cast<wnnc_mlp*>(m);
+    return WNNC_OK;
+}
+
+wnnc_status wnnc_mlp_free(wnnc_mlp* mlp) {
+    if (!mlp) return WNNC_OK;
+    return guarded([&] {
+        Mlp* m = reinterpret_cast<Mlp*>(mlp);
+        WNNC_CUDA(cudaDeviceSynchronize());
+        mlp_free(*m);
+        delete m;
+    });
+}
+
+wnnc_status wnnc_mlp_set_params(wnnc_mlp* mlp, const float* params, void* stream) {
+    return guarded([&] {
+        Mlp& m = unwrap_mlp(mlp);
+        if (!params) fail(WNNC_EINVAL, "params is NULL");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t bytes = sizeof(float) * mlp_param_count();
+        WNNC_CUDA(cudaMemcpyAsync(m.params, params, bytes, cudaMemcpyDeviceToDevice, s));
+        WNNC_CUDA(cudaMemsetAsync(m.m, 0, bytes, s));
+        WNNC_CUDA(cudaMemsetAsync(m.v, 0, bytes, s));
+        m.step = 0;
+    });
+}
+
+wnnc_status wnnc_mlp_get_params(const wnnc_mlp* mlp, float* params, void* stream) {
+    return guarded([&] {
+        Mlp& m = unwrap_mlp(mlp);
+        if (!params) fail(WNNC_EINVAL, "params is NULL");
+        WNNC_CUDA(cudaMemcpyAsync(params, m.params, sizeof(float) * mlp_param_count(), cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream)));
+    });
+}
+
+wnnc_status wnnc_mlp_forward(wnnc_mlp* mlp, const float* x, int64_t B, float* y, void* stream) {
+    return guarded([&] {
+        Mlp& m = unwrap_mlp(mlp);
+        if (!x || !y) fail(WNNC_EINVAL, "x/y is NULL");
+        if (B < 1) fail(WNNC_EINVAL, "B must be >= 1");
+        mlp_forward(m, x, B, y, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wnnc_status wnnc_mlp_set_loss(wnnc_mlp* mlp, int mode) {
+    return guarded([&] {
+        Mlp& m = unwrap_mlp(mlp);
+        if (mode != 0 && mode != 1) fail(WNNC_EINVAL, "loss mode must be 0 or 1");
+        m.loss_mode = mode;
+    });
+}
+
+wnnc_status wnnc_mlp_grad(wnnc_mlp* mlp, const float* x, const float* label, int64_t B, float* grad, float* loss,
+                          void* stream) {
+    return guarded([&] {
+        Mlp& m = unwrap_mlp(mlp);
+        if (!x || !label) fail(WNNC_EINVAL, "x/label is NULL");
+        if (B < 1 || B > m.max_batch) fail(WNNC_EINVAL, "B must be in [1, max_batch]");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        mlp_grad(m, x, label, B, loss, s);
+        if (grad)
+            WNNC_CUDA(cudaMemcpyAsync(grad, m.grad, sizeof(float) * mlp_param_count(), cudaMemcpyDeviceToDevice, s));
+    });
+}
+
+wnnc_status wnnc_mlp_train_step(wnnc_mlp* mlp, const float* x, const float* label, int64_t B, float lr, float* loss,
+                                void* stream) {
+    return guarded([&] {
+        Mlp& m = unwrap_mlp(mlp);
+        if (!x || !label) fail(WNNC_EINVAL, "x/label is NULL");
+        if (B < 1 || B > m.max_batch) fail(WNNC_EINVAL, "B must be in [1, max_batch]");
+        if (!(lr > 0.f) || !std::isfinite(lr)) fail(WNNC_EINVAL, "lr must be finite and > 0");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        mlp_grad(m, x, label, B, loss, s);
+        mlp_adam(m, lr, s);
+    });
+}
+
+wnnc_status wnnc_warm_init(const float* dir, const float* ref, int64_t n, float area, float* mu, void* stream) {
+    return guarded([&] {
+        if (!dir || !mu) fail(WNNC_EINVAL, "dir/mu is NULL");
+        if (n < 1) fail(WNNC_EINVAL, "n must be >= 1");
+        if (!(area >= 0.f) || !std::isfinite(area)) fail(WNNC_EINVAL, "area must be finite and >= 0");
+        warm_init(dir, ref, n, area, mu, static_cast<cudaStream_t>(stream));
+    });
+}
+
 int64_t wnnc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* wnnc_last_error(void) { return g_last_error.c_str(); }

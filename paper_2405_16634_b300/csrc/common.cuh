@@ -238,4 +238,35 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
 void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params& p,
              cudaStream_t s, float* stats);
 
+// k nearest neighbours and patch features (knn.cu)
+void knn16(Tree& t, int* idx_out, float* feat_out, cudaStream_t s);
+
+// point-patch MLP of the warm start (mlp.cu)
+struct Mlp {
+    int64_t max_batch = 0;
+    float* params = nullptr;   // FP32 master parameters (BF16-rounded when read)
+    float* m = nullptr;        // Adam moments
+    float* v = nullptr;
+    float* grad = nullptr;
+    float* h1 = nullptr;       // [B][128] activations (after ReLU)
+    float* h2 = nullptr;
+    float* h3 = nullptr;
+    float* out = nullptr;      // [B][3]
+    float* d3 = nullptr;       // [B][128] gradients w.r.t. pre-activations
+    float* d2 = nullptr;
+    float* d1 = nullptr;
+    float* dout = nullptr;     // [B][3]
+    float* part = nullptr;     // weight-gradient partials [nchunk][params]
+    double* lpart = nullptr;   // loss partials
+    int64_t step = 0;
+    int loss_mode = 0;         // 0: 1 - c (signed), 1: 1 - c^2 (sign-free); c = (v/|v|).label
+};
+int mlp_param_count();
+void mlp_alloc(Mlp& m, int64_t max_batch);
+void mlp_free(Mlp& m);
+void mlp_forward(Mlp& m, const float* x, int64_t B, float* y, cudaStream_t s);
+void mlp_grad(Mlp& m, const float* x, const float* label, int64_t B, float* loss_dev, cudaStream_t s);
+void mlp_adam(Mlp& m, float lr, cudaStream_t s);
+void warm_init(const float* dir, const float* ref, int64_t n, float area, float* mu, cudaStream_t s);
+
 }  // namespace wnnc

@@ -362,3 +362,16 @@ def random_cloud_spec(seed: int) -> dict:
 def init_normals(n: int, seed: int, area_per_point: float) -> np.ndarray:
     """Random unit normals (unoriented) times an equal area weight, float32 (N,3)."""
     return (random_unit_vectors(n, seed) * area_per_point).astype(np.float32)
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Initial parameters of the 48-128-128-128-3 warm-start MLP (He-uniform
+    weights, zero biases), flat float32 in the layout W1, b1, W2, b2, W3, b3,
+    W4, b4."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((128, 48), (128, 128), (128, 128), (3, 128)):
+        lim = math.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
