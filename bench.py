@@ -54,7 +54,7 @@ FLOPS_ITER = 2 * FLOPS_A + FLOPS_AT + FLOPS_G      # A(mu), A(r), A^T(s), G(mu) 
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
 # DRAM bytes (read + write) of one launch of the G kernel on union500k, from ncu
 # (profiles/union500k_treecode_kernels.md); None once the kernel has changed.
-G_TRAFFIC_BYTES = 81.493504e6 + 4.47744e6
+G_TRAFFIC_BYTES = 82.08768e6 + 4.223744e6
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:

@@ -106,8 +106,10 @@ struct TargetSet {
     float4* corig = nullptr;      // chunk origins (chunk = 32 consecutive sorted targets)
     float4* gorig = nullptr;      // group origins
     int* goff = nullptr;          // [ngroups+1] group g = sorted targets goff[g]..goff[g+1]-1
-    double* glo = nullptr;        // group bounding boxes (3 per group), build only
+    double* glo = nullptr;        // group bounding boxes (3 per group)
     double* ghi = nullptr;
+    float4* gbl = nullptr;        // the same boxes in the group's frame, rounded outward
+    float4* gbh = nullptr;
     int* far_off = nullptr;       // [ngroups+1]
     int* far_id = nullptr;        // node ids, ascending per group
     int* near_off = nullptr;      // [ngroups+1]

@@ -14,7 +14,14 @@
 // with rsqrt and FMA chains.  The 1/(4 pi) factor is applied once.  Groups cut
 // into several items write partial sums to scratch slots; a finalize pass adds
 // them in a fixed order (results do not depend on scheduling).
+//
+// Cut-off test per batch: when every staged source of a batch lies farther
+// from the group's box than the cut-off radius (with a margin far above the
+// rounding of the test), no pair of the batch can be cut, and the batch runs
+// an inner loop without the compare/select; its terms are bit-identical to
+// those of the general loop.
 #include <algorithm>
+#include <cmath>
 #include <cfloat>
 #include <utility>
 
@@ -26,6 +33,15 @@ namespace {
 
 constexpr int kTB = 256;
 constexpr int kGatherWarps = 4;
+// Inner-loop unroll depth and minimum resident blocks per SM of the pair
+// kernels (tuning knobs; the defaults are the measured best on B300).
+#ifndef WNNC_UNROLL
+#define WNNC_UNROLL 4
+#endif
+#ifndef WNNC_GATHER_MINB
+#define WNNC_GATHER_MINB 1
+#endif
+constexpr int kUnroll = WNNC_UNROLL;
 
 // ---------------------------------------------------------------------------
 // Node moments, bottom-up in one launch: each leaf sums its points, then the
@@ -160,6 +176,9 @@ struct GatherArgs {
     const float4* nrep;
     const float4* nmom;
     float w2;
+    float fast2;              // squared batch-test radius (cut-off radius plus margin)
+    const float4* tgbl;       // target group boxes in their own frames
+    const float4* tgbh;
     float scale;              // output unit conversion factor
     // epilogue buffers
     float* out;
@@ -171,16 +190,23 @@ struct GatherArgs {
     int rescale_mode;
 };
 
+// Accumulators: (x, y, z) holds the A / A^T sum, or for G the sum of
+// mu / r^3; (u, v, q) holds, for G only, the sum of (d.mu) d / r^5, so that
+// G = (x, y, z) - 3 (u, v, q).
 struct Acc3 {
     float x = 0.f, y = 0.f, z = 0.f;
+    float u = 0.f, v = 0.f, q = 0.f;
 };
 
-template <int OP>
+// One pair term.  CUT: apply the cut-off r^2 >= w2 (otherwise the caller has
+// shown that every pair of the batch passes it).
+template <int OP, bool CUT>
 __device__ __forceinline__ void interact(const float4& t, const float4& sp, const float4& sv, float w2,
                                          Acc3& a) {
     float dx = sp.x - t.x, dy = sp.y - t.y, dz = sp.z - t.z;
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float ir = (r2 >= w2) ? rsqrtf(r2) : 0.f;
+    float ir = rsqrtf(r2);
+    if (CUT) ir = (r2 >= w2) ? ir : 0.f;
     if (OP == kOpA) {
         float ir3 = ir * ir * ir;
         float dm = fmaf(dx, sv.x, fmaf(dy, sv.y, dz * sv.z));
@@ -189,10 +215,13 @@ __device__ __forceinline__ void interact(const float4& t, const float4& sp, cons
         float ir2 = ir * ir;
         float ir3 = ir2 * ir;
         float dm = fmaf(dx, sv.x, fmaf(dy, sv.y, dz * sv.z));
-        float t3 = (3.f * dm) * (ir3 * ir2);
-        a.x = fmaf(sv.x, ir3, fmaf(-dx, t3, a.x));
-        a.y = fmaf(sv.y, ir3, fmaf(-dy, t3, a.y));
-        a.z = fmaf(sv.z, ir3, fmaf(-dz, t3, a.z));
+        float k5 = (dm * ir2) * ir3;
+        a.x = fmaf(sv.x, ir3, a.x);
+        a.y = fmaf(sv.y, ir3, a.y);
+        a.z = fmaf(sv.z, ir3, a.z);
+        a.u = fmaf(dx, k5, a.u);
+        a.v = fmaf(dy, k5, a.v);
+        a.q = fmaf(dz, k5, a.q);
     } else {   // paper-mode A^T: -s d / r^3
         float q = -sv.x * (ir * ir * ir);
         a.x = fmaf(q, dx, a.x);
@@ -205,6 +234,25 @@ __device__ __forceinline__ void interact(const float4& t, const float4& sp, cons
 // (both origins are multiples of 2^-12, so the shift is exact).
 __device__ __forceinline__ float4 shift(const float4& c, const float4& o, const float4& p) {
     return make_float4((c.x - o.x) + p.x, (c.y - o.y) + p.y, (c.z - o.z) + p.z, 0.f);
+}
+
+// Squared distance from p to the box [lo, hi] (zero inside).
+__device__ __forceinline__ float box_gap2(const float4& lo, const float4& hi, const float4& p) {
+    const float ex = fmaxf(fmaxf(lo.x - p.x, p.x - hi.x), 0.f);
+    const float ey = fmaxf(fmaxf(lo.y - p.y, p.y - hi.y), 0.f);
+    const float ez = fmaxf(fmaxf(lo.z - p.z, p.z - hi.z), 0.f);
+    return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+}
+
+// G's two partial sums combined: (x, y, z) - 3 (u, v, q).
+template <int OP>
+__device__ __forceinline__ Acc3 combine(Acc3 a) {
+    if (OP == kOpG) {
+        a.x = fmaf(-3.f, a.u, a.x);
+        a.y = fmaf(-3.f, a.v, a.y);
+        a.z = fmaf(-3.f, a.q, a.z);
+    }
+    return a;
 }
 
 // Epilogue of one group (all 32 lanes call it; lane < size holds target i).
@@ -261,7 +309,7 @@ __device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int6
 }
 
 template <int OP, int EPI>
-__global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs A) {
+__global__ void __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB) k_gather(GatherArgs A) {
     __shared__ float4 sp_all[kGatherWarps][32];
     __shared__ float4 sv_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -276,6 +324,7 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs A) {
     const bool valid = lane < A.goff[g + 1] - i0;
     const float4 o = A.tgorig[g];
     const float4 t = valid ? shift(A.tcorig[i >> 5], o, A.tpos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 blo = A.tgbl[g], bhi = A.tgbh[g];
     Acc3 acc;
 
     // near field: ranges of source points
@@ -283,32 +332,51 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs A) {
         const int2 r = A.near_rng[q];
         for (int base = r.x; base < r.y; base += 32) {
             const int cnt = min(32, r.y - base);
+            bool clear = true;
             if (lane < cnt) {
                 const int j = base + lane;
-                sp[lane] = shift(A.scorig[j >> 5], o, A.spos[j]);
+                const float4 p = shift(A.scorig[j >> 5], o, A.spos[j]);
+                clear = box_gap2(blo, bhi, p) >= A.fast2;
+                sp[lane] = p;
                 if (OP == kOpATpaper) sv[lane] = make_float4(A.sval_s[j], 0.f, 0.f, 0.f);
                 else sv[lane] = A.sval[j];
             }
+            clear = __all_sync(0xffffffffu, clear);
             __syncwarp();
-#pragma unroll 4
-            for (int k = 0; k < cnt; ++k) interact<OP>(t, sp[k], sv[k], A.w2, acc);
+            if (clear) {
+#pragma unroll kUnroll
+                for (int k = 0; k < cnt; ++k) interact<OP, false>(t, sp[k], sv[k], A.w2, acc);
+            } else {
+#pragma unroll kUnroll
+                for (int k = 0; k < cnt; ++k) interact<OP, true>(t, sp[k], sv[k], A.w2, acc);
+            }
             __syncwarp();
         }
     }
     // far field: node representatives
     for (int base = item.f0; base < item.f1; base += 32) {
         const int cnt = min(32, item.f1 - base);
+        bool clear = true;
         if (lane < cnt) {
             const int b = A.far_id[base + lane];
-            sp[lane] = shift(A.ncell[b], o, A.nrep[b]);
+            const float4 p = shift(A.ncell[b], o, A.nrep[b]);
+            clear = box_gap2(blo, bhi, p) >= A.fast2;
+            sp[lane] = p;
             sv[lane] = A.nmom[b];
         }
+        clear = __all_sync(0xffffffffu, clear);
         __syncwarp();
-#pragma unroll 4
-        for (int k = 0; k < cnt; ++k) interact<OP>(t, sp[k], sv[k], A.w2, acc);
+        if (clear) {
+#pragma unroll kUnroll
+            for (int k = 0; k < cnt; ++k) interact<OP, false>(t, sp[k], sv[k], A.w2, acc);
+        } else {
+#pragma unroll kUnroll
+            for (int k = 0; k < cnt; ++k) interact<OP, true>(t, sp[k], sv[k], A.w2, acc);
+        }
         __syncwarp();
     }
 
+    acc = combine<OP>(acc);
     if (item.pslot < 0) {
         gather_epilogue<EPI>(A, g, i, valid, acc, lane);
     } else {
@@ -363,6 +431,9 @@ struct AdjArgs {
     const int* nparent;
     const float4* vnode;
     float w2;
+    float fast2;              // squared batch-test radius (cut-off radius plus margin)
+    const float4* gbl;        // group boxes in their own frames
+    const float4* gbh;
     float scale;
     const int64_t* perm;
     float* out;
@@ -370,7 +441,22 @@ struct AdjArgs {
     double* partial;
 };
 
-__global__ void __launch_bounds__(32 * kGatherWarps) k_adj_far(AdjArgs A) {
+// One adjoint term s_i gradPhi(x_i - x) = s_i (x - x_i) / r^3 at x = p from
+// the target ti = (x_i, s_i).  CUT as in interact().
+template <bool CUT>
+__device__ __forceinline__ void adj_term(const float4& p, const float4& ti, float w2, float& ax, float& ay,
+                                         float& az) {
+    const float dx = p.x - ti.x, dy = p.y - ti.y, dz = p.z - ti.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float ir = rsqrtf(r2);
+    if (CUT) ir = (r2 >= w2) ? ir : 0.f;
+    const float q = ti.w * (ir * ir * ir);
+    ax = fmaf(q, dx, ax);
+    ay = fmaf(q, dy, ay);
+    az = fmaf(q, dz, az);
+}
+
+__global__ void __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB) k_adj_far(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
@@ -384,23 +470,26 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_adj_far(AdjArgs A) {
     float4 p = lane < cnt_t ? shift(A.corig[i >> 5], o, A.pos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
     p.w = lane < cnt_t ? A.sv[i] : 0.f;
     tp[lane] = p;
+    const float4 blo = A.gbl[g], bhi = A.gbh[g];
     __syncwarp();
     for (int base = item.f0; base < item.f1; base += 32) {
         const int e = base + lane;
+        float4 bp = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool clear = true;
         if (e < item.f1) {
             const int b = A.far_id[e];
-            const float4 bp = shift(A.ncell[b], o, A.ncent[b]);
+            bp = shift(A.ncell[b], o, A.ncent[b]);
+            clear = box_gap2(blo, bhi, bp) >= A.fast2;
+        }
+        clear = __all_sync(0xffffffffu, clear);
+        if (e < item.f1) {
             float ax = 0.f, ay = 0.f, az = 0.f;
-#pragma unroll 4
-            for (int k = 0; k < cnt_t; ++k) {
-                const float4 ti = tp[k];
-                const float dx = bp.x - ti.x, dy = bp.y - ti.y, dz = bp.z - ti.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ir = (r2 >= A.w2) ? rsqrtf(r2) : 0.f;
-                const float q = ti.w * (ir * ir * ir);
-                ax = fmaf(q, dx, ax);
-                ay = fmaf(q, dy, ay);
-                az = fmaf(q, dz, az);
+            if (clear) {
+#pragma unroll kUnroll
+                for (int k = 0; k < cnt_t; ++k) adj_term<false>(bp, tp[k], A.w2, ax, ay, az);
+            } else {
+#pragma unroll kUnroll
+                for (int k = 0; k < cnt_t; ++k) adj_term<true>(bp, tp[k], A.w2, ax, ay, az);
             }
             A.contrib[e] = make_float4(ax, ay, az, 0.f);
         }
@@ -455,7 +544,7 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
 }
 
 template <int EPI>
-__global__ void __launch_bounds__(32 * kGatherWarps) k_adj_near(AdjArgs A) {
+__global__ void __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB) k_adj_near(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
@@ -479,19 +568,24 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_adj_near(AdjArgs A) {
             p.w = A.sv[i];
             tp[lane] = p;
         }
+        const bool mine = (mask >> lane) & 1u;
+        bool clear = true;
+        if (mine) {   // the group's box in this chunk's frame
+            const float4 go = A.gorig[g];
+            const float4 sh = make_float4(go.x - o.x, go.y - o.y, go.z - o.z, 0.f);
+            const float4 lo = A.gbl[g], hi = A.gbh[g];
+            clear = box_gap2(make_float4(lo.x + sh.x, lo.y + sh.y, lo.z + sh.z, 0.f),
+                             make_float4(hi.x + sh.x, hi.y + sh.y, hi.z + sh.z, 0.f), xj) >= A.fast2;
+        }
+        clear = __all_sync(0xffffffffu, clear);
         __syncwarp();
-        if ((mask >> lane) & 1u) {
-#pragma unroll 4
-            for (int k = 0; k < cnt_t; ++k) {
-                const float4 ti = tp[k];
-                // s_i gradPhi(x_i - x_j) = s_i (x_j - x_i) / r^3
-                const float dx = xj.x - ti.x, dy = xj.y - ti.y, dz = xj.z - ti.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ir = (r2 >= A.w2) ? rsqrtf(r2) : 0.f;
-                const float qq = ti.w * (ir * ir * ir);
-                ax = fmaf(qq, dx, ax);
-                ay = fmaf(qq, dy, ay);
-                az = fmaf(qq, dz, az);
+        if (mine) {
+            if (clear) {
+#pragma unroll kUnroll
+                for (int k = 0; k < cnt_t; ++k) adj_term<false>(xj, tp[k], A.w2, ax, ay, az);
+            } else {
+#pragma unroll kUnroll
+                for (int k = 0; k < cnt_t; ++k) adj_term<true>(xj, tp[k], A.w2, ax, ay, az);
             }
         }
         __syncwarp();
@@ -609,6 +703,15 @@ __global__ void k_stats_nograd(float* stats, float w) {
 // self term, repeated samples) never count, also when w = 0 (Alg. 1).
 inline float cutoff2(float w) { return fmaxf(w * w, 0x1p-40f); }
 
+// Squared radius of the per-batch cut-off test: a source farther than
+// sqrt(cutoff2) * 1.001 + 4e-6 from a group's box is farther than the cut-off
+// from every target of the group, also after the FP32 rounding of the box, of
+// the frame shifts and of r^2 (all below 1e-6 in normalised units).
+inline float fast_radius2(float w) {
+    const double r = std::sqrt((double)cutoff2(w)) * 1.001 + 4e-6;
+    return (float)(r * r * (1.0 + 1e-6));
+}
+
 GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_acc) {
     GatherArgs a{};
     a.items = ts.work.items;
@@ -630,6 +733,9 @@ GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_a
     a.nrep = t.params.rep_mode == 0 ? t.node_rep : t.node_cent;
     a.nmom = t.mom;
     a.w2 = cutoff2(w);
+    a.fast2 = fast_radius2(w);
+    a.tgbl = ts.gbl;
+    a.tgbh = ts.gbh;
     return a;
 }
 
@@ -663,6 +769,9 @@ AdjArgs adj_args(const Tree& t, float w) {
     a.nparent = t.node_parent;
     a.vnode = t.vnode;
     a.w2 = cutoff2(w);
+    a.fast2 = fast_radius2(w);
+    a.gbl = S.gbl;
+    a.gbh = S.gbh;
     return a;
 }
 

@@ -333,15 +333,16 @@ __global__ void k_chunk_frames(const double* ys, int64_t m, int nchunks, float4*
                              (float)(ys[3 * i + 2] - o[2]), 0.f);
 }
 
-// Warp per group: bounding box and dyadic origin.
+// Warp per group: bounding box and dyadic origin, and the box in the group's
+// frame rounded outward to float (it contains every target of the group).
 __global__ void k_group_boxes(const double* ys, const int* goff, int ng, double* glo, double* ghi,
-                              float4* gorig) {
+                              float4* gorig, float4* gbl, float4* gbh) {
     int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (g >= ng) return;
     int64_t i = (int64_t)goff[g] + lane;
     bool valid = i < goff[g + 1];
-    double o[3];
+    double o[3], bl[3], bh[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         double v = valid ? ys[3 * i + k] : 0.0;
@@ -352,8 +353,14 @@ __global__ void k_group_boxes(const double* ys, const int* goff, int ng, double*
         }
         if (lane == 0) { glo[3 * g + k] = l; ghi[3 * g + k] = h; }
         o[k] = dyadic12(0.5 * (l + h));
+        bl[k] = l - o[k];
+        bh[k] = h - o[k];
     }
-    if (lane == 0) gorig[g] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
+    if (lane == 0) {
+        gorig[g] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
+        gbl[g] = make_float4(__double2float_rd(bl[0]), __double2float_rd(bl[1]), __double2float_rd(bl[2]), 0.f);
+        gbh[g] = make_float4(__double2float_ru(bh[0]), __double2float_ru(bh[1]), __double2float_ru(bh[2]), 0.f);
+    }
 }
 
 // Far test of a group box against node b (see the file comment).
@@ -765,7 +772,10 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     ts.glo = dalloc<double>(3 * (size_t)ng);
     ts.ghi = dalloc<double>(3 * (size_t)ng);
     ts.gorig = dalloc<float4>(ng);
-    k_group_boxes<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(ys, ts.goff, ng, ts.glo, ts.ghi, ts.gorig);
+    ts.gbl = dalloc<float4>(ng);
+    ts.gbh = dalloc<float4>(ng);
+    k_group_boxes<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(ys, ts.goff, ng, ts.glo, ts.ghi, ts.gorig,
+                                                                   ts.gbl, ts.gbh);
     WNNC_LAUNCH_CHECK();
     WNNC_CUDA(cudaStreamSynchronize(s));
     cudaFree(ys);
@@ -886,7 +896,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
 
 void free_target_set(TargetSet& ts) {
     dfree(ts.perm); dfree(ts.pos); dfree(ts.corig); dfree(ts.gorig); dfree(ts.goff); dfree(ts.glo);
-    dfree(ts.ghi); dfree(ts.far_off); dfree(ts.far_id); dfree(ts.near_off); dfree(ts.near_rng);
+    dfree(ts.ghi); dfree(ts.gbl); dfree(ts.gbh); dfree(ts.far_off); dfree(ts.far_id); dfree(ts.near_off); dfree(ts.near_rng);
     free_work(ts.work);
 }
 

@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import sys
 import time
@@ -76,16 +77,18 @@ def make_dataset(seeds, keep: int = 20000, device="cuda"):
 
 def train(mlp: Mlp, X: torch.Tensor, Y: torch.Tensor, epochs: int = 4, batch: int = 32768,
           lr: float = 1e-3, seed: int = 0):
-    """Adam on shuffled mini-batches; returns the mean loss per epoch."""
+    """Adam on shuffled mini-batches, learning rate on a per-epoch cosine
+    decay from lr to lr/20; returns the mean loss per epoch."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     hist = []
     n = X.shape[0]
     for ep in range(epochs):
         perm = torch.randperm(n, generator=g).to(X.device)
+        lr_e = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * ep / max(epochs, 1))))
         losses = []
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
-            losses.append(mlp.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr))
+            losses.append(mlp.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr_e))
         hist.append(float(torch.stack(losses).mean().item()))
     return hist
 
@@ -147,14 +150,22 @@ def evaluate(mlp: Mlp, heldout_seeds, plain_iters=(2, 3, 5, 10, 20, 40),
         for s_, k in warm:
             mu, dt = _timed(lambda: warm_solve(pts, mlp, k, s_))
             r[f"warm_s{s_}_k{k}"] = _metrics(c.normals, mu.cpu().numpy(), c.valid) + (dt,)
+        # stage times of the warm start: tree build, kNN + features, network
+        t = Tree(pts, theta=THETA)
+        _, r["t_tree_s"] = _timed(lambda: Tree(pts, theta=THETA).close())
+        (_, feat), r["t_knn_s"] = _timed(lambda: knn16(t))
+        _, r["t_mlp_s"] = _timed(lambda: mlp.forward(feat))
+        t.close()
         if signed_net:      # the network's own sign, lengths from iteration 1
             mu, dt = _timed(lambda: warm_solve(pts, mlp, 9, 1, signed=False))
             r["warm_netsign_k9"] = _metrics(c.normals, mu.cpu().numpy(), c.valid) + (dt,)
         rows.append(r)
-    keys = [k for k in rows[0] if k not in ("seed", "n")]
+    keys = [k for k in rows[0] if k not in ("seed", "n") and not k.startswith("t_")]
     summary = {k: {"p_co": float(np.mean([r[k][0] for r in rows])),
                    "ae_pcd": float(np.mean([r[k][1] for r in rows])),
                    "time_s": float(np.mean([r[k][2] for r in rows]))} for k in keys}
+    for k in ("n", "t_tree_s", "t_knn_s", "t_mlp_s"):
+        summary[k] = float(np.mean([r[k] for r in rows]))
     return summary, rows
 
 
@@ -163,7 +174,7 @@ def main(argv=None):
     ap.add_argument("--train", type=int, default=200)
     ap.add_argument("--heldout", type=int, default=20)
     ap.add_argument("--keep", type=int, default=20000)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--loss", type=int, default=1, help="0: 1 - c, 1: 1 - c^2 (sign-free)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
