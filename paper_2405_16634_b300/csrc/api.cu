@@ -28,6 +28,7 @@ static void alloc_workspace(Tree& t) {
     t.s_s = dalloc<float>(n);
     t.area_s = dalloc<float>(n);
     t.mom = dalloc<float4>(nn);
+    t.mom_r = dalloc<float4>(nn);
     t.mom_x = dalloc<float4>(nn);
     t.node_rep = dalloc<float4>(nn);
     t.contrib = dalloc<float4>(t.self.far_entries);
@@ -107,7 +108,7 @@ wnnc_status wnnc_tree_params_default(wnnc_tree_params* p) {
         return WNNC_EINVAL;
     }
     p->max_depth = 15;
-    p->leaf_size = 32;
+    p->leaf_size = 12;
     p->theta = 0.5f;
     p->rep_mode = 1;
     p->moments_fp64 = 0;

@@ -63,14 +63,29 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------------------
 // Work lists.  A warp processes one Item: a slice of one group's interaction
-// lists, at most about kItemCost lane-slots long, so that no single warp
-// carries a group whose lists are unusually long.  Items run heaviest first.
-// When a group is cut into several items, each writes its partial sums to a
-// slot of a scratch buffer and a finalize pass adds the parts in order.
+// lists, at most about `cap` lane-slots long, so that no single warp carries
+// a group whose lists are unusually long.  The cap is fixed per list from its
+// total cost: about total / kItemsTarget rounded down to a power of two,
+// within [kItemCostMin, kItemCostMax], so that small problems still have
+// enough items to fill the GPU and large ones keep items long.  Items run
+// heaviest first.  When a group is cut into several items, each writes its
+// partial sums to a slot of a scratch buffer and a finalize pass adds the
+// parts in order.
 // ---------------------------------------------------------------------------
-constexpr int kItemCost = 4096;     // lane-slots per item (about)
+#ifndef WNNC_ITEMS_TARGET
+#define WNNC_ITEMS_TARGET 8192
+#endif
+#ifndef WNNC_ITEM_MIN
+#define WNNC_ITEM_MIN 256
+#endif
+constexpr int64_t kItemsTarget = WNNC_ITEMS_TARGET;
+constexpr int kItemCostMin = WNNC_ITEM_MIN;    // lane-slots per item (about)
+constexpr int kItemCostMax = 4096;
 constexpr int kMaxRange = 256;      // near ranges are cut into pieces of at most this many points
-constexpr int kGroupSlack = 2;      // group rule: see build_target_set
+#ifndef WNNC_GROUP_SLACK
+#define WNNC_GROUP_SLACK 2
+#endif
+constexpr int kGroupSlack = WNNC_GROUP_SLACK;      // group rule: see build_target_set
 
 struct Item {
     int g;          // target group (adjoint near sums: source chunk)
@@ -87,6 +102,7 @@ struct WorkList {
     int4* splits = nullptr;     // (group, first slot, number of parts, -) of cut groups
     int nsplit = 0;
     int nslots = 0;
+    int cap = 0;                // the item cap of this list (lane-slots)
 };
 void free_work(WorkList& w);
 
@@ -197,6 +213,7 @@ struct Tree {
     float* s_s = nullptr;         // sorted scalar field (s or adjoint input)
     float* area_s = nullptr;      // sorted areas (rescale mode 1)
     float4* mom = nullptr;        // node moments: (nu_x, nu_y, nu_z, sum|nu|)
+    float4* mom_r = nullptr;      // node moments of the step direction r (same layout)
     float4* mom_x = nullptr;      // node weighted offsets (rep_mode 0): sum|nu|(x-cell), -
     float4* node_rep = nullptr;   // representative offset from cell centre, per call
     float4* contrib = nullptr;    // per far entry contribution (adjoint)
@@ -230,7 +247,7 @@ void free_tree(Tree& t);
 
 // operators (operators.cu)
 enum Op : int { kOpA = 0, kOpG = 1, kOpATpaper = 2 };
-void moments(Tree& t, const float4* nu_sorted_vec, const float* nu_sorted_scalar, int rep_mode,
+void moments(Tree& t, const float4* nu_sorted_vec, const float* nu_sorted_scalar, int rep_mode, float4* out,
              cudaStream_t s);
 void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s);
 void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s);

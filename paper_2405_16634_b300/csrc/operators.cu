@@ -39,7 +39,12 @@ constexpr int kGatherWarps = 4;
 #define WNNC_UNROLL 4
 #endif
 #ifndef WNNC_GATHER_MINB
-#define WNNC_GATHER_MINB 1
+#define WNNC_GATHER_MINB 0
+#endif
+#if WNNC_GATHER_MINB > 0
+#define WNNC_GATHER_BOUNDS __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB)
+#else
+#define WNNC_GATHER_BOUNDS __launch_bounds__(32 * kGatherWarps)
 #endif
 constexpr int kUnroll = WNNC_UNROLL;
 
@@ -309,7 +314,7 @@ __device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int6
 }
 
 template <int OP, int EPI>
-__global__ void __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB) k_gather(GatherArgs A) {
+__global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
     __shared__ float4 sp_all[kGatherWarps][32];
     __shared__ float4 sv_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -456,7 +461,7 @@ __device__ __forceinline__ void adj_term(const float4& p, const float4& ti, floa
     az = fmaf(q, dz, az);
 }
 
-__global__ void __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB) k_adj_far(AdjArgs A) {
+__global__ void WNNC_GATHER_BOUNDS k_adj_far(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
@@ -496,15 +501,25 @@ __global__ void __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB) k_adj_far
     }
 }
 
+// One warp per node; lanes take the node's entries (consecutive slots of the
+// node-major list) 128 at a time, four independent gathers per lane in
+// flight, then reduce.  The kernel is bound by the latency of the gathers.
 __global__ void k_adj_node(int nnodes, const int* tfar_off, const int* tfar_ent, const float4* contrib,
                            float4* vnode) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= nnodes) return;
     float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int q = tfar_off[b] + lane; q < tfar_off[b + 1]; q += 32) {
-        const float4 c = contrib[tfar_ent[q]];
-        ax += c.x; ay += c.y; az += c.z;
+    const int q1 = tfar_off[b + 1];
+    for (int q = tfar_off[b] + lane; q < q1; q += 128) {
+        int e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = q + 32 * u < q1 ? tfar_ent[q + 32 * u] : -1;
+        float4 c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = e[u] >= 0 ? contrib[e[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { ax += c[u].x; ay += c[u].y; az += c[u].z; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -544,7 +559,7 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
 }
 
 template <int EPI>
-__global__ void __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB) k_adj_near(AdjArgs A) {
+__global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
@@ -687,6 +702,16 @@ __global__ void k_axpy(const float4* mu, const float4* r, const double* scalars,
     const float a = (float)scalars[3];
     const float4 m = mu[i], d = r[i];
     out[i] = make_float4(fmaf(a, d.x, m.x), fmaf(a, d.y, m.y), fmaf(a, d.z, m.z), 0.f);
+}
+
+// Moments of mu + alpha r from those of mu and r (point-centroid
+// representatives: the moments are linear in nu; the .w sums are not used).
+__global__ void k_node_axpy(float4* mom, const float4* mom_r, const double* scalars, int nnodes) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes) return;
+    const float a = (float)scalars[3];
+    const float4 m = mom[b], d = mom_r[b];
+    mom[b] = make_float4(fmaf(a, d.x, m.x), fmaf(a, d.y, m.y), fmaf(a, d.z, m.z), m.w + fabsf(a) * d.w);
 }
 
 __global__ void k_stats_nograd(float* stats, float w) {
@@ -835,8 +860,9 @@ ProfScope::~ProfScope() {
     }
 }
 
-// Moments of nu over all nodes (and the dynamic representatives in rep_mode 0).
-void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, cudaStream_t s) {
+// Moments of nu over all nodes into `out` (and the dynamic representatives
+// in rep_mode 0).
+void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, float4* out, cudaStream_t s) {
     ProfScope ps(&t.prof, WNNC_PROF_MOMENTS, s);
     const int grid = ceil_div(t.nnodes, kTB);
     const bool w = rep_mode == 0;
@@ -845,11 +871,11 @@ void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, cud
     if (fp64)                                                                                     \
         k_moments<SC, WE, double><<<grid, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count,       \
             t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.corig,    \
-            nu_vec, nu_s, t.mom, t.mom_x, t.dmom, t.arrive);                                       \
+            nu_vec, nu_s, out, t.mom_x, t.dmom, t.arrive);                                         \
     else                                                                                          \
         k_moments<SC, WE, float><<<grid, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count,        \
             t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.corig,    \
-            nu_vec, nu_s, t.mom, t.mom_x, (float*)nullptr, t.arrive);
+            nu_vec, nu_s, out, t.mom_x, (float*)nullptr, t.arrive);
     if (nu_s) {
         if (w) { WNNC_MOM(true, true) } else { WNNC_MOM(true, false) }
     } else {
@@ -858,7 +884,7 @@ void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, cud
 #undef WNNC_MOM
     WNNC_LAUNCH_CHECK();
     if (w) {
-        k_weighted_reps<<<grid, kTB, 0, s>>>(t.nnodes, t.mom, t.mom_x, t.node_cent, t.node_rep);
+        k_weighted_reps<<<grid, kTB, 0, s>>>(t.nnodes, out, t.mom_x, t.node_cent, t.node_rep);
         WNNC_LAUNCH_CHECK();
     }
 }
@@ -873,7 +899,7 @@ static void perm_in_vec(Tree& t, const float* in, float f, float4* out, cudaStre
 void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     const float s2 = (float)(t.scale * t.scale);
     perm_in_vec(t, mu, s2, t.mu_a, s);
-    moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
+    moments(t, t.mu_a, nullptr, t.params.rep_mode, t.mom, s);
     GatherArgs a = base_args(t, t.self, w, t.part_acc);
     a.sval = t.mu_a;
     a.out = out;
@@ -883,7 +909,7 @@ void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
 void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     const float s2 = (float)(t.scale * t.scale);
     perm_in_vec(t, mu, s2, t.mu_a, s);
-    moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
+    moments(t, t.mu_a, nullptr, t.params.rep_mode, t.mom, s);
     GatherArgs a = base_args(t, t.self, w, t.part_acc);
     a.sval = t.mu_a;
     a.out = out;
@@ -950,7 +976,7 @@ void eval_adjoint(Tree& t, const float* sv, float w, float* out, cudaStream_t s)
     if (t.params.rep_mode == 1) {
         adjoint_exact(t, t.s_s, w, out, nullptr, nullptr, s);
     } else {
-        moments(t, nullptr, t.s_s, 0, s);
+        moments(t, nullptr, t.s_s, 0, t.mom, s);
         GatherArgs a = base_args(t, t.self, w, t.part_acc);
         a.sval_s = t.s_s;
         a.out = out;
@@ -979,7 +1005,7 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     }
     cudaFree(qn);
     perm_in_vec(t, mu, s2, t.mu_a, s);
-    moments(t, t.mu_a, nullptr, t.params.rep_mode, s);
+    moments(t, t.mu_a, nullptr, t.params.rep_mode, t.mom, s);
     GatherArgs a = base_args(t, Q, w, pacc);
     a.sval = t.mu_a;
     a.out = out;
@@ -1017,6 +1043,9 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
     const int last = p.last_iter > 0 ? p.last_iter : p.n_iter;
     const int rep_mode = t.params.rep_mode;
     const int n_rr = rep_mode == 1 ? S.nchunks : S.ngroups;
+    // With point-centroid representatives the moments are linear in nu: those
+    // of the updated field mu + alpha r follow from the moments of mu and r.
+    const bool linear_mom = rep_mode == 1 && !t.params.moments_fp64;
     for (int it = p.first_iter; it <= last; ++it) {
         const double wd = p.n_iter <= 1 ? (double)p.w1
                                         : (double)p.w2 * (double)(p.n_iter - it) / (double)(p.n_iter - 1) +
@@ -1025,7 +1054,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
         float* st = stats ? stats + 4 * (int64_t)(it - p.first_iter) : nullptr;
         if (p.use_grad) {
             // s = b - A mu
-            moments(t, mu, nullptr, rep_mode, s);
+            moments(t, mu, nullptr, rep_mode, t.mom, s);
             GatherArgs a = base_args(t, S, w, t.part_acc);
             a.sval = mu;
             a.s_out = t.s_s;
@@ -1036,7 +1065,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
                 adjoint_exact(t, t.s_s, w, nullptr, t.r_s, prr, s);
             } else {
                 // the paper's s-representative treecode for A^T
-                moments(t, nullptr, t.s_s, 0, s);
+                moments(t, nullptr, t.s_s, 0, t.mom, s);
                 GatherArgs c = base_args(t, S, w, t.part_acc);
                 c.sval_s = t.s_s;
                 c.mu_out = t.r_s;
@@ -1044,8 +1073,10 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
                 launch_gather<kOpATpaper, kEpiStoreR>(t, c, s);
             }
             // |A r|^2
-            moments(t, t.r_s, nullptr, rep_mode, s);
+            float4* mom_r = linear_mom ? t.mom_r : t.mom;
+            moments(t, t.r_s, nullptr, rep_mode, mom_r, s);
             GatherArgs b = base_args(t, S, w, t.part_acc);
+            b.nmom = mom_r;
             b.sval = t.r_s;
             b.partial = pqq;
             launch_gather<kOpA, kEpiNormSq>(t, b, s);
@@ -1056,6 +1087,10 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
                 WNNC_LAUNCH_CHECK();
                 k_axpy<<<grid_n, kTB, 0, s>>>(mu, t.r_s, t.scalars, n, mu_alt);
                 WNNC_LAUNCH_CHECK();
+                if (linear_mom && p.use_wnnc) {
+                    k_node_axpy<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.mom, t.mom_r, t.scalars, t.nnodes);
+                    WNNC_LAUNCH_CHECK();
+                }
             }
             std::swap(mu, mu_alt);
         } else if (st) {
@@ -1063,7 +1098,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             WNNC_LAUNCH_CHECK();
         }
         if (p.use_wnnc) {
-            moments(t, mu, nullptr, rep_mode, s);
+            if (!(linear_mom && p.use_grad)) moments(t, mu, nullptr, rep_mode, t.mom, s);
             GatherArgs g = base_args(t, S, w, t.part_acc);
             g.sval = mu;
             g.mu_cur = mu;

@@ -583,7 +583,7 @@ __global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* masks, int64
 
 // ---------------------------------------------------------------------------
 // Work lists: each segment's lists (near units, then far entries in blocks of
-// 32) are cut greedily into items of about kItemCost lane-slots.
+// 32) are cut greedily into items of about `cap` lane-slots.
 //   mode 0: near units are ranges costing their length (gather kernels)
 //   mode 1: near units are transposed entries costing 32 each (adjoint near)
 //   mode 2: far entries only (adjoint far)
@@ -608,40 +608,52 @@ struct ItemWalk {
     }
 };
 
-__device__ int walk_items(int mode, int g, const int* near_off, const int2* rng, const int* far_off,
+__device__ int walk_items(int mode, int g, const int* near_off, const int2* rng, const int* far_off, int cap,
                           Item* out, int base, int pslot_base, int nparts, bool partials) {
     const int qb = near_off ? near_off[g] : 0, qe = near_off ? near_off[g + 1] : 0;
     const int fb = far_off ? far_off[g] : 0, fe = far_off ? far_off[g + 1] : 0;
     ItemWalk w{g, qb, fb, 0, 0, out, base, pslot_base, nparts, partials};
     for (int q = qb; q < qe; ++q) {
         int c = mode == 1 ? 32 : rng[q].y - rng[q].x;
-        if (w.cost > 0 && w.cost + c > kItemCost) w.emit(q, fb);
+        if (w.cost > 0 && w.cost + c > cap) w.emit(q, fb);
         w.cost += c;
     }
     for (int e = fb; e < fe; e += 32) {
         int c = min(32, fe - e);
-        if (w.cost > 0 && w.cost + c > kItemCost) w.emit(qe, e);
+        if (w.cost > 0 && w.cost + c > cap) w.emit(qe, e);
         w.cost += c;
     }
     if (w.cost > 0 || w.k == 0) w.emit(qe, fe);
     return w.k;
 }
 
-__global__ void k_items_count(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
-                              int* cnt, int* slots) {
+// Total cost of segment g (its walk without a cap).
+__global__ void k_seg_cost(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
+                           int64_t* cost) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nseg) return;
-    int c = walk_items(mode, g, near_off, rng, far_off, nullptr, 0, 0, 0, false);
+    int64_t c = 0;
+    if (near_off)
+        for (int q = near_off[g]; q < near_off[g + 1]; ++q) c += mode == 1 ? 32 : rng[q].y - rng[q].x;
+    if (far_off) c += far_off[g + 1] - far_off[g];
+    cost[g] = c;
+}
+
+__global__ void k_items_count(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
+                              int cap, int* cnt, int* slots) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg) return;
+    int c = walk_items(mode, g, near_off, rng, far_off, cap, nullptr, 0, 0, 0, false);
     cnt[g] = c;
     slots[g] = c > 1 ? c : 0;
 }
 
 __global__ void k_items_fill(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
-                             const int* cnt, const int* item_off, const int* slot_off, bool partials,
+                             int cap, const int* cnt, const int* item_off, const int* slot_off, bool partials,
                              Item* items, int4* splits, const int* split_off) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nseg) return;
-    walk_items(mode, g, near_off, rng, far_off, items, item_off[g], slot_off[g], cnt[g], partials);
+    walk_items(mode, g, near_off, rng, far_off, cap, items, item_off[g], slot_off[g], cnt[g], partials);
     if (partials && cnt[g] > 1) splits[split_off[g]] = make_int4(g, slot_off[g], cnt[g], 0);
 }
 
@@ -694,7 +706,21 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     int* slot_off = dalloc<int>(nseg + 2);
     int* flag = dalloc<int>(nseg + 1);
     int* split_off = dalloc<int>(nseg + 2);
-    k_items_count<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cnt, slots);
+    // the item cap from the total cost of all segments
+    int64_t* seg_cost = dalloc<int64_t>(nseg + 1);
+    int64_t* cost_scan = dalloc<int64_t>(nseg + 2);
+    k_seg_cost<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, seg_cost);
+    WNNC_LAUNCH_CHECK();
+    exclusive_scan_i64(seg_cost, cost_scan, nseg, s);
+    int64_t total = 0;
+    WNNC_CUDA(cudaMemcpyAsync(&total, cost_scan + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    cudaFree(seg_cost);
+    cudaFree(cost_scan);
+    int cap = kItemCostMin;
+    while (cap < kItemCostMax && (int64_t)cap * 2 * kItemsTarget <= total) cap *= 2;
+    w.cap = cap;
+    k_items_count<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cap, cnt, slots);
     WNNC_LAUNCH_CHECK();
     exclusive_scan_i32(cnt, item_off, nseg, s);
     exclusive_scan_i32(slots, slot_off, nseg, s);
@@ -706,7 +732,7 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     w.nsplit = partials ? read_int(split_off + nseg, s) : 0;
     Item* tmp = dalloc<Item>(w.nitems);
     w.splits = dalloc<int4>(w.nsplit);
-    k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cnt, item_off,
+    k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cap, cnt, item_off,
                                                     slot_off, partials, tmp, w.splits, split_off);
     WNNC_LAUNCH_CHECK();
     uint64_t* keys = dalloc<uint64_t>(w.nitems);
@@ -1089,7 +1115,7 @@ void free_tree(Tree& t) {
     free_work(t.adj_far_work);
     free_work(t.adj_near_work);
     dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
-    dfree(t.mom_x); dfree(t.dmom); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode); dfree(t.arrive);
+    dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode); dfree(t.arrive);
     dfree(t.partials); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
 
