@@ -3,7 +3,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -18,6 +20,51 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 [[noreturn]] void fail(wnnc_status st, const std::string& msg) { throw Error{st, msg}; }
+
+// ---------------------------------------------------------------------------
+// Stream-ordered memory pool (one per device, created on first use).  Its
+// release threshold is unlimited, so memory freed back to it stays reserved
+// for the next allocation instead of returning to the driver.
+// ---------------------------------------------------------------------------
+cudaStream_t& alloc_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+}
+
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaMemPool_t pool_for_current_device() {
+    int dev = 0;
+    WNNC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxPoolDevices) fail(WNNC_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        WNNC_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t keep = UINT64_MAX;
+        WNNC_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pools[dev] = p;
+    }
+    return g_pools[dev];
+}
+}  // namespace
+
+void* pool_alloc(size_t bytes) {
+    void* p = nullptr;
+    WNNC_CUDA(cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), alloc_stream()));
+    return p;
+}
+
+void pool_free(void* p) {
+    if (p) cudaFreeAsync(p, alloc_stream());
+}
 
 static void alloc_workspace(Tree& t) {
     const int64_t n = t.n;
@@ -34,15 +81,15 @@ static void alloc_workspace(Tree& t) {
     t.contrib = dalloc<float4>(t.self.far_entries);
     t.vnode = dalloc<float4>(nn);
     t.arrive = dalloc<int>(nn);
-    WNNC_CUDA(cudaMemset(t.arrive, 0, sizeof(int) * nn));
+    WNNC_CUDA(cudaMemsetAsync(t.arrive, 0, sizeof(int) * nn, alloc_stream()));
     if (t.params.moments_fp64) t.dmom = dalloc<double>(8 * (size_t)nn);
     t.partials = dalloc<double>(3 * (size_t)std::max(t.self.ngroups, t.self.nchunks));
     t.part_slots = std::max(t.self.work.nslots, t.adj_near_work.nslots);
     t.part_acc = dalloc<float4>((size_t)t.part_slots * 32);
     t.scalars = dalloc<double>(4);
-    WNNC_CUDA(cudaMemset(t.scalars, 0, 4 * sizeof(double)));
+    WNNC_CUDA(cudaMemsetAsync(t.scalars, 0, 4 * sizeof(double), alloc_stream()));
     t.err_flag = dalloc<int>(1);
-    WNNC_CUDA(cudaMemset(t.err_flag, 0, sizeof(int)));
+    WNNC_CUDA(cudaMemsetAsync(t.err_flag, 0, sizeof(int), alloc_stream()));
 }
 
 // Read and clear the latched device error flags.
@@ -150,6 +197,7 @@ wnnc_status wnnc_build_tree(const float* pts, int64_t n, const wnnc_tree_params*
         t->params = p;
         WNNC_CUDA(cudaGetDevice(&t->device));
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        AllocStream as(s);
         build_tree(*t, pts, s);
         alloc_workspace(*t);
         WNNC_CUDA(cudaStreamSynchronize(s));
@@ -211,6 +259,7 @@ wnnc_status wnnc_eval_at(const wnnc_tree* tree, const float* mu, const float* q,
         if (m < 1) fail(WNNC_EINVAL, "m must be >= 1");
         if (m > (int64_t)INT32_MAX / 2) fail(WNNC_EINVAL, "m too large");
         check_w(w);
+        AllocStream as(static_cast<cudaStream_t>(stream));
         eval_at(t, mu, q, m, w, grad, out, static_cast<cudaStream_t>(stream));
     });
 }
@@ -325,6 +374,7 @@ wnnc_status wnnc_sync_status(wnnc_tree* tree, void* stream) {
 wnnc_status wnnc_knn16(const wnnc_tree* tree, int32_t* idx, float* feat, void* stream) {
     return guarded([&] {
         Tree& t = unwrap(tree);
+        AllocStream as(static_cast<cudaStream_t>(stream));
         knn16(t, idx, feat, static_cast<cudaStream_t>(stream));
     });
 }
@@ -342,6 +392,7 @@ wnnc_status wnnc_mlp_create(int64_t max_batch, wnnc_mlp** out) {
         if (max_batch < 1 || max_batch > (int64_t)1 << 26) fail(WNNC_EINVAL, "max_batch must be in [1, 2^26]");
         m = new Mlp();
         mlp_alloc(*m, max_batch);
+        WNNC_CUDA(cudaStreamSynchronize(alloc_stream()));   // allocations complete before any stream uses them
     });
     if (st != WNNC_OK) {
         if (m) {

@@ -45,17 +45,32 @@ void count_launch();
         WNNC_CUDA(cudaGetLastError());  \
     } while (0)
 
+// Device memory comes from the library's own stream-ordered pool on the
+// current device, which keeps freed memory for reuse: once it holds enough,
+// the temporary buffers of a tree build neither call the driver's allocator
+// nor synchronise the device.  Allocations and frees are ordered on the
+// stream of the library call in progress on this thread (AllocStream, set by
+// the build, query and kNN entry points; the legacy default stream otherwise).
+cudaStream_t& alloc_stream();
+struct AllocStream {
+    cudaStream_t prev;
+    explicit AllocStream(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+    ~AllocStream() { alloc_stream() = prev; }
+    AllocStream(const AllocStream&) = delete;
+    AllocStream& operator=(const AllocStream&) = delete;
+};
+void* pool_alloc(size_t bytes);     // throws WNNC_ENOMEM / WNNC_ECUDA
+void pool_free(void* p);            // no-op for NULL
+
 // Typed device allocation that throws on failure.
 template <class T>
 T* dalloc(size_t count) {
-    void* p = nullptr;
     if (count == 0) count = 1;
-    WNNC_CUDA(cudaMalloc(&p, count * sizeof(T)));
-    return static_cast<T*>(p);
+    return static_cast<T*>(pool_alloc(count * sizeof(T)));
 }
 template <class T>
 void dfree(T*& p) {
-    if (p) cudaFree(p);
+    pool_free(p);
     p = nullptr;
 }
 
@@ -231,8 +246,11 @@ struct Tree {
 // scan / sort primitives (scan_sort.cu)
 void exclusive_scan_i32(const int* in, int* out, int64_t n, cudaStream_t s);   // out[n] = total
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
-// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
-void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on key bits [lo_bit, bits).  When
+// the input is already ordered by the bits below lo_bit among equal higher
+// bits (e.g. an index appended in ascending order), stability makes the result
+// the same as a sort on all the low `bits` bits.
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s, int lo_bit = 0);
 // off[g] = first index i with (keys[i] >> 32) >= g, for g in [0, ng]; keys sorted.
 void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s);
 

@@ -216,9 +216,9 @@ void knn16(Tree& t, int* idx_out, float* feat_out, cudaStream_t s) {
     int herr = 0;
     WNNC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(idx);
-    cudaFree(d2);
-    cudaFree(err);
+    pool_free(idx);
+    pool_free(d2);
+    pool_free(err);
     if (herr) fail(WNNC_ECAPACITY, "kNN traversal stack overflow");
 }
 

@@ -1000,10 +1000,10 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     } catch (...) {
         cudaStreamSynchronize(s);
         free_target_set(Q);
-        cudaFree(qn);
+        pool_free(qn);
         throw;
     }
-    cudaFree(qn);
+    pool_free(qn);
     perm_in_vec(t, mu, s2, t.mu_a, s);
     moments(t, t.mu_a, nullptr, t.params.rep_mode, t.mom, s);
     GatherArgs a = base_args(t, Q, w, pacc);
@@ -1013,7 +1013,7 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     if (grad) launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
     else launch_gather<kOpA, kEpiStoreW>(t, a, s);
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(pacc);
+    pool_free(pacc);
     free_target_set(Q);
 }
 

@@ -100,7 +100,7 @@ void exclusive_scan_impl(const T* in, T* out, int64_t n, cudaStream_t s) {
     k_scan_apply<T><<<nb, kScanThreads, 0, s>>>(in, out, n, bsum);
     WNNC_LAUNCH_CHECK();
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(bsum);
+    pool_free(bsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -199,8 +199,8 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
     exclusive_scan_impl<int64_t>(in, out, n, s);
 }
 
-void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s) {
-    if (n <= 1 || bits <= 0) return;
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s, int lo_bit) {
+    if (n <= 1 || bits <= lo_bit) return;
     if (n > (int64_t)INT32_MAX) fail(WNNC_EINVAL, "radix_sort_pairs: too many keys");
     int nb = ceil_div(n, kRsTile);
     uint64_t* k2 = dalloc<uint64_t>(n);
@@ -208,9 +208,9 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
     int* hist = dalloc<int>((size_t)256 * nb + 1);
     uint64_t *ka = keys, *kb = k2;
     uint32_t *va = vals, *vb = v2;
-    int passes = (bits + 7) / 8;
+    int passes = (bits - lo_bit + 7) / 8;
     for (int p = 0; p < passes; ++p) {
-        int shift = 8 * p;
+        int shift = lo_bit + 8 * p;
         k_rs_hist<<<nb, kRsThreads, 0, s>>>(ka, n, shift, hist, nb);
         WNNC_LAUNCH_CHECK();
         exclusive_scan_i32(hist, hist, (int64_t)256 * nb, s);
@@ -224,9 +224,9 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
         if (vals) WNNC_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     }
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(k2);
-    if (v2) cudaFree(v2);
-    cudaFree(hist);
+    pool_free(k2);
+    if (v2) pool_free(v2);
+    pool_free(hist);
 }
 
 void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s) {

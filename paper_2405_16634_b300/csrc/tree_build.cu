@@ -662,10 +662,15 @@ __global__ void k_split_flags(const int* cnt, int nseg, int* flag) {
     if (g < nseg) flag[g] = cnt[g] > 1;
 }
 
-// Heaviest first: key = (INT_MAX - cost) << 32 | item index.
+// Heaviest first: key = (kCostKeyMax - cost) << 32 | item index; an item
+// costs at most the cap plus one near unit (a range of at most kMaxRange
+// points or 32 far entries), so the cost field fits kCostKeyBits bits.
+constexpr int kCostKeyBits = 13;
+constexpr int kCostKeyMax = (1 << kCostKeyBits) - 1;
+static_assert(kItemCostMax + kMaxRange <= kCostKeyMax, "item cost key too narrow");
 __global__ void k_item_keys(const Item* items, int n, uint64_t* keys) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) keys[i] = ((uint64_t)(uint32_t)(0x7fffffff - items[i].cost) << 32) | (uint32_t)i;
+    if (i < n) keys[i] = ((uint64_t)(uint32_t)(kCostKeyMax - min(items[i].cost, kCostKeyMax)) << 32) | (uint32_t)i;
 }
 __global__ void k_item_permute(const Item* in, const uint64_t* keys, int n, Item* out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -715,8 +720,8 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     int64_t total = 0;
     WNNC_CUDA(cudaMemcpyAsync(&total, cost_scan + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(seg_cost);
-    cudaFree(cost_scan);
+    pool_free(seg_cost);
+    pool_free(cost_scan);
     int cap = kItemCostMin;
     while (cap < kItemCostMax && (int64_t)cap * 2 * kItemsTarget <= total) cap *= 2;
     w.cap = cap;
@@ -738,13 +743,13 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     uint64_t* keys = dalloc<uint64_t>(w.nitems);
     k_item_keys<<<ceil_div(w.nitems, kTB), kTB, 0, s>>>(tmp, w.nitems, keys);
     WNNC_LAUNCH_CHECK();
-    radix_sort_pairs(keys, nullptr, w.nitems, 63, s);
+    radix_sort_pairs(keys, nullptr, w.nitems, 32 + kCostKeyBits, s, 32);   // indices already ascending
     w.items = dalloc<Item>(w.nitems);
     k_item_permute<<<ceil_div(w.nitems, kTB), kTB, 0, s>>>(tmp, keys, w.nitems, w.items);
     WNNC_LAUNCH_CHECK();
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(cnt); cudaFree(slots); cudaFree(item_off); cudaFree(slot_off); cudaFree(flag);
-    cudaFree(split_off); cudaFree(tmp); cudaFree(keys);
+    pool_free(cnt); pool_free(slots); pool_free(item_off); pool_free(slot_off); pool_free(flag);
+    pool_free(split_off); pool_free(tmp); pool_free(keys);
 }
 
 void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m, bool self,
@@ -787,7 +792,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         k_run_goff<<<ceil_div(nruns, kTB), kTB, 0, s>>>(run_start, nruns, m, roff, ts.goff);
         WNNC_LAUNCH_CHECK();
         WNNC_CUDA(cudaStreamSynchronize(s));
-        cudaFree(cut); cudaFree(cscan); cudaFree(run_start); cudaFree(rcnt); cudaFree(roff);
+        pool_free(cut); pool_free(cscan); pool_free(run_start); pool_free(rcnt); pool_free(roff);
     } else {
         ts.ngroups = ts.nchunks;
         ts.goff = dalloc<int>(ts.ngroups + 1);
@@ -804,9 +809,9 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
                                                                    ts.gbl, ts.gbh);
     WNNC_LAUNCH_CHECK();
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(ys);
-    cudaFree(keys);
-    cudaFree(idx);
+    pool_free(ys);
+    pool_free(keys);
+    pool_free(idx);
 
     ts.far_off = dalloc<int>(ng + 1);
     int* near_off0 = dalloc<int>(ng + 1);     // merged (uncut) ranges
@@ -834,7 +839,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
                                                     nullptr, err);
         WNNC_LAUNCH_CHECK();
         if (read_int(err, s)) {
-            cudaFree(far_cnt); cudaFree(near_cnt); cudaFree(leaf_off); cudaFree(err); cudaFree(near_off0);
+            pool_free(far_cnt); pool_free(near_cnt); pool_free(leaf_off); pool_free(err); pool_free(near_off0);
             fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
         }
         exclusive_scan_i32(far_cnt, ts.far_off, ng, s);
@@ -883,8 +888,8 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(hscan, leaf_off, ng + 1, near_off0);
         WNNC_LAUNCH_CHECK();
         WNNC_CUDA(cudaStreamSynchronize(s));
-        cudaFree(fkeys); cudaFree(nkeys); cudaFree(nvals); cudaFree(head); cudaFree(hscan);
-        cudaFree(far_cnt); cudaFree(near_cnt); cudaFree(leaf_off); cudaFree(err);
+        pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(head); pool_free(hscan);
+        pool_free(far_cnt); pool_free(near_cnt); pool_free(leaf_off); pool_free(err);
     }
     // cut ranges to at most kMaxRange points
     {
@@ -905,7 +910,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(off, near_off0, ng + 1, ts.near_off);
         WNNC_LAUNCH_CHECK();
         WNNC_CUDA(cudaStreamSynchronize(s));
-        cudaFree(cnt); cudaFree(off); cudaFree(rng0); cudaFree(near_off0);
+        pool_free(cnt); pool_free(off); pool_free(rng0); pool_free(near_off0);
     }
     unsigned long long* pc = dalloc<unsigned long long>(2);
     WNNC_CUDA(cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), s));
@@ -914,7 +919,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     unsigned long long hc[2];
     WNNC_CUDA(cudaMemcpyAsync(hc, pc, sizeof(hc), cudaMemcpyDeviceToHost, s));
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(pc);
+    pool_free(pc);
     ts.far_pairs = (int64_t)hc[0];
     ts.near_pairs = (int64_t)hc[1];
     build_work(ts.work, 0, ng, ts.near_off, ts.near_rng, ts.far_off, true, s);
@@ -931,8 +936,8 @@ static void grow_nodes(Tree& t, int& cap, int need) {
     int ncap = std::max(need, 2 * cap);
     auto grow = [&](int*& p) {
         int* q = dalloc<int>(ncap);
-        WNNC_CUDA(cudaMemcpy(q, p, sizeof(int) * cap, cudaMemcpyDeviceToDevice));
-        cudaFree(p);
+        WNNC_CUDA(cudaMemcpyAsync(q, p, sizeof(int) * cap, cudaMemcpyDeviceToDevice, alloc_stream()));
+        pool_free(p);
         p = q;
     };
     grow(t.node_start); grow(t.node_count); grow(t.node_parent);
@@ -973,10 +978,10 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     t.node_child0 = dalloc<int>(cap); t.node_nchild = dalloc<int>(cap); t.node_depth = dalloc<int>(cap);
     {
         int h0 = 0, hn = (int)n, hp = -1;
-        WNNC_CUDA(cudaMemcpy(t.node_start, &h0, sizeof(int), cudaMemcpyHostToDevice));
-        WNNC_CUDA(cudaMemcpy(t.node_count, &hn, sizeof(int), cudaMemcpyHostToDevice));
-        WNNC_CUDA(cudaMemcpy(t.node_parent, &hp, sizeof(int), cudaMemcpyHostToDevice));
-        WNNC_CUDA(cudaMemcpy(t.node_depth, &h0, sizeof(int), cudaMemcpyHostToDevice));
+        WNNC_CUDA(cudaMemcpyAsync(t.node_start, &h0, sizeof(int), cudaMemcpyHostToDevice, s));
+        WNNC_CUDA(cudaMemcpyAsync(t.node_count, &hn, sizeof(int), cudaMemcpyHostToDevice, s));
+        WNNC_CUDA(cudaMemcpyAsync(t.node_parent, &hp, sizeof(int), cudaMemcpyHostToDevice, s));
+        WNNC_CUDA(cudaMemcpyAsync(t.node_depth, &h0, sizeof(int), cudaMemcpyHostToDevice, s));
     }
     std::vector<int> level_off = {0, 1};
     int base = 0, m = 1, depth = 0, total_nodes = 1;
@@ -1001,8 +1006,8 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             ++depth;
         }
     }
-    cudaFree(nkids);
-    cudaFree(koff);
+    pool_free(nkids);
+    pool_free(koff);
     t.nnodes = total_nodes;
     t.nlevels = (int)level_off.size() - 1;
     t.depth_reached = t.nlevels - 1;
@@ -1027,7 +1032,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
                                                         t.node_cent, t.leaf_of);
     WNNC_LAUNCH_CHECK();
     WNNC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(sum);
+    pool_free(sum);
     {
         std::vector<int> nc(t.nnodes);
         WNNC_CUDA(cudaMemcpy(nc.data(), t.node_nchild, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
@@ -1036,11 +1041,11 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
 
     // --- the points as targets: same Morton order as the sources ---
     build_target_set(t, t.self, xn, n, true, s);
-    cudaFree(xn);
-    cudaFree(idx);
-    cudaFree(perm_tmp);
-    cudaFree(part);
-    cudaFree(cs);
+    pool_free(xn);
+    pool_free(idx);
+    pool_free(perm_tmp);
+    pool_free(part);
+    pool_free(cs);
 
     // --- transposed lists and work lists for the adjoint ---
     const TargetSet& S = t.self;
@@ -1053,7 +1058,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, k);
             WNNC_LAUNCH_CHECK();
         }
-        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes), s);
+        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes), s, 32);   // entry indices already ascending
         t.tfar_ent = dalloc<int>(ne);
         if (ne) {
             k_low32<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, t.tfar_ent);
@@ -1061,7 +1066,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         }
         segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
         WNNC_CUDA(cudaStreamSynchronize(s));
-        cudaFree(k);
+        pool_free(k);
     }
     {
         int64_t nr = S.near_ranges;
@@ -1077,7 +1082,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         uint32_t* msk = dalloc<uint32_t>(ne);
         k_tnear_fill<<<ceil_div(ng, kTB), kTB, 0, s>>>(S.near_rng, S.near_off, ng, coff, k, msk);
         WNNC_LAUNCH_CHECK();
-        radix_sort_pairs(k, msk, ne, 32 + bits_for(nch), s);
+        radix_sort_pairs(k, msk, ne, 32 + bits_for(nch), s, 32);   // groups already ascending
         int* head = dalloc<int>(ne + 1);
         int* hscan = dalloc<int>(ne + 2);
         if (ne) {
@@ -1096,8 +1101,8 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         t.tnear_off = dalloc<int>(nch + 1);
         segment_offsets_hi32(uk, nu, t.tnear_off, nch, s);
         WNNC_CUDA(cudaStreamSynchronize(s));
-        cudaFree(cnt); cudaFree(coff); cudaFree(k); cudaFree(msk); cudaFree(head); cudaFree(hscan);
-        cudaFree(uk);
+        pool_free(cnt); pool_free(coff); pool_free(k); pool_free(msk); pool_free(head); pool_free(hscan);
+        pool_free(uk);
     }
     build_work(t.adj_far_work, 2, ng, nullptr, nullptr, S.far_off, false, s);
     build_work(t.adj_near_work, 1, nch, t.tnear_off, nullptr, nullptr, true, s);
