@@ -97,6 +97,7 @@ constexpr int64_t kItemsTarget = WNNC_ITEMS_TARGET;
 constexpr int kItemCostMin = WNNC_ITEM_MIN;    // lane-slots per item (about)
 constexpr int kItemCostMax = 4096;
 constexpr int kMaxRange = 256;      // near ranges are cut into pieces of at most this many points
+constexpr int kAdjChunk = 8;        // points per source chunk of the adjoint near part
 #ifndef WNNC_GROUP_SLACK
 #define WNNC_GROUP_SLACK 2
 #endif
@@ -215,8 +216,9 @@ struct Tree {
     // transposed lists (adjoint, rep_mode 1)
     int* tfar_off = nullptr;      // [nnodes+1]
     int* tfar_ent = nullptr;      // far-entry index (position in self.far_id), grouped by node
-    int* tnear_off = nullptr;     // [nchunks+1], per source chunk
-    int2* tnear_ent = nullptr;    // (target group, lane mask of the source chunk)
+    int nach = 0;                 // source chunks of the adjoint near part (kAdjChunk points each)
+    int* tnear_off = nullptr;     // [nach+1], per source chunk
+    int2* tnear_ent = nullptr;    // (target group, mask of the chunk's points in its near lists)
     int64_t tnear_entries = 0;
     WorkList adj_far_work;        // items over the far lists (per target group)
     WorkList adj_near_work;       // items over the transposed near entries (per source chunk)
@@ -235,7 +237,8 @@ struct Tree {
     float4* vnode = nullptr;      // per node far sum (adjoint)
     int* arrive = nullptr;        // bottom-up arrival counters (zero between launches)
     double* dmom = nullptr;       // double-precision node moments (moments_fp64), 8 per node
-    double* partials = nullptr;   // per-group partial sums (3 x max(ngroups, nchunks))
+    double* partials = nullptr;   // per-group partial sums (3 x max(ngroups, nchunks, nach))
+    double* red = nullptr;        // first-stage sums of the partials (3 x 256)
     float4* part_acc = nullptr;   // scratch: partial sums of cut groups, 32 per slot
     int part_slots = 0;
     double* scalars = nullptr;    // device scalars: [0]=E [1]=rr [2]=qq [3]=alpha

@@ -558,6 +558,11 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
     }
 }
 
+// Near part, one warp per work item: a slice of the transposed entries of
+// source chunk C (kAdjChunk = 8 consecutive sorted points).  Lane l handles
+// source point 8C + (l & 7) against every fourth target (offset l >> 3) of
+// each entry's group, if the entry's mask holds the point; the four partial
+// sums of a point are added at the end (fixed order), into lanes 0..7.
 template <int EPI>
 __global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
@@ -566,10 +571,11 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
     if (it >= A.nitems) return;
     float4* tp = tp_all[wl];
     const Item item = A.items[it];
-    const int gs = item.g;                       // source chunk (outputs)
-    const int64_t j = (int64_t)gs * kGroup + lane;
+    const int sc = item.g;                       // source chunk (outputs)
+    const int sl = lane & (kAdjChunk - 1), tq = lane / kAdjChunk;
+    const int64_t j = (int64_t)sc * kAdjChunk + sl;
     const bool valid = j < A.n;
-    const float4 o = A.corig[gs];
+    const float4 o = A.corig[((int64_t)sc * kAdjChunk) >> 5];   // frame of the chunk's points
     const float4 xj = valid ? A.pos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     float ax = 0.f, ay = 0.f, az = 0.f;
     for (int q = item.q0; q < item.q1; ++q) {
@@ -583,30 +589,21 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
             p.w = A.sv[i];
             tp[lane] = p;
         }
-        const bool mine = (mask >> lane) & 1u;
-        bool clear = true;
-        if (mine) {   // the group's box in this chunk's frame
-            const float4 go = A.gorig[g];
-            const float4 sh = make_float4(go.x - o.x, go.y - o.y, go.z - o.z, 0.f);
-            const float4 lo = A.gbl[g], hi = A.gbh[g];
-            clear = box_gap2(make_float4(lo.x + sh.x, lo.y + sh.y, lo.z + sh.z, 0.f),
-                             make_float4(hi.x + sh.x, hi.y + sh.y, hi.z + sh.z, 0.f), xj) >= A.fast2;
-        }
-        clear = __all_sync(0xffffffffu, clear);
         __syncwarp();
-        if (mine) {
-            if (clear) {
-#pragma unroll kUnroll
-                for (int k = 0; k < cnt_t; ++k) adj_term<false>(xj, tp[k], A.w2, ax, ay, az);
-            } else {
-#pragma unroll kUnroll
-                for (int k = 0; k < cnt_t; ++k) adj_term<true>(xj, tp[k], A.w2, ax, ay, az);
-            }
+        if ((mask >> sl) & 1u) {
+#pragma unroll 2
+            for (int k = tq; k < cnt_t; k += 32 / kAdjChunk) adj_term<true>(xj, tp[k], A.w2, ax, ay, az);
         }
         __syncwarp();
     }
+#pragma unroll
+    for (int o2 = kAdjChunk; o2 < 32; o2 <<= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o2);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o2);
+        az += __shfl_xor_sync(0xffffffffu, az, o2);
+    }
     if (item.pslot < 0) {
-        adj_epilogue<EPI>(A, gs, j, valid, ax, ay, az, lane);
+        adj_epilogue<EPI>(A, sc, j, valid && lane < kAdjChunk, ax, ay, az, lane);
     } else {
         A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(ax, ay, az, 0.f);
     }
@@ -623,8 +620,8 @@ __global__ void k_adj_near_finalize(AdjArgs A) {
         const float4 v = A.part_acc[(int64_t)(sp.y + p) * 32 + lane];
         ax += v.x; ay += v.y; az += v.z;
     }
-    const int64_t j = (int64_t)sp.x * kGroup + lane;
-    adj_epilogue<EPI>(A, sp.x, j, j < A.n, ax, ay, az, lane);
+    const int64_t j = (int64_t)sp.x * kAdjChunk + (lane & (kAdjChunk - 1));
+    adj_epilogue<EPI>(A, sp.x, j, j < A.n && lane < kAdjChunk, ax, ay, az, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -660,6 +657,34 @@ __global__ void k_normalize_queries(const float* q, int64_t m, double cx, double
 
 // Deterministic reduction of the per-group partials and the step length of
 // Alg. 2: alpha = |r|^2 / |A r|^2 (0 if |A r| = 0).  Also records the stats.
+// First stage of the reduction of the three partial-sum arrays: block b adds
+// the b-th of kRedBlocks fixed slices of each array (FP64 runs at a small
+// fraction of the FP32 rate, so one block alone is slow for 10^4-10^5
+// partials).  The order depends only on the sizes.
+constexpr int kRedBlocks = 256;
+__global__ void k_reduce3(const double* a0, int n0, const double* a1, int n1, const double* a2, int n2,
+                          double* out) {
+    __shared__ double sh[3][kTB];
+    const double* arr[3] = {a0, a1, a2};
+    const int n[3] = {n0, n1, n2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int per = (n[c] + kRedBlocks - 1) / kRedBlocks;
+        const int lo = blockIdx.x * per, hi = min(n[c], lo + per);
+        double s = 0.0;
+        for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) s += arr[c][k];
+        sh[c][threadIdx.x] = s;
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) out[c * kRedBlocks + blockIdx.x] = sh[c][0];
+}
+
 __global__ void k_finalize_alpha(const double* pE, int nE, const double* prr, int nrr, const double* pqq,
                                  int nqq, double* scalars, float* stats, float w, int* err) {
     __shared__ double sh[3][1024];
@@ -1022,7 +1047,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
              float* stats) {
     const int64_t n = t.n;
     const TargetSet& S = t.self;
-    const int npart = std::max(S.ngroups, S.nchunks);
+    const int npart = std::max(std::max(S.ngroups, S.nchunks), t.nach);
     const float s2 = (float)(t.scale * t.scale);
     const int grid_n = ceil_div(n, kTB);
     float4* mu = t.mu_a;
@@ -1042,7 +1067,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
     double* pqq = t.partials + 2 * (int64_t)npart;
     const int last = p.last_iter > 0 ? p.last_iter : p.n_iter;
     const int rep_mode = t.params.rep_mode;
-    const int n_rr = rep_mode == 1 ? S.nchunks : S.ngroups;
+    const int n_rr = rep_mode == 1 ? t.nach : S.ngroups;
     // With point-centroid representatives the moments are linear in nu: those
     // of the updated field mu + alpha r follow from the moments of mu and r.
     const bool linear_mom = rep_mode == 1 && !t.params.moments_fp64;
@@ -1082,8 +1107,11 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             launch_gather<kOpA, kEpiNormSq>(t, b, s);
             {
                 ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
-                k_finalize_alpha<<<1, 1024, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.scalars, st, w,
-                                                    t.err_flag);
+                k_reduce3<<<kRedBlocks, kTB, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.red);
+                WNNC_LAUNCH_CHECK();
+                k_finalize_alpha<<<1, kRedBlocks, 0, s>>>(t.red, kRedBlocks, t.red + kRedBlocks, kRedBlocks,
+                                                          t.red + 2 * kRedBlocks, kRedBlocks, t.scalars, st, w,
+                                                          t.err_flag);
                 WNNC_LAUNCH_CHECK();
                 k_axpy<<<grid_n, kTB, 0, s>>>(mu, t.r_s, t.scalars, n, mu_alt);
                 WNNC_LAUNCH_CHECK();

@@ -538,12 +538,13 @@ __global__ void k_tfar_keys(const int* far_id, int64_t nent, uint64_t* keys) {
 }
 
 // Transposed near entries: for each near range of target group g, the source
-// chunks it overlaps, with the mask of overlapped lanes.
+// chunks (kAdjChunk consecutive sorted points) it overlaps, with the mask of
+// the overlapped points.
 __global__ void k_tnear_count(const int2* rng, int64_t nr, int* cnt) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nr) return;
     int2 r = rng[q];
-    cnt[q] = r.y > r.x ? (((r.y - 1) >> 5) - (r.x >> 5) + 1) : 0;
+    cnt[q] = r.y > r.x ? (r.y - 1) / kAdjChunk - r.x / kAdjChunk + 1 : 0;
 }
 
 __global__ void k_tnear_fill(const int2* rng, const int* near_off, int ng, const int* cnt_off,
@@ -554,10 +555,10 @@ __global__ void k_tnear_fill(const int2* rng, const int* near_off, int ng, const
         int2 r = rng[q];
         if (r.y <= r.x) continue;
         int p = cnt_off[q];
-        for (int sg = r.x >> 5; sg <= (r.y - 1) >> 5; ++sg, ++p) {
-            int lo = max(r.x, sg * 32) - sg * 32, hi = min(r.y, sg * 32 + 32) - sg * 32;
-            uint32_t m = (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-            keys[p] = ((uint64_t)(uint32_t)sg << 32) | (uint32_t)g;
+        for (int sc = r.x / kAdjChunk; sc <= (r.y - 1) / kAdjChunk; ++sc, ++p) {
+            int lo = max(r.x, sc * kAdjChunk) - sc * kAdjChunk, hi = min(r.y, (sc + 1) * kAdjChunk) - sc * kAdjChunk;
+            uint32_t m = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+            keys[p] = ((uint64_t)(uint32_t)sc << 32) | (uint32_t)g;
             masks[p] = m;
         }
     }
@@ -585,7 +586,8 @@ __global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* masks, int64
 // Work lists: each segment's lists (near units, then far entries in blocks of
 // 32) are cut greedily into items of about `cap` lane-slots.
 //   mode 0: near units are ranges costing their length (gather kernels)
-//   mode 1: near units are transposed entries costing 32 each (adjoint near)
+//   mode 1: near units are transposed entries costing 8 each (adjoint near:
+//           a quarter of a target group per lane)
 //   mode 2: far entries only (adjoint far)
 // ---------------------------------------------------------------------------
 struct ItemWalk {
@@ -614,7 +616,7 @@ __device__ int walk_items(int mode, int g, const int* near_off, const int2* rng,
     const int fb = far_off ? far_off[g] : 0, fe = far_off ? far_off[g + 1] : 0;
     ItemWalk w{g, qb, fb, 0, 0, out, base, pslot_base, nparts, partials};
     for (int q = qb; q < qe; ++q) {
-        int c = mode == 1 ? 32 : rng[q].y - rng[q].x;
+        int c = mode == 1 ? 8 : rng[q].y - rng[q].x;
         if (w.cost > 0 && w.cost + c > cap) w.emit(q, fb);
         w.cost += c;
     }
@@ -634,7 +636,7 @@ __global__ void k_seg_cost(int mode, int nseg, const int* near_off, const int2* 
     if (g >= nseg) return;
     int64_t c = 0;
     if (near_off)
-        for (int q = near_off[g]; q < near_off[g + 1]; ++q) c += mode == 1 ? 32 : rng[q].y - rng[q].x;
+        for (int q = near_off[g]; q < near_off[g + 1]; ++q) c += mode == 1 ? 8 : rng[q].y - rng[q].x;
     if (far_off) c += far_off[g + 1] - far_off[g];
     cost[g] = c;
 }
@@ -1049,7 +1051,9 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
 
     // --- transposed lists and work lists for the adjoint ---
     const TargetSet& S = t.self;
-    const int ng = S.ngroups, nch = S.nchunks;
+    const int ng = S.ngroups;
+    const int nach = ceil_div(t.n, kAdjChunk);
+    t.nach = nach;
     t.tfar_off = dalloc<int>(t.nnodes + 1);
     {
         int64_t ne = S.far_entries;
@@ -1082,7 +1086,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         uint32_t* msk = dalloc<uint32_t>(ne);
         k_tnear_fill<<<ceil_div(ng, kTB), kTB, 0, s>>>(S.near_rng, S.near_off, ng, coff, k, msk);
         WNNC_LAUNCH_CHECK();
-        radix_sort_pairs(k, msk, ne, 32 + bits_for(nch), s, 32);   // groups already ascending
+        radix_sort_pairs(k, msk, ne, 32 + bits_for(nach), s, 32);   // groups already ascending
         int* head = dalloc<int>(ne + 1);
         int* hscan = dalloc<int>(ne + 2);
         if (ne) {
@@ -1098,14 +1102,14 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             k_tnear_merge<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, msk, ne, hscan, t.tnear_ent, uk);
             WNNC_LAUNCH_CHECK();
         }
-        t.tnear_off = dalloc<int>(nch + 1);
-        segment_offsets_hi32(uk, nu, t.tnear_off, nch, s);
+        t.tnear_off = dalloc<int>(nach + 1);
+        segment_offsets_hi32(uk, nu, t.tnear_off, nach, s);
         WNNC_CUDA(cudaStreamSynchronize(s));
         pool_free(cnt); pool_free(coff); pool_free(k); pool_free(msk); pool_free(head); pool_free(hscan);
         pool_free(uk);
     }
     build_work(t.adj_far_work, 2, ng, nullptr, nullptr, S.far_off, false, s);
-    build_work(t.adj_near_work, 1, nch, t.tnear_off, nullptr, nullptr, true, s);
+    build_work(t.adj_near_work, 1, nach, t.tnear_off, nullptr, nullptr, true, s);
 }
 
 void free_tree(Tree& t) {
@@ -1121,7 +1125,7 @@ void free_tree(Tree& t) {
     free_work(t.adj_near_work);
     dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
     dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode); dfree(t.arrive);
-    dfree(t.partials); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
+    dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
 
 }  // namespace wnnc
