@@ -76,13 +76,10 @@ static void alloc_workspace(Tree& t) {
     t.area_s = dalloc<float>(n);
     t.mom = dalloc<float4>(nn);
     t.mom_r = dalloc<float4>(nn);
-    t.mom_x = dalloc<float4>(nn);
     t.node_rep = dalloc<float4>(nn);
     t.contrib = dalloc<float4>(t.self.far_entries);
     t.vnode = dalloc<float4>(nn);
-    t.arrive = dalloc<int>(nn);
-    WNNC_CUDA(cudaMemsetAsync(t.arrive, 0, sizeof(int) * nn, alloc_stream()));
-    if (t.params.moments_fp64) t.dmom = dalloc<double>(8 * (size_t)nn);
+    t.mom_x = dalloc<float4>(nn);
     t.partials = dalloc<double>(3 * (size_t)std::max(std::max(t.self.ngroups, t.self.nchunks), t.nach));
     t.red = dalloc<double>(3 * 256);
     t.part_slots = std::max(t.self.work.nslots, t.adj_near_work.nslots);

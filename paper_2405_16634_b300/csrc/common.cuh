@@ -98,6 +98,8 @@ constexpr int kItemCostMin = WNNC_ITEM_MIN;    // lane-slots per item (about)
 constexpr int kItemCostMax = 4096;
 constexpr int kMaxRange = 256;      // near ranges are cut into pieces of at most this many points
 constexpr int kAdjChunk = 8;        // points per source chunk of the adjoint near part
+constexpr int kMomSmall = 16;       // node moments: nodes of at most this many points, one thread each
+constexpr int kMomDirect = 1024;    //   up to this many points, one warp each; larger ones from children
 #ifndef WNNC_GROUP_SLACK
 #define WNNC_GROUP_SLACK 2
 #endif
@@ -204,6 +206,9 @@ struct Tree {
     int* node_depth = nullptr;
     int* level_off = nullptr;     // host: first node of each level, [levels+1]
     int nlevels = 0;
+    int mom_top_levels = 0;       // levels 0.. that hold nodes of more than kMomDirect points
+    int nmom_mid = 0;             // nodes of kMomSmall+1 .. kMomDirect points
+    int* mom_mid = nullptr;       // their ids
     double* node_lo = nullptr;    // tight bounding boxes (build)
     double* node_hi = nullptr;
     float4* node_cell = nullptr;  // cell centre (exact) + width
@@ -231,12 +236,10 @@ struct Tree {
     float* area_s = nullptr;      // sorted areas (rescale mode 1)
     float4* mom = nullptr;        // node moments: (nu_x, nu_y, nu_z, sum|nu|)
     float4* mom_r = nullptr;      // node moments of the step direction r (same layout)
-    float4* mom_x = nullptr;      // node weighted offsets (rep_mode 0): sum|nu|(x-cell), -
     float4* node_rep = nullptr;   // representative offset from cell centre, per call
     float4* contrib = nullptr;    // per far entry contribution (adjoint)
     float4* vnode = nullptr;      // per node far sum (adjoint)
-    int* arrive = nullptr;        // bottom-up arrival counters (zero between launches)
-    double* dmom = nullptr;       // double-precision node moments (moments_fp64), 8 per node
+    float4* mom_x = nullptr;      // node weighted offsets (rep_mode 0): sum |nu| (x - cell), -
     double* partials = nullptr;   // per-group partial sums (3 x max(ngroups, nchunks, nach))
     double* red = nullptr;        // first-stage sums of the partials (3 x 256)
     float4* part_acc = nullptr;   // scratch: partial sums of cut groups, 32 per slot

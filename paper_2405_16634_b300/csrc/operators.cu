@@ -49,97 +49,125 @@ constexpr int kGatherWarps = 4;
 constexpr int kUnroll = WNNC_UNROLL;
 
 // ---------------------------------------------------------------------------
-// Node moments, bottom-up in one launch: each leaf sums its points, then the
-// last child to arrive at a parent sums the parent's children (in child
-// order, so the result does not depend on arrival order) and climbs on.
-// No thread waits for another: a thread that is not last simply returns.
-//   mom[b]   = (sum nu, sum |nu|)        (nu = mu: 3 components; nu = s: 1)
-//   momx[b]  = sum |nu| (x - cell_b)     (only for the |nu|-weighted representative)
+// Node moments in three launches, with no dependency chain through the whole
+// tree:
+//   1. one thread per node of at most kMomSmall points sums its point range;
+//   2. one warp per node of up to kMomDirect points sums its range
+//      (lane-strided, then a fixed xor reduction);
+//   3. one block adds the few larger nodes (the top levels) from their
+//      children, deepest level first, in child order.
+//   mom[b]  = (sum nu, sum |nu|)        (nu = mu: 3 components; nu = s: 1)
+//   momx[b] = sum |nu| (x - cell_b)     (only for the |nu|-weighted representative)
+//   rep[b]  = momx[b] / sum |nu|, or the point centroid when sum |nu| = 0
 // ---------------------------------------------------------------------------
-template <bool SCALAR, bool WEIGHTED, class Acc>
-__global__ void k_moments(int nnodes, const int* nstart, const int* ncount, const int* nparent,
-                          const int* nchild, const int* nchild0, const float4* ncell,
-                          const float4* spos, const float4* scorig, const float4* nu_vec,
-                          const float* nu_s, float4* mom, float4* momx, Acc* dmom, int* arrive) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnodes || nchild[b] != 0) return;
-    Acc m0 = 0, m1 = 0, m2 = 0, wsum = 0, x0 = 0, x1 = 0, x2 = 0;
-    const float4 cb = ncell[b];
-    for (int j = nstart[b]; j < nstart[b] + ncount[b]; ++j) {
-        float v0, v1 = 0.f, v2 = 0.f, a;
-        if (SCALAR) {
-            v0 = nu_s[j];
-            a = fabsf(v0);
-        } else {
-            float4 v = nu_vec[j];
-            v0 = v.x; v1 = v.y; v2 = v.z;
-            a = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
-        }
-        m0 += v0; m1 += v1; m2 += v2; wsum += a;
-        if (WEIGHTED) {
-            float4 p = spos[j];
-            float4 go = scorig[j >> 5];   // the point's chunk frame
-            x0 += (Acc)a * (Acc)((go.x - cb.x) + p.x);
-            x1 += (Acc)a * (Acc)((go.y - cb.y) + p.y);
-            x2 += (Acc)a * (Acc)((go.z - cb.z) + p.z);
-        }
+// Point term of the moments: nu (3 or 1 components), |nu|, |nu| (x - cell).
+template <bool SCALAR, bool WEIGHTED>
+__device__ __forceinline__ void mom_point(int j, const float4& cb, const float4* spos, const float4* scorig,
+                                          const float4* nu_vec, const float* nu_s, float& m0, float& m1,
+                                          float& m2, float& ws, float& x0, float& x1, float& x2) {
+    float v0, v1 = 0.f, v2 = 0.f, a;
+    if (SCALAR) {
+        v0 = nu_s[j];
+        a = fabsf(v0);
+    } else {
+        const float4 v = nu_vec[j];
+        v0 = v.x; v1 = v.y; v2 = v.z;
+        a = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
     }
-    for (;;) {
-        mom[b] = make_float4((float)m0, (float)m1, (float)m2, (float)wsum);
-        if (WEIGHTED) momx[b] = make_float4((float)x0, (float)x1, (float)x2, 0.f);
-        if (dmom) {
-            Acc* d = dmom + 8 * (int64_t)b;
-            d[0] = m0; d[1] = m1; d[2] = m2; d[3] = wsum; d[4] = x0; d[5] = x1; d[6] = x2;
-        }
-        int p = nparent[b];
-        if (p < 0) return;
-        __threadfence();
-        int old = atomicAdd(&arrive[p], 1);
-        if (old != nchild[p] - 1) return;
-        arrive[p] = 0;   // reset for the next launch; nobody else touches it now
-        __threadfence();
-        const float4 cp = ncell[p];
-        m0 = m1 = m2 = wsum = x0 = x1 = x2 = 0;
-        for (int q = 0; q < nchild[p]; ++q) {
-            int c = nchild0[p] + q;
-            Acc c0, c1, c2, cw, cx0 = 0, cx1 = 0, cx2 = 0;
-            if (dmom) {
-                const Acc* d = dmom + 8 * (int64_t)c;
-                c0 = __ldcg(d); c1 = __ldcg(d + 1); c2 = __ldcg(d + 2); cw = __ldcg(d + 3);
-                if (WEIGHTED) { cx0 = __ldcg(d + 4); cx1 = __ldcg(d + 5); cx2 = __ldcg(d + 6); }
-            } else {
-                float4 mm = __ldcg(&mom[c]);
-                c0 = mm.x; c1 = mm.y; c2 = mm.z; cw = mm.w;
-                if (WEIGHTED) {
-                    float4 xx = __ldcg(&momx[c]);
-                    cx0 = xx.x; cx1 = xx.y; cx2 = xx.z;
-                }
-            }
-            m0 += c0; m1 += c1; m2 += c2; wsum += cw;
-            if (WEIGHTED) {
-                // re-centre the child's weighted offsets on the parent's cell
-                const float4 cc = ncell[c];
-                x0 += cx0 + cw * (Acc)(cc.x - cp.x);
-                x1 += cx1 + cw * (Acc)(cc.y - cp.y);
-                x2 += cx2 + cw * (Acc)(cc.z - cp.z);
-            }
-        }
-        b = p;
+    m0 += v0; m1 += v1; m2 += v2; ws += a;
+    if (WEIGHTED) {
+        const float4 p = spos[j], go = scorig[j >> 5];   // the point in its chunk frame
+        x0 = fmaf(a, (go.x - cb.x) + p.x, x0);
+        x1 = fmaf(a, (go.y - cb.y) + p.y, x1);
+        x2 = fmaf(a, (go.z - cb.z) + p.z, x2);
     }
 }
 
-// Representative offsets from the cell centre: |nu|-weighted centroid where
-// sum |nu| > 0, else the point centroid.
-__global__ void k_weighted_reps(int nnodes, const float4* mom, const float4* momx,
-                                const float4* cent, float4* rep) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
+template <bool WEIGHTED>
+__device__ __forceinline__ void mom_store(int b, const float4* ncent, float4* mom, float4* momx, float4* rep,
+                                          float m0, float m1, float m2, float ws, float x0, float x1, float x2) {
+    mom[b] = make_float4(m0, m1, m2, ws);
+    if (WEIGHTED) {
+        momx[b] = make_float4(x0, x1, x2, 0.f);
+        rep[b] = ws > 0.f ? make_float4(x0 / ws, x1 / ws, x2 / ws, 0.f) : ncent[b];
+    }
+}
+
+template <bool SCALAR, bool WEIGHTED>
+__global__ void k_mom_small(int nnodes, const int* nstart, const int* ncount, const float4* ncell,
+                            const float4* ncent, const float4* spos, const float4* scorig, const float4* nu_vec,
+                            const float* nu_s, float4* mom, float4* momx, float4* rep) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnodes) return;
-    float w = mom[b].w;
-    if (w > 0.f) {
-        float4 x = momx[b];
-        rep[b] = make_float4(x.x / w, x.y / w, x.z / w, 0.f);
-    } else {
-        rep[b] = cent[b];
+    const int cnt = ncount[b];
+    if (cnt > kMomSmall) return;
+    const int j0 = nstart[b];
+    const float4 cb = ncell[b];
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, ws = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f;
+#pragma unroll 4
+    for (int j = j0; j < j0 + cnt; ++j)
+        mom_point<SCALAR, WEIGHTED>(j, cb, spos, scorig, nu_vec, nu_s, m0, m1, m2, ws, x0, x1, x2);
+    mom_store<WEIGHTED>(b, ncent, mom, momx, rep, m0, m1, m2, ws, x0, x1, x2);
+}
+
+template <bool SCALAR, bool WEIGHTED>
+__global__ void k_mom_direct(int nmid, const int* mid, const int* nstart, const int* ncount, const float4* ncell,
+                             const float4* ncent, const float4* spos, const float4* scorig,
+                             const float4* nu_vec, const float* nu_s, float4* mom, float4* momx, float4* rep) {
+    const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= nmid) return;
+    const int b = mid[k];
+    const int cnt = ncount[b];
+    const int j0 = nstart[b];
+    const float4 cb = ncell[b];
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, ws = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f;
+#pragma unroll 4
+    for (int j = j0 + lane; j < j0 + cnt; j += 32)
+        mom_point<SCALAR, WEIGHTED>(j, cb, spos, scorig, nu_vec, nu_s, m0, m1, m2, ws, x0, x1, x2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+        m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        ws += __shfl_xor_sync(0xffffffffu, ws, o);
+        if (WEIGHTED) {
+            x0 += __shfl_xor_sync(0xffffffffu, x0, o);
+            x1 += __shfl_xor_sync(0xffffffffu, x1, o);
+            x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+        }
+    }
+    if (lane == 0) mom_store<WEIGHTED>(b, ncent, mom, momx, rep, m0, m1, m2, ws, x0, x1, x2);
+}
+
+struct LevelOffsets {
+    int off[17];   // first node of levels 0..15, and the end of the last
+};
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(1024) k_mom_top(int nlev, LevelOffsets lv, const int* ncount,
+                                                  const int* nchild, const int* nchild0, const float4* ncell,
+                                                  const float4* ncent, float4* mom, float4* momx, float4* rep) {
+    for (int d = nlev - 1; d >= 0; --d) {
+        for (int b = lv.off[d] + threadIdx.x; b < lv.off[d + 1]; b += blockDim.x) {
+            if (ncount[b] <= kMomDirect) continue;
+            const float4 cp = ncell[b];
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f, ws = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f;
+            for (int q = 0; q < nchild[b]; ++q) {
+                const int c = nchild0[b] + q;
+                const float4 mm = mom[c];
+                m0 += mm.x; m1 += mm.y; m2 += mm.z; ws += mm.w;
+                if (WEIGHTED) {
+                    // re-centre the child's weighted offsets on this node's cell
+                    const float4 xx = momx[c], cc = ncell[c];
+                    x0 += xx.x + mm.w * (cc.x - cp.x);
+                    x1 += xx.y + mm.w * (cc.y - cp.y);
+                    x2 += xx.z + mm.w * (cc.z - cp.z);
+                }
+            }
+            mom_store<WEIGHTED>(b, ncent, mom, momx, rep, m0, m1, m2, ws, x0, x1, x2);
+        }
+        __syncthreads();
     }
 }
 
@@ -889,27 +917,39 @@ ProfScope::~ProfScope() {
 // in rep_mode 0).
 void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, float4* out, cudaStream_t s) {
     ProfScope ps(&t.prof, WNNC_PROF_MOMENTS, s);
-    const int grid = ceil_div(t.nnodes, kTB);
     const bool w = rep_mode == 0;
-    const bool fp64 = t.params.moments_fp64 != 0;
-#define WNNC_MOM(SC, WE)                                                                          \
-    if (fp64)                                                                                     \
-        k_moments<SC, WE, double><<<grid, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count,       \
-            t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.corig,    \
-            nu_vec, nu_s, out, t.mom_x, t.dmom, t.arrive);                                         \
-    else                                                                                          \
-        k_moments<SC, WE, float><<<grid, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count,        \
-            t.node_parent, t.node_nchild, t.node_child0, t.node_cell, t.self.pos, t.self.corig,    \
-            nu_vec, nu_s, out, t.mom_x, (float*)nullptr, t.arrive);
+    const int grid_s = ceil_div(t.nnodes, kTB), grid_m = ceil_div((int64_t)t.nmom_mid * 32, kTB);
+#define WNNC_MOM_SUMS(SC, WE)                                                                            \
+    do {                                                                                                 \
+        k_mom_small<SC, WE><<<grid_s, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count, t.node_cell,    \
+                                                   t.node_cent, t.self.pos, t.self.corig, nu_vec, nu_s,  \
+                                                   out, t.mom_x, t.node_rep);                            \
+        WNNC_LAUNCH_CHECK();                                                                             \
+        if (t.nmom_mid > 0) {                                                                            \
+            k_mom_direct<SC, WE><<<grid_m, kTB, 0, s>>>(t.nmom_mid, t.mom_mid, t.node_start,             \
+                                                        t.node_count, t.node_cell, t.node_cent,          \
+                                                        t.self.pos, t.self.corig, nu_vec, nu_s, out,     \
+                                                        t.mom_x, t.node_rep);                            \
+            WNNC_LAUNCH_CHECK();                                                                         \
+        }                                                                                                \
+    } while (0)
     if (nu_s) {
-        if (w) { WNNC_MOM(true, true) } else { WNNC_MOM(true, false) }
+        if (w) WNNC_MOM_SUMS(true, true); else WNNC_MOM_SUMS(true, false);
     } else {
-        if (w) { WNNC_MOM(false, true) } else { WNNC_MOM(false, false) }
+        if (w) WNNC_MOM_SUMS(false, true); else WNNC_MOM_SUMS(false, false);
     }
-#undef WNNC_MOM
-    WNNC_LAUNCH_CHECK();
-    if (w) {
-        k_weighted_reps<<<grid, kTB, 0, s>>>(t.nnodes, out, t.mom_x, t.node_cent, t.node_rep);
+#undef WNNC_MOM_SUMS
+    if (t.mom_top_levels > 0) {
+        LevelOffsets lv{};
+        for (int L = 0; L <= t.mom_top_levels && L <= t.nlevels && L < 17; ++L) lv.off[L] = t.level_off[L];
+        if (w)
+            k_mom_top<true><<<1, 1024, 0, s>>>(t.mom_top_levels, lv, t.node_count, t.node_nchild,
+                                               t.node_child0, t.node_cell, t.node_cent, out, t.mom_x,
+                                               t.node_rep);
+        else
+            k_mom_top<false><<<1, 1024, 0, s>>>(t.mom_top_levels, lv, t.node_count, t.node_nchild,
+                                                t.node_child0, t.node_cell, t.node_cent, out, t.mom_x,
+                                                t.node_rep);
         WNNC_LAUNCH_CHECK();
     }
 }

@@ -1036,9 +1036,24 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     WNNC_CUDA(cudaStreamSynchronize(s));
     pool_free(sum);
     {
-        std::vector<int> nc(t.nnodes);
+        std::vector<int> nc(t.nnodes), cnt(t.nnodes);
         WNNC_CUDA(cudaMemcpy(nc.data(), t.node_nchild, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
+        WNNC_CUDA(cudaMemcpy(cnt.data(), t.node_count, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
         t.nleaves = (int)std::count(nc.begin(), nc.end(), 0);
+        // the classes of the moment sums: levels holding nodes too large for
+        // the direct sums, and the list of nodes summed by one warp each
+        t.mom_top_levels = 0;
+        std::vector<int> mid;
+        for (int L = 0; L < t.nlevels; ++L)
+            for (int b = t.level_off[L]; b < t.level_off[L + 1]; ++b) {
+                if (cnt[b] > kMomDirect) t.mom_top_levels = L + 1;
+                else if (cnt[b] > kMomSmall) mid.push_back(b);
+            }
+        t.nmom_mid = (int)mid.size();
+        t.mom_mid = dalloc<int>(mid.size());
+        if (!mid.empty())
+            WNNC_CUDA(cudaMemcpyAsync(t.mom_mid, mid.data(), sizeof(int) * mid.size(), cudaMemcpyHostToDevice, s));
+        WNNC_CUDA(cudaStreamSynchronize(s));
     }
 
     // --- the points as targets: same Morton order as the sources ---
@@ -1124,7 +1139,7 @@ void free_tree(Tree& t) {
     free_work(t.adj_far_work);
     free_work(t.adj_near_work);
     dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
-    dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode); dfree(t.arrive);
+    dfree(t.mom_r); dfree(t.mom_x); dfree(t.mom_mid); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
 
