@@ -60,12 +60,31 @@ __global__ void k_bbox_partial(const float* pts, int64_t n, double* part) {
 }
 
 // centre (3) and scale: centre of the bounding box, largest half-extent -> 10/11
-__global__ void k_bbox_final(const double* part, int nparts, double* cs) {
+// One block: thread b takes partial b, then a tree reduction (min and max are
+// exact, so the result does not depend on the order).
+__global__ void __launch_bounds__(1024) k_bbox_final(const double* part, int nparts, double* cs) {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nparts; ++b)
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
         for (int k = 0; k < 3; ++k) {
             lo[k] = fmin(lo[k], part[6 * b + k]);
             hi[k] = fmax(hi[k], part[6 * b + 3 + k]);
+        }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    __shared__ double sh[2][3][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) { sh[0][k][warp] = lo[k]; sh[1][k][warp] = hi[k]; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], sh[0][k][w]);
+            hi[k] = fmax(hi[k], sh[1][k][w]);
         }
     double hmax = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -383,18 +402,41 @@ __device__ __forceinline__ bool is_far(const double* nlo, const double* nhi, con
 constexpr int kTravWarps = 2;
 constexpr int kStack = 4096;
 
-// Warp-cooperative traversal of the octree for one target group.  Pass 0
-// counts far nodes and near leaves; pass 1 writes keys (group<<32 | node) for
-// far entries and (group<<32 | first point) for near leaves, unsorted within
-// the group.  Up to 32 nodes are tested at once; children of opened nodes are
-// pushed on a per-warp shared stack whose capacity is checked before a push.
+// Warp-cooperative traversal of the octree for one target group, one pass:
+// it writes keys (group<<32 | node) for far entries and (group<<32 | first
+// point) with the leaf id for near leaves, in no particular order (they are
+// sorted afterwards).  Up to 32 nodes are tested at once; children of opened
+// nodes are pushed on a per-warp shared stack whose capacity is checked
+// before a push.  Keys collect in per-warp shared buffers that are flushed to
+// global pools, one atomic reservation per flush; past a pool's capacity
+// nothing is written but the pool's counter still counts, so that the caller
+// can size the pools exactly and run the traversal again.
+constexpr int kTravBuf = 128;
+
+__device__ __forceinline__ void trav_flush(const uint64_t* buf, const uint32_t* vbuf, int cnt, uint64_t* pool,
+                                           uint32_t* vpool, int64_t cap, unsigned long long* counter,
+                                           int lane) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)(base + cnt) <= cap)
+        for (int k = lane; k < cnt; k += 32) {
+            pool[base + k] = buf[k];
+            if (vbuf) vpool[base + k] = vbuf[k];
+        }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(32 * kTravWarps)
 k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* nchild,
            const int* child0, const int* nstart, const double* glo, const double* ghi, int ng,
-           double theta, int pass, int* far_cnt, int* near_cnt, const int* far_off,
-           const int* near_off, uint64_t* far_keys, uint64_t* near_keys, uint32_t* near_vals,
+           double theta, uint64_t* far_pool, int64_t far_cap, unsigned long long* far_count,
+           uint64_t* near_pool, uint32_t* near_vpool, int64_t near_cap, unsigned long long* near_count,
            int* err) {
     __shared__ int stack[kTravWarps][kStack];
+    __shared__ uint64_t fbuf_all[kTravWarps][kTravBuf];
+    __shared__ uint64_t nbuf_all[kTravWarps][kTravBuf];
+    __shared__ uint32_t nvbuf_all[kTravWarps][kTravBuf];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x * kTravWarps + wl;
     if (g >= ng) return;
@@ -404,10 +446,12 @@ k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* n
     for (int k = 0; k < 3; ++k) { bl[k] = glo[3 * g + k]; bh[k] = ghi[3 * g + k]; }
     const double c = 1.0 / theta;
     int* st = stack[wl];
+    uint64_t* fbuf = fbuf_all[wl];
+    uint64_t* nbuf = nbuf_all[wl];
+    uint32_t* nvbuf = nvbuf_all[wl];
     if (lane == 0) st[0] = 0;
     __syncwarp();
-    int top = 1, nfar = 0, nnear = 0;
-    const int fo = pass ? far_off[g] : 0, no = pass ? near_off[g] : 0;
+    int top = 1, fcnt = 0, ncnt = 0;
     while (top > 0) {
         int take = min(top, 32);
         int b = lane < take ? st[top - take + lane] : -1;
@@ -421,16 +465,22 @@ k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* n
             }
         }
         unsigned fm = __ballot_sync(0xffffffffu, far), lm = __ballot_sync(0xffffffffu, leaf);
-        if (pass) {
-            if (far) far_keys[fo + nfar + __popc(fm & lt)] = ((uint64_t)g << 32) | (uint32_t)b;
-            if (leaf) {
-                int p = no + nnear + __popc(lm & lt);
-                near_keys[p] = ((uint64_t)g << 32) | (uint32_t)nstart[b];
-                near_vals[p] = (uint32_t)b;
-            }
+        if (fcnt + 32 > kTravBuf) {
+            trav_flush(fbuf, nullptr, fcnt, far_pool, nullptr, far_cap, far_count, lane);
+            fcnt = 0;
         }
-        nfar += __popc(fm);
-        nnear += __popc(lm);
+        if (ncnt + 32 > kTravBuf) {
+            trav_flush(nbuf, nvbuf, ncnt, near_pool, near_vpool, near_cap, near_count, lane);
+            ncnt = 0;
+        }
+        if (far) fbuf[fcnt + __popc(fm & lt)] = ((uint64_t)g << 32) | (uint32_t)b;
+        if (leaf) {
+            int p = ncnt + __popc(lm & lt);
+            nbuf[p] = ((uint64_t)g << 32) | (uint32_t)nstart[b];
+            nvbuf[p] = (uint32_t)b;
+        }
+        fcnt += __popc(fm);
+        ncnt += __popc(lm);
         int nc = open ? nchild[b] : 0;
         int inc = nc;
 #pragma unroll
@@ -450,10 +500,9 @@ k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* n
         top += total;
         __syncwarp();
     }
-    if (!pass && lane == 0) {
-        far_cnt[g] = nfar;
-        near_cnt[g] = nnear;
-    }
+    __syncwarp();
+    if (fcnt) trav_flush(fbuf, nullptr, fcnt, far_pool, nullptr, far_cap, far_count, lane);
+    if (ncnt) trav_flush(nbuf, nvbuf, ncnt, near_pool, near_vpool, near_cap, near_count, lane);
 }
 
 
@@ -829,36 +878,54 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         k_all_near<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(ng, (int)t.n, near_off0, rng0);
         WNNC_LAUNCH_CHECK();
     } else {
-        int* far_cnt = dalloc<int>(ng + 1);
-        int* near_cnt = dalloc<int>(ng + 1);
         int* leaf_off = dalloc<int>(ng + 1);
         int* err = dalloc<int>(1);
-        WNNC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        unsigned long long* counts = dalloc<unsigned long long>(2);
         const int tgrid = ceil_div(ng, kTravWarps);
-        k_traverse<<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_depth, t.node_nchild,
-                                                    t.node_child0, t.node_start, ts.glo, ts.ghi, ng, theta, 0,
-                                                    far_cnt, near_cnt, nullptr, nullptr, nullptr, nullptr,
-                                                    nullptr, err);
-        WNNC_LAUNCH_CHECK();
-        if (read_int(err, s)) {
-            pool_free(far_cnt); pool_free(near_cnt); pool_free(leaf_off); pool_free(err); pool_free(near_off0);
-            fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
+        // pool estimates (per target); a second pass runs with exact sizes if exceeded
+        int64_t far_cap = 48 * m + 4096, near_cap = 8 * m + 4096;
+        uint64_t* fkeys = nullptr;
+        uint64_t* nkeys = nullptr;
+        uint32_t* nvals = nullptr;
+        int64_t nfar = 0, nleafent = 0;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            fkeys = dalloc<uint64_t>(far_cap);
+            nkeys = dalloc<uint64_t>(near_cap);
+            nvals = dalloc<uint32_t>(near_cap);
+            WNNC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+            WNNC_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
+            k_traverse<<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_depth, t.node_nchild,
+                                                        t.node_child0, t.node_start, ts.glo, ts.ghi, ng, theta,
+                                                        fkeys, far_cap, counts, nkeys, nvals, near_cap,
+                                                        counts + 1, err);
+            WNNC_LAUNCH_CHECK();
+            unsigned long long hc[2] = {0, 0};
+            int herr = 0;
+            WNNC_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+            WNNC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            WNNC_CUDA(cudaStreamSynchronize(s));
+            if (herr) {
+                pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(leaf_off); pool_free(err);
+                pool_free(counts); pool_free(near_off0);
+                fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
+            }
+            nfar = (int64_t)hc[0];
+            nleafent = (int64_t)hc[1];
+            if (nfar <= far_cap && nleafent <= near_cap) break;
+            if (attempt == 1 || nfar > INT32_MAX || nleafent > INT32_MAX) {
+                pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(leaf_off); pool_free(err);
+                pool_free(counts); pool_free(near_off0);
+                fail(WNNC_ECAPACITY, "interaction lists too long");
+            }
+            pool_free(fkeys); pool_free(nkeys); pool_free(nvals);
+            far_cap = std::max<int64_t>(nfar, 1);
+            near_cap = std::max<int64_t>(nleafent, 1);
         }
-        exclusive_scan_i32(far_cnt, ts.far_off, ng, s);
-        exclusive_scan_i32(near_cnt, leaf_off, ng, s);
-        int nfar = read_int(ts.far_off + ng, s);
-        int nleafent = read_int(leaf_off + ng, s);
-        uint64_t* fkeys = dalloc<uint64_t>(nfar);
-        uint64_t* nkeys = dalloc<uint64_t>(nleafent);
-        uint32_t* nvals = dalloc<uint32_t>(nleafent);
-        k_traverse<<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_depth, t.node_nchild,
-                                                    t.node_child0, t.node_start, ts.glo, ts.ghi, ng, theta, 1,
-                                                    nullptr, nullptr, ts.far_off, leaf_off, fkeys, nkeys,
-                                                    nvals, err);
-        WNNC_LAUNCH_CHECK();
         int gbits = bits_for(ng);
         radix_sort_pairs(fkeys, nullptr, nfar, 32 + gbits, s);
         radix_sort_pairs(nkeys, nvals, nleafent, 32 + gbits, s);
+        segment_offsets_hi32(fkeys, nfar, ts.far_off, ng, s);
+        segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s);
         ts.far_entries = nfar;
         ts.far_id = dalloc<int>(nfar);
         if (nfar) {
@@ -891,7 +958,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         WNNC_LAUNCH_CHECK();
         WNNC_CUDA(cudaStreamSynchronize(s));
         pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(head); pool_free(hscan);
-        pool_free(far_cnt); pool_free(near_cnt); pool_free(leaf_off); pool_free(err);
+        pool_free(leaf_off); pool_free(err); pool_free(counts);
     }
     // cut ranges to at most kMaxRange points
     {
@@ -956,7 +1023,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     double* cs = dalloc<double>(4);
     k_bbox_partial<<<nparts, kTB, 0, s>>>(pts, n, part);
     WNNC_LAUNCH_CHECK();
-    k_bbox_final<<<1, 1, 0, s>>>(part, nparts, cs);
+    k_bbox_final<<<1, 1024, 0, s>>>(part, nparts, cs);
     WNNC_LAUNCH_CHECK();
     double hcs[4];
     WNNC_CUDA(cudaMemcpyAsync(hcs, cs, sizeof(hcs), cudaMemcpyDeviceToHost, s));
