@@ -54,7 +54,7 @@ FLOPS_ITER = 2 * FLOPS_A + FLOPS_AT + FLOPS_G      # A(mu), A(r), A^T(s), G(mu) 
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
 # DRAM bytes (read + write) of one launch of the G kernel on union500k, from ncu
 # (profiles/union500k_treecode_kernels.md); None once the kernel has changed.
-G_TRAFFIC_BYTES = 109.978368e6 + 6.256128e6
+G_TRAFFIC_BYTES = 109.79456e6 + 6.637056e6
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:

@@ -73,9 +73,9 @@ typedef struct {
                           tree operator linear so that A^T is its exact transpose (default);
                           0 = |nu|-weighted centroid as in the paper (A^T is then the paper's
                           s-representative treecode, not an exact transpose) */
-    int moments_fp64;  /* node moments are always summed in double precision (prefix sums);
-                          1 = also sum the moments of every G step directly instead of
-                          deriving them from those of mu and r by linearity (default 0) */
+    int moments_fp64;  /* 1 = sum node moments in double precision, and sum the moments of
+                          every G step directly instead of deriving them from those of mu
+                          and r by linearity (default 0: single precision) */
 } wnnc_tree_params;
 
 /* Iteration parameters (Alg. 3; Sec. 5.1.1 defaults n = 40, w1 = 0.002, w2 = 0.016). */

@@ -80,6 +80,7 @@ static void alloc_workspace(Tree& t) {
     t.contrib = dalloc<float4>(t.self.far_entries);
     t.vnode = dalloc<float4>(nn);
     t.mom_x = dalloc<float4>(nn);
+    if (t.params.moments_fp64) t.dmom = dalloc<double>(8 * (size_t)nn);
     t.partials = dalloc<double>(3 * (size_t)std::max(std::max(t.self.ngroups, t.self.nchunks), t.nach));
     t.red = dalloc<double>(3 * 256);
     t.part_slots = std::max(t.self.work.nslots, t.adj_near_work.nslots);

@@ -240,6 +240,7 @@ struct Tree {
     float4* contrib = nullptr;    // per far entry contribution (adjoint)
     float4* vnode = nullptr;      // per node far sum (adjoint)
     float4* mom_x = nullptr;      // node weighted offsets (rep_mode 0): sum |nu| (x - cell), -
+    double* dmom = nullptr;       // double node sums (moments_fp64), 8 per node
     double* partials = nullptr;   // per-group partial sums (3 x max(ngroups, nchunks, nach))
     double* red = nullptr;        // first-stage sums of the partials (3 x 256)
     float4* part_acc = nullptr;   // scratch: partial sums of cut groups, 32 per slot

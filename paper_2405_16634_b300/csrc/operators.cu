@@ -60,11 +60,12 @@ constexpr int kUnroll = WNNC_UNROLL;
 //   momx[b] = sum |nu| (x - cell_b)     (only for the |nu|-weighted representative)
 //   rep[b]  = momx[b] / sum |nu|, or the point centroid when sum |nu| = 0
 // ---------------------------------------------------------------------------
+// Sums run in Acc = float, or double with moments_fp64 (the double sums of
+// every node are then kept in dmom, 8 per node, for the top levels).
 // Point term of the moments: nu (3 or 1 components), |nu|, |nu| (x - cell).
-template <bool SCALAR, bool WEIGHTED>
+template <bool SCALAR, bool WEIGHTED, class Acc>
 __device__ __forceinline__ void mom_point(int j, const float4& cb, const float4* spos, const float4* scorig,
-                                          const float4* nu_vec, const float* nu_s, float& m0, float& m1,
-                                          float& m2, float& ws, float& x0, float& x1, float& x2) {
+                                          const float4* nu_vec, const float* nu_s, Acc (&m)[7]) {
     float v0, v1 = 0.f, v2 = 0.f, a;
     if (SCALAR) {
         v0 = nu_s[j];
@@ -74,46 +75,49 @@ __device__ __forceinline__ void mom_point(int j, const float4& cb, const float4*
         v0 = v.x; v1 = v.y; v2 = v.z;
         a = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
     }
-    m0 += v0; m1 += v1; m2 += v2; ws += a;
+    m[0] += v0; m[1] += v1; m[2] += v2; m[3] += a;
     if (WEIGHTED) {
         const float4 p = spos[j], go = scorig[j >> 5];   // the point in its chunk frame
-        x0 = fmaf(a, (go.x - cb.x) + p.x, x0);
-        x1 = fmaf(a, (go.y - cb.y) + p.y, x1);
-        x2 = fmaf(a, (go.z - cb.z) + p.z, x2);
+        m[4] += (Acc)a * (Acc)((go.x - cb.x) + p.x);
+        m[5] += (Acc)a * (Acc)((go.y - cb.y) + p.y);
+        m[6] += (Acc)a * (Acc)((go.z - cb.z) + p.z);
     }
 }
 
-template <bool WEIGHTED>
+template <bool WEIGHTED, class Acc>
 __device__ __forceinline__ void mom_store(int b, const float4* ncent, float4* mom, float4* momx, float4* rep,
-                                          float m0, float m1, float m2, float ws, float x0, float x1, float x2) {
-    mom[b] = make_float4(m0, m1, m2, ws);
+                                          double* dmom, const Acc (&m)[7]) {
+    mom[b] = make_float4((float)m[0], (float)m[1], (float)m[2], (float)m[3]);
     if (WEIGHTED) {
-        momx[b] = make_float4(x0, x1, x2, 0.f);
-        rep[b] = ws > 0.f ? make_float4(x0 / ws, x1 / ws, x2 / ws, 0.f) : ncent[b];
+        momx[b] = make_float4((float)m[4], (float)m[5], (float)m[6], 0.f);
+        rep[b] = m[3] > 0 ? make_float4((float)(m[4] / m[3]), (float)(m[5] / m[3]), (float)(m[6] / m[3]), 0.f)
+                          : ncent[b];
     }
+    if (dmom)
+        for (int k = 0; k < 7; ++k) dmom[8 * (int64_t)b + k] = (double)m[k];
 }
 
-template <bool SCALAR, bool WEIGHTED>
+template <bool SCALAR, bool WEIGHTED, class Acc>
 __global__ void k_mom_small(int nnodes, const int* nstart, const int* ncount, const float4* ncell,
                             const float4* ncent, const float4* spos, const float4* scorig, const float4* nu_vec,
-                            const float* nu_s, float4* mom, float4* momx, float4* rep) {
+                            const float* nu_s, float4* mom, float4* momx, float4* rep, double* dmom) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnodes) return;
     const int cnt = ncount[b];
     if (cnt > kMomSmall) return;
     const int j0 = nstart[b];
     const float4 cb = ncell[b];
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f, ws = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    Acc m[7] = {0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 4
-    for (int j = j0; j < j0 + cnt; ++j)
-        mom_point<SCALAR, WEIGHTED>(j, cb, spos, scorig, nu_vec, nu_s, m0, m1, m2, ws, x0, x1, x2);
-    mom_store<WEIGHTED>(b, ncent, mom, momx, rep, m0, m1, m2, ws, x0, x1, x2);
+    for (int j = j0; j < j0 + cnt; ++j) mom_point<SCALAR, WEIGHTED, Acc>(j, cb, spos, scorig, nu_vec, nu_s, m);
+    mom_store<WEIGHTED, Acc>(b, ncent, mom, momx, rep, dmom, m);
 }
 
-template <bool SCALAR, bool WEIGHTED>
+template <bool SCALAR, bool WEIGHTED, class Acc>
 __global__ void k_mom_direct(int nmid, const int* mid, const int* nstart, const int* ncount, const float4* ncell,
                              const float4* ncent, const float4* spos, const float4* scorig,
-                             const float4* nu_vec, const float* nu_s, float4* mom, float4* momx, float4* rep) {
+                             const float4* nu_vec, const float* nu_s, float4* mom, float4* momx, float4* rep,
+                             double* dmom) {
     const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (k >= nmid) return;
@@ -121,51 +125,58 @@ __global__ void k_mom_direct(int nmid, const int* mid, const int* nstart, const 
     const int cnt = ncount[b];
     const int j0 = nstart[b];
     const float4 cb = ncell[b];
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f, ws = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    Acc m[7] = {0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 4
     for (int j = j0 + lane; j < j0 + cnt; j += 32)
-        mom_point<SCALAR, WEIGHTED>(j, cb, spos, scorig, nu_vec, nu_s, m0, m1, m2, ws, x0, x1, x2);
+        mom_point<SCALAR, WEIGHTED, Acc>(j, cb, spos, scorig, nu_vec, nu_s, m);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        m0 += __shfl_xor_sync(0xffffffffu, m0, o);
-        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-        m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-        ws += __shfl_xor_sync(0xffffffffu, ws, o);
-        if (WEIGHTED) {
-            x0 += __shfl_xor_sync(0xffffffffu, x0, o);
-            x1 += __shfl_xor_sync(0xffffffffu, x1, o);
-            x2 += __shfl_xor_sync(0xffffffffu, x2, o);
-        }
+    for (int c = 0; c < 7; ++c) {
+        if (!WEIGHTED && c >= 4) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m[c] += __shfl_xor_sync(0xffffffffu, m[c], o);
     }
-    if (lane == 0) mom_store<WEIGHTED>(b, ncent, mom, momx, rep, m0, m1, m2, ws, x0, x1, x2);
+    if (lane == 0) mom_store<WEIGHTED, Acc>(b, ncent, mom, momx, rep, dmom, m);
 }
 
 struct LevelOffsets {
     int off[17];   // first node of levels 0..15, and the end of the last
 };
 
-template <bool WEIGHTED>
+template <bool WEIGHTED, class Acc>
 __global__ void __launch_bounds__(1024) k_mom_top(int nlev, LevelOffsets lv, const int* ncount,
                                                   const int* nchild, const int* nchild0, const float4* ncell,
-                                                  const float4* ncent, float4* mom, float4* momx, float4* rep) {
+                                                  const float4* ncent, float4* mom, float4* momx, float4* rep,
+                                                  double* dmom) {
     for (int d = nlev - 1; d >= 0; --d) {
         for (int b = lv.off[d] + threadIdx.x; b < lv.off[d + 1]; b += blockDim.x) {
             if (ncount[b] <= kMomDirect) continue;
             const float4 cp = ncell[b];
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f, ws = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f;
+            Acc m[7] = {0, 0, 0, 0, 0, 0, 0};
             for (int q = 0; q < nchild[b]; ++q) {
                 const int c = nchild0[b] + q;
-                const float4 mm = mom[c];
-                m0 += mm.x; m1 += mm.y; m2 += mm.z; ws += mm.w;
+                Acc cm[7];
+                if (dmom) {
+                    for (int k = 0; k < 7; ++k) cm[k] = (Acc)dmom[8 * (int64_t)c + k];
+                } else {
+                    const float4 mm = mom[c];
+                    cm[0] = mm.x; cm[1] = mm.y; cm[2] = mm.z; cm[3] = mm.w;
+                    if (WEIGHTED) {
+                        const float4 xx = momx[c];
+                        cm[4] = xx.x; cm[5] = xx.y; cm[6] = xx.z;
+                    } else {
+                        cm[4] = cm[5] = cm[6] = 0;
+                    }
+                }
+                for (int k = 0; k < 4; ++k) m[k] += cm[k];
                 if (WEIGHTED) {
                     // re-centre the child's weighted offsets on this node's cell
-                    const float4 xx = momx[c], cc = ncell[c];
-                    x0 += xx.x + mm.w * (cc.x - cp.x);
-                    x1 += xx.y + mm.w * (cc.y - cp.y);
-                    x2 += xx.z + mm.w * (cc.z - cp.z);
+                    const float4 cc = ncell[c];
+                    m[4] += cm[4] + cm[3] * (Acc)(cc.x - cp.x);
+                    m[5] += cm[5] + cm[3] * (Acc)(cc.y - cp.y);
+                    m[6] += cm[6] + cm[3] * (Acc)(cc.z - cp.z);
                 }
             }
-            mom_store<WEIGHTED>(b, ncent, mom, momx, rep, m0, m1, m2, ws, x0, x1, x2);
+            mom_store<WEIGHTED, Acc>(b, ncent, mom, momx, rep, dmom, m);
         }
         __syncthreads();
     }
@@ -919,39 +930,41 @@ void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, flo
     ProfScope ps(&t.prof, WNNC_PROF_MOMENTS, s);
     const bool w = rep_mode == 0;
     const int grid_s = ceil_div(t.nnodes, kTB), grid_m = ceil_div((int64_t)t.nmom_mid * 32, kTB);
-#define WNNC_MOM_SUMS(SC, WE)                                                                            \
-    do {                                                                                                 \
-        k_mom_small<SC, WE><<<grid_s, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count, t.node_cell,    \
-                                                   t.node_cent, t.self.pos, t.self.corig, nu_vec, nu_s,  \
-                                                   out, t.mom_x, t.node_rep);                            \
-        WNNC_LAUNCH_CHECK();                                                                             \
-        if (t.nmom_mid > 0) {                                                                            \
-            k_mom_direct<SC, WE><<<grid_m, kTB, 0, s>>>(t.nmom_mid, t.mom_mid, t.node_start,             \
-                                                        t.node_count, t.node_cell, t.node_cent,          \
-                                                        t.self.pos, t.self.corig, nu_vec, nu_s, out,     \
-                                                        t.mom_x, t.node_rep);                            \
-            WNNC_LAUNCH_CHECK();                                                                         \
-        }                                                                                                \
+    const bool fp64 = t.params.moments_fp64 != 0;
+    LevelOffsets lv{};
+    for (int L = 0; L <= t.mom_top_levels && L <= t.nlevels && L < 17; ++L) lv.off[L] = t.level_off[L];
+#define WNNC_MOM_SUMS(SC, WE, ACC, DM)                                                                    \
+    do {                                                                                                  \
+        k_mom_small<SC, WE, ACC><<<grid_s, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count, t.node_cell, \
+                                                        t.node_cent, t.self.pos, t.self.corig, nu_vec,    \
+                                                        nu_s, out, t.mom_x, t.node_rep, DM);              \
+        WNNC_LAUNCH_CHECK();                                                                              \
+        if (t.nmom_mid > 0) {                                                                             \
+            k_mom_direct<SC, WE, ACC><<<grid_m, kTB, 0, s>>>(t.nmom_mid, t.mom_mid, t.node_start,         \
+                                                             t.node_count, t.node_cell, t.node_cent,      \
+                                                             t.self.pos, t.self.corig, nu_vec, nu_s, out, \
+                                                             t.mom_x, t.node_rep, DM);                    \
+            WNNC_LAUNCH_CHECK();                                                                          \
+        }                                                                                                 \
+        if (t.mom_top_levels > 0) {                                                                       \
+            k_mom_top<WE, ACC><<<1, 1024, 0, s>>>(t.mom_top_levels, lv, t.node_count, t.node_nchild,      \
+                                                  t.node_child0, t.node_cell, t.node_cent, out, t.mom_x,  \
+                                                  t.node_rep, DM);                                        \
+            WNNC_LAUNCH_CHECK();                                                                          \
+        }                                                                                                 \
+    } while (0)
+#define WNNC_MOM_PREC(SC, WE)                                      \
+    do {                                                           \
+        if (fp64) WNNC_MOM_SUMS(SC, WE, double, t.dmom);           \
+        else WNNC_MOM_SUMS(SC, WE, float, (double*)nullptr);       \
     } while (0)
     if (nu_s) {
-        if (w) WNNC_MOM_SUMS(true, true); else WNNC_MOM_SUMS(true, false);
+        if (w) WNNC_MOM_PREC(true, true); else WNNC_MOM_PREC(true, false);
     } else {
-        if (w) WNNC_MOM_SUMS(false, true); else WNNC_MOM_SUMS(false, false);
+        if (w) WNNC_MOM_PREC(false, true); else WNNC_MOM_PREC(false, false);
     }
+#undef WNNC_MOM_PREC
 #undef WNNC_MOM_SUMS
-    if (t.mom_top_levels > 0) {
-        LevelOffsets lv{};
-        for (int L = 0; L <= t.mom_top_levels && L <= t.nlevels && L < 17; ++L) lv.off[L] = t.level_off[L];
-        if (w)
-            k_mom_top<true><<<1, 1024, 0, s>>>(t.mom_top_levels, lv, t.node_count, t.node_nchild,
-                                               t.node_child0, t.node_cell, t.node_cent, out, t.mom_x,
-                                               t.node_rep);
-        else
-            k_mom_top<false><<<1, 1024, 0, s>>>(t.mom_top_levels, lv, t.node_count, t.node_nchild,
-                                                t.node_child0, t.node_cell, t.node_cent, out, t.mom_x,
-                                                t.node_rep);
-        WNNC_LAUNCH_CHECK();
-    }
 }
 
 static void perm_in_vec(Tree& t, const float* in, float f, float4* out, cudaStream_t s) {
