@@ -6,12 +6,15 @@ on the normals the method itself produces after its full 40 iterations on
 seeded synthetic clouds.  At solve time:
 
 1. build the tree, compute the patch features (``knn16``) and run the network;
-2. run iteration 1 of the schedule from zero: the paper observes that the
-   first iteration already orients the surface globally, and it gives the
-   per-point lengths (areas);
+2. run the first s iterations of the schedule from zero: the paper reports
+   an overall correct orientation within the method's first few iterations
+   (Sec. 5.3); this field gives the sign and the per-point lengths (areas);
 3. start from the network's direction, with the sign and length of that
-   first-iteration field (``warm_init``);
+   field (``warm_init``);
 4. run only the last k iterations of the width schedule.
+
+The network is trained with the sign-free loss 1 - c^2 by default: a local
+patch cannot tell inside from outside.
 
 The plain 40-iteration solve stays the reference for accuracy.  Every numerical
 step runs in the library's kernels; this module only drives them (batch
