@@ -211,6 +211,8 @@ struct Tree {
     int* mom_mid = nullptr;       // their ids
     double* node_lo = nullptr;    // tight bounding boxes (build)
     double* node_hi = nullptr;
+    float4* node_lof = nullptr;   // the same boxes rounded outward to float (traversal pre-test)
+    float4* node_hif = nullptr;
     float4* node_cell = nullptr;  // cell centre (exact) + width
     float4* node_cent = nullptr;  // point centroid - cell centre
     int* leaf_of = nullptr;       // sorted point -> leaf node

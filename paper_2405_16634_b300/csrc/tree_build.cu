@@ -382,6 +382,38 @@ __global__ void k_group_boxes(const double* ys, const int* goff, int ng, double*
     }
 }
 
+// Float copies of the node boxes, rounded outward.
+__global__ void k_node_fbox(const double* lo, const double* hi, int nn, float4* lof, float4* hif) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nn) return;
+    lof[b] = make_float4(__double2float_rd(lo[3 * b]), __double2float_rd(lo[3 * b + 1]),
+                         __double2float_rd(lo[3 * b + 2]), 0.f);
+    hif[b] = make_float4(__double2float_ru(hi[3 * b]), __double2float_ru(hi[3 * b + 1]),
+                         __double2float_ru(hi[3 * b + 2]), 0.f);
+}
+
+// FP32 pre-test of the far criterion on outward-rounded boxes: 1 = far, 0 = not
+// far, -1 = undecided.  Node coordinates lie in [-1, 1] and the group's within
+// [-S, S] (S > 1 only for query points outside the cloud), so each outward
+// rounding moves a face by less than 1.2e-7 S and each float subtraction
+// rounds by at most 1.2e-7 (1 + S): the float gap per axis is within
+// 4.8e-7 (1 + S) of the exact one, the distance within 8.4e-7 (1 + S) (plus a
+// relative 1e-7 from the float sum of squares).  With a margin of
+// 1e-6 (1 + S) + 1e-6 cw a decision here is the one the exact FP64 test would
+// take; the rest goes to that test.
+__device__ __forceinline__ int far_pretest(const float4& nl, const float4& nh, const float4& gl,
+                                           const float4& gh, float cwf, float mscale) {
+    const float ax = fmaxf(fmaxf(nl.x - gh.x, gl.x - nh.x), 0.f);
+    const float ay = fmaxf(fmaxf(nl.y - gh.y, gl.y - nh.y), 0.f);
+    const float az = fmaxf(fmaxf(nl.z - gh.z, gl.z - nh.z), 0.f);
+    const float d2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+    const float m = mscale + 1e-6f * cwf;
+    const float up = cwf + m, dn = cwf - m;
+    if (d2 > up * up) return 1;
+    if (dn > 0.f && d2 < dn * dn) return 0;
+    return -1;
+}
+
 // Far test of a group box against node b (see the file comment).
 __device__ __forceinline__ bool is_far(const double* nlo, const double* nhi, const int* ndepth,
                                        int b, const double* glo, const double* ghi, double c) {
@@ -428,8 +460,8 @@ __device__ __forceinline__ void trav_flush(const uint64_t* buf, const uint32_t* 
 }
 
 __global__ void __launch_bounds__(32 * kTravWarps)
-k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* nchild,
-           const int* child0, const int* nstart, const double* glo, const double* ghi, int ng,
+k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float4* nhif, const int* ndepth,
+           const int* nchild, const int* child0, const int* nstart, const double* glo, const double* ghi, int ng,
            double theta, uint64_t* far_pool, int64_t far_cap, unsigned long long* far_count,
            uint64_t* near_pool, uint32_t* near_vpool, int64_t near_cap, unsigned long long* near_count,
            int* err) {
@@ -445,6 +477,12 @@ k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* n
 #pragma unroll
     for (int k = 0; k < 3; ++k) { bl[k] = glo[3 * g + k]; bh[k] = ghi[3 * g + k]; }
     const double c = 1.0 / theta;
+    const float cf = (float)c;
+    const float4 gl = make_float4(__double2float_rd(bl[0]), __double2float_rd(bl[1]), __double2float_rd(bl[2]), 0.f);
+    const float4 gh = make_float4(__double2float_ru(bh[0]), __double2float_ru(bh[1]), __double2float_ru(bh[2]), 0.f);
+    const float gs = fmaxf(fmaxf(fmaxf(fabsf(gl.x), fabsf(gl.y)), fmaxf(fabsf(gl.z), fabsf(gh.x))),
+                           fmaxf(fabsf(gh.y), fabsf(gh.z)));
+    const float mscale = 1e-6f * (1.f + fmaxf(gs, 1.f));
     int* st = stack[wl];
     uint64_t* fbuf = fbuf_all[wl];
     uint64_t* nbuf = nbuf_all[wl];
@@ -459,7 +497,8 @@ k_traverse(const double* nlo, const double* nhi, const int* ndepth, const int* n
         __syncwarp();
         bool far = false, leaf = false, open = false;
         if (b >= 0) {
-            far = is_far(nlo, nhi, ndepth, b, bl, bh, c);
+            const int q = far_pretest(nlof[b], nhif[b], gl, gh, cf * ldexpf(2.f, -ndepth[b]), mscale);
+            far = q < 0 ? is_far(nlo, nhi, ndepth, b, bl, bh, c) : q == 1;
             if (!far) {
                 if (nchild[b] == 0) leaf = true; else open = true;
             }
@@ -596,20 +635,25 @@ __global__ void k_tnear_count(const int2* rng, int64_t nr, int* cnt) {
     cnt[q] = r.y > r.x ? (r.y - 1) / kAdjChunk - r.x / kAdjChunk + 1 : 0;
 }
 
-__global__ void k_tnear_fill(const int2* rng, const int* near_off, int ng, const int* cnt_off,
+// One thread per near range; its group is found by binary search in near_off.
+__global__ void k_tnear_fill(const int2* rng, int64_t nr, const int* near_off, int ng, const int* cnt_off,
                              uint64_t* keys, uint32_t* masks) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
-    for (int q = near_off[g]; q < near_off[g + 1]; ++q) {
-        int2 r = rng[q];
-        if (r.y <= r.x) continue;
-        int p = cnt_off[q];
-        for (int sc = r.x / kAdjChunk; sc <= (r.y - 1) / kAdjChunk; ++sc, ++p) {
-            int lo = max(r.x, sc * kAdjChunk) - sc * kAdjChunk, hi = min(r.y, (sc + 1) * kAdjChunk) - sc * kAdjChunk;
-            uint32_t m = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
-            keys[p] = ((uint64_t)(uint32_t)sc << 32) | (uint32_t)g;
-            masks[p] = m;
-        }
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nr) return;
+    int lo_g = 0, hi_g = ng - 1;   // the last group g with near_off[g] <= q
+    while (lo_g < hi_g) {
+        const int mid = (lo_g + hi_g + 1) >> 1;
+        if (near_off[mid] <= q) lo_g = mid; else hi_g = mid - 1;
+    }
+    const int g = lo_g;
+    const int2 r = rng[q];
+    if (r.y <= r.x) return;
+    int p = cnt_off[q];
+    for (int sc = r.x / kAdjChunk; sc <= (r.y - 1) / kAdjChunk; ++sc, ++p) {
+        int lo = max(r.x, sc * kAdjChunk) - sc * kAdjChunk, hi = min(r.y, (sc + 1) * kAdjChunk) - sc * kAdjChunk;
+        uint32_t m = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+        keys[p] = ((uint64_t)(uint32_t)sc << 32) | (uint32_t)g;
+        masks[p] = m;
     }
 }
 
@@ -894,7 +938,8 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             nvals = dalloc<uint32_t>(near_cap);
             WNNC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
             WNNC_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
-            k_traverse<<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_depth, t.node_nchild,
+            k_traverse<<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_lof, t.node_hif,
+                                                        t.node_depth, t.node_nchild,
                                                         t.node_child0, t.node_start, ts.glo, ts.ghi, ng, theta,
                                                         fkeys, far_cap, counts, nkeys, nvals, near_cap,
                                                         counts + 1, err);
@@ -1093,6 +1138,10 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
                                                       t.node_nchild, b0, mm, t.node_lo, t.node_hi, sum);
         WNNC_LAUNCH_CHECK();
     }
+    t.node_lof = dalloc<float4>(t.nnodes);
+    t.node_hif = dalloc<float4>(t.nnodes);
+    k_node_fbox<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.node_lo, t.node_hi, t.nnodes, t.node_lof, t.node_hif);
+    WNNC_LAUNCH_CHECK();
     t.node_cell = dalloc<float4>(t.nnodes);
     t.node_cent = dalloc<float4>(t.nnodes);
     t.leaf_of = dalloc<int>(n);
@@ -1166,8 +1215,10 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         int ne = read_int(coff + nr, s);
         uint64_t* k = dalloc<uint64_t>(ne);
         uint32_t* msk = dalloc<uint32_t>(ne);
-        k_tnear_fill<<<ceil_div(ng, kTB), kTB, 0, s>>>(S.near_rng, S.near_off, ng, coff, k, msk);
-        WNNC_LAUNCH_CHECK();
+        if (nr) {
+            k_tnear_fill<<<ceil_div(nr, kTB), kTB, 0, s>>>(S.near_rng, nr, S.near_off, ng, coff, k, msk);
+            WNNC_LAUNCH_CHECK();
+        }
         radix_sort_pairs(k, msk, ne, 32 + bits_for(nach), s, 32);   // groups already ascending
         int* head = dalloc<int>(ne + 1);
         int* hscan = dalloc<int>(ne + 2);
@@ -1197,7 +1248,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
 void free_tree(Tree& t) {
     dfree(t.keys); dfree(t.xs);
     dfree(t.node_start); dfree(t.node_count); dfree(t.node_parent); dfree(t.node_child0);
-    dfree(t.node_nchild); dfree(t.node_depth); dfree(t.node_lo); dfree(t.node_hi);
+    dfree(t.node_nchild); dfree(t.node_depth); dfree(t.node_lo); dfree(t.node_hi); dfree(t.node_lof); dfree(t.node_hif);
     dfree(t.node_cell); dfree(t.node_cent); dfree(t.leaf_of);
     delete[] t.level_off;
     t.level_off = nullptr;
