@@ -38,10 +38,10 @@ W1, W2 = 0.002, 0.016
 THETA = 0.5
 WORKLOADS = {
     "union500k": ("union500k: 500,000 points on a union of 6 tori + 6 ellipsoids, 10x density "
-                  "modulation, 1% outliers; theta=0.5 (c=2), leaf_size=12, depth 15; 40 iterations "
+                  "modulation, 1% outliers; theta=0.5 (c=2), leaf_size=8, group slack 3, depth 15; 40 iterations "
                   "w2=0.016 -> w1=0.002"),
     "union50k": ("union50k: 50,000 points on a union of 2 tori + 2 ellipsoids, noise 0.002; "
-                 "theta=0.5, leaf_size=12, depth 15; 40 iterations w2=0.016 -> w1=0.002 "
+                 "theta=0.5, leaf_size=8, group slack 3, depth 15; 40 iterations w2=0.016 -> w1=0.002 "
                  "(small case for profiling)"),
     "union2m": ("union2m: 2,000,000 points on 24 primitives incl. thin tori (r=0.01) and "
                 "near-touching ellipsoid pairs (gap 0.005), noise 0.001; theta=0.5; 40 iterations"),
@@ -54,7 +54,7 @@ FLOPS_ITER = 2 * FLOPS_A + FLOPS_AT + FLOPS_G      # A(mu), A(r), A^T(s), G(mu) 
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
 # DRAM bytes (read + write) of one launch of the G kernel on union500k, from ncu
 # (profiles/union500k_treecode_kernels.md); None once the kernel has changed.
-G_TRAFFIC_BYTES = 109.79456e6 + 6.637056e6
+G_TRAFFIC_BYTES = 106.016e6 + 6.4448e6
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:

@@ -66,7 +66,7 @@ typedef enum {
 typedef struct {
     int max_depth;     /* maximum octree depth D, root = depth 0; 1..15 (default 15) */
     int leaf_size;     /* a node is split while it holds more than this many points
-                          (the paper splits down to 1 point); 1..1024 (default 12, the
+                          (the paper splits down to 1 point); 1..1024 (default 8, the
                           fastest measured on B300 at 50k-2M points) */
     float theta;       /* opening parameter, 1/c of Alg. 4; 0 = exact direct sums (default 0.5) */
     int rep_mode;      /* node representative (Eq. 13): 1 = point centroid, which makes the
@@ -184,7 +184,7 @@ wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, i
  *               (consecutive near leaves merged, then cut to at most 256 points)
  *   group_off   int32 [ngroups+1]  target group g = sorted points group_off[g]..group_off[g+1]-1
  *               (at most 32; a new group starts where consecutive points' leaves share no
- *               ancestor within 2 levels of the deeper leaf)
+ *               ancestor within 3 levels of the deeper leaf)
  *   center_scale float64 [4]     normalisation centre c (3) and scale s
  */
 wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node_start,

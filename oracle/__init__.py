@@ -41,7 +41,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 OP_A, OP_G, OP_AT = 0, 1, 2
 GROUP_SIZE = 32
-GROUP_SLACK = 2     # target groups never straddle leaves without a common ancestor 2 levels up
+GROUP_SLACK = 3     # target groups never straddle leaves without a common ancestor 3 levels up
 
 
 def build(force: bool = False) -> str:
@@ -155,7 +155,7 @@ def direct(op: int, x, nu, w: float, y=None, amb_tol: float = 0.0):
 class Tree:
     """Source octree + on-surface target groups over normalised points xn."""
 
-    def __init__(self, xn, theta: float, leaf_size: int = 12, max_depth: int = 15,
+    def __init__(self, xn, theta: float, leaf_size: int = 8, max_depth: int = 15,
                  group_size: int = GROUP_SIZE, group_slack: int = GROUP_SLACK):
         self.xn = _f64(xn, (-1, 3))
         self.n = self.xn.shape[0]
@@ -238,7 +238,7 @@ def _setup(points, theta, leaf_size, max_depth):
     return xn, c, s, tree
 
 
-def eval_op(op: int, points, nu, w: float, theta: float = 0.0, leaf_size: int = 12,
+def eval_op(op: int, points, nu, w: float, theta: float = 0.0, leaf_size: int = 8,
             max_depth: int = 15, rep_mode: int = 1, amb_tol: float = 0.0):
     """One operator at the input points, caller units in and out.
 
@@ -264,7 +264,7 @@ def eval_op(op: int, points, nu, w: float, theta: float = 0.0, leaf_size: int = 
     return out, bounds
 
 
-def eval_at(op: int, points, mu, queries, w: float, theta: float = 0.0, leaf_size: int = 12,
+def eval_at(op: int, points, mu, queries, w: float, theta: float = 0.0, leaf_size: int = 8,
             max_depth: int = 15, rep_mode: int = 1, with_bounds: bool = False):
     """A (F) or grad F at off-surface query points (caller units); with
     with_bounds also the per-target bounds (amb is zero here: w applies only
@@ -285,7 +285,7 @@ def eval_at(op: int, points, mu, queries, w: float, theta: float = 0.0, leaf_siz
 
 
 def iterate(points, mu0=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0.016,
-            theta: float = 0.0, leaf_size: int = 12, max_depth: int = 15, rep_mode: int = 1,
+            theta: float = 0.0, leaf_size: int = 8, max_depth: int = 15, rep_mode: int = 1,
             first_iter: int = 1, last_iter: int | None = None, rescale: int = 0, area=None,
             use_grad: bool = True, use_wnnc: bool = True):
     """Alg. 3 on the cloud; returns (mu in caller units, stats[iter] = (w, E, alpha, |r|^2))."""

@@ -150,7 +150,7 @@ def default_iter_params() -> IterParams:
 class Tree:
     """Octree, node data and interaction lists of a point cloud on one GPU."""
 
-    def __init__(self, points, theta: float = 0.5, leaf_size: int = 12, max_depth: int = 15,
+    def __init__(self, points, theta: float = 0.5, leaf_size: int = 8, max_depth: int = 15,
                  rep_mode: int = 1, moments_fp64: bool = False):
         pts = points if isinstance(points, torch.Tensor) else torch.as_tensor(points)
         self.device = pts.device if pts.is_cuda else torch.device("cuda", torch.cuda.current_device())

@@ -154,7 +154,7 @@ wnnc_status wnnc_tree_params_default(wnnc_tree_params* p) {
         return WNNC_EINVAL;
     }
     p->max_depth = 15;
-    p->leaf_size = 12;
+    p->leaf_size = 8;
     p->theta = 0.5f;
     p->rep_mode = 1;
     p->moments_fp64 = 0;

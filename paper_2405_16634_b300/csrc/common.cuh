@@ -101,7 +101,7 @@ constexpr int kAdjChunk = 8;        // points per source chunk of the adjoint ne
 constexpr int kMomSmall = 16;       // node moments: nodes of at most this many points, one thread each
 constexpr int kMomDirect = 1024;    //   up to this many points, one warp each; larger ones from children
 #ifndef WNNC_GROUP_SLACK
-#define WNNC_GROUP_SLACK 2
+#define WNNC_GROUP_SLACK 3
 #endif
 constexpr int kGroupSlack = WNNC_GROUP_SLACK;      // group rule: see build_target_set
 
