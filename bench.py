@@ -48,13 +48,14 @@ WORKLOADS = {
 }
 CONFIG_NAME = "union500k"
 WORKLOAD = WORKLOADS[CONFIG_NAME]
-# algorithmic FP32 flops per pair term (FMA = 2, rsqrt = 1; the cut-off select is not counted)
-FLOPS_A, FLOPS_AT, FLOPS_G = 18, 18, 31
-FLOPS_ITER = 2 * FLOPS_A + FLOPS_AT + FLOPS_G      # A(mu), A(r), A^T(s), G(mu) per iteration
+# algorithmic FP32 flops per pair term (FMA = 2, rsqrt = 1; the cut-off select is not counted):
+# A 18, A^T 18, G 31; A and G together 33 (they share d, r^2, rsqrt, r^-3 and d.mu: 16)
+FLOPS_A, FLOPS_AT, FLOPS_G, FLOPS_AG = 18, 18, 31, 33
+FLOPS_ITER = 2 * FLOPS_AG + FLOPS_AT               # A+G(mu), A^T(s), A+G(r) per iteration
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
-# DRAM bytes (read + write) of one launch of the G kernel on union500k, from ncu
+# DRAM bytes (read + write) of one launch of the fused A+G kernel on union500k, from ncu
 # (profiles/union500k_treecode_kernels.md); None once the kernel has changed.
-G_TRAFFIC_BYTES = 106.016e6 + 6.4448e6
+AG_TRAFFIC_BYTES = None
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
@@ -289,9 +290,9 @@ def run_gpu(args):
     max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
     flops_per_s = FLOPS_ITER * inter_per_op * N_ITER * args.steps * world / (ms / 1e3)
-    g_launch, g_ms = prof.get("G", (0, 0.0))
+    g_launch, g_ms = prof.get("AG", (0, 0.0))
     g_avg_ms = g_ms / max(g_launch, 1)
-    g_achieved = FLOPS_G * inter_per_op / (g_avg_ms / 1e3) / 1e12
+    g_achieved = FLOPS_AG * inter_per_op / (g_avg_ms / 1e3) / 1e12
     shares = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4) for k, v in prof.items()}
     line = {
         "metric": "WNNC iterations/s (500k points)" if CONFIG_NAME == "union500k"
@@ -309,18 +310,18 @@ def run_gpu(args):
         "t_pre_ms": t_pre_ms, "t_main_ms": t_main_ms,
         "iter_per_s_main_only": N_ITER / (t_main_ms / 1e3),
         "tree": info,
-        "roofline": {"kernel": "k_gather<G, rescale> (treecode sum of G + rescale)",
+        "roofline": {"kernel": "k_gather<AG, ...> (fused treecode sums of A and G on one field)",
                      "bound": "alu", "achieved": g_achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": g_achieved / peak,
                      # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
                      # kernel (ncu, profiles/union500k_treecode_kernels.md); only valid for
                      # the default workload and the kernel version that was profiled
-                     "traffic": G_TRAFFIC_BYTES if CONFIG_NAME == "union500k" else None,
+                     "traffic": AG_TRAFFIC_BYTES if CONFIG_NAME == "union500k" else None,
                      "traffic_unit": "bytes",
                      "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 "
                                     f"x {max_mhz:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
                      "avg_launch_ms": g_avg_ms, "launches": g_launch,
-                     "flops_per_launch": FLOPS_G * inter_per_op},
+                     "flops_per_launch": FLOPS_AG * inter_per_op},
         "kernel_time_share": shares,
         "gpu_launches": launches,
         "clocks": clocks,

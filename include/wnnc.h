@@ -202,14 +202,16 @@ wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node
  * entries, either may be NULL).  Enabling adds two event records per launch.
  */
 enum {
-    WNNC_PROF_MOMENTS = 0,   /* bottom-up node moments (Eq. 13, Eq. 14) */
+    WNNC_PROF_MOMENTS = 0,   /* node moments (Eq. 13, Eq. 14) */
     WNNC_PROF_A = 1,         /* treecode sum of A (Eq. 5, Alg. 4) */
     WNNC_PROF_ADJ_FAR = 2,   /* adjoint: far (target group, node) sums */
     WNNC_PROF_ADJ_NODE = 3,  /* adjoint: per-node reduction */
     WNNC_PROF_ADJ_NEAR = 4,  /* adjoint: near sums + push-down of node sums */
     WNNC_PROF_G = 5,         /* treecode sum of G + rescale (Eq. 10, Alg. 3) */
-    WNNC_PROF_SMALL = 6,     /* permutations, step length, axpy */
-    WNNC_PROF_CLASSES = 7
+    WNNC_PROF_SMALL = 6,     /* permutations, step length, axpy, WNNC update */
+    WNNC_PROF_AG = 7,        /* fused treecode sums of A and G on one field (the default
+                                iteration: A(mu) with G(mu), A(r) with G(r)) */
+    WNNC_PROF_CLASSES = 8
 };
 wnnc_status wnnc_profile_enable(wnnc_tree* tree, int enable);
 wnnc_status wnnc_profile_read(wnnc_tree* tree, int64_t* launches, double* total_ms);

@@ -33,7 +33,7 @@ __all__ = ["Tree", "TreeParams", "IterParams", "WnncError", "winding_number", "W
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ECAPACITY",
           6: "ETIMEOUT"}
-PROF_CLASSES = ["moments", "A", "adj_far", "adj_node", "adj_near", "G", "small"]
+PROF_CLASSES = ["moments", "A", "adj_far", "adj_node", "adj_near", "G", "small", "AG"]
 
 
 class WnncError(RuntimeError):

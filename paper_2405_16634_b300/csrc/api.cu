@@ -72,6 +72,8 @@ static void alloc_workspace(Tree& t) {
     t.mu_a = dalloc<float4>(n);
     t.mu_b = dalloc<float4>(n);
     t.r_s = dalloc<float4>(n);
+    t.g_mu = dalloc<float4>(n);
+    t.g_r = dalloc<float4>(n);
     t.s_s = dalloc<float>(n);
     t.area_s = dalloc<float>(n);
     t.mom = dalloc<float4>(nn);

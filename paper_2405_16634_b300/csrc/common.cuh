@@ -234,6 +234,8 @@ struct Tree {
     float4* mu_a = nullptr;       // sorted normalised mu (two buffers)
     float4* mu_b = nullptr;
     float4* r_s = nullptr;        // sorted residual direction r
+    float4* g_mu = nullptr;       // G(mu) and G(r) of the fused iteration (sorted, normalised)
+    float4* g_r = nullptr;
     float* s_s = nullptr;         // sorted scalar field (s or adjoint input)
     float* area_s = nullptr;      // sorted areas (rescale mode 1)
     float4* mom = nullptr;        // node moments: (nu_x, nu_y, nu_z, sum|nu|)
@@ -273,7 +275,7 @@ void free_target_set(TargetSet& ts);
 void free_tree(Tree& t);
 
 // operators (operators.cu)
-enum Op : int { kOpA = 0, kOpG = 1, kOpATpaper = 2 };
+enum Op : int { kOpA = 0, kOpG = 1, kOpATpaper = 2, kOpAG = 3 };
 void moments(Tree& t, const float4* nu_sorted_vec, const float* nu_sorted_scalar, int rep_mode, float4* out,
              cudaStream_t s);
 void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s);

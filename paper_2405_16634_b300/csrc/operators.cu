@@ -193,6 +193,8 @@ enum Epi : int {
     kEpiNormSq,          // partial |F|^2
     kEpiRescale,         // mu_out[i] = Ghat |mu_i| / |Ghat| (or sigma_i / |Ghat|)
     kEpiStoreR,          // mu_out[i] = acc / (4 pi) (sorted, normalised); partial |.|^2
+    kEpiResidualAG,      // kOpAG: s_s[i] = 1/2 - F, partial |s|^2; g_out[i] = G / (4 pi)
+    kEpiNormSqAG,        // kOpAG: partial |F|^2; g_out[i] = G / (4 pi)
 };
 
 struct GatherArgs {
@@ -231,15 +233,17 @@ struct GatherArgs {
     const float4* mu_cur;     // rescale: the field before the WNNC update
     const float* area;        // rescale mode 1
     float4* mu_out;
+    float4* g_out;            // kOpAG: G of the field (sorted, normalised)
     int rescale_mode;
 };
 
 // Accumulators: (x, y, z) holds the A / A^T sum, or for G the sum of
 // mu / r^3; (u, v, q) holds, for G only, the sum of (d.mu) d / r^5, so that
-// G = (x, y, z) - 3 (u, v, q).
+// G = (x, y, z) - 3 (u, v, q); s holds A's sum when both run together.
 struct Acc3 {
     float x = 0.f, y = 0.f, z = 0.f;
     float u = 0.f, v = 0.f, q = 0.f;
+    float s = 0.f;            // A's sum when A and G run together (kOpAG)
 };
 
 // One pair term.  CUT: apply the cut-off r^2 >= w2 (otherwise the caller has
@@ -255,11 +259,12 @@ __device__ __forceinline__ void interact(const float4& t, const float4& sp, cons
         float ir3 = ir * ir * ir;
         float dm = fmaf(dx, sv.x, fmaf(dy, sv.y, dz * sv.z));
         a.x = fmaf(dm, ir3, a.x);
-    } else if (OP == kOpG) {
+    } else if (OP == kOpG || OP == kOpAG) {
         float ir2 = ir * ir;
         float ir3 = ir2 * ir;
         float dm = fmaf(dx, sv.x, fmaf(dy, sv.y, dz * sv.z));
         float k5 = (dm * ir2) * ir3;
+        if (OP == kOpAG) a.s = fmaf(dm, ir3, a.s);
         a.x = fmaf(sv.x, ir3, a.x);
         a.y = fmaf(sv.y, ir3, a.y);
         a.z = fmaf(sv.z, ir3, a.z);
@@ -291,7 +296,7 @@ __device__ __forceinline__ float box_gap2(const float4& lo, const float4& hi, co
 // G's two partial sums combined: (x, y, z) - 3 (u, v, q).
 template <int OP>
 __device__ __forceinline__ Acc3 combine(Acc3 a) {
-    if (OP == kOpG) {
+    if (OP == kOpG || OP == kOpAG) {
         a.x = fmaf(-3.f, a.u, a.x);
         a.y = fmaf(-3.f, a.v, a.y);
         a.z = fmaf(-3.f, a.q, a.z);
@@ -344,8 +349,21 @@ __device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int6
             A.mu_out[i] = v;
             part = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
         }
+    } else if (EPI == kEpiResidualAG || EPI == kEpiNormSqAG) {
+        if (valid) {
+            const float f = acc.s * kInv4Pi;
+            if (EPI == kEpiResidualAG) {
+                const float sres = 0.5f - f;
+                A.s_out[i] = sres;
+                part = (double)sres * (double)sres;
+            } else {
+                part = (double)f * (double)f;
+            }
+            A.g_out[i] = make_float4(acc.x * kInv4Pi, acc.y * kInv4Pi, acc.z * kInv4Pi, 0.f);
+        }
     }
-    if (EPI == kEpiResidual || EPI == kEpiNormSq || EPI == kEpiStoreR) {
+    if (EPI == kEpiResidual || EPI == kEpiNormSq || EPI == kEpiStoreR || EPI == kEpiResidualAG ||
+        EPI == kEpiNormSqAG) {
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
         if (lane == 0) A.partial[g] = part;
@@ -424,7 +442,7 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
     if (item.pslot < 0) {
         gather_epilogue<EPI>(A, g, i, valid, acc, lane);
     } else {
-        A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(acc.x, acc.y, acc.z, 0.f);
+        A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(acc.x, acc.y, acc.z, acc.s);
     }
 }
 
@@ -442,6 +460,7 @@ __global__ void k_gather_finalize(GatherArgs A) {
         acc.x += v.x;
         acc.y += v.y;
         acc.z += v.z;
+        acc.s += v.w;
     }
     const int i0 = A.goff[g];
     gather_epilogue<EPI>(A, g, (int64_t)i0 + lane, lane < A.goff[g + 1] - i0, acc, lane);
@@ -778,6 +797,28 @@ __global__ void k_node_axpy(float4* mom, const float4* mom_r, const double* scal
     mom[b] = make_float4(fmaf(a, d.x, m.x), fmaf(a, d.y, m.y), fmaf(a, d.z, m.z), m.w + fabsf(a) * d.w);
 }
 
+// WNNC update of the fused iteration: mu' = mu + alpha r, G(mu') = G(mu) +
+// alpha G(r) (G is linear with point-centroid representatives), then the
+// rescale of Alg. 3 (or Eq. 19 with fixed areas); mu' is kept where G = 0.
+__global__ void k_wnnc_update(const float4* mu, const float4* r, const float4* gmu, const float4* gr,
+                              const double* scalars, const float* area, int rescale_mode, int64_t n,
+                              float4* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float a = (float)scalars[3];
+    const float4 m = mu[i], d = r[i], g0 = gmu[i], g1 = gr[i];
+    const float4 mp = make_float4(fmaf(a, d.x, m.x), fmaf(a, d.y, m.y), fmaf(a, d.z, m.z), 0.f);
+    const float gx = fmaf(a, g1.x, g0.x), gy = fmaf(a, g1.y, g0.y), gz = fmaf(a, g1.z, g0.z);
+    const float hn = sqrtf(gx * gx + gy * gy + gz * gz);
+    float4 res = mp;
+    if (hn > 0.f) {
+        const float len = rescale_mode == 1 ? area[i] : sqrtf(mp.x * mp.x + mp.y * mp.y + mp.z * mp.z);
+        const float f = len / hn;
+        res = make_float4(gx * f, gy * f, gz * f, 0.f);
+    }
+    out[i] = res;
+}
+
 __global__ void k_stats_nograd(float* stats, float w) {
     stats[0] = w;
     stats[1] = 0.f;
@@ -831,7 +872,10 @@ GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_a
 template <int OP, int EPI>
 void launch_gather(Tree& t, const GatherArgs& a, cudaStream_t s) {
     if (a.nitems == 0) return;
-    ProfScope ps(&t.prof, OP == kOpG ? WNNC_PROF_G : (OP == kOpA ? WNNC_PROF_A : WNNC_PROF_ADJ_NEAR), s);
+    ProfScope ps(&t.prof,
+                 OP == kOpAG ? WNNC_PROF_AG
+                             : (OP == kOpG ? WNNC_PROF_G : (OP == kOpA ? WNNC_PROF_A : WNNC_PROF_ADJ_NEAR)),
+                 s);
     k_gather<OP, EPI><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
     WNNC_LAUNCH_CHECK();
     if (a.nsplit > 0) {
@@ -1124,12 +1168,50 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
     // With point-centroid representatives the moments are linear in nu: those
     // of the updated field mu + alpha r follow from the moments of mu and r.
     const bool linear_mom = rep_mode == 1 && !t.params.moments_fp64;
+    // The default iteration fuses A and G: both are linear and share every pair
+    // term, so one pass gives A(mu) with G(mu) and one A(r) with G(r), and
+    // G(mu + alpha r) = G(mu) + alpha G(r) needs no third pass.
+    const bool fused = linear_mom && p.use_grad && p.use_wnnc;
     for (int it = p.first_iter; it <= last; ++it) {
         const double wd = p.n_iter <= 1 ? (double)p.w1
                                         : (double)p.w2 * (double)(p.n_iter - it) / (double)(p.n_iter - 1) +
                                               (double)p.w1 * (double)(it - 1) / (double)(p.n_iter - 1);
         const float w = (float)wd;
         float* st = stats ? stats + 4 * (int64_t)(it - p.first_iter) : nullptr;
+        if (fused) {
+            // s = b - A mu, with G(mu)
+            moments(t, mu, nullptr, rep_mode, t.mom, s);
+            GatherArgs a = base_args(t, S, w, t.part_acc);
+            a.sval = mu;
+            a.s_out = t.s_s;
+            a.partial = pE;
+            a.g_out = t.g_mu;
+            launch_gather<kOpAG, kEpiResidualAG>(t, a, s);
+            // r = A^T s
+            adjoint_exact(t, t.s_s, w, nullptr, t.r_s, prr, s);
+            // |A r|^2, with G(r)
+            moments(t, t.r_s, nullptr, rep_mode, t.mom_r, s);
+            GatherArgs b = base_args(t, S, w, t.part_acc);
+            b.nmom = t.mom_r;
+            b.sval = t.r_s;
+            b.partial = pqq;
+            b.g_out = t.g_r;
+            launch_gather<kOpAG, kEpiNormSqAG>(t, b, s);
+            {
+                ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
+                k_reduce3<<<kRedBlocks, kTB, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.red);
+                WNNC_LAUNCH_CHECK();
+                k_finalize_alpha<<<1, kRedBlocks, 0, s>>>(t.red, kRedBlocks, t.red + kRedBlocks, kRedBlocks,
+                                                          t.red + 2 * kRedBlocks, kRedBlocks, t.scalars, st, w,
+                                                          t.err_flag);
+                WNNC_LAUNCH_CHECK();
+                k_wnnc_update<<<grid_n, kTB, 0, s>>>(mu, t.r_s, t.g_mu, t.g_r, t.scalars, t.area_s, p.rescale, n,
+                                                     mu_alt);
+                WNNC_LAUNCH_CHECK();
+            }
+            std::swap(mu, mu_alt);
+            continue;
+        }
         if (p.use_grad) {
             // s = b - A mu
             moments(t, mu, nullptr, rep_mode, t.mom, s);

@@ -1256,7 +1256,7 @@ void free_tree(Tree& t) {
     dfree(t.tfar_off); dfree(t.tfar_ent); dfree(t.tnear_off); dfree(t.tnear_ent);
     free_work(t.adj_far_work);
     free_work(t.adj_near_work);
-    dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
+    dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.g_mu); dfree(t.g_r); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
     dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
