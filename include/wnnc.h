@@ -184,7 +184,7 @@ wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, i
  *               (consecutive near leaves merged, then cut to at most 256 points)
  *   group_off   int32 [ngroups+1]  target group g = sorted points group_off[g]..group_off[g+1]-1
  *               (at most 32; a new group starts where consecutive points' leaves share no
- *               ancestor within 3 levels of the deeper leaf)
+ *               ancestor within 3 levels of the deeper leaf, or lie in different depth-3 cells)
  *   center_scale float64 [4]     normalisation centre c (3) and scale s
  */
 wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node_start,

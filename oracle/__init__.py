@@ -42,6 +42,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 OP_A, OP_G, OP_AT = 0, 1, 2
 GROUP_SIZE = 32
 GROUP_SLACK = 3     # target groups never straddle leaves without a common ancestor 3 levels up
+GROUP_MIN_DEPTH = 3  # ... and stay inside one cell of depth 3
 
 
 def build(force: bool = False) -> str:
@@ -65,7 +66,7 @@ def lib():
         L.or_normalize.argtypes = [c_void_p, i64, c_void_p, c_void_p, c_void_p]
         L.or_direct.argtypes = [c_int, c_void_p, i64, c_void_p, c_void_p, i64, d, d, c_void_p, c_void_p,
                                 c_void_p]
-        L.or_tree_build.argtypes = [c_void_p, i64, c_int, c_int, c_int, d, c_int]
+        L.or_tree_build.argtypes = [c_void_p, i64, c_int, c_int, c_int, d, c_int, c_int]
         L.or_tree_ngroups.argtypes = [c_void_p]
         L.or_tree_ngroups.restype = i64
         L.or_tree_groups.argtypes = [c_void_p, c_void_p]
@@ -156,12 +157,13 @@ class Tree:
     """Source octree + on-surface target groups over normalised points xn."""
 
     def __init__(self, xn, theta: float, leaf_size: int = 8, max_depth: int = 15,
-                 group_size: int = GROUP_SIZE, group_slack: int = GROUP_SLACK):
+                 group_size: int = GROUP_SIZE, group_slack: int = GROUP_SLACK,
+                 group_min_depth: int = GROUP_MIN_DEPTH):
         self.xn = _f64(xn, (-1, 3))
         self.n = self.xn.shape[0]
         self.theta = float(theta)
         self._h = lib().or_tree_build(_p(self.xn), self.n, leaf_size, group_size, max_depth, self.theta,
-                                      int(group_slack))
+                                      int(group_slack), int(group_min_depth))
 
     def __del__(self):
         if getattr(self, "_h", None):

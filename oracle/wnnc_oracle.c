@@ -325,11 +325,13 @@ static int common_digits(uint64_t a, uint64_t b) {
  * With the source tree (targets = sources, sorted alike): a new group also
  * starts before sorted point k when the leaves of points k-1 and k do not
  * share an ancestor within `slack` levels of the deeper leaf, i.e. when the
- * keys share fewer than max(depth(leaf(k-1)), depth(leaf(k))) - slack digits.
- * A group then never straddles a jump of the Morton curve between distant
- * cells, which keeps its bounding box (and its interaction lists) compact. */
+ * keys share fewer than max(depth(leaf(k-1)), depth(leaf(k))) - slack digits,
+ * or fewer than min_depth digits (the two points lie in different cells of
+ * depth min_depth).  A group then never straddles a jump of the Morton curve
+ * between distant cells and stays inside one cell of depth min_depth, which
+ * keeps its bounding box (and its interaction lists) compact. */
 static int64_t group_offsets(const or_octree* t, const uint64_t* keys, int64_t m, int group_size,
-                             int slack, int64_t* goff) {
+                             int slack, int min_depth, int64_t* goff) {
     int* ldepth = NULL;
     if (slack >= 0) {
         ldepth = malloc(sizeof(int) * (m > 0 ? m : 1));
@@ -342,7 +344,8 @@ static int64_t group_offsets(const or_octree* t, const uint64_t* keys, int64_t m
         int cut = (k == 0) || (k - start == group_size);
         if (!cut && slack >= 0) {
             int d = ldepth[k - 1] > ldepth[k] ? ldepth[k - 1] : ldepth[k];
-            cut = common_digits(keys[k - 1], keys[k]) < d - slack;
+            const int cd = common_digits(keys[k - 1], keys[k]);
+            cut = cd < d - slack || cd < min_depth;
         }
         if (cut) {
             if (goff) goff[ng] = k;
@@ -356,7 +359,7 @@ static int64_t group_offsets(const or_octree* t, const uint64_t* keys, int64_t m
 }
 
 static void build_targets(or_targets* T, const or_octree* t, const double* yn, int64_t m,
-                          int group_size, double theta, int slack) {
+                          int group_size, double theta, int slack, int min_depth) {
     T->m = m; T->group_size = group_size;
     T->perm = malloc(sizeof(int64_t) * (m > 0 ? m : 1));
     uint64_t* keys = malloc(sizeof(uint64_t) * (m > 0 ? m : 1));
@@ -364,9 +367,9 @@ static void build_targets(or_targets* T, const or_octree* t, const double* yn, i
     T->y = malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
     for (int64_t i = 0; i < m; ++i)
         for (int k = 0; k < 3; ++k) T->y[3 * i + k] = yn[3 * T->perm[i] + k];
-    int64_t ng = group_offsets(t, keys, m, group_size, slack, NULL);
+    int64_t ng = group_offsets(t, keys, m, group_size, slack, min_depth, NULL);
     T->goff = malloc(sizeof(int64_t) * (ng + 1));
-    group_offsets(t, keys, m, group_size, slack, T->goff);
+    group_offsets(t, keys, m, group_size, slack, min_depth, T->goff);
     free(keys);
     T->ngroups = ng;
     T->glo = malloc(sizeof(double) * 3 * (ng > 0 ? ng : 1));
@@ -420,10 +423,10 @@ typedef struct {
     double theta;
 } or_tree;
 
-/* group_slack: the rule of group_offsets for the points as targets (< 0:
- * fixed runs of group_size). */
+/* group_slack, group_min_depth: the rule of group_offsets for the points as
+ * targets (slack < 0: fixed runs of group_size). */
 or_tree* or_tree_build(const double* xn, int64_t n, int leaf_size, int group_size, int max_depth,
-                       double theta, int group_slack) {
+                       double theta, int group_slack, int group_min_depth) {
     or_tree* T = calloc(1, sizeof(or_tree));
     or_octree* t = &T->src;
     t->n = n; t->leaf_size = leaf_size; t->max_depth = max_depth;
@@ -435,7 +438,7 @@ or_tree* or_tree_build(const double* xn, int64_t n, int leaf_size, int group_siz
         for (int k = 0; k < 3; ++k) t->x[3 * i + k] = xn[3 * t->perm[i] + k];
     if (n > 0) build_octree(t);
     T->theta = theta;
-    build_targets(&T->self, t, xn, n, group_size, theta, group_slack);
+    build_targets(&T->self, t, xn, n, group_size, theta, group_slack, group_min_depth);
     return T;
 }
 
@@ -708,7 +711,7 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
     const or_octree* t = &T->src;
     or_targets Q;
     memset(&Q, 0, sizeof(Q));
-    build_targets(&Q, t, qn, m, T->self.group_size, T->theta, -1);
+    build_targets(&Q, t, qn, m, T->self.group_size, T->theta, -1, 0);
     int64_t n = t->n;
     int dout = (op == OP_A) ? 1 : 3;
     double* nus = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));

@@ -104,6 +104,7 @@ constexpr int kMomDirect = 1024;    //   up to this many points, one warp each; 
 #define WNNC_GROUP_SLACK 3
 #endif
 constexpr int kGroupSlack = WNNC_GROUP_SLACK;      // group rule: see build_target_set
+constexpr int kGroupMinDepth = 3;                  // groups stay inside one cell of this depth
 
 struct Item {
     int g;          // target group (adjoint near sums: source chunk)

@@ -287,15 +287,17 @@ __device__ __forceinline__ int common_digits(uint64_t a, uint64_t b) {
 
 // Group rule for the points as targets: a new group starts before sorted
 // point k when the leaves of k-1 and k share no ancestor within `slack`
-// levels of the deeper leaf (the keys share fewer than that many digits).
+// levels of the deeper leaf (the keys share fewer than that many digits), or
+// when the two points lie in different cells of depth `min_depth`.
 __global__ void k_group_cuts(const uint64_t* keys, const int* leaf_of, const int* ndepth, int64_t m,
-                             int slack, int* cut) {
+                             int slack, int min_depth, int* cut) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m) return;
     int c = 1;
     if (k > 0) {
         int d = max(ndepth[leaf_of[k - 1]], ndepth[leaf_of[k]]);
-        c = common_digits(keys[k - 1], keys[k]) < d - slack;
+        const int cd = common_digits(keys[k - 1], keys[k]);
+        c = cd < d - slack || cd < min_depth;
     }
     cut[k] = c;
 }
@@ -432,7 +434,10 @@ __device__ __forceinline__ bool is_far(const double* nlo, const double* nhi, con
 }
 
 constexpr int kTravWarps = 2;
-constexpr int kStack = 4096;
+// Per-warp traversal stack (shared memory).  The smaller stack allows more
+// resident warps; a traversal that overflows it runs again with the larger.
+constexpr int kStackSmall = 2048;
+constexpr int kStackBig = 4096;
 
 // Warp-cooperative traversal of the octree for one target group, one pass:
 // it writes keys (group<<32 | node) for far entries and (group<<32 | first
@@ -459,13 +464,14 @@ __device__ __forceinline__ void trav_flush(const uint64_t* buf, const uint32_t* 
     __syncwarp();
 }
 
+template <int STACK>
 __global__ void __launch_bounds__(32 * kTravWarps)
 k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float4* nhif, const int* ndepth,
            const int* nchild, const int* child0, const int* nstart, const double* glo, const double* ghi, int ng,
            double theta, uint64_t* far_pool, int64_t far_cap, unsigned long long* far_count,
            uint64_t* near_pool, uint32_t* near_vpool, int64_t near_cap, unsigned long long* near_count,
            int* err) {
-    __shared__ int stack[kTravWarps][kStack];
+    __shared__ int stack[kTravWarps][STACK];
     __shared__ uint64_t fbuf_all[kTravWarps][kTravBuf];
     __shared__ uint64_t nbuf_all[kTravWarps][kTravBuf];
     __shared__ uint32_t nvbuf_all[kTravWarps][kTravBuf];
@@ -528,7 +534,7 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
             if (lane >= o) inc += u;
         }
         int total = __shfl_sync(0xffffffffu, inc, 31);
-        if (top + total > kStack) {
+        if (top + total > STACK) {
             if (lane == 0) atomicOr(err, kErrCapacity);
             break;
         }
@@ -870,7 +876,8 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     if (self) {
         int* cut = dalloc<int>(m + 1);
         int* cscan = dalloc<int>(m + 2);
-        k_group_cuts<<<ceil_div(m, kTB), kTB, 0, s>>>(keys, t.leaf_of, t.node_depth, m, kGroupSlack, cut);
+        k_group_cuts<<<ceil_div(m, kTB), kTB, 0, s>>>(keys, t.leaf_of, t.node_depth, m, kGroupSlack,
+                                                      kGroupMinDepth, cut);
         WNNC_LAUNCH_CHECK();
         exclusive_scan_i32(cut, cscan, m, s);
         int nruns = read_int(cscan + m, s);
@@ -932,17 +939,21 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         uint64_t* nkeys = nullptr;
         uint32_t* nvals = nullptr;
         int64_t nfar = 0, nleafent = 0;
-        for (int attempt = 0; attempt < 2; ++attempt) {
+        bool big_stack = false;
+        for (int attempt = 0; attempt < 4; ++attempt) {
             fkeys = dalloc<uint64_t>(far_cap);
             nkeys = dalloc<uint64_t>(near_cap);
             nvals = dalloc<uint32_t>(near_cap);
             WNNC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
             WNNC_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
-            k_traverse<<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_lof, t.node_hif,
-                                                        t.node_depth, t.node_nchild,
-                                                        t.node_child0, t.node_start, ts.glo, ts.ghi, ng, theta,
-                                                        fkeys, far_cap, counts, nkeys, nvals, near_cap,
-                                                        counts + 1, err);
+#define WNNC_TRAVERSE(STK)                                                                                     \
+    k_traverse<STK><<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_lof, t.node_hif,           \
+                                                      t.node_depth, t.node_nchild, t.node_child0,            \
+                                                      t.node_start, ts.glo, ts.ghi, ng, theta, fkeys,        \
+                                                      far_cap, counts, nkeys, nvals, near_cap, counts + 1,  \
+                                                      err)
+            if (big_stack) WNNC_TRAVERSE(kStackBig); else WNNC_TRAVERSE(kStackSmall);
+#undef WNNC_TRAVERSE
             WNNC_LAUNCH_CHECK();
             unsigned long long hc[2] = {0, 0};
             int herr = 0;
@@ -950,14 +961,18 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             WNNC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
             WNNC_CUDA(cudaStreamSynchronize(s));
             if (herr) {
-                pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(leaf_off); pool_free(err);
-                pool_free(counts); pool_free(near_off0);
+                pool_free(fkeys); pool_free(nkeys); pool_free(nvals);
+                if (!big_stack) {   // again with the larger stack
+                    big_stack = true;
+                    continue;
+                }
+                pool_free(leaf_off); pool_free(err); pool_free(counts); pool_free(near_off0);
                 fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
             }
             nfar = (int64_t)hc[0];
             nleafent = (int64_t)hc[1];
             if (nfar <= far_cap && nleafent <= near_cap) break;
-            if (attempt == 1 || nfar > INT32_MAX || nleafent > INT32_MAX) {
+            if (attempt == 3 || nfar > INT32_MAX || nleafent > INT32_MAX) {
                 pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(leaf_off); pool_free(err);
                 pool_free(counts); pool_free(near_off0);
                 fail(WNNC_ECAPACITY, "interaction lists too long");

@@ -75,8 +75,11 @@ def test_library_is_the_cuda_build():
     assert torch.cuda.is_available()
 
 
-@pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
+@pytest.mark.parametrize("theta", [0.05, 0.3, 0.5, 0.8])
 def test_tree_and_lists_match_oracle_exactly(theta):
+    """Tree, groups and lists bit-exact against the oracle; theta = 0.05 opens
+    nearly every node, deep enough to overflow the traversal's smaller stack
+    and exercise the rerun with the larger one."""
     W = _wnnc()
     c = synth.config_cloud("union50k", n=20000)
     t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta)

@@ -262,7 +262,8 @@ def test_tree_lists_partition_sources_and_satisfy_alg4(cloud20k):
 def test_groups_never_straddle_distant_leaves(cloud20k):
     """Target groups are runs of at most 32 sorted points that end where two
     consecutive points' leaves share no ancestor within GROUP_SLACK levels of
-    the deeper one; with a negative slack they are plain runs of 32."""
+    the deeper one or no ancestor at depth GROUP_MIN_DEPTH; with a negative
+    slack they are plain runs of 32."""
     xn = cloud20k[0]
     t = oracle.Tree(xn, 0.5)
     nd = t.nodes()
@@ -278,12 +279,17 @@ def test_groups_never_straddle_distant_leaves(cloud20k):
             out.append(b)
             b = nd["parent"][b]
         return out
+    # cell of depth D of each sorted point, from its 15-bit quantised coordinates
+    xs = xn[t.perm()]
+    q = np.clip(np.floor((xs + 1.0) * 16384.0), 0, 32767).astype(np.int64)
+    cell = q >> (15 - oracle.GROUP_MIN_DEPTH)
     for g in range(len(go) - 1):
         for k in range(go[g] + 1, go[g + 1]):
             a, b = leaf_of[k - 1], leaf_of[k]
             d = max(nd["depth"][a], nd["depth"][b])
             common = set(ancestors(a)) & set(ancestors(b))
             assert max(nd["depth"][c] for c in common) >= d - oracle.GROUP_SLACK
+            assert np.array_equal(cell[k - 1], cell[k])
     fixed = oracle.Tree(xn, 0.5, group_slack=-1).groups()
     assert np.array_equal(fixed, np.minimum(np.arange(len(fixed)) * 32, len(xn)))
 
