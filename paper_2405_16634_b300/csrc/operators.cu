@@ -560,8 +560,10 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_far(AdjArgs A) {
 }
 
 // One warp per node; lanes take the node's entries (consecutive slots of the
-// node-major list) 128 at a time, four independent gathers per lane in
-// flight, then reduce.  The kernel is bound by the latency of the gathers.
+// node-major list) 32 x kNodeGathers at a time, kNodeGathers independent
+// gathers per lane in flight, then reduce.  The kernel is bound by the latency
+// of the gathers.
+constexpr int kNodeGathers = 8;
 __global__ void k_adj_node(int nnodes, const int* tfar_off, const int* tfar_ent, const float4* contrib,
                            float4* vnode) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -569,15 +571,15 @@ __global__ void k_adj_node(int nnodes, const int* tfar_off, const int* tfar_ent,
     if (b >= nnodes) return;
     float ax = 0.f, ay = 0.f, az = 0.f;
     const int q1 = tfar_off[b + 1];
-    for (int q = tfar_off[b] + lane; q < q1; q += 128) {
-        int e[4];
+    for (int q = tfar_off[b] + lane; q < q1; q += 32 * kNodeGathers) {
+        int e[kNodeGathers];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = q + 32 * u < q1 ? tfar_ent[q + 32 * u] : -1;
-        float4 c[4];
+        for (int u = 0; u < kNodeGathers; ++u) e[u] = q + 32 * u < q1 ? tfar_ent[q + 32 * u] : -1;
+        float4 c[kNodeGathers];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = e[u] >= 0 ? contrib[e[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < kNodeGathers; ++u) c[u] = e[u] >= 0 ? contrib[e[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) { ax += c[u].x; ay += c[u].y; az += c[u].z; }
+        for (int u = 0; u < kNodeGathers; ++u) { ax += c[u].x; ay += c[u].y; az += c[u].z; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
