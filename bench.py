@@ -286,6 +286,7 @@ def run_gpu(args):
     inter_per_op = far_pairs + near_pairs
     inter_per_iter = 4 * inter_per_op
     props = torch.cuda.get_device_properties(dev)
+    fp32_measured = W.probe_fp32(dev)
     peaks = read_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
@@ -320,6 +321,8 @@ def run_gpu(args):
                      "traffic_unit": "bytes",
                      "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 "
                                     f"x {max_mhz:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
+                     "peak_measured_fma_stream": fp32_measured,
+                     "frac_of_measured": g_achieved / fp32_measured,
                      "avg_launch_ms": g_avg_ms, "launches": g_launch,
                      "flops_per_launch": FLOPS_AG * inter_per_op},
         "kernel_time_share": shares,

@@ -76,6 +76,10 @@ typedef struct {
     int moments_fp64;  /* 1 = sum node moments in double precision, and sum the moments of
                           every G step directly instead of deriving them from those of mu
                           and r by linearity (default 0: single precision) */
+    int near_bf16;     /* 1 = round the near-field coordinates (offsets in the target group's
+                          frame, sources and targets) to bfloat16 before the pair terms of A, G
+                          and the fused A+G; the adjoint stays in float, so A^T is then not the
+                          exact transpose.  A precision study, not a fast path (default 0) */
 } wnnc_tree_params;
 
 /* Iteration parameters (Alg. 3; Sec. 5.1.1 defaults n = 40, w1 = 0.002, w2 = 0.016). */
@@ -278,6 +282,14 @@ wnnc_status wnnc_warm_init(const float* dir, const float* ref, int64_t n, float 
 /* Number of kernels this library has launched in this process so far (all
  * threads, all trees); for counting the launches inside a timed region. */
 int64_t wnnc_kernel_launches(void);
+
+/*
+ * Diagnostic (no counterpart in the paper): the FP32 FMA throughput of the
+ * current device in TFLOP/s, measured with eight independent FMA chains per
+ * thread on all SMs and timed with CUDA events on `stream` (synchronises).
+ * The pair kernels are bound by FP32 issue; this is their measured ceiling.
+ */
+wnnc_status wnnc_probe_fp32(double* tflops, void* stream);
 
 /*
  * F(q_k; mu) at m query points by direct summation over all n points, with no

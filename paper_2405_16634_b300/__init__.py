@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libwnnc.so")
 
 __all__ = ["Tree", "TreeParams", "IterParams", "WnncError", "winding_number", "WindingNumber",
-           "lib", "LIB_PATH", "PROF_CLASSES", "knn16", "Mlp", "MLP_PARAMS", "warm_init"]
+           "lib", "LIB_PATH", "PROF_CLASSES", "knn16", "Mlp", "MLP_PARAMS", "warm_init", "probe_fp32"]
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ECAPACITY",
           6: "ETIMEOUT"}
@@ -44,7 +44,7 @@ class WnncError(RuntimeError):
 
 class TreeParams(Structure):
     _fields_ = [("max_depth", c_int), ("leaf_size", c_int), ("theta", c_float),
-                ("rep_mode", c_int), ("moments_fp64", c_int)]
+                ("rep_mode", c_int), ("moments_fp64", c_int), ("near_bf16", c_int)]
 
 
 class IterParams(Structure):
@@ -99,6 +99,8 @@ def lib():
     L.wnnc_warm_init.argtypes = [P, P, c_int64, c_float, P, P]
     L.wnnc_last_error.restype = ctypes.c_char_p
     L.wnnc_kernel_launches.restype = c_int64
+    L.wnnc_probe_fp32.argtypes = [P, P]
+    L.wnnc_probe_fp32.restype = c_int
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
                  "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
                  "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_tree_info",
@@ -135,6 +137,15 @@ def kernel_launches() -> int:
     return int(lib().wnnc_kernel_launches())
 
 
+def probe_fp32(device=None) -> float:
+    """Measured FP32 FMA throughput of the device (TFLOP/s)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    v = ctypes.c_double()
+    with torch.cuda.device(dev):
+        _check(lib().wnnc_probe_fp32(ctypes.byref(v), _stream_ptr(dev)))
+    return v.value
+
+
 def default_tree_params() -> TreeParams:
     p = TreeParams()
     _check(lib().wnnc_tree_params_default(ctypes.byref(p)))
@@ -151,7 +162,7 @@ class Tree:
     """Octree, node data and interaction lists of a point cloud on one GPU."""
 
     def __init__(self, points, theta: float = 0.5, leaf_size: int = 8, max_depth: int = 15,
-                 rep_mode: int = 1, moments_fp64: bool = False):
+                 rep_mode: int = 1, moments_fp64: bool = False, near_bf16: bool = False):
         pts = points if isinstance(points, torch.Tensor) else torch.as_tensor(points)
         self.device = pts.device if pts.is_cuda else torch.device("cuda", torch.cuda.current_device())
         pts = _dev_f32(pts, (-1, 3), self.device)
@@ -159,6 +170,7 @@ class Tree:
         p = default_tree_params()
         p.max_depth, p.leaf_size, p.theta = int(max_depth), int(leaf_size), float(theta)
         p.rep_mode, p.moments_fp64 = int(rep_mode), int(bool(moments_fp64))
+        p.near_bf16 = int(bool(near_bf16))
         self.params = p
         h = c_void_p()
         with torch.cuda.device(self.device):

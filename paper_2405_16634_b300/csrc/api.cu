@@ -133,6 +133,7 @@ static void check_params(const wnnc_tree_params& p) {
     if (p.leaf_size < 1 || p.leaf_size > 1024) fail(WNNC_EINVAL, "leaf_size must be in [1, 1024]");
     if (!(p.theta >= 0.f) || !std::isfinite(p.theta)) fail(WNNC_EINVAL, "theta must be finite and >= 0");
     if (p.rep_mode != 0 && p.rep_mode != 1) fail(WNNC_EINVAL, "rep_mode must be 0 or 1");
+    if (p.near_bf16 != 0 && p.near_bf16 != 1) fail(WNNC_EINVAL, "near_bf16 must be 0 or 1");
 }
 
 static void check_w(float w) {
@@ -160,6 +161,7 @@ wnnc_status wnnc_tree_params_default(wnnc_tree_params* p) {
     p->theta = 0.5f;
     p->rep_mode = 1;
     p->moments_fp64 = 0;
+    p->near_bf16 = 0;
     return WNNC_OK;
 }
 
@@ -491,6 +493,14 @@ wnnc_status wnnc_warm_init(const float* dir, const float* ref, int64_t n, float 
 }
 
 int64_t wnnc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+wnnc_status wnnc_probe_fp32(double* tflops, void* stream) {
+    return guarded([&] {
+        if (!tflops) fail(WNNC_EINVAL, "tflops is NULL");
+        AllocStream as(static_cast<cudaStream_t>(stream));
+        *tflops = probe_fp32(static_cast<cudaStream_t>(stream));
+    });
+}
 
 const char* wnnc_last_error(void) { return g_last_error.c_str(); }
 

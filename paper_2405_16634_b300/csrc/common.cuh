@@ -311,6 +311,7 @@ struct Mlp {
     int loss_mode = 0;         // 0: 1 - c (signed), 1: 1 - c^2 (sign-free); c = (v/|v|).label
 };
 int mlp_param_count();
+double probe_fp32(cudaStream_t s);
 void mlp_alloc(Mlp& m, int64_t max_batch);
 void mlp_free(Mlp& m);
 void mlp_forward(Mlp& m, const float* x, int64_t B, float* y, cudaStream_t s);

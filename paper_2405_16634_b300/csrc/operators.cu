@@ -22,6 +22,7 @@
 // those of the general loop.
 #include <algorithm>
 #include <cmath>
+#include <cuda_bf16.h>
 #include <cfloat>
 #include <utility>
 
@@ -223,6 +224,7 @@ struct GatherArgs {
     const float4* nmom;
     float w2;
     float fast2;              // squared batch-test radius (cut-off radius plus margin)
+    int near_bf16;            // round near-field coordinates to bfloat16
     const float4* tgbl;       // target group boxes in their own frames
     const float4* tgbh;
     float scale;              // output unit conversion factor
@@ -283,6 +285,12 @@ __device__ __forceinline__ void interact(const float4& t, const float4& sp, cons
 // (both origins are multiples of 2^-12, so the shift is exact).
 __device__ __forceinline__ float4 shift(const float4& c, const float4& o, const float4& p) {
     return make_float4((c.x - o.x) + p.x, (c.y - o.y) + p.y, (c.z - o.z) + p.z, 0.f);
+}
+
+// A point rounded to bfloat16 per coordinate (the near-field precision study).
+__device__ __forceinline__ float4 bf16_point(const float4& p) {
+    return make_float4(__bfloat162float(__float2bfloat16_rn(p.x)), __bfloat162float(__float2bfloat16_rn(p.y)),
+                       __bfloat162float(__float2bfloat16_rn(p.z)), p.w);
 }
 
 // Squared distance from p to the box [lo, hi] (zero inside).
@@ -370,7 +378,9 @@ __device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int6
     }
 }
 
-template <int OP, int EPI>
+// NB: the near-field bfloat16 study (a template parameter, so that the
+// default kernel carries no trace of it).
+template <int OP, int EPI, bool NB>
 __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
     __shared__ float4 sp_all[kGatherWarps][32];
     __shared__ float4 sv_all[kGatherWarps][32];
@@ -387,6 +397,7 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
     const float4 o = A.tgorig[g];
     const float4 t = valid ? shift(A.tcorig[i >> 5], o, A.tpos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 blo = A.tgbl[g], bhi = A.tgbh[g];
+    const float4 tn = NB ? bf16_point(t) : t;   // the target as the near field sees it
     Acc3 acc;
 
     // near field: ranges of source points
@@ -399,7 +410,7 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
                 const int j = base + lane;
                 const float4 p = shift(A.scorig[j >> 5], o, A.spos[j]);
                 clear = box_gap2(blo, bhi, p) >= A.fast2;
-                sp[lane] = p;
+                sp[lane] = NB ? bf16_point(p) : p;
                 if (OP == kOpATpaper) sv[lane] = make_float4(A.sval_s[j], 0.f, 0.f, 0.f);
                 else sv[lane] = A.sval[j];
             }
@@ -407,10 +418,10 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
             __syncwarp();
             if (clear) {
 #pragma unroll kUnroll
-                for (int k = 0; k < cnt; ++k) interact<OP, false>(t, sp[k], sv[k], A.w2, acc);
+                for (int k = 0; k < cnt; ++k) interact<OP, false>(tn, sp[k], sv[k], A.w2, acc);
             } else {
 #pragma unroll kUnroll
-                for (int k = 0; k < cnt; ++k) interact<OP, true>(t, sp[k], sv[k], A.w2, acc);
+                for (int k = 0; k < cnt; ++k) interact<OP, true>(tn, sp[k], sv[k], A.w2, acc);
             }
             __syncwarp();
         }
@@ -866,6 +877,7 @@ GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_a
     a.nmom = t.mom;
     a.w2 = cutoff2(w);
     a.fast2 = fast_radius2(w);
+    a.near_bf16 = t.params.near_bf16;
     a.tgbl = ts.gbl;
     a.tgbh = ts.gbh;
     return a;
@@ -878,7 +890,11 @@ void launch_gather(Tree& t, const GatherArgs& a, cudaStream_t s) {
                  OP == kOpAG ? WNNC_PROF_AG
                              : (OP == kOpG ? WNNC_PROF_G : (OP == kOpA ? WNNC_PROF_A : WNNC_PROF_ADJ_NEAR)),
                  s);
-    k_gather<OP, EPI><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
+    // the bfloat16 near-field study applies to the sums of A and G only
+    if ((OP == kOpA || OP == kOpG || OP == kOpAG) && a.near_bf16)
+        k_gather<OP, EPI, true><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
+    else
+        k_gather<OP, EPI, false><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
     WNNC_LAUNCH_CHECK();
     if (a.nsplit > 0) {
         k_gather_finalize<EPI><<<ceil_div((int64_t)a.nsplit * 32, kTB), kTB, 0, s>>>(a);

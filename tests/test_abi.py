@@ -34,7 +34,7 @@ def test_defaults_and_argument_errors_without_gpu():
     W.build_if_needed()
     L = W.lib()
     p = W.default_tree_params()
-    assert (p.max_depth, p.leaf_size, p.rep_mode, p.moments_fp64) == (15, 8, 1, 0)
+    assert (p.max_depth, p.leaf_size, p.rep_mode, p.moments_fp64, p.near_bf16) == (15, 8, 1, 0, 0)
     assert abs(p.theta - 0.5) < 1e-7
     q = W.default_iter_params()
     assert (q.n_iter, q.first_iter, q.last_iter, q.init, q.rescale, q.use_grad, q.use_wnnc) == \

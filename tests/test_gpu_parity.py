@@ -369,3 +369,41 @@ def test_profiler_counts_launches():
     assert all(v[1] >= 0 for v in p.values())
     t.profile_reset()
     assert t.profile_read()["AG"] == (0, 0.0)
+
+
+@pytest.mark.gpu
+def test_near_field_bf16_precision_study_at_2m():
+    """The 2M-point configuration: A with the near field in float and in
+    bfloat16 coordinates, against the oracle's FP64 direct sums on a seeded
+    2000-target subset.  The float treecode stays within its theta = 0.5 error;
+    bfloat16 offsets (8 significant bits, ~1e-4 absolute at near-field range)
+    are measurably worse, which is why they stay an opt-in study."""
+    W = _wnnc()
+    c = synth.config_cloud("union2m")
+    n = len(c.points)
+    xn, ctr, s = oracle.normalize(c.points)
+    mu = (c.normals * (4 * np.pi / n) / (s * s)).astype(np.float32)
+    w = 0.002
+    sub = np.sort(np.random.default_rng(5000).choice(n, 2000, replace=False))
+    ref, _ = oracle.direct(oracle.OP_A, xn, mu.astype(np.float64) * s * s, w, y=xn[sub])
+    pts = torch.from_numpy(c.points).cuda()
+    err = {}
+    for bf in (False, True):
+        t = W.Tree(pts, theta=0.5, near_bf16=bf)
+        F = t.eval_w(torch.from_numpy(mu).cuda(), w).cpu().numpy().astype(np.float64)[sub]
+        t.close()
+        err[bf] = (np.linalg.norm(F - ref) / np.linalg.norm(ref), np.abs(F - ref).max())
+    print("near field float / bfloat16: rel L2", err[False][0], err[True][0], "max", err[False][1], err[True][1])
+    assert err[False][0] < 1.5e-2
+    assert err[True][0] < 3e-2
+    assert err[True][1] > err[False][1]
+
+
+@pytest.mark.gpu
+def test_fp32_probe_is_near_the_nominal_peak():
+    W = _wnnc()
+    props = torch.cuda.get_device_properties(0)
+    measured = W.probe_fp32()
+    # nominal: SMs x 128 lanes x 2 flops x the highest SM clock of a B300 (2032 MHz)
+    nominal = props.multi_processor_count * 128 * 2 * 2.032e9 / 1e12
+    assert 0.5 * nominal < measured < 1.05 * nominal
