@@ -268,10 +268,11 @@ void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cud
 
 // tree build (tree_build.cu)
 void build_tree(Tree& t, const float* pts, cudaStream_t s);
-// self = the tree's own points as targets (groups cut at Morton jumps);
+// self = the tree's own points as targets (groups cut at Morton jumps; the
+// tree's sorted keys, coordinates and permutation `self_perm` are reused);
 // otherwise fixed 32-target groups.
 void build_target_set(const Tree& t, TargetSet& ts, const double* yn_unsorted, int64_t m, bool self,
-                      cudaStream_t s);
+                      cudaStream_t s, const int64_t* self_perm = nullptr);
 void free_target_set(TargetSet& ts);
 void free_tree(Tree& t);
 

@@ -99,7 +99,8 @@ void exclusive_scan_impl(const T* in, T* out, int64_t n, cudaStream_t s) {
     exclusive_scan_impl<T>(bsum, bsum, nb, s);
     k_scan_apply<T><<<nb, kScanThreads, 0, s>>>(in, out, n, bsum);
     WNNC_LAUNCH_CHECK();
-    WNNC_CUDA(cudaStreamSynchronize(s));
+    // the pool frees in the order of its stream: no wait when that is s
+    if (alloc_stream() != s) WNNC_CUDA(cudaStreamSynchronize(s));
     pool_free(bsum);
 }
 
@@ -126,15 +127,27 @@ __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, int* hist,
     hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
-                             uint32_t* vout, int64_t n, int shift, const int* offs, int nblocks) {
+// Scatter of one tile: the keys are ranked stably by digit into shared memory
+// (warps in order, rounds in order, lanes in order within a round), then
+// written out in that order, so that each digit's keys go to consecutive
+// global positions (coalesced runs instead of 32 scattered stores a warp).
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, const uint32_t* vin,
+                                                           uint64_t* kout, uint32_t* vout, int64_t n,
+                                                           int shift, const int* offs, int nblocks) {
     __shared__ int whist[kRsWarps][256];
     __shared__ int wbase[kRsWarps][256];
+    __shared__ int dstart[256];
+    __shared__ int gbase[256];
+    __shared__ int wsum[kRsWarps];
+    __shared__ uint64_t skey[kRsTile];
+    __shared__ uint32_t sval[kRsTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&whist[0][0])[i] = 0;
     __syncthreads();
-    const int64_t w0 = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * (32 * kRsRounds);
+    const int64_t t0 = (int64_t)blockIdx.x * kRsTile;
+    const int tcount = (int)(n - t0 < (int64_t)kRsTile ? n - t0 : (int64_t)kRsTile);
+    const int64_t w0 = t0 + (int64_t)warp * (32 * kRsRounds);
     for (int r = 0; r < kRsRounds; ++r) {
         int64_t i = w0 + r * 32 + lane;
         bool valid = i < n;
@@ -148,8 +161,24 @@ __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t*
     }
     __syncthreads();
     {
-        int d = threadIdx.x;   // 256 threads, one digit each
-        int run = offs[d * nblocks + blockIdx.x];
+        // tile-local start of each digit: exclusive scan over the 256 digits
+        const int d = threadIdx.x;   // 256 threads, one digit each
+        int tot = 0;
+        for (int w = 0; w < kRsWarps; ++w) tot += whist[w][d];
+        int x = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        const int ds = before + x - tot;
+        dstart[d] = ds;
+        gbase[d] = offs[d * nblocks + blockIdx.x] - ds;
+        int run = ds;
         for (int w = 0; w < kRsWarps; ++w) {
             wbase[w][d] = run;
             run += whist[w][d];
@@ -166,12 +195,19 @@ __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t*
             unsigned peers = __match_any_sync(vmask, d);
             int base = wbase[warp][d];
             int pos = base + __popc(peers & lt_mask);
-            kout[pos] = key;
-            if (vout) vout[pos] = vin[i];
+            skey[pos] = key;
+            if (vin) sval[pos] = vin[i];
             __syncwarp(vmask);
             if (lane == __ffs(peers) - 1) wbase[warp][d] = base + __popc(peers);
         }
         __syncwarp();
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < tcount; p += kRsThreads) {
+        const uint64_t key = skey[p];
+        const int gpos = gbase[(key >> shift) & 255u] + p;
+        kout[gpos] = key;
+        if (vout) vout[gpos] = sval[p];
     }
 }
 
@@ -223,7 +259,7 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
         WNNC_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         if (vals) WNNC_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     }
-    WNNC_CUDA(cudaStreamSynchronize(s));
+    if (alloc_stream() != s) WNNC_CUDA(cudaStreamSynchronize(s));
     pool_free(k2);
     if (v2) pool_free(v2);
     pool_free(hist);

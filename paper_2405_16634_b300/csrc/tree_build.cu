@@ -854,19 +854,30 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
 }
 
 void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m, bool self,
-                      cudaStream_t s) {
+                      cudaStream_t s, const int64_t* self_perm) {
     ts.m = m;
     ts.nchunks = ceil_div(m, kGroup);
-    // Morton order of the targets (the same order as the sources when self)
-    uint64_t* keys = dalloc<uint64_t>(m);
-    uint32_t* idx = dalloc<uint32_t>(m);
-    k_keys_from_xn<<<ceil_div(m, kTB), kTB, 0, s>>>(yn, m, keys, idx);
-    WNNC_LAUNCH_CHECK();
-    radix_sort_pairs(keys, idx, m, kKeyBits, s);
-    double* ys = dalloc<double>(3 * m);
+    // Morton order of the targets: for the tree's own points it is the
+    // sources' order, already computed by the tree build
+    const bool reuse = self && self_perm != nullptr;
+    uint64_t* keys = nullptr;
+    uint32_t* idx = nullptr;
+    double* ys = nullptr;
     ts.perm = dalloc<int64_t>(m);
-    k_gather_sorted<<<ceil_div(m, kTB), kTB, 0, s>>>(yn, idx, m, ys, ts.perm);
-    WNNC_LAUNCH_CHECK();
+    if (reuse) {
+        keys = t.keys;
+        ys = t.xs;
+        WNNC_CUDA(cudaMemcpyAsync(ts.perm, self_perm, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, s));
+    } else {
+        keys = dalloc<uint64_t>(m);
+        idx = dalloc<uint32_t>(m);
+        k_keys_from_xn<<<ceil_div(m, kTB), kTB, 0, s>>>(yn, m, keys, idx);
+        WNNC_LAUNCH_CHECK();
+        radix_sort_pairs(keys, idx, m, kKeyBits, s);
+        ys = dalloc<double>(3 * m);
+        k_gather_sorted<<<ceil_div(m, kTB), kTB, 0, s>>>(yn, idx, m, ys, ts.perm);
+        WNNC_LAUNCH_CHECK();
+    }
     // coordinate frames of the fixed chunks
     ts.corig = dalloc<float4>(ts.nchunks);
     ts.pos = dalloc<float4>(m);
@@ -911,9 +922,11 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
                                                                    ts.gbl, ts.gbh);
     WNNC_LAUNCH_CHECK();
     WNNC_CUDA(cudaStreamSynchronize(s));
-    pool_free(ys);
-    pool_free(keys);
-    pool_free(idx);
+    if (!reuse) {
+        pool_free(ys);
+        pool_free(keys);
+        pool_free(idx);
+    }
 
     ts.far_off = dalloc<int>(ng + 1);
     int* near_off0 = dalloc<int>(ng + 1);     // merged (uncut) ranges
@@ -1188,7 +1201,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     }
 
     // --- the points as targets: same Morton order as the sources ---
-    build_target_set(t, t.self, xn, n, true, s);
+    build_target_set(t, t.self, xn, n, true, s, perm_tmp);
     pool_free(xn);
     pool_free(idx);
     pool_free(perm_tmp);
