@@ -176,6 +176,19 @@ wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, i
                            int64_t* tnear_entries, int* depth);
 
 /*
+ * How the interaction-list traversal of the tree's own points ran (Alg. 4's
+ * decisions for every target group; either way the lists are the same).  Each
+ * group is first walked breadth first, which writes its far nodes in
+ * ascending id; a group whose walk grows too wide for the per-warp buffer
+ * finishes depth first and has its far list sorted afterwards
+ * (*stack_walk_groups counts them).  If a depth-first walk overflows as well,
+ * every group runs again depth first with a larger buffer and all far lists
+ * are sorted (*big_stack = 1, *stack_walk_groups = 0).  Either output may be
+ * NULL.  Errors: WNNC_EINVAL for a NULL tree.
+ */
+wnnc_status wnnc_tree_walk_stats(const wnnc_tree* tree, int* stack_walk_groups, int* big_stack);
+
+/*
  * Copy the tree's structure to host buffers (any may be NULL), for checking
  * against an independent construction:
  *   perm        int64 [n]        sorted position -> input index

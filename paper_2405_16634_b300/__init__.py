@@ -83,6 +83,7 @@ def lib():
     L.wnnc_get_stats.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
     L.wnnc_tree_info.argtypes = [P] + [POINTER(c_int64)] * 7 + [POINTER(c_int)]
     L.wnnc_tree_export.argtypes = [P] + [P] * 11
+    L.wnnc_tree_walk_stats.argtypes = [P, P, P]
     L.wnnc_profile_enable.argtypes = [P, c_int]
     L.wnnc_profile_read.argtypes = [P, P, P]
     L.wnnc_profile_reset.argtypes = [P]
@@ -104,7 +105,7 @@ def lib():
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
                  "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
                  "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_tree_info",
-                 "wnnc_tree_export", "wnnc_profile_enable", "wnnc_profile_read",
+                 "wnnc_tree_export", "wnnc_tree_walk_stats", "wnnc_profile_enable", "wnnc_profile_read",
                  "wnnc_profile_reset", "wnnc_sync_status", "wnnc_knn16", "wnnc_mlp_create",
                  "wnnc_mlp_free", "wnnc_mlp_set_params", "wnnc_mlp_get_params", "wnnc_mlp_forward",
                  "wnnc_mlp_set_loss", "wnnc_mlp_grad", "wnnc_mlp_train_step", "wnnc_warm_init"):
@@ -261,6 +262,13 @@ class Tree:
         out = {k: x.value for k, x in zip(keys, v)}
         out["depth"] = d.value
         return out
+
+    def walk_stats(self) -> dict:
+        """How the list traversal ran: groups finished as depth-first walks,
+        and whether all groups ran again with the larger buffer."""
+        a, b = c_int(), c_int()
+        _check(lib().wnnc_tree_walk_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return {"stack_walk_groups": a.value, "big_stack": bool(b.value)}
 
     def export(self) -> dict:
         inf = self.info()

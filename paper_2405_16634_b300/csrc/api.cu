@@ -312,6 +312,14 @@ wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, i
     });
 }
 
+wnnc_status wnnc_tree_walk_stats(const wnnc_tree* tree, int* stack_walk_groups, int* big_stack) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (stack_walk_groups) *stack_walk_groups = t.self.walk_stack_groups;
+        if (big_stack) *big_stack = t.self.walk_big_stack;
+    });
+}
+
 wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node_start, int32_t* node_count,
                              int32_t* node_depth, int32_t* node_nchild, int32_t* far_off, int32_t* far_id,
                              int32_t* near_off, int32_t* near_rng, int32_t* group_off,

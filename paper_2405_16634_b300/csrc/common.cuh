@@ -151,6 +151,10 @@ struct TargetSet {
     int2* near_rng = nullptr;     // merged [start,end) source ranges, at most kMaxRange long
     int64_t far_entries = 0, near_ranges = 0;
     int64_t far_pairs = 0, near_pairs = 0;
+    // how the list traversal ran: groups that a first-in first-out walk
+    // finished as stack walks; whether every group ran again as a stack walk
+    // with the larger buffer
+    int walk_stack_groups = 0, walk_big_stack = 0;
     WorkList work;                // items of the gather kernels
 };
 

@@ -136,7 +136,6 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, 
                                                            int shift, const int* offs, int nblocks) {
     __shared__ int whist[kRsWarps][256];
     __shared__ int wbase[kRsWarps][256];
-    __shared__ int dstart[256];
     __shared__ int gbase[256];
     __shared__ int wsum[kRsWarps];
     __shared__ uint64_t skey[kRsTile];
@@ -176,7 +175,6 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, 
         int before = 0;
         for (int w = 0; w < warp; ++w) before += wsum[w];
         const int ds = before + x - tot;
-        dstart[d] = ds;
         gbase[d] = offs[d * nblocks + blockIdx.x] - ds;
         int run = ds;
         for (int w = 0; w < kRsWarps; ++w) {

@@ -434,17 +434,30 @@ __device__ __forceinline__ bool is_far(const double* nlo, const double* nhi, con
 }
 
 constexpr int kTravWarps = 2;
-// Per-warp traversal stack (shared memory).  The smaller stack allows more
-// resident warps; a traversal that overflows it runs again with the larger.
+// Per-warp traversal buffer (shared memory): the first-in first-out walk uses
+// the smaller, which allows more resident warps; a walk that overflows it runs
+// again as a stack walk with the larger.
 constexpr int kStackSmall = 2048;
 constexpr int kStackBig = 4096;
 
 // Warp-cooperative traversal of the octree for one target group, one pass:
 // it writes keys (group<<32 | node) for far entries and (group<<32 | first
-// point) with the leaf id for near leaves, in no particular order (they are
-// sorted afterwards).  Up to 32 nodes are tested at once; children of opened
-// nodes are pushed on a per-warp shared stack whose capacity is checked
-// before a push.  Keys collect in per-warp shared buffers that are flushed to
+// point) with the leaf id for near leaves (sorted by group afterwards).  Up
+// to 32 nodes are tested at once; children of opened nodes go into a per-warp
+// shared buffer whose capacity is checked before a push.
+//
+// FIFO = true: the buffer is a ring visited first-in first-out.  Nodes are
+// numbered level by level, children of one parent consecutively and child
+// blocks in the order of their parents, so a first-in first-out walk from the
+// root visits nodes in ascending id: each group's far nodes are written in
+// ascending order, and a stable sort on the group alone yields the lists
+// sorted by (group, node).  The width of that walk grows with the group's box
+// (a box spanning many cells opens many nodes per level); when fewer than 256
+// free slots (32 nodes x 8 children) remain, the warp finishes its group as a
+// stack walk in the same ring and appends the group to `unsorted`, whose far
+// keys the caller sorts by node afterwards.  FIFO = false: a stack walk
+// (last-in first-out) throughout, whose depth grows far more slowly as theta
+// shrinks; its far keys need the full sort.  Keys collect in per-warp shared buffers that are flushed to
 // global pools, one atomic reservation per flush; past a pool's capacity
 // nothing is written but the pool's counter still counts, so that the caller
 // can size the pools exactly and run the traversal again.
@@ -464,13 +477,13 @@ __device__ __forceinline__ void trav_flush(const uint64_t* buf, const uint32_t* 
     __syncwarp();
 }
 
-template <int STACK>
+template <int STACK, bool FIFO>
 __global__ void __launch_bounds__(32 * kTravWarps)
 k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float4* nhif, const int* ndepth,
            const int* nchild, const int* child0, const int* nstart, const double* glo, const double* ghi, int ng,
            double theta, uint64_t* far_pool, int64_t far_cap, unsigned long long* far_count,
            uint64_t* near_pool, uint32_t* near_vpool, int64_t near_cap, unsigned long long* near_count,
-           int* err) {
+           int* err, uint64_t* unsorted, int* unsorted_count) {
     __shared__ int stack[kTravWarps][STACK];
     __shared__ uint64_t fbuf_all[kTravWarps][kTravBuf];
     __shared__ uint64_t nbuf_all[kTravWarps][kTravBuf];
@@ -493,13 +506,23 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
     uint64_t* fbuf = fbuf_all[wl];
     uint64_t* nbuf = nbuf_all[wl];
     uint32_t* nvbuf = nvbuf_all[wl];
+    static_assert((STACK & (STACK - 1)) == 0, "ring size must be a power of two");
     if (lane == 0) st[0] = 0;
     __syncwarp();
-    int top = 1, fcnt = 0, ncnt = 0;
+    // live entries are [head, head + top) modulo STACK; pushes append at the
+    // end; first-in first-out pops from head, the stack walk from the end
+    int head = 0, top = 1, fcnt = 0, ncnt = 0;
+    bool fifo = FIFO;
     while (top > 0) {
+        if (fifo && top > STACK - 256) {
+            fifo = false;
+            if (lane == 0) unsorted[atomicAdd(unsorted_count, 1)] = (uint64_t)g;
+        }
         int take = min(top, 32);
-        int b = lane < take ? st[top - take + lane] : -1;
+        int b = -1;
+        if (lane < take) b = st[(head + (fifo ? 0 : top - take) + lane) & (STACK - 1)];
         top -= take;
+        if (fifo) head += take;
         __syncwarp();
         bool far = false, leaf = false, open = false;
         if (b >= 0) {
@@ -539,8 +562,8 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
             break;
         }
         if (open) {
-            int c0 = child0[b], p = top + inc - nc;
-            for (int q = 0; q < nc; ++q) st[p + q] = c0 + q;
+            int c0 = child0[b], p = head + top + inc - nc;
+            for (int q = 0; q < nc; ++q) st[(p + q) & (STACK - 1)] = c0 + q;
         }
         top += total;
         __syncwarp();
@@ -853,6 +876,53 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     pool_free(split_off); pool_free(tmp); pool_free(keys);
 }
 
+// Far lists of the groups that a first-in first-out walk finished as stack
+// walks: their keys are sorted by node within each segment.  The segments are
+// copied one after another with compact keys (k << nbits | node), k the
+// group's place in `groups`, sorted, and written back into their own places.
+__global__ void k_seg_sizes(const uint64_t* groups, int nu, const int* far_off, int* sz) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nu) return;
+    const int g = (int)groups[k];
+    sz[k] = far_off[g + 1] - far_off[g];
+}
+__global__ void k_seg_pack(const uint64_t* keys, const uint64_t* groups, const int* far_off, const int* pos,
+                           int nbits, uint64_t* tmp) {
+    const int k = blockIdx.x, g = (int)groups[k];
+    const int e0 = far_off[g], cnt = far_off[g + 1] - e0, p0 = pos[k];
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
+        tmp[p0 + i] = ((uint64_t)k << nbits) | (keys[e0 + i] & 0xffffffffu);
+}
+__global__ void k_seg_unpack(const uint64_t* tmp, const uint64_t* groups, const int* far_off, const int* pos,
+                             int nbits, uint64_t* keys) {
+    const int k = blockIdx.x, g = (int)groups[k];
+    const int e0 = far_off[g], cnt = far_off[g + 1] - e0, p0 = pos[k];
+    const uint64_t low = (uint64_t(1) << nbits) - 1;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
+        keys[e0 + i] = ((uint64_t)g << 32) | (tmp[p0 + i] & low);
+}
+
+static void sort_far_segments(uint64_t* keys, const int* far_off, const uint64_t* groups, int nu, int nbits,
+                              cudaStream_t s) {
+    int* sz = dalloc<int>(nu + 1);
+    int* pos = dalloc<int>(nu + 2);
+    k_seg_sizes<<<ceil_div(nu, kTB), kTB, 0, s>>>(groups, nu, far_off, sz);
+    WNNC_LAUNCH_CHECK();
+    exclusive_scan_i32(sz, pos, nu, s);
+    const int total = read_int(pos + nu, s);
+    if (total > 0) {
+        uint64_t* tmp = dalloc<uint64_t>(total);
+        k_seg_pack<<<nu, 256, 0, s>>>(keys, groups, far_off, pos, nbits, tmp);
+        WNNC_LAUNCH_CHECK();
+        radix_sort_pairs(tmp, nullptr, total, nbits + bits_for(nu), s);
+        k_seg_unpack<<<nu, 256, 0, s>>>(tmp, groups, far_off, pos, nbits, keys);
+        WNNC_LAUNCH_CHECK();
+        pool_free(tmp);
+    }
+    pool_free(sz);
+    pool_free(pos);
+}
+
 void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m, bool self,
                       cudaStream_t s, const int64_t* self_perm) {
     ts.m = m;
@@ -943,7 +1013,8 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         WNNC_LAUNCH_CHECK();
     } else {
         int* leaf_off = dalloc<int>(ng + 1);
-        int* err = dalloc<int>(1);
+        int* err = dalloc<int>(2);        // [0] error flags, [1] groups finished as stack walks
+        uint64_t* unsorted = dalloc<uint64_t>(ng);
         unsigned long long* counts = dalloc<unsigned long long>(2);
         const int tgrid = ceil_div(ng, kTravWarps);
         // pool estimates (per target); a second pass runs with exact sizes if exceeded
@@ -952,34 +1023,40 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         uint64_t* nkeys = nullptr;
         uint32_t* nvals = nullptr;
         int64_t nfar = 0, nleafent = 0;
+        // first the first-in first-out walk (far keys come out sorted within
+        // each group, except the groups it lists as unsorted); if a stack walk
+        // overflows its buffer, everything again as stack walks with the
+        // larger buffer, whose far keys take the full sort
+        int nunsorted = 0;
         bool big_stack = false;
         for (int attempt = 0; attempt < 4; ++attempt) {
             fkeys = dalloc<uint64_t>(far_cap);
             nkeys = dalloc<uint64_t>(near_cap);
             nvals = dalloc<uint32_t>(near_cap);
-            WNNC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+            WNNC_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
             WNNC_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
-#define WNNC_TRAVERSE(STK)                                                                                     \
-    k_traverse<STK><<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_lof, t.node_hif,           \
+#define WNNC_TRAVERSE(STK, FIFO)                                                                               \
+    k_traverse<STK, FIFO><<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_lof, t.node_hif,           \
                                                       t.node_depth, t.node_nchild, t.node_child0,            \
                                                       t.node_start, ts.glo, ts.ghi, ng, theta, fkeys,        \
                                                       far_cap, counts, nkeys, nvals, near_cap, counts + 1,  \
-                                                      err)
-            if (big_stack) WNNC_TRAVERSE(kStackBig); else WNNC_TRAVERSE(kStackSmall);
+                                                      err, unsorted, err + 1)
+            if (big_stack) WNNC_TRAVERSE(kStackBig, false); else WNNC_TRAVERSE(kStackSmall, true);
 #undef WNNC_TRAVERSE
             WNNC_LAUNCH_CHECK();
             unsigned long long hc[2] = {0, 0};
-            int herr = 0;
+            int herr[2] = {0, 0};
             WNNC_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
-            WNNC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            WNNC_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
             WNNC_CUDA(cudaStreamSynchronize(s));
-            if (herr) {
+            nunsorted = herr[1];
+            if (herr[0]) {
                 pool_free(fkeys); pool_free(nkeys); pool_free(nvals);
                 if (!big_stack) {   // again with the larger stack
                     big_stack = true;
                     continue;
                 }
-                pool_free(leaf_off); pool_free(err); pool_free(counts); pool_free(near_off0);
+                pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts); pool_free(near_off0);
                 fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
             }
             nfar = (int64_t)hc[0];
@@ -987,7 +1064,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             if (nfar <= far_cap && nleafent <= near_cap) break;
             if (attempt == 3 || nfar > INT32_MAX || nleafent > INT32_MAX) {
                 pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(leaf_off); pool_free(err);
-                pool_free(counts); pool_free(near_off0);
+                pool_free(unsorted); pool_free(counts); pool_free(near_off0);
                 fail(WNNC_ECAPACITY, "interaction lists too long");
             }
             pool_free(fkeys); pool_free(nkeys); pool_free(nvals);
@@ -995,9 +1072,13 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             near_cap = std::max<int64_t>(nleafent, 1);
         }
         int gbits = bits_for(ng);
-        radix_sort_pairs(fkeys, nullptr, nfar, 32 + gbits, s);
+        radix_sort_pairs(fkeys, nullptr, nfar, 32 + gbits, s, big_stack ? 0 : 32);
         radix_sort_pairs(nkeys, nvals, nleafent, 32 + gbits, s);
         segment_offsets_hi32(fkeys, nfar, ts.far_off, ng, s);
+        if (!big_stack && nunsorted > 0)
+            sort_far_segments(fkeys, ts.far_off, unsorted, nunsorted, bits_for(t.nnodes), s);
+        ts.walk_stack_groups = big_stack ? 0 : nunsorted;
+        ts.walk_big_stack = big_stack ? 1 : 0;
         segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s);
         ts.far_entries = nfar;
         ts.far_id = dalloc<int>(nfar);
@@ -1031,7 +1112,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         WNNC_LAUNCH_CHECK();
         WNNC_CUDA(cudaStreamSynchronize(s));
         pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(head); pool_free(hscan);
-        pool_free(leaf_off); pool_free(err); pool_free(counts);
+        pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts);
     }
     // cut ranges to at most kMaxRange points
     {

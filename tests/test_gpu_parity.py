@@ -75,16 +75,33 @@ def test_library_is_the_cuda_build():
     assert torch.cuda.is_available()
 
 
-@pytest.mark.parametrize("theta", [0.05, 0.3, 0.5, 0.8])
-def test_tree_and_lists_match_oracle_exactly(theta):
-    """Tree, groups and lists bit-exact against the oracle; theta = 0.05 opens
-    nearly every node, deep enough to overflow the traversal's smaller stack
-    and exercise the rerun with the larger one."""
+def _uniform_cube(n, seed):
+    return np.random.default_rng(seed).random((n, 3)).astype(np.float32)
+
+
+# (cloud, theta, traversal path): "bfs" every group breadth first; "mixed"
+# some groups finish depth first and have their far lists sorted afterwards;
+# "big" every group again depth first with the larger buffer.  theta = 0.05
+# opens nearly every node; a uniform cube has large group boxes.
+LIST_CASES = [("union20k", 0.05, "mixed"), ("union20k", 0.3, "bfs"), ("union20k", 0.5, "bfs"),
+              ("union20k", 0.8, "bfs"), ("cube100k", 0.3, "big")]
+
+
+@pytest.mark.parametrize("cloud,theta,path", LIST_CASES)
+def test_tree_and_lists_match_oracle_exactly(cloud, theta, path):
+    """Tree, groups and lists bit-exact against the oracle on every path of
+    the list traversal."""
     W = _wnnc()
-    c = synth.config_cloud("union50k", n=20000)
-    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta)
+    if cloud == "union20k":
+        pts = synth.config_cloud("union50k", n=20000).points
+    else:
+        pts = _uniform_cube(100000, 11)
+    t = W.Tree(torch.from_numpy(pts).cuda(), theta=theta)
+    ws = t.walk_stats()
+    assert ws["big_stack"] == (path == "big")
+    assert (ws["stack_walk_groups"] > 0) == (path == "mixed")
     e = t.export()
-    xn, ctr, s = oracle.normalize(c.points)
+    xn, ctr, s = oracle.normalize(pts)
     assert np.array_equal(e["center_scale"], np.concatenate([ctr, [s]]))
     ot = oracle.Tree(xn, f32(theta))
     assert np.array_equal(e["perm"], ot.perm())
@@ -105,10 +122,10 @@ def test_tree_and_lists_match_oracle_exactly(theta):
     # near: GPU merged ranges cover exactly the oracle's near leaves
     for g in range(0, ng, 7):
         leaves = ni[no[g]:no[g + 1]]
-        cover = np.zeros(len(c.points), bool)
+        cover = np.zeros(len(pts), bool)
         for b in leaves:
             cover[nd["start"][b]:nd["start"][b] + nd["count"][b]] = True
-        gcover = np.zeros(len(c.points), bool)
+        gcover = np.zeros(len(pts), bool)
         for r in e["near_rng"][e["near_off"][g]:e["near_off"][g + 1]]:
             assert not gcover[r[0]:r[1]].any()
             gcover[r[0]:r[1]] = True
