@@ -37,7 +37,7 @@ constexpr int kGatherWarps = 4;
 // Inner-loop unroll depth and minimum resident blocks per SM of the pair
 // kernels (tuning knobs; the defaults are the measured best on B300).
 #ifndef WNNC_UNROLL
-#define WNNC_UNROLL 4
+#define WNNC_UNROLL 8
 #endif
 #ifndef WNNC_GATHER_MINB
 #define WNNC_GATHER_MINB 0
@@ -48,6 +48,11 @@ constexpr int kGatherWarps = 4;
 #define WNNC_GATHER_BOUNDS __launch_bounds__(32 * kGatherWarps)
 #endif
 constexpr int kUnroll = WNNC_UNROLL;
+// targets per lane of the treecode gather (1 or 2)
+#ifndef WNNC_GATHER_TPL
+#define WNNC_GATHER_TPL 2
+#endif
+constexpr int kGatherTPL = WNNC_GATHER_TPL;
 
 // ---------------------------------------------------------------------------
 // Node moments in three launches, with no dependency chain through the whole
@@ -378,10 +383,26 @@ __device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int6
     }
 }
 
-// NB: the near-field bfloat16 study (a template parameter, so that the
-// default kernel carries no trace of it).
-template <int OP, int EPI, bool NB>
+// One warp per work item (a target group's near ranges and far entries).
+// Sources are staged 32 at a time in shared memory, and the loads of the
+// next batch are issued before the current batch is summed, so that their
+// latency overlaps the arithmetic.
+//   * Near sources: the item's ranges (about ten points on average) form one
+//     stream cut into full batches of 32.  Lanes read 32 ranges at once; a
+//     lane finds the range of its stream position by a binary search over the
+//     ranges' prefix sums (shuffles).
+//   * Far entries: the node ids of batch k + 2 and the node data of batch
+//     k + 1 are read while batch k is summed.
+// TPL targets per lane: with TPL = 2, lanes h*16 + k (h = 0, 1) hold targets
+// k and k + 16 of the group and take the staged sources of index h, h + 2,
+// ...; each source load then serves two pair terms, and the two halves' sums
+// are added once per item.  NB: the near-field bfloat16 study (a template
+// parameter, so that the default kernel carries no trace of it).
+template <int OP, int EPI, bool NB, int TPL>
 __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
+    static_assert(TPL == 1 || TPL == 2, "one or two targets per lane");
+    constexpr int kLanesPerStream = 32 / TPL;
+    constexpr unsigned kFull = 0xffffffffu;
     __shared__ float4 sp_all[kGatherWarps][32];
     __shared__ float4 sv_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -392,68 +413,163 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
     const Item item = A.items[it];
     const int g = item.g;
     const int i0 = A.goff[g];
-    const int64_t i = (int64_t)i0 + lane;
-    const bool valid = lane < A.goff[g + 1] - i0;
+    const int gsize = A.goff[g + 1] - i0;
     const float4 o = A.tgorig[g];
-    const float4 t = valid ? shift(A.tcorig[i >> 5], o, A.tpos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 blo = A.tgbl[g], bhi = A.tgbh[g];
-    const float4 tn = NB ? bf16_point(t) : t;   // the target as the near field sees it
-    Acc3 acc;
-
-    // near field: ranges of source points
-    for (int q = item.q0; q < item.q1; ++q) {
-        const int2 r = A.near_rng[q];
-        for (int base = r.x; base < r.y; base += 32) {
-            const int cnt = min(32, r.y - base);
-            bool clear = true;
-            if (lane < cnt) {
-                const int j = base + lane;
-                const float4 p = shift(A.scorig[j >> 5], o, A.spos[j]);
-                clear = box_gap2(blo, bhi, p) >= A.fast2;
-                sp[lane] = NB ? bf16_point(p) : p;
-                if (OP == kOpATpaper) sv[lane] = make_float4(A.sval_s[j], 0.f, 0.f, 0.f);
-                else sv[lane] = A.sval[j];
-            }
-            clear = __all_sync(0xffffffffu, clear);
-            __syncwarp();
-            if (clear) {
-#pragma unroll kUnroll
-                for (int k = 0; k < cnt; ++k) interact<OP, false>(tn, sp[k], sv[k], A.w2, acc);
-            } else {
-#pragma unroll kUnroll
-                for (int k = 0; k < cnt; ++k) interact<OP, true>(tn, sp[k], sv[k], A.w2, acc);
-            }
-            __syncwarp();
-        }
+    const int h = lane / kLanesPerStream;      // source stream of this lane
+    const int tl = lane % kLanesPerStream;
+    float4 t[TPL], tn[TPL];                    // tn: the target as the near field sees it
+    Acc3 acc[TPL];
+#pragma unroll
+    for (int u = 0; u < TPL; ++u) {
+        const int k = tl + u * kLanesPerStream;
+        const int64_t i = (int64_t)i0 + k;
+        t[u] = k < gsize ? shift(A.tcorig[i >> 5], o, A.tpos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        tn[u] = NB ? bf16_point(t[u]) : t[u];
     }
-    // far field: node representatives
-    for (int base = item.f0; base < item.f1; base += 32) {
-        const int cnt = min(32, item.f1 - base);
-        bool clear = true;
-        if (lane < cnt) {
-            const int b = A.far_id[base + lane];
-            const float4 p = shift(A.ncell[b], o, A.nrep[b]);
-            clear = box_gap2(blo, bhi, p) >= A.fast2;
-            sp[lane] = p;
-            sv[lane] = A.nmom[b];
-        }
-        clear = __all_sync(0xffffffffu, clear);
-        __syncwarp();
+    const float4 blo = A.tgbl[g], bhi = A.tgbh[g];
+
+    // the sums of one staged batch of cnt sources against this lane's targets
+    auto sum_batch = [&](int cnt, bool clear, bool near) {
         if (clear) {
 #pragma unroll kUnroll
-            for (int k = 0; k < cnt; ++k) interact<OP, false>(t, sp[k], sv[k], A.w2, acc);
+            for (int k = h; k < cnt; k += TPL) {
+                const float4 p = sp[k], v = sv[k];
+#pragma unroll
+                for (int u = 0; u < TPL; ++u) interact<OP, false>(near ? tn[u] : t[u], p, v, A.w2, acc[u]);
+            }
         } else {
 #pragma unroll kUnroll
-            for (int k = 0; k < cnt; ++k) interact<OP, true>(t, sp[k], sv[k], A.w2, acc);
+            for (int k = h; k < cnt; k += TPL) {
+                const float4 p = sp[k], v = sv[k];
+#pragma unroll
+                for (int u = 0; u < TPL; ++u) interact<OP, true>(near ? tn[u] : t[u], p, v, A.w2, acc[u]);
+            }
         }
+    };
+    // lane < cnt: stage the source held in registers (frame origin c, point p,
+    // value v); returns whether every staged source clears the cut-off radius
+    auto stage = [&](int cnt, const float4& c, const float4& pp, const float4& v, bool near) {
+        bool clear = true;
+        if (lane < cnt) {
+            const float4 p = shift(c, o, pp);
+            clear = box_gap2(blo, bhi, p) >= A.fast2;
+            sp[lane] = (NB && near) ? bf16_point(p) : p;
+            sv[lane] = v;
+        }
+        clear = __all_sync(kFull, clear);
         __syncwarp();
+        return clear;
+    };
+
+    float4 my_c = make_float4(0.f, 0.f, 0.f, 0.f), my_p = my_c, my_v = my_c;
+
+    // ---- near field ----
+    {
+        int qn = item.q0;                 // first range not yet in a window
+        int wx = 0, wpre = 0;             // this lane's range in the window: start, stream offset
+        int wn = 0, wtot = 0, cur = 0;    // ranges in the window, their points, stream position
+        auto next_near = [&]() {
+            int cnt = 0;
+            while (cnt < 32) {
+                if (cur == wtot) {
+                    if (qn >= item.q1) break;
+                    wn = min(32, item.q1 - qn);
+                    int2 r = make_int2(0, 0);
+                    if (lane < wn) r = A.near_rng[qn + lane];
+                    const int len = r.y - r.x;
+                    int inc = len;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int u = __shfl_up_sync(kFull, inc, d);
+                        if (lane >= d) inc += u;
+                    }
+                    wx = r.x;
+                    wpre = inc - len;
+                    wtot = __shfl_sync(kFull, inc, 31);
+                    qn += wn;
+                    cur = 0;
+                    continue;
+                }
+                const int take = min(32 - cnt, wtot - cur);
+                const int x = cur + lane - cnt;           // stream position of this lane's slot
+                int k = 0;                                // last range with wpre <= x
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int c = k + st;
+                    const int pc = __shfl_sync(kFull, wpre, c & 31);
+                    if (c < wn && pc <= x) k = c;
+                }
+                const int rx = __shfl_sync(kFull, wx, k), pk = __shfl_sync(kFull, wpre, k);
+                if (lane >= cnt && lane < cnt + take) {
+                    const int j = rx + (x - pk);
+                    my_p = A.spos[j];
+                    my_c = A.scorig[j >> 5];
+                    if (OP == kOpATpaper) my_v = make_float4(A.sval_s[j], 0.f, 0.f, 0.f);
+                    else my_v = A.sval[j];
+                }
+                cnt += take;
+                cur += take;
+            }
+            return cnt;
+        };
+        int cnt = next_near();
+        while (cnt > 0) {
+            const bool clear = stage(cnt, my_c, my_p, my_v, true);
+            const int cnt_next = next_near();
+            sum_batch(cnt, clear, true);
+            __syncwarp();
+            cnt = cnt_next;
+        }
     }
 
-    acc = combine<OP>(acc);
+    // ---- far field: node representatives ----
+    if (item.f0 < item.f1) {
+        int cnt = min(32, item.f1 - item.f0);
+        if (lane < cnt) {
+            const int b = A.far_id[item.f0 + lane];
+            my_p = A.nrep[b];
+            my_c = A.ncell[b];
+            my_v = A.nmom[b];
+        }
+        int b_next = 0;                   // node ids one batch ahead of the data
+        if (lane < min(32, item.f1 - item.f0 - 32)) b_next = A.far_id[item.f0 + 32 + lane];
+        for (int base = item.f0; base < item.f1; base += 32) {
+            const bool clear = stage(cnt, my_c, my_p, my_v, false);
+            const int cnt_next = min(32, item.f1 - base - 32);   // <= 0 after the last batch
+            if (lane < cnt_next) {
+                my_p = A.nrep[b_next];
+                my_c = A.ncell[b_next];
+                my_v = A.nmom[b_next];
+            }
+            if (lane < min(32, item.f1 - base - 64)) b_next = A.far_id[base + 64 + lane];
+            sum_batch(cnt, clear, false);
+            __syncwarp();
+            cnt = cnt_next;
+        }
+    }
+
+    Acc3 mine = acc[0];
+    if (TPL == 2) {
+        // add the other source stream's sums; lane l then keeps target l
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            acc[u].x += __shfl_xor_sync(kFull, acc[u].x, 16);
+            acc[u].y += __shfl_xor_sync(kFull, acc[u].y, 16);
+            acc[u].z += __shfl_xor_sync(kFull, acc[u].z, 16);
+            acc[u].u += __shfl_xor_sync(kFull, acc[u].u, 16);
+            acc[u].v += __shfl_xor_sync(kFull, acc[u].v, 16);
+            acc[u].q += __shfl_xor_sync(kFull, acc[u].q, 16);
+            acc[u].s += __shfl_xor_sync(kFull, acc[u].s, 16);
+        }
+        mine = h == 0 ? acc[0] : acc[TPL - 1];
+    }
+    mine = combine<OP>(mine);
+    const int64_t i = (int64_t)i0 + lane;
+    const bool valid = lane < gsize;
     if (item.pslot < 0) {
-        gather_epilogue<EPI>(A, g, i, valid, acc, lane);
+        gather_epilogue<EPI>(A, g, i, valid, mine, lane);
     } else {
-        A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(acc.x, acc.y, acc.z, acc.s);
+        A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(mine.x, mine.y, mine.z, mine.s);
     }
 }
 
@@ -892,9 +1008,9 @@ void launch_gather(Tree& t, const GatherArgs& a, cudaStream_t s) {
                  s);
     // the bfloat16 near-field study applies to the sums of A and G only
     if ((OP == kOpA || OP == kOpG || OP == kOpAG) && a.near_bf16)
-        k_gather<OP, EPI, true><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
+        k_gather<OP, EPI, true, kGatherTPL><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
     else
-        k_gather<OP, EPI, false><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
+        k_gather<OP, EPI, false, kGatherTPL><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
     WNNC_LAUNCH_CHECK();
     if (a.nsplit > 0) {
         k_gather_finalize<EPI><<<ceil_div((int64_t)a.nsplit * 32, kTB), kTB, 0, s>>>(a);
