@@ -646,6 +646,11 @@ __device__ __forceinline__ void adj_term(const float4& p, const float4& ti, floa
     az = fmaf(q, dz, az);
 }
 
+// Far part, one warp per work item (a slice of one group's far entries):
+// each lane takes two entries (nodes) of a batch of 64 and sums over the
+// group's targets, staged once in shared memory, so that each target load
+// serves two pair terms.  The node ids of batch k + 2 and the node centroids
+// of batch k + 1 are read while batch k is summed.
 __global__ void WNNC_GATHER_BOUNDS k_adj_far(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -662,27 +667,45 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_far(AdjArgs A) {
     tp[lane] = p;
     const float4 blo = A.gbl[g], bhi = A.gbh[g];
     __syncwarp();
-    for (int base = item.f0; base < item.f1; base += 32) {
-        const int e = base + lane;
-        float4 bp = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool clear = true;
-        if (e < item.f1) {
-            const int b = A.far_id[e];
-            bp = shift(A.ncell[b], o, A.ncent[b]);
-            clear = box_gap2(blo, bhi, bp) >= A.fast2;
-        }
+    // this lane's entries of a batch at `base`: base + lane and base + 32 + lane
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), m0 = c0, c1 = c0, m1 = c0;   // cell origins, centroids
+    int b0 = 0, b1 = 0;
+    {
+        const int e0 = item.f0 + lane, e1 = e0 + 32;
+        if (e0 < item.f1) { const int b = A.far_id[e0]; c0 = A.ncell[b]; m0 = A.ncent[b]; }
+        if (e1 < item.f1) { const int b = A.far_id[e1]; c1 = A.ncell[b]; m1 = A.ncent[b]; }
+        if (e0 + 64 < item.f1) b0 = A.far_id[e0 + 64];
+        if (e1 + 64 < item.f1) b1 = A.far_id[e1 + 64];
+    }
+    for (int base = item.f0; base < item.f1; base += 64) {
+        const int e0 = base + lane, e1 = e0 + 32;
+        const bool v0 = e0 < item.f1, v1 = e1 < item.f1;
+        const float4 bp0 = shift(c0, o, m0), bp1 = shift(c1, o, m1);
+        bool clear = (!v0 || box_gap2(blo, bhi, bp0) >= A.fast2) && (!v1 || box_gap2(blo, bhi, bp1) >= A.fast2);
         clear = __all_sync(0xffffffffu, clear);
-        if (e < item.f1) {
-            float ax = 0.f, ay = 0.f, az = 0.f;
-            if (clear) {
+        // next batch's centroids (ids read one batch earlier), then the ids after it
+        if (e0 + 64 < item.f1) { c0 = A.ncell[b0]; m0 = A.ncent[b0]; }
+        if (e1 + 64 < item.f1) { c1 = A.ncell[b1]; m1 = A.ncent[b1]; }
+        if (e0 + 128 < item.f1) b0 = A.far_id[e0 + 128];
+        if (e1 + 128 < item.f1) b1 = A.far_id[e1 + 128];
+        float ax0 = 0.f, ay0 = 0.f, az0 = 0.f, ax1 = 0.f, ay1 = 0.f, az1 = 0.f;
+        if (clear) {
 #pragma unroll kUnroll
-                for (int k = 0; k < cnt_t; ++k) adj_term<false>(bp, tp[k], A.w2, ax, ay, az);
-            } else {
-#pragma unroll kUnroll
-                for (int k = 0; k < cnt_t; ++k) adj_term<true>(bp, tp[k], A.w2, ax, ay, az);
+            for (int k = 0; k < cnt_t; ++k) {
+                const float4 tk = tp[k];
+                adj_term<false>(bp0, tk, A.w2, ax0, ay0, az0);
+                adj_term<false>(bp1, tk, A.w2, ax1, ay1, az1);
             }
-            A.contrib[e] = make_float4(ax, ay, az, 0.f);
+        } else {
+#pragma unroll kUnroll
+            for (int k = 0; k < cnt_t; ++k) {
+                const float4 tk = tp[k];
+                adj_term<true>(bp0, tk, A.w2, ax0, ay0, az0);
+                adj_term<true>(bp1, tk, A.w2, ax1, ay1, az1);
+            }
         }
+        if (v0) A.contrib[e0] = make_float4(ax0, ay0, az0, 0.f);
+        if (v1) A.contrib[e1] = make_float4(ax1, ay1, az1, 0.f);
     }
 }
 
