@@ -80,6 +80,7 @@ static void alloc_workspace(Tree& t) {
     t.mom_r = dalloc<float4>(nn);
     t.node_rep = dalloc<float4>(nn);
     t.contrib = dalloc<float4>(t.self.far_entries);
+    t.near_contrib = dalloc<float4>(t.near_slots);
     t.vnode = dalloc<float4>(nn);
     t.mom_x = dalloc<float4>(nn);
     if (t.params.moments_fp64) t.dmom = dalloc<double>(8 * (size_t)nn);

@@ -230,9 +230,17 @@ struct Tree {
     int* tfar_ent = nullptr;      // far-entry index (position in self.far_id), grouped by node
     int nach = 0;                 // source chunks of the adjoint near part (kAdjChunk points each)
     int* tnear_off = nullptr;     // [nach+1], per source chunk
-    int2* tnear_ent = nullptr;    // (target group, mask of the chunk's points in its near lists)
+    // per (source chunk, target group): (near slot of the first point of the
+    // chunk in the group's near lists, mask of those points)
+    int2* tnear_ent = nullptr;
     int64_t tnear_entries = 0;
+    // Near slots: the (target group, source point) incidences of the near
+    // lists, numbered group by group along each group's ranges.  rng_slot[q]
+    // is the slot of the first point of near range q.
+    int* rng_slot = nullptr;      // [near_ranges+1]
+    int64_t near_slots = 0;
     WorkList adj_far_work;        // items over the far lists (per target group)
+    WorkList adj_pair_work;       // items over the near ranges (per target group)
     WorkList adj_near_work;       // items over the transposed near entries (per source chunk)
 
     // work buffers (sized at build)
@@ -247,6 +255,7 @@ struct Tree {
     float4* mom_r = nullptr;      // node moments of the step direction r (same layout)
     float4* node_rep = nullptr;   // representative offset from cell centre, per call
     float4* contrib = nullptr;    // per far entry contribution (adjoint)
+    float4* near_contrib = nullptr;   // per near slot contribution (adjoint)
     float4* vnode = nullptr;      // per node far sum (adjoint)
     float4* mom_x = nullptr;      // node weighted offsets (rep_mode 0): sum |nu| (x - cell), -
     double* dmom = nullptr;       // double node sums (moments_fp64), 8 per node

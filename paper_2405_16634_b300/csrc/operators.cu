@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cuda_bf16.h>
 #include <cfloat>
+#include <type_traits>
 #include <utility>
 
 #include "common.cuh"
@@ -617,6 +618,9 @@ struct AdjArgs {
     const float4* ncent;
     float4* contrib;
     const int2* tnear_ent;
+    const int2* near_rng;
+    const int* rng_slot;
+    float4* near_contrib;
     const int* leaf_of;
     const int* nparent;
     const float4* vnode;
@@ -768,43 +772,183 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
     }
 }
 
-// Near part, one warp per work item: a slice of the transposed entries of
-// source chunk C (kAdjChunk = 8 consecutive sorted points).  Lane l handles
-// source point 8C + (l & 7) against every fourth target (offset l >> 3) of
-// each entry's group, if the entry's mask holds the point; the four partial
-// sums of a point are added at the end (fixed order), into lanes 0..7.
-template <int EPI>
-__global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
-    __shared__ float4 tp_all[kGatherWarps][32];
+// Near part, first kernel: target-major pair sums.  One warp per work item
+// (a slice of one target group's near ranges).  Lanes h*16 + k (h = 0, 1)
+// hold targets k and k + 16 of the group (point and s_i).  The item's near
+// sources are staged 32 at a time as in the gather; half-warp h takes sources
+// 8h .. 8h+7 of each 16, and each lane forms, for each of its 8 sources, the
+// sum of its two targets' terms.  A reduce-scatter over the 16 lanes of the
+// half-warp (three halving shuffle stages, then one full stage; no selects)
+// leaves each source's sum over the group's targets in two lanes, one of
+// which writes it to the (group, source) near slot.  The second kernel adds each point's
+// slots in a fixed order.
+__global__ void WNNC_GATHER_BOUNDS k_adj_near_pairs(AdjArgs A) {
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ float4 sp_all[kGatherWarps][32];
+    __shared__ int ss_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
     if (it >= A.nitems) return;
-    float4* tp = tp_all[wl];
+    const Item item = A.items[it];
+    if (item.q0 >= item.q1) return;
+    float4* sp = sp_all[wl];
+    int* ss = ss_all[wl];
+    const int g = item.g;
+    const int i0 = A.goff[g], gsize = A.goff[g + 1] - i0;
+    const float4 o = A.gorig[g];
+    const int h = lane >> 4, tl = lane & 15;
+    // this lane's two targets; past the group: the group's first point with s = 0
+    float4 ta, tb;
+    {
+        const int ka = tl < gsize ? tl : 0, kb = tl + 16 < gsize ? tl + 16 : 0;
+        const int64_t ia = (int64_t)i0 + ka, ib = (int64_t)i0 + kb;
+        ta = shift(A.corig[ia >> 5], o, A.pos[ia]);
+        tb = shift(A.corig[ib >> 5], o, A.pos[ib]);
+        ta.w = tl < gsize ? A.sv[ia] : 0.f;
+        tb.w = tl + 16 < gsize ? A.sv[ib] : 0.f;
+    }
+    const float4 blo = A.gbl[g], bhi = A.gbh[g];
+
+    float4 my_p = make_float4(0.f, 0.f, 0.f, 0.f), my_c = my_p;
+    int my_slot = 0;
+    int qn = item.q0;                 // first range not yet in a window
+    int wx = 0, wpre = 0, wslot = 0;  // this lane's range in the window: start, stream offset, slot
+    int wn = 0, wtot = 0, cur = 0;    // ranges in the window, their points, stream position
+    auto next_near = [&]() {
+        int cnt = 0;
+        while (cnt < 32) {
+            if (cur == wtot) {
+                if (qn >= item.q1) break;
+                wn = min(32, item.q1 - qn);
+                int2 r = make_int2(0, 0);
+                int rs = 0;
+                if (lane < wn) {
+                    r = A.near_rng[qn + lane];
+                    rs = A.rng_slot[qn + lane];
+                }
+                const int len = r.y - r.x;
+                int inc = len;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int u = __shfl_up_sync(kFull, inc, d);
+                    if (lane >= d) inc += u;
+                }
+                wx = r.x;
+                wpre = inc - len;
+                wslot = rs;
+                wtot = __shfl_sync(kFull, inc, 31);
+                qn += wn;
+                cur = 0;
+                continue;
+            }
+            const int take = min(32 - cnt, wtot - cur);
+            const int x = cur + lane - cnt;
+            int k = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int c = k + st;
+                const int pc = __shfl_sync(kFull, wpre, c & 31);
+                if (c < wn && pc <= x) k = c;
+            }
+            const int rx = __shfl_sync(kFull, wx, k), pk = __shfl_sync(kFull, wpre, k);
+            const int rs = __shfl_sync(kFull, wslot, k);
+            if (lane >= cnt && lane < cnt + take) {
+                const int j = rx + (x - pk);
+                my_p = A.pos[j];
+                my_c = A.corig[j >> 5];
+                my_slot = rs + (x - pk);
+            }
+            cnt += take;
+            cur += take;
+        }
+        return cnt;
+    };
+    // one half-warp's 8 sources (staged from `base`) against this lane's two
+    // targets, reduced over the half-warp; the sums go to their near slots.
+    // The lane forms the terms of source base + (k ^ m) in v[k], m = lane
+    // bits 3..1, so that every shuffle stage keeps the lower half of v and
+    // sends the upper half; the lane ends with the sum of source base + m.
+    const int m = (lane >> 1) & 7;
+    auto sum8 = [&](int base, int cnt, auto cut_tag) {
+        constexpr bool CUT = decltype(cut_tag)::value;
+        float v[8][3];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float4 p = sp[base + (k ^ m)];
+            float ax = 0.f, ay = 0.f, az = 0.f;
+            adj_term<CUT>(p, ta, A.w2, ax, ay, az);
+            adj_term<CUT>(p, tb, A.w2, ax, ay, az);
+            v[k][0] = ax;
+            v[k][1] = ay;
+            v[k][2] = az;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[k][c] += __shfl_xor_sync(kFull, v[k + 4][c], 8);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[k][c] += __shfl_xor_sync(kFull, v[k + 2][c], 4);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[0][c] += __shfl_xor_sync(kFull, v[1][c], 2);
+            v[0][c] += __shfl_xor_sync(kFull, v[0][c], 1);
+        }
+        const int src = base + m;
+        if ((lane & 1) == 0 && src < cnt) A.near_contrib[ss[src]] = make_float4(v[0][0], v[0][1], v[0][2], 0.f);
+    };
+
+    int cnt = next_near();
+    while (cnt > 0) {
+        bool clear = true;
+        if (lane < cnt) {
+            const float4 p = shift(my_c, o, my_p);
+            clear = box_gap2(blo, bhi, p) >= A.fast2;
+            sp[lane] = p;
+            ss[lane] = my_slot;
+        }
+        clear = __all_sync(kFull, clear);
+        __syncwarp();
+        const int cnt_next = next_near();
+        for (int sb = 0; sb < cnt; sb += 16) {
+            if (clear) sum8(sb + 8 * h, cnt, std::false_type{});
+            else sum8(sb + 8 * h, cnt, std::true_type{});
+        }
+        __syncwarp();
+        cnt = cnt_next;
+    }
+}
+
+// Near part, second kernel, one warp per work item: a slice of the
+// transposed entries of source chunk C (kAdjChunk = 8 consecutive sorted
+// points).  Lane l handles source point 8C + (l & 7) and every fourth entry
+// (offset l >> 3): if the entry's mask holds the point, it adds the point's
+// near slot of that entry (the entry's slot plus the number of mask bits
+// below the point).  The four partial sums of a point are added at the end
+// (fixed order), into lanes 0..7, followed by the far part and the output.
+template <int EPI>
+__global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x * kGatherWarps + wl;
+    if (it >= A.nitems) return;
     const Item item = A.items[it];
     const int sc = item.g;                       // source chunk (outputs)
     const int sl = lane & (kAdjChunk - 1), tq = lane / kAdjChunk;
     const int64_t j = (int64_t)sc * kAdjChunk + sl;
     const bool valid = j < A.n;
-    const float4 o = A.corig[((int64_t)sc * kAdjChunk) >> 5];   // frame of the chunk's points
-    const float4 xj = valid ? A.pos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const unsigned below = (1u << sl) - 1u;
     float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int q = item.q0; q < item.q1; ++q) {
+#pragma unroll 4
+    for (int q = item.q0 + tq; q < item.q1; q += 32 / kAdjChunk) {
         const int2 ent = A.tnear_ent[q];
-        const int g = ent.x;
         const unsigned mask = (unsigned)ent.y;
-        const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
-        if (lane < cnt_t) {
-            const int64_t i = (int64_t)i0 + lane;
-            float4 p = shift(A.corig[i >> 5], o, A.pos[i]);
-            p.w = A.sv[i];
-            tp[lane] = p;
-        }
-        __syncwarp();
         if ((mask >> sl) & 1u) {
-#pragma unroll 2
-            for (int k = tq; k < cnt_t; k += 32 / kAdjChunk) adj_term<true>(xj, tp[k], A.w2, ax, ay, az);
+            const float4 c = A.near_contrib[ent.x + __popc(mask & below)];
+            ax += c.x;
+            ay += c.y;
+            az += c.z;
         }
-        __syncwarp();
     }
 #pragma unroll
     for (int o2 = kAdjChunk; o2 < 32; o2 <<= 1) {
@@ -1055,6 +1199,9 @@ AdjArgs adj_args(const Tree& t, float w) {
     a.ncent = t.node_cent;
     a.contrib = t.contrib;
     a.tnear_ent = t.tnear_ent;
+    a.near_rng = S.near_rng;
+    a.rng_slot = t.rng_slot;
+    a.near_contrib = t.near_contrib;
     a.leaf_of = t.leaf_of;
     a.nparent = t.node_parent;
     a.vnode = t.vnode;
@@ -1217,6 +1364,14 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
         WNNC_LAUNCH_CHECK();
     } else {
         WNNC_CUDA(cudaMemsetAsync(t.vnode, 0, sizeof(float4) * t.nnodes, s));
+    }
+    if (t.adj_pair_work.nitems > 0) {
+        ProfScope ps(&t.prof, WNNC_PROF_ADJ_NEAR, s);
+        AdjArgs pr = a;
+        pr.items = t.adj_pair_work.items;
+        pr.nitems = t.adj_pair_work.nitems;
+        k_adj_near_pairs<<<ceil_div(pr.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(pr);
+        WNNC_LAUNCH_CHECK();
     }
     a.items = t.adj_near_work.items;
     a.nitems = t.adj_near_work.nitems;

@@ -664,9 +664,17 @@ __global__ void k_tnear_count(const int2* rng, int64_t nr, int* cnt) {
     cnt[q] = r.y > r.x ? (r.y - 1) / kAdjChunk - r.x / kAdjChunk + 1 : 0;
 }
 
+__global__ void k_range_len(const int2* rng, int64_t nr, int* len) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nr) len[q] = rng[q].y - rng[q].x;
+}
+
 // One thread per near range; its group is found by binary search in near_off.
+// Each entry also records the near slot of its first point and its index
+// (the sort's value).
 __global__ void k_tnear_fill(const int2* rng, int64_t nr, const int* near_off, int ng, const int* cnt_off,
-                             uint64_t* keys, uint32_t* masks) {
+                             const int* rng_slot, uint64_t* keys, uint32_t* masks, int* slots,
+                             uint32_t* idx) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nr) return;
     int lo_g = 0, hi_g = ng - 1;   // the last group g with near_off[g] <= q
@@ -683,6 +691,8 @@ __global__ void k_tnear_fill(const int2* rng, int64_t nr, const int* near_off, i
         uint32_t m = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
         keys[p] = ((uint64_t)(uint32_t)sc << 32) | (uint32_t)g;
         masks[p] = m;
+        slots[p] = rng_slot[q] + (sc * kAdjChunk + lo - r.x);
+        idx[p] = (uint32_t)p;
     }
 }
 
@@ -692,15 +702,19 @@ __global__ void k_key_heads(const uint64_t* keys, int64_t n, int* head) {
 }
 
 // Equal (source chunk, target group) keys: OR their masks into one entry.
-__global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* masks, int64_t n,
-                              const int* head_scan, int2* ent, uint64_t* ukeys) {
+// They come from ranges of one group that share the chunk, in range order
+// (the sort is stable), so the first one's slot is the slot of the chunk's
+// first point in the group's near lists, and the chunk's points in those
+// lists hold consecutive slots.
+__global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* idx, const uint32_t* masks,
+                              const int* slots, int64_t n, const int* head_scan, int2* ent, uint64_t* ukeys) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     if (e > 0 && keys[e] == keys[e - 1]) return;
     uint32_t m = 0;
-    for (int64_t f = e; f < n && keys[f] == keys[e]; ++f) m |= masks[f];
+    for (int64_t f = e; f < n && keys[f] == keys[e]; ++f) m |= masks[idx[f]];
     int r = head_scan[e];
-    ent[r] = make_int2((int)(uint32_t)(keys[e] & 0xffffffffu), (int)m);
+    ent[r] = make_int2(slots[idx[e]], (int)m);
     ukeys[r] = keys[e];
 }
 
@@ -1314,6 +1328,16 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     }
     {
         int64_t nr = S.near_ranges;
+        // near slots: lengths of the ranges, scanned (ranges are group-major)
+        int* len = dalloc<int>(nr + 1);
+        t.rng_slot = dalloc<int>(nr + 2);
+        if (nr) {
+            k_range_len<<<ceil_div(nr, kTB), kTB, 0, s>>>(S.near_rng, nr, len);
+            WNNC_LAUNCH_CHECK();
+        }
+        exclusive_scan_i32(len, t.rng_slot, nr, s);
+        t.near_slots = read_int(t.rng_slot + nr, s);
+        pool_free(len);
         int* cnt = dalloc<int>(nr + 1);
         int* coff = dalloc<int>(nr + 2);
         if (nr) {
@@ -1324,11 +1348,14 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         int ne = read_int(coff + nr, s);
         uint64_t* k = dalloc<uint64_t>(ne);
         uint32_t* msk = dalloc<uint32_t>(ne);
+        int* slt = dalloc<int>(ne);
+        uint32_t* idx = dalloc<uint32_t>(ne);
         if (nr) {
-            k_tnear_fill<<<ceil_div(nr, kTB), kTB, 0, s>>>(S.near_rng, nr, S.near_off, ng, coff, k, msk);
+            k_tnear_fill<<<ceil_div(nr, kTB), kTB, 0, s>>>(S.near_rng, nr, S.near_off, ng, coff, t.rng_slot, k,
+                                                          msk, slt, idx);
             WNNC_LAUNCH_CHECK();
         }
-        radix_sort_pairs(k, msk, ne, 32 + bits_for(nach), s, 32);   // groups already ascending
+        radix_sort_pairs(k, idx, ne, 32 + bits_for(nach), s, 32);   // groups already ascending
         int* head = dalloc<int>(ne + 1);
         int* hscan = dalloc<int>(ne + 2);
         if (ne) {
@@ -1341,16 +1368,17 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         t.tnear_ent = dalloc<int2>(nu);
         uint64_t* uk = dalloc<uint64_t>(nu);
         if (ne) {
-            k_tnear_merge<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, msk, ne, hscan, t.tnear_ent, uk);
+            k_tnear_merge<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, idx, msk, slt, ne, hscan, t.tnear_ent, uk);
             WNNC_LAUNCH_CHECK();
         }
         t.tnear_off = dalloc<int>(nach + 1);
         segment_offsets_hi32(uk, nu, t.tnear_off, nach, s);
         WNNC_CUDA(cudaStreamSynchronize(s));
-        pool_free(cnt); pool_free(coff); pool_free(k); pool_free(msk); pool_free(head); pool_free(hscan);
-        pool_free(uk);
+        pool_free(cnt); pool_free(coff); pool_free(k); pool_free(msk); pool_free(slt); pool_free(idx);
+        pool_free(head); pool_free(hscan); pool_free(uk);
     }
     build_work(t.adj_far_work, 2, ng, nullptr, nullptr, S.far_off, false, s);
+    build_work(t.adj_pair_work, 0, ng, S.near_off, S.near_rng, nullptr, false, s);
     build_work(t.adj_near_work, 1, nach, t.tnear_off, nullptr, nullptr, true, s);
 }
 
@@ -1362,11 +1390,13 @@ void free_tree(Tree& t) {
     delete[] t.level_off;
     t.level_off = nullptr;
     free_target_set(t.self);
-    dfree(t.tfar_off); dfree(t.tfar_ent); dfree(t.tnear_off); dfree(t.tnear_ent);
+    dfree(t.tfar_off); dfree(t.tfar_ent); dfree(t.tnear_off); dfree(t.tnear_ent); dfree(t.rng_slot);
+    free_work(t.adj_pair_work);
     free_work(t.adj_far_work);
     free_work(t.adj_near_work);
     dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.g_mu); dfree(t.g_r); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
-    dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.node_rep); dfree(t.contrib); dfree(t.vnode);
+    dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.node_rep); dfree(t.contrib);
+    dfree(t.near_contrib); dfree(t.vnode);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
 

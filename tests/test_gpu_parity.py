@@ -379,10 +379,12 @@ def test_profiler_counts_launches():
     t.profile(True)
     t.iterate(n_iter=2)
     p = t.profile_read()
-    # per iteration: A with G on mu, the exact adjoint, A with G on r, moments of
-    # mu and of r (G of mu + alpha r follows from G(mu) and G(r) by linearity)
+    # per iteration: A with G on mu, the exact adjoint (its near part in two
+    # launches: pair sums into near slots, then each point's slots), A with G
+    # on r, moments of mu and of r (G of mu + alpha r follows from G(mu) and
+    # G(r) by linearity)
     assert p["AG"][0] == 4 and p["A"][0] == 0 and p["G"][0] == 0
-    assert p["adj_near"][0] == 2 and p["moments"][0] == 4
+    assert p["adj_near"][0] == 4 and p["moments"][0] == 4
     assert all(v[1] >= 0 for v in p.values())
     t.profile_reset()
     assert t.profile_read()["AG"] == (0, 0.0)
