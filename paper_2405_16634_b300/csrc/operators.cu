@@ -158,29 +158,45 @@ __global__ void __launch_bounds__(1024) k_mom_top(int nlev, LevelOffsets lv, con
         for (int b = lv.off[d] + threadIdx.x; b < lv.off[d + 1]; b += blockDim.x) {
             if (ncount[b] <= kMomDirect) continue;
             const float4 cp = ncell[b];
+            const int nc = nchild[b], c0 = nchild0[b];
             Acc m[7] = {0, 0, 0, 0, 0, 0, 0};
-            for (int q = 0; q < nchild[b]; ++q) {
-                const int c = nchild0[b] + q;
-                Acc cm[7];
-                if (dmom) {
-                    for (int k = 0; k < 7; ++k) cm[k] = (Acc)dmom[8 * (int64_t)c + k];
-                } else {
-                    const float4 mm = mom[c];
-                    cm[0] = mm.x; cm[1] = mm.y; cm[2] = mm.z; cm[3] = mm.w;
-                    if (WEIGHTED) {
-                        const float4 xx = momx[c];
-                        cm[4] = xx.x; cm[5] = xx.y; cm[6] = xx.z;
-                    } else {
-                        cm[4] = cm[5] = cm[6] = 0;
-                    }
+            if (!dmom && !WEIGHTED) {
+                // all children's sums loaded first (one round trip), then
+                // added in child order; absent children add exact zeros
+                float4 mm[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) mm[q] = q < nc ? mom[c0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    m[0] += mm[q].x;
+                    m[1] += mm[q].y;
+                    m[2] += mm[q].z;
+                    m[3] += mm[q].w;
                 }
-                for (int k = 0; k < 4; ++k) m[k] += cm[k];
-                if (WEIGHTED) {
-                    // re-centre the child's weighted offsets on this node's cell
-                    const float4 cc = ncell[c];
-                    m[4] += cm[4] + cm[3] * (Acc)(cc.x - cp.x);
-                    m[5] += cm[5] + cm[3] * (Acc)(cc.y - cp.y);
-                    m[6] += cm[6] + cm[3] * (Acc)(cc.z - cp.z);
+            } else {
+                for (int q = 0; q < nc; ++q) {
+                    const int c = c0 + q;
+                    Acc cm[7];
+                    if (dmom) {
+                        for (int k = 0; k < 7; ++k) cm[k] = (Acc)dmom[8 * (int64_t)c + k];
+                    } else {
+                        const float4 mm = mom[c];
+                        cm[0] = mm.x; cm[1] = mm.y; cm[2] = mm.z; cm[3] = mm.w;
+                        if (WEIGHTED) {
+                            const float4 xx = momx[c];
+                            cm[4] = xx.x; cm[5] = xx.y; cm[6] = xx.z;
+                        } else {
+                            cm[4] = cm[5] = cm[6] = 0;
+                        }
+                    }
+                    for (int k = 0; k < 4; ++k) m[k] += cm[k];
+                    if (WEIGHTED) {
+                        // re-centre the child's weighted offsets on this node's cell
+                        const float4 cc = ncell[c];
+                        m[4] += cm[4] + cm[3] * (Acc)(cc.x - cp.x);
+                        m[5] += cm[5] + cm[3] * (Acc)(cc.y - cp.y);
+                        m[6] += cm[6] + cm[3] * (Acc)(cc.z - cp.z);
+                    }
                 }
             }
             mom_store<WEIGHTED, Acc>(b, ncent, mom, momx, rep, dmom, m);

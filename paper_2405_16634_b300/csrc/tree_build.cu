@@ -164,27 +164,39 @@ __device__ __forceinline__ int first_digit_ge(const uint64_t* keys, int s, int e
     return lo;
 }
 
+// One level of the octree: eight threads per node, thread q finding by binary
+// search the first point of the node whose digit at this depth is > q (the
+// end of child q's range), all eight searches at once; a node splits if it
+// holds more than leaf_size points and is above the maximum depth.  bnd[8i+q]
+// keeps the ends for k_split_write; nkids[i] counts the non-empty children.
 __global__ void k_split_count(const uint64_t* keys, const int* start, const int* count, int base,
-                              int m, int depth, int leaf_size, int max_depth, int* nkids) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    int b = base + i;
-    int s = start[b], c = count[b];
-    int nk = 0;
-    if (c > leaf_size && depth < max_depth) {
-        int prev = s;
-        for (int q = 1; q <= 8; ++q) {
-            int p = q < 8 ? first_digit_ge(keys, prev, s + c, depth, q) : s + c;
-            if (p > prev) ++nk;
-            prev = p;
-        }
+                              int m, int depth, int leaf_size, int max_depth, int* nkids, int* bnd) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t >> 3), q = (int)(t & 7);
+    const unsigned lane = threadIdx.x & 31u;
+    const bool act = i < m;
+    int s = 0, e = 0;
+    bool split = false;
+    if (act) {
+        const int b = base + i;
+        s = start[b];
+        e = s + count[b];
+        split = count[b] > leaf_size && depth < max_depth;
     }
-    nkids[i] = nk;
+    int p = e;
+    if (split && q < 7) p = first_digit_ge(keys, s, e, depth, q + 1);
+    int pp = __shfl_up_sync(0xffffffffu, p, 1, 8);   // the end of child q - 1
+    if (q == 0) pp = s;
+    const unsigned nonempty = __ballot_sync(0xffffffffu, split && p > pp);
+    if (act) {
+        bnd[(int64_t)8 * i + q] = p;
+        if (q == 0) nkids[i] = __popc((nonempty >> (lane & ~7u)) & 0xffu);
+    }
 }
 
-__global__ void k_split_write(const uint64_t* keys, int* start, int* count, int* parent,
-                              int* child0, int* nchild, int* ndepth, int base, int m, int depth,
-                              int next_base, const int* koff, const int* nkids) {
+__global__ void k_split_write(int* start, int* count, int* parent, int* child0, int* nchild, int* ndepth,
+                              int base, int m, int depth, int next_base, const int* koff, const int* nkids,
+                              const int* bnd) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int b = base + i;
@@ -197,10 +209,9 @@ __global__ void k_split_write(const uint64_t* keys, int* start, int* count, int*
     int c0 = next_base + koff[i];
     child0[b] = c0;
     nchild[b] = nk;
-    int s = start[b], e = s + count[b];
-    int prev = s, w = 0;
-    for (int q = 1; q <= 8; ++q) {
-        int p = q < 8 ? first_digit_ge(keys, prev, e, depth, q) : e;
+    int prev = start[b], w = 0;
+    for (int q = 0; q < 8; ++q) {
+        const int p = bnd[(int64_t)8 * i + q];
         if (p > prev) {
             int c = c0 + w++;
             start[c] = prev;
@@ -1224,16 +1235,17 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     int base = 0, m = 1, depth = 0, total_nodes = 1;
     int* nkids = dalloc<int>(n + 1);
     int* koff = dalloc<int>(n + 2);
+    int* bnd = dalloc<int>(8 * (size_t)(n + 1));   // child range ends; a level holds at most n nodes
     while (m > 0) {
-        k_split_count<<<ceil_div(m, kTB), kTB, 0, s>>>(t.keys, t.node_start, t.node_count, base, m, depth,
-                                                      P.leaf_size, P.max_depth, nkids);
+        k_split_count<<<ceil_div((int64_t)8 * m, kTB), kTB, 0, s>>>(t.keys, t.node_start, t.node_count, base, m,
+                                                                   depth, P.leaf_size, P.max_depth, nkids, bnd);
         WNNC_LAUNCH_CHECK();
         exclusive_scan_i32(nkids, koff, m, s);
         int nnext = read_int(koff + m, s);
         grow_nodes(t, cap, total_nodes + nnext);
-        k_split_write<<<ceil_div(m, kTB), kTB, 0, s>>>(t.keys, t.node_start, t.node_count, t.node_parent,
-                                                      t.node_child0, t.node_nchild, t.node_depth, base, m,
-                                                      depth, total_nodes, koff, nkids);
+        k_split_write<<<ceil_div(m, kTB), kTB, 0, s>>>(t.node_start, t.node_count, t.node_parent, t.node_child0,
+                                                      t.node_nchild, t.node_depth, base, m, depth, total_nodes,
+                                                      koff, nkids, bnd);
         WNNC_LAUNCH_CHECK();
         base = total_nodes;
         total_nodes += nnext;
@@ -1244,6 +1256,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         }
     }
     pool_free(nkids);
+    pool_free(bnd);
     pool_free(koff);
     t.nnodes = total_nodes;
     t.nlevels = (int)level_off.size() - 1;
