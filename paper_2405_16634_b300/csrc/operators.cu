@@ -566,19 +566,23 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
     }
 
     Acc3 mine = acc[0];
-    if (TPL == 2) {
+    if (TPL > 1) {
         // add the other source stream's sums; lane l then keeps target l
 #pragma unroll
-        for (int u = 0; u < TPL; ++u) {
-            acc[u].x += __shfl_xor_sync(kFull, acc[u].x, 16);
-            acc[u].y += __shfl_xor_sync(kFull, acc[u].y, 16);
-            acc[u].z += __shfl_xor_sync(kFull, acc[u].z, 16);
-            acc[u].u += __shfl_xor_sync(kFull, acc[u].u, 16);
-            acc[u].v += __shfl_xor_sync(kFull, acc[u].v, 16);
-            acc[u].q += __shfl_xor_sync(kFull, acc[u].q, 16);
-            acc[u].s += __shfl_xor_sync(kFull, acc[u].s, 16);
-        }
-        mine = h == 0 ? acc[0] : acc[TPL - 1];
+        for (int u = 0; u < TPL; ++u)
+#pragma unroll
+            for (int x = kLanesPerStream; x < 32; x <<= 1) {
+                acc[u].x += __shfl_xor_sync(kFull, acc[u].x, x);
+                acc[u].y += __shfl_xor_sync(kFull, acc[u].y, x);
+                acc[u].z += __shfl_xor_sync(kFull, acc[u].z, x);
+                acc[u].u += __shfl_xor_sync(kFull, acc[u].u, x);
+                acc[u].v += __shfl_xor_sync(kFull, acc[u].v, x);
+                acc[u].q += __shfl_xor_sync(kFull, acc[u].q, x);
+                acc[u].s += __shfl_xor_sync(kFull, acc[u].s, x);
+            }
+#pragma unroll
+        for (int u = 1; u < TPL; ++u)
+            if (h == u) mine = acc[u];
     }
     mine = combine<OP>(mine);
     const int64_t i = (int64_t)i0 + lane;
