@@ -8,8 +8,8 @@ iterations of Alg. 3 (moments, A, A^T, grad step, G + rescale).  Inputs are
 resident in HBM when the timed region starts; L2 is flushed (a 256 MiB write)
 before every step.  `value` is whole-job WNNC iterations/s.  The JSON line also
 reports interactions/s, the fraction of FP32 peak, the roofline of the
-dominant kernel (the G treecode sum, timed live with the library's CUDA-event
-profiler on its launch stream), an end-to-end number through the public API
+dominant kernel (the fused A+G treecode gather, timed live with the library's
+CUDA-event profiler on its launch stream), an end-to-end number through the public API
 from pinned host buffers, the CPU oracle as a baseline, and SM clocks sampled
 during the timed region.
 
@@ -129,16 +129,38 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def dist_setup():
+def dist_setup(backend: str | None = None):
+    """(dist or None, world size, rank, local rank) from the launcher's
+    environment; the process group uses NCCL where CUDA is present, else gloo."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
         return dist, world, rank, local
     return None, 1, 0, 0
+
+
+def max_over_ranks(dist, x: float) -> float:
+    """The largest x over all ranks (the job ends with its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, iters_per_step: int, steps: int, ms: float) -> float:
+    """Iterations/s of the whole job: every rank solves its own cloud in the
+    same (slowest-rank) time."""
+    return world * iters_per_step * steps / (ms / 1e3)
 
 
 def make_cloud(rank: int):
@@ -252,13 +274,9 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = ev_a.elapsed_time(ev_b)
-    if dist:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(dist, ev_a.elapsed_time(ev_b))
     ms_per_step = ms / args.steps
-    value = world * N_ITER * args.steps / (ms / 1e3)
+    value = whole_job_rate(world, N_ITER, args.steps, ms)
 
     # ---- end to end through the public API, pinned host buffers ----
     e2e = None
@@ -275,8 +293,8 @@ def run_gpu(args):
             h_mu.copy_(mu, non_blocking=True)
             tr.close()
         torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
-        e2e = {"value": world * N_ITER * args.steps / dt, "unit": "iter/s",
+        dt = max_over_ranks(dist, time.perf_counter() - t0)
+        e2e = {"value": whole_job_rate(world, N_ITER, args.steps, 1e3 * dt), "unit": "iter/s",
                "h2d_bytes_per_step": int(h_pts.numel() * 4),
                "d2h_bytes_per_step": int(h_mu.numel() * 4)}
 
