@@ -231,6 +231,11 @@ enum {
     WNNC_PROF_CLASSES = 8
 };
 wnnc_status wnnc_profile_enable(wnnc_tree* tree, int enable);
+/* Restrict the recording to the classes whose bit is set in mask (bit k:
+ * class k above); the default is every class.  Each recorded launch group
+ * costs two events on its stream, so a caller timing a long run can record
+ * only the class it needs.  Errors: WNNC_EINVAL for a NULL tree. */
+wnnc_status wnnc_profile_classes(wnnc_tree* tree, unsigned mask);
 wnnc_status wnnc_profile_read(wnnc_tree* tree, int64_t* launches, double* total_ms);
 wnnc_status wnnc_profile_reset(wnnc_tree* tree);
 

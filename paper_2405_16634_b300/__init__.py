@@ -85,6 +85,7 @@ def lib():
     L.wnnc_tree_export.argtypes = [P] + [P] * 11
     L.wnnc_tree_walk_stats.argtypes = [P, P, P]
     L.wnnc_profile_enable.argtypes = [P, c_int]
+    L.wnnc_profile_classes.argtypes = [P, ctypes.c_uint]
     L.wnnc_profile_read.argtypes = [P, P, P]
     L.wnnc_profile_reset.argtypes = [P]
     L.wnnc_sync_status.argtypes = [P, P]
@@ -105,7 +106,7 @@ def lib():
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
                  "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
                  "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_tree_info",
-                 "wnnc_tree_export", "wnnc_tree_walk_stats", "wnnc_profile_enable", "wnnc_profile_read",
+                 "wnnc_tree_export", "wnnc_tree_walk_stats", "wnnc_profile_enable", "wnnc_profile_classes", "wnnc_profile_read",
                  "wnnc_profile_reset", "wnnc_sync_status", "wnnc_knn16", "wnnc_mlp_create",
                  "wnnc_mlp_free", "wnnc_mlp_set_params", "wnnc_mlp_get_params", "wnnc_mlp_forward",
                  "wnnc_mlp_set_loss", "wnnc_mlp_grad", "wnnc_mlp_train_step", "wnnc_warm_init"):
@@ -288,7 +289,11 @@ class Tree:
         a["near_rng"] = a["near_rng"][:inf["near_ranges"]]
         return a
 
-    def profile(self, enable: bool = True):
+    def profile(self, enable: bool = True, classes=None):
+        """Record per-class kernel times (CUDA events); `classes` (names of
+        PROF_CLASSES) restricts the recording, None records every class."""
+        mask = 0xFFFFFFFF if classes is None else sum(1 << PROF_CLASSES.index(c) for c in classes)
+        _check(lib().wnnc_profile_classes(self._h, mask))
         _check(lib().wnnc_profile_enable(self._h, int(bool(enable))))
 
     def profile_read(self) -> dict:

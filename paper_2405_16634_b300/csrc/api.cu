@@ -356,6 +356,13 @@ wnnc_status wnnc_profile_enable(wnnc_tree* tree, int enable) {
     });
 }
 
+wnnc_status wnnc_profile_classes(wnnc_tree* tree, unsigned mask) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        t.prof.mask = mask;
+    });
+}
+
 wnnc_status wnnc_profile_read(wnnc_tree* tree, int64_t* launches, double* total_ms) {
     return guarded([&] {
         Tree& t = unwrap(tree);

@@ -163,6 +163,7 @@ struct TargetSet {
 // ---------------------------------------------------------------------------
 struct Profiler {
     bool on = false;
+    unsigned mask = ~0u;  // classes recorded while on (bit k: class k)
     struct Rec {
         int cls;
         cudaEvent_t a, b;

@@ -566,23 +566,19 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
     }
 
     Acc3 mine = acc[0];
-    if (TPL > 1) {
+    if (TPL == 2) {
         // add the other source stream's sums; lane l then keeps target l
 #pragma unroll
-        for (int u = 0; u < TPL; ++u)
-#pragma unroll
-            for (int x = kLanesPerStream; x < 32; x <<= 1) {
-                acc[u].x += __shfl_xor_sync(kFull, acc[u].x, x);
-                acc[u].y += __shfl_xor_sync(kFull, acc[u].y, x);
-                acc[u].z += __shfl_xor_sync(kFull, acc[u].z, x);
-                acc[u].u += __shfl_xor_sync(kFull, acc[u].u, x);
-                acc[u].v += __shfl_xor_sync(kFull, acc[u].v, x);
-                acc[u].q += __shfl_xor_sync(kFull, acc[u].q, x);
-                acc[u].s += __shfl_xor_sync(kFull, acc[u].s, x);
-            }
-#pragma unroll
-        for (int u = 1; u < TPL; ++u)
-            if (h == u) mine = acc[u];
+        for (int u = 0; u < TPL; ++u) {
+            acc[u].x += __shfl_xor_sync(kFull, acc[u].x, 16);
+            acc[u].y += __shfl_xor_sync(kFull, acc[u].y, 16);
+            acc[u].z += __shfl_xor_sync(kFull, acc[u].z, 16);
+            acc[u].u += __shfl_xor_sync(kFull, acc[u].u, 16);
+            acc[u].v += __shfl_xor_sync(kFull, acc[u].v, 16);
+            acc[u].q += __shfl_xor_sync(kFull, acc[u].q, 16);
+            acc[u].s += __shfl_xor_sync(kFull, acc[u].s, 16);
+        }
+        mine = h == 0 ? acc[0] : acc[TPL - 1];
     }
     mine = combine<OP>(mine);
     const int64_t i = (int64_t)i0 + lane;
@@ -1278,7 +1274,7 @@ Profiler::~Profiler() {
 }
 
 ProfScope::ProfScope(Profiler* p_, int cls_, cudaStream_t s_) : p(p_), cls(cls_), s(s_) {
-    if (p && p->on) {
+    if (p && p->on && ((p->mask >> cls) & 1u)) {
         a = p->get();
         b = p->get();
         cudaEventRecord(a, s);

@@ -388,6 +388,12 @@ def test_profiler_counts_launches():
     assert all(v[1] >= 0 for v in p.values())
     t.profile_reset()
     assert t.profile_read()["AG"] == (0, 0.0)
+    # recording restricted to one class
+    t.profile(True, classes=["AG"])
+    t.iterate(n_iter=2)
+    p = t.profile_read()
+    assert p["AG"][0] == 4 and p["AG"][1] > 0
+    assert all(v == (0, 0.0) for k, v in p.items() if k != "AG")
 
 
 @pytest.mark.gpu
