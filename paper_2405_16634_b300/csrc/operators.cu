@@ -303,6 +303,49 @@ __device__ __forceinline__ void interact(const float4& t, const float4& sp, cons
     }
 }
 
+// Two targets' accumulators of the fused A and G sums, packed in float2
+// halves (.x: first target, .y: second), for the paired FP32 instructions of
+// sm_100 and later (two lanes of FP32 work per issued instruction).
+struct Acc2 {
+    float2 x = {0.f, 0.f}, y = {0.f, 0.f}, z = {0.f, 0.f};
+    float2 u = {0.f, 0.f}, v = {0.f, 0.f}, q = {0.f, 0.f};
+    float2 s = {0.f, 0.f};
+};
+
+// The fused A and G pair term of interact<kOpAG, CUT> for two targets at
+// once: (ntx, nty, ntz) are the targets' negated coordinates.  The same
+// operations in the same order as the scalar form, so each half is
+// bit-identical to it.
+template <bool CUT>
+__device__ __forceinline__ void interact2_ag(const float2& ntx, const float2& nty, const float2& ntz,
+                                             const float4& sp, const float4& sv, float w2, Acc2& a) {
+    const float2 dx = __fadd2_rn(make_float2(sp.x, sp.x), ntx);
+    const float2 dy = __fadd2_rn(make_float2(sp.y, sp.y), nty);
+    const float2 dz = __fadd2_rn(make_float2(sp.z, sp.z), ntz);
+    float2 r2 = __fmul2_rn(dz, dz);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dx, dx, r2);
+    float2 ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (CUT) {
+        ir.x = (r2.x >= w2) ? ir.x : 0.f;
+        ir.y = (r2.y >= w2) ? ir.y : 0.f;
+    }
+    const float2 ir2 = __fmul2_rn(ir, ir);
+    const float2 ir3 = __fmul2_rn(ir2, ir);
+    const float2 vx = make_float2(sv.x, sv.x), vy = make_float2(sv.y, sv.y), vz = make_float2(sv.z, sv.z);
+    float2 dm = __fmul2_rn(dz, vz);
+    dm = __ffma2_rn(dy, vy, dm);
+    dm = __ffma2_rn(dx, vx, dm);
+    const float2 k5 = __fmul2_rn(__fmul2_rn(dm, ir2), ir3);
+    a.s = __ffma2_rn(dm, ir3, a.s);
+    a.x = __ffma2_rn(vx, ir3, a.x);
+    a.y = __ffma2_rn(vy, ir3, a.y);
+    a.z = __ffma2_rn(vz, ir3, a.z);
+    a.u = __ffma2_rn(dx, k5, a.u);
+    a.v = __ffma2_rn(dy, k5, a.v);
+    a.q = __ffma2_rn(dz, k5, a.q);
+}
+
 // Shift a point stored in chunk frame `c` into the frame with origin `o`
 // (both origins are multiples of 2^-12, so the shift is exact).
 __device__ __forceinline__ float4 shift(const float4& c, const float4& o, const float4& p) {
@@ -444,9 +487,27 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
         tn[u] = NB ? bf16_point(t[u]) : t[u];
     }
     const float4 blo = A.tgbl[g], bhi = A.tgbh[g];
+    // fused A and G with two targets per lane: paired FP32 instructions
+    constexpr bool kPack = TPL == 2 && OP == kOpAG;
+    Acc2 acc2;
+    const float2 ntx = make_float2(-t[0].x, -t[TPL - 1].x), nty = make_float2(-t[0].y, -t[TPL - 1].y),
+                 ntz = make_float2(-t[0].z, -t[TPL - 1].z);
+    const float2 nnx = make_float2(-tn[0].x, -tn[TPL - 1].x), nny = make_float2(-tn[0].y, -tn[TPL - 1].y),
+                 nnz = make_float2(-tn[0].z, -tn[TPL - 1].z);
 
     // the sums of one staged batch of cnt sources against this lane's targets
     auto sum_batch = [&](int cnt, bool clear, bool near) {
+        if (kPack) {
+            const float2 &ax = near ? nnx : ntx, &ay = near ? nny : nty, &az = near ? nnz : ntz;
+            if (clear) {
+#pragma unroll kUnroll
+                for (int k = h; k < cnt; k += TPL) interact2_ag<false>(ax, ay, az, sp[k], sv[k], A.w2, acc2);
+            } else {
+#pragma unroll kUnroll
+                for (int k = h; k < cnt; k += TPL) interact2_ag<true>(ax, ay, az, sp[k], sv[k], A.w2, acc2);
+            }
+            return;
+        }
         if (clear) {
 #pragma unroll kUnroll
             for (int k = h; k < cnt; k += TPL) {
@@ -565,6 +626,18 @@ __global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
         }
     }
 
+    if (kPack) {
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            acc[u].x = u == 0 ? acc2.x.x : acc2.x.y;
+            acc[u].y = u == 0 ? acc2.y.x : acc2.y.y;
+            acc[u].z = u == 0 ? acc2.z.x : acc2.z.y;
+            acc[u].u = u == 0 ? acc2.u.x : acc2.u.y;
+            acc[u].v = u == 0 ? acc2.v.x : acc2.v.y;
+            acc[u].q = u == 0 ? acc2.q.x : acc2.q.y;
+            acc[u].s = u == 0 ? acc2.s.x : acc2.s.y;
+        }
+    }
     Acc3 mine = acc[0];
     if (TPL == 2) {
         // add the other source stream's sums; lane l then keeps target l
