@@ -739,6 +739,28 @@ __device__ __forceinline__ void adj_term(const float4& p, const float4& ti, floa
     az = fmaf(q, dz, az);
 }
 
+// Two adjoint terms at once with paired FP32 instructions (one point
+// against two targets, (tx, ty, tz) the targets' negated coordinates, tw
+// their s): the same operations and order as adj_term in each half.  Returns
+// the two terms' factors q and offsets d through the references.
+template <bool CUT>
+__device__ __forceinline__ void adj_term2(const float2& px, const float2& py, const float2& pz, const float2& tx,
+                                          const float2& ty, const float2& tz, const float2& tw, float w2,
+                                          float2& dx, float2& dy, float2& dz, float2& q) {
+    dx = __fadd2_rn(px, tx);
+    dy = __fadd2_rn(py, ty);
+    dz = __fadd2_rn(pz, tz);
+    float2 r2 = __fmul2_rn(dz, dz);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dx, dx, r2);
+    float2 ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (CUT) {
+        ir.x = (r2.x >= w2) ? ir.x : 0.f;
+        ir.y = (r2.y >= w2) ? ir.y : 0.f;
+    }
+    q = __fmul2_rn(tw, __fmul2_rn(__fmul2_rn(ir, ir), ir));
+}
+
 // Far part, one warp per work item (a slice of one group's far entries):
 // each lane takes two entries (nodes) of a batch of 64 and sums over the
 // group's targets, staged once in shared memory, so that each target load
@@ -958,18 +980,23 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_near_pairs(AdjArgs A) {
     // bits 3..1, so that every shuffle stage keeps the lower half of v and
     // sends the upper half; the lane ends with the sum of source base + m.
     const int m = (lane >> 1) & 7;
+    // the two targets in the halves of float2 (paired FP32 instructions)
+    const float2 ntx = make_float2(-ta.x, -tb.x), nty = make_float2(-ta.y, -tb.y), ntz = make_float2(-ta.z, -tb.z);
+    const float2 tw = make_float2(ta.w, tb.w);
     auto sum8 = [&](int base, int cnt, auto cut_tag) {
         constexpr bool CUT = decltype(cut_tag)::value;
         float v[8][3];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const float4 p = sp[base + (k ^ m)];
-            float ax = 0.f, ay = 0.f, az = 0.f;
-            adj_term<CUT>(p, ta, A.w2, ax, ay, az);
-            adj_term<CUT>(p, tb, A.w2, ax, ay, az);
-            v[k][0] = ax;
-            v[k][1] = ay;
-            v[k][2] = az;
+            float2 dx, dy, dz, q;
+            adj_term2<CUT>(make_float2(p.x, p.x), make_float2(p.y, p.y), make_float2(p.z, p.z), ntx, nty, ntz, tw,
+                           A.w2, dx, dy, dz, q);
+            // the first target's term, then the second's added by one fma
+            // (the order of adj_term applied to both)
+            v[k][0] = fmaf(q.y, dx.y, q.x * dx.x);
+            v[k][1] = fmaf(q.y, dy.y, q.x * dy.x);
+            v[k][2] = fmaf(q.y, dz.y, q.x * dz.x);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
