@@ -40,14 +40,14 @@ constexpr int kGatherWarps = 4;
 #ifndef WNNC_UNROLL
 #define WNNC_UNROLL 8
 #endif
+// The treecode gather and the far adjoint sums run with at least 6 resident
+// blocks per SM (the register cap that measured fastest; a few bytes spill in
+// the gather); the other pair kernels take the registers they need.
 #ifndef WNNC_GATHER_MINB
-#define WNNC_GATHER_MINB 0
+#define WNNC_GATHER_MINB 6
 #endif
-#if WNNC_GATHER_MINB > 0
-#define WNNC_GATHER_BOUNDS __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB)
-#else
 #define WNNC_GATHER_BOUNDS __launch_bounds__(32 * kGatherWarps)
-#endif
+#define WNNC_CAPPED_BOUNDS __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB)
 constexpr int kUnroll = WNNC_UNROLL;
 // targets per lane of the treecode gather (1 or 2)
 #ifndef WNNC_GATHER_TPL
@@ -459,7 +459,7 @@ __device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int6
 // are added once per item.  NB: the near-field bfloat16 study (a template
 // parameter, so that the default kernel carries no trace of it).
 template <int OP, int EPI, bool NB, int TPL>
-__global__ void WNNC_GATHER_BOUNDS k_gather(GatherArgs A) {
+__global__ void WNNC_CAPPED_BOUNDS k_gather(GatherArgs A) {
     static_assert(TPL == 1 || TPL == 2, "one or two targets per lane");
     constexpr int kLanesPerStream = 32 / TPL;
     constexpr unsigned kFull = 0xffffffffu;
@@ -766,7 +766,7 @@ __device__ __forceinline__ void adj_term2(const float2& px, const float2& py, co
 // group's targets, staged once in shared memory, so that each target load
 // serves two pair terms.  The node ids of batch k + 2 and the node centroids
 // of batch k + 1 are read while batch k is summed.
-__global__ void WNNC_GATHER_BOUNDS k_adj_far(AdjArgs A) {
+__global__ void WNNC_CAPPED_BOUNDS k_adj_far(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
