@@ -779,7 +779,7 @@ __global__ void WNNC_CAPPED_BOUNDS k_adj_far(AdjArgs A) {
     const float4 o = A.gorig[g];
     float4 p = lane < cnt_t ? shift(A.corig[i >> 5], o, A.pos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
     p.w = lane < cnt_t ? A.sv[i] : 0.f;
-    tp[lane] = p;
+    tp[lane] = make_float4(-p.x, -p.y, -p.z, p.w);   // negated: the paired terms add them
     const float4 blo = A.gbl[g], bhi = A.gbh[g];
     __syncwarp();
     // this lane's entries of a batch at `base`: base + lane and base + 32 + lane
@@ -803,24 +803,27 @@ __global__ void WNNC_CAPPED_BOUNDS k_adj_far(AdjArgs A) {
         if (e1 + 64 < item.f1) { c1 = A.ncell[b1]; m1 = A.ncent[b1]; }
         if (e0 + 128 < item.f1) b0 = A.far_id[e0 + 128];
         if (e1 + 128 < item.f1) b1 = A.far_id[e1 + 128];
-        float ax0 = 0.f, ay0 = 0.f, az0 = 0.f, ax1 = 0.f, ay1 = 0.f, az1 = 0.f;
+        // the two entries' sums in the halves of float2 (paired FP32 instructions)
+        const float2 px = make_float2(bp0.x, bp1.x), py = make_float2(bp0.y, bp1.y), pz = make_float2(bp0.z, bp1.z);
+        float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+        auto term = [&](const float4& tk, auto cut_tag) {
+            constexpr bool CUT = decltype(cut_tag)::value;
+            float2 dx, dy, dz, q;
+            adj_term2<CUT>(px, py, pz, make_float2(tk.x, tk.x), make_float2(tk.y, tk.y), make_float2(tk.z, tk.z),
+                           make_float2(tk.w, tk.w), A.w2, dx, dy, dz, q);
+            ax = __ffma2_rn(q, dx, ax);
+            ay = __ffma2_rn(q, dy, ay);
+            az = __ffma2_rn(q, dz, az);
+        };
         if (clear) {
 #pragma unroll kUnroll
-            for (int k = 0; k < cnt_t; ++k) {
-                const float4 tk = tp[k];
-                adj_term<false>(bp0, tk, A.w2, ax0, ay0, az0);
-                adj_term<false>(bp1, tk, A.w2, ax1, ay1, az1);
-            }
+            for (int k = 0; k < cnt_t; ++k) term(tp[k], std::false_type{});
         } else {
 #pragma unroll kUnroll
-            for (int k = 0; k < cnt_t; ++k) {
-                const float4 tk = tp[k];
-                adj_term<true>(bp0, tk, A.w2, ax0, ay0, az0);
-                adj_term<true>(bp1, tk, A.w2, ax1, ay1, az1);
-            }
+            for (int k = 0; k < cnt_t; ++k) term(tp[k], std::true_type{});
         }
-        if (v0) A.contrib[e0] = make_float4(ax0, ay0, az0, 0.f);
-        if (v1) A.contrib[e1] = make_float4(ax1, ay1, az1, 0.f);
+        if (v0) A.contrib[e0] = make_float4(ax.x, ay.x, az.x, 0.f);
+        if (v1) A.contrib[e1] = make_float4(ax.y, ay.y, az.y, 0.f);
     }
 }
 
