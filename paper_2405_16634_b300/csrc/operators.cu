@@ -312,13 +312,12 @@ struct Acc2 {
     float2 s = {0.f, 0.f};
 };
 
-// The fused A and G pair term of interact<kOpAG, CUT> for two targets at
-// once: (ntx, nty, ntz) are the targets' negated coordinates.  The same
-// operations in the same order as the scalar form, so each half is
-// bit-identical to it.
-template <bool CUT>
-__device__ __forceinline__ void interact2_ag(const float2& ntx, const float2& nty, const float2& ntz,
-                                             const float4& sp, const float4& sv, float w2, Acc2& a) {
+// The pair term of interact<OP, CUT> for two targets at once: (ntx, nty,
+// ntz) are the targets' negated coordinates.  The same operations in the same
+// order as the scalar form, so each half is bit-identical to it.
+template <int OP, bool CUT>
+__device__ __forceinline__ void interact2(const float2& ntx, const float2& nty, const float2& ntz,
+                                          const float4& sp, const float4& sv, float w2, Acc2& a) {
     const float2 dx = __fadd2_rn(make_float2(sp.x, sp.x), ntx);
     const float2 dy = __fadd2_rn(make_float2(sp.y, sp.y), nty);
     const float2 dz = __fadd2_rn(make_float2(sp.z, sp.z), ntz);
@@ -330,20 +329,35 @@ __device__ __forceinline__ void interact2_ag(const float2& ntx, const float2& nt
         ir.x = (r2.x >= w2) ? ir.x : 0.f;
         ir.y = (r2.y >= w2) ? ir.y : 0.f;
     }
-    const float2 ir2 = __fmul2_rn(ir, ir);
-    const float2 ir3 = __fmul2_rn(ir2, ir);
-    const float2 vx = make_float2(sv.x, sv.x), vy = make_float2(sv.y, sv.y), vz = make_float2(sv.z, sv.z);
-    float2 dm = __fmul2_rn(dz, vz);
-    dm = __ffma2_rn(dy, vy, dm);
-    dm = __ffma2_rn(dx, vx, dm);
-    const float2 k5 = __fmul2_rn(__fmul2_rn(dm, ir2), ir3);
-    a.s = __ffma2_rn(dm, ir3, a.s);
-    a.x = __ffma2_rn(vx, ir3, a.x);
-    a.y = __ffma2_rn(vy, ir3, a.y);
-    a.z = __ffma2_rn(vz, ir3, a.z);
-    a.u = __ffma2_rn(dx, k5, a.u);
-    a.v = __ffma2_rn(dy, k5, a.v);
-    a.q = __ffma2_rn(dz, k5, a.q);
+    const float2 vx = make_float2(sv.x, sv.x);
+    if (OP == kOpA) {
+        const float2 ir3 = __fmul2_rn(__fmul2_rn(ir, ir), ir);
+        const float2 vy = make_float2(sv.y, sv.y), vz = make_float2(sv.z, sv.z);
+        float2 dm = __fmul2_rn(dz, vz);
+        dm = __ffma2_rn(dy, vy, dm);
+        dm = __ffma2_rn(dx, vx, dm);
+        a.x = __ffma2_rn(dm, ir3, a.x);
+    } else if (OP == kOpG || OP == kOpAG) {
+        const float2 ir2 = __fmul2_rn(ir, ir);
+        const float2 ir3 = __fmul2_rn(ir2, ir);
+        const float2 vy = make_float2(sv.y, sv.y), vz = make_float2(sv.z, sv.z);
+        float2 dm = __fmul2_rn(dz, vz);
+        dm = __ffma2_rn(dy, vy, dm);
+        dm = __ffma2_rn(dx, vx, dm);
+        const float2 k5 = __fmul2_rn(__fmul2_rn(dm, ir2), ir3);
+        if (OP == kOpAG) a.s = __ffma2_rn(dm, ir3, a.s);
+        a.x = __ffma2_rn(vx, ir3, a.x);
+        a.y = __ffma2_rn(vy, ir3, a.y);
+        a.z = __ffma2_rn(vz, ir3, a.z);
+        a.u = __ffma2_rn(dx, k5, a.u);
+        a.v = __ffma2_rn(dy, k5, a.v);
+        a.q = __ffma2_rn(dz, k5, a.q);
+    } else {   // paper-mode A^T: -s d / r^3
+        const float2 q = __fmul2_rn(make_float2(-sv.x, -sv.x), __fmul2_rn(__fmul2_rn(ir, ir), ir));
+        a.x = __ffma2_rn(q, dx, a.x);
+        a.y = __ffma2_rn(q, dy, a.y);
+        a.z = __ffma2_rn(q, dz, a.z);
+    }
 }
 
 // Shift a point stored in chunk frame `c` into the frame with origin `o`
@@ -487,8 +501,8 @@ __global__ void WNNC_CAPPED_BOUNDS k_gather(GatherArgs A) {
         tn[u] = NB ? bf16_point(t[u]) : t[u];
     }
     const float4 blo = A.tgbl[g], bhi = A.tgbh[g];
-    // fused A and G with two targets per lane: paired FP32 instructions
-    constexpr bool kPack = TPL == 2 && OP == kOpAG;
+    // two targets per lane: paired FP32 instructions
+    constexpr bool kPack = TPL == 2;
     Acc2 acc2;
     const float2 ntx = make_float2(-t[0].x, -t[TPL - 1].x), nty = make_float2(-t[0].y, -t[TPL - 1].y),
                  ntz = make_float2(-t[0].z, -t[TPL - 1].z);
@@ -501,10 +515,10 @@ __global__ void WNNC_CAPPED_BOUNDS k_gather(GatherArgs A) {
             const float2 &ax = near ? nnx : ntx, &ay = near ? nny : nty, &az = near ? nnz : ntz;
             if (clear) {
 #pragma unroll kUnroll
-                for (int k = h; k < cnt; k += TPL) interact2_ag<false>(ax, ay, az, sp[k], sv[k], A.w2, acc2);
+                for (int k = h; k < cnt; k += TPL) interact2<OP, false>(ax, ay, az, sp[k], sv[k], A.w2, acc2);
             } else {
 #pragma unroll kUnroll
-                for (int k = h; k < cnt; k += TPL) interact2_ag<true>(ax, ay, az, sp[k], sv[k], A.w2, acc2);
+                for (int k = h; k < cnt; k += TPL) interact2<OP, true>(ax, ay, az, sp[k], sv[k], A.w2, acc2);
             }
             return;
         }
