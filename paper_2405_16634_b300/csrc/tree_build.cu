@@ -594,6 +594,8 @@ __global__ void k_all_near(int ng, int n, int* near_off, int2* rng) {
     if (g < ng) rng[g] = make_int2(0, n);
 }
 
+__global__ void k_set_i32(int* p, int v) { *p = v; }
+
 __global__ void k_low32(const uint64_t* keys, int64_t n, int* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (int)(uint32_t)(keys[i] & 0xffffffffu);
@@ -832,6 +834,13 @@ __global__ void k_item_permute(const Item* in, const uint64_t* keys, int n, Item
 // Host orchestration
 // ---------------------------------------------------------------------------
 
+// Temporaries go back to the pool in the order of its stream: no wait is
+// needed before pool_free when that stream is s (every build entry point
+// sets it so).
+static void wait_before_free(cudaStream_t s) {
+    if (alloc_stream() != s) WNNC_CUDA(cudaStreamSynchronize(s));
+}
+
 static int read_int(const int* dptr, cudaStream_t s) {
     int v = 0;
     WNNC_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -896,7 +905,7 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     w.items = dalloc<Item>(w.nitems);
     k_item_permute<<<ceil_div(w.nitems, kTB), kTB, 0, s>>>(tmp, keys, w.nitems, w.items);
     WNNC_LAUNCH_CHECK();
-    WNNC_CUDA(cudaStreamSynchronize(s));
+    wait_before_free(s);
     pool_free(cnt); pool_free(slots); pool_free(item_off); pool_free(slot_off); pool_free(flag);
     pool_free(split_off); pool_free(tmp); pool_free(keys);
 }
@@ -999,7 +1008,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         ts.goff = dalloc<int>(ts.ngroups + 1);
         k_run_goff<<<ceil_div(nruns, kTB), kTB, 0, s>>>(run_start, nruns, m, roff, ts.goff);
         WNNC_LAUNCH_CHECK();
-        WNNC_CUDA(cudaStreamSynchronize(s));
+        wait_before_free(s);
         pool_free(cut); pool_free(cscan); pool_free(run_start); pool_free(rcnt); pool_free(roff);
     } else {
         ts.ngroups = ts.nchunks;
@@ -1016,7 +1025,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     k_group_boxes<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(ys, ts.goff, ng, ts.glo, ts.ghi, ts.gorig,
                                                                    ts.gbl, ts.gbh);
     WNNC_LAUNCH_CHECK();
-    WNNC_CUDA(cudaStreamSynchronize(s));
+    wait_before_free(s);
     if (!reuse) {
         pool_free(ys);
         pool_free(keys);
@@ -1118,12 +1127,9 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             k_near_heads<<<ceil_div(nleafent, kTB), kTB, 0, s>>>(nkeys, nvals, nleafent, t.node_count, head);
             WNNC_LAUNCH_CHECK();
         }
-        {
-            // sentinel head[n] = 1 so that the last entry closes its range
-            int one = 1;
-            WNNC_CUDA(cudaMemcpyAsync(head + nleafent, &one, sizeof(int), cudaMemcpyHostToDevice, s));
-            WNNC_CUDA(cudaStreamSynchronize(s));
-        }
+        // sentinel head[n] = 1 so that the last entry closes its range
+        k_set_i32<<<1, 1, 0, s>>>(head + nleafent, 1);
+        WNNC_LAUNCH_CHECK();
         exclusive_scan_i32(head, hscan, nleafent + 1, s);
         nr0 = read_int(hscan + nleafent, s);   // heads among the real entries
         rng0 = dalloc<int2>(nr0);
@@ -1135,7 +1141,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         // range offsets per group = number of heads before the group's first leaf entry
         k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(hscan, leaf_off, ng + 1, near_off0);
         WNNC_LAUNCH_CHECK();
-        WNNC_CUDA(cudaStreamSynchronize(s));
+        wait_before_free(s);
         pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(head); pool_free(hscan);
         pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts);
     }
@@ -1157,7 +1163,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         ts.near_off = dalloc<int>(ng + 1);
         k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(off, near_off0, ng + 1, ts.near_off);
         WNNC_LAUNCH_CHECK();
-        WNNC_CUDA(cudaStreamSynchronize(s));
+        wait_before_free(s);
         pool_free(cnt); pool_free(off); pool_free(rng0); pool_free(near_off0);
     }
     unsigned long long* pc = dalloc<unsigned long long>(2);
@@ -1285,7 +1291,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
                                                         t.node_nchild, sum, t.nnodes, t.node_cell,
                                                         t.node_cent, t.leaf_of);
     WNNC_LAUNCH_CHECK();
-    WNNC_CUDA(cudaStreamSynchronize(s));
+    wait_before_free(s);
     pool_free(sum);
     {
         std::vector<int> nc(t.nnodes), cnt(t.nnodes);
@@ -1336,7 +1342,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             WNNC_LAUNCH_CHECK();
         }
         segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
-        WNNC_CUDA(cudaStreamSynchronize(s));
+        wait_before_free(s);
         pool_free(k);
     }
     {
@@ -1386,7 +1392,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         }
         t.tnear_off = dalloc<int>(nach + 1);
         segment_offsets_hi32(uk, nu, t.tnear_off, nach, s);
-        WNNC_CUDA(cudaStreamSynchronize(s));
+        wait_before_free(s);
         pool_free(cnt); pool_free(coff); pool_free(k); pool_free(msk); pool_free(slt); pool_free(idx);
         pool_free(head); pool_free(hscan); pool_free(uk);
     }
