@@ -56,11 +56,12 @@ constexpr int kUnroll = WNNC_UNROLL;
 constexpr int kGatherTPL = WNNC_GATHER_TPL;
 
 // ---------------------------------------------------------------------------
-// Node moments in three launches, with no dependency chain through the whole
+// Node moments in two launches, with no dependency chain through the whole
 // tree:
 //   1. one thread per node of at most kMomSmall points sums its point range;
 //   2. one warp per node of up to kMomDirect points sums its range
-//      (lane-strided, then a fixed xor reduction);
+//      (lane-strided, then a fixed xor reduction); classes 1 and 2 share a
+//      launch;
 //   3. one block adds the few larger nodes (the top levels) from their
 //      children, deepest level first, in child order.
 //   mom[b]  = (sum nu, sum |nu|)        (nu = mu: 3 components; nu = s: 1)
@@ -105,10 +106,10 @@ __device__ __forceinline__ void mom_store(int b, const float4* ncent, float4* mo
 }
 
 template <bool SCALAR, bool WEIGHTED, class Acc>
-__global__ void k_mom_small(int nnodes, const int* nstart, const int* ncount, const float4* ncell,
-                            const float4* ncent, const float4* spos, const float4* scorig, const float4* nu_vec,
-                            const float* nu_s, float4* mom, float4* momx, float4* rep, double* dmom) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void mom_small(int b, int nnodes, const int* nstart, const int* ncount,
+                                          const float4* ncell, const float4* ncent, const float4* spos,
+                                          const float4* scorig, const float4* nu_vec, const float* nu_s,
+                                          float4* mom, float4* momx, float4* rep, double* dmom) {
     if (b >= nnodes) return;
     const int cnt = ncount[b];
     if (cnt > kMomSmall) return;
@@ -121,12 +122,11 @@ __global__ void k_mom_small(int nnodes, const int* nstart, const int* ncount, co
 }
 
 template <bool SCALAR, bool WEIGHTED, class Acc>
-__global__ void k_mom_direct(int nmid, const int* mid, const int* nstart, const int* ncount, const float4* ncell,
-                             const float4* ncent, const float4* spos, const float4* scorig,
-                             const float4* nu_vec, const float* nu_s, float4* mom, float4* momx, float4* rep,
-                             double* dmom) {
-    const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void mom_direct(int k, int lane, int nmid, const int* mid, const int* nstart,
+                                           const int* ncount, const float4* ncell, const float4* ncent,
+                                           const float4* spos, const float4* scorig, const float4* nu_vec,
+                                           const float* nu_s, float4* mom, float4* momx, float4* rep,
+                                           double* dmom) {
     if (k >= nmid) return;
     const int b = mid[k];
     const int cnt = ncount[b];
@@ -143,6 +143,24 @@ __global__ void k_mom_direct(int nmid, const int* mid, const int* nstart, const 
         for (int o = 16; o > 0; o >>= 1) m[c] += __shfl_xor_sync(0xffffffffu, m[c], o);
     }
     if (lane == 0) mom_store<WEIGHTED, Acc>(b, ncent, mom, momx, rep, dmom, m);
+}
+
+// Classes 1 and 2 in one launch: blocks [0, grid_m) take the warp class
+// (warp per node of the mid list), the rest the thread class.
+template <bool SCALAR, bool WEIGHTED, class Acc>
+__global__ void k_mom_sums(int nnodes, int nmid, int grid_m, const int* mid, const int* nstart,
+                           const int* ncount, const float4* ncell, const float4* ncent, const float4* spos,
+                           const float4* scorig, const float4* nu_vec, const float* nu_s, float4* mom,
+                           float4* momx, float4* rep, double* dmom) {
+    if ((int)blockIdx.x < grid_m) {
+        const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+        mom_direct<SCALAR, WEIGHTED, Acc>(k, threadIdx.x & 31, nmid, mid, nstart, ncount, ncell, ncent, spos,
+                                          scorig, nu_vec, nu_s, mom, momx, rep, dmom);
+    } else {
+        const int b = (int)((blockIdx.x - grid_m) * blockDim.x + threadIdx.x);
+        mom_small<SCALAR, WEIGHTED, Acc>(b, nnodes, nstart, ncount, ncell, ncent, spos, scorig, nu_vec, nu_s,
+                                         mom, momx, rep, dmom);
+    }
 }
 
 struct LevelOffsets {
@@ -1416,17 +1434,10 @@ void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, flo
     for (int L = 0; L <= t.mom_top_levels && L <= t.nlevels && L < 17; ++L) lv.off[L] = t.level_off[L];
 #define WNNC_MOM_SUMS(SC, WE, ACC, DM)                                                                    \
     do {                                                                                                  \
-        k_mom_small<SC, WE, ACC><<<grid_s, kTB, 0, s>>>(t.nnodes, t.node_start, t.node_count, t.node_cell, \
-                                                        t.node_cent, t.self.pos, t.self.corig, nu_vec,    \
-                                                        nu_s, out, t.mom_x, t.node_rep, DM);              \
+        k_mom_sums<SC, WE, ACC><<<grid_m + grid_s, kTB, 0, s>>>(                                          \
+            t.nnodes, t.nmom_mid, grid_m, t.mom_mid, t.node_start, t.node_count, t.node_cell, t.node_cent,  \
+            t.self.pos, t.self.corig, nu_vec, nu_s, out, t.mom_x, t.node_rep, DM);                        \
         WNNC_LAUNCH_CHECK();                                                                              \
-        if (t.nmom_mid > 0) {                                                                             \
-            k_mom_direct<SC, WE, ACC><<<grid_m, kTB, 0, s>>>(t.nmom_mid, t.mom_mid, t.node_start,         \
-                                                             t.node_count, t.node_cell, t.node_cent,      \
-                                                             t.self.pos, t.self.corig, nu_vec, nu_s, out, \
-                                                             t.mom_x, t.node_rep, DM);                    \
-            WNNC_LAUNCH_CHECK();                                                                          \
-        }                                                                                                 \
         if (t.mom_top_levels > 0) {                                                                       \
             k_mom_top<WE, ACC><<<1, 1024, 0, s>>>(t.mom_top_levels, lv, t.node_count, t.node_nchild,      \
                                                   t.node_child0, t.node_cell, t.node_cent, out, t.mom_x,  \

@@ -596,6 +596,14 @@ __global__ void k_all_near(int ng, int n, int* near_off, int2* rng) {
 
 __global__ void k_set_i32(int* p, int v) { *p = v; }
 
+__global__ void k_gather_tot3(const int* a, const int* b, const int* c, int* out) {
+    if (threadIdx.x == 0) {
+        out[0] = *a;
+        out[1] = *b;
+        out[2] = *c;
+    }
+}
+
 __global__ void k_low32(const uint64_t* keys, int64_t n, int* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (int)(uint32_t)(keys[i] & 0xffffffffu);
@@ -890,9 +898,19 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     k_split_flags<<<ceil_div(nseg, kTB), kTB, 0, s>>>(cnt, nseg, flag);
     WNNC_LAUNCH_CHECK();
     exclusive_scan_i32(flag, split_off, nseg, s);
-    w.nitems = read_int(item_off + nseg, s);
-    w.nslots = partials ? read_int(slot_off + nseg, s) : 0;
-    w.nsplit = partials ? read_int(split_off + nseg, s) : 0;
+    {
+        // the three totals in one copy (one wait)
+        int* tot = dalloc<int>(3);
+        k_gather_tot3<<<1, 32, 0, s>>>(item_off + nseg, slot_off + nseg, split_off + nseg, tot);
+        WNNC_LAUNCH_CHECK();
+        int h[3] = {0, 0, 0};
+        WNNC_CUDA(cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, s));
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        pool_free(tot);
+        w.nitems = h[0];
+        w.nslots = partials ? h[1] : 0;
+        w.nsplit = partials ? h[2] : 0;
+    }
     Item* tmp = dalloc<Item>(w.nitems);
     w.splits = dalloc<int4>(w.nsplit);
     k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cap, cnt, item_off,
