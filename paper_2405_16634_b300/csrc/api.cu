@@ -86,6 +86,8 @@ static void alloc_workspace(Tree& t) {
     if (t.params.moments_fp64) t.dmom = dalloc<double>(8 * (size_t)nn);
     t.partials = dalloc<double>(3 * (size_t)std::max(std::max(t.self.ngroups, t.self.nchunks), t.nach));
     t.red = dalloc<double>(3 * 256);
+    t.red_ticket = dalloc<unsigned>(1);
+    WNNC_CUDA(cudaMemsetAsync(t.red_ticket, 0, sizeof(unsigned), alloc_stream()));
     t.part_slots = std::max(t.self.work.nslots, t.adj_near_work.nslots);
     t.part_acc = dalloc<float4>((size_t)t.part_slots * 32);
     t.scalars = dalloc<double>(4);

@@ -112,13 +112,14 @@ struct Item {
     int f0, f1;     // far entries [f0, f1)
     int pslot;      // partial-sum slot if the group is cut into several items, else -1
     int cost;       // lane-slots
-    int pad;
+    int split;      // the group's record in splits if pslot >= 0, else -1
 };
 
 struct WorkList {
     Item* items = nullptr;
     int nitems = 0;
     int4* splits = nullptr;     // (group, first slot, number of parts, -) of cut groups
+    unsigned* split_cnt = nullptr;  // per cut group: parts finished (the last one finishes the group)
     int nsplit = 0;
     int nslots = 0;
     int cap = 0;                // the item cap of this list (lane-slots)
@@ -262,6 +263,7 @@ struct Tree {
     double* dmom = nullptr;       // double node sums (moments_fp64), 8 per node
     double* partials = nullptr;   // per-group partial sums (3 x max(ngroups, nchunks, nach))
     double* red = nullptr;        // first-stage sums of the partials (3 x 256)
+    unsigned* red_ticket = nullptr;   // blocks of the first stage done (the last one finishes)
     float4* part_acc = nullptr;   // scratch: partial sums of cut groups, 32 per slot
     int part_slots = 0;
     double* scalars = nullptr;    // device scalars: [0]=E [1]=rr [2]=qq [3]=alpha

@@ -243,6 +243,7 @@ struct GatherArgs {
     const Item* items;
     int nitems;
     const int4* splits;
+    unsigned* split_cnt;
     int nsplit;
     float4* part_acc;
     // targets
@@ -475,6 +476,22 @@ __device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int6
     }
 }
 
+// A group cut into several work items: each item stores its part (one
+// float4 per lane), and the item that finishes last adds all parts in order
+// (part 0 first) and runs the group's epilogue.  Returns true in the warp of
+// that item.  Each lane fences its store before lane 0 counts the part in; the
+// last item resets the counter for the next launch.
+__device__ __forceinline__ bool last_part(unsigned* cnt, int split, int nparts, int lane) {
+    __threadfence();
+    __syncwarp();
+    unsigned tk = 0;
+    if (lane == 0) tk = atomicAdd(cnt + split, 1u);
+    tk = __shfl_sync(0xffffffffu, tk, 0);
+    const bool last = tk == (unsigned)nparts - 1u;
+    if (last && lane == 0) cnt[split] = 0u;
+    return last;
+}
+
 // One warp per work item (a target group's near ranges and far entries).
 // Sources are staged 32 at a time in shared memory, and the loads of the
 // next batch are issued before the current batch is summed, so that their
@@ -696,6 +713,8 @@ __global__ void WNNC_CAPPED_BOUNDS k_gather(GatherArgs A) {
 }
 
 // Groups cut into several items: add the parts in order, then the epilogue.
+// (A separate launch: finishing a group inside the gather by its last item
+// cost the gather more under its register cap than the launch it saves.)
 template <int EPI>
 __global__ void k_gather_finalize(GatherArgs A) {
     const int sidx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -726,6 +745,7 @@ struct AdjArgs {
     const Item* items;
     int nitems;
     const int4* splits;
+    unsigned* split_cnt;
     int nsplit;
     float4* part_acc;
     int64_t n;
@@ -1111,22 +1131,16 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
         adj_epilogue<EPI>(A, sc, j, valid && lane < kAdjChunk, ax, ay, az, lane);
     } else {
         A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(ax, ay, az, 0.f);
+        const int4 sp = A.splits[item.split];
+        if (last_part(A.split_cnt, item.split, sp.z, lane)) {
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+            for (int p = 0; p < sp.z; ++p) {
+                const float4 v = __ldcg(A.part_acc + (int64_t)(sp.y + p) * 32 + lane);
+                sx += v.x; sy += v.y; sz += v.z;
+            }
+            adj_epilogue<EPI>(A, sc, j, valid && lane < kAdjChunk, sx, sy, sz, lane);
+        }
     }
-}
-
-template <int EPI>
-__global__ void k_adj_near_finalize(AdjArgs A) {
-    const int sidx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (sidx >= A.nsplit) return;
-    const int4 sp = A.splits[sidx];
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int p = 0; p < sp.z; ++p) {
-        const float4 v = A.part_acc[(int64_t)(sp.y + p) * 32 + lane];
-        ax += v.x; ay += v.y; az += v.z;
-    }
-    const int64_t j = (int64_t)sp.x * kAdjChunk + (lane & (kAdjChunk - 1));
-    adj_epilogue<EPI>(A, sp.x, j, j < A.n && lane < kAdjChunk, ax, ay, az, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1167,9 +1181,16 @@ __global__ void k_normalize_queries(const float* q, int64_t m, double cx, double
 // fraction of the FP32 rate, so one block alone is slow for 10^4-10^5
 // partials).  The order depends only on the sizes.
 constexpr int kRedBlocks = 256;
+// The three sums of the step length (E = |s|^2, |r|^2, |A r|^2) from the
+// per-group partials: each of kRedBlocks blocks sums a fixed slice, and the
+// block that finishes last adds the kRedBlocks block sums in index order
+// (the same tree as a separate one-block pass) and sets
+// alpha = |r|^2 / |A r|^2 (0 if |A r| = 0; a non-finite alpha sets the error
+// flag).  The ticket counts finished blocks and is reset by the last one.
 __global__ void k_reduce3(const double* a0, int n0, const double* a1, int n1, const double* a2, int n2,
-                          double* out) {
+                          double* out, double* scalars, float* stats, float w, int* err, unsigned* ticket) {
     __shared__ double sh[3][kTB];
+    __shared__ bool last;
     const double* arr[3] = {a0, a1, a2};
     const int n[3] = {n0, n1, n2};
 #pragma unroll
@@ -1186,20 +1207,17 @@ __global__ void k_reduce3(const double* a0, int n0, const double* a1, int n1, co
             for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int c = 0; c < 3; ++c) out[c * kRedBlocks + blockIdx.x] = sh[c][0];
-}
-
-__global__ void k_finalize_alpha(const double* pE, int nE, const double* prr, int nrr, const double* pqq,
-                                 int nqq, double* scalars, float* stats, float w, int* err) {
-    __shared__ double sh[3][1024];
-    double e = 0, rr = 0, qq = 0;
-    for (int k = threadIdx.x; k < nE; k += blockDim.x) e += pE[k];
-    for (int k = threadIdx.x; k < nrr; k += blockDim.x) rr += prr[k];
-    for (int k = threadIdx.x; k < nqq; k += blockDim.x) qq += pqq[k];
-    sh[0][threadIdx.x] = e;
-    sh[1][threadIdx.x] = rr;
-    sh[2][threadIdx.x] = qq;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == kRedBlocks - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // second stage (one block, kTB = kRedBlocks threads: one block sum each)
+    static_assert(kTB == kRedBlocks, "one block sum per thread");
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] = __ldcg(out + c * kRedBlocks + threadIdx.x);
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s)
@@ -1207,7 +1225,7 @@ __global__ void k_finalize_alpha(const double* pE, int nE, const double* prr, in
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double E = sh[0][0], R = sh[1][0], Q = sh[2][0];
+        const double E = sh[0][0], R = sh[1][0], Q = sh[2][0];
         double alpha = Q > 0.0 ? R / Q : 0.0;
         if (!isfinite(alpha)) {
             atomicOr(err, kErrNonFinite);
@@ -1223,6 +1241,7 @@ __global__ void k_finalize_alpha(const double* pE, int nE, const double* prr, in
             stats[2] = (float)alpha;
             stats[3] = (float)R;
         }
+        *ticket = 0u;
     }
 }
 
@@ -1294,6 +1313,7 @@ GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_a
     a.items = ts.work.items;
     a.nitems = ts.work.nitems;
     a.splits = ts.work.splits;
+    a.split_cnt = ts.work.split_cnt;
     a.nsplit = ts.work.nsplit;
     a.part_acc = part_acc;
     a.ngroups = ts.ngroups;
@@ -1520,6 +1540,7 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
     a.items = t.adj_near_work.items;
     a.nitems = t.adj_near_work.nitems;
     a.splits = t.adj_near_work.splits;
+    a.split_cnt = t.adj_near_work.split_cnt;
     a.nsplit = t.adj_near_work.nsplit;
     a.perm = t.self.perm;
     a.out = out;
@@ -1527,22 +1548,10 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
     a.partial = partial;
     a.scale = out ? (float)(t.scale * t.scale) : 1.f;
     ProfScope ps(&t.prof, WNNC_PROF_ADJ_NEAR, s);
-    const int grid = ceil_div(a.nitems, kGatherWarps), fgrid = ceil_div((int64_t)a.nsplit * 32, kTB);
-    if (out) {
-        k_adj_near<kEpiStoreATpaper><<<grid, 32 * kGatherWarps, 0, s>>>(a);
-        WNNC_LAUNCH_CHECK();
-        if (a.nsplit) {
-            k_adj_near_finalize<kEpiStoreATpaper><<<fgrid, kTB, 0, s>>>(a);
-            WNNC_LAUNCH_CHECK();
-        }
-    } else {
-        k_adj_near<kEpiNormSq><<<grid, 32 * kGatherWarps, 0, s>>>(a);
-        WNNC_LAUNCH_CHECK();
-        if (a.nsplit) {
-            k_adj_near_finalize<kEpiNormSq><<<fgrid, kTB, 0, s>>>(a);
-            WNNC_LAUNCH_CHECK();
-        }
-    }
+    const int grid = ceil_div(a.nitems, kGatherWarps);
+    if (out) k_adj_near<kEpiStoreATpaper><<<grid, 32 * kGatherWarps, 0, s>>>(a);
+    else k_adj_near<kEpiNormSq><<<grid, 32 * kGatherWarps, 0, s>>>(a);
+    WNNC_LAUNCH_CHECK();
 }
 
 void eval_adjoint(Tree& t, const float* sv, float w, float* out, cudaStream_t s) {
@@ -1655,11 +1664,8 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             launch_gather<kOpAG, kEpiNormSqAG>(t, b, s);
             {
                 ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
-                k_reduce3<<<kRedBlocks, kTB, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.red);
-                WNNC_LAUNCH_CHECK();
-                k_finalize_alpha<<<1, kRedBlocks, 0, s>>>(t.red, kRedBlocks, t.red + kRedBlocks, kRedBlocks,
-                                                          t.red + 2 * kRedBlocks, kRedBlocks, t.scalars, st, w,
-                                                          t.err_flag);
+                k_reduce3<<<kRedBlocks, kTB, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.red, t.scalars, st,
+                                                     w, t.err_flag, t.red_ticket);
                 WNNC_LAUNCH_CHECK();
                 k_wnnc_update<<<grid_n, kTB, 0, s>>>(mu, t.r_s, t.g_mu, t.g_r, t.scalars, t.area_s, p.rescale, n,
                                                      mu_alt);
@@ -1698,11 +1704,8 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             launch_gather<kOpA, kEpiNormSq>(t, b, s);
             {
                 ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
-                k_reduce3<<<kRedBlocks, kTB, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.red);
-                WNNC_LAUNCH_CHECK();
-                k_finalize_alpha<<<1, kRedBlocks, 0, s>>>(t.red, kRedBlocks, t.red + kRedBlocks, kRedBlocks,
-                                                          t.red + 2 * kRedBlocks, kRedBlocks, t.scalars, st, w,
-                                                          t.err_flag);
+                k_reduce3<<<kRedBlocks, kTB, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.red, t.scalars, st,
+                                                     w, t.err_flag, t.red_ticket);
                 WNNC_LAUNCH_CHECK();
                 k_axpy<<<grid_n, kTB, 0, s>>>(mu, t.r_s, t.scalars, n, mu_alt);
                 WNNC_LAUNCH_CHECK();

@@ -750,14 +750,15 @@ __global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* idx, const u
 struct ItemWalk {
     int g, q0, f0, cost, k;
     Item* out;
-    int base, pslot_base, nparts;
+    int base, pslot_base, nparts, split;
     bool partials;
     __device__ void emit(int q1, int f1) {
         if (out) {
             Item it;
             it.g = g; it.q0 = q0; it.q1 = q1; it.f0 = f0; it.f1 = f1;
             it.pslot = (partials && nparts > 1) ? pslot_base + k : -1;
-            it.cost = cost; it.pad = 0;
+            it.cost = cost;
+            it.split = it.pslot >= 0 ? split : -1;
             out[base + k] = it;
         }
         ++k;
@@ -768,10 +769,10 @@ struct ItemWalk {
 };
 
 __device__ int walk_items(int mode, int g, const int* near_off, const int2* rng, const int* far_off, int cap,
-                          Item* out, int base, int pslot_base, int nparts, bool partials) {
+                          Item* out, int base, int pslot_base, int nparts, int split, bool partials) {
     const int qb = near_off ? near_off[g] : 0, qe = near_off ? near_off[g + 1] : 0;
     const int fb = far_off ? far_off[g] : 0, fe = far_off ? far_off[g + 1] : 0;
-    ItemWalk w{g, qb, fb, 0, 0, out, base, pslot_base, nparts, partials};
+    ItemWalk w{g, qb, fb, 0, 0, out, base, pslot_base, nparts, split, partials};
     for (int q = qb; q < qe; ++q) {
         int c = mode == 1 ? 8 : rng[q].y - rng[q].x;
         if (w.cost > 0 && w.cost + c > cap) w.emit(q, fb);
@@ -802,7 +803,7 @@ __global__ void k_items_count(int mode, int nseg, const int* near_off, const int
                               int cap, int* cnt, int* slots) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nseg) return;
-    int c = walk_items(mode, g, near_off, rng, far_off, cap, nullptr, 0, 0, 0, false);
+    int c = walk_items(mode, g, near_off, rng, far_off, cap, nullptr, 0, 0, 0, -1, false);
     cnt[g] = c;
     slots[g] = c > 1 ? c : 0;
 }
@@ -812,7 +813,8 @@ __global__ void k_items_fill(int mode, int nseg, const int* near_off, const int2
                              Item* items, int4* splits, const int* split_off) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nseg) return;
-    walk_items(mode, g, near_off, rng, far_off, cap, items, item_off[g], slot_off[g], cnt[g], partials);
+    walk_items(mode, g, near_off, rng, far_off, cap, items, item_off[g], slot_off[g], cnt[g],
+               (partials && cnt[g] > 1) ? split_off[g] : -1, partials);
     if (partials && cnt[g] > 1) splits[split_off[g]] = make_int4(g, slot_off[g], cnt[g], 0);
 }
 
@@ -865,6 +867,7 @@ static int bits_for(int64_t v) {
 void free_work(WorkList& w) {
     dfree(w.items);
     dfree(w.splits);
+    dfree(w.split_cnt);
     w.nitems = w.nsplit = w.nslots = 0;
 }
 
@@ -913,6 +916,8 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     }
     Item* tmp = dalloc<Item>(w.nitems);
     w.splits = dalloc<int4>(w.nsplit);
+    w.split_cnt = dalloc<unsigned>(w.nsplit);
+    WNNC_CUDA(cudaMemsetAsync(w.split_cnt, 0, sizeof(unsigned) * (size_t)std::max(w.nsplit, 1), s));
     k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cap, cnt, item_off,
                                                     slot_off, partials, tmp, w.splits, split_off);
     WNNC_LAUNCH_CHECK();
@@ -1433,7 +1438,7 @@ void free_tree(Tree& t) {
     free_work(t.adj_near_work);
     dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.g_mu); dfree(t.g_r); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
     dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.node_rep); dfree(t.contrib);
-    dfree(t.near_contrib); dfree(t.vnode);
+    dfree(t.near_contrib); dfree(t.vnode); dfree(t.red_ticket);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
 
