@@ -776,25 +776,13 @@ struct AdjArgs {
     double* partial;
 };
 
-// One adjoint term s_i gradPhi(x_i - x) = s_i (x - x_i) / r^3 at x = p from
-// the target ti = (x_i, s_i).  CUT as in interact().
-template <bool CUT>
-__device__ __forceinline__ void adj_term(const float4& p, const float4& ti, float w2, float& ax, float& ay,
-                                         float& az) {
-    const float dx = p.x - ti.x, dy = p.y - ti.y, dz = p.z - ti.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float ir = rsqrtf(r2);
-    if (CUT) ir = (r2 >= w2) ? ir : 0.f;
-    const float q = ti.w * (ir * ir * ir);
-    ax = fmaf(q, dx, ax);
-    ay = fmaf(q, dy, ay);
-    az = fmaf(q, dz, az);
-}
-
-// Two adjoint terms at once with paired FP32 instructions (one point
-// against two targets, (tx, ty, tz) the targets' negated coordinates, tw
-// their s): the same operations and order as adj_term in each half.  Returns
-// the two terms' factors q and offsets d through the references.
+// Adjoint terms s_i gradPhi(x_i - x) = s_i (x - x_i) / r^3 at x = p from a
+// target (x_i, s_i), two at once with paired FP32 instructions: one point
+// against two targets, or two points against one target ((tx, ty, tz) the
+// negated target coordinates, tw the s).  In each half: d = p - x_i,
+// r^2 = d.x^2 + (d.y^2 + d.z^2) by fma, ir = rsqrt(r^2) (0 where the cut-off
+// drops the pair, CUT as in interact()), q = s_i ((ir ir) ir).  Returns q and
+// d through the references; the caller accumulates q d.
 template <bool CUT>
 __device__ __forceinline__ void adj_term2(const float2& px, const float2& py, const float2& pz, const float2& tx,
                                           const float2& ty, const float2& tz, const float2& tw, float w2,
@@ -1048,7 +1036,6 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_near_pairs(AdjArgs A) {
             adj_term2<CUT>(make_float2(p.x, p.x), make_float2(p.y, p.y), make_float2(p.z, p.z), ntx, nty, ntz, tw,
                            A.w2, dx, dy, dz, q);
             // the first target's term, then the second's added by one fma
-            // (the order of adj_term applied to both)
             v[k][0] = fmaf(q.y, dx.y, q.x * dx.x);
             v[k][1] = fmaf(q.y, dy.y, q.x * dy.x);
             v[k][2] = fmaf(q.y, dz.y, q.x * dz.x);
