@@ -121,6 +121,26 @@ def test_gpu_iteration_union50k_matches_oracle():
 
 
 @pytest.mark.gpu
+def test_gpu_iteration_union500k_matches_oracle_at_full_size():
+    """The benchmark's workload at full size (500,000 points, theta = 0.5, the
+    fused iteration that bench.py times): iterations 1 and 2 of the 40-step
+    schedule from zero against the oracle's FP64 iteration on the same lists.
+    The step-length sums (E, |r|^2) and alpha agree to FP32 rounding, and the
+    fields agree point by point."""
+    W = _gpu()
+    c = synth.config_cloud("union500k")
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mg, sg = t.iterate(n_iter=40, last_iter=2, stats=True)
+    mg = mg.cpu().numpy().astype(np.float64)
+    sg = sg.cpu().numpy().astype(np.float64)
+    mo, so = oracle.iterate(c.points, n_iter=40, last_iter=2, theta=f32(0.5))
+    assert np.allclose(sg[:, 0], so[:, 0], rtol=1e-6)                 # widths
+    assert np.allclose(sg[:, 1:], so[:, 1:], rtol=2e-4), (sg, so)      # E, alpha, |r|^2
+    cos, dlen = _compare_fields(mg, mo, min_sign=0.9999, min_cos=0.99999)
+    assert dlen < 1e-4, dlen
+
+
+@pytest.mark.gpu
 def test_gpu_paper_mode_iteration_matches_oracle():
     """rep_mode 0 (the paper's |nu|-weighted representatives and the
     s-representative A^T) through the whole iteration."""
