@@ -84,8 +84,10 @@ def lib():
                                        c_void_p, c_void_p]
         L.or_schedule_width.argtypes = [c_int, c_int, d, d]
         L.or_schedule_width.restype = d
+        L.or_schedule_width2.argtypes = [c_int, c_int, d, d, c_int]
+        L.or_schedule_width2.restype = d
         L.or_iterate.argtypes = [c_void_p, c_void_p, i64, c_void_p, c_int, c_int, c_int, d, d, c_int,
-                                 c_int, c_void_p, c_int, c_int, c_void_p]
+                                 c_int, c_void_p, c_int, c_int, c_int, c_void_p]
         L.or_knn.argtypes = [c_void_p, i64, c_int, c_void_p, c_void_p]
         _lib = L
     return _lib
@@ -289,8 +291,10 @@ def eval_at(op: int, points, mu, queries, w: float, theta: float = 0.0, leaf_siz
 def iterate(points, mu0=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0.016,
             theta: float = 0.0, leaf_size: int = 8, max_depth: int = 15, rep_mode: int = 1,
             first_iter: int = 1, last_iter: int | None = None, rescale: int = 0, area=None,
-            use_grad: bool = True, use_wnnc: bool = True):
-    """Alg. 3 on the cloud; returns (mu in caller units, stats[iter] = (w, E, alpha, |r|^2))."""
+            use_grad: bool = True, use_wnnc: bool = True, schedule="linear"):
+    """Alg. 3 on the cloud; returns (mu in caller units, stats[iter] = (w, E, alpha, |r|^2)).
+    schedule: the width schedule, "linear" (Alg. 3), "cosine" or "exponential"
+    (the alternatives of Sec. 6.1.2; see schedule_width)."""
     xn, c, s, tree = _setup(points, theta, leaf_size, max_depth)
     n = xn.shape[0]
     mu = np.zeros((n, 3)) if mu0 is None else np.array(mu0, dtype=np.float64).reshape(n, 3) * (s * s)
@@ -299,12 +303,26 @@ def iterate(points, mu0=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0
     ar = None if area is None else np.ascontiguousarray(np.asarray(area, np.float64) * (s * s))
     lib().or_iterate(tree._h if tree is not None else None, _p(xn), n, _p(mu), n_iter, first_iter,
                      last, float(w1), float(w2), rep_mode, rescale, _p(ar), int(use_grad),
-                     int(use_wnnc), _p(stats))
+                     int(use_wnnc), _schedule_code(schedule, w1, w2), _p(stats))
     return mu / (s * s), stats
 
 
-def schedule_width(i: int, n_iter: int, w1: float, w2: float) -> float:
-    return lib().or_schedule_width(i, n_iter, w1, w2)
+SCHEDULES = {"linear": 0, "cosine": 1, "exponential": 2}
+
+
+def _schedule_code(schedule, w1, w2) -> int:
+    code = SCHEDULES.get(schedule, -1) if isinstance(schedule, str) else int(schedule)
+    if code not in (0, 1, 2):
+        raise ValueError(f"unknown width schedule {schedule!r}")
+    if code == 2 and not (w1 > 0 and w2 > 0):
+        raise ValueError("the exponential width schedule needs w1 > 0 and w2 > 0")
+    return code
+
+
+def schedule_width(i: int, n_iter: int, w1: float, w2: float, schedule="linear") -> float:
+    """Width of iteration i of n_iter: linear w2 (1-t) + w1 t (Alg. 3), cosine
+    w1 + (w2-w1)(1 + cos(pi t))/2 or exponential w2 (w1/w2)^t, t = (i-1)/(n-1)."""
+    return lib().or_schedule_width2(i, n_iter, w1, w2, _schedule_code(schedule, w1, w2))
 
 
 def knn(x, k: int = 16):

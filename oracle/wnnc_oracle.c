@@ -732,7 +732,7 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
 
 /* ------------------------------------------------------------------------ */
 /* Alg. 3: n iterations of grad step (Alg. 2) + WNNC update + rescale, with  */
-/* the linear width schedule w = w2 (n-i)/(n-1) + w1 (i-1)/(n-1).            */
+/* the width schedule of or_schedule_width2 (the paper's is the linear one). */
 /*   T == NULL: the operators are the direct sums over xn.                   */
 /*   mu (n x 3, input order, normalised units) is updated in place.          */
 /*   rescale 0: mu_i <- muhat_i |mu_i| / |muhat_i|  (Alg. 3)                 */
@@ -748,21 +748,37 @@ static void apply_op(const or_tree* T, const double* xn, int64_t n, int op, int 
     else or_direct(op, xn, n, nu, xn, n, w, 0.0, out, NULL, NULL);
 }
 
-double or_schedule_width(int i, int n_iter, double w1, double w2) {
+/* Width of iteration i of n (Sec. 4.4 and Alg. 3).  With t = (i-1)/(n-1)
+ * running from 0 at the first iteration to 1 at the last:
+ *   schedule 0, linear (the paper's):  w = w2 (1 - t) + w1 t
+ *   schedule 1, cosine:                w = w1 + (w2 - w1) (1 + cos(pi t)) / 2
+ *   schedule 2, exponential:           w = w2 (w1 / w2)^t   (w1, w2 > 0)
+ * Sec. 6.1.2 reports that cosine and exponential decays were tried and gave
+ * no clear difference; it prints no formula for them, so these are the
+ * standard forms that fall smoothly from w2 to w1.  n = 1 gives w1. */
+double or_schedule_width2(int i, int n_iter, double w1, double w2, int schedule) {
     if (n_iter <= 1) return w1;
-    return w2 * (double)(n_iter - i) / (double)(n_iter - 1) + w1 * (double)(i - 1) / (double)(n_iter - 1);
+    if (schedule == 0)
+        return w2 * (double)(n_iter - i) / (double)(n_iter - 1) + w1 * (double)(i - 1) / (double)(n_iter - 1);
+    const double t = (double)(i - 1) / (double)(n_iter - 1);
+    if (schedule == 1) return w1 + (w2 - w1) * 0.5 * (1.0 + cos(acos(-1.0) * t));
+    return w2 * pow(w1 / w2, t);
+}
+
+double or_schedule_width(int i, int n_iter, double w1, double w2) {
+    return or_schedule_width2(i, n_iter, w1, w2, 0);
 }
 
 void or_iterate(const or_tree* T, const double* xn, int64_t n, double* mu, int n_iter, int first_iter,
                 int last_iter, double w1, double w2, int rep_mode, int rescale, const double* area,
-                int use_grad, int use_wnnc, double* stats) {
+                int use_grad, int use_wnnc, int schedule, double* stats) {
     double* a = malloc(sizeof(double) * (n > 0 ? n : 1));
     double* s = malloc(sizeof(double) * (n > 0 ? n : 1));
     double* r = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
     double* q = malloc(sizeof(double) * (n > 0 ? n : 1));
     double* muhat = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
     for (int it = first_iter; it <= last_iter; ++it) {
-        double w = or_schedule_width(it, n_iter, w1, w2);
+        double w = or_schedule_width2(it, n_iter, w1, w2, schedule);
         double E = 0.0, rr = 0.0, qq = 0.0, alpha = 0.0;
         if (use_grad) {
             /* Alg. 2:  r = A^T b - A^T A mu = A^T (b - A mu);  alpha = r.r / |A r|^2;  mu += alpha r */

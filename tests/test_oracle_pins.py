@@ -355,6 +355,47 @@ def test_schedule_endpoints():
     assert np.allclose(np.diff(ws), -(0.016 - 0.002) / 39)
 
 
+@pytest.mark.parametrize("schedule", ["linear", "cosine", "exponential"])
+def test_schedule_alternatives(schedule):
+    """Sec. 6.1.2's cosine and exponential decays (and the linear one of
+    Alg. 3) start at w2, end at w1 and fall monotonically; each has its own
+    shape: constant steps (linear), flat ends and point symmetry about the
+    middle (cosine), a constant ratio with the geometric mean in the middle
+    (exponential)."""
+    n, w1, w2 = 41, 0.002, 0.016
+    ws = np.array([oracle.schedule_width(i, n, w1, w2, schedule) for i in range(1, n + 1)])
+    assert ws[0] == w2
+    assert abs(ws[-1] - w1) < 1e-15
+    d = np.diff(ws)
+    assert np.all(d < 0)
+    mid = ws[(n - 1) // 2]
+    if schedule == "linear":
+        assert np.allclose(d, -(w2 - w1) / (n - 1), rtol=1e-9)
+        assert abs(mid - 0.5 * (w1 + w2)) < 1e-15
+    elif schedule == "cosine":
+        assert np.allclose(ws + ws[::-1], w1 + w2, rtol=0, atol=1e-15)
+        assert abs(mid - 0.5 * (w1 + w2)) < 1e-15
+        # flat at both ends, steepest in the middle: the first step is
+        # (w2 - w1) sin^2(pi / (2 (n - 1))) of the whole drop
+        assert abs(-d[0] - (w2 - w1) * np.sin(np.pi / (2 * (n - 1))) ** 2) < 1e-15
+        assert -d[0] < -d[(n - 1) // 2 - 1]
+    else:
+        ratios = ws[1:] / ws[:-1]
+        assert np.allclose(ratios, (w1 / w2) ** (1.0 / (n - 1)), rtol=1e-12)
+        assert abs(mid - np.sqrt(w1 * w2)) < 1e-15
+    assert oracle.schedule_width(1, 1, w1, w2, schedule) == w1
+    it_stats = oracle.iterate(synth.fibonacci_sphere(200).points, n_iter=n, last_iter=3,
+                              schedule=schedule)[1]
+    assert np.array_equal(it_stats[:, 0], ws[:3])
+
+
+def test_exponential_schedule_needs_positive_widths():
+    with pytest.raises(ValueError):
+        oracle.schedule_width(2, 10, 0.0, 0.016, "exponential")
+    with pytest.raises(ValueError):
+        oracle.schedule_width(2, 10, 0.002, 0.016, "quadratic")
+
+
 def test_first_iteration_closed_form_on_sphere():
     """From mu = 0 on a sphere of radius R (normalised units), r = A^T b is
     radial and the exact line search gives mu = (4 pi R^2/N) n / (1 - w/(2R))
