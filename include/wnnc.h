@@ -84,7 +84,7 @@ typedef struct {
 
 /* Iteration parameters (Alg. 3; Sec. 5.1.1 defaults n = 40, w1 = 0.002, w2 = 0.016). */
 typedef struct {
-    int n_iter;        /* n of the width schedule w_i = w2 (n-i)/(n-1) + w1 (i-1)/(n-1) */
+    int n_iter;        /* n of the width schedule (linear: w_i = w2 (n-i)/(n-1) + w1 (i-1)/(n-1)) */
     int first_iter;    /* first i to run (1 = from the start; >1 resumes a saved run) */
     int last_iter;     /* last i to run (0 = n_iter) */
     float w1, w2;      /* final and initial smoothing widths, normalised units */
@@ -93,6 +93,13 @@ typedef struct {
                           1 = |mu_i| set to the given area sigma_i (Eq. 19) */
     int use_grad;      /* 1 = gradient step of Alg. 2 (default); 0 = skip it (ablation) */
     int use_wnnc;      /* 1 = WNNC update + rescale (default); 0 = skip it (ablation) */
+    int schedule;      /* width schedule from w2 down to w1, with t = (i-1)/(n-1) (n = 1: w1):
+                          0 = linear w2 (1-t) + w1 t (Alg. 3, default);
+                          1 = cosine w1 + (w2-w1)(1 + cos(pi t))/2;
+                          2 = exponential w2 (w1/w2)^t, needs w1, w2 > 0.
+                          Sec. 6.1.2 names cosine and exponential decays as tried
+                          alternatives without giving formulas; these are the standard
+                          smooth forms.  Other values: WNNC_EINVAL */
 } wnnc_iter_params;
 
 /* Fill p with the defaults listed above.  Returns WNNC_EINVAL if p is NULL. */

@@ -33,6 +33,7 @@ __all__ = ["Tree", "TreeParams", "IterParams", "WnncError", "winding_number", "W
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ECAPACITY",
           6: "ETIMEOUT"}
+SCHEDULES = {"linear": 0, "cosine": 1, "exponential": 2}
 PROF_CLASSES = ["moments", "A", "adj_far", "adj_node", "adj_near", "G", "small", "AG"]
 
 
@@ -50,7 +51,7 @@ class TreeParams(Structure):
 class IterParams(Structure):
     _fields_ = [("n_iter", c_int), ("first_iter", c_int), ("last_iter", c_int),
                 ("w1", c_float), ("w2", c_float), ("init", c_int), ("rescale", c_int),
-                ("use_grad", c_int), ("use_wnnc", c_int)]
+                ("use_grad", c_int), ("use_wnnc", c_int), ("schedule", c_int)]
 
 
 _lib = None
@@ -224,13 +225,17 @@ class Tree:
 
     def iterate(self, mu=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0.016,
                 first_iter: int = 1, last_iter: int = 0, area=None, rescale: int = 0,
-                use_grad: bool = True, use_wnnc: bool = True, stats: bool = False, out=None):
-        """Alg. 3.  mu None = zero init; returns mu (and per-iteration stats)."""
+                use_grad: bool = True, use_wnnc: bool = True, stats: bool = False, out=None,
+                schedule="linear"):
+        """Alg. 3.  mu None = zero init; returns mu (and per-iteration stats).
+        schedule: width schedule "linear" (the paper's), "cosine" or "exponential"
+        (or its code 0, 1, 2)."""
         p = default_iter_params()
         p.n_iter, p.first_iter, p.last_iter = int(n_iter), int(first_iter), int(last_iter)
         p.w1, p.w2 = float(w1), float(w2)
         p.init = 0 if mu is None else 1
         p.rescale, p.use_grad, p.use_wnnc = int(rescale), int(bool(use_grad)), int(bool(use_wnnc))
+        p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         if out is not None:
             mu_t = out
             if mu is not None:

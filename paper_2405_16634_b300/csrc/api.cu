@@ -182,6 +182,7 @@ wnnc_status wnnc_iter_params_default(wnnc_iter_params* p) {
     p->rescale = 0;
     p->use_grad = 1;
     p->use_wnnc = 1;
+    p->schedule = 0;
     return WNNC_OK;
 }
 
@@ -287,6 +288,9 @@ wnnc_status wnnc_iterate(wnnc_tree* tree, float* mu_inout, const float* area, co
         if (p.init != 0 && p.init != 1) fail(WNNC_EINVAL, "init must be 0 or 1");
         if (p.rescale != 0 && p.rescale != 1) fail(WNNC_EINVAL, "rescale must be 0 or 1");
         if (p.rescale == 1 && !area) fail(WNNC_EINVAL, "rescale = 1 needs area");
+        if (p.schedule < 0 || p.schedule > 2) fail(WNNC_EINVAL, "schedule must be 0, 1 or 2");
+        if (p.schedule == 2 && !(p.w1 > 0.f && p.w2 > 0.f))
+            fail(WNNC_EINVAL, "the exponential schedule needs w1 > 0 and w2 > 0");
         iterate(t, mu_inout, area, p, static_cast<cudaStream_t>(stream), stats);
     });
 }

@@ -1591,6 +1591,18 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     free_target_set(Q);
 }
 
+// Smoothing width of iteration `it` (Sec. 4.4): from w2 at the first
+// iteration down to w1 at the last, along the schedule p.schedule (the paper's
+// linear one, or the cosine and exponential decays of Sec. 6.1.2).
+static double schedule_width(const wnnc_iter_params& p, int it) {
+    const double w1 = p.w1, w2 = p.w2;
+    if (p.n_iter <= 1) return w1;
+    const double t = (double)(it - 1) / (double)(p.n_iter - 1);
+    if (p.schedule == 1) return w1 + (w2 - w1) * 0.5 * (1.0 + std::cos(3.14159265358979323846 * t));
+    if (p.schedule == 2) return w2 * std::pow(w1 / w2, t);
+    return w2 * (double)(p.n_iter - it) / (double)(p.n_iter - 1) + w1 * (double)(it - 1) / (double)(p.n_iter - 1);
+}
+
 // Alg. 3 with Alg. 2, in the sorted order, normalised units.
 void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params& p, cudaStream_t s,
              float* stats) {
@@ -1625,10 +1637,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
     // G(mu + alpha r) = G(mu) + alpha G(r) needs no third pass.
     const bool fused = linear_mom && p.use_grad && p.use_wnnc;
     for (int it = p.first_iter; it <= last; ++it) {
-        const double wd = p.n_iter <= 1 ? (double)p.w1
-                                        : (double)p.w2 * (double)(p.n_iter - it) / (double)(p.n_iter - 1) +
-                                              (double)p.w1 * (double)(it - 1) / (double)(p.n_iter - 1);
-        const float w = (float)wd;
+        const float w = (float)schedule_width(p, it);
         float* st = stats ? stats + 4 * (int64_t)(it - p.first_iter) : nullptr;
         if (fused) {
             // s = b - A mu, with G(mu)

@@ -37,8 +37,8 @@ def test_defaults_and_argument_errors_without_gpu():
     assert (p.max_depth, p.leaf_size, p.rep_mode, p.moments_fp64, p.near_bf16) == (15, 8, 1, 0, 0)
     assert abs(p.theta - 0.5) < 1e-7
     q = W.default_iter_params()
-    assert (q.n_iter, q.first_iter, q.last_iter, q.init, q.rescale, q.use_grad, q.use_wnnc) == \
-        (40, 1, 0, 0, 0, 1, 1)
+    assert (q.n_iter, q.first_iter, q.last_iter, q.init, q.rescale, q.use_grad, q.use_wnnc,
+            q.schedule) == (40, 1, 0, 0, 0, 1, 1, 0)
     assert abs(q.w1 - 0.002) < 1e-9 and abs(q.w2 - 0.016) < 1e-9
     assert L.wnnc_tree_params_default(None) == 1
     h = ctypes.c_void_p()

@@ -153,6 +153,33 @@ def test_gpu_paper_mode_iteration_matches_oracle():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("schedule", ["cosine", "exponential"])
+def test_gpu_width_schedules_match_oracle(schedule):
+    """The cosine and exponential width decays of Sec. 6.1.2: the CUDA
+    iteration takes the oracle's widths and reaches the oracle's field."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=10000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mg, sg = t.iterate(n_iter=10, schedule=schedule, stats=True)
+    mo, so = oracle.iterate(c.points, n_iter=10, theta=f32(0.5), schedule=schedule)
+    assert np.allclose(sg[:, 0].cpu().numpy(), so[:, 0], rtol=1e-6)
+    assert np.allclose(sg[:3, 1:].cpu().numpy(), so[:3, 1:], rtol=1e-3)
+    _compare_fields(mg.cpu().numpy().astype(np.float64), mo, min_sign=0.995, min_cos=0.995)
+
+
+@pytest.mark.gpu
+def test_gpu_schedule_argument_errors():
+    W = _gpu()
+    c = synth.fibonacci_sphere(500)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    with pytest.raises(W.WnncError):
+        t.iterate(n_iter=3, schedule=3)
+    with pytest.raises(W.WnncError):
+        t.iterate(n_iter=3, w1=0.0, schedule="exponential")
+    assert torch.isfinite(t.iterate(n_iter=3, w1=0.0, schedule="cosine")).all()
+
+
+@pytest.mark.gpu
 def test_gpu_ablations_behave_as_in_the_paper():
     """Sec. 6.1.3: without the gradient step mu stays 0; the grad step alone
     (no WNNC update) decreases the energy monotonically at fixed width."""
