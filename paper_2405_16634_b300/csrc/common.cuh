@@ -213,9 +213,12 @@ struct Tree {
     int* node_depth = nullptr;
     int* level_off = nullptr;     // host: first node of each level, [levels+1]
     int nlevels = 0;
-    int mom_top_levels = 0;       // levels 0.. that hold nodes of more than kMomDirect points
-    int nmom_mid = 0;             // nodes of kMomSmall+1 .. kMomDirect points
+    int nmom_mid = 0;             // nodes of kMomSmall+1 .. kMomDirect points, and leaves of more
     int* mom_mid = nullptr;       // their ids
+    int nmom_top = 0;             // inner nodes of more than kMomDirect points
+    int* mom_top = nullptr;       // their ids
+    int2* mom_top_rng = nullptr;  // per top node: its range of mom_front
+    int* mom_front = nullptr;     // the non-top nodes whose parent is a top node, by first point
     double* node_lo = nullptr;    // tight bounding boxes (build)
     double* node_hi = nullptr;
     float4* node_lof = nullptr;   // the same boxes rounded outward to float (traversal pre-test)

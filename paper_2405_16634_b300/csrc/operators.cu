@@ -59,11 +59,11 @@ constexpr int kGatherTPL = WNNC_GATHER_TPL;
 // Node moments in two launches, with no dependency chain through the whole
 // tree:
 //   1. one thread per node of at most kMomSmall points sums its point range;
-//   2. one warp per node of up to kMomDirect points sums its range
-//      (lane-strided, then a fixed xor reduction); classes 1 and 2 share a
-//      launch;
-//   3. one block adds the few larger nodes (the top levels) from their
-//      children, deepest level first, in child order.
+//   2. one warp per node of up to kMomDirect points (or a leaf of any size)
+//      sums its range (lane-strided, then a fixed xor reduction); classes 1
+//      and 2 share a launch;
+//   3. one block per larger inner node (the top levels) adds the sums of the
+//      class 1 and 2 nodes that partition its points.
 //   mom[b]  = (sum nu, sum |nu|)        (nu = mu: 3 components; nu = s: 1)
 //   momx[b] = sum |nu| (x - cell_b)     (only for the |nu|-weighted representative)
 //   rep[b]  = momx[b] / sum |nu|, or the point centroid when sum |nu| = 0
@@ -163,63 +163,57 @@ __global__ void k_mom_sums(int nnodes, int nmid, int grid_m, const int* mid, con
     }
 }
 
-struct LevelOffsets {
-    int off[17];   // first node of levels 0..15, and the end of the last
-};
-
+// Class 3: one block per top node (an inner node of more than kMomDirect
+// points) adds the moments of its front, the summed nodes that partition its
+// points (ordered by first point): thread k takes front nodes k, k + 256,
+// ..., then a fixed xor reduction per warp and the warps' sums in order.  No
+// top node waits for another, so the top levels cost one short launch.
+constexpr int kMomTopThreads = 256;
 template <bool WEIGHTED, class Acc>
-__global__ void __launch_bounds__(1024) k_mom_top(int nlev, LevelOffsets lv, const int* ncount,
-                                                  const int* nchild, const int* nchild0, const float4* ncell,
-                                                  const float4* ncent, float4* mom, float4* momx, float4* rep,
-                                                  double* dmom) {
-    for (int d = nlev - 1; d >= 0; --d) {
-        for (int b = lv.off[d] + threadIdx.x; b < lv.off[d + 1]; b += blockDim.x) {
-            if (ncount[b] <= kMomDirect) continue;
-            const float4 cp = ncell[b];
-            const int nc = nchild[b], c0 = nchild0[b];
-            Acc m[7] = {0, 0, 0, 0, 0, 0, 0};
-            if (!dmom && !WEIGHTED) {
-                // all children's sums loaded first (one round trip), then
-                // added in child order; absent children add exact zeros
-                float4 mm[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) mm[q] = q < nc ? mom[c0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    m[0] += mm[q].x;
-                    m[1] += mm[q].y;
-                    m[2] += mm[q].z;
-                    m[3] += mm[q].w;
-                }
-            } else {
-                for (int q = 0; q < nc; ++q) {
-                    const int c = c0 + q;
-                    Acc cm[7];
-                    if (dmom) {
-                        for (int k = 0; k < 7; ++k) cm[k] = (Acc)dmom[8 * (int64_t)c + k];
-                    } else {
-                        const float4 mm = mom[c];
-                        cm[0] = mm.x; cm[1] = mm.y; cm[2] = mm.z; cm[3] = mm.w;
-                        if (WEIGHTED) {
-                            const float4 xx = momx[c];
-                            cm[4] = xx.x; cm[5] = xx.y; cm[6] = xx.z;
-                        } else {
-                            cm[4] = cm[5] = cm[6] = 0;
-                        }
-                    }
-                    for (int k = 0; k < 4; ++k) m[k] += cm[k];
-                    if (WEIGHTED) {
-                        // re-centre the child's weighted offsets on this node's cell
-                        const float4 cc = ncell[c];
-                        m[4] += cm[4] + cm[3] * (Acc)(cc.x - cp.x);
-                        m[5] += cm[5] + cm[3] * (Acc)(cc.y - cp.y);
-                        m[6] += cm[6] + cm[3] * (Acc)(cc.z - cp.z);
-                    }
-                }
+__global__ void __launch_bounds__(kMomTopThreads) k_mom_top(const int* top, const int2* top_rng, const int* front,
+                                                            const float4* ncell, const float4* ncent,
+                                                            float4* mom, float4* momx, float4* rep, double* dmom) {
+    __shared__ Acc red[kMomTopThreads / 32][7];
+    const int b = top[blockIdx.x];
+    const int2 fr = top_rng[blockIdx.x];
+    const float4 cp = ncell[b];
+    Acc m[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int q = fr.x + (int)threadIdx.x; q < fr.y; q += kMomTopThreads) {
+        const int c = front[q];
+        Acc cm[7];
+        if (dmom) {
+            for (int k = 0; k < 7; ++k) cm[k] = (Acc)dmom[8 * (int64_t)c + k];
+        } else {
+            const float4 mm = mom[c];
+            cm[0] = mm.x; cm[1] = mm.y; cm[2] = mm.z; cm[3] = mm.w;
+            if (WEIGHTED) {
+                const float4 xx = momx[c];
+                cm[4] = xx.x; cm[5] = xx.y; cm[6] = xx.z;
             }
-            mom_store<WEIGHTED, Acc>(b, ncent, mom, momx, rep, dmom, m);
         }
-        __syncthreads();
+        for (int k = 0; k < 4; ++k) m[k] += cm[k];
+        if (WEIGHTED) {
+            // re-centre the front node's weighted offsets on this node's cell
+            const float4 cc = ncell[c];
+            m[4] += cm[4] + cm[3] * (Acc)(cc.x - cp.x);
+            m[5] += cm[5] + cm[3] * (Acc)(cc.y - cp.y);
+            m[6] += cm[6] + cm[3] * (Acc)(cc.z - cp.z);
+        }
+    }
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        if (!WEIGHTED && k >= 4) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+        if (lane == 0) red[wl][k] = m[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Acc t[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < kMomTopThreads / 32; ++w)
+            for (int k = 0; k < (WEIGHTED ? 7 : 4); ++k) t[k] += red[w][k];
+        mom_store<WEIGHTED, Acc>(b, ncent, mom, momx, rep, dmom, t);
     }
 }
 
@@ -1437,18 +1431,16 @@ void moments(Tree& t, const float4* nu_vec, const float* nu_s, int rep_mode, flo
     const bool w = rep_mode == 0;
     const int grid_s = ceil_div(t.nnodes, kTB), grid_m = ceil_div((int64_t)t.nmom_mid * 32, kTB);
     const bool fp64 = t.params.moments_fp64 != 0;
-    LevelOffsets lv{};
-    for (int L = 0; L <= t.mom_top_levels && L <= t.nlevels && L < 17; ++L) lv.off[L] = t.level_off[L];
 #define WNNC_MOM_SUMS(SC, WE, ACC, DM)                                                                    \
     do {                                                                                                  \
         k_mom_sums<SC, WE, ACC><<<grid_m + grid_s, kTB, 0, s>>>(                                          \
             t.nnodes, t.nmom_mid, grid_m, t.mom_mid, t.node_start, t.node_count, t.node_cell, t.node_cent,  \
             t.self.pos, t.self.corig, nu_vec, nu_s, out, t.mom_x, t.node_rep, DM);                        \
         WNNC_LAUNCH_CHECK();                                                                              \
-        if (t.mom_top_levels > 0) {                                                                       \
-            k_mom_top<WE, ACC><<<1, 1024, 0, s>>>(t.mom_top_levels, lv, t.node_count, t.node_nchild,      \
-                                                  t.node_child0, t.node_cell, t.node_cent, out, t.mom_x,  \
-                                                  t.node_rep, DM);                                        \
+        if (t.nmom_top > 0) {                                                                             \
+            k_mom_top<WE, ACC><<<t.nmom_top, kMomTopThreads, 0, s>>>(t.mom_top, t.mom_top_rng, t.mom_front, \
+                                                                     t.node_cell, t.node_cent, out, t.mom_x, \
+                                                                     t.node_rep, DM);                     \
             WNNC_LAUNCH_CHECK();                                                                          \
         }                                                                                                 \
     } while (0)

@@ -1317,23 +1317,47 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     wait_before_free(s);
     pool_free(sum);
     {
-        std::vector<int> nc(t.nnodes), cnt(t.nnodes);
+        std::vector<int> nc(t.nnodes), cnt(t.nnodes), st(t.nnodes), par(t.nnodes);
         WNNC_CUDA(cudaMemcpy(nc.data(), t.node_nchild, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
         WNNC_CUDA(cudaMemcpy(cnt.data(), t.node_count, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
+        WNNC_CUDA(cudaMemcpy(st.data(), t.node_start, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
+        WNNC_CUDA(cudaMemcpy(par.data(), t.node_parent, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
         t.nleaves = (int)std::count(nc.begin(), nc.end(), 0);
-        // the classes of the moment sums: levels holding nodes too large for
-        // the direct sums, and the list of nodes summed by one warp each
-        t.mom_top_levels = 0;
-        std::vector<int> mid;
-        for (int L = 0; L < t.nlevels; ++L)
-            for (int b = t.level_off[L]; b < t.level_off[L + 1]; ++b) {
-                if (cnt[b] > kMomDirect) t.mom_top_levels = L + 1;
-                else if (cnt[b] > kMomSmall) mid.push_back(b);
-            }
+        // the classes of the moment sums: nodes summed over their points by
+        // one thread (<= kMomSmall points) or one warp (up to kMomDirect
+        // points, and leaves of any size: a leaf at the depth limit may hold
+        // more); the inner nodes above that ("top") are summed from their
+        // "front", the summed nodes whose parent is a top node, which
+        // partition a top node's points in Morton order
+        std::vector<int> mid, top, front;
+        auto is_top = [&](int b) { return cnt[b] > kMomDirect && nc[b] > 0; };
+        for (int b = 0; b < t.nnodes; ++b) {
+            if (is_top(b)) top.push_back(b);
+            else if (cnt[b] > kMomSmall) mid.push_back(b);
+            if (!is_top(b) && par[b] >= 0 && is_top(par[b])) front.push_back(b);
+        }
+        std::sort(front.begin(), front.end(), [&](int a, int b) { return st[a] < st[b]; });
+        std::vector<int> fst(front.size());
+        for (size_t k = 0; k < front.size(); ++k) fst[k] = st[front[k]];
+        std::vector<int2> rng(top.size());
+        for (size_t k = 0; k < top.size(); ++k) {
+            const int b = top[k];
+            rng[k].x = (int)(std::lower_bound(fst.begin(), fst.end(), st[b]) - fst.begin());
+            rng[k].y = (int)(std::lower_bound(fst.begin(), fst.end(), st[b] + cnt[b]) - fst.begin());
+        }
         t.nmom_mid = (int)mid.size();
         t.mom_mid = dalloc<int>(mid.size());
-        if (!mid.empty())
-            WNNC_CUDA(cudaMemcpyAsync(t.mom_mid, mid.data(), sizeof(int) * mid.size(), cudaMemcpyHostToDevice, s));
+        t.nmom_top = (int)top.size();
+        t.mom_top = dalloc<int>(top.size());
+        t.mom_top_rng = dalloc<int2>(top.size());
+        t.mom_front = dalloc<int>(front.size());
+        auto up = [&](void* dst, const void* src, size_t bytes) {
+            if (bytes) WNNC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        };
+        up(t.mom_mid, mid.data(), sizeof(int) * mid.size());
+        up(t.mom_top, top.data(), sizeof(int) * top.size());
+        up(t.mom_top_rng, rng.data(), sizeof(int2) * rng.size());
+        up(t.mom_front, front.data(), sizeof(int) * front.size());
         WNNC_CUDA(cudaStreamSynchronize(s));
     }
 
@@ -1437,7 +1461,7 @@ void free_tree(Tree& t) {
     free_work(t.adj_far_work);
     free_work(t.adj_near_work);
     dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.g_mu); dfree(t.g_r); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
-    dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.node_rep); dfree(t.contrib);
+    dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.mom_top); dfree(t.mom_top_rng); dfree(t.mom_front); dfree(t.node_rep); dfree(t.contrib);
     dfree(t.near_contrib); dfree(t.vnode); dfree(t.red_ticket);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }

@@ -338,6 +338,42 @@ def test_duplicate_points():
     assert t.info()["depth"] == 15
 
 
+@pytest.mark.parametrize("case", ["coincident", "shallow"])
+def test_leaves_of_more_than_1024_points(case):
+    """A leaf can hold more points than the warp class of the node moments
+    (1024): 3000 coincident points stop splitting at depth 15, and a tree cut
+    at depth 2 leaves hundreds to thousands of points per leaf.  Such leaves,
+    and the inner nodes above them, must carry their full moments wherever
+    the lists use them as far nodes (Eq. 13-14), in both representative modes
+    and with FP64 moment sums."""
+    W = _wnnc()
+    if case == "coincident":
+        sph = synth.fibonacci_sphere(2000, radius=0.2).points + 0.8
+        pts = np.concatenate([np.full((3000, 3), -0.8), sph]).astype(np.float32)
+        leaf, depth = 8, 15
+    else:
+        pts = synth.union_cloud(40000, 12, n_tori=1, n_ellipsoids=1).points
+        leaf, depth = 32, 2
+    n = len(pts)
+    mu = synth.init_normals(n, 3, 1e-3)
+    s = np.random.default_rng(4).standard_normal(n).astype(np.float32)
+    xn, _, sc = oracle.normalize(pts)
+    ot = oracle.Tree(xn, f32(0.5), leaf_size=leaf, max_depth=depth)
+    w = 0.01
+    for rep_mode, fp64 in ((1, False), (1, True), (0, False)):
+        t = W.Tree(torch.from_numpy(pts).cuda(), theta=0.5, leaf_size=leaf, max_depth=depth,
+                   rep_mode=rep_mode, moments_fp64=fp64)
+        F = t.eval_w(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Fo, bf = ot.apply(OP_A, mu.astype(np.float64) * sc * sc, w, rep_mode=rep_mode, amb_tol=AMB)
+        check_close(F, Fo, bf, tol=3e-4, what=f"A {case} rep{rep_mode} fp64={fp64}")
+        T = t.eval_adjoint(torch.from_numpy(s).cuda(), w).cpu().numpy()
+        To, bt = ot.apply(OP_AT, s, w, rep_mode=rep_mode, amb_tol=AMB)
+        check_close(T, To * sc * sc, {k: v * sc * sc for k, v in bt.items()}, tol=3e-4,
+                    what=f"AT {case} rep{rep_mode} fp64={fp64}")
+        if case == "shallow":
+            assert t.info()["depth"] == 2
+
+
 def test_errors_are_reported():
     W = _wnnc()
     with pytest.raises(W.WnncError) as e:
