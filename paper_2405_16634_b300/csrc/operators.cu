@@ -38,7 +38,7 @@ constexpr int kGatherWarps = 4;
 // Inner-loop unroll depth and minimum resident blocks per SM of the pair
 // kernels (tuning knobs; the defaults are the measured best on B300).
 #ifndef WNNC_UNROLL
-#define WNNC_UNROLL 8
+#define WNNC_UNROLL 16
 #endif
 // The treecode gather and the far adjoint sums run with at least 6 resident
 // blocks per SM (the register cap that measured fastest; a few bytes spill in

@@ -96,24 +96,25 @@ def train(mlp: Mlp, X: torch.Tensor, Y: torch.Tensor, epochs: int = 4, batch: in
     return hist
 
 
-def plain_solve(points: torch.Tensor, n_iter: int = N_ITER):
+def plain_solve(points: torch.Tensor, n_iter: int = N_ITER, widths=(W1, W2)):
     t = Tree(points, theta=THETA)
-    mu = t.iterate(n_iter=n_iter, w1=W1, w2=W2)
+    mu = t.iterate(n_iter=n_iter, w1=widths[0], w2=widths[1])
     t.close()
     return mu
 
 
-def warm_solve(points: torch.Tensor, mlp: Mlp, k: int, s: int = 1, signed: bool = True):
+def warm_solve(points: torch.Tensor, mlp: Mlp, k: int, s: int = 1, signed: bool = True, widths=(W1, W2)):
     """Iterations 1..s of the schedule from zero (sign and length reference),
     the network's directions with that sign and length, then the last k
     iterations of the schedule.  signed=False keeps the network's own sign."""
+    w1, w2 = widths
     t = Tree(points, theta=THETA)
     _, feat = knn16(t)
     d = mlp.forward(feat)
-    mu_s = t.iterate(n_iter=N_ITER, last_iter=s, w1=W1, w2=W2)
+    mu_s = t.iterate(n_iter=N_ITER, last_iter=s, w1=w1, w2=w2)
     mu0 = warm_init(d, mu_s, 0.0) if signed else warm_init(d, None, float(mu_s.norm(dim=1).mean()))
     first = max(s + 1, N_ITER - k + 1)
-    mu = t.iterate(mu0, n_iter=N_ITER, first_iter=first, w1=W1, w2=W2) if k > 0 else mu0
+    mu = t.iterate(mu0, n_iter=N_ITER, first_iter=first, w1=w1, w2=w2) if k > 0 else mu0
     t.close()
     return mu
 
@@ -172,6 +173,30 @@ def evaluate(mlp: Mlp, heldout_seeds, plain_iters=(2, 3, 5, 10, 20, 40),
     return summary, rows
 
 
+def evaluate_workload(mlp: Mlp, name: str = "union500k", seed: int = 3000, widths=(0.002, 0.016),
+                      plain_iters=(5, 10, 20, 40), warm=((1, 4), (1, 9), (3, 2), (3, 7), (3, 17))):
+    """Plain and warm solves of one benchmark workload (the 500,000-point
+    union by default, with its widths), timed whole including the tree build;
+    orientation accuracy against the primitives' normals (outliers excluded)."""
+    synth = _synth()
+    c = synth.config_cloud(name, seed=seed)
+    pts = torch.from_numpy(c.points).cuda()
+    out = {"workload": name, "n": len(c.points), "widths": list(widths)}
+    for n in plain_iters:
+        mu, dt = _timed(lambda: plain_solve(pts, n, widths))
+        p_co, ae = _metrics(c.normals, mu.cpu().numpy(), c.valid)
+        out[f"plain{n}"] = {"p_co": p_co, "ae_pcd": ae, "time_s": dt}
+    for s_, k in warm:
+        mu, dt = _timed(lambda: warm_solve(pts, mlp, k, s_, widths=widths))
+        p_co, ae = _metrics(c.normals, mu.cpu().numpy(), c.valid)
+        out[f"warm_s{s_}_k{k}"] = {"p_co": p_co, "ae_pcd": ae, "time_s": dt}
+    t = Tree(pts, theta=THETA)
+    (_, feat), out["t_knn_s"] = _timed(lambda: knn16(t))
+    _, out["t_mlp_s"] = _timed(lambda: mlp.forward(feat))
+    t.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=200)
@@ -180,6 +205,8 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--loss", type=int, default=1, help="0: 1 - c, 1: 1 - c^2 (sign-free)")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--workload", default=None,
+                    help="also compare plain and warm solves on this benchmark cloud (e.g. union500k)")
     a = ap.parse_args(argv)
     synth = _synth()
     t0 = time.perf_counter()
@@ -195,6 +222,9 @@ def main(argv=None):
     res = {"loss_mode": a.loss, "train_clouds": a.train, "train_samples": int(X.shape[0]), "epochs": a.epochs,
            "loss_per_epoch": hist, "t_data_s": t_data, "t_train_s": t_train,
            "heldout": a.heldout, "summary": summary, "per_cloud": rows}
+    if a.workload:
+        res["workload"] = evaluate_workload(mlp, a.workload)
+        print(json.dumps({"workload": res["workload"]}, indent=1))
     txt = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:
