@@ -920,49 +920,44 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
     }
 }
 
-// Near part, first kernel: target-major pair sums.  One warp per work item
-// (a slice of one target group's near ranges).  Lanes h*16 + k (h = 0, 1)
-// hold targets k and k + 16 of the group (point and s_i).  The item's near
-// sources are staged 32 at a time as in the gather; half-warp h takes sources
-// 8h .. 8h+7 of each 16, and each lane forms, for each of its 8 sources, the
-// sum of its two targets' terms.  A reduce-scatter over the 16 lanes of the
-// half-warp (three halving shuffle stages, then one full stage; no selects)
-// leaves each source's sum over the group's targets in two lanes, one of
-// which writes it to the (group, source) near slot.  The second kernel adds each point's
-// slots in a fixed order.
-__global__ void WNNC_GATHER_BOUNDS k_adj_near_pairs(AdjArgs A) {
+// Near part, first kernel: the pair sums of each (group, source) near slot.
+// One warp per work item (a slice of one target group's near ranges).  The
+// group's targets (negated point, s_i) are staged once in shared memory;
+// each lane takes two sources of a batch of 64 from the item's near stream
+// (stream positions base + lane and base + 32 + lane: the ranges
+// concatenated, as in the gather) and sums, for each, the terms of all the
+// group's targets in target order, with paired FP32 instructions (one staged
+// target against the lane's two sources).  A source's sum lands whole in its
+// lane and goes to its near slot; the next batch's sources are read while the
+// current batch is summed.  The second kernel adds each point's slots in a
+// fixed order.
+__global__ void WNNC_CAPPED_BOUNDS k_adj_near_pairs(AdjArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
-    __shared__ float4 sp_all[kGatherWarps][32];
-    __shared__ int ss_all[kGatherWarps][32];
+    __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
     if (it >= A.nitems) return;
     const Item item = A.items[it];
     if (item.q0 >= item.q1) return;
-    float4* sp = sp_all[wl];
-    int* ss = ss_all[wl];
+    float4* tp = tp_all[wl];
     const int g = item.g;
-    const int i0 = A.goff[g], gsize = A.goff[g + 1] - i0;
+    const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
     const float4 o = A.gorig[g];
-    const int h = lane >> 4, tl = lane & 15;
-    // this lane's two targets; past the group: the group's first point with s = 0
-    float4 ta, tb;
     {
-        const int ka = tl < gsize ? tl : 0, kb = tl + 16 < gsize ? tl + 16 : 0;
-        const int64_t ia = (int64_t)i0 + ka, ib = (int64_t)i0 + kb;
-        ta = shift(A.corig[ia >> 5], o, A.pos[ia]);
-        tb = shift(A.corig[ib >> 5], o, A.pos[ib]);
-        ta.w = tl < gsize ? A.sv[ia] : 0.f;
-        tb.w = tl + 16 < gsize ? A.sv[ib] : 0.f;
+        const int64_t i = (int64_t)i0 + lane;
+        float4 p = lane < cnt_t ? shift(A.corig[i >> 5], o, A.pos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        p.w = lane < cnt_t ? A.sv[i] : 0.f;
+        tp[lane] = make_float4(-p.x, -p.y, -p.z, p.w);   // negated: the paired terms add them
     }
     const float4 blo = A.gbl[g], bhi = A.gbh[g];
+    __syncwarp();
 
-    float4 my_p = make_float4(0.f, 0.f, 0.f, 0.f), my_c = my_p;
-    int my_slot = 0;
     int qn = item.q0;                 // first range not yet in a window
     int wx = 0, wpre = 0, wslot = 0;  // this lane's range in the window: start, stream offset, slot
     int wn = 0, wtot = 0, cur = 0;    // ranges in the window, their points, stream position
-    auto next_near = [&]() {
+    // the next (up to) 32 sources of the stream into lanes 0..cnt-1: point
+    // dp in chunk frame dc, near slot ds; returns cnt (< 32 only at the end)
+    auto next_near = [&](float4& dp, float4& dc, int& ds) {
         int cnt = 0;
         while (cnt < 32) {
             if (cur == wtot) {
@@ -1002,73 +997,55 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_near_pairs(AdjArgs A) {
             const int rs = __shfl_sync(kFull, wslot, k);
             if (lane >= cnt && lane < cnt + take) {
                 const int j = rx + (x - pk);
-                my_p = A.pos[j];
-                my_c = A.corig[j >> 5];
-                my_slot = rs + (x - pk);
+                dp = A.pos[j];
+                dc = A.corig[j >> 5];
+                ds = rs + (x - pk);
             }
             cnt += take;
             cur += take;
         }
         return cnt;
     };
-    // one half-warp's 8 sources (staged from `base`) against this lane's two
-    // targets, reduced over the half-warp; the sums go to their near slots.
-    // The lane forms the terms of source base + (k ^ m) in v[k], m = lane
-    // bits 3..1, so that every shuffle stage keeps the lower half of v and
-    // sends the upper half; the lane ends with the sum of source base + m.
-    const int m = (lane >> 1) & 7;
-    // the two targets in the halves of float2 (paired FP32 instructions)
-    const float2 ntx = make_float2(-ta.x, -tb.x), nty = make_float2(-ta.y, -tb.y), ntz = make_float2(-ta.z, -tb.z);
-    const float2 tw = make_float2(ta.w, tb.w);
-    auto sum8 = [&](int base, int cnt, auto cut_tag) {
-        constexpr bool CUT = decltype(cut_tag)::value;
-        float v[8][3];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float4 p = sp[base + (k ^ m)];
-            float2 dx, dy, dz, q;
-            adj_term2<CUT>(make_float2(p.x, p.x), make_float2(p.y, p.y), make_float2(p.z, p.z), ntx, nty, ntz, tw,
-                           A.w2, dx, dy, dz, q);
-            // the first target's term, then the second's added by one fma
-            v[k][0] = fmaf(q.y, dx.y, q.x * dx.x);
-            v[k][1] = fmaf(q.y, dy.y, q.x * dy.x);
-            v[k][2] = fmaf(q.y, dz.y, q.x * dz.x);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) v[k][c] += __shfl_xor_sync(kFull, v[k + 4][c], 8);
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) v[k][c] += __shfl_xor_sync(kFull, v[k + 2][c], 4);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            v[0][c] += __shfl_xor_sync(kFull, v[1][c], 2);
-            v[0][c] += __shfl_xor_sync(kFull, v[0][c], 1);
-        }
-        const int src = base + m;
-        if ((lane & 1) == 0 && src < cnt) A.near_contrib[ss[src]] = make_float4(v[0][0], v[0][1], v[0][2], 0.f);
-    };
 
-    int cnt = next_near();
-    while (cnt > 0) {
-        bool clear = true;
-        if (lane < cnt) {
-            const float4 p = shift(my_c, o, my_p);
-            clear = box_gap2(blo, bhi, p) >= A.fast2;
-            sp[lane] = p;
-            ss[lane] = my_slot;
-        }
+    float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), c0 = p0, p1 = p0, c1 = p0;
+    int s0 = 0, s1 = 0;
+    int n0 = next_near(p0, c0, s0);
+    int n1 = n0 == 32 ? next_near(p1, c1, s1) : 0;
+    while (n0 > 0) {
+        const bool v0 = lane < n0, v1 = lane < n1;
+        const float4 bp0 = shift(c0, o, p0), bp1 = shift(c1, o, p1);
+        const int slot0 = s0, slot1 = s1;
+        bool clear = (!v0 || box_gap2(blo, bhi, bp0) >= A.fast2) && (!v1 || box_gap2(blo, bhi, bp1) >= A.fast2);
         clear = __all_sync(kFull, clear);
-        __syncwarp();
-        const int cnt_next = next_near();
-        for (int sb = 0; sb < cnt; sb += 16) {
-            if (clear) sum8(sb + 8 * h, cnt, std::false_type{});
-            else sum8(sb + 8 * h, cnt, std::true_type{});
+        // the next batch's sources, read while this batch is summed
+        int m0 = 0, m1 = 0;
+        if (n1 == 32) {
+            m0 = next_near(p0, c0, s0);
+            if (m0 == 32) m1 = next_near(p1, c1, s1);
         }
-        __syncwarp();
-        cnt = cnt_next;
+        // the two sources' sums in the halves of float2
+        const float2 px = make_float2(bp0.x, bp1.x), py = make_float2(bp0.y, bp1.y), pz = make_float2(bp0.z, bp1.z);
+        float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+        auto term = [&](const float4& tk, auto cut_tag) {
+            constexpr bool CUT = decltype(cut_tag)::value;
+            float2 dx, dy, dz, q;
+            adj_term2<CUT>(px, py, pz, make_float2(tk.x, tk.x), make_float2(tk.y, tk.y), make_float2(tk.z, tk.z),
+                           make_float2(tk.w, tk.w), A.w2, dx, dy, dz, q);
+            ax = __ffma2_rn(q, dx, ax);
+            ay = __ffma2_rn(q, dy, ay);
+            az = __ffma2_rn(q, dz, az);
+        };
+        if (clear) {
+#pragma unroll kUnroll
+            for (int k = 0; k < cnt_t; ++k) term(tp[k], std::false_type{});
+        } else {
+#pragma unroll kUnroll
+            for (int k = 0; k < cnt_t; ++k) term(tp[k], std::true_type{});
+        }
+        if (v0) A.near_contrib[slot0] = make_float4(ax.x, ay.x, az.x, 0.f);
+        if (v1) A.near_contrib[slot1] = make_float4(ax.y, ay.y, az.y, 0.f);
+        n0 = m0;
+        n1 = m1;
     }
 }
 
