@@ -604,6 +604,57 @@ __global__ void k_gather_tot3(const int* a, const int* b, const int* c, int* out
     }
 }
 
+// Classes of the node moments (see build_tree): flags per node in four
+// arrays of nn + 1 (the exclusive sums put the totals in the last entry):
+// warp class (mid), top, front, leaf.
+__global__ void k_mom_flags(const int* nchild, const int* count, const int* parent, int nn, int* fl) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nn) return;
+    const int64_t st = (int64_t)nn + 1;
+    const int cnt = count[b], nc = nchild[b], p = parent[b];
+    const bool top = cnt > kMomDirect && nc > 0;
+    const bool ptop = p >= 0 && count[p] > kMomDirect;   // a parent always has children
+    fl[b] = !top && cnt > kMomSmall;
+    fl[st + b] = top;
+    fl[2 * st + b] = !top && ptop;
+    fl[3 * st + b] = nc == 0;
+}
+
+__global__ void k_mom_totals(const int* fl, int nn, int* tot) {
+    const int c = threadIdx.x;
+    if (c < 4) tot[c] = fl[c * ((int64_t)nn + 1) + nn];
+}
+
+// The lists from the exclusive sums of the flags (a node is in a list where
+// its offset differs from the next one); front keys = (first point, node).
+__global__ void k_mom_lists(const int* off, int nn, const int* start, int* mid, int* top, uint64_t* fkeys) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nn) return;
+    const int64_t st = (int64_t)nn + 1;
+    if (off[b + 1] != off[b]) mid[off[b]] = b;
+    if (off[st + b + 1] != off[st + b]) top[off[st + b]] = b;
+    if (off[2 * st + b + 1] != off[2 * st + b])
+        fkeys[off[2 * st + b]] = ((uint64_t)(uint32_t)start[b] << 32) | (uint32_t)b;
+}
+
+// Per top node: the range of the (sorted) front that covers its points.
+__global__ void k_mom_top_ranges(const int* top, int ntop, const int* start, const int* count,
+                                 const uint64_t* fkeys, int nfront, int2* rng) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ntop) return;
+    const int b = top[k];
+    auto lower = [&](uint32_t v) {
+        int lo = 0, hi = nfront;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((uint32_t)(fkeys[mid] >> 32) < v) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    rng[k] = make_int2(lower((uint32_t)start[b]), lower((uint32_t)(start[b] + count[b])));
+}
+
 __global__ void k_low32(const uint64_t* keys, int64_t n, int* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (int)(uint32_t)(keys[i] & 0xffffffffu);
@@ -1316,49 +1367,51 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     WNNC_LAUNCH_CHECK();
     wait_before_free(s);
     pool_free(sum);
+    // the classes of the moment sums: nodes summed over their points by one
+    // thread (<= kMomSmall points) or one warp (up to kMomDirect points, and
+    // leaves of any size: a leaf at the depth limit may hold more); the inner
+    // nodes above that ("top") are summed from their "front", the summed nodes
+    // whose parent is a top node, which partition a top node's points in
+    // Morton order.  Lists by flags and prefix sums (ascending node id); the
+    // front sorted by first point.
     {
-        std::vector<int> nc(t.nnodes), cnt(t.nnodes), st(t.nnodes), par(t.nnodes);
-        WNNC_CUDA(cudaMemcpy(nc.data(), t.node_nchild, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
-        WNNC_CUDA(cudaMemcpy(cnt.data(), t.node_count, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
-        WNNC_CUDA(cudaMemcpy(st.data(), t.node_start, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
-        WNNC_CUDA(cudaMemcpy(par.data(), t.node_parent, sizeof(int) * t.nnodes, cudaMemcpyDeviceToHost));
-        t.nleaves = (int)std::count(nc.begin(), nc.end(), 0);
-        // the classes of the moment sums: nodes summed over their points by
-        // one thread (<= kMomSmall points) or one warp (up to kMomDirect
-        // points, and leaves of any size: a leaf at the depth limit may hold
-        // more); the inner nodes above that ("top") are summed from their
-        // "front", the summed nodes whose parent is a top node, which
-        // partition a top node's points in Morton order
-        std::vector<int> mid, top, front;
-        auto is_top = [&](int b) { return cnt[b] > kMomDirect && nc[b] > 0; };
-        for (int b = 0; b < t.nnodes; ++b) {
-            if (is_top(b)) top.push_back(b);
-            else if (cnt[b] > kMomSmall) mid.push_back(b);
-            if (!is_top(b) && par[b] >= 0 && is_top(par[b])) front.push_back(b);
-        }
-        std::sort(front.begin(), front.end(), [&](int a, int b) { return st[a] < st[b]; });
-        std::vector<int> fst(front.size());
-        for (size_t k = 0; k < front.size(); ++k) fst[k] = st[front[k]];
-        std::vector<int2> rng(top.size());
-        for (size_t k = 0; k < top.size(); ++k) {
-            const int b = top[k];
-            rng[k].x = (int)(std::lower_bound(fst.begin(), fst.end(), st[b]) - fst.begin());
-            rng[k].y = (int)(std::lower_bound(fst.begin(), fst.end(), st[b] + cnt[b]) - fst.begin());
-        }
-        t.nmom_mid = (int)mid.size();
-        t.mom_mid = dalloc<int>(mid.size());
-        t.nmom_top = (int)top.size();
-        t.mom_top = dalloc<int>(top.size());
-        t.mom_top_rng = dalloc<int2>(top.size());
-        t.mom_front = dalloc<int>(front.size());
-        auto up = [&](void* dst, const void* src, size_t bytes) {
-            if (bytes) WNNC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
-        };
-        up(t.mom_mid, mid.data(), sizeof(int) * mid.size());
-        up(t.mom_top, top.data(), sizeof(int) * top.size());
-        up(t.mom_top_rng, rng.data(), sizeof(int2) * rng.size());
-        up(t.mom_front, front.data(), sizeof(int) * front.size());
+        const int nn = t.nnodes;
+        int* fl = dalloc<int>(4 * ((size_t)nn + 1));   // flags, then offsets: mid, top, front, leaf
+        k_mom_flags<<<ceil_div(nn, kTB), kTB, 0, s>>>(t.node_nchild, t.node_count, t.node_parent, nn, fl);
+        WNNC_LAUNCH_CHECK();
+        // in place; entry nn of each array receives the total
+        for (int c = 0; c < 4; ++c) exclusive_scan_i32(fl + c * ((int64_t)nn + 1), fl + c * ((int64_t)nn + 1), nn, s);
+        int* tot = dalloc<int>(4);
+        k_mom_totals<<<1, 32, 0, s>>>(fl, nn, tot);
+        WNNC_LAUNCH_CHECK();
+        int h[4];
+        WNNC_CUDA(cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, s));
         WNNC_CUDA(cudaStreamSynchronize(s));
+        t.nmom_mid = h[0];
+        t.nmom_top = h[1];
+        t.nleaves = h[3];
+        const int nfront = h[2];
+        t.mom_mid = dalloc<int>(h[0]);
+        t.mom_top = dalloc<int>(h[1]);
+        t.mom_top_rng = dalloc<int2>(h[1]);
+        t.mom_front = dalloc<int>(nfront);
+        uint64_t* fkeys = dalloc<uint64_t>(nfront);
+        k_mom_lists<<<ceil_div(nn, kTB), kTB, 0, s>>>(fl, nn, t.node_start, t.mom_mid, t.mom_top, fkeys);
+        WNNC_LAUNCH_CHECK();
+        radix_sort_pairs(fkeys, nullptr, nfront, 32 + bits_for(n), s, 32);   // node ids already ascending
+        if (nfront > 0) {
+            k_low32<<<ceil_div(nfront, kTB), kTB, 0, s>>>(fkeys, nfront, t.mom_front);
+            WNNC_LAUNCH_CHECK();
+        }
+        if (h[1] > 0) {
+            k_mom_top_ranges<<<ceil_div(h[1], kTB), kTB, 0, s>>>(t.mom_top, h[1], t.node_start, t.node_count, fkeys,
+                                                                  nfront, t.mom_top_rng);
+            WNNC_LAUNCH_CHECK();
+        }
+        wait_before_free(s);
+        pool_free(fl);
+        pool_free(tot);
+        pool_free(fkeys);
     }
 
     // --- the points as targets: same Morton order as the sources ---
