@@ -865,7 +865,7 @@ __global__ void WNNC_CAPPED_BOUNDS k_adj_far(AdjArgs A) {
 // node-major list) 32 x kNodeGathers at a time, kNodeGathers independent
 // gathers per lane in flight, then reduce.  The kernel is bound by the latency
 // of the gathers.
-constexpr int kNodeGathers = 8;
+constexpr int kNodeGathers = 16;
 __global__ void k_adj_node(int nnodes, const int* tfar_off, const int* tfar_ent, const float4* contrib,
                            float4* vnode) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
