@@ -295,6 +295,33 @@ def test_query_points_inside_outside():
     check_close(Gq, Gqo, bq, what="grad at queries")
 
 
+def test_grid_field_of_a_sphere():
+    """The winding-number field on a grid (Eq. 5 at off-surface nodes, Thm. 1):
+    about 1 at the nodes inside a densely sampled sphere with outward normals,
+    about 0 outside, and equal to the oracle's treecode at the same nodes.  The
+    grid goes to the treecode in several chunks; the treecode groups the
+    queries of one call, so each chunk is compared with the oracle on that
+    chunk's queries."""
+    W = _wnnc()
+    from paper_2405_16634_b300 import wnf
+    c = synth.fibonacci_sphere(40000)
+    n = len(c.points)
+    mu = (c.normals * (4 * math.pi / n)).astype(np.float32)
+    pts = torch.from_numpy(c.points).cuda()
+    t = W.Tree(pts, theta=0.3)
+    lo, side = wnf.grid_box(pts, pad=0.2)
+    res, chunk = 24, 5000
+    F = wnf.grid_field(t, torch.from_numpy(mu).cuda(), lo, side, res, w=0.0, chunk=chunk).cpu().numpy().ravel()
+    q = wnf.grid_points(lo, side, res).cpu().numpy()
+    r = np.linalg.norm(q.astype(np.float64), axis=1)
+    assert (r < 0.7).sum() > 500 and (r > 1.3).sum() > 500
+    assert np.abs(F[r < 0.7] - 1).max() < 2e-3
+    assert np.abs(F[r > 1.3]).max() < 2e-3
+    for k0 in range(0, len(q), chunk):
+        Fo, b = oracle.eval_at(OP_A, c.points, mu, q[k0:k0 + chunk], 0.0, theta=f32(0.3), with_bounds=True)
+        check_close(F[k0:k0 + chunk], Fo, b, what=f"grid field, chunk at node {k0}")
+
+
 @pytest.mark.parametrize("n,leaf,depth", [(1, 32, 15), (2, 32, 15), (33, 32, 15), (500, 1, 15),
                                           (3000, 32, 3), (4097, 64, 15)])
 def test_edge_sizes(n, leaf, depth):
