@@ -111,12 +111,13 @@ wnnc_status wnnc_iter_params_default(wnnc_iter_params* p);
  * node boxes and centroids, and the interaction lists of the points as
  * targets (Alg. 4's far / recurse / leaf-direct decisions, taken once per
  * group of at most 32 Morton-consecutive targets against its bounding box).
- *   pts    device, float32 [n][3], caller units; read during the call only.
+ *   pts    device, float32 [n][3], caller units, all finite; read during the
+ *          call only.
  *   n      number of points, >= 1.
  *   params host, may be NULL for the defaults.
  *   out    host; receives the new tree (NULL on failure).
- * Synchronises with `stream`.  Errors: WNNC_EINVAL, WNNC_ENOMEM, WNNC_ECUDA,
- * WNNC_ECAPACITY.
+ * Synchronises with `stream`.  Errors: WNNC_EINVAL (also for a NaN or
+ * infinite coordinate), WNNC_ENOMEM, WNNC_ECUDA, WNNC_ECAPACITY.
  */
 wnnc_status wnnc_build_tree(const float* pts, int64_t n, const wnnc_tree_params* params,
                             void* stream, wnnc_tree** out);
@@ -148,7 +149,7 @@ wnnc_status wnnc_eval_adjoint(const wnnc_tree* tree, const float* s, float w, fl
 /*
  * F(q_k; mu) (grad = 0) or grad F(q_k; mu) (grad = 1) at m query points that
  * need not be input points (Thm. 1: 1 inside, 0 outside, 1/2 on the surface).
- *   q   device, float32 [m][3], caller units;  m >= 1.
+ *   q   device, float32 [m][3], caller units, all finite (else WNNC_EINVAL);  m >= 1.
  *   out device, float32 [m] (grad = 0) or [m][3] (grad = 1).
  * Builds the queries' interaction lists (allocates) and synchronises with `stream`.
  */

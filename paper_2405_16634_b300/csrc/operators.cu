@@ -1124,9 +1124,10 @@ __global__ void k_perm_out_vec(const float4* in, const int64_t* perm, int64_t n,
     out[j + 2] = v.z * f;
 }
 __global__ void k_normalize_queries(const float* q, int64_t m, double cx, double cy, double cz,
-                                    double s, double* qn) {
+                                    double s, double* qn, int* bad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
+    if (!isfinite(q[3 * i]) || !isfinite(q[3 * i + 1]) || !isfinite(q[3 * i + 2])) *bad = 1;
     qn[3 * i] = __dmul_rn(__dsub_rn((double)q[3 * i], cx), s);
     qn[3 * i + 1] = __dmul_rn(__dsub_rn((double)q[3 * i + 1], cy), s);
     qn[3 * i + 2] = __dmul_rn(__dsub_rn((double)q[3 * i + 2], cz), s);
@@ -1532,9 +1533,19 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
              cudaStream_t s) {
     const float s2 = (float)(t.scale * t.scale);
     double* qn = dalloc<double>(3 * m);
+    int* bad = dalloc<int>(1);
+    WNNC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     k_normalize_queries<<<ceil_div(m, kTB), kTB, 0, s>>>(q, m, t.center[0], t.center[1], t.center[2],
-                                                         t.scale, qn);
+                                                         t.scale, qn, bad);
     WNNC_LAUNCH_CHECK();
+    int hbad = 0;
+    WNNC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    pool_free(bad);
+    if (hbad) {
+        pool_free(qn);
+        fail(WNNC_EINVAL, "query coordinates must be finite");
+    }
     TargetSet Q;
     float4* pacc = nullptr;
     try {

@@ -33,6 +33,10 @@ __global__ void k_bbox_partial(const float* pts, int64_t n, double* part) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             double v = (double)pts[3 * i + k];
+            if (!isfinite(v)) {          // the box becomes infinite: the host rejects the cloud
+                lo[k] = -INFINITY;
+                hi[k] = INFINITY;
+            }
             lo[k] = fmin(lo[k], v);
             hi[k] = fmax(hi[k], v);
         }
@@ -1292,6 +1296,8 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     k_normalize_keys<<<ceil_div(n, kTB), kTB, 0, s>>>(pts, n, cs, xn, t.keys, idx);
     WNNC_LAUNCH_CHECK();
     WNNC_CUDA(cudaStreamSynchronize(s));
+    if (!(hcs[3] > 0.0) || !std::isfinite(hcs[3]))
+        fail(WNNC_EINVAL, "point coordinates must be finite");
     for (int k = 0; k < 3; ++k) t.center[k] = hcs[k];
     t.scale = hcs[3];
     radix_sort_pairs(t.keys, idx, n, kKeyBits, s);

@@ -413,6 +413,17 @@ def test_errors_are_reported():
         W.Tree(torch.rand(100, 3, device="cuda"), theta=float("nan"))
     with pytest.raises(W.WnncError):
         t.iterate(n_iter=0)
+    for bad in (float("nan"), float("inf")):
+        p = torch.rand(100, 3, device="cuda")
+        p[17, 1] = bad
+        with pytest.raises(W.WnncError) as e:
+            W.Tree(p)
+        assert e.value.status == 1 and "finite" in str(e.value)
+        q = torch.rand(50, 3, device="cuda")
+        q[3, 2] = bad
+        with pytest.raises(W.WnncError) as e:
+            t.eval_at(torch.zeros(100, 3, device="cuda"), q, 0.0)
+        assert e.value.status == 1
     t.sync_status()
 
 
