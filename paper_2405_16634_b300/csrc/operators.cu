@@ -40,14 +40,19 @@ constexpr int kGatherWarps = 4;
 #ifndef WNNC_UNROLL
 #define WNNC_UNROLL 16
 #endif
-// The treecode gather and the far adjoint sums run with at least 6 resident
-// blocks per SM (the register cap that measured fastest; a few bytes spill in
-// the gather); the other pair kernels take the registers they need.
+// The treecode gather runs with at least 6 resident blocks per SM and the
+// two adjoint pair kernels with at least 7 (the register caps that measured
+// fastest; a few bytes spill in the gather); the other kernels take the
+// registers they need.
 #ifndef WNNC_GATHER_MINB
 #define WNNC_GATHER_MINB 6
 #endif
+#ifndef WNNC_ADJ_MINB
+#define WNNC_ADJ_MINB 7
+#endif
 #define WNNC_GATHER_BOUNDS __launch_bounds__(32 * kGatherWarps)
 #define WNNC_CAPPED_BOUNDS __launch_bounds__(32 * kGatherWarps, WNNC_GATHER_MINB)
+#define WNNC_ADJ_BOUNDS __launch_bounds__(32 * kGatherWarps, WNNC_ADJ_MINB)
 constexpr int kUnroll = WNNC_UNROLL;
 // targets per lane of the treecode gather (1 or 2)
 #ifndef WNNC_GATHER_TPL
@@ -800,7 +805,7 @@ __device__ __forceinline__ void adj_term2(const float2& px, const float2& py, co
 // group's targets, staged once in shared memory, so that each target load
 // serves two pair terms.  The node ids of batch k + 2 and the node centroids
 // of batch k + 1 are read while batch k is summed.
-__global__ void WNNC_CAPPED_BOUNDS k_adj_far(AdjArgs A) {
+__global__ void WNNC_ADJ_BOUNDS k_adj_far(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
@@ -931,7 +936,7 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
 // lane and goes to its near slot; the next batch's sources are read while the
 // current batch is summed.  The second kernel adds each point's slots in a
 // fixed order.
-__global__ void WNNC_CAPPED_BOUNDS k_adj_near_pairs(AdjArgs A) {
+__global__ void WNNC_ADJ_BOUNDS k_adj_near_pairs(AdjArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
