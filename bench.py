@@ -54,7 +54,7 @@ FLOPS_A, FLOPS_AT, FLOPS_G, FLOPS_AG = 18, 18, 31, 33
 FLOPS_ITER = 2 * FLOPS_AG + FLOPS_AT               # A+G(mu), A^T(s), A+G(r) per iteration
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
 # DRAM bytes (read + write) of one launch of the fused A+G kernel on union500k, from ncu
-# (profiles/union500k_treecode_kernels.md); None once the kernel has changed.
+# (one ncu capture of that kernel on this workload); None once the kernel has changed.
 AG_TRAFFIC_BYTES = 107.133440e6 + 6.868736e6
 
 
@@ -340,7 +340,7 @@ def run_gpu(args):
                      "bound": "alu", "achieved": g_achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": g_achieved / peak,
                      # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
-                     # kernel (ncu, profiles/union500k_treecode_kernels.md); only valid for
+                     # kernel (one ncu capture on this workload); only valid for
                      # the default workload and the kernel version that was profiled
                      "traffic": AG_TRAFFIC_BYTES if CONFIG_NAME == "union500k" else None,
                      "traffic_unit": "bytes",
