@@ -64,7 +64,42 @@ k_knn16(int ngroups, const int* goff, const float4* pos, const float4* corig, co
 
     float dk[kK];
     int ik[kK];
-    double r = (double)ncell[leaf_of[i0]].w;   // width of the first target's leaf
+    // First radius: the largest over the lanes of the 16th distance among the
+    // lane's 32 Morton-order neighbours (sorted points i - 16 .. i + 16).  It
+    // bounds every lane's true 16th distance from above, so one search of
+    // that radius (with the 0.1 % margin of the test below) finds all the
+    // neighbours; isolated points (outliers) no longer double the radius from
+    // their leaf's width through many passes.  Fewer than 16 such neighbours:
+    // the width of the first target's leaf, doubled as needed.
+    double r = (double)ncell[leaf_of[i0]].w;
+    {
+        const int n = goff[ngroups];
+#pragma unroll
+        for (int k = 0; k < kK; ++k) dk[k] = INFINITY;
+        if (valid) {
+            for (int q = -kK; q <= kK; ++q) {
+                const int j = i + q;
+                if (q == 0 || j < 0 || j >= n) continue;
+                const float4 p = kshift(corig[j >> 5], o, pos[j]);
+                const float dx = p.x - t.x, dy = p.y - t.y, dz = p.z - t.z;
+                float cd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+#pragma unroll
+                for (int k = 0; k < kK; ++k) {
+                    if (cd < dk[k]) {
+                        const float td = dk[k];
+                        dk[k] = cd;
+                        cd = td;
+                    }
+                }
+            }
+        } else {
+            dk[kK - 1] = 0.f;
+        }
+        float b16 = dk[kK - 1];
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) b16 = fmaxf(b16, __shfl_xor_sync(0xffffffffu, b16, o2));
+        if (b16 < INFINITY) r = fmax(sqrt((double)b16 / 0.999) * 1.0001, 1e-9);
+    }
     for (;;) {
 #pragma unroll
         for (int k = 0; k < kK; ++k) { dk[k] = INFINITY; ik[k] = -1; }

@@ -36,6 +36,22 @@ def test_knn16_matches_exhaustive_search(n, seed):
     assert np.allclose(feat, M.patch_features(xn, idx), atol=2e-6)
 
 
+def test_knn16_with_outliers_and_density_contrast():
+    """The benchmark cloud's recipe at 20,000 points: 10x density modulation
+    and 1 % uniform outliers, whose neighbours lie far away."""
+    W = _W()
+    c = synth.config_cloud("union500k", n=20000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    idx, _ = W.knn16(t)
+    idx = idx.cpu().numpy()
+    xn, _, _ = oracle.normalize(c.points)
+    _, od2 = oracle.knn(xn, 16)
+    gd2 = ((xn[idx] - xn[:, None, :]) ** 2).sum(-1)
+    assert np.all(idx != np.arange(len(xn))[:, None])
+    assert np.allclose(np.sqrt(gd2), np.sqrt(od2), rtol=1e-5, atol=1e-7)
+    assert not c.valid.all()
+
+
 def test_knn16_with_fewer_than_17_points():
     W = _W()
     pts = np.random.default_rng(0).uniform(0, 1, (9, 3)).astype(np.float32)
