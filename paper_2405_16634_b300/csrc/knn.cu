@@ -64,14 +64,17 @@ k_knn16(int ngroups, const int* goff, const float4* pos, const float4* corig, co
 
     float dk[kK];
     int ik[kK];
-    // First radius: the largest over the lanes of the 16th distance among the
-    // lane's 32 Morton-order neighbours (sorted points i - 16 .. i + 16).  It
-    // bounds every lane's true 16th distance from above, so one search of
-    // that radius (with the 0.1 % margin of the test below) finds all the
-    // neighbours; isolated points (outliers) no longer double the radius from
-    // their leaf's width through many passes.  Fewer than 16 such neighbours:
-    // the width of the first target's leaf, doubled as needed.
+    // The first search uses the width of the first target's leaf, which is
+    // enough for most groups on a surface.  The largest over the lanes of the
+    // 16th distance among each lane's 32 Morton-order neighbours (sorted
+    // points i - 16 .. i + 16) bounds every lane's true 16th distance from
+    // above, so a search of that radius (with the 0.1 % margin of the test
+    // below) finds all the neighbours: a group the first search does not
+    // finish goes straight to it instead of doubling the radius through many
+    // passes (isolated points, outliers).  Fewer than 16 such neighbours: the
+    // radius doubles.
     double r = (double)ncell[leaf_of[i0]].w;
+    double r_bound = 0.0;
     {
         const int n = goff[ngroups];
 #pragma unroll
@@ -98,7 +101,7 @@ k_knn16(int ngroups, const int* goff, const float4* pos, const float4* corig, co
         float b16 = dk[kK - 1];
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) b16 = fmaxf(b16, __shfl_xor_sync(0xffffffffu, b16, o2));
-        if (b16 < INFINITY) r = fmax(sqrt((double)b16 / 0.999) * 1.0001, 1e-9);
+        if (b16 < INFINITY) r_bound = sqrt((double)b16 / 0.999) * 1.0001;
     }
     for (;;) {
 #pragma unroll
@@ -186,7 +189,7 @@ k_knn16(int ngroups, const int* goff, const float4* pos, const float4* corig, co
         // done when every lane's 16th candidate lies within r (or r covers the cube)
         const bool ok = !valid || dk[kK - 1] <= (float)r2 * 0.999f;
         if (__all_sync(0xffffffffu, ok) || r > 8.0) break;
-        r *= 2.0;
+        r = r_bound > r ? r_bound : 2.0 * r;
     }
     if (valid) {
 #pragma unroll
