@@ -16,9 +16,15 @@ A^T s like s^2 so that <A mu, v> = <mu, A^T v> holds in caller units).
 Parity status of each function (pins live in tests/test_oracle_pins.py):
   direct A, G, A^T   pinned (closed forms on spheres, F(centre)=1, FD of A = -G,
                      adjointness, symmetry, scaling and rotation invariance)
+  paper treecode     pinned (Alg. 4 per target with the Eq. 13-14 representatives:
+  (PaperTree)        theta->0 equals direct, a hand-worked far node for A, G and
+                     A^T, representatives invariant under sign flips of nu and
+                     inside the node's convex hull, second-order far error for
+                     parallel nu, error vs direct falls with theta, octree cells)
   tree A, G, A^T     pinned (theta->0 limit equals direct, error decreases with
-                     theta, exact adjointness of the rep_mode-1 pair, Alg. 4
-                     per-target criterion holds for every far use)
+  (group treecode)   theta in both representative modes, exact adjointness of
+                     the rep_mode-1 pair, Alg. 4 per-target criterion holds for
+                     every far use, the hand-worked far node in rep_mode 0)
   iterate            pinned (first-iteration closed form on a sphere, energy
                      decrease of the exact line search, P_co = 100% on a sphere,
                      the zero-init / no-grad-step behaviour of Sec. 6.1.3)
@@ -45,12 +51,18 @@ GROUP_SLACK = 3     # target groups never straddle leaves without a common ances
 GROUP_MIN_DEPTH = 3  # ... and stay inside one cell of depth 3
 
 
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2 -fopenmp -ffp-contract=off: a C file of the oracle into a shared library."""
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-std=c11", src, "-o", out, "-lm"])
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the C oracle (gcc, -O2, OpenMP, no FP contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-std=c11", _SRC, "-o", _LIB_PATH, "-lm"])
+        compile_source(_SRC, _LIB_PATH)
     return _LIB_PATH
 
 
@@ -60,37 +72,50 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
-        d, i64, P = c_double, c_int64, POINTER
-        L.or_num_threads.restype = c_int
-        L.or_normalize.argtypes = [c_void_p, i64, c_void_p, c_void_p, c_void_p]
-        L.or_direct.argtypes = [c_int, c_void_p, i64, c_void_p, c_void_p, i64, d, d, c_void_p, c_void_p,
-                                c_void_p]
-        L.or_tree_build.argtypes = [c_void_p, i64, c_int, c_int, c_int, d, c_int, c_int]
-        L.or_tree_ngroups.argtypes = [c_void_p]
-        L.or_tree_ngroups.restype = i64
-        L.or_tree_groups.argtypes = [c_void_p, c_void_p]
-        L.or_tree_build.restype = c_void_p
-        L.or_tree_free.argtypes = [c_void_p]
-        L.or_tree_nnodes.argtypes = [c_void_p]
-        L.or_tree_nnodes.restype = i64
-        L.or_tree_nodes.argtypes = [c_void_p] + [c_void_p] * 5
-        L.or_tree_perm.argtypes = [c_void_p, c_void_p]
-        L.or_tree_boxes.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
-        L.or_tree_counts.argtypes = [c_void_p, c_void_p]
-        L.or_tree_lists.argtypes = [c_void_p] + [c_void_p] * 4
-        L.or_tree_apply.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, d, c_void_p, c_void_p]
-        L.or_tree_apply_at.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, i64, c_void_p,
-                                       c_void_p, c_void_p]
-        L.or_schedule_width.argtypes = [c_int, c_int, d, d]
-        L.or_schedule_width.restype = d
-        L.or_schedule_width2.argtypes = [c_int, c_int, d, d, c_int]
-        L.or_schedule_width2.restype = d
-        L.or_iterate.argtypes = [c_void_p, c_void_p, i64, c_void_p, c_int, c_int, c_int, d, d, c_int,
-                                 c_int, c_void_p, c_int, c_int, c_int, c_void_p]
-        L.or_knn.argtypes = [c_void_p, i64, c_int, c_void_p, c_void_p]
-        _lib = L
+        _lib = load(build())
     return _lib
+
+
+def load(path: str):
+    """Load a build of wnnc_oracle.c and declare its C signatures."""
+    L = ctypes.CDLL(path)
+    d, i64, P = c_double, c_int64, POINTER
+    L.or_num_threads.restype = c_int
+    L.or_normalize.argtypes = [c_void_p, i64, c_void_p, c_void_p, c_void_p]
+    L.or_direct.argtypes = [c_int, c_void_p, i64, c_void_p, c_void_p, i64, d, d, c_void_p, c_void_p,
+                            c_void_p]
+    L.or_tree_build.argtypes = [c_void_p, i64, c_int, c_int, c_int, d, c_int, c_int]
+    L.or_tree_ngroups.argtypes = [c_void_p]
+    L.or_tree_ngroups.restype = i64
+    L.or_tree_groups.argtypes = [c_void_p, c_void_p]
+    L.or_tree_build.restype = c_void_p
+    L.or_tree_free.argtypes = [c_void_p]
+    L.or_tree_nnodes.argtypes = [c_void_p]
+    L.or_tree_nnodes.restype = i64
+    L.or_tree_nodes.argtypes = [c_void_p] + [c_void_p] * 5
+    L.or_tree_perm.argtypes = [c_void_p, c_void_p]
+    L.or_tree_boxes.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.or_tree_counts.argtypes = [c_void_p, c_void_p]
+    L.or_tree_lists.argtypes = [c_void_p] + [c_void_p] * 4
+    L.or_tree_apply.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, d, c_void_p, c_void_p]
+    L.or_tree_apply_at.argtypes = [c_void_p, c_int, c_int, d, c_void_p, c_void_p, i64, c_void_p,
+                                   c_void_p, c_void_p]
+    L.or_schedule_width.argtypes = [c_int, c_int, d, d]
+    L.or_schedule_width.restype = d
+    L.or_schedule_width2.argtypes = [c_int, c_int, d, d, c_int]
+    L.or_schedule_width2.restype = d
+    L.or_iterate.argtypes = [c_void_p, c_void_p, d, c_void_p, i64, c_void_p, c_int, c_int, c_int, d, d,
+                             c_int, c_int, c_void_p, c_int, c_int, c_int, c_void_p]
+    L.or_ptree_build.argtypes = [c_void_p, i64, c_int, c_int]
+    L.or_ptree_build.restype = c_void_p
+    L.or_ptree_free.argtypes = [c_void_p]
+    L.or_ptree_nnodes.argtypes = [c_void_p]
+    L.or_ptree_nnodes.restype = i64
+    L.or_ptree_nodes.argtypes = [c_void_p] + [c_void_p] * 6
+    L.or_ptree_apply.argtypes = [c_void_p, c_int, d, d, c_void_p, c_void_p, i64, c_void_p, d, c_void_p,
+                                 c_void_p, c_void_p]
+    L.or_knn.argtypes = [c_void_p, i64, c_int, c_void_p, c_void_p]
+    return L
 
 
 def _p(a):
@@ -233,6 +258,98 @@ class Tree:
 
 
 # ---------------------------------------------------------------------------
+# The paper's treecode (Sec. 4.5, Eq. 13-14, Alg. 4)
+# ---------------------------------------------------------------------------
+
+class PaperTree:
+    """Alg. 4 as printed: a geometric octree of the sources (cubes of
+    [-1,1]^3 split into octants while they hold more than leaf_size points and
+    are shallower than max_depth; leaf_size 1 is the paper's), the
+    nu-representatives of Eq. 13-14 recomputed per call, and for each target
+    a recursion from the root taking node B as far iff
+    |y - x_{B,nu}| > width(B)/theta.  Coordinates are used as given (call
+    ``normalize`` first for the paper's frame)."""
+
+    def __init__(self, x, leaf_size: int = 1, max_depth: int = 15):
+        self.x = _f64(x, (-1, 3))          # kept alive: the C side points into it
+        self.n = self.x.shape[0]
+        self._h = lib().or_ptree_build(_p(self.x), self.n, int(leaf_size), int(max_depth))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().or_ptree_free(self._h)
+            self._h = None
+
+    def apply(self, op: int, nu, w: float, theta: float, y=None, amb_tol: float = 0.0):
+        """(out, info): op at targets y (default: the sources).  info holds
+        'far' and 'near' term counts and, with amb_tol > 0, per-target 'amb'
+        (sum |term| of cut-off-ambiguous pairs plus the branch difference of
+        far decisions within amb_tol of the threshold) and 'abssum'."""
+        y = self.x if y is None else _f64(y, (-1, 3))
+        nt = y.shape[0]
+        nu = _f64(nu, (self.n, 3) if op != OP_AT else (self.n,))
+        out = np.zeros(nt) if op == OP_A else np.zeros((nt, 3))
+        amb = np.zeros(nt) if amb_tol > 0 else None
+        abssum = np.zeros(nt) if amb_tol > 0 else None
+        cnt = np.zeros(2, np.int64)
+        lib().or_ptree_apply(self._h, op, float(theta), float(w), _p(nu), _p(y), nt, _p(out), float(amb_tol),
+                             _p(amb), _p(abssum), _p(cnt))
+        info = {"far": int(cnt[0]), "near": int(cnt[1])}
+        if amb_tol > 0:
+            info.update(amb=amb, abssum=abssum)
+        return out, info
+
+    def nodes(self):
+        m = lib().or_ptree_nnodes(self._h)
+        start = np.zeros(m, np.int64); count = np.zeros(m, np.int64)
+        depth = np.zeros(m, np.int32); nchild = np.zeros(m, np.int32)
+        ctr = np.zeros((m, 3)); idx = np.zeros(self.n, np.int64)
+        lib().or_ptree_nodes(self._h, _p(start), _p(count), _p(depth), _p(nchild), _p(ctr), _p(idx))
+        return dict(start=start, count=count, depth=depth, nchild=nchild, ctr=ctr, idx=idx)
+
+
+def eval_paper(op: int, points, nu, w: float, theta: float, targets=None, leaf_size: int = 1,
+               max_depth: int = 15, amb_tol: float = 0.0):
+    """The paper's treecode (Alg. 4) in caller units, like ``eval_op``:
+    op A: nu = mu -> F;  op G: nu = mu -> grad F = -G;  op AT: nu = s -> A^T s.
+    targets: indices of the points to evaluate at (default all).  Returns
+    (out, info) with info as in ``PaperTree.apply`` (bounds scaled to caller
+    units)."""
+    xn, c, s = normalize(points)
+    y = xn if targets is None else xn[np.asarray(targets)]
+    nu = np.asarray(nu, dtype=np.float64)
+    nun = nu * (s * s) if op != OP_AT else nu
+    out, info = PaperTree(xn, leaf_size, max_depth).apply(op, nun, w, theta, y=y, amb_tol=amb_tol)
+    f = 1.0
+    if op == OP_G:
+        out, f = -out * s, s
+    elif op == OP_AT:
+        out, f = out * (s * s), s * s
+    for k in ("amb", "abssum"):
+        if k in info:
+            info[k] = info[k] * f
+    return out, info
+
+
+def eval_direct_at(op: int, points, nu, w: float, targets=None, amb_tol: float = 1e-5):
+    """The direct sums in caller units at a subset of the points (indices
+    ``targets``, default all), over all points as sources: (out, bounds)."""
+    xn, c, s = normalize(points)
+    y = xn if targets is None else xn[np.asarray(targets)]
+    nu = np.asarray(nu, dtype=np.float64)
+    nun = nu * (s * s) if op != OP_AT else nu
+    out, b = direct(op, xn, nun, w, y=y, amb_tol=amb_tol)
+    f = 1.0
+    if op == OP_G:
+        out, f = -out * s, s
+    elif op == OP_AT:
+        out, f = out * (s * s), s * s
+    if b is not None:
+        b = {k: v * f for k, v in b.items()}
+    return out, b
+
+
+# ---------------------------------------------------------------------------
 # Boundary-shaped entry points (caller units, like the library's C ABI)
 # ---------------------------------------------------------------------------
 
@@ -291,17 +408,23 @@ def eval_at(op: int, points, mu, queries, w: float, theta: float = 0.0, leaf_siz
 def iterate(points, mu0=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0.016,
             theta: float = 0.0, leaf_size: int = 8, max_depth: int = 15, rep_mode: int = 1,
             first_iter: int = 1, last_iter: int | None = None, rescale: int = 0, area=None,
-            use_grad: bool = True, use_wnnc: bool = True, schedule="linear"):
+            use_grad: bool = True, use_wnnc: bool = True, schedule="linear", paper_theta: float = 0.0,
+            paper_leaf_size: int = 1):
     """Alg. 3 on the cloud; returns (mu in caller units, stats[iter] = (w, E, alpha, |r|^2)).
+    Operators: theta > 0 the group treecode (leaf_size, rep_mode); else
+    paper_theta > 0 the paper's treecode (Alg. 4, per target, paper_leaf_size);
+    else the direct sums.
     schedule: the width schedule, "linear" (Alg. 3), "cosine" or "exponential"
     (the alternatives of Sec. 6.1.2; see schedule_width)."""
     xn, c, s, tree = _setup(points, theta, leaf_size, max_depth)
+    ptree = PaperTree(xn, paper_leaf_size, max_depth) if (tree is None and paper_theta > 0) else None
     n = xn.shape[0]
     mu = np.zeros((n, 3)) if mu0 is None else np.array(mu0, dtype=np.float64).reshape(n, 3) * (s * s)
     last = n_iter if last_iter is None else last_iter
     stats = np.zeros((max(last - first_iter + 1, 0), 4))
     ar = None if area is None else np.ascontiguousarray(np.asarray(area, np.float64) * (s * s))
-    lib().or_iterate(tree._h if tree is not None else None, _p(xn), n, _p(mu), n_iter, first_iter,
+    lib().or_iterate(tree._h if tree is not None else None, ptree._h if ptree is not None else None,
+                     float(paper_theta), _p(xn), n, _p(mu), n_iter, first_iter,
                      last, float(w1), float(w2), rep_mode, rescale, _p(ar), int(use_grad),
                      int(use_wnnc), _schedule_code(schedule, w1, w2), _p(stats))
     return mu / (s * s), stats

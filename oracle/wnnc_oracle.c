@@ -26,8 +26,16 @@
  *    c * width(node), c = 1/theta.  Because both the target and the
  *    representative lie in those boxes, every far use also satisfies the
  *    per-target test of Alg. 4 (|x_i - x_B| > c * width(B)).
+ *  - or_ptree_*: the paper's own treecode, Alg. 4 exactly as printed, with no
+ *    design of this build in it: a plain geometric octree (cubes of
+ *    [-1,1]^3 split into octants while a cube holds more than leaf_size
+ *    points and is shallower than D; leaf_size 1 is the paper's), the
+ *    nu-representatives of Eq. 13-14 recomputed for every call, and for
+ *    every target separately a recursion from the root that takes node B
+ *    as far iff |y - x_{B,nu}| > c * width(B).  A^T is the paper's
+ *    s-representative treecode (nu = s).
  *  - or_iterate: Alg. 3 (width schedule, grad step of Alg. 2, WNNC update,
- *    rescale), on either the direct sums or a tree.
+ *    rescale), on the direct sums, the group treecode or the paper's treecode.
  */
 #include <math.h>
 #include <stdint.h>
@@ -731,9 +739,245 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
 }
 
 /* ------------------------------------------------------------------------ */
+/* The paper's treecode (Sec. 4.5, Eq. 13-14, Alg. 4), per target.           */
+/*                                                                          */
+/* Octree: the root is the cube [-1,1]^3 (depth 0, width 2); a cube of      */
+/* depth d has width 2/2^d and is split into its eight octants (a point     */
+/* goes to the upper half of an axis iff its coordinate is >= the cube's    */
+/* centre on that axis) while it holds more than leaf_size points and       */
+/* d < max_depth.  Empty octants are dropped.  Each node's points are one   */
+/* contiguous range of the permutation idx.                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n, nnodes, cap;
+    int leaf_size, max_depth;
+    const double* x;      /* sources, caller's array (n x 3), not copied */
+    int64_t* idx;         /* node ranges index into this permutation of 0..n-1 */
+    int64_t *start, *count;
+    int64_t* child;       /* 8 per node, -1 for an empty octant */
+    int* depth;
+    int* nchild;
+    double* ctr;          /* cube centre (3 per node) */
+} or_ptree;
+
+static int64_t pt_new_node(or_ptree* P) {
+    if (P->nnodes == P->cap) {
+        P->cap = P->cap ? 2 * P->cap : 1024;
+        P->start = realloc(P->start, sizeof(int64_t) * P->cap);
+        P->count = realloc(P->count, sizeof(int64_t) * P->cap);
+        P->child = realloc(P->child, sizeof(int64_t) * 8 * P->cap);
+        P->depth = realloc(P->depth, sizeof(int) * P->cap);
+        P->nchild = realloc(P->nchild, sizeof(int) * P->cap);
+        P->ctr = realloc(P->ctr, sizeof(double) * 3 * P->cap);
+    }
+    int64_t b = P->nnodes++;
+    for (int q = 0; q < 8; ++q) P->child[8 * b + q] = -1;
+    P->nchild[b] = 0;
+    return b;
+}
+
+/* Split node b into octants (recursively).  tmp: scratch of n entries. */
+static void pt_split(or_ptree* P, int64_t b, int64_t* tmp) {
+    if (P->count[b] <= P->leaf_size || P->depth[b] >= P->max_depth) return;
+    const int64_t s = P->start[b], e = s + P->count[b];
+    const double* c = P->ctr + 3 * b;
+    const double quarter = ldexp(1.0, -P->depth[b]) * 0.5;   /* child half-width = width/4 */
+    int64_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int* oct = malloc(sizeof(int) * (size_t)(e - s));
+    for (int64_t k = s; k < e; ++k) {
+        const double* p = P->x + 3 * P->idx[k];
+        int o = (p[0] >= c[0] ? 4 : 0) | (p[1] >= c[1] ? 2 : 0) | (p[2] >= c[2] ? 1 : 0);
+        oct[k - s] = o;
+        cnt[o]++;
+    }
+    int64_t off[8];
+    off[0] = s;
+    for (int o = 1; o < 8; ++o) off[o] = off[o - 1] + cnt[o - 1];
+    int64_t pos[8];
+    memcpy(pos, off, sizeof(pos));
+    for (int64_t k = s; k < e; ++k) tmp[pos[oct[k - s]]++] = P->idx[k];
+    memcpy(P->idx + s, tmp + s, sizeof(int64_t) * (size_t)(e - s));
+    free(oct);
+    for (int o = 0; o < 8; ++o) {
+        if (cnt[o] == 0) continue;
+        int64_t ch = pt_new_node(P);
+        c = P->ctr + 3 * b;                       /* the node arrays may have moved */
+        P->child[8 * b + o] = ch;
+        P->nchild[b]++;
+        P->start[ch] = off[o];
+        P->count[ch] = cnt[o];
+        P->depth[ch] = P->depth[b] + 1;
+        P->ctr[3 * ch + 0] = c[0] + ((o & 4) ? quarter : -quarter);
+        P->ctr[3 * ch + 1] = c[1] + ((o & 2) ? quarter : -quarter);
+        P->ctr[3 * ch + 2] = c[2] + ((o & 1) ? quarter : -quarter);
+    }
+    for (int o = 0; o < 8; ++o)
+        if (P->child[8 * b + o] >= 0) pt_split(P, P->child[8 * b + o], tmp);
+}
+
+or_ptree* or_ptree_build(const double* xs, int64_t n, int leaf_size, int max_depth) {
+    or_ptree* P = calloc(1, sizeof(or_ptree));
+    P->n = n; P->x = xs; P->leaf_size = leaf_size; P->max_depth = max_depth;
+    P->idx = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) P->idx[i] = i;
+    if (n > 0) {
+        int64_t r = pt_new_node(P);
+        P->start[r] = 0; P->count[r] = n; P->depth[r] = 0;
+        P->ctr[0] = P->ctr[1] = P->ctr[2] = 0.0;
+        int64_t* tmp = malloc(sizeof(int64_t) * (size_t)n);
+        pt_split(P, r, tmp);
+        free(tmp);
+    }
+    return P;
+}
+
+void or_ptree_free(or_ptree* P) {
+    if (!P) return;
+    free(P->idx); free(P->start); free(P->count); free(P->child); free(P->depth); free(P->nchild);
+    free(P->ctr);
+    free(P);
+}
+
+int64_t or_ptree_nnodes(const or_ptree* P) { return P->nnodes; }
+/* per node: first index into idx, point count, depth, number of children */
+void or_ptree_nodes(const or_ptree* P, int64_t* start, int64_t* count, int* depth, int* nchild, double* ctr,
+                    int64_t* idx) {
+    for (int64_t b = 0; b < P->nnodes; ++b) {
+        start[b] = P->start[b]; count[b] = P->count[b]; depth[b] = P->depth[b]; nchild[b] = P->nchild[b];
+        for (int k = 0; k < 3; ++k) ctr[3 * b + k] = P->ctr[3 * b + k];
+    }
+    memcpy(idx, P->idx, sizeof(int64_t) * (size_t)P->n);
+}
+
+/* Representatives of one call (Eq. 13, Eq. 14):
+ *   x_{B,nu} = sum_i |nu_i| x_i / sum_j |nu_j|,   nu_B = sum_i nu_i,
+ * |nu_i| the Euclidean length (dim 3) or the absolute value (dim 1).  A
+ * node whose nu all vanish has nu_B = 0 and contributes nothing whichever
+ * way it is used; its representative is then the plain centroid. */
+static void pt_reps(const or_ptree* P, const double* nu, int dim, double* rep, double* nuB) {
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t b = 0; b < P->nnodes; ++b) {
+        double sw = 0.0, sx[3] = {0, 0, 0}, sc[3] = {0, 0, 0}, sn[3] = {0, 0, 0};
+        for (int64_t k = P->start[b]; k < P->start[b] + P->count[b]; ++k) {
+            const int64_t i = P->idx[k];
+            double a = 0.0;
+            for (int q = 0; q < dim; ++q) { sn[q] += nu[dim * i + q]; a += nu[dim * i + q] * nu[dim * i + q]; }
+            a = sqrt(a);
+            sw += a;
+            for (int q = 0; q < 3; ++q) { sx[q] += a * P->x[3 * i + q]; sc[q] += P->x[3 * i + q]; }
+        }
+        for (int q = 0; q < 3; ++q)
+            rep[3 * b + q] = sw > 0.0 ? sx[q] / sw : sc[q] / (double)P->count[b];
+        for (int q = 0; q < dim; ++q) nuB[dim * b + q] = sn[q];
+    }
+}
+
+typedef struct {
+    const or_ptree* P;
+    int op, dim;
+    double c, w2, amb_tol;
+    const double* nu;
+    const double *rep, *nuB;
+} pt_ctx;
+
+typedef struct { double v[3]; double amb, abssum; int64_t far, near; } pt_acc;
+
+/* One term with the cut-off of Sec. 4.4 (kept iff r >= w), d = y - x. */
+static void pt_term(const pt_ctx* C, const double d[3], const double* nu, pt_acc* a) {
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const int amb_p = C->amb_tol > 0.0 && ambiguous(r2, C->w2, C->amb_tol);
+    if (!keep_pair(r2, C->w2) && !amb_p) return;
+    double v[3] = {0, 0, 0};
+    if (C->op == OP_A) v[0] = term_A(d, r2, nu);
+    else if (C->op == OP_G) term_G(d, r2, nu, v);
+    else term_AT(d, r2, nu[0], v);
+    const double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (amb_p) a->amb += vn;
+    if (keep_pair(r2, C->w2)) {
+        for (int k = 0; k < 3; ++k) a->v[k] += v[k];
+        a->abssum += vn;
+    }
+}
+
+/* Alg. 4, apply(y, B): far term, else recurse into the children, else the
+ * leaf's points.  A far decision whose squared distance lies within
+ * amb_tol (c width)^2 of the threshold is "ambiguous": a lower-precision
+ * evaluation may take the other branch, so both branches are evaluated and
+ * their difference is added to the ambiguity budget. */
+static void pt_apply(const pt_ctx* C, const double* y, int64_t b, pt_acc* a) {
+    const or_ptree* P = C->P;
+    const double* xb = C->rep + 3 * b;
+    const double d[3] = {y[0] - xb[0], y[1] - xb[1], y[2] - xb[2]};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double cw = C->c * ldexp(2.0, -P->depth[b]);
+    const int far = C->c < INFINITY && r2 > cw * cw;
+    const int amb_far = C->amb_tol > 0.0 && C->c < INFINITY && fabs(r2 - cw * cw) <= C->amb_tol * cw * cw;
+    pt_acc fa = {{0, 0, 0}, 0, 0, 0, 0}, re = {{0, 0, 0}, 0, 0, 0, 0};
+    if (far || amb_far) {
+        pt_term(C, d, C->nuB + C->dim * b, &fa);
+        fa.far = 1;
+    }
+    if (!far || amb_far) {
+        if (P->nchild[b] > 0) {
+            for (int q = 0; q < 8; ++q)
+                if (P->child[8 * b + q] >= 0) pt_apply(C, y, P->child[8 * b + q], &re);
+        } else {
+            for (int64_t k = P->start[b]; k < P->start[b] + P->count[b]; ++k) {
+                const int64_t j = P->idx[k];
+                const double dj[3] = {y[0] - P->x[3 * j], y[1] - P->x[3 * j + 1], y[2] - P->x[3 * j + 2]};
+                pt_term(C, dj, C->nu + C->dim * j, &re);
+                re.near++;
+            }
+        }
+    }
+    const pt_acc* take = far ? &fa : &re;
+    for (int k = 0; k < 3; ++k) a->v[k] += take->v[k];
+    a->abssum += take->abssum;
+    a->amb += take->amb;
+    a->far += take->far;
+    a->near += take->near;
+    if (amb_far) {
+        const double dd[3] = {fa.v[0] - re.v[0], fa.v[1] - re.v[1], fa.v[2] - re.v[2]};
+        const pt_acc* other = far ? &re : &fa;
+        a->amb += sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]) + other->amb;
+    }
+}
+
+/* Treecode sum of op at nt targets yt (nt x 3):
+ *   op A : nu = mu (ns x 3), out (nt)        op G : nu = mu, out (nt x 3) = -sum HPhi mu
+ *   op AT: nu = s (ns),      out (nt x 3) = sum_i s_i gradPhi(x_i - y)  (s-representatives)
+ * theta = 1/c (0: never far, the direct sum).  amb, abssum (optional, per
+ * target) as in or_direct, amb also covering ambiguous far decisions.
+ * counts (optional): total far (target, node) and near (target, point) terms. */
+void or_ptree_apply(const or_ptree* P, int op, double theta, double w, const double* nu, const double* yt,
+                    int64_t nt, double* out, double amb_tol, double* amb, double* abssum, int64_t* counts) {
+    const int dim = (op == OP_AT) ? 1 : 3;
+    const int64_t nn = P->nnodes > 0 ? P->nnodes : 1;
+    double* rep = malloc(sizeof(double) * 3 * (size_t)nn);
+    double* nuB = malloc(sizeof(double) * (size_t)dim * (size_t)nn);
+    pt_reps(P, nu, dim, rep, nuB);
+    pt_ctx C = {P, op, dim, theta > 0.0 ? 1.0 / theta : INFINITY, eff_w2(w), amb_tol, nu, rep, nuB};
+    int64_t tfar = 0, tnear = 0;
+    #pragma omp parallel for schedule(dynamic, 16) reduction(+ : tfar, tnear)
+    for (int64_t t = 0; t < nt; ++t) {
+        pt_acc a = {{0, 0, 0}, 0, 0, 0, 0};
+        if (P->nnodes > 0) pt_apply(&C, yt + 3 * t, 0, &a);
+        if (op == OP_A) out[t] = a.v[0];
+        else for (int k = 0; k < 3; ++k) out[3 * t + k] = a.v[k];
+        if (amb) amb[t] = a.amb;
+        if (abssum) abssum[t] = a.abssum;
+        tfar += a.far;
+        tnear += a.near;
+    }
+    if (counts) { counts[0] = tfar; counts[1] = tnear; }
+    free(rep); free(nuB);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Alg. 3: n iterations of grad step (Alg. 2) + WNNC update + rescale, with  */
 /* the width schedule of or_schedule_width2 (the paper's is the linear one). */
-/*   T == NULL: the operators are the direct sums over xn.                   */
+/*   T != NULL: the group treecode; else P != NULL: the paper's treecode    */
+/*   (Alg. 4) at opening parameter ptheta; else the direct sums over xn.     */
 /*   mu (n x 3, input order, normalised units) is updated in place.          */
 /*   rescale 0: mu_i <- muhat_i |mu_i| / |muhat_i|  (Alg. 3)                 */
 /*   rescale 1: mu_i <- muhat_i sigma_i / |muhat_i|  (Eq. 19, needs area)    */
@@ -742,9 +986,12 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
 /*   stats (optional, per iteration): w, E = |A mu - b|^2 before the step,   */
 /*   alpha, |r|^2.                                                           */
 /* ------------------------------------------------------------------------ */
-static void apply_op(const or_tree* T, const double* xn, int64_t n, int op, int rep_mode, double w,
-                     const double* nu, double* out) {
+/* The operator of the iteration: the group treecode T, else the paper's
+ * treecode P at opening parameter ptheta, else the direct sums. */
+static void apply_op(const or_tree* T, const or_ptree* P, double ptheta, const double* xn, int64_t n, int op,
+                     int rep_mode, double w, const double* nu, double* out) {
     if (T) or_tree_apply(T, op, rep_mode, w, nu, out, 0.0, NULL, NULL);
+    else if (P) or_ptree_apply(P, op, ptheta, w, nu, xn, n, out, 0.0, NULL, NULL, NULL);
     else or_direct(op, xn, n, nu, xn, n, w, 0.0, out, NULL, NULL);
 }
 
@@ -769,9 +1016,9 @@ double or_schedule_width(int i, int n_iter, double w1, double w2) {
     return or_schedule_width2(i, n_iter, w1, w2, 0);
 }
 
-void or_iterate(const or_tree* T, const double* xn, int64_t n, double* mu, int n_iter, int first_iter,
-                int last_iter, double w1, double w2, int rep_mode, int rescale, const double* area,
-                int use_grad, int use_wnnc, int schedule, double* stats) {
+void or_iterate(const or_tree* T, const or_ptree* P, double ptheta, const double* xn, int64_t n, double* mu,
+                int n_iter, int first_iter, int last_iter, double w1, double w2, int rep_mode, int rescale,
+                const double* area, int use_grad, int use_wnnc, int schedule, double* stats) {
     double* a = malloc(sizeof(double) * (n > 0 ? n : 1));
     double* s = malloc(sizeof(double) * (n > 0 ? n : 1));
     double* r = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
@@ -782,18 +1029,18 @@ void or_iterate(const or_tree* T, const double* xn, int64_t n, double* mu, int n
         double E = 0.0, rr = 0.0, qq = 0.0, alpha = 0.0;
         if (use_grad) {
             /* Alg. 2:  r = A^T b - A^T A mu = A^T (b - A mu);  alpha = r.r / |A r|^2;  mu += alpha r */
-            apply_op(T, xn, n, OP_A, rep_mode, w, mu, a);
+            apply_op(T, P, ptheta, xn, n, OP_A, rep_mode, w, mu, a);
             for (int64_t i = 0; i < n; ++i) { s[i] = 0.5 - a[i]; E += s[i] * s[i]; }
-            apply_op(T, xn, n, OP_AT, rep_mode, w, s, r);
+            apply_op(T, P, ptheta, xn, n, OP_AT, rep_mode, w, s, r);
             for (int64_t i = 0; i < 3 * n; ++i) rr += r[i] * r[i];
-            apply_op(T, xn, n, OP_A, rep_mode, w, r, q);
+            apply_op(T, P, ptheta, xn, n, OP_A, rep_mode, w, r, q);
             for (int64_t i = 0; i < n; ++i) qq += q[i] * q[i];
             alpha = qq > 0.0 ? rr / qq : 0.0;
             for (int64_t i = 0; i < 3 * n; ++i) mu[i] += alpha * r[i];
         }
         if (use_wnnc) {
             /* WNNC update muhat = G_w(mu), then rescale */
-            apply_op(T, xn, n, OP_G, rep_mode, w, mu, muhat);
+            apply_op(T, P, ptheta, xn, n, OP_G, rep_mode, w, mu, muhat);
             for (int64_t i = 0; i < n; ++i) {
                 double hn = sqrt(muhat[3 * i] * muhat[3 * i] + muhat[3 * i + 1] * muhat[3 * i + 1] +
                                  muhat[3 * i + 2] * muhat[3 * i + 2]);

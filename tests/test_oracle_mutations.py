@@ -1,0 +1,64 @@
+"""The representative pins must fail on a wrong oracle (CPU only).
+
+Each case plants one plausible mistake in a copy of the oracle's C source --
+Eq. 13's weights taken as the signed s_i instead of |s_i|, or its
+normalisation by sum |nu_j| dropped -- in the paper's treecode or in the group
+treecode's rep_mode 0, compiles the copy, swaps it in for the real oracle and
+checks that the pins of tests/test_oracle_paper_tree.py then fail.  The copy
+lives in pytest's temporary directory; the real oracle is untouched.
+"""
+import os
+
+import pytest
+
+import oracle
+from oracle import OP_A, OP_AT, OP_G
+
+import test_oracle_paper_tree as pins  # the pin module, on sys.path as a test file
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "wnnc_oracle.c")
+
+# (name, text in the source, replacement, pins that must fail)
+MUTATIONS = [
+    ("paper tree: signed weights",
+     "            a = sqrt(a);\n            sw += a;\n            for (int q = 0; q < 3; ++q) { sx[q] += a * P->x",
+     "            a = (dim == 1) ? nu[i] : sqrt(a);\n            sw += a;\n"
+     "            for (int q = 0; q < 3; ++q) { sx[q] += a * P->x",
+     [lambda: pins.test_paper_tree_worked_far_node(OP_AT),
+      lambda: pins.test_representative_ignores_the_sign_of_nu("paper")]),
+    ("paper tree: no normalisation",
+     "rep[3 * b + q] = sw > 0.0 ? sx[q] / sw : sc[q] / (double)P->count[b];",
+     "rep[3 * b + q] = sw > 0.0 ? sx[q] : sc[q] / (double)P->count[b];",
+     [lambda: pins.test_paper_tree_worked_far_node(OP_A),
+      lambda: pins.test_paper_tree_worked_far_node(OP_G),
+      lambda: pins.test_paper_tree_worked_far_node(OP_AT)]),
+    ("group tree rep_mode 0: signed weights",
+     "            a = sqrt(a);\n            sw += a;\n            for (int k = 0; k < 3; ++k) sx[k] += a * t->x",
+     "            a = (dim == 1) ? nu[i] : sqrt(a);\n            sw += a;\n"
+     "            for (int k = 0; k < 3; ++k) sx[k] += a * t->x",
+     [lambda: pins.test_group_tree_worked_far_node(OP_AT, 0),
+      lambda: pins.test_representative_ignores_the_sign_of_nu("group")]),
+    ("group tree rep_mode 0: no normalisation",
+     "rep[3 * b + k] = (rep_mode == 0 && sw > 0.0) ? sx[k] / sw : t->cent[3 * b + k];",
+     "rep[3 * b + k] = (rep_mode == 0 && sw > 0.0) ? sx[k] : t->cent[3 * b + k];",
+     [lambda: pins.test_group_tree_worked_far_node(OP_A, 0),
+      lambda: pins.test_group_tree_worked_far_node(OP_G, 0),
+      lambda: pins.test_group_tree_worked_far_node(OP_AT, 0)]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(MUTATIONS)), ids=[m[0] for m in MUTATIONS])
+def test_pins_fail_on_a_mutated_representative(case, tmp_path, monkeypatch):
+    name, old, new, must_fail = MUTATIONS[case]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site of '{name}' not found once in the oracle source"
+    src = tmp_path / "mutant.c"
+    src.write_text(text.replace(old, new))
+    mutant = oracle.load(oracle.compile_source(str(src), str(tmp_path / "libmutant.so")))
+    # the unmutated oracle passes these pins (they run in the pin file too)
+    for pin in must_fail:
+        pin()
+    monkeypatch.setattr(oracle, "_lib", mutant)
+    for pin in must_fail:
+        with pytest.raises(AssertionError):
+            pin()
