@@ -11,8 +11,12 @@ Also the patch features of a point: the offsets of its 16 nearest neighbours
 (nearest first, from the exhaustive search of oracle.knn) divided by the 16th
 neighbour's distance, and the warm-start combination.
 
+And the Adam step (Kingma & Ba, "Adam: A Method for Stochastic
+Optimization", Algorithm 1, with its bias correction) that trains it.
+
 Pins (tests/test_oracle_mlp.py): finite differences of the loss for the
-gradient; worked BF16 rounding values.
+gradient; worked BF16 rounding values; Adam's closed forms (first step
+lr g/(|g| + eps), constant-gradient steps, a worked two-step example).
 """
 from __future__ import annotations
 
@@ -166,3 +170,17 @@ def warm_init(direction, reference, area):
     if reference is not None:
         f = np.where((d * np.asarray(reference, np.float64)).sum(1, keepdims=True) < 0, -f, f)
     return d * f
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step t >= 1 (Kingma & Ba, Algorithm 1), in float64:
+        m <- b1 m + (1 - b1) g,   v <- b2 v + (1 - b2) g^2,
+        m_hat = m / (1 - b1^t),  v_hat = v / (1 - b2^t),
+        p <- p - lr m_hat / (sqrt(v_hat) + eps).
+    Returns the new (p, m, v)."""
+    p, g, m, v = (np.asarray(a, np.float64) for a in (p, g, m, v))
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -429,6 +429,7 @@ typedef struct {
     or_octree src;
     or_targets self;
     double theta;
+    int far_order;      /* 0: monopole far terms (Eq. 13-14); 1: plus the first-order Taylor terms */
 } or_tree;
 
 /* group_slack, group_min_depth: the rule of group_offsets for the points as
@@ -458,6 +459,11 @@ void or_tree_free(or_tree* T) {
     free_targets(&T->self);
     free(T);
 }
+
+/* Order of the far-field expansion of the group treecode (rep_mode 1 only):
+ * 0 = one term per far node at its point centroid x_B (Eq. 13-14);
+ * 1 = plus the first-order Taylor term of the kernel about x_B. */
+void or_tree_set_far_order(or_tree* T, int order) { T->far_order = order; }
 
 /* Structure queries (for the structural pins and for comparing list sizes). */
 int64_t or_tree_nnodes(const or_tree* T) { return T->src.nnodes; }
@@ -521,6 +527,60 @@ static void node_reps(const or_octree* t, const double* nu, int dim, int rep_mod
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* First-order far field (rep_mode 1, about the point centroid x_B).  With   */
+/* d = y - x_B and a source x_j = x_B + delta_j, Taylor's theorem gives       */
+/*   gradPhi(d - delta) = gradPhi(d) - HPhi(d) delta + O(|delta|^2)           */
+/*   HPhi(d - delta)    = HPhi(d) - T(d)[delta] + O(|delta|^2),               */
+/* T_abc = d_c HPhi_ab = (3 (I_ab d_c + I_ac d_b + I_bc d_a)/r^5              */
+/*                        - 15 d_a d_b d_c / r^7) / (4 pi),                   */
+/* and summed over the node's sources the first-order terms need only the     */
+/* symmetric moment S = sum_j sym(delta_j mu_j^T) (HPhi and T are symmetric): */
+/*   A: - HPhi(d) : S = tr S/(4 pi r^3) - 3 d.S d/(4 pi r^5)                  */
+/*   G: + T(d) : S    = (6 S d + 3 tr S d)/(4 pi r^5) - 15 (d.S d) d/(4 pi r^7) */
+/* S is stored as (Sxx, Syy, Szz, Sxy, Sxz, Syz).                             */
+/* ------------------------------------------------------------------------ */
+static void node_dipoles(const or_octree* t, const double* nu, double* S) {
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t b = 0; b < t->nnodes; ++b) {
+        double m[6] = {0, 0, 0, 0, 0, 0};
+        const double* c = t->cent + 3 * b;
+        for (int64_t i = t->start[b]; i < t->start[b] + t->count[b]; ++i) {
+            const double dl[3] = {t->x[3 * i] - c[0], t->x[3 * i + 1] - c[1], t->x[3 * i + 2] - c[2]};
+            const double* v = nu + 3 * i;
+            m[0] += dl[0] * v[0];
+            m[1] += dl[1] * v[1];
+            m[2] += dl[2] * v[2];
+            m[3] += 0.5 * (dl[0] * v[1] + dl[1] * v[0]);
+            m[4] += 0.5 * (dl[0] * v[2] + dl[2] * v[0]);
+            m[5] += 0.5 * (dl[1] * v[2] + dl[2] * v[1]);
+        }
+        for (int k = 0; k < 6; ++k) S[6 * b + k] = m[k];
+    }
+}
+
+static inline void sym_mul(const double* S, const double d[3], double out[3]) {
+    out[0] = S[0] * d[0] + S[3] * d[1] + S[4] * d[2];
+    out[1] = S[3] * d[0] + S[1] * d[1] + S[5] * d[2];
+    out[2] = S[4] * d[0] + S[5] * d[1] + S[2] * d[2];
+}
+
+/* First-order correction of a far term (op A: out[0]; op G: out[0..2]). */
+static void far_correction(int op, const double d[3], double r2, const double* S, double out[3]) {
+    const double r = sqrt(r2), r3 = r2 * r, r5 = r3 * r2, r7 = r5 * r2;
+    const double tr = S[0] + S[1] + S[2];
+    double Sd[3];
+    sym_mul(S, d, Sd);
+    const double dSd = d[0] * Sd[0] + d[1] * Sd[1] + d[2] * Sd[2];
+    if (op == OP_A) {
+        out[0] = tr / (4.0 * OR_PI * r3) - 3.0 * dSd / (4.0 * OR_PI * r5);
+        out[1] = out[2] = 0.0;
+    } else {
+        for (int k = 0; k < 3; ++k)
+            out[k] = (6.0 * Sd[k] + 3.0 * tr * d[k]) / (4.0 * OR_PI * r5) - 15.0 * dSd * d[k] / (4.0 * OR_PI * r7);
+    }
+}
+
 /* Gather-form treecode for targets T against the source octree:
  *   op A : out (m)    = sum_far gradPhi(y - x_B) . mu_B + sum_near gradPhi(y - x_j) . mu_j
  *   op G : out (m x 3) = sum_far -HPhi(y - x_B) mu_B  + sum_near -HPhi(y - x_j) mu_j
@@ -530,11 +590,14 @@ static void node_reps(const or_octree* t, const double* nu, int dim, int rep_mod
  */
 static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep_mode, double w,
                         const double* nu_sorted, double* out_sorted, double amb_tol, double* amb_sorted,
-                        double* abs_sorted) {
+                        double* abs_sorted, int far_order) {
     int dim = (op == OP_AT) ? 1 : 3;
     double* rep = malloc(sizeof(double) * 3 * (t->nnodes > 0 ? t->nnodes : 1));
     double* nuB = malloc(sizeof(double) * dim * (t->nnodes > 0 ? t->nnodes : 1));
     node_reps(t, nu_sorted, dim, rep_mode, rep, nuB);
+    const int dip = far_order == 1 && rep_mode == 1 && op != OP_AT;
+    double* S = dip ? malloc(sizeof(double) * 6 * (t->nnodes > 0 ? t->nnodes : 1)) : NULL;
+    if (dip) node_dipoles(t, nu_sorted, S);
     const double w2 = eff_w2(w);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < T->ngroups; ++g) {
@@ -553,6 +616,12 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
                 else if (op == OP_G) term_G(d, r2, nuB + 3 * b, v);
                 else term_AT(d, r2, nuB[b], v);
                 double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                if (dip) {
+                    double cr[3];
+                    far_correction(op, d, r2, S + 6 * b, cr);
+                    for (int k = 0; k < 3; ++k) v[k] += cr[k];
+                    vn += sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+                }
                 if (amb_p) ab += vn;
                 if (keep_pair(r2, w2)) {
                     for (int k = 0; k < 3; ++k) acc[k] += v[k];
@@ -585,7 +654,7 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
             if (abs_sorted) abs_sorted[i] = as;
         }
     }
-    free(rep); free(nuB);
+    free(rep); free(nuB); free(S);
 }
 
 /* Exact transpose of the rep_mode-1 tree operator A (targets = sources):
@@ -597,9 +666,14 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
  *   V_B = sum_{g: B far for g} sum_{i in g} s_i gradPhi(x_i - x_B).
  * The node sums and the leaf sums are gathered through the transposed lists so
  * that each output is a sum in a fixed order (groups ascending, then i). */
+/* With far_order 1 the tree operator A carries the first-order terms
+ *   A_tree(mu)_i += - sum_{B far for g(i)} sum_{j in B} (HPhi(x_i - x_B) delta_jB) . mu_j,
+ * delta_jB = x_j - x_B, whose transpose adds to every point j
+ *   - sum_{B containing j} H_B delta_jB,   H_B = sum_{g: B far} sum_{i in g} s_i HPhi(x_i - x_B),
+ * with the same cut-off decision as the node's monopole term. */
 static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w,
                                const double* s_sorted, double* out_sorted, double amb_tol,
-                               double* amb_sorted, double* abs_sorted) {
+                               double* amb_sorted, double* abs_sorted, int far_order) {
     int64_t nn = t->nnodes, ng = T->ngroups;
     const double w2 = eff_w2(w);
     /* transposed lists: node -> groups using it (far), leaf -> groups using it (near) */
@@ -621,10 +695,12 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
     double* V = calloc((size_t)(nn > 0 ? nn : 1) * 3, sizeof(double));
     double* VA = calloc((size_t)(nn > 0 ? nn : 1), sizeof(double));
     double* VS = calloc((size_t)(nn > 0 ? nn : 1), sizeof(double));
+    double* H = calloc((size_t)(nn > 0 ? nn : 1) * 6, sizeof(double));   /* (xx, yy, zz, xy, xz, yz) */
+    double* HN = calloc((size_t)(nn > 0 ? nn : 1), sizeof(double));      /* sum of |s_i| |HPhi|_F */
     const double* rep = t->cent;
     #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t b = 0; b < nn; ++b) {
-        double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
+        double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0, h[6] = {0, 0, 0, 0, 0, 0}, hn = 0.0;
         for (int64_t q = fcnt[b]; q < fcnt[b + 1]; ++q) {
             int64_t g = fg[q];
             int64_t s = T->goff[g], e = T->goff[g + 1];
@@ -642,12 +718,25 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                 if (keep_pair(r2, w2)) {
                     for (int k = 0; k < 3; ++k) acc[k] += v[k];
                     as += vn;
+                    if (far_order == 1) {
+                        /* s_i HPhi(d), HPhi(d) = (3 d d^T - r^2 I)/(4 pi r^5), even in d */
+                        const double r = sqrt(r2), f = s_sorted[i] / (4.0 * OR_PI * r2 * r2 * r);
+                        h[0] += f * (3.0 * d[0] * d[0] - r2);
+                        h[1] += f * (3.0 * d[1] * d[1] - r2);
+                        h[2] += f * (3.0 * d[2] * d[2] - r2);
+                        h[3] += f * 3.0 * d[0] * d[1];
+                        h[4] += f * 3.0 * d[0] * d[2];
+                        h[5] += f * 3.0 * d[1] * d[2];
+                        hn += fabs(f) * sqrt(6.0) * r2;
+                    }
                 }
             }
         }
         for (int k = 0; k < 3; ++k) V[3 * b + k] = acc[k];
+        for (int k = 0; k < 6; ++k) H[6 * b + k] = h[k];
         VA[b] = ab;
         VS[b] = as;
+        HN[b] = hn;
     }
     /* near part, per source leaf, then add the far sums of all nodes containing j */
     #pragma omp parallel for schedule(dynamic, 16)
@@ -679,6 +768,13 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                 for (int k = 0; k < 3; ++k) far[k] += V[3 * a + k];
                 ab += VA[a];
                 as += VS[a];
+                if (far_order == 1) {
+                    const double dl[3] = {x[0] - rep[3 * a], x[1] - rep[3 * a + 1], x[2] - rep[3 * a + 2]};
+                    double hd[3];
+                    sym_mul(H + 6 * a, dl, hd);
+                    for (int k = 0; k < 3; ++k) far[k] -= hd[k];
+                    as += HN[a] * sqrt(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
+                }
             }
             for (int k = 0; k < 3; ++k) out_sorted[3 * j + k] = acc[k] + far[k];
             if (amb_sorted) amb_sorted[j] = ab;
@@ -686,6 +782,7 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         }
     }
     free(fcnt); free(ncnt); free(fg); free(ngp); free(fpos); free(npos); free(V); free(VA); free(VS);
+    free(H); free(HN);
 }
 
 /* On-surface application of an operator.  nu and out are in input order,
@@ -702,8 +799,9 @@ void or_tree_apply(const or_tree* T, int op, int rep_mode, double w, const doubl
     double* abss = abssum ? malloc(sizeof(double) * (n > 0 ? n : 1)) : NULL;
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < din; ++k) nus[din * i + k] = nu[din * t->perm[i] + k];
-    if (op == OP_AT && rep_mode == 1) tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs, abss);
-    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs, abss);
+    if (op == OP_AT && rep_mode == 1)
+        tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs, abss, T->far_order);
+    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs, abss, T->far_order);
     for (int64_t i = 0; i < n; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * T->self.perm[i] + k] = outs[dout * i + k];
         if (amb) amb[T->self.perm[i]] = ambs[i];
@@ -727,7 +825,7 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) nus[3 * i + k] = nu[3 * t->perm[i] + k];
     double* abss = abssum ? malloc(sizeof(double) * (m > 0 ? m : 1)) : NULL;
-    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL, abss);
+    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL, abss, T->far_order);
     for (int64_t i = 0; i < m; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * Q.perm[i] + k] = outs[dout * i + k];
         if (abssum) abssum[Q.perm[i]] = abss[i];

@@ -2,9 +2,11 @@
 
 Each case plants one plausible mistake in a copy of the oracle's C source --
 Eq. 13's weights taken as the signed s_i instead of |s_i|, or its
-normalisation by sum |nu_j| dropped -- in the paper's treecode or in the group
-treecode's rep_mode 0, compiles the copy, swaps it in for the real oracle and
-checks that the pins of tests/test_oracle_paper_tree.py then fail.  The copy
+normalisation by sum |nu_j| dropped, in the paper's treecode or in the group
+treecode's rep_mode 0; a sign or factor of the first-order far-field terms or
+of their transpose -- compiles the copy, swaps it in for the real oracle and
+checks that the pins of tests/test_oracle_paper_tree.py and
+tests/test_oracle_dipole.py then fail.  The copy
 lives in pytest's temporary directory; the real oracle is untouched.
 """
 import os
@@ -14,7 +16,8 @@ import pytest
 import oracle
 from oracle import OP_A, OP_AT, OP_G
 
-import test_oracle_paper_tree as pins  # the pin module, on sys.path as a test file
+import test_oracle_dipole as dpins     # the pin modules, on sys.path as test files
+import test_oracle_paper_tree as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "wnnc_oracle.c")
 
@@ -44,6 +47,18 @@ MUTATIONS = [
      [lambda: pins.test_group_tree_worked_far_node(OP_A, 0),
       lambda: pins.test_group_tree_worked_far_node(OP_G, 0),
       lambda: pins.test_group_tree_worked_far_node(OP_AT, 0)]),
+    ("first-order far field: sign of A's term",
+     "out[0] = tr / (4.0 * OR_PI * r3) - 3.0 * dSd / (4.0 * OR_PI * r5);",
+     "out[0] = -(tr / (4.0 * OR_PI * r3) - 3.0 * dSd / (4.0 * OR_PI * r5));",
+     [lambda: dpins.test_far_error_order(OP_A)]),
+    ("first-order far field: factor of G's S d term",
+     "out[k] = (6.0 * Sd[k] + 3.0 * tr * d[k])",
+     "out[k] = (3.0 * Sd[k] + 3.0 * tr * d[k])",
+     [lambda: dpins.test_far_error_order(OP_G)]),
+    ("first-order far field: sign of the transposed push-down",
+     "for (int k = 0; k < 3; ++k) far[k] -= hd[k];",
+     "for (int k = 0; k < 3; ++k) far[k] += hd[k];",
+     [lambda: dpins.test_far_error_order_of_the_transpose()]),
 ]
 
 
