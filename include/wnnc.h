@@ -80,6 +80,19 @@ typedef struct {
                           frame, sources and targets) to bfloat16 before the pair terms of A, G
                           and the fused A+G; the adjoint stays in float, so A^T is then not the
                           exact transpose.  A precision study, not a fast path (default 0) */
+    int criterion;     /* far-field decisions (Alg. 4):
+                          0 = once per group of at most 32 Morton-consecutive targets: node B is
+                              far when the gap between the group's box and B's box exceeds
+                              width(B)/theta, so every target also passes Alg. 4's test; the
+                              lists are built once with the tree and reused by every call
+                              (default, the fast path);
+                          1 = the paper's own test, per target and per call: every target walks
+                              the octree from the root and takes B as far iff
+                              |x_i - x_{B,nu}| > width(B)/theta with the representative of that
+                              call (Eq. 13).  Needs rep_mode 0 and near_bf16 0 (else
+                              WNNC_EINVAL).  With leaf_size 1 this is Alg. 4 as printed.  A
+                              reference mode: warps diverge, several times slower.
+                              wnnc_get_stats still counts the group lists' pairs */
 } wnnc_tree_params;
 
 /* Iteration parameters (Alg. 3; Sec. 5.1.1 defaults n = 40, w1 = 0.002, w2 = 0.016). */
@@ -269,10 +282,12 @@ enum { WNNC_MLP_PARAMS = 39683 };   /* 48*128+128 + 2*(128*128+128) + 128*3+3 */
 
 /*
  * Parameter layout (FP32, flat): W1 [128][48], b1 [128], W2 [128][128], b2,
- * W3 [128][128], b3, W4 [3][128], b4 [3].  Weights are rounded to BF16 when
- * read; products accumulate in FP32.  max_batch bounds the rows of one
- * gradient or training call (forward calls of any size are processed in
- * max_batch chunks).  The MLP owns its work buffers (allocated here).
+ * W3 [128][128], b3, W4 [3][128], b4 [3].  Every parameter (weights and
+ * biases) is rounded to BF16 when read; products accumulate in FP32.  The
+ * forward runs on the BF16 tensor cores (activations enter as BF16 hi + lo
+ * pairs, ~16 significant bits).  max_batch bounds the rows of one gradient or
+ * training call (forward calls take any number of rows).  The MLP owns its
+ * work buffers (allocated here).
  */
 wnnc_status wnnc_mlp_create(int64_t max_batch, wnnc_mlp** out);
 wnnc_status wnnc_mlp_free(wnnc_mlp* mlp);
@@ -323,17 +338,23 @@ wnnc_status wnnc_probe_fp32(double* tflops, void* stream);
  * point exists for callers that cannot call cudaMalloc (a host application
  * that owns all device memory through its own pool, a plugin sandbox, or a
  * latency-critical path where an allocation that may synchronise the device is
- * not acceptable).  Results equal wnnc_eval_at on a tree built with theta = 0
- * from the same points (same normalisation, cut-off and units).
- *   pts device, float32 [n][3]; mu device, float32 [n][3]; q device, float32 [m][3]
- *   out device, float32 [m];  w smoothing width (normalised units), >= 0
+ * not acceptable).  It uses the normalisation, cut-off and units of the tree
+ * entry points, and its results agree with wnnc_eval_at on a tree built with
+ * theta = 0 from the same points within the FP32 rounding of the two sums
+ * (the sums run in different frames and orders, so a pair at r = w can fall
+ * on either side of the cut-off).
+ *   pts device, float32 [n][3], all finite; mu device, float32 [n][3];
+ *   q   device, float32 [m][3], all finite;  out device, float32 [m];
+ *   w   smoothing width (normalised units), >= 0
  *   n   at most 32768 points (larger n returns WNNC_EINVAL with a message).
- * Scratch lives in a fixed array of about 1 MiB inside the library's device
- * image (held by every GPU that loads the library until the process exits).
- * The first call on a device looks up that array's device address; make that
- * first call before any stream capture.  All calls on a device share the
- * array: calls whose kernels may overlap on the GPU (different streams
- * without ordering) race, so order them.  Asynchronous on `stream`.
+ * A NaN or infinite point or query coordinate returns WNNC_EINVAL (out is
+ * then unspecified).  Scratch lives in a fixed array of about 1 MiB inside
+ * the library's device image (held by every GPU that loads the library until
+ * the process exits).  The first call on a device looks up that array's
+ * device address; make that first call before any stream capture.  All calls
+ * on a device share the array: calls whose kernels may overlap on the GPU
+ * (different streams without ordering) race, so order them.  The call waits
+ * for its stream before it returns (it reads back the non-finite flags).
  */
 wnnc_status wnnc_eval_w_direct_noalloc(const float* pts, int64_t n, const float* mu, const float* q,
                                        int64_t m, float w, float* out, void* stream);

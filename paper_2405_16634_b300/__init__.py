@@ -45,7 +45,7 @@ class WnncError(RuntimeError):
 
 class TreeParams(Structure):
     _fields_ = [("max_depth", c_int), ("leaf_size", c_int), ("theta", c_float),
-                ("rep_mode", c_int), ("moments_fp64", c_int), ("near_bf16", c_int)]
+                ("rep_mode", c_int), ("moments_fp64", c_int), ("near_bf16", c_int), ("criterion", c_int)]
 
 
 class IterParams(Structure):
@@ -165,7 +165,11 @@ class Tree:
     """Octree, node data and interaction lists of a point cloud on one GPU."""
 
     def __init__(self, points, theta: float = 0.5, leaf_size: int = 8, max_depth: int = 15,
-                 rep_mode: int = 1, moments_fp64: bool = False, near_bf16: bool = False):
+                 rep_mode: int = 1, moments_fp64: bool = False, near_bf16: bool = False,
+                 criterion: int = 0):
+        """criterion 0: far decisions per target group on boxes, lists built once
+        (default); 1: the paper's per-target test of Alg. 4 on every call
+        (needs rep_mode 0; with leaf_size 1 it is Alg. 4 as printed)."""
         pts = points if isinstance(points, torch.Tensor) else torch.as_tensor(points)
         self.device = pts.device if pts.is_cuda else torch.device("cuda", torch.cuda.current_device())
         pts = _dev_f32(pts, (-1, 3), self.device)
@@ -174,6 +178,7 @@ class Tree:
         p.max_depth, p.leaf_size, p.theta = int(max_depth), int(leaf_size), float(theta)
         p.rep_mode, p.moments_fp64 = int(rep_mode), int(bool(moments_fp64))
         p.near_bf16 = int(bool(near_bf16))
+        p.criterion = int(criterion)
         self.params = p
         h = c_void_p()
         with torch.cuda.device(self.device):
@@ -401,11 +406,21 @@ def warm_init(direction, reference, area: float) -> torch.Tensor:
 class WindingNumber(torch.autograd.Function):
     """F(mu) = A_w(mu) at the tree's points; backward = A_w^T (Sec. 4.5).
 
-    With rep_mode 1 the backward is the exact transpose of the forward tree
-    operator, so gradients agree with finite differences of the forward."""
+    The backward is the exact transpose of the forward tree operator only for
+    a tree with point-centroid representatives (rep_mode 1) and float
+    near-field coordinates: then gradients agree with finite differences of
+    the forward.  With the paper's |nu|-weighted representatives (rep_mode 0)
+    the forward is not even linear in mu (the representatives move with mu)
+    and A^T is the paper's separate s-representative treecode; with bfloat16
+    near-field coordinates the forward rounds coordinates that the adjoint
+    does not.  forward() refuses such trees rather than return a gradient
+    that is not the forward's."""
 
     @staticmethod
     def forward(ctx, mu, tree: Tree, w: float):
+        if tree.params.rep_mode != 1 or tree.params.near_bf16:
+            raise ValueError("winding_number needs a tree with rep_mode=1 and near_bf16=False: "
+                             "only then is the backward (A^T) the exact transpose of the forward")
         ctx.tree, ctx.w = tree, w
         return tree.eval_w(mu.detach(), w)
 

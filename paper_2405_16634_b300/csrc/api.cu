@@ -137,6 +137,9 @@ static void check_params(const wnnc_tree_params& p) {
     if (!(p.theta >= 0.f) || !std::isfinite(p.theta)) fail(WNNC_EINVAL, "theta must be finite and >= 0");
     if (p.rep_mode != 0 && p.rep_mode != 1) fail(WNNC_EINVAL, "rep_mode must be 0 or 1");
     if (p.near_bf16 != 0 && p.near_bf16 != 1) fail(WNNC_EINVAL, "near_bf16 must be 0 or 1");
+    if (p.criterion != 0 && p.criterion != 1) fail(WNNC_EINVAL, "criterion must be 0 or 1");
+    if (p.criterion == 1 && (p.rep_mode != 0 || p.near_bf16 != 0))
+        fail(WNNC_EINVAL, "criterion 1 (per-target Alg. 4) needs rep_mode 0 and near_bf16 0");
 }
 
 static void check_w(float w) {
@@ -165,6 +168,7 @@ wnnc_status wnnc_tree_params_default(wnnc_tree_params* p) {
     p->rep_mode = 1;
     p->moments_fp64 = 0;
     p->near_bf16 = 0;
+    p->criterion = 0;
     return WNNC_OK;
 }
 

@@ -277,6 +277,14 @@ struct GatherArgs {
     float4* mu_out;
     float4* g_out;            // kOpAG: G of the field (sorted, normalised)
     int rescale_mode;
+    // per-target walk (criterion 1)
+    int walk;                 // 1: k_walk instead of the list gather
+    float copen;              // c = 1/theta (infinite for theta = 0)
+    const int* nchild0;       // first child of each node
+    const int* nnchild;       // number of children (0 for leaves)
+    const int* nstart;        // first sorted point of each node
+    const int* ncount;        // points of each node
+    int* err_flag;            // device error flags (a walk stack overflow sets kErrCapacity)
 };
 
 // Accumulators: (x, y, z) holds the A / A^T sum, or for G the sum of
@@ -731,6 +739,68 @@ __global__ void k_gather_finalize(GatherArgs A) {
     }
     const int i0 = A.goff[g];
     gather_epilogue<EPI>(A, g, (int64_t)i0 + lane, lane < A.goff[g + 1] - i0, acc, lane);
+}
+
+// ---------------------------------------------------------------------------
+// The paper's treecode, Alg. 4 per target (tree parameter criterion = 1).
+// One warp per target group, one target per lane, in the group's frame.
+// Each lane walks the octree from the root on its own stack: node B is far
+// for target x_i iff |x_i - x_B| > c width(B) (c = 1/theta, x_B the node's
+// representative of this call, Eq. 13), and then contributes one term with
+// nu_B (Eq. 14); else its children are visited; else (a leaf) its points
+// are summed.  Every term takes the cut-off of Sec. 4.4.  The sums and the
+// epilogues are the gather's.  With depth D <= 15 the stack holds at most
+// 1 + 7 D entries; a push that would not fit sets the capacity flag and the
+// lane drops that node (the result is then reported as an error, not used).
+// ---------------------------------------------------------------------------
+constexpr int kWalkStack = 128;
+
+template <int OP, int EPI>
+__global__ void __launch_bounds__(32 * kGatherWarps) k_walk(GatherArgs A) {
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kGatherWarps + wl;
+    if (g >= A.ngroups) return;
+    const int i0 = A.goff[g], cnt = A.goff[g + 1] - i0;
+    const int64_t i = (int64_t)i0 + lane;
+    const bool valid = lane < cnt;
+    const float4 o = A.tgorig[g];
+    Acc3 acc;
+    if (valid) {
+        const float4 t = shift(A.tcorig[i >> 5], o, A.tpos[i]);
+        int stk[kWalkStack];
+        int sp = 0;
+        stk[sp++] = 0;
+        while (sp > 0) {
+            const int b = stk[--sp];
+            const float4 cell = A.ncell[b];
+            const float4 rp = shift(cell, o, A.nrep[b]);
+            const float dx = rp.x - t.x, dy = rp.y - t.y, dz = rp.z - t.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float cw = A.copen * cell.w;
+            if (r2 > cw * cw) {
+                const float4 nv = A.nmom[b];
+                interact<OP, true>(t, rp, nv, A.w2, acc);
+                continue;
+            }
+            const int nc = A.nnchild[b];
+            if (nc > 0) {
+                if (sp + nc > kWalkStack) {
+                    atomicOr(A.err_flag, kErrCapacity);
+                    continue;
+                }
+                const int c0 = A.nchild0[b];
+                for (int q = nc - 1; q >= 0; --q) stk[sp++] = c0 + q;
+                continue;
+            }
+            const int j0 = A.nstart[b], j1 = j0 + A.ncount[b];
+            for (int j = j0; j < j1; ++j) {
+                const float4 sp4 = shift(A.scorig[j >> 5], o, A.spos[j]);
+                const float4 sv = OP == kOpATpaper ? make_float4(A.sval_s[j], 0.f, 0.f, 0.f) : A.sval[j];
+                interact<OP, true>(t, sp4, sv, A.w2, acc);
+            }
+        }
+    }
+    gather_epilogue<EPI>(A, g, i, valid, combine<OP>(acc), lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1298,6 +1368,13 @@ GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_a
     a.near_bf16 = t.params.near_bf16;
     a.tgbl = ts.gbl;
     a.tgbh = ts.gbh;
+    a.walk = t.params.criterion == 1;
+    a.copen = t.params.theta > 0.f ? 1.f / t.params.theta : INFINITY;
+    a.nchild0 = t.node_child0;
+    a.nnchild = t.node_nchild;
+    a.nstart = t.node_start;
+    a.ncount = t.node_count;
+    a.err_flag = t.err_flag;
     return a;
 }
 
@@ -1308,6 +1385,11 @@ void launch_gather(Tree& t, const GatherArgs& a, cudaStream_t s) {
                  OP == kOpAG ? WNNC_PROF_AG
                              : (OP == kOpG ? WNNC_PROF_G : (OP == kOpA ? WNNC_PROF_A : WNNC_PROF_ADJ_NEAR)),
                  s);
+    if (a.walk) {
+        k_walk<OP, EPI><<<ceil_div(a.ngroups, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
+        WNNC_LAUNCH_CHECK();
+        return;
+    }
     // the bfloat16 near-field study applies to the sums of A and G only
     if ((OP == kOpA || OP == kOpG || OP == kOpAG) && a.near_bf16)
         k_gather<OP, EPI, true, kGatherTPL><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);

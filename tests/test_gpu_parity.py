@@ -56,6 +56,9 @@ def check_close(gpu, ora, bounds=None, tol=TOL, what=""):
     bad = err > bound
     assert not bad.any(), (f"{what}: {bad.sum()} outputs out of tolerance; worst err/bound = "
                            f"{(err / bound).max():.3e}")
+    rel = float((err / np.maximum(mag, rms)).max())
+    print(f"[parity] {what}: max |gpu - ora| / max(|ora|, rms) = {rel:.2e}, "
+          f"max err/bound = {(err / bound).max():.3f}")
     return float((err / bound).max())
 
 
@@ -227,6 +230,108 @@ def test_treecode_error_vs_direct_is_bounded_and_monotone():
         errs.append(e_gpu)
     assert errs[0] > errs[1] > errs[2]
     assert errs[1] < 1e-2
+
+
+@pytest.fixture(scope="module")
+def union500k_sample():
+    """The 500,000-point benchmark cloud, a smooth oriented field (ground-truth
+    normals times the mean area; outliers get zero), a random s, and a seeded
+    10,000-point target subset."""
+    c = synth.config_cloud("union500k")
+    n = len(c.points)
+    mu = (np.nan_to_num(c.normals) * (c.area / n)).astype(np.float32)
+    s = np.random.default_rng(2).standard_normal(n).astype(np.float32)
+    sub = np.sort(np.random.default_rng(77).choice(n, 10000, replace=False))
+    return c.points, mu, s, sub, {}
+
+
+@pytest.mark.parametrize("rep_mode", [1, 0])
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
+def test_production_theta_against_direct_sums(union500k_sample, theta, rep_mode):
+    """The GPU treecode at the theta of production use against the plain
+    definitions (the oracle's FP64 direct sums over all 500,000 sources), per
+    element, for A, grad F = -G and A^T, at 10,000 seeded targets.
+
+    The bound is the paper's own treecode: Alg. 4 run as printed (per target,
+    leaf size 1, Eq. 13-14 representatives, far iff |x_i - x_B| > width/theta)
+    at the same theta on the same targets.  For every target i
+        |gpu_i - dir_i| <= max_j |paper_j - dir_j|
+        |gpu_i - dir_i| / S_i <= max_j |paper_j - dir_j| / S_j
+    (S_i = sum_j |term_ij|, the scale of target i's sum), and in relative L2
+        ||gpu - dir|| <= ||paper - dir||:
+    no element of the GPU path is worse than the paper's treecode at its worst,
+    and its overall error is no larger.  The measured errors are printed."""
+    W = _wnnc()
+    pts, mu, s, sub, direct_cache = union500k_sample
+    w = 0.004
+    t = W.Tree(torch.from_numpy(pts).cuda(), theta=theta, rep_mode=rep_mode)
+    got = {OP_A: t.eval_w(torch.from_numpy(mu).cuda(), w),
+           OP_G: t.eval_grad(torch.from_numpy(mu).cuda(), w),
+           OP_AT: t.eval_adjoint(torch.from_numpy(s).cuda(), w)}
+    for op, nu in ((OP_A, mu), (OP_G, mu), (OP_AT, s)):
+        g = got[op].cpu().numpy().astype(np.float64)[sub]
+        if op not in direct_cache:
+            direct_cache[op] = oracle.eval_direct_at(op, pts, nu, w, targets=sub)
+        d, b = direct_cache[op]
+        p, _ = oracle.eval_paper(op, pts, nu, w, f32(theta), targets=sub)
+        norm = (lambda v: np.abs(v)) if d.ndim == 1 else (lambda v: np.linalg.norm(v, axis=1))
+        eg, ep, S = norm(g - d), norm(p - d), b["abssum"]
+        rms = np.linalg.norm(d) / np.sqrt(len(sub))
+        l2g, l2p = np.linalg.norm(g - d) / np.linalg.norm(d), np.linalg.norm(p - d) / np.linalg.norm(d)
+        print(f"[theta-parity] rep_mode={rep_mode} theta={theta} op={'A G AT'.split()[op]}: "
+              f"gpu relL2 {l2g:.3e} max/rms {eg.max() / rms:.3e} max/S {(eg / S).max():.3e} | "
+              f"paper treecode relL2 {l2p:.3e} max/rms {ep.max() / rms:.3e} max/S {(ep / S).max():.3e}")
+        assert np.all(eg <= ep.max()), (op, eg.max(), ep.max())
+        assert np.all(eg / S <= (ep / S).max()), (op, (eg / S).max(), (ep / S).max())
+        assert l2g <= l2p, (op, l2g, l2p)
+
+
+@pytest.mark.parametrize("leaf", [1, 8])
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
+def test_per_target_criterion_matches_the_papers_treecode(theta, leaf):
+    """criterion = 1: every target walks the octree on its own and applies
+    Alg. 4's test |x_i - x_B| > width(B)/theta with the |nu|-weighted
+    representative of the call (Eq. 13); with leaf_size 1 this is the
+    paper's treecode as printed.  Against the oracle's independent
+    implementation of Alg. 4 (its own geometric octree and recursion), element
+    by element within the usual bound plus the ambiguity budget of far
+    decisions within 1e-5 of the threshold (FP32 representatives may take the
+    other branch there), for A, grad F and the s-representative A^T."""
+    W = _wnnc()
+    c = synth.config_cloud("union50k", n=20000)
+    n = len(c.points)
+    mu = (c.normals * (c.area / n)).astype(np.float32)
+    s = np.random.default_rng(3).standard_normal(n).astype(np.float32)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta, leaf_size=leaf, rep_mode=0, criterion=1)
+    xn, _, _ = oracle.normalize(c.points)
+    assert t.info()["nnodes"] == len(oracle.PaperTree(xn, leaf_size=leaf).nodes()["start"])
+    w = 0.004
+    for op, nu, call in ((OP_A, mu, t.eval_w), (OP_G, mu, t.eval_grad), (OP_AT, s, t.eval_adjoint)):
+        gpu = call(torch.from_numpy(nu).cuda(), w).cpu().numpy()
+        ora, info = oracle.eval_paper(op, c.points, nu, w, f32(theta), leaf_size=leaf, amb_tol=AMB)
+        check_close(gpu, ora, info, what=f"per-target Alg. 4 theta={theta} leaf={leaf} op={op}")
+    t.sync_status()
+
+
+def test_per_target_criterion_needs_paper_representatives():
+    W = _wnnc()
+    pts = torch.rand(500, 3, device="cuda")
+    for kw in ({"rep_mode": 1}, {"rep_mode": 0, "near_bf16": True}):
+        with pytest.raises(W.WnncError) as e:
+            W.Tree(pts, criterion=1, **kw)
+        assert e.value.status == 1
+
+
+def test_winding_number_refuses_trees_without_an_exact_transpose():
+    """The autograd wrapper's backward is the exact transpose of its forward
+    only with point-centroid representatives and float near-field coordinates."""
+    W = _wnnc()
+    c = synth.union_cloud(2000, 8, n_tori=1, n_ellipsoids=1)
+    mu = torch.from_numpy(synth.init_normals(2000, 2, 1e-3)).cuda().requires_grad_(True)
+    for kw in ({"rep_mode": 0}, {"near_bf16": True}):
+        t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, **kw)
+        with pytest.raises(ValueError):
+            W.winding_number(t, mu, 0.004)
 
 
 def test_exact_adjoint_identity(union5k):

@@ -141,6 +141,123 @@ def test_gpu_iteration_union500k_matches_oracle_at_full_size():
 
 
 @pytest.mark.gpu
+def test_gpu_full_solve_union500k_matches_oracle():
+    """The benchmark solve end to end: all 40 iterations on the 500,000-point
+    cloud (theta = 0.5, zero init) on the GPU against the oracle's FP64
+    iteration over the same interaction lists.  Normal signs agree at
+    >= 99.5 % of the points and the median cosine is >= 0.999; the orientation
+    accuracy against ground truth (surface points) agrees to 0.1 %."""
+    W = _gpu()
+    c = synth.config_cloud("union500k")
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mg = t.iterate(n_iter=40).cpu().numpy().astype(np.float64)
+    mo, _ = oracle.iterate(c.points, n_iter=40, theta=f32(0.5))
+    cos, dlen = _compare_fields(mg, mo, min_sign=0.995, min_cos=0.999)
+    ok = np.isfinite(c.normals).all(1)
+    pg, po = oracle.p_co(c.normals[ok], mg[ok]), oracle.p_co(c.normals[ok], mo[ok])
+    print(f"[iterate-500k] sign agreement {np.mean(cos > 0):.6f}, median cos {np.median(cos):.7f}, "
+          f"median |len ratio - 1| {dlen:.2e}, P_co gpu {pg:.6f} oracle {po:.6f}")
+    assert abs(pg - po) < 1e-3
+
+
+@pytest.mark.gpu
+def test_gpu_treecode_solve_matches_direct_sum_iteration():
+    """Alg. 3 on the plain definitions: the GPU solve at the production
+    theta = 0.5 (and theta = 0.3) against the oracle's iteration on the FP64
+    direct sums (no treecode) on a 20,000-point union, 40 iterations.
+
+    The widths follow the point spacing, as the paper sets them per data set:
+    at 20,000 points this cloud is about 3x sparser than at 50,000, and the
+    paper's preset for sparser, noisier scans (w1 = 0.01, w2 = 0.04,
+    Sec. 5.2.6) lets the exact method converge (P_co 0.992).  There the
+    treecode's ~1e-2 operator error changes no sign: agreement >= 99.5 %
+    (measured 100 %).  With the default widths (w1 = 0.002 < spacing) the exact
+    method itself orients only ~93 % of the points correctly and the treecode
+    solve flips ~0.6 % of signs among those it cannot orient; there its
+    accuracy against ground truth must equal the exact method's."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=20000)
+    mo, _ = oracle.iterate(c.points, n_iter=40, w1=0.01, w2=0.04)
+    for theta, min_cos in ((0.5, 0.999), (0.3, 0.999)):
+        t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta)
+        mg = t.iterate(n_iter=40, w1=0.01, w2=0.04).cpu().numpy().astype(np.float64)
+        cos, dlen = _compare_fields(mg, mo, min_sign=0.995, min_cos=min_cos)
+        print(f"[iterate-direct] theta={theta} w=0.04->0.01: sign agreement {np.mean(cos > 0):.5f}, "
+              f"median cos {np.median(cos):.6f}, median |len ratio - 1| {dlen:.2e}, "
+              f"P_co gpu {oracle.p_co(c.normals, mg):.5f} direct {oracle.p_co(c.normals, mo):.5f}")
+    mo, _ = oracle.iterate(c.points, n_iter=40)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mg = t.iterate(n_iter=40).cpu().numpy().astype(np.float64)
+    cos = (oracle.unit(mg) * oracle.unit(mo)).sum(1)
+    pg, po = oracle.p_co(c.normals, mg), oracle.p_co(c.normals, mo)
+    print(f"[iterate-direct] theta=0.5 w=0.016->0.002: sign agreement {np.mean(cos > 0):.5f}, "
+          f"P_co gpu {pg:.5f} direct {po:.5f}")
+    assert pg >= po - 0.005
+
+
+@pytest.mark.gpu
+def test_gpu_solve_matches_the_papers_treecode_iteration():
+    """The GPU solve (group lists, theta = 0.5, leaf size 8) against the
+    oracle's Alg. 3 on the paper's own treecode run as printed (Alg. 4 per
+    target, leaf size 1, |nu|-weighted representatives, theta = 0.5) on a
+    20,000-point union, 40 iterations with the widths of the sparser-scan
+    preset (w1 = 0.01, w2 = 0.04; see the direct-sum test above): the two
+    treecodes differ in every far-field decision, yet the orientations agree
+    (>= 99.5 % of signs; measured 100 %)."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=20000)
+    mo, _ = oracle.iterate(c.points, n_iter=40, w1=0.01, w2=0.04, paper_theta=0.5, paper_leaf_size=1)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mg = t.iterate(n_iter=40, w1=0.01, w2=0.04).cpu().numpy().astype(np.float64)
+    cos, dlen = _compare_fields(mg, mo, min_sign=0.995, min_cos=0.999)
+    print(f"[iterate-paper-tree] sign agreement {np.mean(cos > 0):.5f}, median cos {np.median(cos):.6f}, "
+          f"P_co gpu {oracle.p_co(c.normals, mg):.5f} paper treecode {oracle.p_co(c.normals, mo):.5f}")
+    assert oracle.p_co(c.normals, mg) >= oracle.p_co(c.normals, mo) - 0.005
+
+
+@pytest.mark.gpu
+def test_gpu_ablations_match_oracle():
+    """The ablations of Sec. 6.1.3 against the oracle's iteration with the
+    same switch: gradient steps only (no WNNC update), from zero; WNNC updates
+    only (no gradient step), from a random init (Sec. 6.1.3 and Fig. 12: the
+    update alone keeps whatever orientation it is given)."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=10000)
+    n = len(c.points)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
+    mg, sg = t.iterate(n_iter=6, w1=0.02, w2=0.02, use_wnnc=False, stats=True)
+    mo, so = oracle.iterate(c.points, n_iter=6, w1=0.02, w2=0.02, use_wnnc=False, theta=f32(0.5))
+    assert np.allclose(sg.cpu().numpy()[:, 1:], so[:, 1:], rtol=1e-3)
+    _compare_fields(mg.cpu().numpy().astype(np.float64), mo, min_sign=0.999, min_cos=0.9999)
+    mu0 = synth.init_normals(n, 7, c.area / n)
+    mg = t.iterate(torch.from_numpy(mu0).cuda(), n_iter=10, use_grad=False).cpu().numpy().astype(np.float64)
+    mo, _ = oracle.iterate(c.points, mu0=mu0, n_iter=10, use_grad=False, theta=f32(0.5))
+    _compare_fields(mg, mo, min_sign=0.995, min_cos=0.995)
+    assert np.allclose(np.linalg.norm(mg, axis=1), np.linalg.norm(mu0, axis=1), rtol=1e-4)
+
+
+@pytest.mark.gpu
+def test_gpu_paper_exact_iteration_matches_oracle():
+    """The paper's method as printed on the GPU -- Alg. 3 with every operator
+    on the per-target treecode of Alg. 4 (criterion 1, leaf size 1, the
+    |nu|-weighted representatives and the s-representative A^T) -- against
+    the oracle's Alg. 3 on its own implementation of that treecode, 40
+    iterations on a 10,000-point union (sparser-scan widths w1 = 0.01,
+    w2 = 0.04, at which the method converges on a cloud this sparse)."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=10000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, leaf_size=1, rep_mode=0, criterion=1)
+    mg, sg = t.iterate(n_iter=40, w1=0.01, w2=0.04, stats=True)
+    mg = mg.cpu().numpy().astype(np.float64)
+    mo, so = oracle.iterate(c.points, n_iter=40, w1=0.01, w2=0.04, paper_theta=0.5, paper_leaf_size=1)
+    assert np.allclose(sg[:3, 1:].cpu().numpy(), so[:3, 1:], rtol=1e-3)
+    cos, dlen = _compare_fields(mg, mo, min_sign=0.995, min_cos=0.999)
+    print(f"[iterate-paper-exact] sign agreement {np.mean(cos > 0):.5f}, median cos {np.median(cos):.7f}, "
+          f"P_co gpu {oracle.p_co(c.normals, mg):.5f} oracle {oracle.p_co(c.normals, mo):.5f}")
+    t.sync_status()
+
+
+@pytest.mark.gpu
 def test_gpu_paper_mode_iteration_matches_oracle():
     """rep_mode 0 (the paper's |nu|-weighted representatives and the
     s-representative A^T) through the whole iteration."""
