@@ -6,12 +6,24 @@
 // distance (knn.cu).  Output v; the predicted oriented unit normal is
 // v / |v|.  Loss per point: 1 - (v/|v|) . y for the label normal y (mean over
 // the batch).  Parameters are one flat FP32 master buffer (for Adam); every
-// weight is rounded to BF16 when it is read, and all products are accumulated
-// in FP32.
+// parameter, weights and biases, is rounded to BF16 when it is read, and all
+// products are accumulated in FP32.
 //
-// Each layer is a small dense product X W^T over a batch of points, done as a
-// shared-memory-tiled FP32 kernel (64 x 64 outputs per block, 4 x 4 per
-// thread).  Weight gradients are reduced over the batch in chunks of 1024
+// Forward (inference and the training forward): one fused kernel over all
+// four layers on the BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate).
+// Each block stages the BF16-rounded weights once in shared memory, in the
+// register order of the mma B operand; each warp then runs 16-row tiles
+// through the four layers with the activations kept in registers (the f32
+// accumulator fragment of one layer is, element for element, the A fragment
+// of the next).  Activations are FP32 values; each enters the mma as a
+// BF16 pair hi + lo (hi = bf16(a), lo = bf16(a - hi)), two products per
+// weight tile, so an activation carries ~16 significant bits and the
+// network computes what its FP32-activation definition says to ~1e-5
+// relative -- BF16 weights, FP32 accumulation.
+//
+// Backward: each layer's data and weight gradients are small dense products
+// done as shared-memory-tiled FP32 kernels (64 x 64 outputs per block, 4 x 4
+// per thread).  Weight gradients are reduced over the batch in chunks of 1024
 // rows into per-chunk partials and summed in a fixed order (deterministic).
 #include <cuda_bf16.h>
 
@@ -76,7 +88,7 @@ __global__ void __launch_bounds__(256) k_lin_fwd(const float* X, const float* W,
         for (int q = 0; q < 4; ++q) {
             const int col = c0 + tx * 4 + q;
             if (col >= N) continue;
-            float y = acc[p][q] + bias[col];
+            float y = acc[p][q] + bf16r(bias[col]);
             if (RELU) y = fmaxf(y, 0.f);
             Y[row * N + col] = y;
         }
@@ -259,6 +271,175 @@ __global__ void k_warm_init(const float* dir, const float* ref, int64_t n, float
     mu[3 * i + 2] = dz * f;
 }
 
+// ---------------------------------------------------------------------------
+// Fused forward on the tensor cores.
+// ---------------------------------------------------------------------------
+constexpr int kTcWarps = 8;                          // 16-row tiles in flight per block
+constexpr int kTileWords = 64;                       // one B fragment: 32 lanes x 2 registers
+constexpr int kNt = kHid / 8;                        // n-tiles of a 128-wide layer
+constexpr int kL1Tiles = (kIn / 16) * kNt;           // 48
+constexpr int kL2Tiles = (kHid / 16) * kNt;          // 128 (layers 2 and 3)
+constexpr int kL4Tiles = kHid / 16;                  // 8 (3 outputs padded to one n-tile of 8)
+constexpr int kOffT1 = 0, kOffT2 = kL1Tiles, kOffT3 = kOffT2 + kL2Tiles, kOffT4 = kOffT3 + kL2Tiles;
+constexpr int kWTiles = kOffT4 + kL4Tiles;           // 312 tiles = 79,872 bytes
+constexpr int kBiasF = 3 * kHid + 8;
+constexpr size_t kTcSmem = sizeof(uint32_t) * kWTiles * kTileWords + sizeof(float) * kBiasF;
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
+// Two FP32 values (lower index first) as BF16 pairs hi and lo = bf16(a - hi).
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    hi = bf16x2_bits(h);
+    lo = bf16x2_bits(__floats2bfloat162_rn(a - hf.x, b - hf.y));
+}
+
+// D = A B + D, m16n8k16, BF16 in, FP32 accumulate.
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// B fragments of y = x W^T (W [N][K] row-major, N <= 8 nt_count): tile
+// (kt, nt) holds, for lane 4g + t, register r: W[8nt + g][16kt + 2t + 8r]
+// and the next k, BF16-rounded, zero for rows n >= N.
+__device__ void fill_tiles(uint32_t* dst, const float* W, int K, int N, int nt_count) {
+    const int ntiles = (K / 16) * nt_count;
+    for (int e = threadIdx.x; e < ntiles * kTileWords; e += blockDim.x) {
+        const int tile = e / kTileWords, word = e % kTileWords;
+        const int kt = tile / nt_count, nt = tile % nt_count;
+        const int lane = word >> 1, r = word & 1;
+        const int n = 8 * nt + (lane >> 2), k = 16 * kt + 2 * (lane & 3) + 8 * r;
+        const float a = n < N ? W[(int64_t)n * K + k] : 0.f;
+        const float b = n < N ? W[(int64_t)n * K + k + 1] : 0.f;
+        dst[e] = bf16x2_bits(__floats2bfloat162_rn(a, b));
+    }
+}
+
+// One 128-wide layer: acc[nt] = sum over k-tiles of (hi + lo) A times the tiles.
+template <int KT>
+__device__ __forceinline__ void tc_layer(const uint32_t (&ahi)[KT][4], const uint32_t (&alo)[KT][4],
+                                         const uint32_t* tiles, float (&acc)[kNt][4], int lane) {
+#pragma unroll
+    for (int nt = 0; nt < kNt; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt) {
+#pragma unroll
+        for (int nt = 0; nt < kNt; ++nt) {
+            const uint2 b = reinterpret_cast<const uint2*>(tiles + (kt * kNt + nt) * kTileWords)[lane];
+            mma_bf16(acc[nt], ahi[kt], b.x, b.y);
+            mma_bf16(acc[nt], alo[kt], b.x, b.y);
+        }
+    }
+}
+
+// Bias and ReLU on a layer's accumulators (rows r0 + g and r0 + g + 8,
+// columns 8nt + 2t, +1), optional FP32 store of the activations, and the
+// next layer's A fragments: k-tile kt takes n-tiles 2kt (columns 16kt + 2t)
+// and 2kt + 1 (columns 16kt + 8 + 2t).
+__device__ __forceinline__ void tc_activate(float (&acc)[kNt][4], const float* bias, float* hstore, int64_t r0,
+                                            int64_t B, int lane, uint32_t (&ahi)[8][4], uint32_t (&alo)[8][4]) {
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ra = r0 + g, rb = ra + 8;
+#pragma unroll
+    for (int nt = 0; nt < kNt; ++nt) {
+        const int col = 8 * nt + 2 * t;
+        const float b0 = bias[col], b1 = bias[col + 1];
+        acc[nt][0] = fmaxf(acc[nt][0] + b0, 0.f);
+        acc[nt][1] = fmaxf(acc[nt][1] + b1, 0.f);
+        acc[nt][2] = fmaxf(acc[nt][2] + b0, 0.f);
+        acc[nt][3] = fmaxf(acc[nt][3] + b1, 0.f);
+        if (hstore) {
+            if (ra < B) *reinterpret_cast<float2*>(hstore + ra * kHid + col) = make_float2(acc[nt][0], acc[nt][1]);
+            if (rb < B) *reinterpret_cast<float2*>(hstore + rb * kHid + col) = make_float2(acc[nt][2], acc[nt][3]);
+        }
+    }
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt) {
+        split_bf16x2(acc[2 * kt][0], acc[2 * kt][1], ahi[kt][0], alo[kt][0]);
+        split_bf16x2(acc[2 * kt][2], acc[2 * kt][3], ahi[kt][1], alo[kt][1]);
+        split_bf16x2(acc[2 * kt + 1][0], acc[2 * kt + 1][1], ahi[kt][2], alo[kt][2]);
+        split_bf16x2(acc[2 * kt + 1][2], acc[2 * kt + 1][3], ahi[kt][3], alo[kt][3]);
+    }
+}
+
+// y [B][3] = network(x [B][48]); with h1 (h1, h2, h3 non-null) the hidden
+// activations are stored too (the training forward).  Persistent blocks of
+// kTcWarps warps; warp w of block b takes the 16-row tiles b kTcWarps + w,
+// then every gridDim.x kTcWarps tiles further.
+__global__ void __launch_bounds__(32 * kTcWarps) k_mlp_fwd_tc(const float* x, const float* P, int64_t B, float* y,
+                                                              float* h1, float* h2, float* h3) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t* tiles = reinterpret_cast<uint32_t*>(smem_raw);
+    float* bias = reinterpret_cast<float*>(tiles + kWTiles * kTileWords);
+    fill_tiles(tiles + kOffT1 * kTileWords, P + kOffW1, kIn, kHid, kNt);
+    fill_tiles(tiles + kOffT2 * kTileWords, P + kOffW2, kHid, kHid, kNt);
+    fill_tiles(tiles + kOffT3 * kTileWords, P + kOffW3, kHid, kHid, kNt);
+    fill_tiles(tiles + kOffT4 * kTileWords, P + kOffW4, kHid, kOut, 1);
+    for (int e = threadIdx.x; e < kBiasF; e += blockDim.x) {
+        float v = 0.f;
+        if (e < kHid) v = P[kOffB1 + e];
+        else if (e < 2 * kHid) v = P[kOffB2 + e - kHid];
+        else if (e < 3 * kHid) v = P[kOffB3 + e - 2 * kHid];
+        else if (e < 3 * kHid + kOut) v = P[kOffB4 + e - 3 * kHid];
+        bias[e] = bf16r(v);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ntiles = (B + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * kTcWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTcWarps) {
+        const int64_t r0 = tile * 16, ra = r0 + g, rb = ra + 8;
+        // layer 1 A fragments from the input rows
+        uint32_t xhi[3][4], xlo[3][4];
+#pragma unroll
+        for (int kt = 0; kt < 3; ++kt) {
+            const int c = 16 * kt + 2 * t;
+            float v[8];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cc = c + 8 * h;
+                v[4 * h + 0] = ra < B ? x[ra * kIn + cc] : 0.f;
+                v[4 * h + 1] = ra < B ? x[ra * kIn + cc + 1] : 0.f;
+                v[4 * h + 2] = rb < B ? x[rb * kIn + cc] : 0.f;
+                v[4 * h + 3] = rb < B ? x[rb * kIn + cc + 1] : 0.f;
+            }
+            split_bf16x2(v[0], v[1], xhi[kt][0], xlo[kt][0]);   // row g,     cols c, c+1
+            split_bf16x2(v[2], v[3], xhi[kt][1], xlo[kt][1]);   // row g + 8, cols c, c+1
+            split_bf16x2(v[4], v[5], xhi[kt][2], xlo[kt][2]);   // row g,     cols c+8, c+9
+            split_bf16x2(v[6], v[7], xhi[kt][3], xlo[kt][3]);   // row g + 8, cols c+8, c+9
+        }
+        float acc[kNt][4];
+        uint32_t ahi[8][4], alo[8][4];
+        tc_layer<3>(xhi, xlo, tiles + kOffT1 * kTileWords, acc, lane);
+        tc_activate(acc, bias, h1, r0, B, lane, ahi, alo);
+        tc_layer<8>(ahi, alo, tiles + kOffT2 * kTileWords, acc, lane);
+        tc_activate(acc, bias + kHid, h2, r0, B, lane, ahi, alo);
+        tc_layer<8>(ahi, alo, tiles + kOffT3 * kTileWords, acc, lane);
+        tc_activate(acc, bias + 2 * kHid, h3, r0, B, lane, ahi, alo);
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < 8; ++kt) {
+            const uint2 b = reinterpret_cast<const uint2*>(tiles + (kOffT4 + kt) * kTileWords)[lane];
+            mma_bf16(o, ahi[kt], b.x, b.y);
+            mma_bf16(o, alo[kt], b.x, b.y);
+        }
+        // lane (g, t) holds columns 2t, 2t + 1 of rows g and g + 8; columns < 3 are outputs
+        const float* b4 = bias + 3 * kHid;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int col = 2 * t + q;
+            if (col < kOut) {
+                if (ra < B) y[ra * kOut + col] = o[q] + b4[col];
+                if (rb < B) y[rb * kOut + col] = o[2 + q] + b4[col];
+            }
+        }
+    }
+}
+
 dim3 grid2(int64_t B, int N) { return dim3((unsigned)((B + kT - 1) / kT), (unsigned)((N + kT - 1) / kT)); }
 
 }  // namespace
@@ -291,8 +472,27 @@ void mlp_free(Mlp& m) {
     dfree(m.out); dfree(m.d1); dfree(m.d2); dfree(m.d3); dfree(m.dout); dfree(m.part); dfree(m.lpart);
 }
 
-// Forward of B <= max_batch rows into m.h1..h3 and y.
-static void forward_rows(Mlp& m, const float* x, int64_t B, float* y, cudaStream_t s) {
+// Fused tensor-core forward of B rows; with keep, the hidden activations go
+// to m.h1..h3 (B <= max_batch then).
+static void forward_tc(Mlp& m, const float* x, int64_t B, float* y, bool keep, cudaStream_t s) {
+    // the attribute is set on the current device's copy of the kernel (every call: it is cheap)
+    WNNC_CUDA(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+    int dev = 0, sms = 0, per_sm = 0;
+    WNNC_CUDA(cudaGetDevice(&dev));
+    WNNC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WNNC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_fwd_tc, 32 * kTcWarps, kTcSmem));
+    // persistent blocks: as many as are resident at once, fewer for small batches
+    const int64_t tiles = (B + 15) / 16;
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, (tiles + kTcWarps - 1) / kTcWarps));
+    k_mlp_fwd_tc<<<grid, 32 * kTcWarps, kTcSmem, s>>>(x, m.params, B, y, keep ? m.h1 : nullptr,
+                                                      keep ? m.h2 : nullptr, keep ? m.h3 : nullptr);
+    WNNC_LAUNCH_CHECK();
+}
+
+// The FP32 SIMT forward of B <= max_batch rows into m.h1..h3 and y (kept for
+// comparison with the tensor-core path; not used by the entry points).
+[[maybe_unused]] static void forward_rows_simt(Mlp& m, const float* x, int64_t B, float* y, cudaStream_t s) {
     const float* P = m.params;
     k_lin_fwd<true><<<grid2(B, kHid), 256, 0, s>>>(x, P + kOffW1, P + kOffB1, m.h1, B, kIn, kHid);
     WNNC_LAUNCH_CHECK();
@@ -305,15 +505,12 @@ static void forward_rows(Mlp& m, const float* x, int64_t B, float* y, cudaStream
 }
 
 void mlp_forward(Mlp& m, const float* x, int64_t B, float* y, cudaStream_t s) {
-    for (int64_t b0 = 0; b0 < B; b0 += m.max_batch) {
-        const int64_t nb = std::min<int64_t>(m.max_batch, B - b0);
-        forward_rows(m, x + b0 * kIn, nb, y + b0 * kOut, s);
-    }
+    forward_tc(m, x, B, y, false, s);
 }
 
 // Gradient of the mean loss over B <= max_batch rows into m.grad; loss to loss_dev.
 void mlp_grad(Mlp& m, const float* x, const float* label, int64_t B, float* loss_dev, cudaStream_t s) {
-    forward_rows(m, x, B, m.out, s);
+    forward_tc(m, x, B, m.out, true, s);
     const int nlb = ceil_div(B, 256);
     k_cos_loss<<<nlb, 256, 0, s>>>(m.out, label, B, m.loss_mode, m.dout, m.lpart);
     WNNC_LAUNCH_CHECK();

@@ -62,3 +62,23 @@ def test_patch_features_are_scale_free_and_nearest_first():
     assert np.all(np.diff(nrm, axis=1) >= -1e-12)
     f2 = M.patch_features(3.0 * x, idx)
     assert np.allclose(f2, f.reshape(-1, 48))
+
+
+def test_adam_closed_forms():
+    """Adam's bias correction makes the first step lr g/(|g| + eps) and every
+    step under a constant gradient g the same size; a worked two-step case:
+    g1 = 1, g2 = -1 (b1 = 0.9, b2 = 0.999) gives m2 = -0.01, v2 = 0.001999,
+    m_hat = -0.01/0.19, v_hat = 0.001999/0.001999 = 1, so p moves by
+    +lr (0.01/0.19)/(1 + eps) in the second step."""
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    p1, m, v = M.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, 0.01)
+    assert np.allclose(p1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-14, atol=0)
+    p, m, v = p1, m, v
+    for t in range(2, 12):
+        q, m, v = M.adam_step(p, g, m, v, t, 0.01)
+        assert np.allclose(q - p, p1, rtol=1e-12, atol=1e-18)
+        p = q
+    p, m, v = M.adam_step(np.zeros(1), np.ones(1), np.zeros(1), np.zeros(1), 1, 0.1)
+    q, m, v = M.adam_step(p, -np.ones(1), m, v, 2, 0.1)
+    assert np.isclose(m[0], -0.01, rtol=1e-14) and np.isclose(v[0], 0.001999, rtol=1e-13)
+    assert np.isclose(q[0] - p[0], 0.1 * (0.01 / 0.19) / (1 + 1e-8), rtol=1e-12)
