@@ -93,6 +93,15 @@ typedef struct {
                               WNNC_EINVAL).  With leaf_size 1 this is Alg. 4 as printed.  A
                               reference mode: warps diverge, several times slower.
                               wnnc_get_stats still counts the group lists' pairs */
+    int far_order;     /* order of each far node's term (criterion 0, rep_mode 1):
+                          0 = the node's summed nu at its point centroid x_B (Eq. 13-14; default);
+                          1 = plus the first-order Taylor terms of gradPhi and HPhi about x_B,
+                              from the node moment S = sum_j sym((x_j - x_B) nu_j^T); A^T stays
+                              the exact transpose (per-node sums of s HPhi pushed down as
+                              -H_B (x_j - x_B)).  The step toward the expansions of an FMM that
+                              Sec. 4.5 and Sec. 6.3 name for precision control: the far-field
+                              error falls as (h/R)^2 instead of h/R.  Other values, or
+                              far_order 1 with rep_mode 0 or criterion 1: WNNC_EINVAL */
 } wnnc_tree_params;
 
 /* Iteration parameters (Alg. 3; Sec. 5.1.1 defaults n = 40, w1 = 0.002, w2 = 0.016). */

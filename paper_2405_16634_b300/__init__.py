@@ -45,7 +45,8 @@ class WnncError(RuntimeError):
 
 class TreeParams(Structure):
     _fields_ = [("max_depth", c_int), ("leaf_size", c_int), ("theta", c_float),
-                ("rep_mode", c_int), ("moments_fp64", c_int), ("near_bf16", c_int), ("criterion", c_int)]
+                ("rep_mode", c_int), ("moments_fp64", c_int), ("near_bf16", c_int), ("criterion", c_int),
+                ("far_order", c_int)]
 
 
 class IterParams(Structure):
@@ -166,10 +167,12 @@ class Tree:
 
     def __init__(self, points, theta: float = 0.5, leaf_size: int = 8, max_depth: int = 15,
                  rep_mode: int = 1, moments_fp64: bool = False, near_bf16: bool = False,
-                 criterion: int = 0):
+                 criterion: int = 0, far_order: int = 0):
         """criterion 0: far decisions per target group on boxes, lists built once
         (default); 1: the paper's per-target test of Alg. 4 on every call
-        (needs rep_mode 0; with leaf_size 1 it is Alg. 4 as printed)."""
+        (needs rep_mode 0; with leaf_size 1 it is Alg. 4 as printed).
+        far_order 1: far nodes also carry the first-order Taylor terms of the
+        kernels about their centroid (rep_mode 1, criterion 0)."""
         pts = points if isinstance(points, torch.Tensor) else torch.as_tensor(points)
         self.device = pts.device if pts.is_cuda else torch.device("cuda", torch.cuda.current_device())
         pts = _dev_f32(pts, (-1, 3), self.device)
@@ -179,6 +182,7 @@ class Tree:
         p.rep_mode, p.moments_fp64 = int(rep_mode), int(bool(moments_fp64))
         p.near_bf16 = int(bool(near_bf16))
         p.criterion = int(criterion)
+        p.far_order = int(far_order)
         self.params = p
         h = c_void_p()
         with torch.cuda.device(self.device):

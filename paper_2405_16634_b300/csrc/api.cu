@@ -94,6 +94,15 @@ static void alloc_workspace(Tree& t) {
     WNNC_CUDA(cudaMemsetAsync(t.scalars, 0, 4 * sizeof(double), alloc_stream()));
     t.err_flag = dalloc<int>(1);
     WNNC_CUDA(cudaMemsetAsync(t.err_flag, 0, sizeof(int), alloc_stream()));
+    if (t.params.far_order == 1) {
+        t.mom_dip = dalloc<float4>(2 * (size_t)nn);
+        t.mom_dip_r = dalloc<float4>(2 * (size_t)nn);
+        t.dip_corr = dalloc<float4>(n);
+        t.contrib_h0 = dalloc<float4>(t.self.far_entries);
+        t.contrib_h1 = dalloc<float4>(t.self.far_entries);
+        t.hnode0 = dalloc<float4>(nn);
+        t.hnode1 = dalloc<float4>(nn);
+    }
 }
 
 // Read and clear the latched device error flags.
@@ -140,6 +149,9 @@ static void check_params(const wnnc_tree_params& p) {
     if (p.criterion != 0 && p.criterion != 1) fail(WNNC_EINVAL, "criterion must be 0 or 1");
     if (p.criterion == 1 && (p.rep_mode != 0 || p.near_bf16 != 0))
         fail(WNNC_EINVAL, "criterion 1 (per-target Alg. 4) needs rep_mode 0 and near_bf16 0");
+    if (p.far_order != 0 && p.far_order != 1) fail(WNNC_EINVAL, "far_order must be 0 or 1");
+    if (p.far_order == 1 && (p.rep_mode != 1 || p.criterion != 0))
+        fail(WNNC_EINVAL, "far_order 1 needs rep_mode 1 and criterion 0");
 }
 
 static void check_w(float w) {
@@ -169,6 +181,7 @@ wnnc_status wnnc_tree_params_default(wnnc_tree_params* p) {
     p->moments_fp64 = 0;
     p->near_bf16 = 0;
     p->criterion = 0;
+    p->far_order = 0;
     return WNNC_OK;
 }
 

@@ -264,6 +264,14 @@ struct Tree {
     float4* vnode = nullptr;      // per node far sum (adjoint)
     float4* mom_x = nullptr;      // node weighted offsets (rep_mode 0): sum |nu| (x - cell), -
     double* dmom = nullptr;       // double node sums (moments_fp64), 8 per node
+    // first-order far field (far_order 1)
+    float4* mom_dip = nullptr;    // per node 2 float4: (Sxx, Syy, Szz, Sxy), (Sxz, Syz, tr S, 0) of mu
+    float4* mom_dip_r = nullptr;  // the same of the step direction r
+    float4* dip_corr = nullptr;   // per sorted target: first-order far terms (G x, y, z, A), sum units
+    float4* contrib_h0 = nullptr; // per far entry: sum s HPhi, (xx, yy, zz, -) and (xy, xz, yz, -)
+    float4* contrib_h1 = nullptr;
+    float4* hnode0 = nullptr;     // per node: the entries' sums of s HPhi (same two parts)
+    float4* hnode1 = nullptr;
     double* partials = nullptr;   // per-group partial sums (3 x max(ngroups, nchunks, nach))
     double* red = nullptr;        // first-stage sums of the partials (3 x 256)
     unsigned* red_ticket = nullptr;   // blocks of the first stage done (the last one finishes)

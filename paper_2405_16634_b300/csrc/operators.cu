@@ -285,6 +285,7 @@ struct GatherArgs {
     const int* nstart;        // first sorted point of each node
     const int* ncount;        // points of each node
     int* err_flag;            // device error flags (a walk stack overflow sets kErrCapacity)
+    const float4* dip_corr;   // far_order 1: per sorted target, the first-order far terms (G x,y,z, A)
 };
 
 // Accumulators: (x, y, z) holds the A / A^T sum, or for G the sum of
@@ -420,8 +421,21 @@ __device__ __forceinline__ Acc3 combine(Acc3 a) {
 // Epilogue of one group (all 32 lanes call it; lane < size holds target i).
 template <int EPI>
 __device__ __forceinline__ void gather_epilogue(const GatherArgs& A, int g, int64_t i, bool valid,
-                                                const Acc3& acc, int lane) {
+                                                Acc3 acc, int lane) {
     double part = 0.0;
+    // far_order 1: the first-order far terms of the target, summed over its
+    // group's far list by k_far_dip (same units as the sums here)
+    if (A.dip_corr && valid) {
+        const float4 c = A.dip_corr[i];
+        if (EPI == kEpiStoreW || EPI == kEpiResidual || EPI == kEpiNormSq) {
+            acc.x += c.w;
+        } else if (EPI == kEpiStoreGrad || EPI == kEpiRescale) {
+            acc.x += c.x; acc.y += c.y; acc.z += c.z;
+        } else if (EPI == kEpiResidualAG || EPI == kEpiNormSqAG) {
+            acc.s += c.w;
+            acc.x += c.x; acc.y += c.y; acc.z += c.z;
+        }
+    }
     if (EPI == kEpiStoreW) {
         if (valid) A.out[A.tperm[i]] = acc.x * kInv4Pi;
     } else if (EPI == kEpiStoreGrad || EPI == kEpiStoreATpaper) {
@@ -843,6 +857,10 @@ struct AdjArgs {
     float* out;
     float4* r_out;
     double* partial;
+    const float4* hnode0;     // far_order 1: per node sum of s HPhi, (xx, yy, zz, -)
+    const float4* hnode1;     //   and (xy, xz, yz, -)
+    float4* contrib_h0;       // the same per far entry (k_adj_far_h)
+    float4* contrib_h1;
 };
 
 // Adjoint terms s_i gradPhi(x_i - x) = s_i (x - x_i) / r^3 at x = p from a
@@ -976,6 +994,16 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
         for (int a = A.leaf_of[j]; a >= 0; a = A.nparent[a]) {
             const float4 v = A.vnode[a];
             ax += v.x; ay += v.y; az += v.z;
+            if (A.hnode0) {
+                // far_order 1: - H_a (x_j - x_a), x_a the node's point centroid
+                const float4 p = shift(A.corig[j >> 5], A.ncell[a], A.pos[j]);
+                const float4 c = A.ncent[a];
+                const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+                const float4 h0 = A.hnode0[a], h1 = A.hnode1[a];   // (xx, yy, zz), (xy, xz, yz)
+                ax -= fmaf(h0.x, dx, fmaf(h1.x, dy, h1.y * dz));
+                ay -= fmaf(h1.x, dx, fmaf(h0.y, dy, h1.z * dz));
+                az -= fmaf(h1.y, dx, fmaf(h1.z, dy, h0.z * dz));
+            }
         }
         ax *= kInv4Pi; ay *= kInv4Pi; az *= kInv4Pi;
         if (EPI == kEpiStoreATpaper) {
@@ -993,6 +1021,204 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
         for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
         if (lane == 0) A.partial[gs] = part;
     }
+}
+
+// ---------------------------------------------------------------------------
+// First-order far field (tree parameter far_order = 1; rep_mode 1).  With
+// d = x_B - x_i (node centroid minus target, as in the pair terms), r = |d|,
+// and the node moment S = sum_j sym((x_j - x_B) nu_j^T), the first-order
+// Taylor terms of the kernels about x_B add to a far node's term, in the
+// units of the sums (times 4 pi):
+//   A:   tr S / r^3 - 3 (d.S d) / r^5
+//   G:   -(6 S d + 3 tr S d) / r^5 + 15 (d.S d) d / r^7
+// and the exact transpose adds, for every point j of a node B, -H_B (x_j - x_B)
+// with H_B = sum over the node's far entries of s_i (3 d d^T - r^2 I) / r^5.
+// Pairs take the cut-off decision of the node's monopole term (the same r^2,
+// computed in the same order).
+// ---------------------------------------------------------------------------
+// S of every node that is not a top node (at most kMomDirect points, or a
+// leaf), one warp per node over its range: (Sxx, Syy, Szz, Sxy), (Sxz, Syz,
+// tr S, 0) at out[2b], out[2b + 1].
+__global__ void k_mom_dipole(int nnodes, const int* nstart, const int* ncount, const int* nnchild,
+                             const float4* ncell, const float4* ncent, const float4* spos, const float4* scorig,
+                             const float4* nu, float4* out) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nnodes) return;
+    const int cnt = ncount[b];
+    if (cnt > kMomDirect && nnchild[b] > 0) return;      // top node: from its front (k_mom_dipole_top)
+    const float4 cb = ncell[b], cc = ncent[b];
+    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int j0 = nstart[b];
+    for (int j = j0 + lane; j < j0 + cnt; j += 32) {
+        const float4 p = shift(scorig[j >> 5], cb, spos[j]);   // the point relative to the cell centre
+        const float dx = p.x - cc.x, dy = p.y - cc.y, dz = p.z - cc.z;
+        const float4 v = nu[j];
+        m[0] = fmaf(dx, v.x, m[0]);
+        m[1] = fmaf(dy, v.y, m[1]);
+        m[2] = fmaf(dz, v.z, m[2]);
+        m[3] = fmaf(0.5f, fmaf(dx, v.y, dy * v.x), m[3]);
+        m[4] = fmaf(0.5f, fmaf(dx, v.z, dz * v.x), m[4]);
+        m[5] = fmaf(0.5f, fmaf(dy, v.z, dz * v.y), m[5]);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m[c] += __shfl_xor_sync(0xffffffffu, m[c], o);
+    if (lane == 0) {
+        out[2 * (int64_t)b] = make_float4(m[0], m[1], m[2], m[3]);
+        out[2 * (int64_t)b + 1] = make_float4(m[4], m[5], m[0] + m[1] + m[2], 0.f);
+    }
+}
+
+// S of the top nodes from their fronts (the non-top nodes under a top node
+// that partition its points), moved to the top node's centroid:
+//   S_top = sum_f S_f + sym((x_f - x_top) nu_f^T),  nu_f the front node's sum.
+// One warp per top node, lanes over the front, then a fixed xor reduction.
+__global__ void k_mom_dipole_top(int ntop, const int* top, const int2* top_rng, const int* front,
+                                 const float4* ncell, const float4* ncent, const float4* mom, float4* out) {
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= ntop) return;
+    const int b = top[k];
+    const int2 rg = top_rng[k];
+    const float4 cb = ncell[b], cc = ncent[b];
+    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int q = rg.x + lane; q < rg.y; q += 32) {
+        const int f = front[q];
+        const float4 cf = ncell[f], ef = ncent[f], v = mom[f];
+        const float dx = ((cf.x - cb.x) + ef.x) - cc.x;   // centroid of f minus that of b
+        const float dy = ((cf.y - cb.y) + ef.y) - cc.y;
+        const float dz = ((cf.z - cb.z) + ef.z) - cc.z;
+        const float4 s0 = out[2 * (int64_t)f], s1 = out[2 * (int64_t)f + 1];
+        m[0] += fmaf(dx, v.x, s0.x);
+        m[1] += fmaf(dy, v.y, s0.y);
+        m[2] += fmaf(dz, v.z, s0.z);
+        m[3] += fmaf(0.5f, fmaf(dx, v.y, dy * v.x), s0.w);
+        m[4] += fmaf(0.5f, fmaf(dx, v.z, dz * v.x), s1.x);
+        m[5] += fmaf(0.5f, fmaf(dy, v.z, dz * v.y), s1.y);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m[c] += __shfl_xor_sync(0xffffffffu, m[c], o);
+    if (lane == 0) {
+        out[2 * (int64_t)b] = make_float4(m[0], m[1], m[2], m[3]);
+        out[2 * (int64_t)b + 1] = make_float4(m[4], m[5], m[0] + m[1] + m[2], 0.f);
+    }
+}
+
+// The first-order far terms of every target: one warp per target group, one
+// target per lane; the group's far nodes (centroid in the group's frame, S)
+// staged 32 at a time in shared memory.  OP kOpA: A's term in .w; kOpG: G's
+// in .xyz; kOpAG: both.
+template <int OP>
+__global__ void __launch_bounds__(32 * kGatherWarps) k_far_dip(GatherArgs A, const int* far_off,
+                                                               const float4* mdip, float4* corr) {
+    __shared__ float4 sp_all[kGatherWarps][32], s0_all[kGatherWarps][32], s1_all[kGatherWarps][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kGatherWarps + wl;
+    if (g >= A.ngroups) return;
+    float4* sp = sp_all[wl];
+    float4* s0 = s0_all[wl];
+    float4* s1 = s1_all[wl];
+    const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
+    const int64_t i = (int64_t)i0 + lane;
+    const bool valid = lane < cnt_t;
+    const float4 o = A.tgorig[g];
+    const float4 t = valid ? shift(A.tcorig[i >> 5], o, A.tpos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float cx = 0.f, cy = 0.f, cz = 0.f, ca = 0.f;
+    const int f0 = far_off[g], f1 = far_off[g + 1];
+    for (int base = f0; base < f1; base += 32) {
+        const int cnt = min(32, f1 - base);
+        if (lane < cnt) {
+            const int b = A.far_id[base + lane];
+            sp[lane] = shift(A.ncell[b], o, A.nrep[b]);
+            s0[lane] = mdip[2 * (int64_t)b];
+            s1[lane] = mdip[2 * (int64_t)b + 1];
+        }
+        __syncwarp();
+        if (valid) {
+            for (int k = 0; k < cnt; ++k) {
+                const float4 p = sp[k];
+                const float dx = p.x - t.x, dy = p.y - t.y, dz = p.z - t.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (!(r2 >= A.w2)) continue;
+                const float ir = rsqrtf(r2);
+                const float ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+                const float4 a0 = s0[k], a1 = s1[k];
+                const float sdx = fmaf(a0.x, dx, fmaf(a0.w, dy, a1.x * dz));
+                const float sdy = fmaf(a0.w, dx, fmaf(a0.y, dy, a1.y * dz));
+                const float sdz = fmaf(a1.x, dx, fmaf(a1.y, dy, a0.z * dz));
+                const float dsd = fmaf(dx, sdx, fmaf(dy, sdy, dz * sdz));
+                const float tr = a1.z;
+                if (OP == kOpA || OP == kOpAG) ca += fmaf(tr, ir3, -3.f * dsd * ir5);
+                if (OP == kOpG || OP == kOpAG) {
+                    const float f15 = 15.f * dsd * (ir5 * ir2);
+                    cx += fmaf(f15, dx, -fmaf(6.f, sdx, 3.f * tr * dx) * ir5);
+                    cy += fmaf(f15, dy, -fmaf(6.f, sdy, 3.f * tr * dy) * ir5);
+                    cz += fmaf(f15, dz, -fmaf(6.f, sdz, 3.f * tr * dz) * ir5);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (valid) corr[i] = make_float4(cx, cy, cz, ca);
+}
+
+// H per far entry for the transpose of the first-order terms: one warp per
+// work item of the far adjoint (a slice of one group's far entries), the
+// group's targets (point, s) staged once; lane e of a batch sums, over the
+// targets, s_i (3 d d^T - r^2 I) / r^5 with d = x_B - x_i.
+__global__ void WNNC_ADJ_BOUNDS k_adj_far_h(AdjArgs A) {
+    __shared__ float4 tp_all[kGatherWarps][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x * kGatherWarps + wl;
+    if (it >= A.nitems) return;
+    float4* tp = tp_all[wl];
+    const Item item = A.items[it];
+    const int g = item.g;
+    const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
+    const int64_t i = (int64_t)i0 + lane;
+    const float4 o = A.gorig[g];
+    float4 p = lane < cnt_t ? shift(A.corig[i >> 5], o, A.pos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    p.w = lane < cnt_t ? A.sv[i] : 0.f;
+    tp[lane] = make_float4(-p.x, -p.y, -p.z, p.w);   // negated, as in the monopole's far adjoint
+    __syncwarp();
+    for (int base = item.f0; base < item.f1; base += 32) {
+        const int e = base + lane;
+        if (e >= item.f1) continue;
+        const int b = A.far_id[e];
+        const float4 bp = shift(A.ncell[b], o, A.ncent[b]);
+        float h[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < cnt_t; ++k) {
+            const float4 tk = tp[k];
+            const float dx = bp.x + tk.x, dy = bp.y + tk.y, dz = bp.z + tk.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (!(r2 >= A.w2)) continue;
+            const float ir = rsqrtf(r2);
+            const float ir2 = ir * ir;
+            const float q = tk.w * (ir2 * ir2 * ir);
+            const float q3 = 3.f * q;
+            h[0] = fmaf(q, fmaf(3.f * dx, dx, -r2), h[0]);
+            h[1] = fmaf(q, fmaf(3.f * dy, dy, -r2), h[1]);
+            h[2] = fmaf(q, fmaf(3.f * dz, dz, -r2), h[2]);
+            h[3] = fmaf(q3, dx * dy, h[3]);
+            h[4] = fmaf(q3, dx * dz, h[4]);
+            h[5] = fmaf(q3, dy * dz, h[5]);
+        }
+        A.contrib_h0[e] = make_float4(h[0], h[1], h[2], 0.f);   // k_adj_node sums x, y, z
+        A.contrib_h1[e] = make_float4(h[3], h[4], h[5], 0.f);
+    }
+}
+
+// x += a y over all four components (the first-order moments of mu + alpha r).
+__global__ void k_axpy4(float4* x, const float4* y, const double* scalars, int64_t n) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float a = (float)scalars[3];
+    const float4 u = x[k], v = y[k];
+    x[k] = make_float4(fmaf(a, v.x, u.x), fmaf(a, v.y, u.y), fmaf(a, v.z, u.z), fmaf(a, v.w, u.w));
 }
 
 // Near part, first kernel: the pair sums of each (group, source) near slot.
@@ -1529,12 +1755,44 @@ static void perm_in_vec(Tree& t, const float* in, float f, float4* out, cudaStre
     WNNC_LAUNCH_CHECK();
 }
 
+// far_order 1: the first-order moments S of the sorted field nu into mdip
+// (mom: the field's monopole moments, already computed).
+static void dipole_moments(Tree& t, const float4* nu, const float4* mom, float4* mdip, cudaStream_t s) {
+    ProfScope ps(&t.prof, WNNC_PROF_MOMENTS, s);
+    k_mom_dipole<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(
+        t.nnodes, t.node_start, t.node_count, t.node_nchild, t.node_cell, t.node_cent, t.self.pos, t.self.corig, nu,
+        mdip);
+    WNNC_LAUNCH_CHECK();
+    if (t.nmom_top > 0) {
+        k_mom_dipole_top<<<ceil_div((int64_t)t.nmom_top * 32, kTB), kTB, 0, s>>>(
+            t.nmom_top, t.mom_top, t.mom_top_rng, t.mom_front, t.node_cell, t.node_cent, mom, mdip);
+        WNNC_LAUNCH_CHECK();
+    }
+}
+
+// far_order 1: the first-order far terms of the targets of ts (moments mdip)
+// into corr, and the gather arguments a told to add them.
+template <int OP>
+static void far_dipole(Tree& t, const TargetSet& ts, const float4* mdip, GatherArgs& a, float4* corr,
+                       cudaStream_t s) {
+    ProfScope ps(&t.prof, OP == kOpAG ? WNNC_PROF_AG : (OP == kOpG ? WNNC_PROF_G : WNNC_PROF_A), s);
+    if (ts.ngroups > 0) {
+        k_far_dip<OP><<<ceil_div(ts.ngroups, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a, ts.far_off, mdip, corr);
+        WNNC_LAUNCH_CHECK();
+    }
+    a.dip_corr = corr;
+}
+
 
 void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     const float s2 = (float)(t.scale * t.scale);
     perm_in_vec(t, mu, s2, t.mu_a, s);
     moments(t, t.mu_a, nullptr, t.params.rep_mode, t.mom, s);
     GatherArgs a = base_args(t, t.self, w, t.part_acc);
+    if (t.params.far_order == 1) {
+        dipole_moments(t, t.mu_a, t.mom, t.mom_dip, s);
+        far_dipole<kOpA>(t, t.self, t.mom_dip, a, t.dip_corr, s);
+    }
     a.sval = t.mu_a;
     a.out = out;
     launch_gather<kOpA, kEpiStoreW>(t, a, s);
@@ -1545,6 +1803,10 @@ void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     perm_in_vec(t, mu, s2, t.mu_a, s);
     moments(t, t.mu_a, nullptr, t.params.rep_mode, t.mom, s);
     GatherArgs a = base_args(t, t.self, w, t.part_acc);
+    if (t.params.far_order == 1) {
+        dipole_moments(t, t.mu_a, t.mom, t.mom_dip, s);
+        far_dipole<kOpG>(t, t.self, t.mom_dip, a, t.dip_corr, s);
+    }
     a.sval = t.mu_a;
     a.out = out;
     a.scale = (float)t.scale;
@@ -1570,6 +1832,25 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
         k_adj_node<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(t.nnodes, t.tfar_off, t.tfar_ent,
                                                                          t.contrib, t.vnode);
         WNNC_LAUNCH_CHECK();
+        if (t.params.far_order == 1) {
+            // the transpose of the first-order far terms: s HPhi per far entry,
+            // summed per node, pushed down in the near kernel's epilogue
+            AdjArgs f = a;
+            f.items = t.adj_far_work.items;
+            f.nitems = t.adj_far_work.nitems;
+            f.contrib_h0 = t.contrib_h0;
+            f.contrib_h1 = t.contrib_h1;
+            k_adj_far_h<<<ceil_div(f.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(f);
+            WNNC_LAUNCH_CHECK();
+            k_adj_node<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(t.nnodes, t.tfar_off, t.tfar_ent,
+                                                                             t.contrib_h0, t.hnode0);
+            WNNC_LAUNCH_CHECK();
+            k_adj_node<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(t.nnodes, t.tfar_off, t.tfar_ent,
+                                                                             t.contrib_h1, t.hnode1);
+            WNNC_LAUNCH_CHECK();
+            a.hnode0 = t.hnode0;
+            a.hnode1 = t.hnode1;
+        }
     } else {
         WNNC_CUDA(cudaMemsetAsync(t.vnode, 0, sizeof(float4) * t.nnodes, s));
     }
@@ -1648,12 +1929,20 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     perm_in_vec(t, mu, s2, t.mu_a, s);
     moments(t, t.mu_a, nullptr, t.params.rep_mode, t.mom, s);
     GatherArgs a = base_args(t, Q, w, pacc);
+    float4* qcorr = nullptr;
+    if (t.params.far_order == 1) {
+        qcorr = dalloc<float4>((size_t)m);
+        dipole_moments(t, t.mu_a, t.mom, t.mom_dip, s);
+        if (grad) far_dipole<kOpG>(t, Q, t.mom_dip, a, qcorr, s);
+        else far_dipole<kOpA>(t, Q, t.mom_dip, a, qcorr, s);
+    }
     a.sval = t.mu_a;
     a.out = out;
     a.scale = (float)t.scale;
     if (grad) launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
     else launch_gather<kOpA, kEpiStoreW>(t, a, s);
     WNNC_CUDA(cudaStreamSynchronize(s));
+    pool_free(qcorr);
     pool_free(pacc);
     free_target_set(Q);
 }
@@ -1703,6 +1992,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
     // term, so one pass gives A(mu) with G(mu) and one A(r) with G(r), and
     // G(mu + alpha r) = G(mu) + alpha G(r) needs no third pass.
     const bool fused = linear_mom && p.use_grad && p.use_wnnc;
+    const bool dip = t.params.far_order == 1;   // first-order far terms (rep_mode 1)
     for (int it = p.first_iter; it <= last; ++it) {
         const float w = (float)schedule_width(p, it);
         float* st = stats ? stats + 4 * (int64_t)(it - p.first_iter) : nullptr;
@@ -1710,6 +2000,10 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             // s = b - A mu, with G(mu)
             moments(t, mu, nullptr, rep_mode, t.mom, s);
             GatherArgs a = base_args(t, S, w, t.part_acc);
+            if (dip) {
+                dipole_moments(t, mu, t.mom, t.mom_dip, s);
+                far_dipole<kOpAG>(t, S, t.mom_dip, a, t.dip_corr, s);
+            }
             a.sval = mu;
             a.s_out = t.s_s;
             a.partial = pE;
@@ -1720,6 +2014,10 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             // |A r|^2, with G(r)
             moments(t, t.r_s, nullptr, rep_mode, t.mom_r, s);
             GatherArgs b = base_args(t, S, w, t.part_acc);
+            if (dip) {
+                dipole_moments(t, t.r_s, t.mom_r, t.mom_dip_r, s);
+                far_dipole<kOpAG>(t, S, t.mom_dip_r, b, t.dip_corr, s);
+            }
             b.nmom = t.mom_r;
             b.sval = t.r_s;
             b.partial = pqq;
@@ -1741,6 +2039,10 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             // s = b - A mu
             moments(t, mu, nullptr, rep_mode, t.mom, s);
             GatherArgs a = base_args(t, S, w, t.part_acc);
+            if (dip) {
+                dipole_moments(t, mu, t.mom, t.mom_dip, s);
+                far_dipole<kOpA>(t, S, t.mom_dip, a, t.dip_corr, s);
+            }
             a.sval = mu;
             a.s_out = t.s_s;
             a.partial = pE;
@@ -1759,8 +2061,13 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             }
             // |A r|^2
             float4* mom_r = linear_mom ? t.mom_r : t.mom;
+            float4* mdip_r = linear_mom ? t.mom_dip_r : t.mom_dip;
             moments(t, t.r_s, nullptr, rep_mode, mom_r, s);
             GatherArgs b = base_args(t, S, w, t.part_acc);
+            if (dip) {
+                dipole_moments(t, t.r_s, mom_r, mdip_r, s);
+                far_dipole<kOpA>(t, S, mdip_r, b, t.dip_corr, s);
+            }
             b.nmom = mom_r;
             b.sval = t.r_s;
             b.partial = pqq;
@@ -1775,6 +2082,11 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
                 if (linear_mom && p.use_wnnc) {
                     k_node_axpy<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.mom, t.mom_r, t.scalars, t.nnodes);
                     WNNC_LAUNCH_CHECK();
+                    if (dip) {
+                        k_axpy4<<<ceil_div(2 * (int64_t)t.nnodes, kTB), kTB, 0, s>>>(t.mom_dip, t.mom_dip_r,
+                                                                                  t.scalars, 2 * (int64_t)t.nnodes);
+                        WNNC_LAUNCH_CHECK();
+                    }
                 }
             }
             std::swap(mu, mu_alt);
@@ -1783,8 +2095,12 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             WNNC_LAUNCH_CHECK();
         }
         if (p.use_wnnc) {
-            if (!(linear_mom && p.use_grad)) moments(t, mu, nullptr, rep_mode, t.mom, s);
+            if (!(linear_mom && p.use_grad)) {
+                moments(t, mu, nullptr, rep_mode, t.mom, s);
+                if (dip) dipole_moments(t, mu, t.mom, t.mom_dip, s);
+            }
             GatherArgs g = base_args(t, S, w, t.part_acc);
+            if (dip) far_dipole<kOpG>(t, S, t.mom_dip, g, t.dip_corr, s);
             g.sval = mu;
             g.mu_cur = mu;
             g.mu_out = mu_alt;

@@ -1522,6 +1522,8 @@ void free_tree(Tree& t) {
     dfree(t.mu_a); dfree(t.mu_b); dfree(t.r_s); dfree(t.g_mu); dfree(t.g_r); dfree(t.s_s); dfree(t.area_s); dfree(t.mom);
     dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.mom_top); dfree(t.mom_top_rng); dfree(t.mom_front); dfree(t.node_rep); dfree(t.contrib);
     dfree(t.near_contrib); dfree(t.vnode); dfree(t.red_ticket);
+    dfree(t.mom_dip); dfree(t.mom_dip_r); dfree(t.dip_corr); dfree(t.contrib_h0); dfree(t.contrib_h1);
+    dfree(t.hnode0); dfree(t.hnode1);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
 

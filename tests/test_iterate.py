@@ -258,6 +258,26 @@ def test_gpu_paper_exact_iteration_matches_oracle():
 
 
 @pytest.mark.gpu
+def test_gpu_first_order_far_field_iteration_matches_oracle():
+    """The fused iteration with the first-order far field (far_order 1,
+    theta = 0.8) on the 50,000-point union against the oracle's iteration on
+    its first-order treecode, 40 iterations; and the first two iterations of
+    the unfused path (the WNNC update switched off) against the oracle's."""
+    W = _gpu()
+    c = synth.config_cloud("union50k")
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.8, far_order=1)
+    mg, sg = t.iterate(n_iter=40, stats=True)
+    mo, so = oracle.iterate(c.points, n_iter=40, theta=f32(0.8), far_order=1)
+    assert np.allclose(sg.cpu().numpy()[:3, 1:], so[:3, 1:], rtol=1e-3)
+    cos, dlen = _compare_fields(mg.cpu().numpy().astype(np.float64), mo, min_sign=0.995, min_cos=0.995)
+    print(f"[iterate-first-order] sign agreement {np.mean(cos > 0):.5f}, median cos {np.median(cos):.6f}")
+    mg, sg = t.iterate(n_iter=6, w1=0.02, w2=0.02, use_wnnc=False, stats=True)
+    mo, so = oracle.iterate(c.points, n_iter=6, w1=0.02, w2=0.02, use_wnnc=False, theta=f32(0.8), far_order=1)
+    assert np.allclose(sg.cpu().numpy()[:, 1:], so[:, 1:], rtol=1e-3)
+    t.sync_status()
+
+
+@pytest.mark.gpu
 def test_gpu_paper_mode_iteration_matches_oracle():
     """rep_mode 0 (the paper's |nu|-weighted representatives and the
     s-representative A^T) through the whole iteration."""
