@@ -440,6 +440,167 @@ __global__ void __launch_bounds__(32 * kTcWarps) k_mlp_fwd_tc(const float* x, co
     }
 }
 
+// ---------------------------------------------------------------------------
+// Backward on the tensor cores.
+// ---------------------------------------------------------------------------
+// B fragments of dX = dY W (W [N][K] row-major; the mma reduces over n and
+// its columns are k): tile (kt over N/16, padded; nt over K/8), lane 4g + t,
+// register r: W[16kt + 2t + 8r][8nt + g] and W[16kt + 2t + 8r + 1][8nt + g],
+// BF16-rounded, zero for n >= N.
+__device__ void fill_tiles_t(uint32_t* dst, const float* W, int K, int N, int kt_count) {
+    const int nt_count = K / 8;
+    const int ntiles = kt_count * nt_count;
+    for (int e = threadIdx.x; e < ntiles * kTileWords; e += blockDim.x) {
+        const int tile = e / kTileWords, word = e % kTileWords;
+        const int kt = tile / nt_count, nt = tile % nt_count;
+        const int lane = word >> 1, r = word & 1;
+        const int n = 16 * kt + 2 * (lane & 3) + 8 * r, k = 8 * nt + (lane >> 2);
+        const float a = n < N ? W[(int64_t)n * K + k] : 0.f;
+        const float b = n + 1 < N ? W[(int64_t)(n + 1) * K + k] : 0.f;
+        dst[e] = bf16x2_bits(__floats2bfloat162_rn(a, b));
+    }
+}
+
+constexpr int kBwT3 = 1 * kNt;                  // dY (3 columns, padded to 16) times W4: 1 x 16 tiles
+constexpr int kBwOffT3 = 0, kBwOffT2 = kBwT3, kBwOffT1 = kBwT3 + kL2Tiles;
+constexpr int kBwTiles = kBwT3 + 2 * kL2Tiles;  // 272 tiles = 69,632 bytes
+constexpr size_t kBwSmem = sizeof(uint32_t) * kBwTiles * kTileWords;
+
+// ReLU mask of a layer's accumulators from its stored activations, the
+// store of the gradient with respect to the pre-activations, and the next
+// (earlier) layer's A fragments, as in tc_activate.
+__device__ __forceinline__ void tc_relu_grad(float (&acc)[kNt][4], const float* h, float* dstore, int64_t r0,
+                                             int64_t B, int lane, uint32_t (&ahi)[8][4], uint32_t (&alo)[8][4]) {
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ra = r0 + g, rb = ra + 8;
+#pragma unroll
+    for (int nt = 0; nt < kNt; ++nt) {
+        const int col = 8 * nt + 2 * t;
+        const float2 ha = ra < B ? *reinterpret_cast<const float2*>(h + ra * kHid + col) : make_float2(0.f, 0.f);
+        const float2 hb = rb < B ? *reinterpret_cast<const float2*>(h + rb * kHid + col) : make_float2(0.f, 0.f);
+        acc[nt][0] = ha.x > 0.f ? acc[nt][0] : 0.f;
+        acc[nt][1] = ha.y > 0.f ? acc[nt][1] : 0.f;
+        acc[nt][2] = hb.x > 0.f ? acc[nt][2] : 0.f;
+        acc[nt][3] = hb.y > 0.f ? acc[nt][3] : 0.f;
+        if (ra < B) *reinterpret_cast<float2*>(dstore + ra * kHid + col) = make_float2(acc[nt][0], acc[nt][1]);
+        if (rb < B) *reinterpret_cast<float2*>(dstore + rb * kHid + col) = make_float2(acc[nt][2], acc[nt][3]);
+    }
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt) {
+        split_bf16x2(acc[2 * kt][0], acc[2 * kt][1], ahi[kt][0], alo[kt][0]);
+        split_bf16x2(acc[2 * kt][2], acc[2 * kt][3], ahi[kt][1], alo[kt][1]);
+        split_bf16x2(acc[2 * kt + 1][0], acc[2 * kt + 1][1], ahi[kt][2], alo[kt][2]);
+        split_bf16x2(acc[2 * kt + 1][2], acc[2 * kt + 1][3], ahi[kt][3], alo[kt][3]);
+    }
+}
+
+// Gradients with respect to the three hidden pre-activations, fused:
+//   d3 = (dout W4) * (h3 > 0),  d2 = (d3 W3) * (h2 > 0),  d1 = (d2 W2) * (h1 > 0)
+// (dout [B][3]; h, d [B][128]).  Persistent blocks as in the forward.
+__global__ void __launch_bounds__(32 * kTcWarps) k_mlp_bwd_data_tc(const float* dout, const float* P, int64_t B,
+                                                                   const float* h1, const float* h2, const float* h3,
+                                                                   float* d1, float* d2, float* d3) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t* tiles = reinterpret_cast<uint32_t*>(smem_raw);
+    fill_tiles_t(tiles + kBwOffT3 * kTileWords, P + kOffW4, kHid, kOut, 1);
+    fill_tiles_t(tiles + kBwOffT2 * kTileWords, P + kOffW3, kHid, kHid, kHid / 16);
+    fill_tiles_t(tiles + kBwOffT1 * kTileWords, P + kOffW2, kHid, kHid, kHid / 16);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ntiles = (B + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * kTcWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTcWarps) {
+        const int64_t r0 = tile * 16, ra = r0 + g, rb = ra + 8;
+        // A fragments of dout: columns 2t, 2t + 1 (< 3), the rest zero
+        float v[4];
+        v[0] = (ra < B && 2 * t < kOut) ? dout[ra * kOut + 2 * t] : 0.f;
+        v[1] = (ra < B && 2 * t + 1 < kOut) ? dout[ra * kOut + 2 * t + 1] : 0.f;
+        v[2] = (rb < B && 2 * t < kOut) ? dout[rb * kOut + 2 * t] : 0.f;
+        v[3] = (rb < B && 2 * t + 1 < kOut) ? dout[rb * kOut + 2 * t + 1] : 0.f;
+        uint32_t ohi[1][4], olo[1][4];
+        split_bf16x2(v[0], v[1], ohi[0][0], olo[0][0]);
+        split_bf16x2(v[2], v[3], ohi[0][1], olo[0][1]);
+        ohi[0][2] = ohi[0][3] = olo[0][2] = olo[0][3] = 0u;   // columns 8..15 of the padded k-tile
+        float acc[kNt][4];
+        uint32_t ahi[8][4], alo[8][4];
+        tc_layer<1>(ohi, olo, tiles + kBwOffT3 * kTileWords, acc, lane);
+        tc_relu_grad(acc, h3, d3, r0, B, lane, ahi, alo);
+        tc_layer<8>(ahi, alo, tiles + kBwOffT2 * kTileWords, acc, lane);
+        tc_relu_grad(acc, h2, d2, r0, B, lane, ahi, alo);
+        tc_layer<8>(ahi, alo, tiles + kBwOffT1 * kTileWords, acc, lane);
+        tc_relu_grad(acc, h1, d1, r0, B, lane, ahi, alo);
+    }
+}
+
+// Weight-gradient partials of one layer over one chunk of kChunk rows:
+//   part[c][woff + n K + k] = sum_{b in chunk c} dY[b][n] X[b][k],
+//   part[c][boff + n]       = sum_{b in chunk c} dY[b][n]
+// on the tensor cores: the mma's rows are n (16 per warp), its columns k and
+// its reduction the chunk's rows; both factors are FP32 activations and enter
+// as BF16 hi + lo pairs (three products: hi hi, hi lo, lo hi).  The chunk's
+// rows are staged 16 at a time in shared memory.  Block = kTcWarps warps,
+// warp w takes rows n = 16w .. 16w + 15 (warps past N idle).
+constexpr int kWgPad = 4;
+__global__ void __launch_bounds__(32 * kTcWarps) k_mlp_bwd_weight_tc(const float* dY, const float* X, int64_t B,
+                                                                     int K, int N, float* part, int woff, int boff) {
+    __shared__ float ds[16][kHid + kWgPad];
+    __shared__ float xs[16][kHid + kWgPad];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t b0 = (int64_t)blockIdx.x * kChunk, b1 = min(B, b0 + kChunk);
+    const int n0 = 16 * warp;
+    const int ntk = K / 8;                 // column tiles of this layer (6 or 16)
+    float acc[kNt][4];
+#pragma unroll
+    for (int nt = 0; nt < kNt; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    float bsum = 0.f;                      // lanes 0..15: the bias gradient of row n0 + lane
+    for (int64_t bb = b0; bb < b1; bb += 16) {
+        for (int e = threadIdx.x; e < 16 * kHid; e += blockDim.x) {
+            const int q = e / kHid, c = e % kHid;
+            const int64_t row = bb + q;
+            ds[q][c] = (row < b1 && c < N) ? dY[row * N + c] : 0.f;
+            xs[q][c] = (row < b1 && c < K) ? X[row * K + c] : 0.f;
+        }
+        __syncthreads();
+        if (n0 < N) {
+            if (lane < 16) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) bsum += ds[q][n0 + lane];
+            }
+            // A: rows n0 + g (+8), reduction columns 2t, 2t + 1 (+8) = batch rows of the step
+            uint32_t ahi[4], alo[4];
+            split_bf16x2(ds[2 * t][n0 + g], ds[2 * t + 1][n0 + g], ahi[0], alo[0]);
+            split_bf16x2(ds[2 * t][n0 + g + 8], ds[2 * t + 1][n0 + g + 8], ahi[1], alo[1]);
+            split_bf16x2(ds[2 * t + 8][n0 + g], ds[2 * t + 9][n0 + g], ahi[2], alo[2]);
+            split_bf16x2(ds[2 * t + 8][n0 + g + 8], ds[2 * t + 9][n0 + g + 8], ahi[3], alo[3]);
+#pragma unroll
+            for (int nt = 0; nt < kNt; ++nt) {
+                if (nt < ntk) {
+                    const int k = 8 * nt + g;
+                    uint32_t bhi0, blo0, bhi1, blo1;
+                    split_bf16x2(xs[2 * t][k], xs[2 * t + 1][k], bhi0, blo0);
+                    split_bf16x2(xs[2 * t + 8][k], xs[2 * t + 9][k], bhi1, blo1);
+                    mma_bf16(acc[nt], ahi, bhi0, bhi1);
+                    mma_bf16(acc[nt], ahi, blo0, blo1);
+                    mma_bf16(acc[nt], alo, bhi0, bhi1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (n0 >= N) return;
+    float* Pc = part + (int64_t)blockIdx.x * kParams;
+#pragma unroll
+    for (int nt = 0; nt < kNt; ++nt) {
+        if (nt >= ntk) continue;
+        const int k = 8 * nt + 2 * t;
+        const int na = n0 + g, nb = na + 8;
+        if (na < N) { Pc[woff + na * K + k] = acc[nt][0]; Pc[woff + na * K + k + 1] = acc[nt][1]; }
+        if (nb < N) { Pc[woff + nb * K + k] = acc[nt][2]; Pc[woff + nb * K + k + 1] = acc[nt][3]; }
+    }
+    if (lane < 16 && n0 + lane < N) Pc[boff + n0 + lane] = bsum;
+}
+
 dim3 grid2(int64_t B, int N) { return dim3((unsigned)((B + kT - 1) / kT), (unsigned)((N + kT - 1) / kT)); }
 
 }  // namespace
@@ -508,6 +669,12 @@ void mlp_forward(Mlp& m, const float* x, int64_t B, float* y, cudaStream_t s) {
     forward_tc(m, x, B, y, false, s);
 }
 
+static void k_lin_bwd_weight_tc_launch(const float* dY, const float* X, int64_t B, int K, int N, float* part,
+                                       int woff, int boff, int nch, cudaStream_t s) {
+    k_mlp_bwd_weight_tc<<<nch, 32 * kTcWarps, 0, s>>>(dY, X, B, K, N, part, woff, boff);
+    WNNC_LAUNCH_CHECK();
+}
+
 // Gradient of the mean loss over B <= max_batch rows into m.grad; loss to loss_dev.
 void mlp_grad(Mlp& m, const float* x, const float* label, int64_t B, float* loss_dev, cudaStream_t s) {
     forward_tc(m, x, B, m.out, true, s);
@@ -520,24 +687,38 @@ void mlp_grad(Mlp& m, const float* x, const float* label, int64_t B, float* loss
     }
     const float* P = m.params;
     const int nch = ceil_div(B, kChunk);
-    // output layer
+    // gradients with respect to the hidden pre-activations, fused on the tensor cores
+    WNNC_CUDA(cudaFuncSetAttribute(k_mlp_bwd_data_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwSmem));
+    int dev = 0, sms = 0, per_sm = 0;
+    WNNC_CUDA(cudaGetDevice(&dev));
+    WNNC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WNNC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_bwd_data_tc, 32 * kTcWarps, kBwSmem));
+    const int64_t rtiles = (B + 15) / 16;
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, (rtiles + kTcWarps - 1) / kTcWarps));
+    k_mlp_bwd_data_tc<<<grid, 32 * kTcWarps, kBwSmem, s>>>(m.dout, P, B, m.h1, m.h2, m.h3, m.d1, m.d2, m.d3);
+    WNNC_LAUNCH_CHECK();
+    // weight gradients per chunk of rows, on the tensor cores
+    k_lin_bwd_weight_tc_launch(m.dout, m.h3, B, kHid, kOut, m.part, kOffW4, kOffB4, nch, s);
+    k_lin_bwd_weight_tc_launch(m.d3, m.h2, B, kHid, kHid, m.part, kOffW3, kOffB3, nch, s);
+    k_lin_bwd_weight_tc_launch(m.d2, m.h1, B, kHid, kHid, m.part, kOffW2, kOffB2, nch, s);
+    k_lin_bwd_weight_tc_launch(m.d1, x, B, kIn, kHid, m.part, kOffW1, kOffB1, nch, s);
+    k_sum_partials<<<ceil_div(kParams, 256), 256, 0, s>>>(m.part, nch, m.grad);
+    WNNC_LAUNCH_CHECK();
+}
+
+// The FP32 SIMT backward of B <= max_batch rows (kept for comparison with the
+// tensor-core path; not used by the entry points).
+[[maybe_unused]] static void backward_simt(Mlp& m, const float* x, int64_t B, cudaStream_t s) {
+    const float* P = m.params;
+    const int nch = ceil_div(B, kChunk);
     k_lin_bwd_weight<<<dim3(1, 2, nch), 256, 0, s>>>(m.dout, m.h3, B, kHid, kOut, m.part, kOffW4, kOffB4);
-    WNNC_LAUNCH_CHECK();
     k_lin_bwd_data<<<grid2(B, kHid), 256, 0, s>>>(m.dout, P + kOffW4, m.h3, m.d3, B, kHid, kOut);
-    WNNC_LAUNCH_CHECK();
-    // hidden 3
     k_lin_bwd_weight<<<dim3(2, 2, nch), 256, 0, s>>>(m.d3, m.h2, B, kHid, kHid, m.part, kOffW3, kOffB3);
-    WNNC_LAUNCH_CHECK();
     k_lin_bwd_data<<<grid2(B, kHid), 256, 0, s>>>(m.d3, P + kOffW3, m.h2, m.d2, B, kHid, kHid);
-    WNNC_LAUNCH_CHECK();
-    // hidden 2
     k_lin_bwd_weight<<<dim3(2, 2, nch), 256, 0, s>>>(m.d2, m.h1, B, kHid, kHid, m.part, kOffW2, kOffB2);
-    WNNC_LAUNCH_CHECK();
     k_lin_bwd_data<<<grid2(B, kHid), 256, 0, s>>>(m.d2, P + kOffW2, m.h1, m.d1, B, kHid, kHid);
-    WNNC_LAUNCH_CHECK();
-    // hidden 1 (input layer weights)
     k_lin_bwd_weight<<<dim3(2, 1, nch), 256, 0, s>>>(m.d1, x, B, kIn, kHid, m.part, kOffW1, kOffB1);
-    WNNC_LAUNCH_CHECK();
     k_sum_partials<<<ceil_div(kParams, 256), 256, 0, s>>>(m.part, nch, m.grad);
     WNNC_LAUNCH_CHECK();
 }

@@ -148,6 +148,18 @@ def test_mlp_forward_and_gradient_match_fp64_reference(mode):
         rep[name] = (np.linalg.norm(a - b) / np.linalg.norm(b), np.max(np.abs(a - b) / (s_ + 1e-30)))
         o += k
     print("gradient errors (rel L2, max |err|/sum|term|):", rep)
+    X, Y = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    for _ in range(3):
+        m.grad(X, Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        m.grad(X, Y)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"[mlp] gradient of {len(x)} rows (forward, loss, backward data and weights): "
+          f"{e0.elapsed_time(e1) / 10:.3f} ms")
     for name, (rel, scaled) in rep.items():
         assert rel <= 1e-4 or scaled <= 1e-5, (name, rel, scaled)
 
