@@ -55,7 +55,7 @@ FLOPS_ITER = 2 * FLOPS_AG + FLOPS_AT               # A+G(mu), A^T(s), A+G(r) per
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
 # DRAM bytes (read + write) of one launch of the fused A+G kernel on union500k, from ncu
 # (one ncu capture of that kernel on this workload); None once the kernel has changed.
-AG_TRAFFIC_BYTES = 107.133440e6 + 6.868736e6
+AG_TRAFFIC_BYTES = 107.010304e6 + 7.056640e6
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
