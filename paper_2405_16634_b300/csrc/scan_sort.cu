@@ -105,44 +105,53 @@ void exclusive_scan_impl(const T* in, T* out, int64_t n, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Radix sort: 8-bit digits, tiles of 2048 keys (8 warps x 8 rounds x 32 lanes).
-// Ranks inside a tile are stable: warps in order, rounds in order, and lanes
-// in order within a round (peers found with match_any).
+// Radix sort: RB-bit digits (8 or 9: a sort of b key bits takes the digit width
+// that needs the fewest passes), tiles of 2048 keys (8 warps x 8 rounds x 32
+// lanes).  Ranks inside a tile are stable: warps in order, rounds in order,
+// and lanes in order within a round (peers found with match_any).
 // ---------------------------------------------------------------------------
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsRounds = 8;
 constexpr int kRsTile = kRsThreads * kRsRounds;
 
+template <int RB>
 __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, int* hist, int nblocks) {
-    __shared__ int h[256];
-    h[threadIdx.x] = 0;
+    constexpr int kB = 1 << RB;
+    constexpr unsigned kMask = kB - 1u;
+    __shared__ int h[kB];
+    for (int d = threadIdx.x; d < kB; d += kRsThreads) h[d] = 0;
     __syncthreads();
     int64_t t0 = (int64_t)blockIdx.x * kRsTile;
     for (int k = threadIdx.x; k < kRsTile; k += kRsThreads) {
         int64_t i = t0 + k;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & kMask], 1);
     }
     __syncthreads();
-    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    for (int d = threadIdx.x; d < kB; d += kRsThreads) hist[d * nblocks + blockIdx.x] = h[d];
 }
 
 // Scatter of one tile: the keys are ranked stably by digit into shared memory
 // (warps in order, rounds in order, lanes in order within a round), then
 // written out in that order, so that each digit's keys go to consecutive
 // global positions (coalesced runs instead of 32 scattered stores a warp).
+// wcnt holds each warp's digit counts, then (in place) each warp's first
+// tile position per digit.
+template <int RB>
 __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, const uint32_t* vin,
                                                            uint64_t* kout, uint32_t* vout, int64_t n,
                                                            int shift, const int* offs, int nblocks) {
-    __shared__ int whist[kRsWarps][256];
-    __shared__ int wbase[kRsWarps][256];
-    __shared__ int gbase[256];
+    constexpr int kB = 1 << RB;
+    constexpr int kPer = kB / kRsThreads;     // digits per thread in the tile scan (1 or 2)
+    constexpr unsigned kMask = kB - 1u;
+    __shared__ int wcnt[kRsWarps][kB];
+    __shared__ int gbase[kB];
     __shared__ int wsum[kRsWarps];
     __shared__ uint64_t skey[kRsTile];
     __shared__ uint32_t sval[kRsTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&whist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kRsWarps * kB; i += kRsThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const int64_t t0 = (int64_t)blockIdx.x * kRsTile;
     const int tcount = (int)(n - t0 < (int64_t)kRsTile ? n - t0 : (int64_t)kRsTile);
@@ -152,19 +161,26 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, 
         bool valid = i < n;
         unsigned vmask = __ballot_sync(0xffffffffu, valid);
         if (valid) {
-            unsigned d = (unsigned)((kin[i] >> shift) & 255u);
+            unsigned d = (unsigned)((kin[i] >> shift) & kMask);
             unsigned peers = __match_any_sync(vmask, d);
-            if (lane == __ffs(peers) - 1) whist[warp][d] += __popc(peers);
+            if (lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
         }
         __syncwarp();
     }
     __syncthreads();
     {
-        // tile-local start of each digit: exclusive scan over the 256 digits
-        const int d = threadIdx.x;   // 256 threads, one digit each
-        int tot = 0;
-        for (int w = 0; w < kRsWarps; ++w) tot += whist[w][d];
-        int x = tot;
+        // tile-local start of each digit: thread j takes digits kPer j .. kPer j + kPer - 1,
+        // an exclusive scan over the threads gives their starts
+        int tot[kPer];
+        int mine = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int d = kPer * threadIdx.x + q;
+            tot[q] = 0;
+            for (int w = 0; w < kRsWarps; ++w) tot[q] += wcnt[w][d];
+            mine += tot[q];
+        }
+        int x = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, x, o);
@@ -174,12 +190,18 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, 
         __syncthreads();
         int before = 0;
         for (int w = 0; w < warp; ++w) before += wsum[w];
-        const int ds = before + x - tot;
-        gbase[d] = offs[d * nblocks + blockIdx.x] - ds;
-        int run = ds;
-        for (int w = 0; w < kRsWarps; ++w) {
-            wbase[w][d] = run;
-            run += whist[w][d];
+        int ds = before + x - mine;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int d = kPer * threadIdx.x + q;
+            gbase[d] = offs[d * nblocks + blockIdx.x] - ds;
+            int run = ds;
+            for (int w = 0; w < kRsWarps; ++w) {
+                const int c = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += c;
+            }
+            ds += tot[q];
         }
     }
     __syncthreads();
@@ -189,21 +211,21 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, 
         unsigned vmask = __ballot_sync(0xffffffffu, valid);
         if (valid) {
             uint64_t key = kin[i];
-            unsigned d = (unsigned)((key >> shift) & 255u);
+            unsigned d = (unsigned)((key >> shift) & kMask);
             unsigned peers = __match_any_sync(vmask, d);
-            int base = wbase[warp][d];
+            int base = wcnt[warp][d];
             int pos = base + __popc(peers & lt_mask);
             skey[pos] = key;
             if (vin) sval[pos] = vin[i];
             __syncwarp(vmask);
-            if (lane == __ffs(peers) - 1) wbase[warp][d] = base + __popc(peers);
+            if (lane == __ffs(peers) - 1) wcnt[warp][d] = base + __popc(peers);
         }
         __syncwarp();
     }
     __syncthreads();
     for (int p = threadIdx.x; p < tcount; p += kRsThreads) {
         const uint64_t key = skey[p];
-        const int gpos = gbase[(key >> shift) & 255u] + p;
+        const int gpos = gbase[(key >> shift) & kMask] + p;
         kout[gpos] = key;
         if (vout) vout[gpos] = sval[p];
     }
@@ -239,16 +261,22 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
     int nb = ceil_div(n, kRsTile);
     uint64_t* k2 = dalloc<uint64_t>(n);
     uint32_t* v2 = vals ? dalloc<uint32_t>(n) : nullptr;
-    int* hist = dalloc<int>((size_t)256 * nb + 1);
+    // digit width: 8 bits, or 9 where that saves a pass (e.g. 18 bits: 2 passes, not 3)
+    const int nbits = bits - lo_bit;
+    const int passes8 = (nbits + 7) / 8, passes9 = (nbits + 8) / 9;
+    const int rb = passes9 < passes8 ? 9 : 8;
+    const int passes = rb == 9 ? passes9 : passes8;
+    int* hist = dalloc<int>(((size_t)1 << rb) * nb + 1);
     uint64_t *ka = keys, *kb = k2;
     uint32_t *va = vals, *vb = v2;
-    int passes = (bits - lo_bit + 7) / 8;
     for (int p = 0; p < passes; ++p) {
-        int shift = lo_bit + 8 * p;
-        k_rs_hist<<<nb, kRsThreads, 0, s>>>(ka, n, shift, hist, nb);
+        int shift = lo_bit + rb * p;
+        if (rb == 9) k_rs_hist<9><<<nb, kRsThreads, 0, s>>>(ka, n, shift, hist, nb);
+        else k_rs_hist<8><<<nb, kRsThreads, 0, s>>>(ka, n, shift, hist, nb);
         WNNC_LAUNCH_CHECK();
-        exclusive_scan_i32(hist, hist, (int64_t)256 * nb, s);
-        k_rs_scatter<<<nb, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, nb);
+        exclusive_scan_i32(hist, hist, ((int64_t)1 << rb) * nb, s);
+        if (rb == 9) k_rs_scatter<9><<<nb, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, nb);
+        else k_rs_scatter<8><<<nb, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, nb);
         WNNC_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);
