@@ -107,16 +107,28 @@ def test_gpu_first_iteration_closed_form():
 
 
 @pytest.mark.gpu
-def test_gpu_iteration_union50k_matches_oracle():
-    """Second configuration: 50,000 union points, theta = 0.5, 40 iterations."""
+@pytest.mark.parametrize("theta,init", [(0.5, "zero"), (0.3, "random"), (0.5, "random"), (0.8, "random")])
+def test_gpu_iteration_union50k_matches_oracle(theta, init):
+    """Second configuration: 50,000 union points, 40 iterations at
+    theta = 0.3, 0.5, 0.8, from the configuration's random unit normals (times
+    the mean area) and from zero (the paper's init).  The GPU solve agrees
+    with the oracle's FP64 solve on the same lists, and so does its accuracy
+    against ground truth.  (Sec. 6.1.3: from a random init the method need
+    not find the ground-truth orientation; the agreement is what is tested.)"""
     W = _gpu()
     c = synth.config_cloud("union50k")
-    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5)
-    mg = t.iterate(n_iter=40).cpu().numpy().astype(np.float64)
-    mo, _ = oracle.iterate(c.points, n_iter=40, theta=f32(0.5))
-    _compare_fields(mg, mo, min_sign=0.995, min_cos=0.995)
+    n = len(c.points)
+    mu0 = None if init == "zero" else synth.init_normals(n, 2001, c.area / n)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta)
+    mg = t.iterate(None if mu0 is None else torch.from_numpy(mu0).cuda(), n_iter=40)
+    mg = mg.cpu().numpy().astype(np.float64)
+    mo, _ = oracle.iterate(c.points, mu0=mu0, n_iter=40, theta=f32(theta))
+    cos, _ = _compare_fields(mg, mo, min_sign=0.995, min_cos=0.995)
+    pg, po = oracle.p_co(c.normals, mg), oracle.p_co(c.normals, mo)
+    print(f"[iterate-50k] theta={theta} init={init}: sign agreement {np.mean(cos > 0):.5f}, "
+          f"median cos {np.median(cos):.6f}, P_co gpu {pg:.5f} oracle {po:.5f}")
     # orientation accuracy against ground truth equals the oracle's
-    assert abs(oracle.p_co(c.normals, mg) - oracle.p_co(c.normals, mo)) < 0.005
+    assert abs(pg - po) < 0.005
     assert abs(oracle.ae_pcd(c.normals, mg) - oracle.ae_pcd(c.normals, mo)) < 0.005
 
 
