@@ -859,7 +859,7 @@ struct AdjArgs {
     double* partial;
     const float4* hnode0;     // far_order 1: per node sum of s HPhi, (xx, yy, zz, -)
     const float4* hnode1;     //   and (xy, xz, yz, -)
-    float4* contrib_h0;       // the same per far entry (k_adj_far_h)
+    float4* contrib_h0;       // the same per far entry (k_adj_far_dip)
     float4* contrib_h1;
 };
 
@@ -1036,39 +1036,56 @@ __device__ __forceinline__ void adj_epilogue(const AdjArgs& A, int gs, int64_t j
 // Pairs take the cut-off decision of the node's monopole term (the same r^2,
 // computed in the same order).
 // ---------------------------------------------------------------------------
-// S of every node that is not a top node (at most kMomDirect points, or a
-// leaf), one warp per node over its range: (Sxx, Syy, Szz, Sxy), (Sxz, Syz,
-// tr S, 0) at out[2b], out[2b + 1].
-__global__ void k_mom_dipole(int nnodes, const int* nstart, const int* ncount, const int* nnchild,
+// S of every node that is not a top node, by the size classes of the
+// monopole moments: one thread per node of at most kMomSmall points, one warp
+// per node of the mid list (up to kMomDirect points, or a leaf of any size);
+// blocks [0, grid_m) take the warp class.  Stored as (Sxx, Syy, Szz, Sxy),
+// (Sxz, Syz, tr S, 0) at out[2b], out[2b + 1].
+__device__ __forceinline__ void dip_point(int j, const float4& cb, const float4& cc, const float4* spos,
+                                          const float4* scorig, const float4* nu, float (&m)[6]) {
+    const float4 p = shift(scorig[j >> 5], cb, spos[j]);   // the point relative to the cell centre
+    const float dx = p.x - cc.x, dy = p.y - cc.y, dz = p.z - cc.z;
+    const float4 v = nu[j];
+    m[0] = fmaf(dx, v.x, m[0]);
+    m[1] = fmaf(dy, v.y, m[1]);
+    m[2] = fmaf(dz, v.z, m[2]);
+    m[3] = fmaf(0.5f, fmaf(dx, v.y, dy * v.x), m[3]);
+    m[4] = fmaf(0.5f, fmaf(dx, v.z, dz * v.x), m[4]);
+    m[5] = fmaf(0.5f, fmaf(dy, v.z, dz * v.y), m[5]);
+}
+
+__device__ __forceinline__ void dip_store(int b, const float (&m)[6], float4* out) {
+    out[2 * (int64_t)b] = make_float4(m[0], m[1], m[2], m[3]);
+    out[2 * (int64_t)b + 1] = make_float4(m[4], m[5], m[0] + m[1] + m[2], 0.f);
+}
+
+__global__ void k_mom_dipole(int nnodes, int nmid, int grid_m, const int* mid, const int* nstart, const int* ncount,
                              const float4* ncell, const float4* ncent, const float4* spos, const float4* scorig,
                              const float4* nu, float4* out) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if ((int)blockIdx.x < grid_m) {
+        const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+        const int lane = threadIdx.x & 31;
+        if (k >= nmid) return;
+        const int b = mid[k];
+        const float4 cb = ncell[b], cc = ncent[b];
+        const int j0 = nstart[b], cnt = ncount[b];
+        for (int j = j0 + lane; j < j0 + cnt; j += 32) dip_point(j, cb, cc, spos, scorig, nu, m);
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m[c] += __shfl_xor_sync(0xffffffffu, m[c], o);
+        if (lane == 0) dip_store(b, m, out);
+        return;
+    }
+    const int b = (int)((blockIdx.x - grid_m) * blockDim.x + threadIdx.x);
     if (b >= nnodes) return;
     const int cnt = ncount[b];
-    if (cnt > kMomDirect && nnchild[b] > 0) return;      // top node: from its front (k_mom_dipole_top)
+    if (cnt > kMomSmall) return;                          // warp class or top node
     const float4 cb = ncell[b], cc = ncent[b];
-    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int j0 = nstart[b];
-    for (int j = j0 + lane; j < j0 + cnt; j += 32) {
-        const float4 p = shift(scorig[j >> 5], cb, spos[j]);   // the point relative to the cell centre
-        const float dx = p.x - cc.x, dy = p.y - cc.y, dz = p.z - cc.z;
-        const float4 v = nu[j];
-        m[0] = fmaf(dx, v.x, m[0]);
-        m[1] = fmaf(dy, v.y, m[1]);
-        m[2] = fmaf(dz, v.z, m[2]);
-        m[3] = fmaf(0.5f, fmaf(dx, v.y, dy * v.x), m[3]);
-        m[4] = fmaf(0.5f, fmaf(dx, v.z, dz * v.x), m[4]);
-        m[5] = fmaf(0.5f, fmaf(dy, v.z, dz * v.y), m[5]);
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m[c] += __shfl_xor_sync(0xffffffffu, m[c], o);
-    if (lane == 0) {
-        out[2 * (int64_t)b] = make_float4(m[0], m[1], m[2], m[3]);
-        out[2 * (int64_t)b + 1] = make_float4(m[4], m[5], m[0] + m[1] + m[2], 0.f);
-    }
+    for (int j = j0; j < j0 + cnt; ++j) dip_point(j, cb, cc, spos, scorig, nu, m);
+    dip_store(b, m, out);
 }
 
 // S of the top nodes from their fronts (the non-top nodes under a top node
@@ -1108,29 +1125,34 @@ __global__ void k_mom_dipole_top(int ntop, const int* top, const int2* top_rng, 
     }
 }
 
-// The first-order far terms of every target: one warp per target group, one
-// target per lane; the group's far nodes (centroid in the group's frame, S)
-// staged 32 at a time in shared memory.  OP kOpA: A's term in .w; kOpG: G's
-// in .xyz; kOpAG: both.
+// The first-order far terms of every target: one warp per work item of the
+// gather (a slice of one target group's far entries; the items are cut and
+// ordered heaviest first, so the groups with the longest lists do not set the
+// kernel's time), one target per lane; the item's far nodes (centroid in the
+// group's frame, S) staged 32 at a time in shared memory.  OP kOpA: A's term
+// in .w; kOpG: G's in .xyz; kOpAG: both.  A group cut into several items
+// writes one part per item into `parts` (every lane), and
+// k_far_dip_finalize adds the parts in order.
 template <int OP>
-__global__ void __launch_bounds__(32 * kGatherWarps) k_far_dip(GatherArgs A, const int* far_off,
-                                                               const float4* mdip, float4* corr) {
+__global__ void __launch_bounds__(32 * kGatherWarps) k_far_dip(GatherArgs A, const float4* mdip, float4* corr,
+                                                               float4* parts) {
     __shared__ float4 sp_all[kGatherWarps][32], s0_all[kGatherWarps][32], s1_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.x * kGatherWarps + wl;
-    if (g >= A.ngroups) return;
+    const int it = blockIdx.x * kGatherWarps + wl;
+    if (it >= A.nitems) return;
     float4* sp = sp_all[wl];
     float4* s0 = s0_all[wl];
     float4* s1 = s1_all[wl];
+    const Item item = A.items[it];
+    const int g = item.g;
     const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
     const int64_t i = (int64_t)i0 + lane;
     const bool valid = lane < cnt_t;
     const float4 o = A.tgorig[g];
     const float4 t = valid ? shift(A.tcorig[i >> 5], o, A.tpos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
     float cx = 0.f, cy = 0.f, cz = 0.f, ca = 0.f;
-    const int f0 = far_off[g], f1 = far_off[g + 1];
-    for (int base = f0; base < f1; base += 32) {
-        const int cnt = min(32, f1 - base);
+    for (int base = item.f0; base < item.f1; base += 32) {
+        const int cnt = min(32, item.f1 - base);
         if (lane < cnt) {
             const int b = A.far_id[base + lane];
             sp[lane] = shift(A.ncell[b], o, A.nrep[b]);
@@ -1139,6 +1161,7 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_far_dip(GatherArgs A, con
         }
         __syncwarp();
         if (valid) {
+#pragma unroll 4
             for (int k = 0; k < cnt; ++k) {
                 const float4 p = sp[k];
                 const float dx = p.x - t.x, dy = p.y - t.y, dz = p.z - t.z;
@@ -1163,14 +1186,35 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_far_dip(GatherArgs A, con
         }
         __syncwarp();
     }
-    if (valid) corr[i] = make_float4(cx, cy, cz, ca);
+    if (item.pslot < 0) {
+        if (valid) corr[i] = make_float4(cx, cy, cz, ca);
+    } else {
+        parts[(int64_t)item.pslot * 32 + lane] = make_float4(cx, cy, cz, ca);
+    }
 }
 
-// H per far entry for the transpose of the first-order terms: one warp per
-// work item of the far adjoint (a slice of one group's far entries), the
-// group's targets (point, s) staged once; lane e of a batch sums, over the
-// targets, s_i (3 d d^T - r^2 I) / r^5 with d = x_B - x_i.
-__global__ void WNNC_ADJ_BOUNDS k_adj_far_h(AdjArgs A) {
+// Groups cut into several items: the parts of k_far_dip added in order.
+__global__ void k_far_dip_finalize(GatherArgs A, const float4* parts, float4* corr) {
+    const int sidx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sidx >= A.nsplit) return;
+    const int4 sp = A.splits[sidx];
+    const int g = sp.x;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int p = 0; p < sp.z; ++p) {
+        const float4 v = parts[(int64_t)(sp.y + p) * 32 + lane];
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    const int i0 = A.goff[g];
+    if (lane < A.goff[g + 1] - i0) corr[(int64_t)i0 + lane] = acc;
+}
+
+// far_order 1: the far adjoint with the transpose of the first-order terms.
+// k_adj_far's layout (one warp per work item, the group's targets staged once,
+// two entries per lane in the halves of float2, paired FP32 instructions),
+// summing per entry both V = sum s_i d / r^3 and H = sum s_i (3 d d^T - r^2 I) / r^5
+// (d = x_B - x_i), with the same cut-off decisions as k_adj_far.
+__global__ void __launch_bounds__(32 * kGatherWarps) k_adj_far_dip(AdjArgs A) {
     __shared__ float4 tp_all[kGatherWarps][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it = blockIdx.x * kGatherWarps + wl;
@@ -1183,32 +1227,95 @@ __global__ void WNNC_ADJ_BOUNDS k_adj_far_h(AdjArgs A) {
     const float4 o = A.gorig[g];
     float4 p = lane < cnt_t ? shift(A.corig[i >> 5], o, A.pos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
     p.w = lane < cnt_t ? A.sv[i] : 0.f;
-    tp[lane] = make_float4(-p.x, -p.y, -p.z, p.w);   // negated, as in the monopole's far adjoint
+    tp[lane] = make_float4(-p.x, -p.y, -p.z, p.w);   // negated: the paired terms add them
     __syncwarp();
-    for (int base = item.f0; base < item.f1; base += 32) {
-        const int e = base + lane;
-        if (e >= item.f1) continue;
-        const int b = A.far_id[e];
-        const float4 bp = shift(A.ncell[b], o, A.ncent[b]);
-        float h[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int base = item.f0; base < item.f1; base += 64) {
+        const int e0 = base + lane, e1 = e0 + 32;
+        const bool v0 = e0 < item.f1, v1 = e1 < item.f1;
+        float4 bp0 = make_float4(0.f, 0.f, 0.f, 0.f), bp1 = bp0;
+        if (v0) { const int b = A.far_id[e0]; bp0 = shift(A.ncell[b], o, A.ncent[b]); }
+        if (v1) { const int b = A.far_id[e1]; bp1 = shift(A.ncell[b], o, A.ncent[b]); }
+        const float2 px = make_float2(bp0.x, bp1.x), py = make_float2(bp0.y, bp1.y), pz = make_float2(bp0.z, bp1.z);
+        float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+        float2 hxx = ax, hyy = ax, hzz = ax, hxy = ax, hxz = ax, hyz = ax;
+#pragma unroll 4
         for (int k = 0; k < cnt_t; ++k) {
             const float4 tk = tp[k];
-            const float dx = bp.x + tk.x, dy = bp.y + tk.y, dz = bp.z + tk.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (!(r2 >= A.w2)) continue;
-            const float ir = rsqrtf(r2);
-            const float ir2 = ir * ir;
-            const float q = tk.w * (ir2 * ir2 * ir);
-            const float q3 = 3.f * q;
-            h[0] = fmaf(q, fmaf(3.f * dx, dx, -r2), h[0]);
-            h[1] = fmaf(q, fmaf(3.f * dy, dy, -r2), h[1]);
-            h[2] = fmaf(q, fmaf(3.f * dz, dz, -r2), h[2]);
-            h[3] = fmaf(q3, dx * dy, h[3]);
-            h[4] = fmaf(q3, dx * dz, h[4]);
-            h[5] = fmaf(q3, dy * dz, h[5]);
+            // the pair of adj_term2 (same operations and order, so the same cut-off decisions)
+            const float2 dx = __fadd2_rn(px, make_float2(tk.x, tk.x));
+            const float2 dy = __fadd2_rn(py, make_float2(tk.y, tk.y));
+            const float2 dz = __fadd2_rn(pz, make_float2(tk.z, tk.z));
+            float2 r2 = __fmul2_rn(dz, dz);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dx, dx, r2);
+            float2 ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            ir.x = (r2.x >= A.w2) ? ir.x : 0.f;
+            ir.y = (r2.y >= A.w2) ? ir.y : 0.f;
+            const float2 ir2 = __fmul2_rn(ir, ir);
+            const float2 q = __fmul2_rn(make_float2(tk.w, tk.w), __fmul2_rn(ir2, ir));   // s / r^3
+            ax = __ffma2_rn(q, dx, ax);
+            ay = __ffma2_rn(q, dy, ay);
+            az = __ffma2_rn(q, dz, az);
+            // s (3 d d^T - r^2 I) / r^5 = (3 q / r^2) d d^T - q I
+            const float2 q3 = __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), q), ir2);
+            const float2 nq = __fmul2_rn(make_float2(-1.f, -1.f), q);
+            const float2 q3x = __fmul2_rn(q3, dx), q3y = __fmul2_rn(q3, dy);
+            hxx = __ffma2_rn(q3x, dx, __fadd2_rn(hxx, nq));
+            hyy = __ffma2_rn(q3y, dy, __fadd2_rn(hyy, nq));
+            hzz = __ffma2_rn(__fmul2_rn(q3, dz), dz, __fadd2_rn(hzz, nq));
+            hxy = __ffma2_rn(q3x, dy, hxy);
+            hxz = __ffma2_rn(q3x, dz, hxz);
+            hyz = __ffma2_rn(q3y, dz, hyz);
         }
-        A.contrib_h0[e] = make_float4(h[0], h[1], h[2], 0.f);   // k_adj_node sums x, y, z
-        A.contrib_h1[e] = make_float4(h[3], h[4], h[5], 0.f);
+        if (v0) {
+            A.contrib[e0] = make_float4(ax.x, ay.x, az.x, 0.f);
+            A.contrib_h0[e0] = make_float4(hxx.x, hyy.x, hzz.x, 0.f);
+            A.contrib_h1[e0] = make_float4(hxy.x, hxz.x, hyz.x, 0.f);
+        }
+        if (v1) {
+            A.contrib[e1] = make_float4(ax.y, ay.y, az.y, 0.f);
+            A.contrib_h0[e1] = make_float4(hxx.y, hyy.y, hzz.y, 0.f);
+            A.contrib_h1[e1] = make_float4(hxy.y, hxz.y, hyz.y, 0.f);
+        }
+    }
+}
+
+// far_order 1: the node gather of k_adj_node for the three per-entry sums
+// (V, and H in two parts) at once, sharing the entry-id reads.
+__global__ void k_adj_node3(int nnodes, const int* tfar_off, const int* tfar_ent, const float4* c0,
+                            const float4* c1, const float4* c2, float4* v0, float4* v1, float4* v2) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nnodes) return;
+    float a[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int q1 = tfar_off[b + 1];
+    for (int q = tfar_off[b] + lane; q < q1; q += 32 * 4) {
+        int e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = q + 32 * u < q1 ? tfar_ent[q + 32 * u] : -1;
+        float4 x[4], y[4], z[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            x[u] = e[u] >= 0 ? c0[e[u]] : zero;
+            y[u] = e[u] >= 0 ? c1[e[u]] : zero;
+            z[u] = e[u] >= 0 ? c2[e[u]] : zero;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[0] += x[u].x; a[1] += x[u].y; a[2] += x[u].z;
+            a[3] += y[u].x; a[4] += y[u].y; a[5] += y[u].z;
+            a[6] += z[u].x; a[7] += z[u].y; a[8] += z[u].z;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+    if (lane == 0) {
+        v0[b] = make_float4(a[0], a[1], a[2], 0.f);
+        v1[b] = make_float4(a[3], a[4], a[5], 0.f);
+        v2[b] = make_float4(a[6], a[7], a[8], 0.f);
     }
 }
 
@@ -1759,9 +1866,10 @@ static void perm_in_vec(Tree& t, const float* in, float f, float4* out, cudaStre
 // (mom: the field's monopole moments, already computed).
 static void dipole_moments(Tree& t, const float4* nu, const float4* mom, float4* mdip, cudaStream_t s) {
     ProfScope ps(&t.prof, WNNC_PROF_MOMENTS, s);
-    k_mom_dipole<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(
-        t.nnodes, t.node_start, t.node_count, t.node_nchild, t.node_cell, t.node_cent, t.self.pos, t.self.corig, nu,
-        mdip);
+    const int grid_s = ceil_div(t.nnodes, kTB), grid_m = ceil_div((int64_t)t.nmom_mid * 32, kTB);
+    k_mom_dipole<<<grid_m + grid_s, kTB, 0, s>>>(t.nnodes, t.nmom_mid, grid_m, t.mom_mid, t.node_start,
+                                                  t.node_count, t.node_cell, t.node_cent, t.self.pos, t.self.corig,
+                                                  nu, mdip);
     WNNC_LAUNCH_CHECK();
     if (t.nmom_top > 0) {
         k_mom_dipole_top<<<ceil_div((int64_t)t.nmom_top * 32, kTB), kTB, 0, s>>>(
@@ -1774,11 +1882,15 @@ static void dipole_moments(Tree& t, const float4* nu, const float4* mom, float4*
 // into corr, and the gather arguments a told to add them.
 template <int OP>
 static void far_dipole(Tree& t, const TargetSet& ts, const float4* mdip, GatherArgs& a, float4* corr,
-                       cudaStream_t s) {
+                       float4* parts, cudaStream_t s) {
     ProfScope ps(&t.prof, OP == kOpAG ? WNNC_PROF_AG : (OP == kOpG ? WNNC_PROF_G : WNNC_PROF_A), s);
-    if (ts.ngroups > 0) {
-        k_far_dip<OP><<<ceil_div(ts.ngroups, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a, ts.far_off, mdip, corr);
+    if (a.nitems > 0) {
+        k_far_dip<OP><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a, mdip, corr, parts);
         WNNC_LAUNCH_CHECK();
+        if (a.nsplit > 0) {
+            k_far_dip_finalize<<<ceil_div((int64_t)a.nsplit * 32, kTB), kTB, 0, s>>>(a, parts, corr);
+            WNNC_LAUNCH_CHECK();
+        }
     }
     a.dip_corr = corr;
 }
@@ -1791,7 +1903,7 @@ void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     GatherArgs a = base_args(t, t.self, w, t.part_acc);
     if (t.params.far_order == 1) {
         dipole_moments(t, t.mu_a, t.mom, t.mom_dip, s);
-        far_dipole<kOpA>(t, t.self, t.mom_dip, a, t.dip_corr, s);
+        far_dipole<kOpA>(t, t.self, t.mom_dip, a, t.dip_corr, t.part_acc, s);
     }
     a.sval = t.mu_a;
     a.out = out;
@@ -1805,7 +1917,7 @@ void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     GatherArgs a = base_args(t, t.self, w, t.part_acc);
     if (t.params.far_order == 1) {
         dipole_moments(t, t.mu_a, t.mom, t.mom_dip, s);
-        far_dipole<kOpG>(t, t.self, t.mom_dip, a, t.dip_corr, s);
+        far_dipole<kOpG>(t, t.self, t.mom_dip, a, t.dip_corr, t.part_acc, s);
     }
     a.sval = t.mu_a;
     a.out = out;
@@ -1820,37 +1932,34 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
     AdjArgs a = adj_args(t, w);
     a.sv = s_sorted;
     if (t.self.far_entries > 0) {
+        const bool dip = t.params.far_order == 1;
         {
             ProfScope ps(&t.prof, WNNC_PROF_ADJ_FAR, s);
             AdjArgs f = a;
             f.items = t.adj_far_work.items;
             f.nitems = t.adj_far_work.nitems;
-            k_adj_far<<<ceil_div(f.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(f);
+            if (dip) {
+                // with the transpose of the first-order far terms (s HPhi per entry)
+                f.contrib_h0 = t.contrib_h0;
+                f.contrib_h1 = t.contrib_h1;
+                k_adj_far_dip<<<ceil_div(f.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(f);
+            } else {
+                k_adj_far<<<ceil_div(f.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(f);
+            }
             WNNC_LAUNCH_CHECK();
         }
         ProfScope ps(&t.prof, WNNC_PROF_ADJ_NODE, s);
-        k_adj_node<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(t.nnodes, t.tfar_off, t.tfar_ent,
-                                                                         t.contrib, t.vnode);
-        WNNC_LAUNCH_CHECK();
-        if (t.params.far_order == 1) {
-            // the transpose of the first-order far terms: s HPhi per far entry,
-            // summed per node, pushed down in the near kernel's epilogue
-            AdjArgs f = a;
-            f.items = t.adj_far_work.items;
-            f.nitems = t.adj_far_work.nitems;
-            f.contrib_h0 = t.contrib_h0;
-            f.contrib_h1 = t.contrib_h1;
-            k_adj_far_h<<<ceil_div(f.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(f);
-            WNNC_LAUNCH_CHECK();
-            k_adj_node<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(t.nnodes, t.tfar_off, t.tfar_ent,
-                                                                             t.contrib_h0, t.hnode0);
-            WNNC_LAUNCH_CHECK();
-            k_adj_node<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(t.nnodes, t.tfar_off, t.tfar_ent,
-                                                                             t.contrib_h1, t.hnode1);
-            WNNC_LAUNCH_CHECK();
+        if (dip) {
+            // the node sums of V and H, pushed down in the near kernel's epilogue
+            k_adj_node3<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(
+                t.nnodes, t.tfar_off, t.tfar_ent, t.contrib, t.contrib_h0, t.contrib_h1, t.vnode, t.hnode0, t.hnode1);
             a.hnode0 = t.hnode0;
             a.hnode1 = t.hnode1;
+        } else {
+            k_adj_node<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(t.nnodes, t.tfar_off, t.tfar_ent,
+                                                                             t.contrib, t.vnode);
         }
+        WNNC_LAUNCH_CHECK();
     } else {
         WNNC_CUDA(cudaMemsetAsync(t.vnode, 0, sizeof(float4) * t.nnodes, s));
     }
@@ -1933,8 +2042,8 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     if (t.params.far_order == 1) {
         qcorr = dalloc<float4>((size_t)m);
         dipole_moments(t, t.mu_a, t.mom, t.mom_dip, s);
-        if (grad) far_dipole<kOpG>(t, Q, t.mom_dip, a, qcorr, s);
-        else far_dipole<kOpA>(t, Q, t.mom_dip, a, qcorr, s);
+        if (grad) far_dipole<kOpG>(t, Q, t.mom_dip, a, qcorr, pacc, s);
+        else far_dipole<kOpA>(t, Q, t.mom_dip, a, qcorr, pacc, s);
     }
     a.sval = t.mu_a;
     a.out = out;
@@ -2002,7 +2111,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             GatherArgs a = base_args(t, S, w, t.part_acc);
             if (dip) {
                 dipole_moments(t, mu, t.mom, t.mom_dip, s);
-                far_dipole<kOpAG>(t, S, t.mom_dip, a, t.dip_corr, s);
+                far_dipole<kOpAG>(t, S, t.mom_dip, a, t.dip_corr, t.part_acc, s);
             }
             a.sval = mu;
             a.s_out = t.s_s;
@@ -2016,7 +2125,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             GatherArgs b = base_args(t, S, w, t.part_acc);
             if (dip) {
                 dipole_moments(t, t.r_s, t.mom_r, t.mom_dip_r, s);
-                far_dipole<kOpAG>(t, S, t.mom_dip_r, b, t.dip_corr, s);
+                far_dipole<kOpAG>(t, S, t.mom_dip_r, b, t.dip_corr, t.part_acc, s);
             }
             b.nmom = t.mom_r;
             b.sval = t.r_s;
@@ -2041,7 +2150,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             GatherArgs a = base_args(t, S, w, t.part_acc);
             if (dip) {
                 dipole_moments(t, mu, t.mom, t.mom_dip, s);
-                far_dipole<kOpA>(t, S, t.mom_dip, a, t.dip_corr, s);
+                far_dipole<kOpA>(t, S, t.mom_dip, a, t.dip_corr, t.part_acc, s);
             }
             a.sval = mu;
             a.s_out = t.s_s;
@@ -2066,7 +2175,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             GatherArgs b = base_args(t, S, w, t.part_acc);
             if (dip) {
                 dipole_moments(t, t.r_s, mom_r, mdip_r, s);
-                far_dipole<kOpA>(t, S, mdip_r, b, t.dip_corr, s);
+                far_dipole<kOpA>(t, S, mdip_r, b, t.dip_corr, t.part_acc, s);
             }
             b.nmom = mom_r;
             b.sval = t.r_s;
@@ -2100,7 +2209,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
                 if (dip) dipole_moments(t, mu, t.mom, t.mom_dip, s);
             }
             GatherArgs g = base_args(t, S, w, t.part_acc);
-            if (dip) far_dipole<kOpG>(t, S, t.mom_dip, g, t.dip_corr, s);
+            if (dip) far_dipole<kOpG>(t, S, t.mom_dip, g, t.dip_corr, t.part_acc, s);
             g.sval = mu;
             g.mu_cur = mu;
             g.mu_out = mu_alt;
