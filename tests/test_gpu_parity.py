@@ -365,9 +365,9 @@ def test_first_order_far_field_against_direct_sums(union500k_sample, theta):
     grad F and A^T the relative L2 error is below the monopole's at the same
     theta, and at theta = 0.8 the error of A^T is below the monopole's at
     theta = 0.5 (the paper's c = 2).  Printed per result.  A gains less
-    (1.5x at theta = 0.5 against 5.7x for A^T): most of its remaining error
-    comes from far nodes some of whose points lie inside the cut-off radius
-    w of the target, which the node's terms, of any order, count."""
+    (1.5x at theta = 0.5 against 5.7x for A^T): A, about 1/2 on the surface,
+    is a sum of far contributions that largely cancel, and their
+    second-order errors remain."""
     W = _wnnc()
     pts, mu, s, sub, direct_cache = union500k_sample
     w = 0.004
