@@ -313,6 +313,77 @@ def test_per_target_criterion_matches_the_papers_treecode(theta, leaf):
     t.sync_status()
 
 
+@pytest.mark.parametrize("n,leaf,depth", [(2, 1, 15), (33, 1, 15), (500, 1, 15), (3000, 32, 3)])
+def test_modes_on_edge_sizes(n, leaf, depth):
+    """The per-target criterion (criterion 1) and the first-order far field
+    (far_order 1) on ragged and degenerate trees: two points, one ragged
+    group, leaf size 1, a depth-3 tree whose leaves hold hundreds of points;
+    each against the oracle's independent implementation of the same mode."""
+    W = _wnnc()
+    c = synth.union_cloud(max(n, 4), 11, n_tori=1, n_ellipsoids=1)
+    pts = np.ascontiguousarray(c.points[:n])
+    mu = synth.init_normals(n, 3, 1e-3)
+    s = np.random.default_rng(1).standard_normal(n).astype(np.float32)
+    w = 0.01
+    tp = W.Tree(torch.from_numpy(pts).cuda(), theta=0.5, leaf_size=leaf, max_depth=depth, rep_mode=0,
+                criterion=1)
+    for op, nu, call in ((OP_A, mu, tp.eval_w), (OP_G, mu, tp.eval_grad), (OP_AT, s, tp.eval_adjoint)):
+        gpu = call(torch.from_numpy(nu).cuda(), w).cpu().numpy()
+        ora, info = oracle.eval_paper(op, pts, nu, w, 0.5, leaf_size=leaf, max_depth=depth, amb_tol=AMB)
+        check_close(gpu, ora, info, what=f"per-target n={n} leaf={leaf} depth={depth} op={op}")
+    tf = W.Tree(torch.from_numpy(pts).cuda(), theta=0.5, leaf_size=leaf, max_depth=depth, far_order=1)
+    for op, nu, call in ((OP_A, mu, tf.eval_w), (OP_G, mu, tf.eval_grad), (OP_AT, s, tf.eval_adjoint)):
+        gpu = call(torch.from_numpy(nu).cuda(), w).cpu().numpy()
+        ora, b = oracle.eval_op(op, pts, nu, w, theta=0.5, leaf_size=leaf, max_depth=depth, amb_tol=AMB,
+                                far_order=1)
+        check_close(gpu, ora, b, what=f"first-order n={n} leaf={leaf} depth={depth} op={op}")
+    tp.sync_status()
+    tf.sync_status()
+
+
+def test_modes_on_coincident_points_and_large_leaves():
+    """3000 coincident points (a depth-15 leaf of 3000 points, above the
+    1024-point warp class of the moments) next to a small sphere: the
+    per-target criterion and the first-order far field against the oracle
+    (the first-order moments of the top nodes come from their fronts)."""
+    W = _wnnc()
+    sph = synth.fibonacci_sphere(2000, radius=0.2).points + 0.8
+    pts = np.concatenate([np.full((3000, 3), -0.8), sph]).astype(np.float32)
+    n = len(pts)
+    mu = synth.init_normals(n, 3, 1e-3)
+    s = np.random.default_rng(4).standard_normal(n).astype(np.float32)
+    w = 0.01
+    tf = W.Tree(torch.from_numpy(pts).cuda(), theta=0.5, far_order=1)
+    for op, nu, call in ((OP_A, mu, tf.eval_w), (OP_G, mu, tf.eval_grad), (OP_AT, s, tf.eval_adjoint)):
+        gpu = call(torch.from_numpy(nu).cuda(), w).cpu().numpy()
+        ora, b = oracle.eval_op(op, pts, nu, w, theta=0.5, amb_tol=AMB, far_order=1)
+        check_close(gpu, ora, b, tol=3e-4, what=f"first-order coincident op={op}")
+    tp = W.Tree(torch.from_numpy(pts).cuda(), theta=0.5, leaf_size=8, rep_mode=0, criterion=1)
+    for op, nu, call in ((OP_A, mu, tp.eval_w), (OP_AT, s, tp.eval_adjoint)):
+        gpu = call(torch.from_numpy(nu).cuda(), w).cpu().numpy()
+        ora, info = oracle.eval_paper(op, pts, nu, w, 0.5, leaf_size=8, amb_tol=AMB)
+        check_close(gpu, ora, info, tol=3e-4, what=f"per-target coincident op={op}")
+
+
+def test_per_target_criterion_at_query_points():
+    """criterion 1 at off-surface query points: the oracle's paper treecode
+    evaluated at the same queries (F = 1 inside a densely sampled sphere)."""
+    W = _wnnc()
+    c = synth.fibonacci_sphere(20000)
+    n = len(c.points)
+    mu = (c.normals * (4 * math.pi / n)).astype(np.float32)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, leaf_size=1, rep_mode=0, criterion=1)
+    q = synth.ball_queries(2000, 5, (0, 0, 0), 1.3)
+    F = t.eval_at(torch.from_numpy(mu).cuda(), torch.from_numpy(q).cuda(), 0.0).cpu().numpy()
+    xn, ctr, sc = oracle.normalize(c.points)
+    qn = oracle.apply_normalization(q, ctr, sc)
+    Fo, info = oracle.PaperTree(xn, leaf_size=1).apply(OP_A, mu.astype(np.float64) * sc * sc, 0.0, 0.5, y=qn,
+                                                        amb_tol=AMB)
+    check_close(F, Fo, info, what="per-target criterion at queries")
+    inside = np.linalg.norm(q, axis=1) < 0.7
+    assert np.abs(F[inside] - 1).max() < 5e-2
+
+
 def test_per_target_criterion_needs_paper_representatives():
     W = _wnnc()
     pts = torch.rand(500, 3, device="cuda")
