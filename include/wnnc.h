@@ -368,6 +368,17 @@ wnnc_status wnnc_probe_fp32(double* tflops, void* stream);
 wnnc_status wnnc_eval_w_direct_noalloc(const float* pts, int64_t n, const float* mu, const float* q,
                                        int64_t m, float w, float* out, void* stream);
 
+/*
+ * Fault injection for tests (no counterpart in the paper): after `after` more
+ * successful device allocations by the library, the next one fails as if the
+ * device were out of memory, and the call that made it returns WNNC_ENOMEM
+ * (then the injection switches itself off).  after < 0 switches it off.
+ * Building a tree allocates; evaluation and iteration do not (wnnc_eval_at
+ * allocates its query lists).  A process-wide setting: do not use it while
+ * other threads call the library.  Returns WNNC_OK.
+ */
+wnnc_status wnnc_debug_fail_alloc(int64_t after);
+
 /* Wait for the stream and return (and clear) any condition latched on the device. */
 wnnc_status wnnc_sync_status(wnnc_tree* tree, void* stream);
 

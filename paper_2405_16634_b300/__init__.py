@@ -103,6 +103,8 @@ def lib():
     L.wnnc_warm_init.argtypes = [P, P, c_int64, c_float, P, P]
     L.wnnc_last_error.restype = ctypes.c_char_p
     L.wnnc_kernel_launches.restype = c_int64
+    L.wnnc_debug_fail_alloc.argtypes = [c_int64]
+    L.wnnc_debug_fail_alloc.restype = c_int
     L.wnnc_probe_fp32.argtypes = [P, P]
     L.wnnc_probe_fp32.restype = c_int
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
@@ -134,6 +136,12 @@ def _dev_f32(t, shape, device) -> torch.Tensor:
     if tuple(t.shape) != tuple(shape):
         t = t.reshape(shape)
     return t
+
+
+def debug_fail_alloc(after: int) -> None:
+    """Fault injection for tests: the device allocation after the next
+    `after` successful ones fails with WNNC_ENOMEM (after < 0: off)."""
+    _check(lib().wnnc_debug_fail_alloc(int(after)))
 
 
 def kernel_launches() -> int:

@@ -56,7 +56,15 @@ cudaMemPool_t pool_for_current_device() {
 }
 }  // namespace
 
+// Fault injection on the host (wnnc_debug_fail_alloc): device allocations
+// left before the next one fails with WNNC_ENOMEM; -1 = off.
+static std::atomic<int64_t> g_fail_alloc_after{-1};
+
 void* pool_alloc(size_t bytes) {
+    int64_t k = g_fail_alloc_after.load();
+    while (k >= 0 && !g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) fail(WNNC_ENOMEM, "injected device allocation failure (wnnc_debug_fail_alloc)");
     void* p = nullptr;
     WNNC_CUDA(cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), alloc_stream()));
     return p;
@@ -200,6 +208,11 @@ wnnc_status wnnc_iter_params_default(wnnc_iter_params* p) {
     p->use_grad = 1;
     p->use_wnnc = 1;
     p->schedule = 0;
+    return WNNC_OK;
+}
+
+wnnc_status wnnc_debug_fail_alloc(int64_t after) {
+    g_fail_alloc_after.store(after < 0 ? -1 : after);
     return WNNC_OK;
 }
 

@@ -47,3 +47,24 @@ def test_defaults_and_argument_errors_without_gpu():
     assert b"NULL" in L.wnnc_last_error()
     assert L.wnnc_eval_w(None, None, ctypes.c_float(0.0), None, None) == 1
     assert L.wnnc_tree_free(None) == 0
+
+
+def test_mode_parameters_are_checked_before_any_device_work():
+    """criterion and far_order: defaults 0; values out of range or in
+    combinations the modes do not support are WNNC_EINVAL, reported before the
+    library touches the device (the point pointer below is never read)."""
+    import paper_2405_16634_b300 as W
+    W.build_if_needed()
+    L = W.lib()
+    p = W.default_tree_params()
+    assert (p.criterion, p.far_order) == (0, 0)
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(256)
+    for kw, msg in (({"criterion": 2}, b"criterion"), ({"criterion": 1, "rep_mode": 1}, b"rep_mode 0"),
+                    ({"far_order": 2}, b"far_order"), ({"far_order": 1, "rep_mode": 0}, b"far_order 1"),
+                    ({"far_order": 1, "rep_mode": 0, "criterion": 1}, b"far_order 1")):
+        q = W.default_tree_params()
+        for k, v in kw.items():
+            setattr(q, k, v)
+        assert L.wnnc_build_tree(fake, 10, ctypes.byref(q), None, ctypes.byref(h)) == 1
+        assert msg in L.wnnc_last_error(), (kw, L.wnnc_last_error())

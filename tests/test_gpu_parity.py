@@ -673,6 +673,44 @@ def test_errors_are_reported():
     t.sync_status()
 
 
+def test_allocation_failures_are_reported_and_leave_the_library_usable():
+    """Failure detection by host-side fault injection: the k-th device
+    allocation of a tree build (or of the query lists of eval_at) fails as if
+    the device were out of memory.  Every such call returns WNNC_ENOMEM with
+    its message, and afterwards a build on the same stream gives bit-identical
+    results to one made before any failure."""
+    W = _wnnc()
+    c = synth.union_cloud(20000, 9, n_tori=1, n_ellipsoids=1)
+    pts = torch.from_numpy(c.points).cuda()
+    mu = torch.from_numpy(synth.init_normals(20000, 5, 1e-3)).cuda()
+    ref = W.Tree(pts, theta=0.5).iterate(n_iter=3).cpu()
+    failed = 0
+    try:
+        for k in (0, 1, 2, 5, 10, 20, 40, 80, 160, 320):
+            W.debug_fail_alloc(k)
+            try:
+                W.Tree(pts, theta=0.5).close()
+            except W.WnncError as e:
+                assert e.status == 2 and "injected" in str(e)
+                failed += 1
+            W.debug_fail_alloc(-1)
+        t = W.Tree(pts, theta=0.5)
+        q = torch.rand(3000, 3, device="cuda")
+        for k in (0, 3):
+            W.debug_fail_alloc(k)
+            with pytest.raises(W.WnncError) as e:
+                t.eval_at(mu, q, 0.0)
+            assert e.value.status == 2
+        W.debug_fail_alloc(-1)
+        assert torch.isfinite(t.eval_at(mu, q, 0.0)).all()
+    finally:
+        W.debug_fail_alloc(-1)
+    assert failed >= 8
+    again = W.Tree(pts, theta=0.5).iterate(n_iter=3).cpu()
+    assert torch.equal(again, ref)
+    t.sync_status()
+
+
 def test_units_scale_invariance():
     """x -> k x (mu -> k^2 mu): F unchanged, grad F scales 1/k, A^T 1/k^2."""
     W = _wnnc()
