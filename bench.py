@@ -13,6 +13,10 @@ CUDA-event profiler on its launch stream), an end-to-end number through the publ
 from pinned host buffers, the CPU oracle as a baseline, and SM clocks sampled
 during the timed region.
 
+After the timed region the line adds `variants`: one or two whole solves of the paper's own
+treecode as printed (per-target Alg. 4, leaf size 1) and of the first-order far field on the
+same cloud, for comparison (not part of `value`; `--no-variants` skips them).
+
 `--impl reference` times the FP64 CPU oracle on the same workload: each step
 is one full iteration of Alg. 3 on the whole cloud (the oracle builds its own
 tree inside the call).  With N > 1 (torchrun) every rank solves its own cloud
@@ -53,6 +57,18 @@ WORKLOAD = WORKLOADS[CONFIG_NAME]
 FLOPS_A, FLOPS_AT, FLOPS_G, FLOPS_AG = 18, 18, 31, 33
 FLOPS_ITER = 2 * FLOPS_AG + FLOPS_AT               # A+G(mu), A^T(s), A+G(r) per iteration
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
+# Variants solved once each after the timed region (name, tree parameters, timed solves):
+# the paper's own treecode as printed (Alg. 4 per target and per call, leaf size 1,
+# |nu|-weighted representatives), and the first-order far field at two opening angles.
+# Also the default method at theta = 0.8, where its errors against the direct sums (A 2.2e-2,
+# grad F 5.8e-3, A^T 3.6e-2 at 500k) are still below those of the paper's own treecode at the
+# paper's theta = 0.5 (2.4e-2, 4.6e-2, 1.5e-1): the speed at the paper's accuracy.
+VARIANTS = [
+    ("paper_alg4_per_target_leaf1_theta0.5", dict(theta=0.5, leaf_size=1, rep_mode=0, criterion=1), 1),
+    ("group_lists_theta0.8", dict(theta=0.8), 3),
+    ("first_order_far_field_theta0.5", dict(theta=0.5, far_order=1), 2),
+    ("first_order_far_field_theta0.8", dict(theta=0.8, far_order=1), 2),
+]
 # DRAM bytes (read + write) of one launch of the fused A+G kernel on union500k, from ncu
 # (one ncu capture of that kernel on this workload); None once the kernel has changed.
 AG_TRAFFIC_BYTES = 107.010304e6 + 7.056640e6
@@ -304,6 +320,30 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(h_pts.numel() * 4),
                "d2h_bytes_per_step": int(h_mu.numel() * 4)}
 
+    # ---- variants of the method on the same cloud (after the timed region;
+    # not part of `value`): the paper's own treecode as printed, and the
+    # first-order far field ----
+    variants = None
+    if not args.no_variants and rank == 0:
+        variants = {}
+        for name, kw, steps in VARIANTS:
+            vt = []
+            for k in range(1 + steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                tv = W.Tree(pts, **kw)
+                tv.iterate(n_iter=N_ITER, w1=W1, w2=W2, out=mu)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                if k > 0:
+                    vt.append(a.elapsed_time(b))
+                vf, vn = tv.stats()
+                tv.close()
+            ms_v = sum(vt) / len(vt)
+            variants[name] = {"tree": kw, "iter_per_s": N_ITER / (ms_v / 1e3), "ms_per_solve": ms_v,
+                              "steps": steps, "far_pairs_group_lists": vf, "near_pairs_group_lists": vn}
+
     if rank != 0:
         return 0
 
@@ -357,6 +397,8 @@ def run_gpu(args):
     }
     if e2e:
         line["e2e"] = e2e
+    if variants:
+        line["variants"] = variants
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(c.points)
     print(json.dumps(line), flush=True)
@@ -371,6 +413,8 @@ def main():
     ap.add_argument("--impl", default="wnnc", choices=["wnnc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the solves of the method's variants after the timed region")
     ap.add_argument("--config", default="union500k", choices=sorted(WORKLOADS),
                     help="workload (the default is the one the metric is quoted on)")
     args = ap.parse_args()
