@@ -192,6 +192,24 @@ wnnc_status wnnc_eval_at(const wnnc_tree* tree, const float* mu, const float* q,
 wnnc_status wnnc_iterate(wnnc_tree* tree, float* mu_inout, const float* area,
                          const wnnc_iter_params* params, void* stream, float* stats);
 
+/*
+ * The whole orientation from host memory to host memory (Sec. 4.5 + Alg. 3):
+ * copy the points to the device, build the tree, run iterations first..last of
+ * Alg. 3, copy the field back.  For callers without device buffers; the
+ * copies are faster from pinned (page-locked) host memory.
+ *   pts_host  host, float32 [n][3], caller units, all finite.
+ *   tree_params, iter_params  host, either may be NULL for the defaults.
+ *   area_host host, float32 [n] (rescale = 1), else NULL.
+ *   mu_host   host, float32 [n][3]: the initial field when init = 1, the
+ *             oriented field (caller units) on return.
+ * Allocates its device buffers and the tree, frees them before returning, and
+ * synchronises with `stream`.  Errors: those of wnnc_build_tree,
+ * wnnc_iterate and wnnc_sync_status; mu_host is unspecified after an error.
+ */
+wnnc_status wnnc_orient(const float* pts_host, int64_t n, const wnnc_tree_params* tree_params,
+                        const wnnc_iter_params* iter_params, const float* area_host, float* mu_host,
+                        void* stream);
+
 /* Interaction counts of one on-surface operator evaluation: far (target, node)
  * pairs and near (target, source) pairs, cut-off ones included.  host out. */
 wnnc_status wnnc_get_stats(const wnnc_tree* tree, int64_t* far_pairs, int64_t* near_pairs);

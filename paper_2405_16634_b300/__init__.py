@@ -14,6 +14,7 @@ caller's units):
 * ``Tree.eval_adjoint(s, w)``   A_w^T(s)                         (Sec. 4.5)
 * ``Tree.eval_at(mu, q, w)``    F (or grad F) at query points
 * ``Tree.iterate(...)``         Alg. 3 with the gradient step of Alg. 2
+* ``orient(points_host)``       the whole solve from host memory to host memory
 * ``winding_number(tree, mu, w)`` differentiable F(mu) whose backward is A^T.
 """
 from __future__ import annotations
@@ -29,7 +30,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libwnnc.so")
 
 __all__ = ["Tree", "TreeParams", "IterParams", "WnncError", "winding_number", "WindingNumber",
-           "lib", "LIB_PATH", "PROF_CLASSES", "knn16", "Mlp", "MLP_PARAMS", "warm_init", "probe_fp32"]
+           "lib", "LIB_PATH", "PROF_CLASSES", "knn16", "Mlp", "MLP_PARAMS", "warm_init", "probe_fp32",
+           "orient"]
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ECAPACITY",
           6: "ETIMEOUT"}
@@ -103,6 +105,8 @@ def lib():
     L.wnnc_warm_init.argtypes = [P, P, c_int64, c_float, P, P]
     L.wnnc_last_error.restype = ctypes.c_char_p
     L.wnnc_kernel_launches.restype = c_int64
+    L.wnnc_orient.argtypes = [P, c_int64, POINTER(TreeParams), POINTER(IterParams), P, P, P]
+    L.wnnc_orient.restype = c_int
     L.wnnc_debug_fail_alloc.argtypes = [c_int64]
     L.wnnc_debug_fail_alloc.restype = c_int
     L.wnnc_probe_fp32.argtypes = [P, P]
@@ -136,6 +140,40 @@ def _dev_f32(t, shape, device) -> torch.Tensor:
     if tuple(t.shape) != tuple(shape):
         t = t.reshape(shape)
     return t
+
+
+def orient(points_host, out=None, mu0=None, theta: float = 0.5, leaf_size: int = 8, n_iter: int = 40,
+           w1: float = 0.002, w2: float = 0.016, device=None, **tree_kw):
+    """The whole orientation through one C-ABI call with host buffers
+    (wnnc_orient): points [n][3] float32 on the host (a numpy array or a CPU
+    tensor, ideally pinned) in, the oriented field [n][3] out (into `out`, a
+    float32 host tensor or array, if given).  mu0: initial field (host) or None
+    for the paper's zero start.  Other tree parameters as in Tree."""
+    pts = points_host if isinstance(points_host, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(
+        points_host, dtype=np.float32))
+    if pts.is_cuda or pts.dtype != torch.float32 or not pts.is_contiguous():
+        raise ValueError("points_host must be a contiguous float32 host tensor or array")
+    n = pts.shape[0]
+    if out is None:
+        out = torch.empty(n, 3, dtype=torch.float32)
+    elif isinstance(out, np.ndarray):
+        out = torch.from_numpy(out)
+    if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != 3 * n:
+        raise ValueError("out must be a contiguous float32 host tensor of n x 3")
+    tp = default_tree_params()
+    tp.theta, tp.leaf_size = float(theta), int(leaf_size)
+    for k, v in tree_kw.items():
+        setattr(tp, k, int(v) if not isinstance(v, float) else v)
+    ip = default_iter_params()
+    ip.n_iter, ip.w1, ip.w2 = int(n_iter), float(w1), float(w2)
+    if mu0 is not None:
+        out.copy_(torch.as_tensor(mu0, dtype=torch.float32).reshape(n, 3))
+        ip.init = 1
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    with torch.cuda.device(dev):
+        _check(lib().wnnc_orient(pts.data_ptr(), n, ctypes.byref(tp), ctypes.byref(ip), None, out.data_ptr(),
+                                 _stream_ptr(dev)))
+    return out
 
 
 def debug_fail_alloc(after: int) -> None:

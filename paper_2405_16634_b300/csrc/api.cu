@@ -325,6 +325,52 @@ wnnc_status wnnc_iterate(wnnc_tree* tree, float* mu_inout, const float* area, co
     });
 }
 
+wnnc_status wnnc_orient(const float* pts_host, int64_t n, const wnnc_tree_params* tree_params,
+                        const wnnc_iter_params* iter_params, const float* area_host, float* mu_host,
+                        void* stream) {
+    float* dpts = nullptr;
+    float* dmu = nullptr;
+    float* darea = nullptr;
+    wnnc_tree* tree = nullptr;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    wnnc_status st = guarded([&] {
+        if (!pts_host || !mu_host) fail(WNNC_EINVAL, "pts_host/mu_host is NULL");
+        if (n < 1) fail(WNNC_EINVAL, "n must be >= 1");
+        if (n > (int64_t)INT32_MAX / 2) fail(WNNC_EINVAL, "n too large (max 2^30 points)");
+        wnnc_iter_params p;
+        wnnc_iter_params_default(&p);
+        if (iter_params) p = *iter_params;
+        if (p.rescale == 1 && !area_host) fail(WNNC_EINVAL, "rescale = 1 needs area_host");
+        AllocStream as(s);
+        const size_t bytes = sizeof(float) * 3 * (size_t)n;
+        dpts = dalloc<float>(3 * (size_t)n);
+        dmu = dalloc<float>(3 * (size_t)n);
+        WNNC_CUDA(cudaMemcpyAsync(dpts, pts_host, bytes, cudaMemcpyHostToDevice, s));
+        if (p.init == 1) WNNC_CUDA(cudaMemcpyAsync(dmu, mu_host, bytes, cudaMemcpyHostToDevice, s));
+        if (area_host) {
+            darea = dalloc<float>((size_t)n);
+            WNNC_CUDA(cudaMemcpyAsync(darea, area_host, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, s));
+        }
+        wnnc_status b = wnnc_build_tree(dpts, n, tree_params, stream, &tree);
+        if (b != WNNC_OK) fail(b, wnnc_last_error());
+        b = wnnc_iterate(tree, dmu, darea, &p, stream, nullptr);
+        if (b != WNNC_OK) fail(b, wnnc_last_error());
+        WNNC_CUDA(cudaMemcpyAsync(mu_host, dmu, bytes, cudaMemcpyDeviceToHost, s));
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        b = wnnc_sync_status(tree, stream);
+        if (b != WNNC_OK) fail(b, wnnc_last_error());
+    });
+    if (st != WNNC_OK) cudaStreamSynchronize(s);
+    if (tree) wnnc_tree_free(tree);
+    {
+        AllocStream as(s);
+        pool_free(dpts);
+        pool_free(dmu);
+        pool_free(darea);
+    }
+    return st;
+}
+
 wnnc_status wnnc_get_stats(const wnnc_tree* tree, int64_t* far_pairs, int64_t* near_pairs) {
     return guarded([&] {
         Tree& t = unwrap(tree);

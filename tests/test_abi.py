@@ -68,3 +68,17 @@ def test_mode_parameters_are_checked_before_any_device_work():
             setattr(q, k, v)
         assert L.wnnc_build_tree(fake, 10, ctypes.byref(q), None, ctypes.byref(h)) == 1
         assert msg in L.wnnc_last_error(), (kw, L.wnnc_last_error())
+
+
+def test_orient_argument_errors_without_gpu():
+    import paper_2405_16634_b300 as W
+    W.build_if_needed()
+    L = W.lib()
+    buf = (ctypes.c_float * 30)()
+    assert L.wnnc_orient(None, 10, None, None, None, buf, None) == 1
+    assert L.wnnc_orient(buf, 10, None, None, None, None, None) == 1
+    assert L.wnnc_orient(buf, 0, None, None, None, buf, None) == 1
+    q = W.default_iter_params()
+    q.rescale = 1
+    assert L.wnnc_orient(buf, 10, None, ctypes.byref(q), None, buf, None) == 1
+    assert b"area_host" in L.wnnc_last_error()

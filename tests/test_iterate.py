@@ -143,6 +143,27 @@ def test_gpu_iteration_sphere2k_matches_oracle(init):
 
 
 @pytest.mark.gpu
+def test_orient_from_host_memory_equals_the_device_path():
+    """wnnc_orient (host points in, host field out, one call) gives the field
+    of the device entry points bit for bit, from zero and from a given init."""
+    W = _gpu()
+    c = synth.config_cloud("union50k", n=20000)
+    n = len(c.points)
+    ref = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5).iterate(n_iter=10).cpu()
+    h_pts = torch.from_numpy(c.points).pin_memory()
+    got = W.orient(h_pts, n_iter=10, out=torch.empty(n, 3).pin_memory())
+    assert torch.equal(got, ref)
+    mu0 = synth.init_normals(n, 3, c.area / n)
+    ref = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5).iterate(torch.from_numpy(mu0).cuda(), n_iter=10).cpu()
+    got = W.orient(c.points, mu0=mu0, n_iter=10)          # pageable host memory works too
+    assert torch.equal(got, ref)
+    with pytest.raises(W.WnncError):
+        bad = c.points.copy()
+        bad[7, 1] = np.nan
+        W.orient(bad, n_iter=2)
+
+
+@pytest.mark.gpu
 def test_gpu_first_iteration_closed_form():
     W = _gpu()
     c = synth.fibonacci_sphere(40000)
