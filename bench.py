@@ -71,7 +71,7 @@ VARIANTS = [
 ]
 # DRAM bytes (read + write) of one launch of the fused A+G kernel on union500k, from ncu
 # (one ncu capture of that kernel on this workload); None once the kernel has changed.
-AG_TRAFFIC_BYTES = 107.010304e6 + 7.056640e6
+AG_TRAFFIC_BYTES = 107.725568e6 + 4.595968e6
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:

@@ -569,6 +569,19 @@ __global__ void WNNC_CAPPED_BOUNDS k_gather(GatherArgs A) {
     auto sum_batch = [&](int cnt, bool clear, bool near) {
         if (kPack) {
             const float2 &ax = near ? nnx : ntx, &ay = near ? nny : nty, &az = near ? nnz : ntz;
+            if (cnt == 32) {
+                // a full batch (almost all of them): a compile-time trip count, no bounds guards
+                if (clear) {
+#pragma unroll
+                    for (int j = 0; j < 32 / TPL; ++j)
+                        interact2<OP, false>(ax, ay, az, sp[h + TPL * j], sv[h + TPL * j], A.w2, acc2);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32 / TPL; ++j)
+                        interact2<OP, true>(ax, ay, az, sp[h + TPL * j], sv[h + TPL * j], A.w2, acc2);
+                }
+                return;
+            }
             if (clear) {
 #pragma unroll kUnroll
                 for (int k = h; k < cnt; k += TPL) interact2<OP, false>(ax, ay, az, sp[k], sv[k], A.w2, acc2);
@@ -942,7 +955,16 @@ __global__ void WNNC_ADJ_BOUNDS k_adj_far(AdjArgs A) {
             ay = __ffma2_rn(q, dy, ay);
             az = __ffma2_rn(q, dz, az);
         };
-        if (clear) {
+        if (cnt_t == 32) {
+            // a full group: a compile-time trip count, no bounds guards
+            if (clear) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) term(tp[k], std::false_type{});
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) term(tp[k], std::true_type{});
+            }
+        } else if (clear) {
 #pragma unroll kUnroll
             for (int k = 0; k < cnt_t; ++k) term(tp[k], std::false_type{});
         } else {
@@ -1443,7 +1465,16 @@ __global__ void WNNC_ADJ_BOUNDS k_adj_near_pairs(AdjArgs A) {
             ay = __ffma2_rn(q, dy, ay);
             az = __ffma2_rn(q, dz, az);
         };
-        if (clear) {
+        if (cnt_t == 32) {
+            // a full group: a compile-time trip count, no bounds guards
+            if (clear) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) term(tp[k], std::false_type{});
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) term(tp[k], std::true_type{});
+            }
+        } else if (clear) {
 #pragma unroll kUnroll
             for (int k = 0; k < cnt_t; ++k) term(tp[k], std::false_type{});
         } else {
