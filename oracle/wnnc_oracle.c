@@ -296,8 +296,7 @@ static void ivec_push(ivec* a, int64_t x) {
 /* Far test for a target group box (glo, ghi) against node b: the gap between
  * the boxes, squared, must exceed (c * width(b))^2.  Evaluated as written, in
  * double precision, without fused multiply-adds. */
-static int is_far(const or_octree* t, int64_t b, const double* glo, const double* ghi, double c) {
-    if (!(c < INFINITY)) return 0;
+static double box_gap2(const or_octree* t, int64_t b, const double* glo, const double* ghi) {
     double g[3];
     for (int k = 0; k < 3; ++k) {
         double a = t->lo[3 * b + k] - ghi[k];
@@ -306,10 +305,31 @@ static int is_far(const or_octree* t, int64_t b, const double* glo, const double
         g[k] = m > 0.0 ? m : 0.0;
     }
     double gx = g[0] * g[0], gy = g[1] * g[1], gz = g[2] * g[2];
-    double d2 = (gx + gy) + gz;
+    return (gx + gy) + gz;
+}
+
+static int is_far(const or_octree* t, int64_t b, const double* glo, const double* ghi, double c) {
+    if (!(c < INFINITY)) return 0;
+    double d2 = box_gap2(t, b, glo, ghi);
     double width = ldexp(2.0, -t->depth[b]);
     double cw = c * width;
     return d2 > cw * cw;
+}
+
+/* Local-expansion test for a far node b of a group with box (glo, ghi): the
+ * box gap, squared, must exceed (cL * e)^2, e the largest extent of the group
+ * box (same evaluation rules as is_far).  cL = 0 switches local expansions off. */
+static double group_extent(const double* glo, const double* ghi) {
+    double e = ghi[0] - glo[0];
+    if (ghi[1] - glo[1] > e) e = ghi[1] - glo[1];
+    if (ghi[2] - glo[2] > e) e = ghi[2] - glo[2];
+    return e;
+}
+
+static int is_local(const or_octree* t, int64_t b, const double* glo, const double* ghi, double cL) {
+    if (!(cL > 0.0)) return 0;
+    double ce = cL * group_extent(glo, ghi);
+    return box_gap2(t, b, glo, ghi) > ce * ce;
 }
 
 static void traverse(const or_octree* t, int64_t b, const double* glo, const double* ghi, double c,
@@ -430,6 +450,8 @@ typedef struct {
     or_targets self;
     double theta;
     int far_order;      /* 0: monopole far terms (Eq. 13-14); 1: plus the first-order Taylor terms */
+    double local_c;     /* > 0: first-order local expansions about the group box centre for far
+                           nodes with box gap > local_c x group extent (far_order 0, rep_mode 1) */
 } or_tree;
 
 /* group_slack, group_min_depth: the rule of group_offsets for the points as
@@ -464,6 +486,12 @@ void or_tree_free(or_tree* T) {
  * 0 = one term per far node at its point centroid x_B (Eq. 13-14);
  * 1 = plus the first-order Taylor term of the kernel about x_B. */
 void or_tree_set_far_order(or_tree* T, int order) { T->far_order = order; }
+
+/* Local expansions of the far field about the target group's box centre
+ * (rep_mode 1, far_order 0): a far node b is expanded for a group when the box
+ * gap exceeds 1/local_theta times the group box's largest extent; local_theta
+ * 0 switches them off. */
+void or_tree_set_local(or_tree* T, double local_theta) { T->local_c = local_theta > 0.0 ? 1.0 / local_theta : 0.0; }
 
 /* Structure queries (for the structural pins and for comparing list sizes). */
 int64_t or_tree_nnodes(const or_tree* T) { return T->src.nnodes; }
@@ -581,6 +609,75 @@ static void far_correction(int op, const double d[3], double r2, const double* S
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Local (target-side) expansion of the far field, the counterpart on the     */
+/* target side of the expansions named in Sec. 4.5 and Sec. 6.3 (rep_mode 1,  */
+/* far_order 0).  For a far node B of group g with D = c_g - x_B (c_g the     */
+/* centre of the group box) and a target y = c_g + delta, Taylor's theorem    */
+/* about c_g gives, with a(d) = gradPhi(d) . mu_B and g(d) = -HPhi(d) mu_B    */
+/* (the far terms of A and G, G = -grad A):                                   */
+/*   a(D + delta) = a(D) - delta . g(D) + O(|delta|^2)                        */
+/*   g(D + delta) = g(D) - J(D) delta   + O(|delta|^2),                       */
+/* J_ac = sum_b d_c HPhi_ab(D) mu_b                                           */
+/*      = (3 (mu D^T + D mu^T)_ac + 3 (D.mu) I_ac)/(4 pi r^5)                */
+/*        - 15 (D.mu) D_a D_c/(4 pi r^7),                                     */
+/* symmetric, stored as (xx, yy, zz, xy, xz, yz).  A group sums a, g and J    */
+/* over its local entries once and evaluates the two polynomials per target.  */
+/* The transpose (the adjoint A^T) gives node B, per local entry,             */
+/*   S_g gradPhi(D) + HPhi(D) D_g,  S_g = sum_i s_i, D_g = sum_i s_i delta_i. */
+/* A group uses its local entries only when every one of their pairs clears   */
+/* the cut-off (w^2 below the smallest squared box gap of those entries);    */
+/* otherwise they are summed pair by pair like the other far entries.         */
+/* ------------------------------------------------------------------------ */
+static void local_coeffs(const double D[3], const double* mu, double out[10]) {
+    const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+    const double r = sqrt(r2), r5 = r2 * r2 * r, r7 = r5 * r2;
+    out[0] = term_A(D, r2, mu);
+    term_G(D, r2, mu, out + 1);
+    const double dm = D[0] * mu[0] + D[1] * mu[1] + D[2] * mu[2];
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ic[6] = {0, 1, 2, 1, 2, 2};
+    for (int q = 0; q < 6; ++q) {
+        const int a = ia[q], c = ic[q];
+        const double diag = a == c ? 3.0 * dm : 0.0;
+        out[4 + q] = (3.0 * (mu[a] * D[c] + D[a] * mu[c]) + diag) / (4.0 * OR_PI * r5)
+                   - 15.0 * dm * D[a] * D[c] / (4.0 * OR_PI * r7);
+    }
+}
+
+/* The transposed local term of one entry: S gradPhi(D) + HPhi(D) Dg. */
+static void local_adjoint(const double D[3], double S, const double Dg[3], double out[3]) {
+    const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+    const double r = sqrt(r2), r3 = r2 * r, r5 = r3 * r2;
+    const double dd = D[0] * Dg[0] + D[1] * Dg[1] + D[2] * Dg[2];
+    for (int k = 0; k < 3; ++k)
+        out[k] = -S * D[k] / (4.0 * OR_PI * r3) + (3.0 * D[k] * dd - r2 * Dg[k]) / (4.0 * OR_PI * r5);
+}
+
+/* Per group: the expansion centre, whether the local entries are used at this
+ * cut-off (w2 = the effective squared width) and whether that decision is
+ * cut-off ambiguous (w2 within amb_tol of the threshold). */
+typedef struct { double c[3]; int use, amb; } local_state;
+
+static local_state group_local(const or_octree* t, const or_targets* T, int64_t g, double cL,
+                               double w2, double amb_tol) {
+    local_state L;
+    const double* glo = T->glo + 3 * g;
+    const double* ghi = T->ghi + 3 * g;
+    for (int k = 0; k < 3; ++k) L.c[k] = 0.5 * (glo[k] + ghi[k]);
+    double gmin = INFINITY;
+    int any = 0;
+    for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
+        const int64_t b = T->far_id[q];
+        if (!is_local(t, b, glo, ghi, cL)) continue;
+        any = 1;
+        double g2 = box_gap2(t, b, glo, ghi);
+        if (g2 < gmin) gmin = g2;
+    }
+    L.use = any && w2 < gmin;
+    L.amb = any && amb_tol > 0.0 && fabs(w2 - gmin) <= amb_tol * gmin;
+    return L;
+}
+
 /* Gather-form treecode for targets T against the source octree:
  *   op A : out (m)    = sum_far gradPhi(y - x_B) . mu_B + sum_near gradPhi(y - x_j) . mu_j
  *   op G : out (m x 3) = sum_far -HPhi(y - x_B) mu_B  + sum_near -HPhi(y - x_j) mu_j
@@ -590,7 +687,7 @@ static void far_correction(int op, const double d[3], double r2, const double* S
  */
 static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep_mode, double w,
                         const double* nu_sorted, double* out_sorted, double amb_tol, double* amb_sorted,
-                        double* abs_sorted, int far_order) {
+                        double* abs_sorted, int far_order, double local_c) {
     int dim = (op == OP_AT) ? 1 : 3;
     double* rep = malloc(sizeof(double) * 3 * (t->nnodes > 0 ? t->nnodes : 1));
     double* nuB = malloc(sizeof(double) * dim * (t->nnodes > 0 ? t->nnodes : 1));
@@ -599,14 +696,36 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
     double* S = dip ? malloc(sizeof(double) * 6 * (t->nnodes > 0 ? t->nnodes : 1)) : NULL;
     if (dip) node_dipoles(t, nu_sorted, S);
     const double w2 = eff_w2(w);
+    const int loc = local_c > 0.0 && rep_mode == 1 && !dip && op != OP_AT;
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < T->ngroups; ++g) {
         int64_t s = T->goff[g], e = T->goff[g + 1];
+        local_state L = {{0, 0, 0}, 0, 0};
+        double co[10] = {0}, coabs[3] = {0, 0, 0};
+        if (loc) {
+            L = group_local(t, T, g, local_c, w2, amb_sorted ? amb_tol : 0.0);
+            if (L.use || L.amb)
+                for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
+                    int64_t b = T->far_id[q];
+                    if (!is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c)) continue;
+                    const double D[3] = {L.c[0] - rep[3 * b], L.c[1] - rep[3 * b + 1], L.c[2] - rep[3 * b + 2]};
+                    double ce[10];
+                    local_coeffs(D, nuB + 3 * b, ce);
+                    for (int k = 0; k < 10; ++k) co[k] += ce[k];
+                    coabs[0] += fabs(ce[0]);
+                    coabs[1] += sqrt(ce[1] * ce[1] + ce[2] * ce[2] + ce[3] * ce[3]);
+                    coabs[2] += sqrt(ce[4] * ce[4] + ce[5] * ce[5] + ce[6] * ce[6]
+                                     + 2.0 * (ce[7] * ce[7] + ce[8] * ce[8] + ce[9] * ce[9]));
+                }
+        }
         for (int64_t i = s; i < e; ++i) {
             const double* y = T->y + 3 * i;
             double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
+            double pwl[3] = {0, 0, 0};     /* local entries pair by pair (the other side of an ambiguous decision) */
             for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
                 int64_t b = T->far_id[q];
+                const int lq = (L.use || L.amb) && is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c);
+                if (lq && L.use && !L.amb) continue;     /* in the expansion */
                 double d[3] = {y[0] - rep[3 * b], y[1] - rep[3 * b + 1], y[2] - rep[3 * b + 2]};
                 double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                 int amb_p = amb_sorted && ambiguous(r2, w2, amb_tol);
@@ -622,11 +741,36 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
                     for (int k = 0; k < 3; ++k) v[k] += cr[k];
                     vn += sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
                 }
+                if (lq) {
+                    if (keep_pair(r2, w2)) for (int k = 0; k < 3; ++k) pwl[k] += v[k];
+                    if (L.use) continue;
+                }
                 if (amb_p) ab += vn;
                 if (keep_pair(r2, w2)) {
                     for (int k = 0; k < 3; ++k) acc[k] += v[k];
                     as += vn;
                 }
+            }
+            if (L.use || L.amb) {
+                const double dl[3] = {y[0] - L.c[0], y[1] - L.c[1], y[2] - L.c[2]};
+                const double dn = sqrt(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
+                double ev[3] = {0, 0, 0}, evabs;
+                if (op == OP_A) {
+                    ev[0] = co[0] - (dl[0] * co[1] + dl[1] * co[2] + dl[2] * co[3]);
+                    evabs = coabs[0] + dn * coabs[1];
+                } else {
+                    double jd[3];
+                    sym_mul(co + 4, dl, jd);
+                    for (int k = 0; k < 3; ++k) ev[k] = co[1 + k] - jd[k];
+                    evabs = coabs[1] + dn * coabs[2];
+                }
+                if (L.use) {
+                    for (int k = 0; k < 3; ++k) acc[k] += ev[k];
+                    as += evabs;
+                }
+                if (L.amb)
+                    ab += sqrt((ev[0] - pwl[0]) * (ev[0] - pwl[0]) + (ev[1] - pwl[1]) * (ev[1] - pwl[1])
+                               + (ev[2] - pwl[2]) * (ev[2] - pwl[2]));
             }
             for (int64_t q = T->near_off[g]; q < T->near_off[g + 1]; ++q) {
                 int64_t b = T->near_id[q];
@@ -673,9 +817,29 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
  * with the same cut-off decision as the node's monopole term. */
 static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w,
                                const double* s_sorted, double* out_sorted, double amb_tol,
-                               double* amb_sorted, double* abs_sorted, int far_order) {
+                               double* amb_sorted, double* abs_sorted, int far_order, double local_c) {
     int64_t nn = t->nnodes, ng = T->ngroups;
     const double w2 = eff_w2(w);
+    /* local expansions: per group its decision, S_g, D_g and the bounds of their terms */
+    const int loc = local_c > 0.0 && far_order == 0;
+    local_state* LS = calloc((size_t)(ng > 0 ? ng : 1), sizeof(local_state));
+    double* SD = calloc((size_t)(ng > 0 ? ng : 1) * 6, sizeof(double));   /* S, Dg[3], sum|s|, sum|s||delta| */
+    if (loc) {
+        #pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t g = 0; g < ng; ++g) {
+            LS[g] = group_local(t, T, g, local_c, w2, amb_sorted ? amb_tol : 0.0);
+            double* sd = SD + 6 * g;
+            for (int64_t i = T->goff[g]; i < T->goff[g + 1]; ++i) {
+                const double dl[3] = {T->y[3 * i] - LS[g].c[0], T->y[3 * i + 1] - LS[g].c[1],
+                                      T->y[3 * i + 2] - LS[g].c[2]};
+                const double si = s_sorted[i];
+                sd[0] += si;
+                for (int k = 0; k < 3; ++k) sd[1 + k] += si * dl[k];
+                sd[4] += fabs(si);
+                sd[5] += fabs(si) * sqrt(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
+            }
+        }
+    }
     /* transposed lists: node -> groups using it (far), leaf -> groups using it (near) */
     int64_t* fcnt = calloc((size_t)nn + 1, sizeof(int64_t));
     int64_t* ncnt = calloc((size_t)nn + 1, sizeof(int64_t));
@@ -704,6 +868,21 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         for (int64_t q = fcnt[b]; q < fcnt[b + 1]; ++q) {
             int64_t g = fg[q];
             int64_t s = T->goff[g], e = T->goff[g + 1];
+            const int lq = loc && (LS[g].use || LS[g].amb)
+                           && is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c);
+            double lv[3] = {0, 0, 0}, pw[3] = {0, 0, 0};
+            if (lq) {
+                const double D[3] = {LS[g].c[0] - rep[3 * b], LS[g].c[1] - rep[3 * b + 1],
+                                     LS[g].c[2] - rep[3 * b + 2]};
+                const double* sd = SD + 6 * g;
+                local_adjoint(D, sd[0], sd + 1, lv);
+                if (LS[g].use) {
+                    const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+                    for (int k = 0; k < 3; ++k) acc[k] += lv[k];
+                    as += sd[4] / (4.0 * OR_PI * r2) + 2.0 * sd[5] / (4.0 * OR_PI * r2 * sqrt(r2));
+                    if (!LS[g].amb) continue;
+                }
+            }
             for (int64_t i = s; i < e; ++i) {
                 /* s_i gradPhi(x_i - x_B) = s_i (x_B - x_i) / (4 pi r^3) */
                 double d[3] = {rep[3 * b] - T->y[3 * i], rep[3 * b + 1] - T->y[3 * i + 1],
@@ -714,6 +893,10 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                 double v[3];
                 term_AT(d, r2, s_sorted[i], v);
                 double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                if (lq) {
+                    if (keep_pair(r2, w2)) for (int k = 0; k < 3; ++k) pw[k] += v[k];
+                    if (LS[g].use) continue;
+                }
                 if (amb_p) ab += vn;
                 if (keep_pair(r2, w2)) {
                     for (int k = 0; k < 3; ++k) acc[k] += v[k];
@@ -731,6 +914,9 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                     }
                 }
             }
+            if (lq && LS[g].amb)
+                ab += sqrt((lv[0] - pw[0]) * (lv[0] - pw[0]) + (lv[1] - pw[1]) * (lv[1] - pw[1])
+                           + (lv[2] - pw[2]) * (lv[2] - pw[2]));
         }
         for (int k = 0; k < 3; ++k) V[3 * b + k] = acc[k];
         for (int k = 0; k < 6; ++k) H[6 * b + k] = h[k];
@@ -782,7 +968,7 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         }
     }
     free(fcnt); free(ncnt); free(fg); free(ngp); free(fpos); free(npos); free(V); free(VA); free(VS);
-    free(H); free(HN);
+    free(H); free(HN); free(LS); free(SD);
 }
 
 /* On-surface application of an operator.  nu and out are in input order,
@@ -800,8 +986,8 @@ void or_tree_apply(const or_tree* T, int op, int rep_mode, double w, const doubl
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < din; ++k) nus[din * i + k] = nu[din * t->perm[i] + k];
     if (op == OP_AT && rep_mode == 1)
-        tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs, abss, T->far_order);
-    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs, abss, T->far_order);
+        tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs, abss, T->far_order, T->local_c);
+    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs, abss, T->far_order, T->local_c);
     for (int64_t i = 0; i < n; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * T->self.perm[i] + k] = outs[dout * i + k];
         if (amb) amb[T->self.perm[i]] = ambs[i];
@@ -825,7 +1011,7 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) nus[3 * i + k] = nu[3 * t->perm[i] + k];
     double* abss = abssum ? malloc(sizeof(double) * (m > 0 ? m : 1)) : NULL;
-    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL, abss, T->far_order);
+    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL, abss, T->far_order, T->local_c);
     for (int64_t i = 0; i < m; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * Q.perm[i] + k] = outs[dout * i + k];
         if (abssum) abssum[Q.perm[i]] = abss[i];

@@ -4,9 +4,10 @@ Each case plants one plausible mistake in a copy of the oracle's C source --
 Eq. 13's weights taken as the signed s_i instead of |s_i|, or its
 normalisation by sum |nu_j| dropped, in the paper's treecode or in the group
 treecode's rep_mode 0; a sign or factor of the first-order far-field terms or
-of their transpose -- compiles the copy, swaps it in for the real oracle and
-checks that the pins of tests/test_oracle_paper_tree.py and
-tests/test_oracle_dipole.py then fail.  The copy
+of their transpose; a sign or factor of the local expansions, of their
+transpose, or their cut-off decision -- compiles the copy, swaps it in for the
+real oracle and checks that the pins of tests/test_oracle_paper_tree.py,
+tests/test_oracle_dipole.py and tests/test_oracle_local.py then fail.  The copy
 lives in pytest's temporary directory; the real oracle is untouched.
 """
 import os
@@ -17,6 +18,7 @@ import oracle
 from oracle import OP_A, OP_AT, OP_G
 
 import test_oracle_dipole as dpins     # the pin modules, on sys.path as test files
+import test_oracle_local as lpins
 import test_oracle_paper_tree as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "wnnc_oracle.c")
@@ -59,6 +61,22 @@ MUTATIONS = [
      "for (int k = 0; k < 3; ++k) far[k] -= hd[k];",
      "for (int k = 0; k < 3; ++k) far[k] += hd[k];",
      [lambda: dpins.test_far_error_order_of_the_transpose()]),
+    ("local expansion: sign of A's first-order term",
+     "ev[0] = co[0] - (dl[0] * co[1] + dl[1] * co[2] + dl[2] * co[3]);",
+     "ev[0] = co[0] + (dl[0] * co[1] + dl[1] * co[2] + dl[2] * co[3]);",
+     [lambda: lpins.test_local_error_order(OP_A)]),
+    ("local expansion: factor of J's trace term",
+     "const double diag = a == c ? 3.0 * dm : 0.0;",
+     "const double diag = a == c ? dm : 0.0;",
+     [lambda: lpins.test_local_error_order(OP_G)]),
+    ("local expansion: sign of the transposed HPhi term",
+     "out[k] = -S * D[k] / (4.0 * OR_PI * r3) + (3.0 * D[k] * dd - r2 * Dg[k]) / (4.0 * OR_PI * r5);",
+     "out[k] = -S * D[k] / (4.0 * OR_PI * r3) - (3.0 * D[k] * dd - r2 * Dg[k]) / (4.0 * OR_PI * r5);",
+     [lambda: lpins.test_local_error_order_of_the_transpose()]),
+    ("local expansion: the cut-off decision taken at w instead of w^2",
+     "L.use = any && w2 < gmin;",
+     "L.use = any && sqrt(w2) < gmin;",
+     [lambda: lpins.test_groups_fall_back_to_pairs_at_wide_cutoffs()]),
 ]
 
 
