@@ -625,9 +625,10 @@ static void far_correction(int op, const double d[3], double r2, const double* S
 /* over its local entries once and evaluates the two polynomials per target.  */
 /* The transpose (the adjoint A^T) gives node B, per local entry,             */
 /*   S_g gradPhi(D) + HPhi(D) D_g,  S_g = sum_i s_i, D_g = sum_i s_i delta_i. */
-/* A group uses its local entries only when every one of their pairs clears   */
-/* the cut-off (w^2 below the smallest squared box gap of those entries);    */
-/* otherwise they are summed pair by pair like the other far entries.         */
+/* An entry is expanded only when every one of its pairs clears the cut-off:  */
+/* with rho_g the largest distance of the group's targets from c_g, every     */
+/* pair distance is at least |D| - rho_g, so the test is |D| - rho_g >= w;    */
+/* otherwise the entry is summed pair by pair like the other far entries.    */
 /* ------------------------------------------------------------------------ */
 static void local_coeffs(const double D[3], const double* mu, double out[10]) {
     const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
@@ -653,29 +654,48 @@ static void local_adjoint(const double D[3], double S, const double Dg[3], doubl
         out[k] = -S * D[k] / (4.0 * OR_PI * r3) + (3.0 * D[k] * dd - r2 * Dg[k]) / (4.0 * OR_PI * r5);
 }
 
-/* Per group: the expansion centre, whether the local entries are used at this
- * cut-off (w2 = the effective squared width) and whether that decision is
- * cut-off ambiguous (w2 within amb_tol of the threshold). */
-typedef struct { double c[3]; int use, amb; } local_state;
+/* Per group: the expansion centre c_g (the centre of the group box) and rho_g. */
+typedef struct { double c[3], rho; } local_frame;
 
-static local_state group_local(const or_octree* t, const or_targets* T, int64_t g, double cL,
-                               double w2, double amb_tol) {
-    local_state L;
+static local_frame group_frame(const or_targets* T, int64_t g) {
+    local_frame L;
     const double* glo = T->glo + 3 * g;
     const double* ghi = T->ghi + 3 * g;
     for (int k = 0; k < 3; ++k) L.c[k] = 0.5 * (glo[k] + ghi[k]);
-    double gmin = INFINITY;
-    int any = 0;
-    for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
-        const int64_t b = T->far_id[q];
-        if (!is_local(t, b, glo, ghi, cL)) continue;
-        any = 1;
-        double g2 = box_gap2(t, b, glo, ghi);
-        if (g2 < gmin) gmin = g2;
+    L.rho = 0.0;
+    for (int64_t i = T->goff[g]; i < T->goff[g + 1]; ++i) {
+        const double* y = T->y + 3 * i;
+        const double dl[3] = {y[0] - L.c[0], y[1] - L.c[1], y[2] - L.c[2]};
+        const double r = sqrt(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
+        if (r > L.rho) L.rho = r;
     }
-    L.use = any && w2 < gmin;
-    L.amb = any && amb_tol > 0.0 && fabs(w2 - gmin) <= amb_tol * gmin;
     return L;
+}
+
+/* Whether a local entry with D = c_g - x_B is expanded at the effective
+ * squared width w2 (*amb: the decision lies within amb_tol of its threshold). */
+static int local_use(const double D[3], double rho, double w2, double amb_tol, int* amb) {
+    const double m = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]) - rho;
+    const double m2 = m > 0.0 ? m * m : 0.0;
+    *amb = amb_tol > 0.0 && m > 0.0 && fabs(m2 - w2) <= amb_tol * w2;
+    return m > 0.0 && m2 >= w2;
+}
+
+/* The expanded term of one entry at the target offset dl from c_g
+ * (op A: out[0]; op G: out[0..2]) and a bound of its size. */
+static double local_eval(int op, const double* ce, const double dl[3], double out[3]) {
+    const double dn = sqrt(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
+    if (op == OP_A) {
+        out[0] = ce[0] - (dl[0] * ce[1] + dl[1] * ce[2] + dl[2] * ce[3]);
+        out[1] = out[2] = 0.0;
+        return fabs(ce[0]) + dn * sqrt(ce[1] * ce[1] + ce[2] * ce[2] + ce[3] * ce[3]);
+    }
+    double jd[3];
+    sym_mul(ce + 4, dl, jd);
+    for (int k = 0; k < 3; ++k) out[k] = ce[1 + k] - jd[k];
+    return sqrt(ce[1] * ce[1] + ce[2] * ce[2] + ce[3] * ce[3])
+         + dn * sqrt(ce[4] * ce[4] + ce[5] * ce[5] + ce[6] * ce[6]
+                     + 2.0 * (ce[7] * ce[7] + ce[8] * ce[8] + ce[9] * ce[9]));
 }
 
 /* Gather-form treecode for targets T against the source octree:
@@ -700,36 +720,35 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < T->ngroups; ++g) {
         int64_t s = T->goff[g], e = T->goff[g + 1];
-        local_state L = {{0, 0, 0}, 0, 0};
-        double co[10] = {0}, coabs[3] = {0, 0, 0};
-        if (loc) {
-            L = group_local(t, T, g, local_c, w2, amb_sorted ? amb_tol : 0.0);
-            if (L.use || L.amb)
-                for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
-                    int64_t b = T->far_id[q];
-                    if (!is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c)) continue;
-                    const double D[3] = {L.c[0] - rep[3 * b], L.c[1] - rep[3 * b + 1], L.c[2] - rep[3 * b + 2]};
-                    double ce[10];
-                    local_coeffs(D, nuB + 3 * b, ce);
-                    for (int k = 0; k < 10; ++k) co[k] += ce[k];
-                    coabs[0] += fabs(ce[0]);
-                    coabs[1] += sqrt(ce[1] * ce[1] + ce[2] * ce[2] + ce[3] * ce[3]);
-                    coabs[2] += sqrt(ce[4] * ce[4] + ce[5] * ce[5] + ce[6] * ce[6]
-                                     + 2.0 * (ce[7] * ce[7] + ce[8] * ce[8] + ce[9] * ce[9]));
-                }
-        }
+        local_frame L = {{0, 0, 0}, 0.0};
+        if (loc) L = group_frame(T, g);
         for (int64_t i = s; i < e; ++i) {
             const double* y = T->y + 3 * i;
             double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
-            double pwl[3] = {0, 0, 0};     /* local entries pair by pair (the other side of an ambiguous decision) */
             for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
                 int64_t b = T->far_id[q];
-                const int lq = (L.use || L.amb) && is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c);
-                if (lq && L.use && !L.amb) continue;     /* in the expansion */
+                /* a local entry: its term expanded about c_g when all its pairs clear the cut-off */
+                int use = 0, lamb = 0;
+                double ev[3] = {0, 0, 0}, evabs = 0.0;
+                if (loc && is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c)) {
+                    const double D[3] = {L.c[0] - rep[3 * b], L.c[1] - rep[3 * b + 1], L.c[2] - rep[3 * b + 2]};
+                    use = local_use(D, L.rho, w2, amb_sorted ? amb_tol : 0.0, &lamb);
+                    if (use || lamb) {
+                        double ce[10];
+                        local_coeffs(D, nuB + 3 * b, ce);
+                        const double dl[3] = {y[0] - L.c[0], y[1] - L.c[1], y[2] - L.c[2]};
+                        evabs = local_eval(op, ce, dl, ev);
+                    }
+                }
+                if (use && !lamb) {
+                    for (int k = 0; k < 3; ++k) acc[k] += ev[k];
+                    as += evabs;
+                    continue;
+                }
                 double d[3] = {y[0] - rep[3 * b], y[1] - rep[3 * b + 1], y[2] - rep[3 * b + 2]};
                 double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                 int amb_p = amb_sorted && ambiguous(r2, w2, amb_tol);
-                if (!keep_pair(r2, w2) && !amb_p) continue;
+                if (!keep_pair(r2, w2) && !amb_p && !lamb) continue;
                 double v[3] = {0, 0, 0};
                 if (op == OP_A) v[0] = term_A(d, r2, nuB + 3 * b);
                 else if (op == OP_G) term_G(d, r2, nuB + 3 * b, v);
@@ -741,36 +760,22 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
                     for (int k = 0; k < 3; ++k) v[k] += cr[k];
                     vn += sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
                 }
-                if (lq) {
-                    if (keep_pair(r2, w2)) for (int k = 0; k < 3; ++k) pwl[k] += v[k];
-                    if (L.use) continue;
+                if (lamb) {
+                    /* either side of the decision may be taken: bound their difference */
+                    const double kp = keep_pair(r2, w2) ? 1.0 : 0.0;
+                    ab += sqrt((ev[0] - kp * v[0]) * (ev[0] - kp * v[0]) + (ev[1] - kp * v[1]) * (ev[1] - kp * v[1])
+                               + (ev[2] - kp * v[2]) * (ev[2] - kp * v[2]));
+                    if (use) {
+                        for (int k = 0; k < 3; ++k) acc[k] += ev[k];
+                        as += evabs;
+                        continue;
+                    }
                 }
                 if (amb_p) ab += vn;
                 if (keep_pair(r2, w2)) {
                     for (int k = 0; k < 3; ++k) acc[k] += v[k];
                     as += vn;
                 }
-            }
-            if (L.use || L.amb) {
-                const double dl[3] = {y[0] - L.c[0], y[1] - L.c[1], y[2] - L.c[2]};
-                const double dn = sqrt(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
-                double ev[3] = {0, 0, 0}, evabs;
-                if (op == OP_A) {
-                    ev[0] = co[0] - (dl[0] * co[1] + dl[1] * co[2] + dl[2] * co[3]);
-                    evabs = coabs[0] + dn * coabs[1];
-                } else {
-                    double jd[3];
-                    sym_mul(co + 4, dl, jd);
-                    for (int k = 0; k < 3; ++k) ev[k] = co[1 + k] - jd[k];
-                    evabs = coabs[1] + dn * coabs[2];
-                }
-                if (L.use) {
-                    for (int k = 0; k < 3; ++k) acc[k] += ev[k];
-                    as += evabs;
-                }
-                if (L.amb)
-                    ab += sqrt((ev[0] - pwl[0]) * (ev[0] - pwl[0]) + (ev[1] - pwl[1]) * (ev[1] - pwl[1])
-                               + (ev[2] - pwl[2]) * (ev[2] - pwl[2]));
             }
             for (int64_t q = T->near_off[g]; q < T->near_off[g + 1]; ++q) {
                 int64_t b = T->near_id[q];
@@ -820,14 +825,14 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                                double* amb_sorted, double* abs_sorted, int far_order, double local_c) {
     int64_t nn = t->nnodes, ng = T->ngroups;
     const double w2 = eff_w2(w);
-    /* local expansions: per group its decision, S_g, D_g and the bounds of their terms */
+    /* local expansions: per group c_g, rho_g, S_g, D_g and the bounds of their terms */
     const int loc = local_c > 0.0 && far_order == 0;
-    local_state* LS = calloc((size_t)(ng > 0 ? ng : 1), sizeof(local_state));
+    local_frame* LS = calloc((size_t)(ng > 0 ? ng : 1), sizeof(local_frame));
     double* SD = calloc((size_t)(ng > 0 ? ng : 1) * 6, sizeof(double));   /* S, Dg[3], sum|s|, sum|s||delta| */
     if (loc) {
         #pragma omp parallel for schedule(dynamic, 16)
         for (int64_t g = 0; g < ng; ++g) {
-            LS[g] = group_local(t, T, g, local_c, w2, amb_sorted ? amb_tol : 0.0);
+            LS[g] = group_frame(T, g);
             double* sd = SD + 6 * g;
             for (int64_t i = T->goff[g]; i < T->goff[g + 1]; ++i) {
                 const double dl[3] = {T->y[3 * i] - LS[g].c[0], T->y[3 * i + 1] - LS[g].c[1],
@@ -868,19 +873,20 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         for (int64_t q = fcnt[b]; q < fcnt[b + 1]; ++q) {
             int64_t g = fg[q];
             int64_t s = T->goff[g], e = T->goff[g + 1];
-            const int lq = loc && (LS[g].use || LS[g].amb)
-                           && is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c);
+            /* a local entry: the transposed expansion when all its pairs clear the cut-off */
+            int use = 0, lamb = 0;
             double lv[3] = {0, 0, 0}, pw[3] = {0, 0, 0};
-            if (lq) {
+            if (loc && is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c)) {
                 const double D[3] = {LS[g].c[0] - rep[3 * b], LS[g].c[1] - rep[3 * b + 1],
                                      LS[g].c[2] - rep[3 * b + 2]};
+                use = local_use(D, LS[g].rho, w2, amb_sorted ? amb_tol : 0.0, &lamb);
                 const double* sd = SD + 6 * g;
                 local_adjoint(D, sd[0], sd + 1, lv);
-                if (LS[g].use) {
+                if (use) {
                     const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
                     for (int k = 0; k < 3; ++k) acc[k] += lv[k];
                     as += sd[4] / (4.0 * OR_PI * r2) + 2.0 * sd[5] / (4.0 * OR_PI * r2 * sqrt(r2));
-                    if (!LS[g].amb) continue;
+                    if (!lamb) continue;
                 }
             }
             for (int64_t i = s; i < e; ++i) {
@@ -893,9 +899,9 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                 double v[3];
                 term_AT(d, r2, s_sorted[i], v);
                 double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                if (lq) {
+                if (lamb) {
                     if (keep_pair(r2, w2)) for (int k = 0; k < 3; ++k) pw[k] += v[k];
-                    if (LS[g].use) continue;
+                    if (use) continue;
                 }
                 if (amb_p) ab += vn;
                 if (keep_pair(r2, w2)) {
@@ -914,7 +920,7 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
                     }
                 }
             }
-            if (lq && LS[g].amb)
+            if (lamb)
                 ab += sqrt((lv[0] - pw[0]) * (lv[0] - pw[0]) + (lv[1] - pw[1]) * (lv[1] - pw[1])
                            + (lv[2] - pw[2]) * (lv[2] - pw[2]));
         }

@@ -14,9 +14,11 @@ re-typing the oracle's formulas:
     which only halves;
   - the same for the transposed terms, seen at the source point;
   - the transpose: <A mu, s> = <mu, A^T s> exactly;
-  - the fallback: at a width w that reaches a group's nearest expanded node
-    the group sums those nodes pair by pair with the cut-off, so the result
-    equals the one without expansions, bit for bit;
+  - the fallback: an entry is expanded only when every pair of it clears
+    the cut-off, i.e. |c_g - x_B| - rho_g >= w (rho_g: the largest distance
+    of the group's targets from the centre c_g); at a wider w the entry is
+    summed pair by pair with the cut-off, so the result equals the one
+    without expansions, bit for bit;
   - against the direct sums on a cloud: the error stays within a small
     factor of the error without expansions.
 """
@@ -102,11 +104,12 @@ def test_local_operator_is_transposed_exactly(cloud20k):
 
 
 def test_groups_fall_back_to_pairs_at_wide_cutoffs():
-    """P0 to the cluster: box gap about 2.64, pair distances 2.70 to 2.75.
-    At w = 2.72 the cut-off reaches the expanded node: the cluster's group
-    sums P0 pair by pair with the cut-off (some pairs kept, some not), equal
-    bit for bit to the operator without expansions.  At w = 2.5 every pair
-    clears the cut-off and the expansion is used."""
+    """P0 to the cluster: |c_g - P0| = 2.713 and rho_g = 0.063, so the
+    entry's bound |c_g - P0| - rho_g is 2.650; pair distances 2.697 to
+    2.750.  At w = 2.71 the bound is below w: the cluster's group sums P0
+    pair by pair with the cut-off (four pairs kept, four not), equal bit for
+    bit to the operator without expansions.  At w = 2.5 the expansion is
+    used."""
     x, rng = _cloud(0.1)
     mu = np.zeros((9, 3))
     mu[0] = rng.standard_normal(3)
@@ -114,9 +117,9 @@ def test_groups_fall_back_to_pairs_at_wide_cutoffs():
     s[1:] = 1.0 + 0.3 * rng.standard_normal(8)
     t0, t1 = _structure(x, 0.0), _structure(x, 0.5)
     r = np.linalg.norm(x[1:] - x[0], axis=1)
-    assert (r < 2.72).any() and (r >= 2.72).any()
+    assert (r < 2.71).sum() == 4 and (r >= 2.71).sum() == 4
     for op, nu, rows in ((OP_A, mu, slice(1, 9)), (OP_G, mu, slice(1, 9)), (OP_AT, s, slice(0, 1))):
-        wide0, wide1 = t0.apply(op, nu, 2.72)[rows], t1.apply(op, nu, 2.72)[rows]
+        wide0, wide1 = t0.apply(op, nu, 2.71)[rows], t1.apply(op, nu, 2.71)[rows]
         assert np.abs(wide0).max() > 0.0
         assert np.array_equal(wide0, wide1), op
         assert not np.array_equal(t0.apply(op, nu, 2.5)[rows], t1.apply(op, nu, 2.5)[rows]), op

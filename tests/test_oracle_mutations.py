@@ -62,8 +62,8 @@ MUTATIONS = [
      "for (int k = 0; k < 3; ++k) far[k] += hd[k];",
      [lambda: dpins.test_far_error_order_of_the_transpose()]),
     ("local expansion: sign of A's first-order term",
-     "ev[0] = co[0] - (dl[0] * co[1] + dl[1] * co[2] + dl[2] * co[3]);",
-     "ev[0] = co[0] + (dl[0] * co[1] + dl[1] * co[2] + dl[2] * co[3]);",
+     "out[0] = ce[0] - (dl[0] * ce[1] + dl[1] * ce[2] + dl[2] * ce[3]);",
+     "out[0] = ce[0] + (dl[0] * ce[1] + dl[1] * ce[2] + dl[2] * ce[3]);",
      [lambda: lpins.test_local_error_order(OP_A)]),
     ("local expansion: factor of J's trace term",
      "const double diag = a == c ? 3.0 * dm : 0.0;",
@@ -73,9 +73,13 @@ MUTATIONS = [
      "out[k] = -S * D[k] / (4.0 * OR_PI * r3) + (3.0 * D[k] * dd - r2 * Dg[k]) / (4.0 * OR_PI * r5);",
      "out[k] = -S * D[k] / (4.0 * OR_PI * r3) - (3.0 * D[k] * dd - r2 * Dg[k]) / (4.0 * OR_PI * r5);",
      [lambda: lpins.test_local_error_order_of_the_transpose()]),
-    ("local expansion: the cut-off decision taken at w instead of w^2",
-     "L.use = any && w2 < gmin;",
-     "L.use = any && sqrt(w2) < gmin;",
+    ("local expansion: the cut-off bound compared with w^2 unsquared",
+     "return m > 0.0 && m2 >= w2;",
+     "return m > 0.0 && m >= w2;",
+     [lambda: lpins.test_groups_fall_back_to_pairs_at_wide_cutoffs()]),
+    ("local expansion: the cut-off bound without the group radius",
+     "const double m = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]) - rho;",
+     "const double m = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);",
      [lambda: lpins.test_groups_fall_back_to_pairs_at_wide_cutoffs()]),
 ]
 
