@@ -56,6 +56,12 @@ WORKLOAD = WORKLOADS[CONFIG_NAME]
 # A 18, A^T 18, G 31; A and G together 33 (they share d, r^2, rsqrt, r^-3 and d.mu: 16)
 FLOPS_A, FLOPS_AT, FLOPS_G, FLOPS_AG = 18, 18, 31, 33
 FLOPS_ITER = 2 * FLOPS_AG + FLOPS_AT               # A+G(mu), A^T(s), A+G(r) per iteration
+# per far entry expanded about its group's centre (local_theta > 0): the value
+# of A and G and the Jacobian of G at the centre (A+G), the transposed
+# expansion from the group's sums (A^T); an FMA counts two
+FLOPS_LOCAL_AG, FLOPS_LOCAL_AT = 88, 41
+FLOPS_LOCAL_ITER = 2 * FLOPS_LOCAL_AG + FLOPS_LOCAL_AT
+LOCAL_THETA = 0.5    # local expansions of far nodes about target groups (0 = off)
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
 # Variants solved once each after the timed region (name, tree parameters, timed solves):
 # the paper's own treecode as printed (Alg. 4 per target and per call, leaf size 1,
@@ -65,7 +71,9 @@ PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different mo
 # paper's theta = 0.5 (2.4e-2, 4.6e-2, 1.5e-1): the speed at the paper's accuracy.
 VARIANTS = [
     ("paper_alg4_per_target_leaf1_theta0.5", dict(theta=0.5, leaf_size=1, rep_mode=0, criterion=1), 1),
+    ("pairwise_far_field_theta0.5", dict(theta=0.5, local_theta=0.0), 3),
     ("group_lists_theta0.8", dict(theta=0.8), 3),
+    ("local_expansions_theta0.8", dict(theta=0.8, local_theta=0.5), 3),
     ("first_order_far_field_theta0.5", dict(theta=0.5, far_order=1), 2),
     ("first_order_far_field_theta0.8", dict(theta=0.8, far_order=1), 2),
 ]
@@ -244,7 +252,7 @@ def run_gpu(args):
 
     def step(prof: dict | None, classes=None):
         flush.zero_()
-        t = W.Tree(pts, theta=THETA)
+        t = W.Tree(pts, theta=THETA, local_theta=LOCAL_THETA)
         if prof is not None:
             t.profile(True, classes=classes)
         t.iterate(n_iter=N_ITER, w1=W1, w2=W2, out=mu)
@@ -252,7 +260,7 @@ def run_gpu(args):
             for k, (cnt, ms) in t.profile_read().items():
                 a, b = prof.get(k, (0, 0.0))
                 prof[k] = (a + cnt, b + ms)
-        stats = t.stats()
+        stats = t.stats() + t.local_stats()
         t.close()
         return stats
 
@@ -263,7 +271,7 @@ def run_gpu(args):
     # T_pre / T_main split on one untimed step (CUDA events)
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record(stream)
-    t = W.Tree(pts, theta=THETA)
+    t = W.Tree(pts, theta=THETA, local_theta=LOCAL_THETA)
     e1.record(stream)
     t.iterate(n_iter=N_ITER, w1=W1, w2=W2, out=mu)
     e2.record(stream)
@@ -289,7 +297,7 @@ def run_gpu(args):
     ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev_a.record(stream)
     for _ in range(args.steps):
-        far_pairs, near_pairs = step(prof, classes=["AG"])
+        far_pairs, near_pairs, local_entries, local_pairs = step(prof, classes=["AG"])
     ev_b.record(stream)
     torch.cuda.synchronize(dev)
     launches = W.kernel_launches() - launches0
@@ -307,11 +315,11 @@ def run_gpu(args):
     if not args.no_e2e:
         h_pts = torch.from_numpy(c.points).pin_memory()
         h_mu = torch.empty(n, 3, dtype=torch.float32).pin_memory()
-        W.orient(h_pts, out=h_mu, theta=THETA, n_iter=N_ITER, w1=W1, w2=W2)     # warm-up
+        W.orient(h_pts, out=h_mu, theta=THETA, n_iter=N_ITER, w1=W1, w2=W2, local_theta=LOCAL_THETA)  # warm-up
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            W.orient(h_pts, out=h_mu, theta=THETA, n_iter=N_ITER, w1=W1, w2=W2)
+            W.orient(h_pts, out=h_mu, theta=THETA, n_iter=N_ITER, w1=W1, w2=W2, local_theta=LOCAL_THETA)
         torch.cuda.synchronize(dev)
         dt = max_over_ranks(dist, time.perf_counter() - t0)
         e2e = {"value": whole_job_rate(world, N_ITER, args.steps, 1e3 * dt), "unit": "iter/s",
@@ -353,10 +361,12 @@ def run_gpu(args):
     peaks = read_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
-    flops_per_s = FLOPS_ITER * inter_per_op * N_ITER * args.steps * world / (ms / 1e3)
+    flops_iter = FLOPS_ITER * inter_per_op + FLOPS_LOCAL_ITER * local_entries
+    flops_per_s = flops_iter * N_ITER * args.steps * world / (ms / 1e3)
     g_launch, g_ms = prof.get("AG", (0, 0.0))
     g_avg_ms = g_ms / max(g_launch, 1)
-    g_achieved = FLOPS_AG * inter_per_op / (g_avg_ms / 1e3) / 1e12
+    flops_ag = FLOPS_AG * inter_per_op        # the gather's pair terms (the expanded entries run apart)
+    g_achieved = flops_ag / (g_avg_ms / 1e3) / 1e12
     shares = {k: round(v[1] / max(sum(x[1] for x in share_prof.values()), 1e-9), 4)
               for k, v in share_prof.items()}
     line = {
@@ -366,10 +376,13 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_points": n, "iterations_per_step": N_ITER,
+                   "theta": THETA, "local_theta": LOCAL_THETA,
                    "l2": "flushed before every step (256 MiB write, inside the timed region)",
                    "step": "tree build + 40 iterations"},
         "interactions_per_s": inter_per_iter * N_ITER * args.steps * world / (ms / 1e3),
         "interactions_per_iteration": inter_per_iter,
+        "local_entries_per_operator": local_entries,
+        "local_pairs_per_operator": local_pairs,
         "fp32_tflops": flops_per_s / 1e12,
         "fp32_peak_frac": flops_per_s / 1e12 / peak,
         "t_pre_ms": t_pre_ms, "t_main_ms": t_main_ms,
@@ -388,7 +401,7 @@ def run_gpu(args):
                      "peak_measured_fma_stream": fp32_measured,
                      "frac_of_measured": g_achieved / fp32_measured,
                      "avg_launch_ms": g_avg_ms, "launches": g_launch,
-                     "flops_per_launch": FLOPS_AG * inter_per_op},
+                     "flops_per_launch": flops_ag},
         "kernel_time_share": shares,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -405,6 +418,7 @@ def run_gpu(args):
 
 
 def main():
+    global CONFIG_NAME, WORKLOAD, LOCAL_THETA
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -416,9 +430,11 @@ def main():
                     help="skip the solves of the method's variants after the timed region")
     ap.add_argument("--config", default="union500k", choices=sorted(WORKLOADS),
                     help="workload (the default is the one the metric is quoted on)")
+    ap.add_argument("--local-theta", type=float, default=LOCAL_THETA,
+                    help="local expansions of far nodes about target groups (0 = off)")
     args = ap.parse_args()
-    global CONFIG_NAME, WORKLOAD
     CONFIG_NAME, WORKLOAD = args.config, WORKLOADS[args.config]
+    LOCAL_THETA = args.local_theta
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

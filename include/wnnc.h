@@ -102,6 +102,21 @@ typedef struct {
                               Sec. 4.5 and Sec. 6.3 name for precision control: the far-field
                               error falls as (h/R)^2 instead of h/R.  Other values, or
                               far_order 1 with rep_mode 0 or criterion 1: WNNC_EINVAL */
+    float local_theta; /* local expansions of the far field about each target group (criterion 0,
+                          rep_mode 1, far_order 0): a far node B whose box gap to a group's
+                          box exceeds the box's largest extent / local_theta is not summed
+                          against each target; its terms of A and G are expanded to first order
+                          about the group box centre c_g (value and gradient of A, value and
+                          Jacobian of G = -grad A, summed over those nodes once per group and
+                          evaluated at each target), and A^T takes the exact transpose
+                          (per entry, S_g gradPhi + HPhi D_g from the group's sum of s and of
+                          s (x_i - c_g)).  An entry is expanded only when every one of its pairs
+                          clears the cut-off (|c_g - x_B| - rho_g >= w, rho_g the group's
+                          radius about c_g); otherwise it is summed pair by pair.  The
+                          target-side counterpart of the expansions that Sec. 4.5 and Sec. 6.3
+                          name; its error is second order in (group extent / distance).
+                          0 = off (default); negative, non-finite, or > 0 with rep_mode 0,
+                          criterion 1 or far_order 1: WNNC_EINVAL */
 } wnnc_tree_params;
 
 /* Iteration parameters (Alg. 3; Sec. 5.1.1 defaults n = 40, w1 = 0.002, w2 = 0.016). */
@@ -211,8 +226,16 @@ wnnc_status wnnc_orient(const float* pts_host, int64_t n, const wnnc_tree_params
                         void* stream);
 
 /* Interaction counts of one on-surface operator evaluation: far (target, node)
- * pairs and near (target, source) pairs, cut-off ones included.  host out. */
+ * pairs and near (target, source) pairs summed pair by pair, cut-off ones
+ * included (far entries expanded about their group's centre are counted by
+ * wnnc_get_local_stats instead).  host out. */
 wnnc_status wnnc_get_stats(const wnnc_tree* tree, int64_t* far_pairs, int64_t* near_pairs);
+
+/* Far entries that the local expansions (local_theta > 0) evaluate once per
+ * target group instead of per target, and the (target, node) pairs they stand
+ * for; both 0 when local_theta = 0.  An entry that the cut-off reaches on a
+ * call is summed pair by pair on that call but still counted here.  host out. */
+wnnc_status wnnc_get_local_stats(const wnnc_tree* tree, int64_t* local_entries, int64_t* local_pairs);
 
 /*
  * Sizes of the tree (host out, any may be NULL): points, nodes, leaves,
@@ -245,6 +268,7 @@ wnnc_status wnnc_tree_walk_stats(const wnnc_tree* tree, int* stack_walk_groups, 
  *   node_depth  int32 [nnodes]
  *   node_nchild int32 [nnodes]   0 for leaves
  *   far_off     int32 [ngroups+1], far_id int32 [far_entries]  per group, ascending node id
+ *               (local_theta > 0: two ascending parts, see wnnc_tree_export_local)
  *   near_off    int32 [ngroups+1], near_rng int32 [near_ranges][2]  [start,end) point ranges
  *               (consecutive near leaves merged, then cut to at most 256 points)
  *   group_off   int32 [ngroups+1]  target group g = sorted points group_off[g]..group_off[g+1]-1
@@ -256,6 +280,13 @@ wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node
                              int32_t* node_count, int32_t* node_depth, int32_t* node_nchild,
                              int32_t* far_off, int32_t* far_id, int32_t* near_off,
                              int32_t* near_rng, int32_t* group_off, double* center_scale);
+
+/* With local_theta > 0 each group's far list holds first the entries summed
+ * pair by pair, then (from far_lsplit[g] on) the entries expanded about the
+ * group's centre, each part ascending by node id.  far_lsplit: int32
+ * [ngroups], host out (far_off[g + 1] for every group when local_theta = 0).
+ * WNNC_EINVAL if far_lsplit is NULL. */
+wnnc_status wnnc_tree_export_local(const wnnc_tree* tree, int32_t* far_lsplit);
 
 /*
  * Kernel timing (not in the paper; the tracing facility of this library).
@@ -276,7 +307,9 @@ enum {
     WNNC_PROF_SMALL = 6,     /* permutations, step length, axpy, WNNC update */
     WNNC_PROF_AG = 7,        /* fused treecode sums of A and G on one field (the default
                                 iteration: A(mu) with G(mu), A(r) with G(r)) */
-    WNNC_PROF_CLASSES = 8
+    WNNC_PROF_LOCAL = 8,     /* far entries expanded about their target group's centre
+                                (local_theta > 0): the terms of A and G, and of A^T */
+    WNNC_PROF_CLASSES = 9
 };
 wnnc_status wnnc_profile_enable(wnnc_tree* tree, int enable);
 /* Restrict the recording to the classes whose bit is set in mask (bit k:

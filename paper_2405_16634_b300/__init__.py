@@ -36,7 +36,7 @@ __all__ = ["Tree", "TreeParams", "IterParams", "WnncError", "winding_number", "W
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ECAPACITY",
           6: "ETIMEOUT"}
 SCHEDULES = {"linear": 0, "cosine": 1, "exponential": 2}
-PROF_CLASSES = ["moments", "A", "adj_far", "adj_node", "adj_near", "G", "small", "AG"]
+PROF_CLASSES = ["moments", "A", "adj_far", "adj_node", "adj_near", "G", "small", "AG", "local"]
 
 
 class WnncError(RuntimeError):
@@ -48,7 +48,7 @@ class WnncError(RuntimeError):
 class TreeParams(Structure):
     _fields_ = [("max_depth", c_int), ("leaf_size", c_int), ("theta", c_float),
                 ("rep_mode", c_int), ("moments_fp64", c_int), ("near_bf16", c_int), ("criterion", c_int),
-                ("far_order", c_int)]
+                ("far_order", c_int), ("local_theta", c_float)]
 
 
 class IterParams(Structure):
@@ -85,6 +85,8 @@ def lib():
     L.wnnc_eval_at.argtypes = [P, P, P, c_int64, c_float, c_int, P, P]
     L.wnnc_iterate.argtypes = [P, P, P, POINTER(IterParams), P, P]
     L.wnnc_get_stats.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
+    L.wnnc_get_local_stats.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
+    L.wnnc_tree_export_local.argtypes = [P, P]
     L.wnnc_tree_info.argtypes = [P] + [POINTER(c_int64)] * 7 + [POINTER(c_int)]
     L.wnnc_tree_export.argtypes = [P] + [P] * 11
     L.wnnc_tree_walk_stats.argtypes = [P, P, P]
@@ -113,7 +115,8 @@ def lib():
     L.wnnc_probe_fp32.restype = c_int
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
                  "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
-                 "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_tree_info",
+                 "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_get_local_stats", "wnnc_tree_info",
+                 "wnnc_tree_export_local",
                  "wnnc_tree_export", "wnnc_tree_walk_stats", "wnnc_profile_enable", "wnnc_profile_classes", "wnnc_profile_read",
                  "wnnc_profile_reset", "wnnc_sync_status", "wnnc_knn16", "wnnc_mlp_create",
                  "wnnc_mlp_free", "wnnc_mlp_set_params", "wnnc_mlp_get_params", "wnnc_mlp_forward",
@@ -213,12 +216,16 @@ class Tree:
 
     def __init__(self, points, theta: float = 0.5, leaf_size: int = 8, max_depth: int = 15,
                  rep_mode: int = 1, moments_fp64: bool = False, near_bf16: bool = False,
-                 criterion: int = 0, far_order: int = 0):
+                 criterion: int = 0, far_order: int = 0, local_theta: float = 0.0):
         """criterion 0: far decisions per target group on boxes, lists built once
         (default); 1: the paper's per-target test of Alg. 4 on every call
         (needs rep_mode 0; with leaf_size 1 it is Alg. 4 as printed).
         far_order 1: far nodes also carry the first-order Taylor terms of the
-        kernels about their centroid (rep_mode 1, criterion 0)."""
+        kernels about their centroid (rep_mode 1, criterion 0).
+        local_theta > 0: far nodes whose box gap to a target group exceeds the
+        group box's extent / local_theta are expanded to first order about the
+        group's centre instead of summed per target (rep_mode 1, criterion 0,
+        far_order 0; A^T stays the exact transpose)."""
         pts = points if isinstance(points, torch.Tensor) else torch.as_tensor(points)
         self.device = pts.device if pts.is_cuda else torch.device("cuda", torch.cuda.current_device())
         pts = _dev_f32(pts, (-1, 3), self.device)
@@ -229,6 +236,7 @@ class Tree:
         p.near_bf16 = int(bool(near_bf16))
         p.criterion = int(criterion)
         p.far_order = int(far_order)
+        p.local_theta = float(local_theta)
         self.params = p
         h = c_void_p()
         with torch.cuda.device(self.device):
@@ -310,10 +318,17 @@ class Tree:
 
     # -- inspection ----------------------------------------------------------
     def stats(self):
-        """(far pairs, near pairs) of one operator evaluation on the points."""
+        """(far pairs, near pairs) summed pair by pair in one operator evaluation
+        on the points."""
         f, nn = c_int64(), c_int64()
         _check(lib().wnnc_get_stats(self._h, ctypes.byref(f), ctypes.byref(nn)))
         return f.value, nn.value
+
+    def local_stats(self):
+        """(far entries expanded about their group's centre, the pairs they stand for)."""
+        e, pp = c_int64(), c_int64()
+        _check(lib().wnnc_get_local_stats(self._h, ctypes.byref(e), ctypes.byref(pp)))
+        return e.value, pp.value
 
     def info(self) -> dict:
         v = [c_int64() for _ in range(7)]
@@ -347,6 +362,9 @@ class Tree:
             "near_off", "near_rng", "group_off", "center_scale")]))
         a["far_id"] = a["far_id"][:inf["far_entries"]]
         a["near_rng"] = a["near_rng"][:inf["near_ranges"]]
+        a["far_lsplit"] = np.zeros(ng, np.int32)
+        if ng:
+            _check(lib().wnnc_tree_export_local(self._h, ptr(a["far_lsplit"])))
         return a
 
     def profile(self, enable: bool = True, classes=None):

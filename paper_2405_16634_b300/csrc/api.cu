@@ -111,6 +111,13 @@ static void alloc_workspace(Tree& t) {
         t.hnode0 = dalloc<float4>(nn);
         t.hnode1 = dalloc<float4>(nn);
     }
+    if (t.self.far_lsplit) {
+        t.dip_corr = dalloc<float4>(n);   // per-target terms of the expanded entries
+        t.node_abs = dalloc<float4>(nn);
+        t.local_rec = dalloc<float4>(2 * (size_t)nn);
+        t.gadj = dalloc<float4>(2 * (size_t)t.self.ngroups);
+        local_setup(t, alloc_stream());
+    }
 }
 
 // Read and clear the latched device error flags.
@@ -160,6 +167,10 @@ static void check_params(const wnnc_tree_params& p) {
     if (p.far_order != 0 && p.far_order != 1) fail(WNNC_EINVAL, "far_order must be 0 or 1");
     if (p.far_order == 1 && (p.rep_mode != 1 || p.criterion != 0))
         fail(WNNC_EINVAL, "far_order 1 needs rep_mode 1 and criterion 0");
+    if (!(p.local_theta >= 0.f) || !std::isfinite(p.local_theta))
+        fail(WNNC_EINVAL, "local_theta must be finite and >= 0");
+    if (p.local_theta > 0.f && (p.rep_mode != 1 || p.criterion != 0 || p.far_order != 0))
+        fail(WNNC_EINVAL, "local_theta > 0 needs rep_mode 1, criterion 0 and far_order 0");
 }
 
 static void check_w(float w) {
@@ -190,6 +201,7 @@ wnnc_status wnnc_tree_params_default(wnnc_tree_params* p) {
     p->near_bf16 = 0;
     p->criterion = 0;
     p->far_order = 0;
+    p->local_theta = 0.f;
     return WNNC_OK;
 }
 
@@ -379,6 +391,14 @@ wnnc_status wnnc_get_stats(const wnnc_tree* tree, int64_t* far_pairs, int64_t* n
     });
 }
 
+wnnc_status wnnc_get_local_stats(const wnnc_tree* tree, int64_t* local_entries, int64_t* local_pairs) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (local_entries) *local_entries = t.self.local_entries;
+        if (local_pairs) *local_pairs = t.self.local_pairs;
+    });
+}
+
 wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, int64_t* nleaves,
                            int64_t* ngroups, int64_t* far_entries, int64_t* near_ranges,
                            int64_t* tnear_entries, int* depth) {
@@ -428,6 +448,18 @@ wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node
             for (int k = 0; k < 3; ++k) center_scale[k] = t.center[k];
             center_scale[3] = t.scale;
         }
+    });
+}
+
+wnnc_status wnnc_tree_export_local(const wnnc_tree* tree, int32_t* far_lsplit) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (!far_lsplit) fail(WNNC_EINVAL, "far_lsplit is NULL");
+        WNNC_CUDA(cudaDeviceSynchronize());
+        const TargetSet& S = t.self;
+        if (S.ngroups == 0) return;
+        const int* src = S.far_lsplit ? S.far_lsplit : S.far_off + 1;
+        WNNC_CUDA(cudaMemcpy(far_lsplit, src, sizeof(int) * S.ngroups, cudaMemcpyDeviceToHost));
     });
 }
 

@@ -147,11 +147,18 @@ struct TargetSet {
     float4* gbl = nullptr;        // the same boxes in the group's frame, rounded outward
     float4* gbh = nullptr;
     int* far_off = nullptr;       // [ngroups+1]
-    int* far_id = nullptr;        // node ids, ascending per group
+    int* far_id = nullptr;        // node ids per group: summed pair by pair, then (from
+                                  // far_lsplit[g] on) expanded about the group centre;
+                                  // ascending within each part
+    int* far_lsplit = nullptr;    // [ngroups] first expanded entry of each group (local_theta > 0)
+    float4* gctr = nullptr;       // [ngroups] expansion centre in the group's frame, and the
+                                  // group's radius about it (w), rounded up
     int* near_off = nullptr;      // [ngroups+1]
     int2* near_rng = nullptr;     // merged [start,end) source ranges, at most kMaxRange long
     int64_t far_entries = 0, near_ranges = 0;
     int64_t far_pairs = 0, near_pairs = 0;
+    int64_t local_entries = 0;    // far entries expanded about the group centre (local_theta > 0)
+    int64_t local_pairs = 0;      // the pairs those entries stand for (not in far_pairs)
     // how the list traversal ran: groups that a first-in first-out walk
     // finished as stack walks; whether every group ran again as a stack walk
     // with the larger buffer
@@ -267,7 +274,13 @@ struct Tree {
     // first-order far field (far_order 1)
     float4* mom_dip = nullptr;    // per node 2 float4: (Sxx, Syy, Szz, Sxy), (Sxz, Syz, tr S, 0) of mu
     float4* mom_dip_r = nullptr;  // the same of the step direction r
-    float4* dip_corr = nullptr;   // per sorted target: first-order far terms (G x, y, z, A), sum units
+    float4* dip_corr = nullptr;   // per sorted target: first-order far terms (G x, y, z, A), sum units,
+                                  // or the terms of the expanded far entries (local_theta > 0)
+    // local expansions (local_theta > 0)
+    float4* node_abs = nullptr;   // per node: point centroid in normalised coordinates (float)
+    float4* local_rec = nullptr;  // per node, 32 bytes, rebuilt per call: (centroid, M_x), (M_y, M_z, 0, 0)
+    int* tfar_grp = nullptr;      // per transposed far entry: its group, bit 31 set when expanded
+    float4* gadj = nullptr;       // per group, rebuilt per adjoint call: (c_g, rho_g), (D, S)
     float4* contrib_h0 = nullptr; // per far entry: sum s HPhi, (xx, yy, zz, -) and (xy, xz, yz, -)
     float4* contrib_h1 = nullptr;
     float4* hnode0 = nullptr;     // per node: the entries' sums of s HPhi (same two parts)
@@ -298,6 +311,10 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s);
 // self = the tree's own points as targets (groups cut at Morton jumps; the
 // tree's sorted keys, coordinates and permutation `self_perm` are reused);
 // otherwise fixed 32-target groups.
+// Per-node data of the local expansions (local_theta > 0): the absolute
+// centroids, computed once after the build.
+void local_setup(Tree& t, cudaStream_t s);
+
 void build_target_set(const Tree& t, TargetSet& ts, const double* yn_unsorted, int64_t m, bool self,
                       cudaStream_t s, const int64_t* self_perm = nullptr);
 void free_target_set(TargetSet& ts);

@@ -285,7 +285,12 @@ struct GatherArgs {
     const int* nstart;        // first sorted point of each node
     const int* ncount;        // points of each node
     int* err_flag;            // device error flags (a walk stack overflow sets kErrCapacity)
-    const float4* dip_corr;   // far_order 1: per sorted target, the first-order far terms (G x,y,z, A)
+    const float4* dip_corr;   // per sorted target, far terms added in the epilogue (G x,y,z, A): the
+                              // first-order terms (far_order 1) or the local expansions (local_theta > 0)
+    const int* far_off;       // far list offsets per group
+    const int* lsplit;        // local_theta > 0: first expanded far entry of each group
+    const float4* gctr;       //   the expansion centre in the group's frame and the group's radius
+    const float4* lrec;       //   per node (centroid, M_x), (M_y, M_z, 0, 0) of this call's field
 };
 
 // Accumulators: (x, y, z) holds the A / A^T sum, or for G the sum of
@@ -769,6 +774,181 @@ __global__ void k_gather_finalize(GatherArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Far entries expanded about the target group's centre (local_theta > 0).
+// One warp per target group (kLocalWarps groups per block); the lanes take
+// the group's expanded entries [lsplit[g], far_off[g + 1]) two at a time
+// (entries base + lane and base + 32 + lane), the next two nodes' 32-byte
+// records (centroid and moment, one sector) read while these are summed.
+// With E = x_B - c_g (group frame) and M the node's moment, in the units of
+// the gather's sums (4 pi times the operator), each entry adds the value of
+// A, the value of G and the Jacobian of G at c_g:
+//   a = (E.M)/r^3,  g = M/r^3 - 3 (E.M) E/r^5,
+//   J = 3 (M E^T + E M^T + (E.M) I)/r^5 - 15 (E.M) E E^T/r^7,
+// so that a target at c_g + d gets A = a - d.g and G = g + J d (G = -grad A,
+// first-order Taylor expansion of both about c_g).  When both entries of a
+// lane pass, their terms run in the two halves of paired FP32 instructions.
+// An entry whose pairs may straddle the cut-off (|E| - rho_g < w) is queued
+// and summed pair by pair with the cut-off instead (from the node's exact
+// cell-relative data), every lane taking one target.  Each target's result
+// goes to corr (G x, y, z, A), which the gather's epilogue adds.
+// ---------------------------------------------------------------------------
+constexpr int kLocalWarps = 4;
+
+// Node centroids in normalised coordinates (cell centre + offset, rounded to
+// float): the expansions need them to about 1e-7 only, far from the group.
+__global__ void k_node_abs(int nn, const float4* ncell, const float4* ncent, float4* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nn) return;
+    const float4 c = ncell[b], d = ncent[b];
+    out[b] = make_float4(c.x + d.x, c.y + d.y, c.z + d.z, 0.f);
+}
+
+// Per node one 32-byte record of the centroid and this call's moment.
+__global__ void k_local_pack(int nn, const float4* nabs, const float4* mom, float4* rec) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nn) return;
+    const float4 x = nabs[b], m = mom[b];
+    rec[2 * b] = make_float4(x.x, x.y, x.z, m.x);
+    rec[2 * b + 1] = make_float4(m.y, m.z, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// The expansion accumulators of one lane: two halves per coefficient (added
+// at the end), (a, g_x, g_y, g_z, J_xx, J_yy, J_zz, J_xy, J_xz, J_yz).
+struct LocalAcc {
+    float2 c[10];
+};
+
+// One or two entries' terms (halves .x, .y; a half with keep = 0 adds nothing).
+template <bool kG>
+__device__ __forceinline__ void local_terms(const float2& ex, const float2& ey, const float2& ez, const float2& ir,
+                                            const float2& mx, const float2& my, const float2& mz, LocalAcc& L) {
+    const float2 ir2 = __fmul2_rn(ir, ir), ir3 = __fmul2_rn(ir2, ir), ir5 = __fmul2_rn(ir3, ir2);
+    float2 em = __fmul2_rn(ez, mz);
+    em = __ffma2_rn(ey, my, em);
+    em = __ffma2_rn(ex, mx, em);
+    const float2 emr5 = __fmul2_rn(em, ir5);
+    const float2 k3n = __fmul2_rn(emr5, f2(-3.f));                  // -3 (E.M)/r^5
+    L.c[0] = __ffma2_rn(em, ir3, L.c[0]);
+    L.c[1] = __ffma2_rn(k3n, ex, __ffma2_rn(mx, ir3, L.c[1]));
+    L.c[2] = __ffma2_rn(k3n, ey, __ffma2_rn(my, ir3, L.c[2]));
+    L.c[3] = __ffma2_rn(k3n, ez, __ffma2_rn(mz, ir3, L.c[3]));
+    if (kG) {
+        const float2 t3 = __fmul2_rn(ir5, f2(3.f));
+        const float2 t15n = __fmul2_rn(__fmul2_rn(emr5, ir2), f2(-15.f));   // -15 (E.M)/r^7
+        const float2 vx = __fmul2_rn(t15n, ex), vy = __fmul2_rn(t15n, ey), vz = __fmul2_rn(t15n, ez);
+        L.c[4] = __ffma2_rn(vx, ex, __ffma2_rn(t3, __ffma2_rn(__fadd2_rn(mx, mx), ex, em), L.c[4]));
+        L.c[5] = __ffma2_rn(vy, ey, __ffma2_rn(t3, __ffma2_rn(__fadd2_rn(my, my), ey, em), L.c[5]));
+        L.c[6] = __ffma2_rn(vz, ez, __ffma2_rn(t3, __ffma2_rn(__fadd2_rn(mz, mz), ez, em), L.c[6]));
+        L.c[7] = __ffma2_rn(vx, ey, __ffma2_rn(t3, __ffma2_rn(mx, ey, __fmul2_rn(my, ex)), L.c[7]));
+        L.c[8] = __ffma2_rn(vx, ez, __ffma2_rn(t3, __ffma2_rn(mx, ez, __fmul2_rn(mz, ex)), L.c[8]));
+        L.c[9] = __ffma2_rn(vy, ez, __ffma2_rn(t3, __ffma2_rn(my, ez, __fmul2_rn(mz, ey)), L.c[9]));
+    }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(32 * kLocalWarps) k_local_ag(GatherArgs A, float4* corr) {
+    constexpr bool kG = OP == kOpG || OP == kOpAG;
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ int qb_all[kLocalWarps][32];                // queued entries' nodes
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kLocalWarps + wl;
+    if (g >= A.ngroups) return;
+    int* qb = qb_all[wl];
+    const int i0 = A.goff[g], gsize = A.goff[g + 1] - i0;
+    const float4 o = A.tgorig[g];
+    const float4 cg = A.gctr[g];
+    const int64_t it = (int64_t)i0 + lane;
+    const float4 tl = lane < gsize ? shift(A.tcorig[it >> 5], o, A.tpos[it]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int w0 = A.lsplit[g], w1 = A.far_off[g + 1];
+    LocalAcc L;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) L.c[q] = make_float2(0.f, 0.f);
+    float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);           // this lane's target: queued pair sums (G, A)
+    int nq = 0;                                             // entries queued
+    // the queued entries' pair terms at this lane's target, with the cut-off
+    auto flush = [&]() {
+        for (int k = 0; k < nq; ++k) {
+            const int b = qb[k];
+            const float4 p = shift(A.ncell[b], o, A.nrep[b]), m = A.nmom[b];
+            const float dx = p.x - tl.x, dy = p.y - tl.y, dz = p.z - tl.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ir = r2 >= A.w2 ? rsqrtf(r2) : 0.f;
+            const float ir2 = ir * ir, ir3 = ir2 * ir;
+            const float dm = fmaf(dx, m.x, fmaf(dy, m.y, dz * m.z));
+            const float k5 = 3.f * (dm * ir2) * ir3;
+            fs.w = fmaf(dm, ir3, fs.w);
+            fs.x += fmaf(m.x, ir3, -k5 * dx);
+            fs.y += fmaf(m.y, ir3, -k5 * dy);
+            fs.z += fmaf(m.z, ir3, -k5 * dz);
+        }
+        __syncwarp();
+        nq = 0;
+    };
+    auto queue = [&](bool fall, int b) {
+        const unsigned fm = __ballot_sync(kFull, fall);
+        if (!fm) return;
+        const int nf = __popc(fm);
+        if (nq + nf > 32) flush();
+        if (fall) qb[nq + __popc(fm & ((1u << lane) - 1u))] = b;
+        nq += nf;
+        __syncwarp();
+    };
+    // node records one step ahead, node ids two steps ahead
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+    int ia = 0, ib = 0, na = 0, nb = 0;
+    if (w0 + lane < w1) { ia = A.far_id[w0 + lane]; a0 = A.lrec[2 * ia]; a1 = A.lrec[2 * ia + 1]; }
+    if (w0 + 32 + lane < w1) { ib = A.far_id[w0 + 32 + lane]; b0 = A.lrec[2 * ib]; b1 = A.lrec[2 * ib + 1]; }
+    if (w0 + 64 + lane < w1) na = A.far_id[w0 + 64 + lane];
+    if (w0 + 96 + lane < w1) nb = A.far_id[w0 + 96 + lane];
+    for (int base = w0; base < w1; base += 64) {
+        const int ea = base + lane, eb = ea + 32;
+        const bool va = ea < w1, vb = eb < w1;
+        const float2 ex = __fadd2_rn(make_float2(a0.x, b0.x), f2(-(o.x + cg.x)));
+        const float2 ey = __fadd2_rn(make_float2(a0.y, b0.y), f2(-(o.y + cg.y)));
+        const float2 ez = __fadd2_rn(make_float2(a0.z, b0.z), f2(-(o.z + cg.z)));
+        const float2 mx = make_float2(a0.w, b0.w), my = make_float2(a1.x, b1.x), mz = make_float2(a1.y, b1.y);
+        const int ca = ia, cb = ib;
+        if (ea + 64 < w1) { ia = na; a0 = A.lrec[2 * ia]; a1 = A.lrec[2 * ia + 1]; }
+        if (eb + 64 < w1) { ib = nb; b0 = A.lrec[2 * ib]; b1 = A.lrec[2 * ib + 1]; }
+        if (ea + 128 < w1) na = A.far_id[ea + 128];
+        if (eb + 128 < w1) nb = A.far_id[eb + 128];
+        float2 r2 = __fmul2_rn(ez, ez);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ex, ex, r2);
+        float2 ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 bound = __ffma2_rn(r2, ir, f2(-cg.w));     // |E| - rho_g
+        const bool oka = va && bound.x > 0.f && bound.x * bound.x >= A.w2;
+        const bool okb = vb && bound.y > 0.f && bound.y * bound.y >= A.w2;
+        // a half that is invalid or queued adds nothing (1/r = 0 zeroes each of its terms)
+        ir = make_float2(oka ? ir.x : 0.f, okb ? ir.y : 0.f);
+        local_terms<kG>(ex, ey, ez, ir, mx, my, mz, L);
+        queue(va && !oka, ca);
+        queue(vb && !okb, cb);
+    }
+    if (nq) flush();
+    float k[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        k[q] = L.c[q].x + L.c[q].y;
+        if (q < 4 || kG) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) k[q] += __shfl_xor_sync(kFull, k[q], d);
+        }
+    }
+    const float dx = tl.x - cg.x, dy = tl.y - cg.y, dz = tl.z - cg.z;
+    float4 f = fs;
+    f.w += k[0] - fmaf(dx, k[1], fmaf(dy, k[2], dz * k[3]));
+    if (kG) {
+        f.x += k[1] + fmaf(k[4], dx, fmaf(k[7], dy, k[8] * dz));
+        f.y += k[2] + fmaf(k[7], dx, fmaf(k[5], dy, k[9] * dz));
+        f.z += k[3] + fmaf(k[8], dx, fmaf(k[9], dy, k[6] * dz));
+    }
+    if (lane < gsize) corr[i0 + lane] = f;
+}
+
+// ---------------------------------------------------------------------------
 // The paper's treecode, Alg. 4 per target (tree parameter criterion = 1).
 // One warp per target group, one target per lane, in the group's frame.
 // Each lane walks the octree from the root on its own stack: node B is far
@@ -874,6 +1054,16 @@ struct AdjArgs {
     const float4* hnode1;     //   and (xy, xz, yz, -)
     float4* contrib_h0;       // the same per far entry (k_adj_far_dip)
     float4* contrib_h1;
+    const int* far_off;       // far list offsets per group
+    const int* lsplit;        // local_theta > 0: first expanded far entry of each group
+    const float4* gctr;       //   the expansion centre in the group's frame and the group's radius
+    const float4* nabs;       //   per node the centroid in normalised coordinates
+    int ngroups;
+    int nnodes;
+    const int* tfar_off;      // transposed far lists (node -> entries)
+    const int* tfar_ent;
+    const int* tfar_grp;      //   the entries' groups, bit 31 set when expanded
+    float4* gadj;             //   per group (c_g, rho_g), (D, S), normalised coordinates
 };
 
 // Adjoint terms s_i gradPhi(x_i - x) = s_i (x - x_i) / r^3 at x = p from a
@@ -974,6 +1164,130 @@ __global__ void WNNC_ADJ_BOUNDS k_adj_far(AdjArgs A) {
         if (v0) A.contrib[e0] = make_float4(ax.x, ay.x, az.x, 0.f);
         if (v1) A.contrib[e1] = make_float4(ax.y, ay.y, az.y, 0.f);
     }
+}
+
+// Expanded far entries of the adjoint (local_theta > 0), the transpose of
+// k_local_ag's expansion: with E = x_B - c_g, S = sum_i s_i and
+// D = sum_i s_i (x_i - c_g) over group g, entry (g, B) adds to node B
+//   S E/r^3 + (3 E (E.D) - r^2 D)/r^5
+// (first order in x_i - c_g of sum_i s_i (x_B - x_i)/|x_B - x_i|^3), unless
+// its pairs may straddle the cut-off (|E| - rho_g < w): then its pairs.
+// k_local_groups writes each group's (c_g, rho_g), (D, S); the node gather
+// evaluates the expanded entries as it meets them.
+__global__ void k_local_groups(AdjArgs A) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= A.ngroups) return;
+    const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
+    const float4 o = A.gorig[g];
+    const float4 cg = A.gctr[g];
+    const int64_t i = (int64_t)i0 + lane;
+    const float4 p = lane < cnt_t ? shift(A.corig[i >> 5], o, A.pos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float sv = lane < cnt_t ? A.sv[i] : 0.f;
+    float sS = sv, sx = sv * (p.x - cg.x), sy = sv * (p.y - cg.y), sz = sv * (p.z - cg.z);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        sS += __shfl_xor_sync(0xffffffffu, sS, d);
+        sx += __shfl_xor_sync(0xffffffffu, sx, d);
+        sy += __shfl_xor_sync(0xffffffffu, sy, d);
+        sz += __shfl_xor_sync(0xffffffffu, sz, d);
+    }
+    if (lane == 0) {
+        A.gadj[2 * g] = make_float4(o.x + cg.x, o.y + cg.y, o.z + cg.z, cg.w);
+        A.gadj[2 * g + 1] = make_float4(sx, sy, sz, sS);
+    }
+}
+
+// The pairs of one expanded entry (g, b) whose pairs may straddle the cut-off,
+// in the group's frame from the exact cell-relative data.
+__device__ __noinline__ float4 local_entry_pairs(const AdjArgs& A, int g, int b) {
+    const int i0 = A.goff[g], i1 = A.goff[g + 1];
+    const float4 o = A.gorig[g];
+    const float4 xb = shift(A.ncell[b], o, A.ncent[b]);
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    for (int i = i0; i < i1; ++i) {
+        const float4 x = shift(A.corig[i >> 5], o, A.pos[i]);
+        const float dx = xb.x - x.x, dy = xb.y - x.y, dz = xb.z - x.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float ir = r2 >= A.w2 ? rsqrtf(r2) : 0.f;
+        const float q = A.sv[i] * (ir * ir * ir);
+        cx = fmaf(q, dx, cx);
+        cy = fmaf(q, dy, cy);
+        cz = fmaf(q, dz, cz);
+    }
+    return make_float4(cx, cy, cz, 0.f);
+}
+
+// The node gather with expanded entries: one warp per node, lanes over the
+// node's transposed entries kLocalGathers at a time (loads first, then sums);
+// an entry summed pair by pair reads its contrib, an expanded one its group's
+// record.
+constexpr int kLocalGathers = 4;
+__global__ void k_adj_node_local(AdjArgs A, float4* vnode) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= A.nnodes) return;
+    const float4 xb = A.nabs[b];
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    const int q1 = A.tfar_off[b + 1];
+    for (int q = A.tfar_off[b] + lane; q < q1; q += 32 * kLocalGathers) {
+        int e[kLocalGathers], gg[kLocalGathers];
+#pragma unroll
+        for (int u = 0; u < kLocalGathers; ++u) {
+            const bool v = q + 32 * u < q1;
+            e[u] = v ? A.tfar_ent[q + 32 * u] : -1;
+            gg[u] = v ? A.tfar_grp[q + 32 * u] : 0;
+        }
+        float4 c0[kLocalGathers], c1[kLocalGathers];
+#pragma unroll
+        for (int u = 0; u < kLocalGathers; ++u) {
+            c0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            c1[u] = c0[u];
+            if (e[u] >= 0) {
+                if (gg[u] < 0) {
+                    const int g = gg[u] & 0x7fffffff;
+                    c0[u] = A.gadj[2 * g];
+                    c1[u] = A.gadj[2 * g + 1];
+                } else {
+                    c0[u] = A.contrib[e[u]];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLocalGathers; ++u) {
+            if (e[u] >= 0 && gg[u] < 0) {
+                const float ex = xb.x - c0[u].x, ey = xb.y - c0[u].y, ez = xb.z - c0[u].z;
+                const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                const float ir = rsqrtf(r2);
+                const float bound = fmaf(r2, ir, -c0[u].w);
+                if (bound > 0.f && bound * bound >= A.w2) {
+                    const float4 D = c1[u];
+                    const float ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
+                    const float ed3 = 3.f * fmaf(ex, D.x, fmaf(ey, D.y, ez * D.z));
+                    const float sr = D.w * ir3;
+                    ax += fmaf(sr, ex, fmaf(ed3, ex, -r2 * D.x) * ir5);
+                    ay += fmaf(sr, ey, fmaf(ed3, ey, -r2 * D.y) * ir5);
+                    az += fmaf(sr, ez, fmaf(ed3, ez, -r2 * D.z) * ir5);
+                } else {
+                    const float4 c = local_entry_pairs(A, gg[u] & 0x7fffffff, b);
+                    ax += c.x;
+                    ay += c.y;
+                    az += c.z;
+                }
+            } else {
+                ax += c0[u].x;
+                ay += c0[u].y;
+                az += c0[u].z;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    if (lane == 0) vnode[b] = make_float4(ax, ay, az, 0.f);
 }
 
 // One warp per node; lanes take the node's entries (consecutive slots of the
@@ -1739,6 +2053,9 @@ GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_a
     a.nstart = t.node_start;
     a.ncount = t.node_count;
     a.err_flag = t.err_flag;
+    a.far_off = ts.far_off;
+    a.lsplit = ts.far_lsplit;
+    a.gctr = ts.gctr;
     return a;
 }
 
@@ -1790,6 +2107,16 @@ AdjArgs adj_args(const Tree& t, float w) {
     a.fast2 = fast_radius2(w);
     a.gbl = S.gbl;
     a.gbh = S.gbh;
+    a.far_off = S.far_off;
+    a.lsplit = S.far_lsplit;
+    a.gctr = S.gctr;
+    a.nabs = t.node_abs;
+    a.ngroups = S.ngroups;
+    a.nnodes = t.nnodes;
+    a.tfar_off = t.tfar_off;
+    a.tfar_ent = t.tfar_ent;
+    a.tfar_grp = t.tfar_grp;
+    a.gadj = t.gadj;
     return a;
 }
 
@@ -1927,6 +2254,29 @@ static void far_dipole(Tree& t, const TargetSet& ts, const float4* mdip, GatherA
 }
 
 
+// Far terms of the entries expanded about each target group's centre
+// (local_theta > 0), stored per target in corr and added by the gather's
+// epilogue; a's moments must be those of the field summed.  The nodes'
+// centroids and this field's moments are packed first into one 32-byte
+// record per node.
+template <int OP>
+static void local_far(Tree& t, const TargetSet& ts, GatherArgs& a, float4* corr, cudaStream_t s) {
+    if (!ts.far_lsplit || ts.ngroups == 0) return;
+    ProfScope ps(&t.prof, WNNC_PROF_LOCAL, s);
+    k_local_pack<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.nnodes, t.node_abs, a.nmom, t.local_rec);
+    WNNC_LAUNCH_CHECK();
+    a.lrec = t.local_rec;
+    k_local_ag<OP><<<ceil_div(ts.ngroups, kLocalWarps), 32 * kLocalWarps, 0, s>>>(a, corr);
+    WNNC_LAUNCH_CHECK();
+    a.dip_corr = corr;
+}
+
+void local_setup(Tree& t, cudaStream_t s) {
+    if (t.nnodes == 0) return;
+    k_node_abs<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.nnodes, t.node_cell, t.node_cent, t.node_abs);
+    WNNC_LAUNCH_CHECK();
+}
+
 void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     const float s2 = (float)(t.scale * t.scale);
     perm_in_vec(t, mu, s2, t.mu_a, s);
@@ -1938,6 +2288,7 @@ void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     }
     a.sval = t.mu_a;
     a.out = out;
+    local_far<kOpA>(t, t.self, a, t.dip_corr, s);
     launch_gather<kOpA, kEpiStoreW>(t, a, s);
 }
 
@@ -1953,6 +2304,7 @@ void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     a.sval = t.mu_a;
     a.out = out;
     a.scale = (float)t.scale;
+    local_far<kOpG>(t, t.self, a, t.dip_corr, s);
     launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
 }
 
@@ -1979,8 +2331,16 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
             }
             WNNC_LAUNCH_CHECK();
         }
+        if (a.lsplit) {
+            // each group's record for its expanded entries
+            ProfScope ps(&t.prof, WNNC_PROF_LOCAL, s);
+            k_local_groups<<<ceil_div((int64_t)t.self.ngroups * 32, kTB), kTB, 0, s>>>(a);
+            WNNC_LAUNCH_CHECK();
+        }
         ProfScope ps(&t.prof, WNNC_PROF_ADJ_NODE, s);
-        if (dip) {
+        if (a.lsplit) {
+            k_adj_node_local<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);
+        } else if (dip) {
             // the node sums of V and H, pushed down in the near kernel's epilogue
             k_adj_node3<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(
                 t.nnodes, t.tfar_off, t.tfar_ent, t.contrib, t.contrib_h0, t.contrib_h1, t.vnode, t.hnode0, t.hnode1);
@@ -2079,6 +2439,11 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     a.sval = t.mu_a;
     a.out = out;
     a.scale = (float)t.scale;
+    if (Q.far_lsplit) {
+        qcorr = dalloc<float4>((size_t)m);
+        if (grad) local_far<kOpG>(t, Q, a, qcorr, s);
+        else local_far<kOpA>(t, Q, a, qcorr, s);
+    }
     if (grad) launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
     else launch_gather<kOpA, kEpiStoreW>(t, a, s);
     WNNC_CUDA(cudaStreamSynchronize(s));
@@ -2148,6 +2513,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             a.s_out = t.s_s;
             a.partial = pE;
             a.g_out = t.g_mu;
+            local_far<kOpAG>(t, S, a, t.dip_corr, s);
             launch_gather<kOpAG, kEpiResidualAG>(t, a, s);
             // r = A^T s
             adjoint_exact(t, t.s_s, w, nullptr, t.r_s, prr, s);
@@ -2162,6 +2528,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             b.sval = t.r_s;
             b.partial = pqq;
             b.g_out = t.g_r;
+            local_far<kOpAG>(t, S, b, t.dip_corr, s);
             launch_gather<kOpAG, kEpiNormSqAG>(t, b, s);
             {
                 ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
@@ -2186,6 +2553,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             a.sval = mu;
             a.s_out = t.s_s;
             a.partial = pE;
+            local_far<kOpA>(t, S, a, t.dip_corr, s);
             launch_gather<kOpA, kEpiResidual>(t, a, s);
             // r = A^T s
             if (rep_mode == 1) {
@@ -2211,6 +2579,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             b.nmom = mom_r;
             b.sval = t.r_s;
             b.partial = pqq;
+            local_far<kOpA>(t, S, b, t.dip_corr, s);
             launch_gather<kOpA, kEpiNormSq>(t, b, s);
             {
                 ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
@@ -2246,6 +2615,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             g.mu_out = mu_alt;
             g.area = t.area_s;
             g.rescale_mode = p.rescale;
+            local_far<kOpG>(t, S, g, t.dip_corr, s);
             launch_gather<kOpG, kEpiRescale>(t, g, s);
             std::swap(mu, mu_alt);
         }

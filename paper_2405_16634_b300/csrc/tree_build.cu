@@ -369,28 +369,42 @@ __global__ void k_chunk_frames(const double* ys, int64_t m, int nchunks, float4*
                              (float)(ys[3 * i + 2] - o[2]), 0.f);
 }
 
-// Warp per group: bounding box and dyadic origin, and the box in the group's
-// frame rounded outward to float (it contains every target of the group).
+// Warp per group: bounding box and dyadic origin, the box in the group's
+// frame rounded outward to float (it contains every target of the group), and
+// for the local expansions (gctr, may be null) the box centre in that frame
+// with the group's radius about it, rounded up.
 __global__ void k_group_boxes(const double* ys, const int* goff, int ng, double* glo, double* ghi,
-                              float4* gorig, float4* gbl, float4* gbh) {
+                              float4* gorig, float4* gbl, float4* gbh, float4* gctr) {
     int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (g >= ng) return;
     int64_t i = (int64_t)goff[g] + lane;
     bool valid = i < goff[g + 1];
-    double o[3], bl[3], bh[3];
+    double o[3], bl[3], bh[3], v[3], c[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double v = valid ? ys[3 * i + k] : 0.0;
-        double l = valid ? v : INFINITY, h = valid ? v : -INFINITY;
+        v[k] = valid ? ys[3 * i + k] : 0.0;
+        double l = valid ? v[k] : INFINITY, h = valid ? v[k] : -INFINITY;
         for (int d = 16; d > 0; d >>= 1) {
             l = fmin(l, __shfl_xor_sync(0xffffffffu, l, d));
             h = fmax(h, __shfl_xor_sync(0xffffffffu, h, d));
         }
         if (lane == 0) { glo[3 * g + k] = l; ghi[3 * g + k] = h; }
-        o[k] = dyadic12(0.5 * (l + h));
+        c[k] = 0.5 * (l + h);
+        o[k] = dyadic12(c[k]);
         bl[k] = l - o[k];
         bh[k] = h - o[k];
+    }
+    if (gctr) {
+        double r = 0.0;
+        if (valid) {
+            const double dx = v[0] - c[0], dy = v[1] - c[1], dz = v[2] - c[2];
+            r = sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        for (int d = 16; d > 0; d >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, d));
+        if (lane == 0)
+            gctr[g] = make_float4((float)(c[0] - o[0]), (float)(c[1] - o[1]), (float)(c[2] - o[2]),
+                                  __double2float_ru(r));
     }
     if (lane == 0) {
         gorig[g] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
@@ -418,12 +432,15 @@ __global__ void k_node_fbox(const double* lo, const double* hi, int nn, float4* 
 // relative 1e-7 from the float sum of squares).  With a margin of
 // 1e-6 (1 + S) + 1e-6 cw a decision here is the one the exact FP64 test would
 // take; the rest goes to that test.
-__device__ __forceinline__ int far_pretest(const float4& nl, const float4& nh, const float4& gl,
-                                           const float4& gh, float cwf, float mscale) {
+__device__ __forceinline__ float gap2_f(const float4& nl, const float4& nh, const float4& gl, const float4& gh) {
     const float ax = fmaxf(fmaxf(nl.x - gh.x, gl.x - nh.x), 0.f);
     const float ay = fmaxf(fmaxf(nl.y - gh.y, gl.y - nh.y), 0.f);
     const float az = fmaxf(fmaxf(nl.z - gh.z, gl.z - nh.z), 0.f);
-    const float d2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+    return fmaf(ax, ax, fmaf(ay, ay, az * az));
+}
+
+// The same pre-test of d2 (the float gap squared) against a threshold cwf.
+__device__ __forceinline__ int far_pretest(float d2, float cwf, float mscale) {
     const float m = mscale + 1e-6f * cwf;
     const float up = cwf + m, dn = cwf - m;
     if (d2 > up * up) return 1;
@@ -431,9 +448,10 @@ __device__ __forceinline__ int far_pretest(const float4& nl, const float4& nh, c
     return -1;
 }
 
-// Far test of a group box against node b (see the file comment).
-__device__ __forceinline__ bool is_far(const double* nlo, const double* nhi, const int* ndepth,
-                                       int b, const double* glo, const double* ghi, double c) {
+// Squared gap between a group box and node b's box, in double precision as
+// written (no fused multiply-adds).
+__device__ __forceinline__ double box_gap2_d(const double* nlo, const double* nhi, int b, const double* glo,
+                                             const double* ghi) {
     double gq[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -443,9 +461,22 @@ __device__ __forceinline__ bool is_far(const double* nlo, const double* nhi, con
         gq[k] = mm > 0.0 ? mm : 0.0;
     }
     double gx = __dmul_rn(gq[0], gq[0]), gy = __dmul_rn(gq[1], gq[1]), gz = __dmul_rn(gq[2], gq[2]);
-    double d2 = __dadd_rn(__dadd_rn(gx, gy), gz);
+    return __dadd_rn(__dadd_rn(gx, gy), gz);
+}
+
+// Far test of a group box against node b (see the file comment).
+__device__ __forceinline__ bool is_far(const double* nlo, const double* nhi, const int* ndepth,
+                                       int b, const double* glo, const double* ghi, double c) {
+    double d2 = box_gap2_d(nlo, nhi, b, glo, ghi);
     double cw = __dmul_rn(c, ldexp(2.0, -ndepth[b]));
     return d2 > __dmul_rn(cw, cw);
+}
+
+// Local-expansion test of a far node b: its squared box gap to the group
+// exceeds (cL e)^2, e the group box's largest extent (cle = cL e).
+__device__ __forceinline__ bool is_local(const double* nlo, const double* nhi, int b, const double* glo,
+                                         const double* ghi, double cle) {
+    return box_gap2_d(nlo, nhi, b, glo, ghi) > __dmul_rn(cle, cle);
 }
 
 constexpr int kTravWarps = 2;
@@ -496,7 +527,7 @@ template <int STACK, bool FIFO>
 __global__ void __launch_bounds__(32 * kTravWarps)
 k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float4* nhif, const int* ndepth,
            const int* nchild, const int* child0, const int* nstart, const double* glo, const double* ghi, int ng,
-           double theta, uint64_t* far_pool, int64_t far_cap, unsigned long long* far_count,
+           double theta, double clocal, uint64_t* far_pool, int64_t far_cap, unsigned long long* far_count,
            uint64_t* near_pool, uint32_t* near_vpool, int64_t near_cap, unsigned long long* near_count,
            int* err, uint64_t* unsorted, int* unsorted_count) {
     __shared__ int stack[kTravWarps][STACK];
@@ -517,6 +548,14 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
     const float gs = fmaxf(fmaxf(fmaxf(fabsf(gl.x), fabsf(gl.y)), fmaxf(fabsf(gl.z), fabsf(gh.x))),
                            fmaxf(fabsf(gh.y), fabsf(gh.z)));
     const float mscale = 1e-6f * (1.f + fmaxf(gs, 1.f));
+    // local expansions (clocal = 1/local_theta, 0 = off): a far node is expanded
+    // about the group centre when its box gap exceeds clocal x the group box's
+    // largest extent (flag bit 31 of the key's low word)
+    double ext = __dsub_rn(bh[0], bl[0]);
+    if (__dsub_rn(bh[1], bl[1]) > ext) ext = __dsub_rn(bh[1], bl[1]);
+    if (__dsub_rn(bh[2], bl[2]) > ext) ext = __dsub_rn(bh[2], bl[2]);
+    const double cle = __dmul_rn(clocal, ext);
+    const float clef = (float)cle;
     int* st = stack[wl];
     uint64_t* fbuf = fbuf_all[wl];
     uint64_t* nbuf = nbuf_all[wl];
@@ -539,10 +578,15 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
         top -= take;
         if (fifo) head += take;
         __syncwarp();
-        bool far = false, leaf = false, open = false;
+        bool far = false, leaf = false, open = false, loc = false;
         if (b >= 0) {
-            const int q = far_pretest(nlof[b], nhif[b], gl, gh, cf * ldexpf(2.f, -ndepth[b]), mscale);
+            const float d2f = gap2_f(nlof[b], nhif[b], gl, gh);
+            const int q = far_pretest(d2f, cf * ldexpf(2.f, -ndepth[b]), mscale);
             far = q < 0 ? is_far(nlo, nhi, ndepth, b, bl, bh, c) : q == 1;
+            if (far && clocal > 0.0) {
+                const int ql = far_pretest(d2f, clef, mscale);
+                loc = ql < 0 ? is_local(nlo, nhi, b, bl, bh, cle) : ql == 1;
+            }
             if (!far) {
                 if (nchild[b] == 0) leaf = true; else open = true;
             }
@@ -556,7 +600,7 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
             trav_flush(nbuf, nvbuf, ncnt, near_pool, near_vpool, near_cap, near_count, lane);
             ncnt = 0;
         }
-        if (far) fbuf[fcnt + __popc(fm & lt)] = ((uint64_t)g << 32) | (uint32_t)b;
+        if (far) fbuf[fcnt + __popc(fm & lt)] = ((uint64_t)g << 32) | (loc ? 0x80000000u : 0u) | (uint32_t)b;
         if (leaf) {
             int p = ncnt + __popc(lm & lt);
             nbuf[p] = ((uint64_t)g << 32) | (uint32_t)nstart[b];
@@ -711,17 +755,59 @@ __global__ void k_gather_i32(const int* src, const int* idx, int n, int* dst) {
     if (i < n) dst[i] = src[idx[i]];
 }
 
-// Interaction pair counts: far pairs = sum_g |g| * far(g), near = sum_g |g| * sum |range|
-__global__ void k_pair_counts(int ng, const int* goff, const int* far_off, const int* near_off,
+// Interaction counts: far pairs = sum_g |g| * (far entries summed pair by
+// pair), near = sum_g |g| * sum |range|, the expanded entries and the pairs
+// they stand for.
+__global__ void k_pair_counts(int ng, const int* goff, const int* far_off, const int* lsplit, const int* near_off,
                               const int2* rng, unsigned long long* out) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
     int64_t sz = goff[g + 1] - goff[g];
-    int64_t nf = far_off[g + 1] - far_off[g];
+    const int fl = lsplit ? lsplit[g] : far_off[g + 1];
+    int64_t nf = fl - far_off[g], nl = far_off[g + 1] - fl;
     int64_t nn = 0;
     for (int q = near_off[g]; q < near_off[g + 1]; ++q) nn += rng[q].y - rng[q].x;
     atomicAdd(&out[0], (unsigned long long)(sz * nf));
     atomicAdd(&out[1], (unsigned long long)(sz * nn));
+    if (nl) {
+        atomicAdd(&out[2], (unsigned long long)nl);
+        atomicAdd(&out[3], (unsigned long long)(sz * nl));
+    }
+}
+
+// Far keys (group << 32 | local flag << 31 | node), sorted by group and flag:
+// node ids, and each group's first flagged entry (lsplit[g], initialised to
+// the end of the group's list by k_lsplit_init).
+__global__ void k_lsplit_init(const int* far_off, int ng, int* lsplit) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) lsplit[g] = far_off[g + 1];
+}
+__global__ void k_far_ids(const uint64_t* keys, int64_t n, int* far_id, int* lsplit) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const uint64_t k = keys[e];
+    far_id[e] = (int)(uint32_t)(k & 0x7fffffffu);
+    if (lsplit && (k & 0x80000000u)) {
+        const bool first = e == 0 || (keys[e - 1] >> 32) != (k >> 32) || !(keys[e - 1] & 0x80000000u);
+        if (first) lsplit[(int)(k >> 32)] = (int)e;
+    }
+}
+
+// Group of every far entry (warp per group over its range).
+__global__ void k_entry_groups(const int* far_off, int ng, int* egrp) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    for (int e = far_off[g] + lane; e < far_off[g + 1]; e += 32) egrp[e] = g;
+}
+
+// Per transposed entry: the group of its entry, bit 31 set when the entry is
+// expanded about the group's centre (at or after lsplit of its group).
+__global__ void k_tfar_groups(const int* tfar_ent, int64_t ne, const int* egrp, const int* lsplit, int* out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ne) return;
+    const int e = tfar_ent[q], g = egrp[e];
+    out[q] = g | (e >= lsplit[g] ? (int)0x80000000u : 0);
 }
 
 // Transposed far lists: key (node << 32 | entry index).
@@ -823,10 +909,14 @@ struct ItemWalk {
     }
 };
 
-__device__ int walk_items(int mode, int g, const int* near_off, const int2* rng, const int* far_off, int cap,
-                          Item* out, int base, int pslot_base, int nparts, int split, bool partials) {
+// Far entries expanded about the group centre (from lsplit[g] on) are not in
+// the items: the local-expansion kernels take them.
+__device__ int walk_items(int mode, int g, const int* near_off, const int2* rng, const int* far_off,
+                          const int* lsplit, int cap, Item* out, int base, int pslot_base, int nparts, int split,
+                          bool partials) {
     const int qb = near_off ? near_off[g] : 0, qe = near_off ? near_off[g + 1] : 0;
-    const int fb = far_off ? far_off[g] : 0, fe = far_off ? far_off[g + 1] : 0;
+    const int fb = far_off ? far_off[g] : 0;
+    const int fe = far_off ? (lsplit ? min(max(lsplit[g], fb), far_off[g + 1]) : far_off[g + 1]) : 0;
     ItemWalk w{g, qb, fb, 0, 0, out, base, pslot_base, nparts, split, partials};
     for (int q = qb; q < qe; ++q) {
         int c = mode == 1 ? 8 : rng[q].y - rng[q].x;
@@ -844,31 +934,34 @@ __device__ int walk_items(int mode, int g, const int* near_off, const int2* rng,
 
 // Total cost of segment g (its walk without a cap).
 __global__ void k_seg_cost(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
-                           int64_t* cost) {
+                           const int* lsplit, int64_t* cost) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nseg) return;
     int64_t c = 0;
     if (near_off)
         for (int q = near_off[g]; q < near_off[g + 1]; ++q) c += mode == 1 ? 8 : rng[q].y - rng[q].x;
-    if (far_off) c += far_off[g + 1] - far_off[g];
+    if (far_off) {
+        const int fb = far_off[g];
+        c += (lsplit ? min(max(lsplit[g], fb), far_off[g + 1]) : far_off[g + 1]) - fb;
+    }
     cost[g] = c;
 }
 
 __global__ void k_items_count(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
-                              int cap, int* cnt, int* slots) {
+                              const int* lsplit, int cap, int* cnt, int* slots) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nseg) return;
-    int c = walk_items(mode, g, near_off, rng, far_off, cap, nullptr, 0, 0, 0, -1, false);
+    int c = walk_items(mode, g, near_off, rng, far_off, lsplit, cap, nullptr, 0, 0, 0, -1, false);
     cnt[g] = c;
     slots[g] = c > 1 ? c : 0;
 }
 
 __global__ void k_items_fill(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
-                             int cap, const int* cnt, const int* item_off, const int* slot_off, bool partials,
-                             Item* items, int4* splits, const int* split_off) {
+                             const int* lsplit, int cap, const int* cnt, const int* item_off, const int* slot_off,
+                             bool partials, Item* items, int4* splits, const int* split_off) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nseg) return;
-    walk_items(mode, g, near_off, rng, far_off, cap, items, item_off[g], slot_off[g], cnt[g],
+    walk_items(mode, g, near_off, rng, far_off, lsplit, cap, items, item_off[g], slot_off[g], cnt[g],
                (partials && cnt[g] > 1) ? split_off[g] : -1, partials);
     if (partials && cnt[g] > 1) splits[split_off[g]] = make_int4(g, slot_off[g], cnt[g], 0);
 }
@@ -928,7 +1021,7 @@ void free_work(WorkList& w) {
 
 // Build the work list of nseg segments (see walk_items), heaviest item first.
 static void build_work(WorkList& w, int mode, int nseg, const int* near_off, const int2* rng,
-                       const int* far_off, bool partials, cudaStream_t s) {
+                       const int* far_off, const int* lsplit, bool partials, cudaStream_t s) {
     int* cnt = dalloc<int>(nseg + 1);
     int* slots = dalloc<int>(nseg + 1);
     int* item_off = dalloc<int>(nseg + 2);
@@ -938,7 +1031,7 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     // the item cap from the total cost of all segments
     int64_t* seg_cost = dalloc<int64_t>(nseg + 1);
     int64_t* cost_scan = dalloc<int64_t>(nseg + 2);
-    k_seg_cost<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, seg_cost);
+    k_seg_cost<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit, seg_cost);
     WNNC_LAUNCH_CHECK();
     exclusive_scan_i64(seg_cost, cost_scan, nseg, s);
     int64_t total = 0;
@@ -949,7 +1042,8 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     int cap = kItemCostMin;
     while (cap < kItemCostMax && (int64_t)cap * 2 * kItemsTarget <= total) cap *= 2;
     w.cap = cap;
-    k_items_count<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cap, cnt, slots);
+    k_items_count<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit, cap, cnt,
+                                                     slots);
     WNNC_LAUNCH_CHECK();
     exclusive_scan_i32(cnt, item_off, nseg, s);
     exclusive_scan_i32(slots, slot_off, nseg, s);
@@ -973,8 +1067,8 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     w.splits = dalloc<int4>(w.nsplit);
     w.split_cnt = dalloc<unsigned>(w.nsplit);
     WNNC_CUDA(cudaMemsetAsync(w.split_cnt, 0, sizeof(unsigned) * (size_t)std::max(w.nsplit, 1), s));
-    k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, cap, cnt, item_off,
-                                                    slot_off, partials, tmp, w.splits, split_off);
+    k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit, cap, cnt,
+                                                    item_off, slot_off, partials, tmp, w.splits, split_off);
     WNNC_LAUNCH_CHECK();
     uint64_t* keys = dalloc<uint64_t>(w.nitems);
     k_item_keys<<<ceil_div(w.nitems, kTB), kTB, 0, s>>>(tmp, w.nitems, keys);
@@ -1100,8 +1194,11 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     ts.gorig = dalloc<float4>(ng);
     ts.gbl = dalloc<float4>(ng);
     ts.gbh = dalloc<float4>(ng);
+    const bool local = t.params.local_theta > 0.f && t.params.theta > 0.f;
+    const double clocal = local ? 1.0 / (double)t.params.local_theta : 0.0;
+    ts.gctr = local ? dalloc<float4>(ng) : nullptr;
     k_group_boxes<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(ys, ts.goff, ng, ts.glo, ts.ghi, ts.gorig,
-                                                                   ts.gbl, ts.gbh);
+                                                                   ts.gbl, ts.gbh, ts.gctr);
     WNNC_LAUNCH_CHECK();
     wait_before_free(s);
     if (!reuse) {
@@ -1150,7 +1247,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
 #define WNNC_TRAVERSE(STK, FIFO)                                                                               \
     k_traverse<STK, FIFO><<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_lof, t.node_hif,           \
                                                       t.node_depth, t.node_nchild, t.node_child0,            \
-                                                      t.node_start, ts.glo, ts.ghi, ng, theta, fkeys,        \
+                                                      t.node_start, ts.glo, ts.ghi, ng, theta, clocal, fkeys,\
                                                       far_cap, counts, nkeys, nvals, near_cap, counts + 1,  \
                                                       err, unsorted, err + 1)
             if (big_stack) WNNC_TRAVERSE(kStackBig, false); else WNNC_TRAVERSE(kStackSmall, true);
@@ -1184,18 +1281,25 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             near_cap = std::max<int64_t>(nleafent, 1);
         }
         int gbits = bits_for(ng);
-        radix_sort_pairs(fkeys, nullptr, nfar, 32 + gbits, s, big_stack ? 0 : 32);
+        // by group (and, with local expansions, by the flag in bit 31 next):
+        // the first-in first-out walk wrote each group's nodes ascending
+        radix_sort_pairs(fkeys, nullptr, nfar, 32 + gbits, s, big_stack ? 0 : (local ? 31 : 32));
         radix_sort_pairs(nkeys, nvals, nleafent, 32 + gbits, s);
         segment_offsets_hi32(fkeys, nfar, ts.far_off, ng, s);
         if (!big_stack && nunsorted > 0)
-            sort_far_segments(fkeys, ts.far_off, unsorted, nunsorted, bits_for(t.nnodes), s);
+            sort_far_segments(fkeys, ts.far_off, unsorted, nunsorted, local ? 32 : bits_for(t.nnodes), s);
         ts.walk_stack_groups = big_stack ? 0 : nunsorted;
         ts.walk_big_stack = big_stack ? 1 : 0;
         segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s);
         ts.far_entries = nfar;
         ts.far_id = dalloc<int>(nfar);
+        if (local) {
+            ts.far_lsplit = dalloc<int>(ng);
+            k_lsplit_init<<<ceil_div(ng, kTB), kTB, 0, s>>>(ts.far_off, ng, ts.far_lsplit);
+            WNNC_LAUNCH_CHECK();
+        }
         if (nfar) {
-            k_low32<<<ceil_div(nfar, kTB), kTB, 0, s>>>(fkeys, nfar, ts.far_id);
+            k_far_ids<<<ceil_div(nfar, kTB), kTB, 0, s>>>(fkeys, nfar, ts.far_id, ts.far_lsplit);
             WNNC_LAUNCH_CHECK();
         }
         // merge consecutive near leaves into ranges
@@ -1244,22 +1348,26 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         wait_before_free(s);
         pool_free(cnt); pool_free(off); pool_free(rng0); pool_free(near_off0);
     }
-    unsigned long long* pc = dalloc<unsigned long long>(2);
-    WNNC_CUDA(cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), s));
-    k_pair_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ng, ts.goff, ts.far_off, ts.near_off, ts.near_rng, pc);
+    unsigned long long* pc = dalloc<unsigned long long>(4);
+    WNNC_CUDA(cudaMemsetAsync(pc, 0, 4 * sizeof(unsigned long long), s));
+    k_pair_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ng, ts.goff, ts.far_off, ts.far_lsplit, ts.near_off,
+                                                    ts.near_rng, pc);
     WNNC_LAUNCH_CHECK();
-    unsigned long long hc[2];
+    unsigned long long hc[4];
     WNNC_CUDA(cudaMemcpyAsync(hc, pc, sizeof(hc), cudaMemcpyDeviceToHost, s));
     WNNC_CUDA(cudaStreamSynchronize(s));
     pool_free(pc);
     ts.far_pairs = (int64_t)hc[0];
     ts.near_pairs = (int64_t)hc[1];
-    build_work(ts.work, 0, ng, ts.near_off, ts.near_rng, ts.far_off, true, s);
+    ts.local_entries = (int64_t)hc[2];
+    ts.local_pairs = (int64_t)hc[3];
+    build_work(ts.work, 0, ng, ts.near_off, ts.near_rng, ts.far_off, ts.far_lsplit, true, s);
 }
 
 void free_target_set(TargetSet& ts) {
     dfree(ts.perm); dfree(ts.pos); dfree(ts.corig); dfree(ts.gorig); dfree(ts.goff); dfree(ts.glo);
     dfree(ts.ghi); dfree(ts.gbl); dfree(ts.gbh); dfree(ts.far_off); dfree(ts.far_id); dfree(ts.near_off); dfree(ts.near_rng);
+    dfree(ts.far_lsplit); dfree(ts.gctr);
     free_work(ts.work);
 }
 
@@ -1448,6 +1556,17 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             WNNC_LAUNCH_CHECK();
         }
         segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
+        if (S.far_lsplit && ne) {
+            // per transposed entry its group, bit 31 set for an expanded entry
+            int* egrp = dalloc<int>(ne);
+            k_entry_groups<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(S.far_off, ng, egrp);
+            WNNC_LAUNCH_CHECK();
+            t.tfar_grp = dalloc<int>(ne);
+            k_tfar_groups<<<ceil_div(ne, kTB), kTB, 0, s>>>(t.tfar_ent, ne, egrp, S.far_lsplit, t.tfar_grp);
+            WNNC_LAUNCH_CHECK();
+            wait_before_free(s);
+            pool_free(egrp);
+        }
         wait_before_free(s);
         pool_free(k);
     }
@@ -1502,9 +1621,9 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         pool_free(cnt); pool_free(coff); pool_free(k); pool_free(msk); pool_free(slt); pool_free(idx);
         pool_free(head); pool_free(hscan); pool_free(uk);
     }
-    build_work(t.adj_far_work, 2, ng, nullptr, nullptr, S.far_off, false, s);
-    build_work(t.adj_pair_work, 0, ng, S.near_off, S.near_rng, nullptr, false, s);
-    build_work(t.adj_near_work, 1, nach, t.tnear_off, nullptr, nullptr, true, s);
+    build_work(t.adj_far_work, 2, ng, nullptr, nullptr, S.far_off, S.far_lsplit, false, s);
+    build_work(t.adj_pair_work, 0, ng, S.near_off, S.near_rng, nullptr, nullptr, false, s);
+    build_work(t.adj_near_work, 1, nach, t.tnear_off, nullptr, nullptr, nullptr, true, s);
 }
 
 void free_tree(Tree& t) {
@@ -1523,6 +1642,7 @@ void free_tree(Tree& t) {
     dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.mom_top); dfree(t.mom_top_rng); dfree(t.mom_front); dfree(t.node_rep); dfree(t.contrib);
     dfree(t.near_contrib); dfree(t.vnode); dfree(t.red_ticket);
     dfree(t.mom_dip); dfree(t.mom_dip_r); dfree(t.dip_corr); dfree(t.contrib_h0); dfree(t.contrib_h1);
+    dfree(t.node_abs); dfree(t.local_rec); dfree(t.tfar_grp); dfree(t.gadj);
     dfree(t.hnode0); dfree(t.hnode1);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
