@@ -279,7 +279,8 @@ struct Tree {
     // local expansions (local_theta > 0)
     float4* node_abs = nullptr;   // per node: point centroid in normalised coordinates (float)
     float4* local_rec = nullptr;  // per node, 32 bytes, rebuilt per call: (centroid, M_x), (M_y, M_z, 0, 0)
-    int* tfar_grp = nullptr;      // per transposed far entry: its group, bit 31 set when expanded
+    int* tfar_lsplit = nullptr;   // per node: first expanded transposed entry; tfar_ent holds the
+                                  // entry index before it and the entry's group from it on
     float4* gadj = nullptr;       // per group, rebuilt per adjoint call: (c_g, rho_g), (D, S)
     float4* contrib_h0 = nullptr; // per far entry: sum s HPhi, (xx, yy, zz, -) and (xy, xz, yz, -)
     float4* contrib_h1 = nullptr;

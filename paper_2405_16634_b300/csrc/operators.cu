@@ -1062,7 +1062,7 @@ struct AdjArgs {
     int nnodes;
     const int* tfar_off;      // transposed far lists (node -> entries)
     const int* tfar_ent;
-    const int* tfar_grp;      //   the entries' groups, bit 31 set when expanded
+    const int* tfar_lsplit;   //   per node the first expanded entry (tfar_ent: its group from there)
     float4* gadj;             //   per group (c_g, rho_g), (D, S), normalised coordinates
 };
 
@@ -1218,44 +1218,45 @@ __device__ __noinline__ float4 local_entry_pairs(const AdjArgs& A, int g, int b)
     return make_float4(cx, cy, cz, 0.f);
 }
 
-// The node gather with expanded entries: one warp per node, lanes over the
-// node's transposed entries kLocalGathers at a time (loads first, then sums);
-// an entry summed pair by pair reads its contrib, an expanded one its group's
-// record.
+// The node gather with expanded entries: one warp per node.  The node's
+// entries summed pair by pair come first (their contrib, kPairGathers reads
+// in flight per lane), then its expanded entries (tfar_ent holds their group;
+// kLocalGathers group records in flight per lane, then the terms).
+constexpr int kNodeGathers = 16;
+constexpr int kPairGathers = 8;
 constexpr int kLocalGathers = 4;
 __global__ void k_adj_node_local(AdjArgs A, float4* vnode) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= A.nnodes) return;
-    const float4 xb = A.nabs[b];
+    const int q0 = A.tfar_off[b], qs = A.tfar_lsplit[b], q1 = A.tfar_off[b + 1];
     float ax = 0.f, ay = 0.f, az = 0.f;
-    const int q1 = A.tfar_off[b + 1];
-    for (int q = A.tfar_off[b] + lane; q < q1; q += 32 * kLocalGathers) {
-        int e[kLocalGathers], gg[kLocalGathers];
+    for (int q = q0 + lane; q < qs; q += 32 * kPairGathers) {
+        int e[kPairGathers];
 #pragma unroll
-        for (int u = 0; u < kLocalGathers; ++u) {
-            const bool v = q + 32 * u < q1;
-            e[u] = v ? A.tfar_ent[q + 32 * u] : -1;
-            gg[u] = v ? A.tfar_grp[q + 32 * u] : 0;
-        }
-        float4 c0[kLocalGathers], c1[kLocalGathers];
+        for (int u = 0; u < kPairGathers; ++u) e[u] = q + 32 * u < qs ? A.tfar_ent[q + 32 * u] : -1;
+        float4 c[kPairGathers];
 #pragma unroll
-        for (int u = 0; u < kLocalGathers; ++u) {
-            c0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            c1[u] = c0[u];
-            if (e[u] >= 0) {
-                if (gg[u] < 0) {
-                    const int g = gg[u] & 0x7fffffff;
-                    c0[u] = A.gadj[2 * g];
-                    c1[u] = A.gadj[2 * g + 1];
-                } else {
-                    c0[u] = A.contrib[e[u]];
-                }
+        for (int u = 0; u < kPairGathers; ++u) c[u] = e[u] >= 0 ? A.contrib[e[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kPairGathers; ++u) { ax += c[u].x; ay += c[u].y; az += c[u].z; }
+    }
+    if (qs < q1) {
+        const float4 xb = A.nabs[b];
+        for (int q = qs + lane; q < q1; q += 32 * kLocalGathers) {
+            int g[kLocalGathers];
+#pragma unroll
+            for (int u = 0; u < kLocalGathers; ++u) g[u] = q + 32 * u < q1 ? A.tfar_ent[q + 32 * u] : -1;
+            float4 c0[kLocalGathers], c1[kLocalGathers];
+#pragma unroll
+            for (int u = 0; u < kLocalGathers; ++u) {
+                const int gg = g[u] >= 0 ? g[u] : 0;
+                c0[u] = A.gadj[2 * gg];
+                c1[u] = A.gadj[2 * gg + 1];
             }
-        }
 #pragma unroll
-        for (int u = 0; u < kLocalGathers; ++u) {
-            if (e[u] >= 0 && gg[u] < 0) {
+            for (int u = 0; u < kLocalGathers; ++u) {
+                if (g[u] < 0) continue;
                 const float ex = xb.x - c0[u].x, ey = xb.y - c0[u].y, ez = xb.z - c0[u].z;
                 const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
                 const float ir = rsqrtf(r2);
@@ -1269,15 +1270,11 @@ __global__ void k_adj_node_local(AdjArgs A, float4* vnode) {
                     ay += fmaf(sr, ey, fmaf(ed3, ey, -r2 * D.y) * ir5);
                     az += fmaf(sr, ez, fmaf(ed3, ez, -r2 * D.z) * ir5);
                 } else {
-                    const float4 c = local_entry_pairs(A, gg[u] & 0x7fffffff, b);
-                    ax += c.x;
-                    ay += c.y;
-                    az += c.z;
+                    const float4 cc = local_entry_pairs(A, g[u], b);
+                    ax += cc.x;
+                    ay += cc.y;
+                    az += cc.z;
                 }
-            } else {
-                ax += c0[u].x;
-                ay += c0[u].y;
-                az += c0[u].z;
             }
         }
     }
@@ -1294,7 +1291,6 @@ __global__ void k_adj_node_local(AdjArgs A, float4* vnode) {
 // node-major list) 32 x kNodeGathers at a time, kNodeGathers independent
 // gathers per lane in flight, then reduce.  The kernel is bound by the latency
 // of the gathers.
-constexpr int kNodeGathers = 16;
 __global__ void k_adj_node(int nnodes, const int* tfar_off, const int* tfar_ent, const float4* contrib,
                            float4* vnode) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -2115,7 +2111,7 @@ AdjArgs adj_args(const Tree& t, float w) {
     a.nnodes = t.nnodes;
     a.tfar_off = t.tfar_off;
     a.tfar_ent = t.tfar_ent;
-    a.tfar_grp = t.tfar_grp;
+    a.tfar_lsplit = t.tfar_lsplit;
     a.gadj = t.gadj;
     return a;
 }

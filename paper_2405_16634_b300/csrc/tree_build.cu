@@ -801,19 +801,28 @@ __global__ void k_entry_groups(const int* far_off, int ng, int* egrp) {
     for (int e = far_off[g] + lane; e < far_off[g + 1]; e += 32) egrp[e] = g;
 }
 
-// Per transposed entry: the group of its entry, bit 31 set when the entry is
-// expanded about the group's centre (at or after lsplit of its group).
-__global__ void k_tfar_groups(const int* tfar_ent, int64_t ne, const int* egrp, const int* lsplit, int* out) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= ne) return;
-    const int e = tfar_ent[q], g = egrp[e];
-    out[q] = g | (e >= lsplit[g] ? (int)0x80000000u : 0);
+// Transposed far lists: key (node << 32 | expanded << 31 | entry index);
+// expanded = the entry lies at or after lsplit of its group (egrp and lsplit
+// null: no expanded entries).
+__global__ void k_tfar_keys(const int* far_id, int64_t nent, const int* egrp, const int* lsplit,
+                            uint64_t* keys) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nent) return;
+    const bool x = egrp && e >= lsplit[egrp[e]];
+    keys[e] = ((uint64_t)(uint32_t)far_id[e] << 32) | (x ? 0x80000000u : 0u) | (uint32_t)e;
 }
 
-// Transposed far lists: key (node << 32 | entry index).
-__global__ void k_tfar_keys(const int* far_id, int64_t nent, uint64_t* keys) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < nent) keys[e] = ((uint64_t)(uint32_t)far_id[e] << 32) | (uint32_t)e;
+// Sorted transposed keys -> per node its entries summed pair by pair (their
+// entry index), then from tlsplit[node] on its expanded entries (their group).
+__global__ void k_tfar_ids(const uint64_t* keys, int64_t n, const int* egrp, int* tfar_ent, int* tlsplit) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint64_t k = keys[q];
+    const int e = (int)(uint32_t)(k & 0x7fffffffu);
+    const bool x = (k & 0x80000000u) != 0;
+    tfar_ent[q] = x ? egrp[e] : e;
+    if (x && (q == 0 || (keys[q - 1] >> 32) != (k >> 32) || !(keys[q - 1] & 0x80000000u)))
+        tlsplit[(int)(k >> 32)] = (int)q;
 }
 
 // Transposed near entries: for each near range of target group g, the source
@@ -1544,31 +1553,35 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     t.tfar_off = dalloc<int>(t.nnodes + 1);
     {
         int64_t ne = S.far_entries;
+        const bool local = S.far_lsplit != nullptr;
         uint64_t* k = dalloc<uint64_t>(ne);
-        if (ne) {
-            k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, k);
-            WNNC_LAUNCH_CHECK();
-        }
-        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes), s, 32);   // entry indices already ascending
-        t.tfar_ent = dalloc<int>(ne);
-        if (ne) {
-            k_low32<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, t.tfar_ent);
-            WNNC_LAUNCH_CHECK();
-        }
-        segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
-        if (S.far_lsplit && ne) {
-            // per transposed entry its group, bit 31 set for an expanded entry
-            int* egrp = dalloc<int>(ne);
+        // with local expansions: the group of every entry, and bit 31 of the
+        // key set for an expanded entry (sorted after the node's others)
+        int* egrp = local ? dalloc<int>(ne) : nullptr;
+        if (local && ne) {
             k_entry_groups<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(S.far_off, ng, egrp);
             WNNC_LAUNCH_CHECK();
-            t.tfar_grp = dalloc<int>(ne);
-            k_tfar_groups<<<ceil_div(ne, kTB), kTB, 0, s>>>(t.tfar_ent, ne, egrp, S.far_lsplit, t.tfar_grp);
+        }
+        if (ne) {
+            k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, egrp, S.far_lsplit, k);
             WNNC_LAUNCH_CHECK();
-            wait_before_free(s);
-            pool_free(egrp);
+        }
+        // entry indices already ascending
+        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes), s, local ? 31 : 32);
+        t.tfar_ent = dalloc<int>(ne);
+        segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
+        if (local) {
+            t.tfar_lsplit = dalloc<int>(t.nnodes);
+            k_lsplit_init<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.tfar_off, t.nnodes, t.tfar_lsplit);
+            WNNC_LAUNCH_CHECK();
+        }
+        if (ne) {
+            k_tfar_ids<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, egrp, t.tfar_ent, t.tfar_lsplit);
+            WNNC_LAUNCH_CHECK();
         }
         wait_before_free(s);
         pool_free(k);
+        pool_free(egrp);
     }
     {
         int64_t nr = S.near_ranges;
@@ -1642,7 +1655,7 @@ void free_tree(Tree& t) {
     dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.mom_top); dfree(t.mom_top_rng); dfree(t.mom_front); dfree(t.node_rep); dfree(t.contrib);
     dfree(t.near_contrib); dfree(t.vnode); dfree(t.red_ticket);
     dfree(t.mom_dip); dfree(t.mom_dip_r); dfree(t.dip_corr); dfree(t.contrib_h0); dfree(t.contrib_h1);
-    dfree(t.node_abs); dfree(t.local_rec); dfree(t.tfar_grp); dfree(t.gadj);
+    dfree(t.node_abs); dfree(t.local_rec); dfree(t.tfar_lsplit); dfree(t.gadj);
     dfree(t.hnode0); dfree(t.hnode1);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }
