@@ -78,8 +78,9 @@ VARIANTS = [
     ("first_order_far_field_theta0.8", dict(theta=0.8, far_order=1), 2),
 ]
 # DRAM bytes (read + write) of one launch of the fused A+G kernel on union500k, from ncu
-# (one ncu capture of that kernel on this workload); None once the kernel has changed.
-AG_TRAFFIC_BYTES = 107.725568e6 + 4.595968e6
+# (one ncu capture of that kernel on this workload), with and without the local
+# expansions (their far lists differ); None once the kernel has changed.
+AG_TRAFFIC_BYTES = {0.5: 56.804352e6 + 0.589312e6, 0.0: 107.725568e6 + 4.595968e6}
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
@@ -394,7 +395,7 @@ def run_gpu(args):
                      # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
                      # kernel (one ncu capture on this workload); only valid for
                      # the default workload and the kernel version that was profiled
-                     "traffic": AG_TRAFFIC_BYTES if CONFIG_NAME == "union500k" else None,
+                     "traffic": AG_TRAFFIC_BYTES.get(LOCAL_THETA) if CONFIG_NAME == "union500k" else None,
                      "traffic_unit": "bytes",
                      "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 "
                                     f"x {max_mhz:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
