@@ -90,7 +90,7 @@ def load(path: str):
     L.or_tree_groups.argtypes = [c_void_p, c_void_p]
     L.or_tree_build.restype = c_void_p
     L.or_tree_set_far_order.argtypes = [c_void_p, c_int]
-    L.or_tree_set_local.argtypes = [c_void_p, d]
+    L.or_tree_set_local.argtypes = [c_void_p, d, c_int]
     L.or_tree_free.argtypes = [c_void_p]
     L.or_tree_nnodes.argtypes = [c_void_p]
     L.or_tree_nnodes.restype = i64
@@ -188,21 +188,24 @@ class Tree:
     def __init__(self, xn, theta: float, leaf_size: int = 8, max_depth: int = 15,
                  group_size: int = GROUP_SIZE, group_slack: int = GROUP_SLACK,
                  group_min_depth: int = GROUP_MIN_DEPTH, far_order: int = 0,
-                 local_theta: float = 0.0):
+                 local_theta: float = 0.0, local_cluster: int = 0):
         """far_order 1 adds the first-order Taylor terms of the kernels about
         each far node's point centroid (rep_mode 1; A, G and the exact A^T).
         local_theta > 0 (far_order 0, rep_mode 1) expands the far field of
         every far node whose box gap to a target group exceeds the group
         box's largest extent / local_theta to first order about the group box
-        centre (A, G and the exact A^T); a group falls back to pair terms at
-        widths w that reach its nearest such node."""
+        centre (A, G and the exact A^T); an entry falls back to pair terms at
+        widths w that may reach one of its pairs.  local_cluster >= 2 also
+        expands, once per cluster of that many consecutive groups, the far
+        nodes in the expanded part of every member's list that are local for
+        the cluster's box, about the cluster's centre."""
         self.xn = _f64(xn, (-1, 3))
         self.n = self.xn.shape[0]
         self.theta = float(theta)
         self._h = lib().or_tree_build(_p(self.xn), self.n, leaf_size, group_size, max_depth, self.theta,
                                       int(group_slack), int(group_min_depth))
         lib().or_tree_set_far_order(self._h, int(far_order))
-        lib().or_tree_set_local(self._h, float(local_theta))
+        lib().or_tree_set_local(self._h, float(local_theta), int(local_cluster))
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -365,21 +368,22 @@ def eval_direct_at(op: int, points, nu, w: float, targets=None, amb_tol: float =
 # Boundary-shaped entry points (caller units, like the library's C ABI)
 # ---------------------------------------------------------------------------
 
-def _setup(points, theta, leaf_size, max_depth, far_order=0, local_theta=0.0):
+def _setup(points, theta, leaf_size, max_depth, far_order=0, local_theta=0.0, local_cluster=0):
     xn, c, s = normalize(points)
-    tree = (Tree(xn, theta, leaf_size, max_depth, far_order=far_order, local_theta=local_theta)
+    tree = (Tree(xn, theta, leaf_size, max_depth, far_order=far_order, local_theta=local_theta,
+                 local_cluster=local_cluster)
             if theta > 0 else None)
     return xn, c, s, tree
 
 
 def eval_op(op: int, points, nu, w: float, theta: float = 0.0, leaf_size: int = 8,
             max_depth: int = 15, rep_mode: int = 1, amb_tol: float = 0.0, far_order: int = 0,
-            local_theta: float = 0.0):
+            local_theta: float = 0.0, local_cluster: int = 0):
     """One operator at the input points, caller units in and out.
 
     op A: nu = mu (N,3) -> F (N,);  op G: nu = mu -> grad F = -G (N,3);
     op AT: nu = s (N,) -> A^T s (N,3).  theta = 0 uses the direct sums."""
-    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth, far_order, local_theta)
+    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth, far_order, local_theta, local_cluster)
     nu = np.asarray(nu, dtype=np.float64)
     nun = nu * (s * s) if op != OP_AT else nu
     bounds = None
@@ -401,11 +405,11 @@ def eval_op(op: int, points, nu, w: float, theta: float = 0.0, leaf_size: int = 
 
 def eval_at(op: int, points, mu, queries, w: float, theta: float = 0.0, leaf_size: int = 8,
             max_depth: int = 15, rep_mode: int = 1, with_bounds: bool = False, far_order: int = 0,
-            local_theta: float = 0.0):
+            local_theta: float = 0.0, local_cluster: int = 0):
     """A (F) or grad F at off-surface query points (caller units); with
     with_bounds also the per-target bounds (amb is zero here: w applies only
     through the cut-off, and off-surface tests use w = 0)."""
-    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth, far_order, local_theta)
+    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth, far_order, local_theta, local_cluster)
     qn = apply_normalization(queries, c, s)
     mun = np.asarray(mu, dtype=np.float64) * (s * s)
     if tree is None:
@@ -424,14 +428,15 @@ def iterate(points, mu0=None, n_iter: int = 40, w1: float = 0.002, w2: float = 0
             theta: float = 0.0, leaf_size: int = 8, max_depth: int = 15, rep_mode: int = 1,
             first_iter: int = 1, last_iter: int | None = None, rescale: int = 0, area=None,
             use_grad: bool = True, use_wnnc: bool = True, schedule="linear", paper_theta: float = 0.0,
-            paper_leaf_size: int = 1, far_order: int = 0, local_theta: float = 0.0):
+            paper_leaf_size: int = 1, far_order: int = 0, local_theta: float = 0.0,
+            local_cluster: int = 0):
     """Alg. 3 on the cloud; returns (mu in caller units, stats[iter] = (w, E, alpha, |r|^2)).
     Operators: theta > 0 the group treecode (leaf_size, rep_mode); else
     paper_theta > 0 the paper's treecode (Alg. 4, per target, paper_leaf_size);
     else the direct sums.
     schedule: the width schedule, "linear" (Alg. 3), "cosine" or "exponential"
     (the alternatives of Sec. 6.1.2; see schedule_width)."""
-    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth, far_order, local_theta)
+    xn, c, s, tree = _setup(points, theta, leaf_size, max_depth, far_order, local_theta, local_cluster)
     ptree = PaperTree(xn, paper_leaf_size, max_depth) if (tree is None and paper_theta > 0) else None
     n = xn.shape[0]
     mu = np.zeros((n, 3)) if mu0 is None else np.array(mu0, dtype=np.float64).reshape(n, 3) * (s * s)

@@ -452,7 +452,11 @@ typedef struct {
     int far_order;      /* 0: monopole far terms (Eq. 13-14); 1: plus the first-order Taylor terms */
     double local_c;     /* > 0: first-order local expansions about the group box centre for far
                            nodes with box gap > local_c x group extent (far_order 0, rep_mode 1) */
+    int local_cluster;  /* >= 2: also about the centres of clusters of that many groups */
+    signed char* self_cls;   /* the class of every far entry of the points as targets */
 } or_tree;
+
+static signed char* local_classes(const or_octree* t, const or_targets* T, double c, int K);
 
 /* group_slack, group_min_depth: the rule of group_offsets for the points as
  * targets (slack < 0: fixed runs of group_size). */
@@ -479,6 +483,7 @@ void or_tree_free(or_tree* T) {
     free(t->x); free(t->perm); free(t->key); free(t->start); free(t->count); free(t->parent);
     free(t->child0); free(t->depth); free(t->nchild); free(t->lo); free(t->hi); free(t->cent);
     free_targets(&T->self);
+    free(T->self_cls);
     free(T);
 }
 
@@ -491,7 +496,12 @@ void or_tree_set_far_order(or_tree* T, int order) { T->far_order = order; }
  * (rep_mode 1, far_order 0): a far node b is expanded for a group when the box
  * gap exceeds 1/local_theta times the group box's largest extent; local_theta
  * 0 switches them off. */
-void or_tree_set_local(or_tree* T, double local_theta) { T->local_c = local_theta > 0.0 ? 1.0 / local_theta : 0.0; }
+void or_tree_set_local(or_tree* T, double local_theta, int cluster) {
+    T->local_c = local_theta > 0.0 ? 1.0 / local_theta : 0.0;
+    T->local_cluster = cluster;
+    free(T->self_cls);
+    T->self_cls = T->local_c > 0.0 ? local_classes(&T->src, &T->self, T->local_c, cluster) : NULL;
+}
 
 /* Structure queries (for the structural pins and for comparing list sizes). */
 int64_t or_tree_nnodes(const or_tree* T) { return T->src.nnodes; }
@@ -698,6 +708,101 @@ static double local_eval(int op, const double* ce, const double dl[3], double ou
                      + 2.0 * (ce[7] * ce[7] + ce[8] * ce[8] + ce[9] * ce[9]));
 }
 
+/* Clusters of K consecutive target groups (K >= 2; cluster C = groups
+ * C K .. C K + K - 1, the last one possibly shorter).  A far node that lies in
+ * the expanded part of every member group's list, and is itself local for the
+ * cluster's box (the union of the members' boxes; the same test as for a
+ * group), is expanded once about the cluster's centre c_C instead of once per
+ * member: each member's target at c_C + d gets a(D_C) - d.g(D_C) and
+ * g(D_C) + J(D_C) d, D_C = c_C - x_B, when |D_C| - rho_C >= w (rho_C the
+ * largest distance of the cluster's targets from c_C); otherwise the entry is
+ * summed pair by pair.  The transpose takes the cluster's sums of s and of
+ * s (x_i - c_C), once per (node, cluster). */
+static int64_t cluster_end(const or_targets* T, int64_t C, int K) {
+    int64_t e = (C + 1) * K;
+    return e < T->ngroups ? e : T->ngroups;
+}
+
+static void cluster_box(const or_targets* T, int64_t C, int K, double lo[3], double hi[3]) {
+    for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+    for (int64_t g = C * K; g < cluster_end(T, C, K); ++g)
+        for (int k = 0; k < 3; ++k) {
+            if (T->glo[3 * g + k] < lo[k]) lo[k] = T->glo[3 * g + k];
+            if (T->ghi[3 * g + k] > hi[k]) hi[k] = T->ghi[3 * g + k];
+        }
+}
+
+static local_frame cluster_frame(const or_targets* T, int64_t C, int K) {
+    local_frame L;
+    double lo[3], hi[3];
+    cluster_box(T, C, K, lo, hi);
+    for (int k = 0; k < 3; ++k) L.c[k] = 0.5 * (lo[k] + hi[k]);
+    L.rho = 0.0;
+    for (int64_t i = T->goff[C * K]; i < T->goff[cluster_end(T, C, K)]; ++i) {
+        const double* y = T->y + 3 * i;
+        const double dl[3] = {y[0] - L.c[0], y[1] - L.c[1], y[2] - L.c[2]};
+        const double r = sqrt(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
+        if (r > L.rho) L.rho = r;
+    }
+    return L;
+}
+
+/* The local expansions of one target set: c = 1/local_theta, the cluster size
+ * K (0 or 1: groups only) and per far entry its class: 0 summed pair by pair,
+ * 1 expanded about its group's centre, 2 about its cluster's centre. */
+typedef struct { double c; int K; signed char* cls; } local_cfg;
+
+typedef struct { int64_t b, q; } node_entry;
+static int cmp_node_entry(const void* a, const void* b) {
+    const int64_t x = ((const node_entry*)a)->b, y = ((const node_entry*)b)->b;
+    return (x > y) - (x < y);
+}
+
+static signed char* local_classes(const or_octree* t, const or_targets* T, double c, int K) {
+    const int64_t ng = T->ngroups, nf = T->far_off[ng];
+    signed char* cls = calloc((size_t)(nf > 0 ? nf : 1), 1);
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t g = 0; g < ng; ++g)
+        for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q)
+            cls[q] = (signed char)is_local(t, T->far_id[q], T->glo + 3 * g, T->ghi + 3 * g, c);
+    if (K < 2) return cls;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t C = 0; C < (ng + K - 1) / K; ++C) {
+        const int64_t g0 = C * K, g1 = cluster_end(T, C, K), nm = g1 - g0;
+        if (nm < 2) continue;
+        double lo[3], hi[3];
+        cluster_box(T, C, K, lo, hi);
+        /* each member's expanded entries, sorted by node */
+        node_entry** ent = malloc(sizeof(node_entry*) * nm);
+        int64_t* cnt = calloc((size_t)nm, sizeof(int64_t));
+        for (int64_t m = 0; m < nm; ++m) {
+            const int64_t g = g0 + m;
+            ent[m] = malloc(sizeof(node_entry) * (T->far_off[g + 1] - T->far_off[g] + 1));
+            for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q)
+                if (cls[q] == 1) ent[m][cnt[m]++] = (node_entry){T->far_id[q], q};
+            qsort(ent[m], (size_t)cnt[m], sizeof(node_entry), cmp_node_entry);
+        }
+        int64_t* qm = malloc(sizeof(int64_t) * nm);
+        for (int64_t k = 0; k < cnt[0]; ++k) {
+            const int64_t b = ent[0][k].b;
+            if (!is_local(t, b, lo, hi, c)) continue;
+            int all = 1;
+            qm[0] = ent[0][k].q;
+            for (int64_t m = 1; m < nm && all; ++m) {
+                node_entry key = {b, 0};
+                node_entry* f = bsearch(&key, ent[m], (size_t)cnt[m], sizeof(node_entry), cmp_node_entry);
+                if (!f) all = 0;
+                else qm[m] = f->q;
+            }
+            if (all)
+                for (int64_t m = 0; m < nm; ++m) cls[qm[m]] = 2;
+        }
+        for (int64_t m = 0; m < nm; ++m) free(ent[m]);
+        free(ent); free(cnt); free(qm);
+    }
+    return cls;
+}
+
 /* Gather-form treecode for targets T against the source octree:
  *   op A : out (m)    = sum_far gradPhi(y - x_B) . mu_B + sum_near gradPhi(y - x_j) . mu_j
  *   op G : out (m x 3) = sum_far -HPhi(y - x_B) mu_B  + sum_near -HPhi(y - x_j) mu_j
@@ -707,7 +812,7 @@ static double local_eval(int op, const double* ce, const double dl[3], double ou
  */
 static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep_mode, double w,
                         const double* nu_sorted, double* out_sorted, double amb_tol, double* amb_sorted,
-                        double* abs_sorted, int far_order, double local_c) {
+                        double* abs_sorted, int far_order, const local_cfg* LC) {
     int dim = (op == OP_AT) ? 1 : 3;
     double* rep = malloc(sizeof(double) * 3 * (t->nnodes > 0 ? t->nnodes : 1));
     double* nuB = malloc(sizeof(double) * dim * (t->nnodes > 0 ? t->nnodes : 1));
@@ -716,27 +821,31 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
     double* S = dip ? malloc(sizeof(double) * 6 * (t->nnodes > 0 ? t->nnodes : 1)) : NULL;
     if (dip) node_dipoles(t, nu_sorted, S);
     const double w2 = eff_w2(w);
-    const int loc = local_c > 0.0 && rep_mode == 1 && !dip && op != OP_AT;
+    const int loc = LC && LC->c > 0.0 && rep_mode == 1 && !dip && op != OP_AT;
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < T->ngroups; ++g) {
         int64_t s = T->goff[g], e = T->goff[g + 1];
-        local_frame L = {{0, 0, 0}, 0.0};
-        if (loc) L = group_frame(T, g);
+        local_frame L[3] = {{{0, 0, 0}, 0.0}, {{0, 0, 0}, 0.0}, {{0, 0, 0}, 0.0}};   /* by class */
+        if (loc) L[1] = group_frame(T, g);
+        if (loc && LC->K >= 2) L[2] = cluster_frame(T, g / LC->K, LC->K);
         for (int64_t i = s; i < e; ++i) {
             const double* y = T->y + 3 * i;
             double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0;
             for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
                 int64_t b = T->far_id[q];
-                /* a local entry: its term expanded about c_g when all its pairs clear the cut-off */
+                /* an expanded entry: its term expanded about the centre of its group
+                 * (class 1) or cluster (class 2) when all its pairs clear the cut-off */
                 int use = 0, lamb = 0;
                 double ev[3] = {0, 0, 0}, evabs = 0.0;
-                if (loc && is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c)) {
-                    const double D[3] = {L.c[0] - rep[3 * b], L.c[1] - rep[3 * b + 1], L.c[2] - rep[3 * b + 2]};
-                    use = local_use(D, L.rho, w2, amb_sorted ? amb_tol : 0.0, &lamb);
+                const int cl = loc ? LC->cls[q] : 0;
+                if (cl) {
+                    const local_frame* F = &L[cl];
+                    const double D[3] = {F->c[0] - rep[3 * b], F->c[1] - rep[3 * b + 1], F->c[2] - rep[3 * b + 2]};
+                    use = local_use(D, F->rho, w2, amb_sorted ? amb_tol : 0.0, &lamb);
                     if (use || lamb) {
                         double ce[10];
                         local_coeffs(D, nuB + 3 * b, ce);
-                        const double dl[3] = {y[0] - L.c[0], y[1] - L.c[1], y[2] - L.c[2]};
+                        const double dl[3] = {y[0] - F->c[0], y[1] - F->c[1], y[2] - F->c[2]};
                         evabs = local_eval(op, ce, dl, ev);
                     }
                 }
@@ -822,27 +931,37 @@ static void tree_gather(const or_octree* t, const or_targets* T, int op, int rep
  * with the same cut-off decision as the node's monopole term. */
 static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w,
                                const double* s_sorted, double* out_sorted, double amb_tol,
-                               double* amb_sorted, double* abs_sorted, int far_order, double local_c) {
+                               double* amb_sorted, double* abs_sorted, int far_order, const local_cfg* LC) {
     int64_t nn = t->nnodes, ng = T->ngroups;
     const double w2 = eff_w2(w);
-    /* local expansions: per group c_g, rho_g, S_g, D_g and the bounds of their terms */
-    const int loc = local_c > 0.0 && far_order == 0;
+    /* local expansions: per group (and per cluster) its centre, rho, S = sum s_i,
+     * D = sum s_i (x_i - c) and the bounds of their terms */
+    const int loc = LC && LC->c > 0.0 && far_order == 0;
+    const int K = loc && LC->K >= 2 ? LC->K : 0;
+    const int64_t ncl = K ? (ng + K - 1) / K : 0;
     local_frame* LS = calloc((size_t)(ng > 0 ? ng : 1), sizeof(local_frame));
-    double* SD = calloc((size_t)(ng > 0 ? ng : 1) * 6, sizeof(double));   /* S, Dg[3], sum|s|, sum|s||delta| */
+    double* SD = calloc((size_t)(ng > 0 ? ng : 1) * 6, sizeof(double));   /* S, D[3], sum|s|, sum|s||delta| */
+    local_frame* LSC = calloc((size_t)(ncl > 0 ? ncl : 1), sizeof(local_frame));
+    double* SDC = calloc((size_t)(ncl > 0 ? ncl : 1) * 6, sizeof(double));
     if (loc) {
         #pragma omp parallel for schedule(dynamic, 16)
-        for (int64_t g = 0; g < ng; ++g) {
-            LS[g] = group_frame(T, g);
-            double* sd = SD + 6 * g;
-            for (int64_t i = T->goff[g]; i < T->goff[g + 1]; ++i) {
-                const double dl[3] = {T->y[3 * i] - LS[g].c[0], T->y[3 * i + 1] - LS[g].c[1],
-                                      T->y[3 * i + 2] - LS[g].c[2]};
+        for (int64_t u = 0; u < ng + ncl; ++u) {
+            const int is_cl = u >= ng;
+            const int64_t id = is_cl ? u - ng : u;
+            const local_frame F = is_cl ? cluster_frame(T, id, K) : group_frame(T, id);
+            double* sd = is_cl ? SDC + 6 * id : SD + 6 * id;
+            const int64_t i0 = is_cl ? T->goff[id * K] : T->goff[id];
+            const int64_t i1 = is_cl ? T->goff[cluster_end(T, id, K)] : T->goff[id + 1];
+            for (int64_t i = i0; i < i1; ++i) {
+                const double dl[3] = {T->y[3 * i] - F.c[0], T->y[3 * i + 1] - F.c[1], T->y[3 * i + 2] - F.c[2]};
                 const double si = s_sorted[i];
                 sd[0] += si;
                 for (int k = 0; k < 3; ++k) sd[1 + k] += si * dl[k];
                 sd[4] += fabs(si);
                 sd[5] += fabs(si) * sqrt(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
             }
+            if (is_cl) LSC[id] = F;
+            else LS[id] = F;
         }
     }
     /* transposed lists: node -> groups using it (far), leaf -> groups using it (near) */
@@ -852,13 +971,17 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
     for (int64_t q = 0; q < T->near_off[ng]; ++q) ncnt[T->near_id[q] + 1]++;
     for (int64_t b = 0; b < nn; ++b) { fcnt[b + 1] += fcnt[b]; ncnt[b + 1] += ncnt[b]; }
     int64_t* fg = malloc(sizeof(int64_t) * (fcnt[nn] > 0 ? fcnt[nn] : 1));
+    int64_t* fq = malloc(sizeof(int64_t) * (fcnt[nn] > 0 ? fcnt[nn] : 1));   /* the far entry */
     int64_t* ngp = malloc(sizeof(int64_t) * (ncnt[nn] > 0 ? ncnt[nn] : 1));
     int64_t* fpos = malloc(sizeof(int64_t) * (nn > 0 ? nn : 1));
     int64_t* npos = malloc(sizeof(int64_t) * (nn > 0 ? nn : 1));
     memcpy(fpos, fcnt, sizeof(int64_t) * nn);
     memcpy(npos, ncnt, sizeof(int64_t) * nn);
     for (int64_t g = 0; g < ng; ++g) {
-        for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) fg[fpos[T->far_id[q]]++] = g;
+        for (int64_t q = T->far_off[g]; q < T->far_off[g + 1]; ++q) {
+            fq[fpos[T->far_id[q]]] = q;
+            fg[fpos[T->far_id[q]]++] = g;
+        }
         for (int64_t q = T->near_off[g]; q < T->near_off[g + 1]; ++q) ngp[npos[T->near_id[q]]++] = g;
     }
     double* V = calloc((size_t)(nn > 0 ? nn : 1) * 3, sizeof(double));
@@ -872,15 +995,18 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         double acc[3] = {0, 0, 0}, ab = 0.0, as = 0.0, h[6] = {0, 0, 0, 0, 0, 0}, hn = 0.0;
         for (int64_t q = fcnt[b]; q < fcnt[b + 1]; ++q) {
             int64_t g = fg[q];
-            int64_t s = T->goff[g], e = T->goff[g + 1];
-            /* a local entry: the transposed expansion when all its pairs clear the cut-off */
+            const int cl = loc ? LC->cls[fq[q]] : 0;
+            if (cl == 2 && g % K != 0) continue;     /* a cluster's entry: carried by its first member */
+            /* the targets behind the entry: the group's, or for class 2 the cluster's */
+            int64_t s = T->goff[g], e = cl == 2 ? T->goff[cluster_end(T, g / K, K)] : T->goff[g + 1];
+            /* an expanded entry: the transposed expansion when all its pairs clear the cut-off */
             int use = 0, lamb = 0;
             double lv[3] = {0, 0, 0}, pw[3] = {0, 0, 0};
-            if (loc && is_local(t, b, T->glo + 3 * g, T->ghi + 3 * g, local_c)) {
-                const double D[3] = {LS[g].c[0] - rep[3 * b], LS[g].c[1] - rep[3 * b + 1],
-                                     LS[g].c[2] - rep[3 * b + 2]};
-                use = local_use(D, LS[g].rho, w2, amb_sorted ? amb_tol : 0.0, &lamb);
-                const double* sd = SD + 6 * g;
+            if (cl) {
+                const local_frame* F = cl == 2 ? &LSC[g / K] : &LS[g];
+                const double D[3] = {F->c[0] - rep[3 * b], F->c[1] - rep[3 * b + 1], F->c[2] - rep[3 * b + 2]};
+                use = local_use(D, F->rho, w2, amb_sorted ? amb_tol : 0.0, &lamb);
+                const double* sd = cl == 2 ? SDC + 6 * (g / K) : SD + 6 * g;
                 local_adjoint(D, sd[0], sd + 1, lv);
                 if (use) {
                     const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
@@ -974,7 +1100,7 @@ static void tree_adjoint_exact(const or_octree* t, const or_targets* T, double w
         }
     }
     free(fcnt); free(ncnt); free(fg); free(ngp); free(fpos); free(npos); free(V); free(VA); free(VS);
-    free(H); free(HN); free(LS); free(SD);
+    free(H); free(HN); free(LS); free(SD); free(LSC); free(SDC); free(fq);
 }
 
 /* On-surface application of an operator.  nu and out are in input order,
@@ -991,9 +1117,12 @@ void or_tree_apply(const or_tree* T, int op, int rep_mode, double w, const doubl
     double* abss = abssum ? malloc(sizeof(double) * (n > 0 ? n : 1)) : NULL;
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < din; ++k) nus[din * i + k] = nu[din * t->perm[i] + k];
+    local_cfg cfg = {T->local_c, T->local_cluster, T->self_cls};
     if (op == OP_AT && rep_mode == 1)
-        tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs, abss, T->far_order, T->local_c);
-    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs, abss, T->far_order, T->local_c);
+        tree_adjoint_exact(t, &T->self, w, nus, outs, amb_tol, ambs, abss, T->far_order,
+                           T->self_cls ? &cfg : NULL);
+    else tree_gather(t, &T->self, op, rep_mode, w, nus, outs, amb_tol, ambs, abss, T->far_order,
+                     T->self_cls ? &cfg : NULL);
     for (int64_t i = 0; i < n; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * T->self.perm[i] + k] = outs[dout * i + k];
         if (amb) amb[T->self.perm[i]] = ambs[i];
@@ -1017,7 +1146,10 @@ void or_tree_apply_at(const or_tree* T, int op, int rep_mode, double w, const do
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) nus[3 * i + k] = nu[3 * t->perm[i] + k];
     double* abss = abssum ? malloc(sizeof(double) * (m > 0 ? m : 1)) : NULL;
-    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL, abss, T->far_order, T->local_c);
+    local_cfg cfg = {T->local_c, T->local_cluster, NULL};
+    if (T->local_c > 0.0) cfg.cls = local_classes(t, &Q, T->local_c, T->local_cluster);
+    tree_gather(t, &Q, op, rep_mode, w, nus, outs, 0.0, NULL, abss, T->far_order, cfg.cls ? &cfg : NULL);
+    free(cfg.cls);
     for (int64_t i = 0; i < m; ++i) {
         for (int k = 0; k < dout; ++k) out[dout * Q.perm[i] + k] = outs[dout * i + k];
         if (abssum) abssum[Q.perm[i]] = abss[i];

@@ -5,7 +5,8 @@ Eq. 13's weights taken as the signed s_i instead of |s_i|, or its
 normalisation by sum |nu_j| dropped, in the paper's treecode or in the group
 treecode's rep_mode 0; a sign or factor of the first-order far-field terms or
 of their transpose; a sign or factor of the local expansions, of their
-transpose, or their cut-off decision -- compiles the copy, swaps it in for the
+transpose, or their cut-off decision; the clusters' centre, sums or count --
+compiles the copy, swaps it in for the
 real oracle and checks that the pins of tests/test_oracle_paper_tree.py,
 tests/test_oracle_dipole.py and tests/test_oracle_local.py then fail.  The copy
 lives in pytest's temporary directory; the real oracle is untouched.
@@ -77,6 +78,18 @@ MUTATIONS = [
      "return m > 0.0 && m2 >= w2;",
      "return m > 0.0 && m >= w2;",
      [lambda: lpins.test_groups_fall_back_to_pairs_at_wide_cutoffs()]),
+    ("cluster expansion: taken about the group's centre",
+     "if (loc && LC->K >= 2) L[2] = cluster_frame(T, g / LC->K, LC->K);",
+     "if (loc && LC->K >= 2) L[2] = group_frame(T, g);",
+     [lambda: lpins.test_cluster_error_order(OP_A), lambda: lpins.test_cluster_error_order(OP_G)]),
+    ("cluster expansion: its transpose from the first member's sums only",
+     "const double* sd = cl == 2 ? SDC + 6 * (g / K) : SD + 6 * g;",
+     "const double* sd = SD + 6 * g;",
+     [lambda: lpins.test_cluster_error_order_of_the_transpose()]),
+    ("cluster expansion: its transpose counted once per member",
+     "if (cl == 2 && g % K != 0) continue;",
+     "if (cl == 2 && g % K != 0 && 0) continue;",
+     [lambda: lpins.test_cluster_error_order_of_the_transpose()]),
     ("local expansion: the cut-off bound without the group radius",
      "const double m = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]) - rho;",
      "const double m = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);",
