@@ -62,6 +62,7 @@ FLOPS_ITER = 2 * FLOPS_AG + FLOPS_AT               # A+G(mu), A^T(s), A+G(r) per
 FLOPS_LOCAL_AG, FLOPS_LOCAL_AT = 88, 41
 FLOPS_LOCAL_ITER = 2 * FLOPS_LOCAL_AG + FLOPS_LOCAL_AT
 LOCAL_THETA = 0.5    # local expansions of far nodes about target groups (0 = off)
+LOCAL_CLUSTER = 4    # second expansion level: clusters of that many groups (0 = none)
 PAPER_RTX3090_ITER_PER_S_500K = 40 / 31.63          # context only (different model and GPU)
 # Variants solved once each after the timed region (name, tree parameters, timed solves):
 # the paper's own treecode as printed (Alg. 4 per target and per call, leaf size 1,
@@ -73,7 +74,8 @@ VARIANTS = [
     ("paper_alg4_per_target_leaf1_theta0.5", dict(theta=0.5, leaf_size=1, rep_mode=0, criterion=1), 1),
     ("pairwise_far_field_theta0.5", dict(theta=0.5, local_theta=0.0), 3),
     ("group_lists_theta0.8", dict(theta=0.8), 3),
-    ("local_expansions_theta0.8", dict(theta=0.8, local_theta=0.5), 3),
+    ("local_expansions_one_level_theta0.5", dict(theta=0.5, local_theta=0.5), 3),
+    ("local_expansions_theta0.8", dict(theta=0.8, local_theta=0.5, local_cluster=4), 3),
     ("first_order_far_field_theta0.5", dict(theta=0.5, far_order=1), 2),
     ("first_order_far_field_theta0.8", dict(theta=0.8, far_order=1), 2),
 ]
@@ -253,7 +255,7 @@ def run_gpu(args):
 
     def step(prof: dict | None, classes=None):
         flush.zero_()
-        t = W.Tree(pts, theta=THETA, local_theta=LOCAL_THETA)
+        t = W.Tree(pts, theta=THETA, local_theta=LOCAL_THETA, local_cluster=LOCAL_CLUSTER)
         if prof is not None:
             t.profile(True, classes=classes)
         t.iterate(n_iter=N_ITER, w1=W1, w2=W2, out=mu)
@@ -261,7 +263,7 @@ def run_gpu(args):
             for k, (cnt, ms) in t.profile_read().items():
                 a, b = prof.get(k, (0, 0.0))
                 prof[k] = (a + cnt, b + ms)
-        stats = t.stats() + t.local_stats()
+        stats = t.stats() + tuple(a + b for a, b in zip(t.local_stats(), t.cluster_stats()))
         t.close()
         return stats
 
@@ -272,7 +274,7 @@ def run_gpu(args):
     # T_pre / T_main split on one untimed step (CUDA events)
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record(stream)
-    t = W.Tree(pts, theta=THETA, local_theta=LOCAL_THETA)
+    t = W.Tree(pts, theta=THETA, local_theta=LOCAL_THETA, local_cluster=LOCAL_CLUSTER)
     e1.record(stream)
     t.iterate(n_iter=N_ITER, w1=W1, w2=W2, out=mu)
     e2.record(stream)
@@ -316,11 +318,13 @@ def run_gpu(args):
     if not args.no_e2e:
         h_pts = torch.from_numpy(c.points).pin_memory()
         h_mu = torch.empty(n, 3, dtype=torch.float32).pin_memory()
-        W.orient(h_pts, out=h_mu, theta=THETA, n_iter=N_ITER, w1=W1, w2=W2, local_theta=LOCAL_THETA)  # warm-up
+        W.orient(h_pts, out=h_mu, theta=THETA, n_iter=N_ITER, w1=W1, w2=W2, local_theta=LOCAL_THETA,
+                 local_cluster=LOCAL_CLUSTER)  # warm-up
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            W.orient(h_pts, out=h_mu, theta=THETA, n_iter=N_ITER, w1=W1, w2=W2, local_theta=LOCAL_THETA)
+            W.orient(h_pts, out=h_mu, theta=THETA, n_iter=N_ITER, w1=W1, w2=W2, local_theta=LOCAL_THETA,
+                     local_cluster=LOCAL_CLUSTER)
         torch.cuda.synchronize(dev)
         dt = max_over_ranks(dist, time.perf_counter() - t0)
         e2e = {"value": whole_job_rate(world, N_ITER, args.steps, 1e3 * dt), "unit": "iter/s",
@@ -377,7 +381,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_points": n, "iterations_per_step": N_ITER,
-                   "theta": THETA, "local_theta": LOCAL_THETA,
+                   "theta": THETA, "local_theta": LOCAL_THETA, "local_cluster": LOCAL_CLUSTER,
                    "l2": "flushed before every step (256 MiB write, inside the timed region)",
                    "step": "tree build + 40 iterations"},
         "interactions_per_s": inter_per_iter * N_ITER * args.steps * world / (ms / 1e3),
@@ -419,7 +423,7 @@ def run_gpu(args):
 
 
 def main():
-    global CONFIG_NAME, WORKLOAD, LOCAL_THETA
+    global CONFIG_NAME, WORKLOAD, LOCAL_THETA, LOCAL_CLUSTER
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -433,9 +437,12 @@ def main():
                     help="workload (the default is the one the metric is quoted on)")
     ap.add_argument("--local-theta", type=float, default=LOCAL_THETA,
                     help="local expansions of far nodes about target groups (0 = off)")
+    ap.add_argument("--local-cluster", type=int, default=LOCAL_CLUSTER,
+                    help="second expansion level: clusters of that many groups (0 = none)")
     args = ap.parse_args()
     CONFIG_NAME, WORKLOAD = args.config, WORKLOADS[args.config]
     LOCAL_THETA = args.local_theta
+    LOCAL_CLUSTER = args.local_cluster
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -117,6 +117,14 @@ typedef struct {
                           name; its error is second order in (group extent / distance).
                           0 = off (default); negative, non-finite, or > 0 with rep_mode 0,
                           criterion 1 or far_order 1: WNNC_EINVAL */
+    int local_cluster; /* with local_theta > 0, a second level of local expansions: clusters of
+                          local_cluster consecutive target groups (2..8; 0 = none, the default).
+                          A far node that lies in the expanded part of every member group's list
+                          and is itself local for the cluster's box (the union of the members'
+                          boxes, the same test) is expanded once about the cluster's box centre
+                          instead of once per member, and its A^T term is taken once per
+                          cluster; the cut-off rule is the group's with the cluster's radius
+                          (otherwise the entry's pairs are summed).  Other values: WNNC_EINVAL */
 } wnnc_tree_params;
 
 /* Iteration parameters (Alg. 3; Sec. 5.1.1 defaults n = 40, w1 = 0.002, w2 = 0.016). */
@@ -237,6 +245,11 @@ wnnc_status wnnc_get_stats(const wnnc_tree* tree, int64_t* far_pairs, int64_t* n
  * call is summed pair by pair on that call but still counted here.  host out. */
 wnnc_status wnnc_get_local_stats(const wnnc_tree* tree, int64_t* local_entries, int64_t* local_pairs);
 
+/* With local_cluster > 0: the (cluster, node) expansions of the second level
+ * and the (target, node) pairs they stand for (not counted by
+ * wnnc_get_local_stats); both 0 otherwise.  host out. */
+wnnc_status wnnc_get_cluster_stats(const wnnc_tree* tree, int64_t* cluster_entries, int64_t* cluster_pairs);
+
 /*
  * Sizes of the tree (host out, any may be NULL): points, nodes, leaves,
  * target groups, far-list entries, merged near ranges, transposed near entries,
@@ -283,10 +296,11 @@ wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node
 
 /* With local_theta > 0 each group's far list holds first the entries summed
  * pair by pair, then (from far_lsplit[g] on) the entries expanded about the
- * group's centre, each part ascending by node id.  far_lsplit: int32
- * [ngroups], host out (far_off[g + 1] for every group when local_theta = 0).
- * WNNC_EINVAL if far_lsplit is NULL. */
-wnnc_status wnnc_tree_export_local(const wnnc_tree* tree, int32_t* far_lsplit);
+ * group's centre, then (from far_csplit[g] on, local_cluster > 0) those
+ * expanded about its cluster's centre, each part ascending by node id.
+ * far_lsplit, far_csplit: int32 [ngroups], host out (far_off[g + 1] where a
+ * part is absent).  WNNC_EINVAL if either is NULL. */
+wnnc_status wnnc_tree_export_local(const wnnc_tree* tree, int32_t* far_lsplit, int32_t* far_csplit);
 
 /*
  * Kernel timing (not in the paper; the tracing facility of this library).

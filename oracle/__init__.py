@@ -91,6 +91,7 @@ def load(path: str):
     L.or_tree_build.restype = c_void_p
     L.or_tree_set_far_order.argtypes = [c_void_p, c_int]
     L.or_tree_set_local.argtypes = [c_void_p, d, c_int]
+    L.or_tree_local_classes.argtypes = [c_void_p, c_void_p]
     L.or_tree_free.argtypes = [c_void_p]
     L.or_tree_nnodes.argtypes = [c_void_p]
     L.or_tree_nnodes.restype = i64
@@ -262,6 +263,13 @@ class Tree:
         g = np.zeros(ng + 1, np.int64)
         lib().or_tree_groups(self._h, _p(g))
         return g
+
+    def local_classes(self):
+        """Per far entry (in the order of ``lists``): 0 summed pair by pair, 1
+        expanded about its group's centre, 2 about its cluster's."""
+        c = np.zeros(max(self.counts()[0], 1), np.int8)
+        lib().or_tree_local_classes(self._h, _p(c))
+        return c[:self.counts()[0]]
 
     def lists(self):
         ng = lib().or_tree_ngroups(self._h)

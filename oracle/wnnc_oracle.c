@@ -496,6 +496,14 @@ void or_tree_set_far_order(or_tree* T, int order) { T->far_order = order; }
  * (rep_mode 1, far_order 0): a far node b is expanded for a group when the box
  * gap exceeds 1/local_theta times the group box's largest extent; local_theta
  * 0 switches them off. */
+/* The class of every far entry of the points as targets (in the order of
+ * or_tree_lists): 0 summed pair by pair, 1 expanded about its group's centre,
+ * 2 about its cluster's; all 0 without local expansions. */
+void or_tree_local_classes(const or_tree* T, signed char* out) {
+    const int64_t nf = T->self.far_off[T->self.ngroups];
+    for (int64_t q = 0; q < nf; ++q) out[q] = T->self_cls ? T->self_cls[q] : 0;
+}
+
 void or_tree_set_local(or_tree* T, double local_theta, int cluster) {
     T->local_c = local_theta > 0.0 ? 1.0 / local_theta : 0.0;
     T->local_cluster = cluster;

@@ -48,7 +48,7 @@ class WnncError(RuntimeError):
 class TreeParams(Structure):
     _fields_ = [("max_depth", c_int), ("leaf_size", c_int), ("theta", c_float),
                 ("rep_mode", c_int), ("moments_fp64", c_int), ("near_bf16", c_int), ("criterion", c_int),
-                ("far_order", c_int), ("local_theta", c_float)]
+                ("far_order", c_int), ("local_theta", c_float), ("local_cluster", c_int)]
 
 
 class IterParams(Structure):
@@ -86,7 +86,8 @@ def lib():
     L.wnnc_iterate.argtypes = [P, P, P, POINTER(IterParams), P, P]
     L.wnnc_get_stats.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
     L.wnnc_get_local_stats.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
-    L.wnnc_tree_export_local.argtypes = [P, P]
+    L.wnnc_tree_export_local.argtypes = [P, P, P]
+    L.wnnc_get_cluster_stats.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
     L.wnnc_tree_info.argtypes = [P] + [POINTER(c_int64)] * 7 + [POINTER(c_int)]
     L.wnnc_tree_export.argtypes = [P] + [P] * 11
     L.wnnc_tree_walk_stats.argtypes = [P, P, P]
@@ -116,7 +117,7 @@ def lib():
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
                  "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
                  "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_get_local_stats", "wnnc_tree_info",
-                 "wnnc_tree_export_local",
+                 "wnnc_tree_export_local", "wnnc_get_cluster_stats",
                  "wnnc_tree_export", "wnnc_tree_walk_stats", "wnnc_profile_enable", "wnnc_profile_classes", "wnnc_profile_read",
                  "wnnc_profile_reset", "wnnc_sync_status", "wnnc_knn16", "wnnc_mlp_create",
                  "wnnc_mlp_free", "wnnc_mlp_set_params", "wnnc_mlp_get_params", "wnnc_mlp_forward",
@@ -216,7 +217,8 @@ class Tree:
 
     def __init__(self, points, theta: float = 0.5, leaf_size: int = 8, max_depth: int = 15,
                  rep_mode: int = 1, moments_fp64: bool = False, near_bf16: bool = False,
-                 criterion: int = 0, far_order: int = 0, local_theta: float = 0.0):
+                 criterion: int = 0, far_order: int = 0, local_theta: float = 0.0,
+                 local_cluster: int = 0):
         """criterion 0: far decisions per target group on boxes, lists built once
         (default); 1: the paper's per-target test of Alg. 4 on every call
         (needs rep_mode 0; with leaf_size 1 it is Alg. 4 as printed).
@@ -225,7 +227,10 @@ class Tree:
         local_theta > 0: far nodes whose box gap to a target group exceeds the
         group box's extent / local_theta are expanded to first order about the
         group's centre instead of summed per target (rep_mode 1, criterion 0,
-        far_order 0; A^T stays the exact transpose)."""
+        far_order 0; A^T stays the exact transpose).  local_cluster = K (2..8)
+        adds a second level: far nodes expanded for all K groups of a cluster
+        of consecutive groups and local for the cluster's box are expanded once
+        about the cluster's centre."""
         pts = points if isinstance(points, torch.Tensor) else torch.as_tensor(points)
         self.device = pts.device if pts.is_cuda else torch.device("cuda", torch.cuda.current_device())
         pts = _dev_f32(pts, (-1, 3), self.device)
@@ -237,6 +242,7 @@ class Tree:
         p.criterion = int(criterion)
         p.far_order = int(far_order)
         p.local_theta = float(local_theta)
+        p.local_cluster = int(local_cluster)
         self.params = p
         h = c_void_p()
         with torch.cuda.device(self.device):
@@ -330,6 +336,12 @@ class Tree:
         _check(lib().wnnc_get_local_stats(self._h, ctypes.byref(e), ctypes.byref(pp)))
         return e.value, pp.value
 
+    def cluster_stats(self):
+        """((cluster, node) expansions of the second level, the pairs they stand for)."""
+        e, pp = c_int64(), c_int64()
+        _check(lib().wnnc_get_cluster_stats(self._h, ctypes.byref(e), ctypes.byref(pp)))
+        return e.value, pp.value
+
     def info(self) -> dict:
         v = [c_int64() for _ in range(7)]
         d = c_int()
@@ -363,8 +375,9 @@ class Tree:
         a["far_id"] = a["far_id"][:inf["far_entries"]]
         a["near_rng"] = a["near_rng"][:inf["near_ranges"]]
         a["far_lsplit"] = np.zeros(ng, np.int32)
+        a["far_csplit"] = np.zeros(ng, np.int32)
         if ng:
-            _check(lib().wnnc_tree_export_local(self._h, ptr(a["far_lsplit"])))
+            _check(lib().wnnc_tree_export_local(self._h, ptr(a["far_lsplit"]), ptr(a["far_csplit"])))
         return a
 
     def profile(self, enable: bool = True, classes=None):

@@ -116,6 +116,7 @@ static void alloc_workspace(Tree& t) {
         t.node_abs = dalloc<float4>(nn);
         t.local_rec = dalloc<float4>(2 * (size_t)nn);
         t.gadj = dalloc<float4>(2 * (size_t)t.self.ngroups);
+        if (t.self.nclusters) t.cadj = dalloc<float4>(2 * (size_t)t.self.nclusters);
         local_setup(t, alloc_stream());
     }
 }
@@ -171,6 +172,10 @@ static void check_params(const wnnc_tree_params& p) {
         fail(WNNC_EINVAL, "local_theta must be finite and >= 0");
     if (p.local_theta > 0.f && (p.rep_mode != 1 || p.criterion != 0 || p.far_order != 0))
         fail(WNNC_EINVAL, "local_theta > 0 needs rep_mode 1, criterion 0 and far_order 0");
+    if (p.local_cluster != 0 && (p.local_cluster < 2 || p.local_cluster > kMaxCluster))
+        fail(WNNC_EINVAL, "local_cluster must be 0 or in [2, 8]");
+    if (p.local_cluster != 0 && !(p.local_theta > 0.f))
+        fail(WNNC_EINVAL, "local_cluster needs local_theta > 0");
 }
 
 static void check_w(float w) {
@@ -202,6 +207,7 @@ wnnc_status wnnc_tree_params_default(wnnc_tree_params* p) {
     p->criterion = 0;
     p->far_order = 0;
     p->local_theta = 0.f;
+    p->local_cluster = 0;
     return WNNC_OK;
 }
 
@@ -399,6 +405,14 @@ wnnc_status wnnc_get_local_stats(const wnnc_tree* tree, int64_t* local_entries, 
     });
 }
 
+wnnc_status wnnc_get_cluster_stats(const wnnc_tree* tree, int64_t* cluster_entries, int64_t* cluster_pairs) {
+    return guarded([&] {
+        Tree& t = unwrap(tree);
+        if (cluster_entries) *cluster_entries = t.self.cluster_entries;
+        if (cluster_pairs) *cluster_pairs = t.self.cluster_pairs;
+    });
+}
+
 wnnc_status wnnc_tree_info(const wnnc_tree* tree, int64_t* n, int64_t* nnodes, int64_t* nleaves,
                            int64_t* ngroups, int64_t* far_entries, int64_t* near_ranges,
                            int64_t* tnear_entries, int* depth) {
@@ -451,15 +465,17 @@ wnnc_status wnnc_tree_export(const wnnc_tree* tree, int64_t* perm, int32_t* node
     });
 }
 
-wnnc_status wnnc_tree_export_local(const wnnc_tree* tree, int32_t* far_lsplit) {
+wnnc_status wnnc_tree_export_local(const wnnc_tree* tree, int32_t* far_lsplit, int32_t* far_csplit) {
     return guarded([&] {
         Tree& t = unwrap(tree);
-        if (!far_lsplit) fail(WNNC_EINVAL, "far_lsplit is NULL");
+        if (!far_lsplit || !far_csplit) fail(WNNC_EINVAL, "far_lsplit or far_csplit is NULL");
         WNNC_CUDA(cudaDeviceSynchronize());
         const TargetSet& S = t.self;
         if (S.ngroups == 0) return;
-        const int* src = S.far_lsplit ? S.far_lsplit : S.far_off + 1;
-        WNNC_CUDA(cudaMemcpy(far_lsplit, src, sizeof(int) * S.ngroups, cudaMemcpyDeviceToHost));
+        const int* ls = S.far_lsplit ? S.far_lsplit : S.far_off + 1;
+        const int* cs = S.far_csplit ? S.far_csplit : S.far_off + 1;
+        WNNC_CUDA(cudaMemcpy(far_lsplit, ls, sizeof(int) * S.ngroups, cudaMemcpyDeviceToHost));
+        WNNC_CUDA(cudaMemcpy(far_csplit, cs, sizeof(int) * S.ngroups, cudaMemcpyDeviceToHost));
     });
 }
 

@@ -15,6 +15,7 @@ constexpr int kWarp = 32;
 constexpr int kGroup = 32;          // targets per group = one warp, one target per lane
 constexpr int kKeyBits = 45;        // 15 bits per axis -> depth 15
 constexpr int kMaxDepth = 15;
+constexpr int kMaxCluster = 8;      // largest local_cluster (groups per cluster)
 constexpr float kInv4Pi = 0.0795774715459476678f;   // 1/(4 pi)
 
 // Device-side error flags (latched per tree, read by wnnc_sync_status).
@@ -151,6 +152,12 @@ struct TargetSet {
                                   // far_lsplit[g] on) expanded about the group centre;
                                   // ascending within each part
     int* far_lsplit = nullptr;    // [ngroups] first expanded entry of each group (local_theta > 0)
+    int* far_csplit = nullptr;    // [ngroups] first entry expanded about the group's cluster
+                                  // (local_cluster > 0; the group's expansions end there)
+    int nclusters = 0;            // clusters of cluster_k consecutive groups (local_cluster > 0)
+    int cluster_k = 0;
+    float4* cctr = nullptr;       // [nclusters] cluster frame origin (dyadic) in xyz
+    float4* cexp = nullptr;       // [nclusters] expansion centre in that frame and the radius (w)
     float4* gctr = nullptr;       // [ngroups] expansion centre in the group's frame, and the
                                   // group's radius about it (w), rounded up
     int* near_off = nullptr;      // [ngroups+1]
@@ -159,6 +166,8 @@ struct TargetSet {
     int64_t far_pairs = 0, near_pairs = 0;
     int64_t local_entries = 0;    // far entries expanded about the group centre (local_theta > 0)
     int64_t local_pairs = 0;      // the pairs those entries stand for (not in far_pairs)
+    int64_t cluster_entries = 0;  // (cluster, node) expansions standing for cluster_pairs of them
+    int64_t cluster_pairs = 0;
     // how the list traversal ran: groups that a first-in first-out walk
     // finished as stack walks; whether every group ran again as a stack walk
     // with the larger buffer
@@ -282,6 +291,9 @@ struct Tree {
     int* tfar_lsplit = nullptr;   // per node: first expanded transposed entry; tfar_ent holds the
                                   // entry index before it and the entry's group from it on
     float4* gadj = nullptr;       // per group, rebuilt per adjoint call: (c_g, rho_g), (D, S)
+    int* tfar_csplit = nullptr;   // per node: first transposed entry expanded about a cluster
+                                  // (local_cluster > 0; tfar_ent holds the cluster from there)
+    float4* cadj = nullptr;       // per cluster, rebuilt per adjoint call: (c_C, rho_C), (D, S)
     float4* contrib_h0 = nullptr; // per far entry: sum s HPhi, (xx, yy, zz, -) and (xy, xz, yz, -)
     float4* contrib_h1 = nullptr;
     float4* hnode0 = nullptr;     // per node: the entries' sums of s HPhi (same two parts)

@@ -291,6 +291,11 @@ struct GatherArgs {
     const int* lsplit;        // local_theta > 0: first expanded far entry of each group
     const float4* gctr;       //   the expansion centre in the group's frame and the group's radius
     const float4* lrec;       //   per node (centroid, M_x), (M_y, M_z, 0, 0) of this call's field
+    const int* csplit;        // local_cluster > 0: first entry expanded about the group's cluster
+    int cluster_k;            //   groups per cluster
+    int nclusters;
+    const float4* cctr;       //   cluster frame origins
+    const float4* cexp;       //   expansion centre in the cluster's frame and the cluster's radius
 };
 
 // Accumulators: (x, y, z) holds the A / A^T sum, or for G the sum of
@@ -861,7 +866,7 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_local_ag(GatherArgs A, flo
     const float4 cg = A.gctr[g];
     const int64_t it = (int64_t)i0 + lane;
     const float4 tl = lane < gsize ? shift(A.tcorig[it >> 5], o, A.tpos[it]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int w0 = A.lsplit[g], w1 = A.far_off[g + 1];
+    const int w0 = A.lsplit[g], w1 = A.csplit ? A.csplit[g] : A.far_off[g + 1];
     LocalAcc L;
 #pragma unroll
     for (int q = 0; q < 10; ++q) L.c[q] = make_float2(0.f, 0.f);
@@ -946,6 +951,129 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_local_ag(GatherArgs A, flo
         f.z += k[3] + fmaf(k[8], dx, fmaf(k[9], dy, k[6] * dz));
     }
     if (lane < gsize) corr[i0 + lane] = f;
+}
+
+// The second level (local_cluster = K): one warp per cluster of K consecutive
+// groups, over the entries expanded about the cluster's centre (the first
+// member's part from csplit on; every member lists the same nodes).  The same
+// terms as k_local_ag about the cluster's centre c_C, evaluated at each of the
+// cluster's up to 32 K targets (lane l takes targets l, l + 32, ...) and added
+// to corr; an entry whose pairs may straddle the cut-off (|E| - rho_C < w) is
+// queued and summed pair by pair at every target of the cluster.
+template <int OP>
+__global__ void __launch_bounds__(32 * kLocalWarps) k_local_cl(GatherArgs A, float4* corr) {
+    constexpr bool kG = OP == kOpG || OP == kOpAG;
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ float4 tq_all[kLocalWarps][32 * kMaxCluster];   // targets in the cluster's frame
+    __shared__ float4 fs_all[kLocalWarps][32 * kMaxCluster];   // queued entries' pair sums (G, A)
+    __shared__ int qb_all[kLocalWarps][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int C = blockIdx.x * kLocalWarps + wl;
+    if (C >= A.nclusters) return;
+    const int K = A.cluster_k;
+    const int g0 = C * K, g1 = min(g0 + K, A.ngroups);
+    const int i0 = A.goff[g0], nt = A.goff[g1] - i0;
+    const float4 o = A.cctr[C];
+    const float4 cg = A.cexp[C];
+    float4* tq = tq_all[wl];
+    float4* fsum = fs_all[wl];
+    int* qb = qb_all[wl];
+    for (int k = lane; k < nt; k += 32) {
+        const int64_t i = (int64_t)i0 + k;
+        tq[k] = shift(A.tcorig[i >> 5], o, A.tpos[i]);
+        fsum[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    const int w0 = A.csplit[g0], w1 = A.far_off[g0 + 1];
+    LocalAcc L;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) L.c[q] = make_float2(0.f, 0.f);
+    int nq = 0;
+    auto flush = [&]() {
+        for (int k = lane; k < nt; k += 32) {
+            const float4 tl = tq[k];
+            float4 fs = fsum[k];
+            for (int j = 0; j < nq; ++j) {
+                const int b = qb[j];
+                const float4 p = shift(A.ncell[b], o, A.nrep[b]), m = A.nmom[b];
+                const float dx = p.x - tl.x, dy = p.y - tl.y, dz = p.z - tl.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ir = r2 >= A.w2 ? rsqrtf(r2) : 0.f;
+                const float ir2 = ir * ir, ir3 = ir2 * ir;
+                const float dm = fmaf(dx, m.x, fmaf(dy, m.y, dz * m.z));
+                const float k5 = 3.f * (dm * ir2) * ir3;
+                fs.w = fmaf(dm, ir3, fs.w);
+                fs.x += fmaf(m.x, ir3, -k5 * dx);
+                fs.y += fmaf(m.y, ir3, -k5 * dy);
+                fs.z += fmaf(m.z, ir3, -k5 * dz);
+            }
+            fsum[k] = fs;
+        }
+        __syncwarp();
+        nq = 0;
+    };
+    auto queue = [&](bool fall, int b) {
+        const unsigned fm = __ballot_sync(kFull, fall);
+        if (!fm) return;
+        const int nf = __popc(fm);
+        if (nq + nf > 32) flush();
+        if (fall) qb[nq + __popc(fm & ((1u << lane) - 1u))] = b;
+        nq += nf;
+        __syncwarp();
+    };
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+    int ia = 0, ib = 0, na = 0, nb = 0;
+    if (w0 + lane < w1) { ia = A.far_id[w0 + lane]; a0 = A.lrec[2 * ia]; a1 = A.lrec[2 * ia + 1]; }
+    if (w0 + 32 + lane < w1) { ib = A.far_id[w0 + 32 + lane]; b0 = A.lrec[2 * ib]; b1 = A.lrec[2 * ib + 1]; }
+    if (w0 + 64 + lane < w1) na = A.far_id[w0 + 64 + lane];
+    if (w0 + 96 + lane < w1) nb = A.far_id[w0 + 96 + lane];
+    for (int base = w0; base < w1; base += 64) {
+        const int ea = base + lane, eb = ea + 32;
+        const bool va = ea < w1, vb = eb < w1;
+        const float2 ex = __fadd2_rn(make_float2(a0.x, b0.x), f2(-(o.x + cg.x)));
+        const float2 ey = __fadd2_rn(make_float2(a0.y, b0.y), f2(-(o.y + cg.y)));
+        const float2 ez = __fadd2_rn(make_float2(a0.z, b0.z), f2(-(o.z + cg.z)));
+        const float2 mx = make_float2(a0.w, b0.w), my = make_float2(a1.x, b1.x), mz = make_float2(a1.y, b1.y);
+        const int ca = ia, cb = ib;
+        if (ea + 64 < w1) { ia = na; a0 = A.lrec[2 * ia]; a1 = A.lrec[2 * ia + 1]; }
+        if (eb + 64 < w1) { ib = nb; b0 = A.lrec[2 * ib]; b1 = A.lrec[2 * ib + 1]; }
+        if (ea + 128 < w1) na = A.far_id[ea + 128];
+        if (eb + 128 < w1) nb = A.far_id[eb + 128];
+        float2 r2 = __fmul2_rn(ez, ez);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ex, ex, r2);
+        float2 ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 bound = __ffma2_rn(r2, ir, f2(-cg.w));     // |E| - rho_C
+        const bool oka = va && bound.x > 0.f && bound.x * bound.x >= A.w2;
+        const bool okb = vb && bound.y > 0.f && bound.y * bound.y >= A.w2;
+        ir = make_float2(oka ? ir.x : 0.f, okb ? ir.y : 0.f);
+        local_terms<kG>(ex, ey, ez, ir, mx, my, mz, L);
+        queue(va && !oka, ca);
+        queue(vb && !okb, cb);
+    }
+    if (nq) flush();
+    float k[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        k[q] = L.c[q].x + L.c[q].y;
+        if (q < 4 || kG) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) k[q] += __shfl_xor_sync(kFull, k[q], d);
+        }
+    }
+    for (int j = lane; j < nt; j += 32) {
+        const float4 tl = tq[j];
+        const float dx = tl.x - cg.x, dy = tl.y - cg.y, dz = tl.z - cg.z;
+        float4 f = fsum[j];
+        f.w += k[0] - fmaf(dx, k[1], fmaf(dy, k[2], dz * k[3]));
+        if (kG) {
+            f.x += k[1] + fmaf(k[4], dx, fmaf(k[7], dy, k[8] * dz));
+            f.y += k[2] + fmaf(k[7], dx, fmaf(k[5], dy, k[9] * dz));
+            f.z += k[3] + fmaf(k[8], dx, fmaf(k[9], dy, k[6] * dz));
+        }
+        const float4 c = corr[i0 + j];
+        corr[i0 + j] = make_float4(c.x + f.x, c.y + f.y, c.z + f.z, c.w + f.w);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1064,6 +1192,12 @@ struct AdjArgs {
     const int* tfar_ent;
     const int* tfar_lsplit;   //   per node the first expanded entry (tfar_ent: its group from there)
     float4* gadj;             //   per group (c_g, rho_g), (D, S), normalised coordinates
+    const int* tfar_csplit;   // local_cluster > 0: per node the first entry expanded about a cluster
+    float4* cadj;             //   per cluster (c_C, rho_C), (D, S)
+    int cluster_k;
+    int nclusters;
+    const float4* cctr;       //   cluster frame origins
+    const float4* cexp;       //   expansion centre in the cluster's frame and the cluster's radius
 };
 
 // Adjoint terms s_i gradPhi(x_i - x) = s_i (x - x_i) / r^3 at x = p from a
@@ -1198,11 +1332,41 @@ __global__ void k_local_groups(AdjArgs A) {
     }
 }
 
-// The pairs of one expanded entry (g, b) whose pairs may straddle the cut-off,
-// in the group's frame from the exact cell-relative data.
-__device__ __noinline__ float4 local_entry_pairs(const AdjArgs& A, int g, int b) {
-    const int i0 = A.goff[g], i1 = A.goff[g + 1];
-    const float4 o = A.gorig[g];
+// The same records per cluster of the second level (warp per cluster, its
+// up to 32 K targets in the cluster's frame).
+__global__ void k_local_clusters(AdjArgs A) {
+    const int C = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (C >= A.nclusters) return;
+    const int g0 = C * A.cluster_k, g1 = min(g0 + A.cluster_k, A.ngroups);
+    const float4 o = A.cctr[C];
+    const float4 cg = A.cexp[C];
+    float sS = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int i = A.goff[g0] + lane; i < A.goff[g1]; i += 32) {
+        const float4 p = shift(A.corig[i >> 5], o, A.pos[i]);
+        const float sv = A.sv[i];
+        sS += sv;
+        sx += sv * (p.x - cg.x);
+        sy += sv * (p.y - cg.y);
+        sz += sv * (p.z - cg.z);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        sS += __shfl_xor_sync(0xffffffffu, sS, d);
+        sx += __shfl_xor_sync(0xffffffffu, sx, d);
+        sy += __shfl_xor_sync(0xffffffffu, sy, d);
+        sz += __shfl_xor_sync(0xffffffffu, sz, d);
+    }
+    if (lane == 0) {
+        A.cadj[2 * C] = make_float4(o.x + cg.x, o.y + cg.y, o.z + cg.z, cg.w);
+        A.cadj[2 * C + 1] = make_float4(sx, sy, sz, sS);
+    }
+}
+
+// The pairs of one expanded entry whose pairs may straddle the cut-off: node
+// b against the targets i0 .. i1 - 1, in the frame with origin o, from the
+// exact cell-relative data.
+__device__ __noinline__ float4 local_entry_pairs(const AdjArgs& A, int i0, int i1, const float4& o, int b) {
     const float4 xb = shift(A.ncell[b], o, A.ncent[b]);
     float cx = 0.f, cy = 0.f, cz = 0.f;
     for (int i = i0; i < i1; ++i) {
@@ -1218,63 +1382,65 @@ __device__ __noinline__ float4 local_entry_pairs(const AdjArgs& A, int g, int b)
     return make_float4(cx, cy, cz, 0.f);
 }
 
-// The node gather with expanded entries: one warp per node.  The node's
-// entries summed pair by pair come first (their contrib, kPairGathers reads
-// in flight per lane), then its expanded entries (tfar_ent holds their group;
-// kLocalGathers group records in flight per lane, then the terms).
+// The node gather with expanded entries: one warp per node, lanes over the
+// node's whole transposed list (U reads in flight per lane, then the sums:
+// 4 for the longer lists of one expansion level, 2 with clusters, whose
+// shorter lists gain more from the extra resident warps of the smaller
+// register count).  The list holds the entries summed pair by pair (their contrib),
+// from tlsplit on those expanded about a group (tfar_ent: the group; its
+// record gadj) and from tcsplit on those expanded about a cluster (the
+// cluster; cadj): a lane's class follows from its position.
 constexpr int kNodeGathers = 16;
-constexpr int kPairGathers = 8;
-constexpr int kLocalGathers = 4;
+
+// The transposed term of one expanded entry from its group's or cluster's
+// record (c, rho), (D, S) at the node centroid xb: S E/r^3 + (3 E (E.D) - r^2 D)/r^5,
+// E = xb - c, or, when |E| - rho < w, the entry's pairs (targets i0 .. i1 - 1,
+// frame origin o).
+__device__ __forceinline__ void adj_local_term(const AdjArgs& A, const float4& xb, const float4& c0,
+                                               const float4& c1, int b, int i0, int i1, const float4& o,
+                                               float& ax, float& ay, float& az);
+
+template <int U>
 __global__ void k_adj_node_local(AdjArgs A, float4* vnode) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= A.nnodes) return;
     const int q0 = A.tfar_off[b], qs = A.tfar_lsplit[b], q1 = A.tfar_off[b + 1];
+    const int qc = A.tfar_csplit ? A.tfar_csplit[b] : q1;      // [qs, qc) groups, [qc, q1) clusters
     float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int q = q0 + lane; q < qs; q += 32 * kPairGathers) {
-        int e[kPairGathers];
+    const float4 xb = A.nabs[b];
+    for (int q = q0 + lane; q < q1; q += 32 * U) {
+        int id[U];
 #pragma unroll
-        for (int u = 0; u < kPairGathers; ++u) e[u] = q + 32 * u < qs ? A.tfar_ent[q + 32 * u] : -1;
-        float4 c[kPairGathers];
+        for (int u = 0; u < U; ++u) id[u] = q + 32 * u < q1 ? A.tfar_ent[q + 32 * u] : -1;
+        float4 c0[U], c1[U];
 #pragma unroll
-        for (int u = 0; u < kPairGathers; ++u) c[u] = e[u] >= 0 ? A.contrib[e[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < kPairGathers; ++u) { ax += c[u].x; ay += c[u].y; az += c[u].z; }
-    }
-    if (qs < q1) {
-        const float4 xb = A.nabs[b];
-        for (int q = qs + lane; q < q1; q += 32 * kLocalGathers) {
-            int g[kLocalGathers];
-#pragma unroll
-            for (int u = 0; u < kLocalGathers; ++u) g[u] = q + 32 * u < q1 ? A.tfar_ent[q + 32 * u] : -1;
-            float4 c0[kLocalGathers], c1[kLocalGathers];
-#pragma unroll
-            for (int u = 0; u < kLocalGathers; ++u) {
-                const int gg = g[u] >= 0 ? g[u] : 0;
-                c0[u] = A.gadj[2 * gg];
-                c1[u] = A.gadj[2 * gg + 1];
+        for (int u = 0; u < U; ++u) {
+            const int qq = q + 32 * u;
+            c0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            c1[u] = c0[u];
+            if (id[u] < 0) continue;
+            if (qq < qs) {
+                c0[u] = A.contrib[id[u]];
+            } else {
+                const float4* rec = qq < qc ? A.gadj : A.cadj;
+                c0[u] = rec[2 * id[u]];
+                c1[u] = rec[2 * id[u] + 1];
             }
+        }
 #pragma unroll
-            for (int u = 0; u < kLocalGathers; ++u) {
-                if (g[u] < 0) continue;
-                const float ex = xb.x - c0[u].x, ey = xb.y - c0[u].y, ez = xb.z - c0[u].z;
-                const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                const float ir = rsqrtf(r2);
-                const float bound = fmaf(r2, ir, -c0[u].w);
-                if (bound > 0.f && bound * bound >= A.w2) {
-                    const float4 D = c1[u];
-                    const float ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
-                    const float ed3 = 3.f * fmaf(ex, D.x, fmaf(ey, D.y, ez * D.z));
-                    const float sr = D.w * ir3;
-                    ax += fmaf(sr, ex, fmaf(ed3, ex, -r2 * D.x) * ir5);
-                    ay += fmaf(sr, ey, fmaf(ed3, ey, -r2 * D.y) * ir5);
-                    az += fmaf(sr, ez, fmaf(ed3, ez, -r2 * D.z) * ir5);
-                } else {
-                    const float4 cc = local_entry_pairs(A, g[u], b);
-                    ax += cc.x;
-                    ay += cc.y;
-                    az += cc.z;
-                }
+        for (int u = 0; u < U; ++u) {
+            const int qq = q + 32 * u;
+            if (id[u] < 0) continue;
+            if (qq < qs) {
+                ax += c0[u].x;
+                ay += c0[u].y;
+                az += c0[u].z;
+            } else if (qq < qc) {
+                adj_local_term(A, xb, c0[u], c1[u], b, A.goff[id[u]], A.goff[id[u] + 1], A.gorig[id[u]], ax, ay, az);
+            } else {
+                const int g0 = id[u] * A.cluster_k, g1 = min(g0 + A.cluster_k, A.ngroups);
+                adj_local_term(A, xb, c0[u], c1[u], b, A.goff[g0], A.goff[g1], A.cctr[id[u]], ax, ay, az);
             }
         }
     }
@@ -1285,6 +1451,28 @@ __global__ void k_adj_node_local(AdjArgs A, float4* vnode) {
         az += __shfl_xor_sync(0xffffffffu, az, o);
     }
     if (lane == 0) vnode[b] = make_float4(ax, ay, az, 0.f);
+}
+
+__device__ __forceinline__ void adj_local_term(const AdjArgs& A, const float4& xb, const float4& c0,
+                                               const float4& c1, int b, int i0, int i1, const float4& o,
+                                               float& ax, float& ay, float& az) {
+    const float ex = xb.x - c0.x, ey = xb.y - c0.y, ez = xb.z - c0.z;
+    const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    const float ir = rsqrtf(r2);
+    const float bound = fmaf(r2, ir, -c0.w);
+    if (bound > 0.f && bound * bound >= A.w2) {
+        const float ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
+        const float ed3 = 3.f * fmaf(ex, c1.x, fmaf(ey, c1.y, ez * c1.z));
+        const float sr = c1.w * ir3;
+        ax += fmaf(sr, ex, fmaf(ed3, ex, -r2 * c1.x) * ir5);
+        ay += fmaf(sr, ey, fmaf(ed3, ey, -r2 * c1.y) * ir5);
+        az += fmaf(sr, ez, fmaf(ed3, ez, -r2 * c1.z) * ir5);
+    } else {
+        const float4 cc = local_entry_pairs(A, i0, i1, o, b);
+        ax += cc.x;
+        ay += cc.y;
+        az += cc.z;
+    }
 }
 
 // One warp per node; lanes take the node's entries (consecutive slots of the
@@ -2052,6 +2240,11 @@ GatherArgs base_args(const Tree& t, const TargetSet& ts, float w, float4* part_a
     a.far_off = ts.far_off;
     a.lsplit = ts.far_lsplit;
     a.gctr = ts.gctr;
+    a.csplit = ts.far_csplit;
+    a.cluster_k = ts.cluster_k;
+    a.nclusters = ts.nclusters;
+    a.cctr = ts.cctr;
+    a.cexp = ts.cexp;
     return a;
 }
 
@@ -2113,6 +2306,12 @@ AdjArgs adj_args(const Tree& t, float w) {
     a.tfar_ent = t.tfar_ent;
     a.tfar_lsplit = t.tfar_lsplit;
     a.gadj = t.gadj;
+    a.tfar_csplit = t.tfar_csplit;
+    a.cadj = t.cadj;
+    a.cluster_k = S.cluster_k;
+    a.nclusters = S.nclusters;
+    a.cctr = S.cctr;
+    a.cexp = S.cexp;
     return a;
 }
 
@@ -2264,6 +2463,10 @@ static void local_far(Tree& t, const TargetSet& ts, GatherArgs& a, float4* corr,
     a.lrec = t.local_rec;
     k_local_ag<OP><<<ceil_div(ts.ngroups, kLocalWarps), 32 * kLocalWarps, 0, s>>>(a, corr);
     WNNC_LAUNCH_CHECK();
+    if (ts.far_csplit) {
+        k_local_cl<OP><<<ceil_div(ts.nclusters, kLocalWarps), 32 * kLocalWarps, 0, s>>>(a, corr);
+        WNNC_LAUNCH_CHECK();
+    }
     a.dip_corr = corr;
 }
 
@@ -2332,10 +2535,16 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
             ProfScope ps(&t.prof, WNNC_PROF_LOCAL, s);
             k_local_groups<<<ceil_div((int64_t)t.self.ngroups * 32, kTB), kTB, 0, s>>>(a);
             WNNC_LAUNCH_CHECK();
+            if (a.tfar_csplit) {
+                k_local_clusters<<<ceil_div((int64_t)t.self.nclusters * 32, kTB), kTB, 0, s>>>(a);
+                WNNC_LAUNCH_CHECK();
+            }
         }
         ProfScope ps(&t.prof, WNNC_PROF_ADJ_NODE, s);
-        if (a.lsplit) {
-            k_adj_node_local<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);
+        if (a.lsplit && a.tfar_csplit) {
+            k_adj_node_local<2><<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);
+        } else if (a.lsplit) {
+            k_adj_node_local<4><<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);
         } else if (dip) {
             // the node sums of V and H, pushed down in the near kernel's epilogue
             k_adj_node3<<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(

@@ -758,13 +758,14 @@ __global__ void k_gather_i32(const int* src, const int* idx, int n, int* dst) {
 // Interaction counts: far pairs = sum_g |g| * (far entries summed pair by
 // pair), near = sum_g |g| * sum |range|, the expanded entries and the pairs
 // they stand for.
-__global__ void k_pair_counts(int ng, const int* goff, const int* far_off, const int* lsplit, const int* near_off,
-                              const int2* rng, unsigned long long* out) {
+__global__ void k_pair_counts(int ng, const int* goff, const int* far_off, const int* lsplit, const int* csplit,
+                              int K, const int* near_off, const int2* rng, unsigned long long* out) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
     int64_t sz = goff[g + 1] - goff[g];
     const int fl = lsplit ? lsplit[g] : far_off[g + 1];
-    int64_t nf = fl - far_off[g], nl = far_off[g + 1] - fl;
+    const int fc = csplit ? csplit[g] : far_off[g + 1];
+    int64_t nf = fl - far_off[g], nl = fc - fl;
     int64_t nn = 0;
     for (int q = near_off[g]; q < near_off[g + 1]; ++q) nn += rng[q].y - rng[q].x;
     atomicAdd(&out[0], (unsigned long long)(sz * nf));
@@ -773,6 +774,123 @@ __global__ void k_pair_counts(int ng, const int* goff, const int* far_off, const
         atomicAdd(&out[2], (unsigned long long)nl);
         atomicAdd(&out[3], (unsigned long long)(sz * nl));
     }
+    if (csplit && g % K == 0 && far_off[g + 1] > fc) {
+        // a cluster's (cluster, node) expansions, counted at its first member
+        const int64_t nce = far_off[g + 1] - fc;
+        const int64_t csz = goff[min(g + K, ng)] - goff[g];
+        atomicAdd(&out[4], (unsigned long long)nce);
+        atomicAdd(&out[5], (unsigned long long)(csz * nce));
+    }
+}
+
+// Clusters of K consecutive target groups (local_cluster = K): warp per
+// cluster.  The FP64 box (union of the members' boxes), its largest extent
+// times clocal (cle), a dyadic frame origin and, in that frame, the box
+// centre and the largest distance of the cluster's targets from it (FP64,
+// rounded up).
+__global__ void k_cluster_frames(const double* ys, const int* goff, const double* glo, const double* ghi, int ng,
+                                 int K, double clocal, double* clo, double* chi, double* cle, float4* cctr,
+                                 float4* cexp) {
+    const int C = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nc = (ng + K - 1) / K;
+    if (C >= nc) return;
+    const int g0 = C * K, g1 = min(g0 + K, ng);
+    double lo[3], hi[3], c[3], o[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double l = INFINITY, h = -INFINITY;
+        if (g0 + lane < g1) { l = glo[3 * (g0 + lane) + k]; h = ghi[3 * (g0 + lane) + k]; }
+        for (int d = 16; d > 0; d >>= 1) {
+            l = fmin(l, __shfl_xor_sync(0xffffffffu, l, d));
+            h = fmax(h, __shfl_xor_sync(0xffffffffu, h, d));
+        }
+        lo[k] = l;
+        hi[k] = h;
+        c[k] = 0.5 * (l + h);
+        o[k] = dyadic12(c[k]);
+    }
+    double r = 0.0;
+    for (int i = goff[g0] + lane; i < goff[g1]; i += 32) {
+        const double dx = ys[3 * (int64_t)i] - c[0], dy = ys[3 * (int64_t)i + 1] - c[1], dz = ys[3 * (int64_t)i + 2] - c[2];
+        r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+    }
+    for (int d = 16; d > 0; d >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, d));
+    if (lane == 0) {
+        double e = __dsub_rn(hi[0], lo[0]);
+        if (__dsub_rn(hi[1], lo[1]) > e) e = __dsub_rn(hi[1], lo[1]);
+        if (__dsub_rn(hi[2], lo[2]) > e) e = __dsub_rn(hi[2], lo[2]);
+        for (int k = 0; k < 3; ++k) { clo[3 * C + k] = lo[k]; chi[3 * C + k] = hi[k]; }
+        cle[C] = __dmul_rn(clocal, e);
+        cctr[C] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
+        cexp[C] = make_float4((float)(c[0] - o[0]), (float)(c[1] - o[1]), (float)(c[2] - o[2]), __double2float_ru(r));
+    }
+}
+
+// Warp per cluster of at least two groups: the entries of the first member's
+// expanded part whose node also lies in every other member's expanded part
+// (each ascending: binary search) and is local for the cluster's box (the
+// exact FP64 test of the group's: squared box gap > cle^2) are flagged in
+// every member.
+__global__ void k_cluster_classes(const int* far_off, const int* lsplit, const int* far_id, int ng, int K,
+                                  const double* nlo, const double* nhi, const double* clo, const double* chi,
+                                  const double* cle, unsigned char* moved) {
+    const int C = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nc = (ng + K - 1) / K;
+    if (C >= nc) return;
+    const int g0 = C * K, g1 = min(g0 + K, ng);
+    if (g1 - g0 < 2) return;
+    double lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) { lo[k] = clo[3 * C + k]; hi[k] = chi[3 * C + k]; }
+    const double c2 = __dmul_rn(cle[C], cle[C]);
+    for (int e = lsplit[g0] + lane; e < far_off[g0 + 1]; e += 32) {
+        const int b = far_id[e];
+        int qm[kMaxCluster];
+        bool all = true;
+        for (int m = 1; m < g1 - g0 && all; ++m) {
+            int a = lsplit[g0 + m], z = far_off[g0 + m + 1];    // search [a, z)
+            while (a < z) {
+                const int mid = (a + z) >> 1;
+                if (far_id[mid] < b) a = mid + 1; else z = mid;
+            }
+            if (a < far_off[g0 + m + 1] && far_id[a] == b) qm[m] = a;
+            else all = false;
+        }
+        if (!all || !(box_gap2_d(nlo, nhi, b, lo, hi) > c2)) continue;
+        moved[e] = 1;
+        for (int m = 1; m < g1 - g0; ++m) moved[qm[m]] = 1;
+    }
+}
+
+// Warp per group: its expanded part [lsplit, end) reordered stably into the
+// entries not flagged, then the flagged ones (from csplit on), into out; the
+// rest of the list copied.
+__global__ void k_cluster_partition(const int* far_off, const int* lsplit, const int* far_id,
+                                    const unsigned char* moved, int ng, int* out, int* csplit) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    const unsigned lt = (1u << lane) - 1u;
+    const int f0 = far_off[g], l0 = lsplit[g], f1 = far_off[g + 1];
+    for (int e = f0 + lane; e < l0; e += 32) out[e] = far_id[e];
+    int nstay = 0;
+    for (int e = l0; e < f1; e += 32) {
+        const bool v = e + lane < f1 && !moved[e + lane];
+        nstay += __popc(__ballot_sync(0xffffffffu, v));
+    }
+    int ps = l0, pm = l0 + nstay;
+    for (int base = l0; base < f1; base += 32) {
+        const int e = base + lane;
+        const bool v = e < f1;
+        const bool mv = v && moved[e];
+        const unsigned bs = __ballot_sync(0xffffffffu, v && !mv), bm = __ballot_sync(0xffffffffu, mv);
+        if (v && !mv) out[ps + __popc(bs & lt)] = far_id[e];
+        if (mv) out[pm + __popc(bm & lt)] = far_id[e];
+        ps += __popc(bs);
+        pm += __popc(bm);
+    }
+    if (lane == 0) csplit[g] = l0 + nstay;
 }
 
 // Far keys (group << 32 | local flag << 31 | node), sorted by group and flag:
@@ -801,28 +919,46 @@ __global__ void k_entry_groups(const int* far_off, int ng, int* egrp) {
     for (int e = far_off[g] + lane; e < far_off[g + 1]; e += 32) egrp[e] = g;
 }
 
-// Transposed far lists: key (node << 32 | expanded << 31 | entry index);
-// expanded = the entry lies at or after lsplit of its group (egrp and lsplit
-// null: no expanded entries).
-__global__ void k_tfar_keys(const int* far_id, int64_t nent, const int* egrp, const int* lsplit,
-                            uint64_t* keys) {
+// Transposed far lists: key (node << 32 | class << 30 | entry index), class 0
+// for an entry summed pair by pair, 1 for one expanded about its group (at or
+// after lsplit of its group), 2 for one expanded about its cluster (at or
+// after csplit; only the first member's copy: the other members' copies get
+// node = nnodes and sort past every node).  egrp null: all class 0.
+__global__ void k_tfar_keys(const int* far_id, int64_t nent, const int* egrp, const int* lsplit, const int* csplit,
+                            int K, int nnodes, uint64_t* keys) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nent) return;
-    const bool x = egrp && e >= lsplit[egrp[e]];
-    keys[e] = ((uint64_t)(uint32_t)far_id[e] << 32) | (x ? 0x80000000u : 0u) | (uint32_t)e;
+    uint32_t cls = 0, node = (uint32_t)far_id[e];
+    if (egrp) {
+        const int g = egrp[e];
+        if (csplit && e >= csplit[g]) {
+            cls = 2;
+            if (g % K != 0) node = (uint32_t)nnodes;
+        } else if (e >= lsplit[g]) {
+            cls = 1;
+        }
+    }
+    keys[e] = ((uint64_t)node << 32) | ((uint64_t)cls << 30) | (uint32_t)e;
 }
 
 // Sorted transposed keys -> per node its entries summed pair by pair (their
-// entry index), then from tlsplit[node] on its expanded entries (their group).
-__global__ void k_tfar_ids(const uint64_t* keys, int64_t n, const int* egrp, int* tfar_ent, int* tlsplit) {
+// entry index), then from tlsplit[node] on those expanded about a group (their
+// group), then from tcsplit[node] on those expanded about a cluster (their
+// cluster).  Both splits start at the end of the node's list.
+__global__ void k_tfar_ids(const uint64_t* keys, int64_t n, const int* egrp, int K, int nnodes, int* tfar_ent,
+                           int* tlsplit, int* tcsplit) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const uint64_t k = keys[q];
-    const int e = (int)(uint32_t)(k & 0x7fffffffu);
-    const bool x = (k & 0x80000000u) != 0;
-    tfar_ent[q] = x ? egrp[e] : e;
-    if (x && (q == 0 || (keys[q - 1] >> 32) != (k >> 32) || !(keys[q - 1] & 0x80000000u)))
-        tlsplit[(int)(k >> 32)] = (int)q;
+    const int node = (int)(k >> 32);
+    if (node >= nnodes) return;
+    const int e = (int)(uint32_t)(k & 0x3fffffffu);
+    const int cls = (int)((k >> 30) & 3u);
+    tfar_ent[q] = cls == 0 ? e : (cls == 1 ? egrp[e] : egrp[e] / K);
+    const bool first = q == 0 || (int)(keys[q - 1] >> 32) != node;
+    const int pcls = first ? -1 : (int)((keys[q - 1] >> 30) & 3u);
+    if (cls >= 1 && pcls < 1) tlsplit[node] = (int)q;
+    if (cls == 2 && pcls < 2 && tcsplit) tcsplit[node] = (int)q;
 }
 
 // Transposed near entries: for each near range of target group g, the source
@@ -1209,6 +1345,21 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     k_group_boxes<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(ys, ts.goff, ng, ts.glo, ts.ghi, ts.gorig,
                                                                    ts.gbl, ts.gbh, ts.gctr);
     WNNC_LAUNCH_CHECK();
+    // clusters of the second expansion level: boxes, frames, radii (targets still in FP64)
+    const int K = (local && t.params.local_cluster >= 2) ? t.params.local_cluster : 0;
+    double *cl_lo = nullptr, *cl_hi = nullptr, *cl_e = nullptr;
+    if (K) {
+        ts.cluster_k = K;
+        ts.nclusters = (ng + K - 1) / K;
+        cl_lo = dalloc<double>(3 * (size_t)ts.nclusters);
+        cl_hi = dalloc<double>(3 * (size_t)ts.nclusters);
+        cl_e = dalloc<double>(ts.nclusters);
+        ts.cctr = dalloc<float4>(ts.nclusters);
+        ts.cexp = dalloc<float4>(ts.nclusters);
+        k_cluster_frames<<<ceil_div((int64_t)ts.nclusters * 32, kTB), kTB, 0, s>>>(
+            ys, ts.goff, ts.glo, ts.ghi, ng, K, clocal, cl_lo, cl_hi, cl_e, ts.cctr, ts.cexp);
+        WNNC_LAUNCH_CHECK();
+    }
     wait_before_free(s);
     if (!reuse) {
         pool_free(ys);
@@ -1311,6 +1462,24 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             k_far_ids<<<ceil_div(nfar, kTB), kTB, 0, s>>>(fkeys, nfar, ts.far_id, ts.far_lsplit);
             WNNC_LAUNCH_CHECK();
         }
+        if (K) {
+            // entries expanded about their cluster: flagged, then each group's expanded
+            // part reordered into [group | cluster] (csplit)
+            ts.far_csplit = dalloc<int>(ng);
+            unsigned char* moved = dalloc<unsigned char>(std::max<int64_t>(nfar, 1));
+            WNNC_CUDA(cudaMemsetAsync(moved, 0, std::max<int64_t>(nfar, 1), s));
+            k_cluster_classes<<<ceil_div((int64_t)ts.nclusters * 32, kTB), kTB, 0, s>>>(
+                ts.far_off, ts.far_lsplit, ts.far_id, ng, K, t.node_lo, t.node_hi, cl_lo, cl_hi, cl_e, moved);
+            WNNC_LAUNCH_CHECK();
+            int* reordered = dalloc<int>(std::max<int64_t>(nfar, 1));
+            k_cluster_partition<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(
+                ts.far_off, ts.far_lsplit, ts.far_id, moved, ng, reordered, ts.far_csplit);
+            WNNC_LAUNCH_CHECK();
+            wait_before_free(s);
+            pool_free(ts.far_id);
+            ts.far_id = reordered;
+            pool_free(moved);
+        }
         // merge consecutive near leaves into ranges
         int* head = dalloc<int>(nleafent + 2);
         int* hscan = dalloc<int>(nleafent + 2);
@@ -1357,12 +1526,16 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         wait_before_free(s);
         pool_free(cnt); pool_free(off); pool_free(rng0); pool_free(near_off0);
     }
-    unsigned long long* pc = dalloc<unsigned long long>(4);
-    WNNC_CUDA(cudaMemsetAsync(pc, 0, 4 * sizeof(unsigned long long), s));
-    k_pair_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ng, ts.goff, ts.far_off, ts.far_lsplit, ts.near_off,
-                                                    ts.near_rng, pc);
+    if (K) {
+        wait_before_free(s);
+        pool_free(cl_lo); pool_free(cl_hi); pool_free(cl_e);
+    }
+    unsigned long long* pc = dalloc<unsigned long long>(6);
+    WNNC_CUDA(cudaMemsetAsync(pc, 0, 6 * sizeof(unsigned long long), s));
+    k_pair_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ng, ts.goff, ts.far_off, ts.far_lsplit, ts.far_csplit, K,
+                                                    ts.near_off, ts.near_rng, pc);
     WNNC_LAUNCH_CHECK();
-    unsigned long long hc[4];
+    unsigned long long hc[6];
     WNNC_CUDA(cudaMemcpyAsync(hc, pc, sizeof(hc), cudaMemcpyDeviceToHost, s));
     WNNC_CUDA(cudaStreamSynchronize(s));
     pool_free(pc);
@@ -1370,13 +1543,15 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     ts.near_pairs = (int64_t)hc[1];
     ts.local_entries = (int64_t)hc[2];
     ts.local_pairs = (int64_t)hc[3];
+    ts.cluster_entries = (int64_t)hc[4];
+    ts.cluster_pairs = (int64_t)hc[5];
     build_work(ts.work, 0, ng, ts.near_off, ts.near_rng, ts.far_off, ts.far_lsplit, true, s);
 }
 
 void free_target_set(TargetSet& ts) {
     dfree(ts.perm); dfree(ts.pos); dfree(ts.corig); dfree(ts.gorig); dfree(ts.goff); dfree(ts.glo);
     dfree(ts.ghi); dfree(ts.gbl); dfree(ts.gbh); dfree(ts.far_off); dfree(ts.far_id); dfree(ts.near_off); dfree(ts.near_rng);
-    dfree(ts.far_lsplit); dfree(ts.gctr);
+    dfree(ts.far_lsplit); dfree(ts.gctr); dfree(ts.far_csplit); dfree(ts.cctr); dfree(ts.cexp);
     free_work(ts.work);
 }
 
@@ -1554,6 +1729,7 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     {
         int64_t ne = S.far_entries;
         const bool local = S.far_lsplit != nullptr;
+        if (local && ne >= (int64_t(1) << 30)) fail(WNNC_ECAPACITY, "too many far entries for local expansions");
         uint64_t* k = dalloc<uint64_t>(ne);
         // with local expansions: the group of every entry, and bit 31 of the
         // key set for an expanded entry (sorted after the node's others)
@@ -1563,20 +1739,27 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             WNNC_LAUNCH_CHECK();
         }
         if (ne) {
-            k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, egrp, S.far_lsplit, k);
+            k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, egrp, S.far_lsplit, S.far_csplit,
+                                                          S.cluster_k, t.nnodes, k);
             WNNC_LAUNCH_CHECK();
         }
-        // entry indices already ascending
-        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes), s, local ? 31 : 32);
+        // entry indices already ascending; the class bits sort too
+        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes + 1), s, local ? 30 : 32);
         t.tfar_ent = dalloc<int>(ne);
         segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
         if (local) {
             t.tfar_lsplit = dalloc<int>(t.nnodes);
             k_lsplit_init<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.tfar_off, t.nnodes, t.tfar_lsplit);
             WNNC_LAUNCH_CHECK();
+            if (S.far_csplit) {
+                t.tfar_csplit = dalloc<int>(t.nnodes);
+                k_lsplit_init<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.tfar_off, t.nnodes, t.tfar_csplit);
+                WNNC_LAUNCH_CHECK();
+            }
         }
         if (ne) {
-            k_tfar_ids<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, egrp, t.tfar_ent, t.tfar_lsplit);
+            k_tfar_ids<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, egrp, S.cluster_k, t.nnodes, t.tfar_ent,
+                                                         t.tfar_lsplit, t.tfar_csplit);
             WNNC_LAUNCH_CHECK();
         }
         wait_before_free(s);
@@ -1655,7 +1838,8 @@ void free_tree(Tree& t) {
     dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.mom_top); dfree(t.mom_top_rng); dfree(t.mom_front); dfree(t.node_rep); dfree(t.contrib);
     dfree(t.near_contrib); dfree(t.vnode); dfree(t.red_ticket);
     dfree(t.mom_dip); dfree(t.mom_dip_r); dfree(t.dip_corr); dfree(t.contrib_h0); dfree(t.contrib_h1);
-    dfree(t.node_abs); dfree(t.local_rec); dfree(t.tfar_lsplit); dfree(t.gadj);
+    dfree(t.node_abs); dfree(t.local_rec); dfree(t.tfar_lsplit); dfree(t.gadj); dfree(t.tfar_csplit);
+    dfree(t.cadj);
     dfree(t.hnode0); dfree(t.hnode1);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
 }

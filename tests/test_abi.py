@@ -50,7 +50,7 @@ def test_defaults_and_argument_errors_without_gpu():
 
 
 def test_mode_parameters_are_checked_before_any_device_work():
-    """criterion, far_order and local_theta: defaults 0; values out of range
+    """criterion, far_order, local_theta and local_cluster: defaults 0; values out of range
     or in combinations the modes do not support are WNNC_EINVAL, reported
     before the library touches the device (the point pointer below is never
     read)."""
@@ -58,7 +58,7 @@ def test_mode_parameters_are_checked_before_any_device_work():
     W.build_if_needed()
     L = W.lib()
     p = W.default_tree_params()
-    assert (p.criterion, p.far_order, p.local_theta) == (0, 0, 0.0)
+    assert (p.criterion, p.far_order, p.local_theta, p.local_cluster) == (0, 0, 0.0, 0)
     h = ctypes.c_void_p()
     fake = ctypes.c_void_p(256)
     for kw, msg in (({"criterion": 2}, b"criterion"), ({"criterion": 1, "rep_mode": 1}, b"rep_mode 0"),
@@ -68,7 +68,11 @@ def test_mode_parameters_are_checked_before_any_device_work():
                     ({"local_theta": float("nan")}, b"local_theta"),
                     ({"local_theta": 0.5, "rep_mode": 0}, b"local_theta > 0"),
                     ({"local_theta": 0.5, "far_order": 1}, b"local_theta > 0"),
-                    ({"local_theta": 0.5, "rep_mode": 0, "criterion": 1}, b"local_theta > 0")):
+                    ({"local_theta": 0.5, "rep_mode": 0, "criterion": 1}, b"local_theta > 0"),
+                    ({"local_theta": 0.5, "local_cluster": 1}, b"local_cluster"),
+                    ({"local_theta": 0.5, "local_cluster": 9}, b"local_cluster"),
+                    ({"local_theta": 0.5, "local_cluster": -4}, b"local_cluster"),
+                    ({"local_cluster": 4}, b"local_cluster needs")):
         q = W.default_tree_params()
         for k, v in kw.items():
             setattr(q, k, v)

@@ -187,19 +187,105 @@ def test_local_iteration_matches_oracle():
 
 
 def test_local_solve_at_500k_agrees_with_the_pairwise_far_field():
-    """The benchmark's 500k solve (tree build + 40 iterations) with and
-    without the expansions: the oriented fields agree point by point."""
+    """The benchmark's 500k solve (tree build + 40 iterations) with the
+    expansions (one level, and two with clusters of 4 groups) and without:
+    the oriented fields agree point by point."""
     W = _wnnc()
     c = synth.config_cloud("union500k")
     pts = torch.from_numpy(c.points).cuda()
     fields = []
-    for lt in (0.0, 0.5):
-        t = W.Tree(pts, theta=0.5, local_theta=lt)
+    for lt, k in ((0.0, 0), (0.5, 0), (0.5, 4)):
+        t = W.Tree(pts, theta=0.5, local_theta=lt, local_cluster=k)
         fields.append(t.iterate(n_iter=40).cpu().numpy().astype(np.float64))
         t.close()
-    cos, dlen = _compare_fields(fields[1], fields[0], min_sign=0.9999, min_cos=0.99999)
     valid = np.all(np.isfinite(c.normals), axis=1)
-    p0, p1 = oracle.p_co(c.normals[valid], fields[0][valid]), oracle.p_co(c.normals[valid], fields[1][valid])
-    print(f"[local-500k] sign agreement {np.mean(cos > 0):.6f}, median cos {np.median(cos):.7f}, "
-          f"median |len| diff {dlen:.2e}, P_co pairwise {p0:.5f} expanded {p1:.5f}")
-    assert abs(p1 - p0) < 1e-3
+    p0 = oracle.p_co(c.normals[valid], fields[0][valid])
+    for name, f in (("one level", fields[1]), ("clusters of 4", fields[2])):
+        cos, dlen = _compare_fields(f, fields[0], min_sign=0.9999, min_cos=0.99999)
+        p1 = oracle.p_co(c.normals[valid], f[valid])
+        print(f"[local-500k] {name}: sign agreement {np.mean(cos > 0):.6f}, median cos {np.median(cos):.7f}, "
+              f"median |len| diff {dlen:.2e}, P_co pairwise {p0:.5f} expanded {p1:.5f}")
+        assert abs(p1 - p0) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# The second level: clusters of K consecutive groups (local_cluster = K).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("theta,k", [(0.5, 4), (0.5, 2), (0.8, 8)])
+def test_cluster_partition_matches_oracle(theta, k):
+    """Every group's far list in three parts, pair by pair / expanded about
+    the group / about its cluster, equal as sets (each part ascending on the
+    GPU) to the oracle's classes; the counts of both levels follow."""
+    W = _wnnc()
+    c = synth.config_cloud("union50k", n=20000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=theta, local_theta=0.5, local_cluster=k)
+    ex = t.export()
+    xn, _, _ = oracle.normalize(c.points)
+    ot = oracle.Tree(xn, f32(theta), local_theta=0.5, local_cluster=k)
+    fo_o, fi_o, _, _ = ot.lists()
+    cls = ot.local_classes()
+    fo, fid, ls, cs = ex["far_off"], ex["far_id"], ex["far_lsplit"], ex["far_csplit"]
+    gsize = np.diff(ex["group_off"])
+    n_cl = n_cl_pairs = 0
+    for g in range(len(ls)):
+        ids, cl = fi_o[fo_o[g]:fo_o[g + 1]], cls[fo_o[g]:fo_o[g + 1]]
+        for part, (a, b) in enumerate(((fo[g], ls[g]), (ls[g], cs[g]), (cs[g], fo[g + 1]))):
+            assert np.array_equal(fid[a:b], np.sort(ids[cl == part])), (g, part)
+        if g % k == 0:
+            n_cl += fo[g + 1] - cs[g]
+            n_cl_pairs += (fo[g + 1] - cs[g]) * int(gsize[g:g + k].sum())
+    assert (cls == 2).sum() > 0
+    assert t.cluster_stats() == (n_cl, n_cl_pairs)
+    assert t.local_stats()[0] == int((cls == 1).sum())
+
+
+@pytest.mark.parametrize("k", [4, 2])
+def test_cluster_operators_match_oracle(union5k, k):
+    """A, grad F and A^T with both levels, element by element, at three
+    widths, the last (w = 0.3) reaching about 2,000 expanded entries of either
+    level: their pairs are summed instead."""
+    W = _wnnc()
+    c, mu, s = union5k
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, local_theta=0.5, local_cluster=k)
+    assert t.cluster_stats()[0] > 0
+    for w in (0.002, 0.016, 0.3):
+        kw = dict(theta=0.5, amb_tol=AMB, local_theta=0.5, local_cluster=k)
+        F = t.eval_w(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Fo, amb = oracle.eval_op(OP_A, c.points, mu, w, **kw)
+        check_close(F, Fo, amb, what=f"A cluster {k} w={w}")
+        G = t.eval_grad(torch.from_numpy(mu).cuda(), w).cpu().numpy()
+        Go, amb = oracle.eval_op(OP_G, c.points, mu, w, **kw)
+        check_close(G, Go, amb, what=f"grad cluster {k} w={w}")
+        T = t.eval_adjoint(torch.from_numpy(s).cuda(), w).cpu().numpy()
+        To, amb = oracle.eval_op(OP_AT, c.points, s, w, **kw)
+        check_close(T, To, amb, what=f"AT cluster {k} w={w}")
+        lhs, rhs = (F.astype(np.float64) * s).sum(), (mu.astype(np.float64) * T).sum()
+        assert abs(lhs - rhs) <= 1e-5 * np.abs(F.astype(np.float64) * s).sum()
+
+
+def test_cluster_queries_match_oracle(union5k):
+    W = _wnnc()
+    c, mu, _ = union5k
+    rng = np.random.default_rng(9)
+    lo, hi = c.points.min(0), c.points.max(0)
+    q = (lo + (hi - lo) * (1.3 * rng.random((4000, 3)) - 0.15)).astype(np.float32)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, local_theta=0.5, local_cluster=4)
+    for grad in (False, True):
+        got = t.eval_at(torch.from_numpy(mu).cuda(), torch.from_numpy(q).cuda(), 0.0, grad=grad).cpu().numpy()
+        ref, b = oracle.eval_at(OP_G if grad else OP_A, c.points, mu, q, 0.0, theta=0.5, with_bounds=True,
+                                local_theta=0.5, local_cluster=4)
+        check_close(got, ref, b, what=f"queries cluster grad={grad}")
+
+
+def test_cluster_iteration_matches_oracle():
+    W = _wnnc()
+    c = synth.config_cloud("union50k", n=20000)
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, local_theta=0.5, local_cluster=4)
+    mg = t.iterate(n_iter=40).cpu().numpy().astype(np.float64)
+    mo, _ = oracle.iterate(c.points, n_iter=40, theta=0.5, local_theta=0.5, local_cluster=4)
+    cos, dlen = _compare_fields(mg, mo, min_sign=0.995, min_cos=0.995)
+    pg, po = oracle.p_co(c.normals, mg), oracle.p_co(c.normals, mo)
+    print(f"[cluster-iterate-20k] sign agreement {np.mean(cos > 0):.5f}, median cos {np.median(cos):.6f}, "
+          f"median |len| diff {dlen:.2e}, P_co gpu {pg:.5f} oracle {po:.5f}")
+    assert abs(pg - po) < 0.005

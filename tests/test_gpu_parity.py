@@ -245,9 +245,9 @@ def union500k_sample():
     return c.points, mu, s, sub, {}
 
 
-@pytest.mark.parametrize("rep_mode,local_theta", [(1, 0.0), (0, 0.0), (1, 0.5)])
+@pytest.mark.parametrize("rep_mode,local_theta,local_cluster", [(1, 0.0, 0), (0, 0.0, 0), (1, 0.5, 0), (1, 0.5, 4)])
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
-def test_production_theta_against_direct_sums(union500k_sample, theta, rep_mode, local_theta):
+def test_production_theta_against_direct_sums(union500k_sample, theta, rep_mode, local_theta, local_cluster):
     """The GPU treecode at the theta of production use against the plain
     definitions (the oracle's FP64 direct sums over all 500,000 sources), per
     element, for A, grad F = -G and A^T, at 10,000 seeded targets.
@@ -261,14 +261,16 @@ def test_production_theta_against_direct_sums(union500k_sample, theta, rep_mode,
         ||gpu - dir|| <= ||paper - dir||:
     no element of the GPU path is worse than the paper's treecode at its worst,
     and its overall error is no larger.  The measured errors are printed.
-    With local expansions (local_theta = 0.5) the same bound holds, and the
-    expansions add at most a tenth of the paper treecode's relative L2 error
-    to that of the pairwise far field at the same theta (their own error, of
-    second order in group extent / distance, does not shrink with theta)."""
+    With local expansions (local_theta = 0.5; one level, and two with clusters
+    of 4 groups) the same bound holds, and the expansions add at most a tenth
+    of the paper treecode's relative L2 error to that of the pairwise far
+    field at the same theta (their own error, of second order in group extent
+    / distance, does not shrink with theta)."""
     W = _wnnc()
     pts, mu, s, sub, direct_cache = union500k_sample
     w = 0.004
-    t = W.Tree(torch.from_numpy(pts).cuda(), theta=theta, rep_mode=rep_mode, local_theta=local_theta)
+    t = W.Tree(torch.from_numpy(pts).cuda(), theta=theta, rep_mode=rep_mode, local_theta=local_theta,
+               local_cluster=local_cluster)
     got = {OP_A: t.eval_w(torch.from_numpy(mu).cuda(), w),
            OP_G: t.eval_grad(torch.from_numpy(mu).cuda(), w),
            OP_AT: t.eval_adjoint(torch.from_numpy(s).cuda(), w)}
@@ -284,16 +286,16 @@ def test_production_theta_against_direct_sums(union500k_sample, theta, rep_mode,
         eg, ep, S = norm(g - d), norm(p - d), b["abssum"]
         rms = np.linalg.norm(d) / np.sqrt(len(sub))
         l2g, l2p = np.linalg.norm(g - d) / np.linalg.norm(d), np.linalg.norm(p - d) / np.linalg.norm(d)
-        print(f"[theta-parity] rep_mode={rep_mode} local_theta={local_theta} theta={theta} "
+        print(f"[theta-parity] rep_mode={rep_mode} local_theta={local_theta} cluster={local_cluster} theta={theta} "
               f"op={'A G AT'.split()[op]}: "
               f"gpu relL2 {l2g:.3e} max/rms {eg.max() / rms:.3e} max/S {(eg / S).max():.3e} | "
               f"paper treecode relL2 {l2p:.3e} max/rms {ep.max() / rms:.3e} max/S {(ep / S).max():.3e}")
         assert np.all(eg <= ep.max()), (op, eg.max(), ep.max())
         assert np.all(eg / S <= (ep / S).max()), (op, (eg / S).max(), (ep / S).max())
         assert l2g <= l2p, (op, l2g, l2p)
-        direct_cache[("gpu", rep_mode, local_theta, op, theta)] = l2g
-        if local_theta > 0 and ("gpu", 1, 0.0, op, theta) in direct_cache:
-            assert l2g <= direct_cache[("gpu", 1, 0.0, op, theta)] + 0.1 * l2p, op
+        direct_cache[("gpu", rep_mode, local_theta, local_cluster, op, theta)] = l2g
+        if local_theta > 0 and ("gpu", 1, 0.0, 0, op, theta) in direct_cache:
+            assert l2g <= direct_cache[("gpu", 1, 0.0, 0, op, theta)] + 0.1 * l2p, op
 
 
 @pytest.mark.parametrize("leaf", [1, 8])
