@@ -305,6 +305,9 @@ struct Tree {
     int part_slots = 0;
     double* scalars = nullptr;    // device scalars: [0]=E [1]=rr [2]=qq [3]=alpha
     int* err_flag = nullptr;      // device error flags
+    // a second stream for the adjoint's near pair sums, which overlap its far path
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     Profiler prof;
 };
 

@@ -2513,6 +2513,19 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
                           double* partial, cudaStream_t s) {
     AdjArgs a = adj_args(t, w);
     a.sv = s_sorted;
+    // the near pair sums need only s: on the second stream, overlapping the far path
+    const bool fork = t.adj_pair_work.nitems > 0 && t.aux;
+    if (fork) {
+        WNNC_CUDA(cudaEventRecord(t.ev_fork, s));
+        WNNC_CUDA(cudaStreamWaitEvent(t.aux, t.ev_fork, 0));
+        ProfScope ps(&t.prof, WNNC_PROF_ADJ_NEAR, t.aux);
+        AdjArgs pr = a;
+        pr.items = t.adj_pair_work.items;
+        pr.nitems = t.adj_pair_work.nitems;
+        k_adj_near_pairs<<<ceil_div(pr.nitems, kGatherWarps), 32 * kGatherWarps, 0, t.aux>>>(pr);
+        WNNC_LAUNCH_CHECK();
+        WNNC_CUDA(cudaEventRecord(t.ev_join, t.aux));
+    }
     if (t.self.far_entries > 0) {
         const bool dip = t.params.far_order == 1;
         {
@@ -2559,7 +2572,9 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
     } else {
         WNNC_CUDA(cudaMemsetAsync(t.vnode, 0, sizeof(float4) * t.nnodes, s));
     }
-    if (t.adj_pair_work.nitems > 0) {
+    if (fork) {
+        WNNC_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
+    } else if (t.adj_pair_work.nitems > 0) {
         ProfScope ps(&t.prof, WNNC_PROF_ADJ_NEAR, s);
         AdjArgs pr = a;
         pr.items = t.adj_pair_work.items;

@@ -1823,6 +1823,11 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
 }
 
 void free_tree(Tree& t) {
+    if (t.aux) cudaStreamDestroy(t.aux);
+    if (t.ev_fork) cudaEventDestroy(t.ev_fork);
+    if (t.ev_join) cudaEventDestroy(t.ev_join);
+    t.aux = nullptr;
+    t.ev_fork = t.ev_join = nullptr;
     dfree(t.keys); dfree(t.xs);
     dfree(t.node_start); dfree(t.node_count); dfree(t.node_parent); dfree(t.node_child0);
     dfree(t.node_nchild); dfree(t.node_depth); dfree(t.node_lo); dfree(t.node_hi); dfree(t.node_lof); dfree(t.node_hif);
