@@ -116,6 +116,7 @@ static void alloc_workspace(Tree& t) {
     }
     if (t.self.far_lsplit) {
         t.dip_corr = dalloc<float4>(n);   // per-target terms of the expanded entries
+        t.gather_raw = dalloc<float4>(n);
         t.node_abs = dalloc<float4>(nn);
         t.local_rec = dalloc<float4>(2 * (size_t)nn);
         t.gadj = dalloc<float4>(2 * (size_t)t.self.ngroups);

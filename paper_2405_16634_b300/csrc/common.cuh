@@ -121,6 +121,7 @@ struct WorkList {
     int nitems = 0;
     int4* splits = nullptr;     // (group, first slot, number of parts, -) of cut groups
     unsigned* split_cnt = nullptr;  // per cut group: parts finished (the last one finishes the group)
+    int* gsplit = nullptr;      // per group: its record in splits, or -1 (lists with partial sums)
     int nsplit = 0;
     int nslots = 0;
     int cap = 0;                // the item cap of this list (lane-slots)
@@ -305,8 +306,10 @@ struct Tree {
     int part_slots = 0;
     double* scalars = nullptr;    // device scalars: [0]=E [1]=rr [2]=qq [3]=alpha
     int* err_flag = nullptr;      // device error flags
-    // a second stream for the adjoint's near pair sums, which overlap its far path
+    // a second stream for the adjoint's near pair sums, which overlap its far path, and
+    // for the expanded far entries, which overlap the gather (its sums wait in gather_raw)
     cudaStream_t aux = nullptr;
+    float4* gather_raw = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     Profiler prof;
 };

@@ -291,6 +291,9 @@ struct GatherArgs {
     const int* lsplit;        // local_theta > 0: first expanded far entry of each group
     const float4* gctr;       //   the expansion centre in the group's frame and the group's radius
     const float4* lrec;       //   per node (centroid, M_x), (M_y, M_z, 0, 0) of this call's field
+    float4* raw;              // set: items of groups not cut store their sums here (G x,y,z, A)
+                              // instead of running the epilogue (k_gather_finalize_all does)
+    const int* gsplit;        //   per group its record in splits, or -1
     const int* csplit;        // local_cluster > 0: first entry expanded about the group's cluster
     int cluster_k;            //   groups per cluster
     int nclusters;
@@ -749,10 +752,12 @@ __global__ void WNNC_CAPPED_BOUNDS k_gather(GatherArgs A) {
     mine = combine<OP>(mine);
     const int64_t i = (int64_t)i0 + lane;
     const bool valid = lane < gsize;
-    if (item.pslot < 0) {
-        gather_epilogue<EPI>(A, g, i, valid, mine, lane);
-    } else {
+    if (item.pslot >= 0) {
         A.part_acc[(int64_t)item.pslot * 32 + lane] = make_float4(mine.x, mine.y, mine.z, mine.s);
+    } else if (A.raw) {
+        if (valid) A.raw[i] = make_float4(mine.x, mine.y, mine.z, mine.s);
+    } else {
+        gather_epilogue<EPI>(A, g, i, valid, mine, lane);
     }
 }
 
@@ -1074,6 +1079,36 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_local_cl(GatherArgs A, flo
         const float4 c = corr[i0 + j];
         corr[i0 + j] = make_float4(c.x + f.x, c.y + f.y, c.z + f.z, c.w + f.w);
     }
+}
+
+// Every group's epilogue after a gather that left its sums in A.raw (groups
+// not cut) or in the part slots (cut groups, added in order): warp per group.
+template <int EPI>
+__global__ void k_gather_finalize_all(GatherArgs A) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= A.ngroups) return;
+    const int i0 = A.goff[g];
+    const bool valid = lane < A.goff[g + 1] - i0;
+    Acc3 acc;
+    const int sp = A.gsplit[g];
+    if (sp >= 0) {
+        const int4 r = A.splits[sp];
+        for (int p = 0; p < r.z; ++p) {
+            const float4 v = A.part_acc[(int64_t)(r.y + p) * 32 + lane];
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.s += v.w;
+        }
+    } else if (valid) {
+        const float4 v = A.raw[i0 + lane];
+        acc.x = v.x;
+        acc.y = v.y;
+        acc.z = v.z;
+        acc.s = v.w;
+    }
+    gather_epilogue<EPI>(A, g, (int64_t)i0 + lane, valid, acc, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -2476,6 +2511,42 @@ void local_setup(Tree& t, cudaStream_t s) {
     WNNC_LAUNCH_CHECK();
 }
 
+// The gather of one field with its expanded far entries.  On the points as
+// targets, with a second stream: the expanded entries (latency-bound) run on
+// it while the gather (FP32-bound) sums the pairs on s and leaves its sums in
+// gather_raw; after the join, one pass per group adds both and runs the
+// epilogue.  Otherwise the expanded entries first, then the gather.
+template <int OP, int EPI>
+static void gather_with_local(Tree& t, const TargetSet& ts, GatherArgs& a, cudaStream_t s) {
+    if (!ts.far_lsplit) {
+        launch_gather<OP, EPI>(t, a, s);
+        return;
+    }
+    if (!t.aux || &ts != &t.self || !ts.work.gsplit || a.walk || a.near_bf16) {
+        local_far<OP>(t, ts, a, t.dip_corr, s);
+        launch_gather<OP, EPI>(t, a, s);
+        return;
+    }
+    WNNC_CUDA(cudaEventRecord(t.ev_fork, s));
+    WNNC_CUDA(cudaStreamWaitEvent(t.aux, t.ev_fork, 0));
+    local_far<OP>(t, ts, a, t.dip_corr, t.aux);
+    WNNC_CUDA(cudaEventRecord(t.ev_join, t.aux));
+    a.raw = t.gather_raw;
+    a.gsplit = ts.work.gsplit;
+    {
+        ProfScope ps(&t.prof,
+                     OP == kOpAG ? WNNC_PROF_AG : (OP == kOpG ? WNNC_PROF_G : WNNC_PROF_A), s);
+        if (a.nitems > 0) {
+            k_gather<OP, EPI, false, kGatherTPL><<<ceil_div(a.nitems, kGatherWarps), 32 * kGatherWarps, 0, s>>>(a);
+            WNNC_LAUNCH_CHECK();
+        }
+    }
+    WNNC_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
+    ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
+    k_gather_finalize_all<EPI><<<ceil_div((int64_t)ts.ngroups * 32, kTB), kTB, 0, s>>>(a);
+    WNNC_LAUNCH_CHECK();
+}
+
 void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     const float s2 = (float)(t.scale * t.scale);
     perm_in_vec(t, mu, s2, t.mu_a, s);
@@ -2487,8 +2558,7 @@ void eval_w(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     }
     a.sval = t.mu_a;
     a.out = out;
-    local_far<kOpA>(t, t.self, a, t.dip_corr, s);
-    launch_gather<kOpA, kEpiStoreW>(t, a, s);
+    gather_with_local<kOpA, kEpiStoreW>(t, t.self, a, s);
 }
 
 void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
@@ -2503,8 +2573,7 @@ void eval_grad(Tree& t, const float* mu, float w, float* out, cudaStream_t s) {
     a.sval = t.mu_a;
     a.out = out;
     a.scale = (float)t.scale;
-    local_far<kOpG>(t, t.self, a, t.dip_corr, s);
-    launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
+    gather_with_local<kOpG, kEpiStoreGrad>(t, t.self, a, s);
 }
 
 // r_sorted <- A^T(s_sorted) in normalised units (exact transpose, rep_mode 1),
@@ -2733,8 +2802,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             a.s_out = t.s_s;
             a.partial = pE;
             a.g_out = t.g_mu;
-            local_far<kOpAG>(t, S, a, t.dip_corr, s);
-            launch_gather<kOpAG, kEpiResidualAG>(t, a, s);
+            gather_with_local<kOpAG, kEpiResidualAG>(t, S, a, s);
             // r = A^T s
             adjoint_exact(t, t.s_s, w, nullptr, t.r_s, prr, s);
             // |A r|^2, with G(r)
@@ -2748,8 +2816,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             b.sval = t.r_s;
             b.partial = pqq;
             b.g_out = t.g_r;
-            local_far<kOpAG>(t, S, b, t.dip_corr, s);
-            launch_gather<kOpAG, kEpiNormSqAG>(t, b, s);
+            gather_with_local<kOpAG, kEpiNormSqAG>(t, S, b, s);
             {
                 ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
                 k_reduce3<<<kRedBlocks, kTB, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.red, t.scalars, st,
@@ -2773,8 +2840,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             a.sval = mu;
             a.s_out = t.s_s;
             a.partial = pE;
-            local_far<kOpA>(t, S, a, t.dip_corr, s);
-            launch_gather<kOpA, kEpiResidual>(t, a, s);
+            gather_with_local<kOpA, kEpiResidual>(t, S, a, s);
             // r = A^T s
             if (rep_mode == 1) {
                 adjoint_exact(t, t.s_s, w, nullptr, t.r_s, prr, s);
@@ -2799,8 +2865,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             b.nmom = mom_r;
             b.sval = t.r_s;
             b.partial = pqq;
-            local_far<kOpA>(t, S, b, t.dip_corr, s);
-            launch_gather<kOpA, kEpiNormSq>(t, b, s);
+            gather_with_local<kOpA, kEpiNormSq>(t, S, b, s);
             {
                 ProfScope ps(&t.prof, WNNC_PROF_SMALL, s);
                 k_reduce3<<<kRedBlocks, kTB, 0, s>>>(pE, S.ngroups, prr, n_rr, pqq, S.ngroups, t.red, t.scalars, st,
@@ -2835,8 +2900,7 @@ void iterate(Tree& t, float* mu_inout, const float* area, const wnnc_iter_params
             g.mu_out = mu_alt;
             g.area = t.area_s;
             g.rescale_mode = p.rescale;
-            local_far<kOpG>(t, S, g, t.dip_corr, s);
-            launch_gather<kOpG, kEpiRescale>(t, g, s);
+            gather_with_local<kOpG, kEpiRescale>(t, S, g, s);
             std::swap(mu, mu_alt);
         }
     }

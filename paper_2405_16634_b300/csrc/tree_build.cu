@@ -1111,6 +1111,11 @@ __global__ void k_items_fill(int mode, int nseg, const int* near_off, const int2
     if (partials && cnt[g] > 1) splits[split_off[g]] = make_int4(g, slot_off[g], cnt[g], 0);
 }
 
+__global__ void k_group_splits(const int* cnt, const int* split_off, int nseg, int* gsplit) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < nseg) gsplit[g] = cnt[g] > 1 ? split_off[g] : -1;
+}
+
 __global__ void k_split_flags(const int* cnt, int nseg, int* flag) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g < nseg) flag[g] = cnt[g] > 1;
@@ -1161,6 +1166,7 @@ void free_work(WorkList& w) {
     dfree(w.items);
     dfree(w.splits);
     dfree(w.split_cnt);
+    dfree(w.gsplit);
     w.nitems = w.nsplit = w.nslots = 0;
 }
 
@@ -1211,6 +1217,11 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     Item* tmp = dalloc<Item>(w.nitems);
     w.splits = dalloc<int4>(w.nsplit);
     w.split_cnt = dalloc<unsigned>(w.nsplit);
+    if (partials) {
+        w.gsplit = dalloc<int>(nseg);
+        k_group_splits<<<ceil_div(nseg, kTB), kTB, 0, s>>>(cnt, split_off, nseg, w.gsplit);
+        WNNC_LAUNCH_CHECK();
+    }
     WNNC_CUDA(cudaMemsetAsync(w.split_cnt, 0, sizeof(unsigned) * (size_t)std::max(w.nsplit, 1), s));
     k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit, cap, cnt,
                                                     item_off, slot_off, partials, tmp, w.splits, split_off);
@@ -1844,6 +1855,7 @@ void free_tree(Tree& t) {
     dfree(t.near_contrib); dfree(t.vnode); dfree(t.red_ticket);
     dfree(t.mom_dip); dfree(t.mom_dip_r); dfree(t.dip_corr); dfree(t.contrib_h0); dfree(t.contrib_h1);
     dfree(t.node_abs); dfree(t.local_rec); dfree(t.tfar_lsplit); dfree(t.gadj); dfree(t.tfar_csplit);
+    dfree(t.gather_raw);
     dfree(t.cadj);
     dfree(t.hnode0); dfree(t.hnode1);
     dfree(t.partials); dfree(t.red); dfree(t.part_acc); dfree(t.scalars); dfree(t.err_flag);
