@@ -828,10 +828,10 @@ __global__ void k_cluster_frames(const double* ys, const int* goff, const double
 }
 
 // Warp per cluster of at least two groups: the entries of the first member's
-// expanded part whose node also lies in every other member's expanded part
-// (each ascending: binary search) and is local for the cluster's box (the
-// exact FP64 test of the group's: squared box gap > cle^2) are flagged in
-// every member.
+// expanded part whose node is local for the cluster's box (the exact FP64
+// test of the group's: squared box gap > cle^2) and also lies in every other
+// member's expanded part (each ascending: binary search) are flagged in every
+// member.
 __global__ void k_cluster_classes(const int* far_off, const int* lsplit, const int* far_id, int ng, int K,
                                   const double* nlo, const double* nhi, const double* clo, const double* chi,
                                   const double* cle, unsigned char* moved) {
@@ -846,6 +846,7 @@ __global__ void k_cluster_classes(const int* far_off, const int* lsplit, const i
     const double c2 = __dmul_rn(cle[C], cle[C]);
     for (int e = lsplit[g0] + lane; e < far_off[g0 + 1]; e += 32) {
         const int b = far_id[e];
+        if (!(box_gap2_d(nlo, nhi, b, lo, hi) > c2)) continue;
         int qm[kMaxCluster];
         bool all = true;
         for (int m = 1; m < g1 - g0 && all; ++m) {
@@ -857,7 +858,7 @@ __global__ void k_cluster_classes(const int* far_off, const int* lsplit, const i
             if (a < far_off[g0 + m + 1] && far_id[a] == b) qm[m] = a;
             else all = false;
         }
-        if (!all || !(box_gap2_d(nlo, nhi, b, lo, hi) > c2)) continue;
+        if (!all) continue;
         moved[e] = 1;
         for (int m = 1; m < g1 - g0; ++m) moved[qm[m]] = 1;
     }

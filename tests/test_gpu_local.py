@@ -289,3 +289,31 @@ def test_cluster_iteration_matches_oracle():
     print(f"[cluster-iterate-20k] sign agreement {np.mean(cos > 0):.5f}, median cos {np.median(cos):.6f}, "
           f"median |len| diff {dlen:.2e}, P_co gpu {pg:.5f} oracle {po:.5f}")
     assert abs(pg - po) < 0.005
+
+
+def test_autograd_with_both_levels(union5k):
+    """The expanded forward is linear in mu and A^T is its exact transpose, so
+    the autograd backward equals central differences of the forward: with
+    s = dL/dF, dL/dmu_k = <A e_k, s> = (A^T s)_k."""
+    W = _wnnc()
+    c, mu, s = union5k
+    t = W.Tree(torch.from_numpy(c.points).cuda(), theta=0.5, local_theta=0.5, local_cluster=4)
+    w = 0.004
+    m = torch.from_numpy(mu).cuda().requires_grad_()
+    sv = torch.from_numpy(s).cuda()
+    F = W.winding_number(t, m, w)
+    (F * sv).sum().backward()
+    g = m.grad.double().cpu().numpy()
+    assert np.array_equal(g, t.eval_adjoint(sv, w).double().cpu().numpy())
+    rng = np.random.default_rng(3)
+    h = 1e-3 * float(np.abs(mu).max())
+    for k in rng.choice(mu.size, 24, replace=False):
+        i, j = divmod(int(k), 3)
+        mp, mm = mu.copy(), mu.copy()
+        mp[i, j] += h
+        mm[i, j] -= h
+        fp = t.eval_w(torch.from_numpy(mp).cuda(), w).double().cpu().numpy()
+        fm = t.eval_w(torch.from_numpy(mm).cuda(), w).double().cpu().numpy()
+        fd = ((fp - fm) * s).sum() / (2 * h)
+        scale = np.abs(g).max()
+        assert abs(fd - g[i, j]) <= 2e-3 * scale, (i, j, fd, g[i, j])
