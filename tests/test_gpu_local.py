@@ -306,14 +306,16 @@ def test_autograd_with_both_levels(union5k):
     g = m.grad.double().cpu().numpy()
     assert np.array_equal(g, t.eval_adjoint(sv, w).double().cpu().numpy())
     rng = np.random.default_rng(3)
-    h = 1e-3 * float(np.abs(mu).max())
-    for k in rng.choice(mu.size, 24, replace=False):
+    idx = rng.choice(mu.size, 32, replace=False)
+    h = 1e-3                                   # F is linear: the step costs no truncation
+    fd = []
+    for k in idx:
         i, j = divmod(int(k), 3)
         mp, mm = mu.copy(), mu.copy()
         mp[i, j] += h
         mm[i, j] -= h
         fp = t.eval_w(torch.from_numpy(mp).cuda(), w).double().cpu().numpy()
         fm = t.eval_w(torch.from_numpy(mm).cuda(), w).double().cpu().numpy()
-        fd = ((fp - fm) * s).sum() / (2 * h)
-        scale = np.abs(g).max()
-        assert abs(fd - g[i, j]) <= 2e-3 * scale, (i, j, fd, g[i, j])
+        fd.append(((fp - fm) * s).sum() / (2 * h))
+    ag = g.reshape(-1)[idx]
+    assert np.abs(np.array(fd) - ag).max() <= 1e-3 * np.abs(ag).max()
