@@ -249,7 +249,9 @@ struct Tree {
 
     // transposed lists (adjoint, rep_mode 1)
     int* tfar_off = nullptr;      // [nnodes+1]
-    int* tfar_ent = nullptr;      // far-entry index (position in self.far_id), grouped by node
+    int* tfar_ent = nullptr;      // far-entry index (position in self.far_id), grouped by node; with
+                                  // local expansions class << 30 | id: 0 the entry, 1 (expanded about
+                                  // a group) the group, 2 (about a cluster) the cluster
     int nach = 0;                 // source chunks of the adjoint near part (kAdjChunk points each)
     int* tnear_off = nullptr;     // [nach+1], per source chunk
     // per (source chunk, target group): (near slot of the first point of the
@@ -289,11 +291,7 @@ struct Tree {
     // local expansions (local_theta > 0)
     float4* node_abs = nullptr;   // per node: point centroid in normalised coordinates (float)
     float4* local_rec = nullptr;  // per node, 32 bytes, rebuilt per call: (centroid, M_x), (M_y, M_z, 0, 0)
-    int* tfar_lsplit = nullptr;   // per node: first expanded transposed entry; tfar_ent holds the
-                                  // entry index before it and the entry's group from it on
     float4* gadj = nullptr;       // per group, rebuilt per adjoint call: (c_g, rho_g), (D, S)
-    int* tfar_csplit = nullptr;   // per node: first transposed entry expanded about a cluster
-                                  // (local_cluster > 0; tfar_ent holds the cluster from there)
     float4* cadj = nullptr;       // per cluster, rebuilt per adjoint call: (c_C, rho_C), (D, S)
     float4* contrib_h0 = nullptr; // per far entry: sum s HPhi, (xx, yy, zz, -) and (xy, xz, yz, -)
     float4* contrib_h1 = nullptr;
@@ -322,8 +320,8 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
 // bits (e.g. an index appended in ascending order), stability makes the result
 // the same as a sort on all the low `bits` bits.
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s, int lo_bit = 0);
-// off[g] = first index i with (keys[i] >> 32) >= g, for g in [0, ng]; keys sorted.
-void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s);
+// off[g] = first index i with (keys[i] >> shift) >= g, for g in [0, ng]; keys sorted.
+void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s, int shift = 32);
 
 // tree build (tree_build.cu)
 void build_tree(Tree& t, const float* pts, cudaStream_t s);

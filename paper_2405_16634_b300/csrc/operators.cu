@@ -1224,11 +1224,9 @@ struct AdjArgs {
     int ngroups;
     int nnodes;
     const int* tfar_off;      // transposed far lists (node -> entries)
-    const int* tfar_ent;
-    const int* tfar_lsplit;   //   per node the first expanded entry (tfar_ent: its group from there)
+    const int* tfar_ent;      //   with local_theta > 0: class << 30 | id (0 the entry, 1 a group, 2 a cluster)
     float4* gadj;             //   per group (c_g, rho_g), (D, S), normalised coordinates
-    const int* tfar_csplit;   // local_cluster > 0: per node the first entry expanded about a cluster
-    float4* cadj;             //   per cluster (c_C, rho_C), (D, S)
+    float4* cadj;             //   local_cluster > 0: per cluster (c_C, rho_C), (D, S)
     int cluster_k;
     int nclusters;
     const float4* cctr;       //   cluster frame origins
@@ -1421,10 +1419,9 @@ __device__ __noinline__ float4 local_entry_pairs(const AdjArgs& A, int i0, int i
 // node's whole transposed list (U reads in flight per lane, then the sums:
 // 4 for the longer lists of one expansion level, 2 with clusters, whose
 // shorter lists gain more from the extra resident warps of the smaller
-// register count).  The list holds the entries summed pair by pair (their contrib),
-// from tlsplit on those expanded about a group (tfar_ent: the group; its
-// record gadj) and from tcsplit on those expanded about a cluster (the
-// cluster; cadj): a lane's class follows from its position.
+// register count).  Each list item carries its class in bits 30-31: an entry
+// summed pair by pair (its contrib), one expanded about a group (the group;
+// its record gadj) or one expanded about a cluster (the cluster; cadj).
 constexpr int kNodeGathers = 16;
 
 // The transposed term of one expanded entry from its group's or cluster's
@@ -1440,42 +1437,41 @@ __global__ void k_adj_node_local(AdjArgs A, float4* vnode) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= A.nnodes) return;
-    const int q0 = A.tfar_off[b], qs = A.tfar_lsplit[b], q1 = A.tfar_off[b + 1];
-    const int qc = A.tfar_csplit ? A.tfar_csplit[b] : q1;      // [qs, qc) groups, [qc, q1) clusters
+    const int q0 = A.tfar_off[b], q1 = A.tfar_off[b + 1];
     float ax = 0.f, ay = 0.f, az = 0.f;
     const float4 xb = A.nabs[b];
     for (int q = q0 + lane; q < q1; q += 32 * U) {
-        int id[U];
+        int v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) id[u] = q + 32 * u < q1 ? A.tfar_ent[q + 32 * u] : -1;
+        for (int u = 0; u < U; ++u) v[u] = q + 32 * u < q1 ? A.tfar_ent[q + 32 * u] : -1;
         float4 c0[U], c1[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int qq = q + 32 * u;
             c0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             c1[u] = c0[u];
-            if (id[u] < 0) continue;
-            if (qq < qs) {
-                c0[u] = A.contrib[id[u]];
+            if (v[u] == -1) continue;   // class 2 sets the sign bit
+            const int cls = (unsigned)v[u] >> 30, id = v[u] & 0x3fffffff;
+            if (cls == 0) {
+                c0[u] = A.contrib[id];
             } else {
-                const float4* rec = qq < qc ? A.gadj : A.cadj;
-                c0[u] = rec[2 * id[u]];
-                c1[u] = rec[2 * id[u] + 1];
+                const float4* rec = cls == 1 ? A.gadj : A.cadj;
+                c0[u] = rec[2 * id];
+                c1[u] = rec[2 * id + 1];
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int qq = q + 32 * u;
-            if (id[u] < 0) continue;
-            if (qq < qs) {
+            if (v[u] == -1) continue;   // class 2 sets the sign bit
+            const int cls = (unsigned)v[u] >> 30, id = v[u] & 0x3fffffff;
+            if (cls == 0) {
                 ax += c0[u].x;
                 ay += c0[u].y;
                 az += c0[u].z;
-            } else if (qq < qc) {
-                adj_local_term(A, xb, c0[u], c1[u], b, A.goff[id[u]], A.goff[id[u] + 1], A.gorig[id[u]], ax, ay, az);
+            } else if (cls == 1) {
+                adj_local_term(A, xb, c0[u], c1[u], b, A.goff[id], A.goff[id + 1], A.gorig[id], ax, ay, az);
             } else {
-                const int g0 = id[u] * A.cluster_k, g1 = min(g0 + A.cluster_k, A.ngroups);
-                adj_local_term(A, xb, c0[u], c1[u], b, A.goff[g0], A.goff[g1], A.cctr[id[u]], ax, ay, az);
+                const int g0 = id * A.cluster_k, g1 = min(g0 + A.cluster_k, A.ngroups);
+                adj_local_term(A, xb, c0[u], c1[u], b, A.goff[g0], A.goff[g1], A.cctr[id], ax, ay, az);
             }
         }
     }
@@ -2339,9 +2335,7 @@ AdjArgs adj_args(const Tree& t, float w) {
     a.nnodes = t.nnodes;
     a.tfar_off = t.tfar_off;
     a.tfar_ent = t.tfar_ent;
-    a.tfar_lsplit = t.tfar_lsplit;
     a.gadj = t.gadj;
-    a.tfar_csplit = t.tfar_csplit;
     a.cadj = t.cadj;
     a.cluster_k = S.cluster_k;
     a.nclusters = S.nclusters;
@@ -2617,13 +2611,13 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
             ProfScope ps(&t.prof, WNNC_PROF_LOCAL, s);
             k_local_groups<<<ceil_div((int64_t)t.self.ngroups * 32, kTB), kTB, 0, s>>>(a);
             WNNC_LAUNCH_CHECK();
-            if (a.tfar_csplit) {
+            if (a.cadj) {
                 k_local_clusters<<<ceil_div((int64_t)t.self.nclusters * 32, kTB), kTB, 0, s>>>(a);
                 WNNC_LAUNCH_CHECK();
             }
         }
         ProfScope ps(&t.prof, WNNC_PROF_ADJ_NODE, s);
-        if (a.lsplit && a.tfar_csplit) {
+        if (a.lsplit && a.cadj) {
             k_adj_node_local<2><<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);
         } else if (a.lsplit) {
             k_adj_node_local<4><<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);

@@ -231,11 +231,11 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, 
     }
 }
 
-__global__ void k_seg_off(const uint64_t* keys, int64_t n, int* off, int ng) {
+__global__ void k_seg_off(const uint64_t* keys, int64_t n, int* off, int ng, int shift) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int64_t g = (int64_t)(keys[i] >> 32);
-    int64_t gp = i > 0 ? (int64_t)(keys[i - 1] >> 32) : -1;
+    int64_t g = (int64_t)(keys[i] >> shift);
+    int64_t gp = i > 0 ? (int64_t)(keys[i - 1] >> shift) : -1;
     for (int64_t q = gp + 1; q <= g && q <= ng; ++q) off[q] = (int)i;
     if (i == n - 1)
         for (int64_t q = g + 1; q <= ng; ++q) off[q] = (int)n;
@@ -291,13 +291,13 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
     pool_free(hist);
 }
 
-void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s) {
+void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s, int shift) {
     if (n == 0) {
         k_fill_i32<<<ceil_div(ng + 1, 256), 256, 0, s>>>(off, ng + 1, 0);
         WNNC_LAUNCH_CHECK();
         return;
     }
-    k_seg_off<<<ceil_div(n, 256), 256, 0, s>>>(keys, n, off, ng);
+    k_seg_off<<<ceil_div(n, 256), 256, 0, s>>>(keys, n, off, ng, shift);
     WNNC_LAUNCH_CHECK();
 }
 

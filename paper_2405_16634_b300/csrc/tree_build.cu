@@ -487,51 +487,94 @@ constexpr int kStackSmall = 2048;
 constexpr int kStackBig = 4096;
 
 // Warp-cooperative traversal of the octree for one target group, one pass:
-// it writes keys (group<<32 | node) for far entries and (group<<32 | first
-// point) with the leaf id for near leaves (sorted by group afterwards).  Up
-// to 32 nodes are tested at once; children of opened nodes go into a per-warp
-// shared buffer whose capacity is checked before a push.
+// it writes far node ids in chunks (below) and, for near leaves, keys
+// (group << nsh | first point) with the leaf id (sorted by key afterwards).
+// Up to 32 nodes are tested at once; children of opened nodes go into a
+// per-warp shared buffer whose capacity is checked before a push.
 //
 // FIFO = true: the buffer is a ring visited first-in first-out.  Nodes are
 // numbered level by level, children of one parent consecutively and child
 // blocks in the order of their parents, so a first-in first-out walk from the
-// root visits nodes in ascending id: each group's far nodes are written in
-// ascending order, and a stable sort on the group alone yields the lists
-// sorted by (group, node).  The width of that walk grows with the group's box
-// (a box spanning many cells opens many nodes per level); when fewer than 256
-// free slots (32 nodes x 8 children) remain, the warp finishes its group as a
+// root visits nodes in ascending id and each group's far nodes come out
+// ascending.  The width of that walk grows with the group's box (a box
+// spanning many cells opens many nodes per level); when fewer than 256 free
+// slots (32 nodes x 8 children) remain, the warp finishes its group as a
 // stack walk in the same ring and appends the group to `unsorted`, whose far
-// keys the caller sorts by node afterwards.  FIFO = false: a stack walk
+// lists the caller sorts by node afterwards.  FIFO = false: a stack walk
 // (last-in first-out) throughout, whose depth grows far more slowly as theta
-// shrinks; its far keys need the full sort.  Keys collect in per-warp shared buffers that are flushed to
-// global pools, one atomic reservation per flush; past a pool's capacity
-// nothing is written but the pool's counter still counts, so that the caller
-// can size the pools exactly and run the traversal again.
+// shrinks; all its far lists are sorted afterwards.
+//
+// Far ids collect in per-warp shared buffers, one for the entries summed pair
+// by pair (class 0) and, with local expansions, one for the expanded entries
+// (class 1).  A buffer is flushed to the global pool with one atomic
+// reservation, and the flush writes a chunk record (pool position, count,
+// group, class << 31 | the number of the group's entries of that class
+// flushed before).  A warp's flushes take ascending pool positions, so the
+// records place every chunk in its group's list with no sort: the list is the
+// class-0 entries, then the class-1 ones, each in the order of the walk.  At
+// the end the warp writes its group's two counts.  Past a pool's capacity
+// nothing is written but the counters still count, so that the caller can
+// size the pools exactly and run the traversal again.
 constexpr int kTravBuf = 128;
 
-__device__ __forceinline__ void trav_flush(const uint64_t* buf, const uint32_t* vbuf, int cnt, uint64_t* pool,
-                                           uint32_t* vpool, int64_t cap, unsigned long long* counter,
-                                           int lane) {
+__device__ __forceinline__ void trav_flush_far(const int* buf, int cnt, int* pool, int64_t cap,
+                                               unsigned long long* counter, int4* chunks, int64_t chunk_cap,
+                                               unsigned long long* chunk_counter, int g, int cls, int prefix,
+                                               int lane) {
+    unsigned long long base = 0, ck = 0;
+    if (lane == 0) {
+        base = atomicAdd(counter, (unsigned long long)cnt);
+        ck = atomicAdd(chunk_counter, 1ull);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    ck = __shfl_sync(0xffffffffu, ck, 0);
+    if ((int64_t)(base + cnt) <= cap && (int64_t)ck < chunk_cap) {
+        for (int k = lane; k < cnt; k += 32) pool[base + k] = buf[k];
+        if (lane == 0) chunks[ck] = make_int4((int)base, cnt, g, (cls << 31) | prefix);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void trav_flush_near(const uint64_t* buf, const uint32_t* vbuf, int cnt, uint64_t* pool,
+                                                uint32_t* vpool, int64_t cap, unsigned long long* counter,
+                                                int lane) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(counter, (unsigned long long)cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
     if ((int64_t)(base + cnt) <= cap)
         for (int k = lane; k < cnt; k += 32) {
             pool[base + k] = buf[k];
-            if (vbuf) vpool[base + k] = vbuf[k];
+            vpool[base + k] = vbuf[k];
         }
     __syncwarp();
 }
+
+struct TravOut {
+    int* far_pool;                    // far node ids, in chunks
+    int64_t far_cap;
+    unsigned long long* far_count;
+    int4* chunks;                     // chunk records
+    int64_t chunk_cap;
+    unsigned long long* chunk_count;
+    int2* gcount;                     // per group: class-0 and class-1 far entries
+    uint64_t* near_pool;              // near keys (group << nsh | first point)
+    uint32_t* near_vpool;             //   and leaf ids
+    int64_t near_cap;
+    unsigned long long* near_count;
+    int nsh;
+    int* err;
+    uint64_t* unsorted;               // groups whose walk was finished as a stack walk
+    int* unsorted_count;
+};
 
 template <int STACK, bool FIFO>
 __global__ void __launch_bounds__(32 * kTravWarps)
 k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float4* nhif, const int* ndepth,
            const int* nchild, const int* child0, const int* nstart, const double* glo, const double* ghi, int ng,
-           double theta, double clocal, uint64_t* far_pool, int64_t far_cap, unsigned long long* far_count,
-           uint64_t* near_pool, uint32_t* near_vpool, int64_t near_cap, unsigned long long* near_count,
-           int* err, uint64_t* unsorted, int* unsorted_count) {
+           double theta, double clocal, TravOut out) {
     __shared__ int stack[kTravWarps][STACK];
-    __shared__ uint64_t fbuf_all[kTravWarps][kTravBuf];
+    __shared__ int fbuf_all[kTravWarps][kTravBuf];
+    __shared__ int lbuf_all[kTravWarps][kTravBuf];
     __shared__ uint64_t nbuf_all[kTravWarps][kTravBuf];
     __shared__ uint32_t nvbuf_all[kTravWarps][kTravBuf];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -550,14 +593,15 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
     const float mscale = 1e-6f * (1.f + fmaxf(gs, 1.f));
     // local expansions (clocal = 1/local_theta, 0 = off): a far node is expanded
     // about the group centre when its box gap exceeds clocal x the group box's
-    // largest extent (flag bit 31 of the key's low word)
+    // largest extent (class 1)
     double ext = __dsub_rn(bh[0], bl[0]);
     if (__dsub_rn(bh[1], bl[1]) > ext) ext = __dsub_rn(bh[1], bl[1]);
     if (__dsub_rn(bh[2], bl[2]) > ext) ext = __dsub_rn(bh[2], bl[2]);
     const double cle = __dmul_rn(clocal, ext);
     const float clef = (float)cle;
     int* st = stack[wl];
-    uint64_t* fbuf = fbuf_all[wl];
+    int* fbuf = fbuf_all[wl];
+    int* lbuf = lbuf_all[wl];
     uint64_t* nbuf = nbuf_all[wl];
     uint32_t* nvbuf = nvbuf_all[wl];
     static_assert((STACK & (STACK - 1)) == 0, "ring size must be a power of two");
@@ -565,12 +609,12 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
     __syncwarp();
     // live entries are [head, head + top) modulo STACK; pushes append at the
     // end; first-in first-out pops from head, the stack walk from the end
-    int head = 0, top = 1, fcnt = 0, ncnt = 0;
+    int head = 0, top = 1, fcnt = 0, lcnt = 0, ncnt = 0, fdone = 0, ldone = 0;
     bool fifo = FIFO;
     while (top > 0) {
         if (fifo && top > STACK - 256) {
             fifo = false;
-            if (lane == 0) unsorted[atomicAdd(unsorted_count, 1)] = (uint64_t)g;
+            if (lane == 0) out.unsorted[atomicAdd(out.unsorted_count, 1)] = (uint64_t)g;
         }
         int take = min(top, 32);
         int b = -1;
@@ -591,22 +635,33 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
                 if (nchild[b] == 0) leaf = true; else open = true;
             }
         }
-        unsigned fm = __ballot_sync(0xffffffffu, far), lm = __ballot_sync(0xffffffffu, leaf);
+        const unsigned fm = __ballot_sync(0xffffffffu, far && !loc), xm = __ballot_sync(0xffffffffu, loc);
+        const unsigned lm = __ballot_sync(0xffffffffu, leaf);
         if (fcnt + 32 > kTravBuf) {
-            trav_flush(fbuf, nullptr, fcnt, far_pool, nullptr, far_cap, far_count, lane);
+            trav_flush_far(fbuf, fcnt, out.far_pool, out.far_cap, out.far_count, out.chunks, out.chunk_cap,
+                           out.chunk_count, g, 0, fdone, lane);
+            fdone += fcnt;
             fcnt = 0;
         }
+        if (lcnt + 32 > kTravBuf) {
+            trav_flush_far(lbuf, lcnt, out.far_pool, out.far_cap, out.far_count, out.chunks, out.chunk_cap,
+                           out.chunk_count, g, 1, ldone, lane);
+            ldone += lcnt;
+            lcnt = 0;
+        }
         if (ncnt + 32 > kTravBuf) {
-            trav_flush(nbuf, nvbuf, ncnt, near_pool, near_vpool, near_cap, near_count, lane);
+            trav_flush_near(nbuf, nvbuf, ncnt, out.near_pool, out.near_vpool, out.near_cap, out.near_count, lane);
             ncnt = 0;
         }
-        if (far) fbuf[fcnt + __popc(fm & lt)] = ((uint64_t)g << 32) | (loc ? 0x80000000u : 0u) | (uint32_t)b;
+        if (far && !loc) fbuf[fcnt + __popc(fm & lt)] = b;
+        if (loc) lbuf[lcnt + __popc(xm & lt)] = b;
         if (leaf) {
-            int p = ncnt + __popc(lm & lt);
-            nbuf[p] = ((uint64_t)g << 32) | (uint32_t)nstart[b];
+            const int p = ncnt + __popc(lm & lt);
+            nbuf[p] = ((uint64_t)g << out.nsh) | (uint32_t)nstart[b];
             nvbuf[p] = (uint32_t)b;
         }
         fcnt += __popc(fm);
+        lcnt += __popc(xm);
         ncnt += __popc(lm);
         int nc = open ? nchild[b] : 0;
         int inc = nc;
@@ -617,7 +672,7 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
         }
         int total = __shfl_sync(0xffffffffu, inc, 31);
         if (top + total > STACK) {
-            if (lane == 0) atomicOr(err, kErrCapacity);
+            if (lane == 0) atomicOr(out.err, kErrCapacity);
             break;
         }
         if (open) {
@@ -628,8 +683,37 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
         __syncwarp();
     }
     __syncwarp();
-    if (fcnt) trav_flush(fbuf, nullptr, fcnt, far_pool, nullptr, far_cap, far_count, lane);
-    if (ncnt) trav_flush(nbuf, nvbuf, ncnt, near_pool, near_vpool, near_cap, near_count, lane);
+    if (fcnt)
+        trav_flush_far(fbuf, fcnt, out.far_pool, out.far_cap, out.far_count, out.chunks, out.chunk_cap,
+                       out.chunk_count, g, 0, fdone, lane);
+    if (lcnt)
+        trav_flush_far(lbuf, lcnt, out.far_pool, out.far_cap, out.far_count, out.chunks, out.chunk_cap,
+                       out.chunk_count, g, 1, ldone, lane);
+    if (ncnt) trav_flush_near(nbuf, nvbuf, ncnt, out.near_pool, out.near_vpool, out.near_cap, out.near_count, lane);
+    if (lane == 0) out.gcount[g] = make_int2(fdone + fcnt, ldone + lcnt);
+}
+
+// Far list offsets from the per-group counts: tot[g] = class 0 + class 1.
+__global__ void k_gcount_tot(const int2* gcount, int ng, int* tot) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) tot[g] = gcount[g].x + gcount[g].y;
+}
+
+// Each chunk of the pool to its place in its group's list (warp per chunk);
+// with local expansions also lsplit[g] = the start of the group's class-1 part.
+__global__ void k_far_place(const int4* chunks, int64_t nchunks, const int* pool, const int* far_off,
+                            const int2* gcount, int* far_id) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= nchunks) return;
+    const int4 c = chunks[k];
+    const int cls = (unsigned)c.w >> 31, prefix = c.w & 0x7fffffff;
+    const int dst = far_off[c.z] + (cls ? gcount[c.z].x : 0) + prefix;
+    for (int i = lane; i < c.y; i += 32) far_id[dst + i] = pool[c.x + i];
+}
+__global__ void k_lsplit_from_counts(const int* far_off, const int2* gcount, int ng, int* lsplit) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) lsplit[g] = far_off[g] + gcount[g].x;
 }
 
 
@@ -711,15 +795,16 @@ __global__ void k_low32(const uint64_t* keys, int64_t n, int* out) {
 // Near leaves (sorted by group, then first point) -> merged ranges.
 // head[e] = 1 where entry e starts a range (first of its group, or not
 // contiguous with the previous leaf).
-__global__ void k_near_heads(const uint64_t* keys, const uint32_t* leaf, int64_t n,
+__global__ void k_near_heads(const uint64_t* keys, const uint32_t* leaf, int64_t n, int nsh,
                              const int* ncount, int* head) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
+    const uint64_t low = (uint64_t(1) << nsh) - 1;
     int h = 1;
-    if (e > 0 && (keys[e] >> 32) == (keys[e - 1] >> 32)) {
+    if (e > 0 && (keys[e] >> nsh) == (keys[e - 1] >> nsh)) {
         uint32_t prev = leaf[e - 1];
-        int prev_end = (int)(keys[e - 1] & 0xffffffffu) + ncount[prev];
-        if (prev_end == (int)(keys[e] & 0xffffffffu)) h = 0;
+        int prev_end = (int)(keys[e - 1] & low) + ncount[prev];
+        if (prev_end == (int)(keys[e] & low)) h = 0;
     }
     head[e] = h;
 }
@@ -727,12 +812,12 @@ __global__ void k_near_heads(const uint64_t* keys, const uint32_t* leaf, int64_t
 // hscan = exclusive scan of head over n+1 entries (head[n] = 1 sentinel).
 // Entry e belongs to range hscan[e+1]-1; it starts it if head[e], and ends
 // it if head[e+1].
-__global__ void k_near_ranges(const uint64_t* keys, const uint32_t* leaf, int64_t n,
+__global__ void k_near_ranges(const uint64_t* keys, const uint32_t* leaf, int64_t n, int nsh,
                               const int* ncount, const int* hscan, int2* rng) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     int r = hscan[e + 1] - 1;
-    int s = (int)(keys[e] & 0xffffffffu);
+    int s = (int)(keys[e] & ((uint64_t(1) << nsh) - 1));
     if (hscan[e + 1] != hscan[e]) rng[r].x = s;
     if (hscan[e + 2] - hscan[e + 1] == 1) rng[r].y = s + ncount[leaf[e]];
 }
@@ -894,24 +979,6 @@ __global__ void k_cluster_partition(const int* far_off, const int* lsplit, const
     if (lane == 0) csplit[g] = l0 + nstay;
 }
 
-// Far keys (group << 32 | local flag << 31 | node), sorted by group and flag:
-// node ids, and each group's first flagged entry (lsplit[g], initialised to
-// the end of the group's list by k_lsplit_init).
-__global__ void k_lsplit_init(const int* far_off, int ng, int* lsplit) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < ng) lsplit[g] = far_off[g + 1];
-}
-__global__ void k_far_ids(const uint64_t* keys, int64_t n, int* far_id, int* lsplit) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const uint64_t k = keys[e];
-    far_id[e] = (int)(uint32_t)(k & 0x7fffffffu);
-    if (lsplit && (k & 0x80000000u)) {
-        const bool first = e == 0 || (keys[e - 1] >> 32) != (k >> 32) || !(keys[e - 1] & 0x80000000u);
-        if (first) lsplit[(int)(k >> 32)] = (int)e;
-    }
-}
-
 // Group of every far entry (warp per group over its range).
 __global__ void k_entry_groups(const int* far_off, int ng, int* egrp) {
     const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -920,51 +987,44 @@ __global__ void k_entry_groups(const int* far_off, int ng, int* egrp) {
     for (int e = far_off[g] + lane; e < far_off[g + 1]; e += 32) egrp[e] = g;
 }
 
-// Transposed far lists: key (node << 32 | class << 30 | entry index), class 0
-// for an entry summed pair by pair, 1 for one expanded about its group (at or
-// after lsplit of its group), 2 for one expanded about its cluster (at or
-// after csplit; only the first member's copy: the other members' copies get
-// node = nnodes and sort past every node).  egrp null: all class 0.
-__global__ void k_tfar_keys(const int* far_id, int64_t nent, const int* egrp, const int* lsplit, const int* csplit,
-                            int K, int nnodes, uint64_t* keys) {
+// Transposed far lists: key (node << 32 | entry index).  With local
+// expansions, an entry expanded about a cluster is kept only in the first
+// member's copy: the other members' copies get node = nnodes and sort past
+// every node.
+__global__ void k_tfar_keys(const int* far_id, int64_t nent, const int* egrp, const int* csplit, int K, int nnodes,
+                            uint64_t* keys) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nent) return;
-    uint32_t cls = 0, node = (uint32_t)far_id[e];
-    if (egrp) {
+    uint32_t node = (uint32_t)far_id[e];
+    if (csplit) {
         const int g = egrp[e];
-        if (csplit && e >= csplit[g]) {
-            cls = 2;
-            if (g % K != 0) node = (uint32_t)nnodes;
-        } else if (e >= lsplit[g]) {
-            cls = 1;
-        }
+        if (e >= csplit[g] && g % K != 0) node = (uint32_t)nnodes;
     }
-    keys[e] = ((uint64_t)node << 32) | ((uint64_t)cls << 30) | (uint32_t)e;
+    keys[e] = ((uint64_t)node << 32) | (uint32_t)e;
 }
 
-// Sorted transposed keys -> per node its entries summed pair by pair (their
-// entry index), then from tlsplit[node] on those expanded about a group (their
-// group), then from tcsplit[node] on those expanded about a cluster (their
-// cluster).  Both splits start at the end of the node's list.
-__global__ void k_tfar_ids(const uint64_t* keys, int64_t n, const int* egrp, int K, int nnodes, int* tfar_ent,
-                           int* tlsplit, int* tcsplit) {
+// Sorted transposed keys -> tfar_ent.  Without local expansions: the entry
+// index.  With them (egrp set): class << 30 | id, class 0 for an entry summed
+// pair by pair (id = the entry), 1 for one expanded about its group (before
+// csplit, from lsplit on; id = the group), 2 for one expanded about its
+// cluster (id = the cluster).
+__global__ void k_tfar_ids(const uint64_t* keys, int64_t n, const int* egrp, const int* lsplit, const int* csplit,
+                           int K, int nnodes, int* tfar_ent) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const uint64_t k = keys[q];
-    const int node = (int)(k >> 32);
-    if (node >= nnodes) return;
-    const int e = (int)(uint32_t)(k & 0x3fffffffu);
-    const int cls = (int)((k >> 30) & 3u);
-    tfar_ent[q] = cls == 0 ? e : (cls == 1 ? egrp[e] : egrp[e] / K);
-    const bool first = q == 0 || (int)(keys[q - 1] >> 32) != node;
-    const int pcls = first ? -1 : (int)((keys[q - 1] >> 30) & 3u);
-    if (cls >= 1 && pcls < 1) tlsplit[node] = (int)q;
-    if (cls == 2 && pcls < 2 && tcsplit) tcsplit[node] = (int)q;
+    if ((int)(k >> 32) >= nnodes) return;
+    const int e = (int)(uint32_t)(k & 0xffffffffu);
+    if (!egrp) {
+        tfar_ent[q] = e;
+        return;
+    }
+    const int g = egrp[e];
+    if (csplit && e >= csplit[g]) tfar_ent[q] = (2 << 30) | (g / K);
+    else if (e >= lsplit[g]) tfar_ent[q] = (1 << 30) | g;
+    else tfar_ent[q] = e;
 }
 
-// Transposed near entries: for each near range of target group g, the source
-// chunks (kAdjChunk consecutive sorted points) it overlaps, with the mask of
-// the overlapped points.
 __global__ void k_tnear_count(const int2* rng, int64_t nr, int* cnt) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nr) return;
@@ -1240,45 +1300,60 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
 }
 
 // Far lists of the groups that a first-in first-out walk finished as stack
-// walks: their keys are sorted by node within each segment.  The segments are
-// copied one after another with compact keys (k << nbits | node), k the
-// group's place in `groups`, sorted, and written back into their own places.
-__global__ void k_seg_sizes(const uint64_t* groups, int nu, const int* far_off, int* sz) {
+// walks (or of every group after stack walks throughout): each class part of
+// such a list is sorted by node.  The parts are copied one after another with
+// compact keys (k << nbits | node), k = 2 x the group's place in `groups` +
+// the class, sorted, and written back into their own places.
+__device__ __forceinline__ void far_part(const int* far_off, const int* lsplit, int g, int cls, int& e0, int& e1) {
+    const int mid = lsplit ? lsplit[g] : far_off[g + 1];
+    e0 = cls ? mid : far_off[g];
+    e1 = cls ? far_off[g + 1] : mid;
+}
+__global__ void k_seg_sizes(const uint64_t* groups, int nu, const int* far_off, const int* lsplit, int* sz) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nu) return;
-    const int g = (int)groups[k];
-    sz[k] = far_off[g + 1] - far_off[g];
+    if (k >= 2 * nu) return;
+    int e0, e1;
+    far_part(far_off, lsplit, (int)groups[k >> 1], k & 1, e0, e1);
+    sz[k] = e1 - e0;
 }
-__global__ void k_seg_pack(const uint64_t* keys, const uint64_t* groups, const int* far_off, const int* pos,
-                           int nbits, uint64_t* tmp) {
-    const int k = blockIdx.x, g = (int)groups[k];
-    const int e0 = far_off[g], cnt = far_off[g + 1] - e0, p0 = pos[k];
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
-        tmp[p0 + i] = ((uint64_t)k << nbits) | (keys[e0 + i] & 0xffffffffu);
+__global__ void k_seg_pack(const int* far_id, const uint64_t* groups, const int* far_off, const int* lsplit,
+                           const int* pos, int nbits, uint64_t* tmp) {
+    const int k = blockIdx.x;
+    int e0, e1;
+    far_part(far_off, lsplit, (int)groups[k >> 1], k & 1, e0, e1);
+    const int p0 = pos[k];
+    for (int i = threadIdx.x; i < e1 - e0; i += blockDim.x)
+        tmp[p0 + i] = ((uint64_t)k << nbits) | (uint32_t)far_id[e0 + i];
 }
-__global__ void k_seg_unpack(const uint64_t* tmp, const uint64_t* groups, const int* far_off, const int* pos,
-                             int nbits, uint64_t* keys) {
-    const int k = blockIdx.x, g = (int)groups[k];
-    const int e0 = far_off[g], cnt = far_off[g + 1] - e0, p0 = pos[k];
+__global__ void k_seg_unpack(const uint64_t* tmp, const uint64_t* groups, const int* far_off, const int* lsplit,
+                             const int* pos, int nbits, int* far_id) {
+    const int k = blockIdx.x;
+    int e0, e1;
+    far_part(far_off, lsplit, (int)groups[k >> 1], k & 1, e0, e1);
+    const int p0 = pos[k];
     const uint64_t low = (uint64_t(1) << nbits) - 1;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
-        keys[e0 + i] = ((uint64_t)g << 32) | (tmp[p0 + i] & low);
+    for (int i = threadIdx.x; i < e1 - e0; i += blockDim.x) far_id[e0 + i] = (int)(tmp[p0 + i] & low);
+}
+__global__ void k_iota_u64(uint64_t* p, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (uint64_t)i;
 }
 
-static void sort_far_segments(uint64_t* keys, const int* far_off, const uint64_t* groups, int nu, int nbits,
-                              cudaStream_t s) {
-    int* sz = dalloc<int>(nu + 1);
-    int* pos = dalloc<int>(nu + 2);
-    k_seg_sizes<<<ceil_div(nu, kTB), kTB, 0, s>>>(groups, nu, far_off, sz);
+static void sort_far_segments(int* far_id, const int* far_off, const int* lsplit, const uint64_t* groups, int nu,
+                              int nbits, cudaStream_t s) {
+    const int nseg = 2 * nu;
+    int* sz = dalloc<int>(nseg + 1);
+    int* pos = dalloc<int>(nseg + 2);
+    k_seg_sizes<<<ceil_div(nseg, kTB), kTB, 0, s>>>(groups, nu, far_off, lsplit, sz);
     WNNC_LAUNCH_CHECK();
-    exclusive_scan_i32(sz, pos, nu, s);
-    const int total = read_int(pos + nu, s);
+    exclusive_scan_i32(sz, pos, nseg, s);
+    const int total = read_int(pos + nseg, s);
     if (total > 0) {
         uint64_t* tmp = dalloc<uint64_t>(total);
-        k_seg_pack<<<nu, 256, 0, s>>>(keys, groups, far_off, pos, nbits, tmp);
+        k_seg_pack<<<nseg, 256, 0, s>>>(far_id, groups, far_off, lsplit, pos, nbits, tmp);
         WNNC_LAUNCH_CHECK();
-        radix_sort_pairs(tmp, nullptr, total, nbits + bits_for(nu), s);
-        k_seg_unpack<<<nu, 256, 0, s>>>(tmp, groups, far_off, pos, nbits, keys);
+        radix_sort_pairs(tmp, nullptr, total, nbits + bits_for(nseg), s);
+        k_seg_unpack<<<nseg, 256, 0, s>>>(tmp, groups, far_off, lsplit, pos, nbits, far_id);
         WNNC_LAUNCH_CHECK();
         pool_free(tmp);
     }
@@ -1396,84 +1471,118 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         int* leaf_off = dalloc<int>(ng + 1);
         int* err = dalloc<int>(2);        // [0] error flags, [1] groups finished as stack walks
         uint64_t* unsorted = dalloc<uint64_t>(ng);
-        unsigned long long* counts = dalloc<unsigned long long>(2);
+        unsigned long long* counts = dalloc<unsigned long long>(3);   // far ids, chunks, near entries
+        int2* gcount = dalloc<int2>(ng);
         const int tgrid = ceil_div(ng, kTravWarps);
+        const int nsh = bits_for(t.n);    // near keys: group << nsh | first point
         // pool estimates (per target); a second pass runs with exact sizes if exceeded
-        int64_t far_cap = 48 * m + 4096, near_cap = 8 * m + 4096;
-        uint64_t* fkeys = nullptr;
+        int64_t far_cap = std::min<int64_t>(48 * m + 4096, INT32_MAX), near_cap = 8 * m + 4096;
+        int* fpool = nullptr;
+        int4* chunks = nullptr;
         uint64_t* nkeys = nullptr;
         uint32_t* nvals = nullptr;
-        int64_t nfar = 0, nleafent = 0;
-        // first the first-in first-out walk (far keys come out sorted within
-        // each group, except the groups it lists as unsorted); if a stack walk
-        // overflows its buffer, everything again as stack walks with the
-        // larger buffer, whose far keys take the full sort
+        int64_t nfar = 0, nchunk = 0, nleafent = 0;
+        // first the first-in first-out walk (far ids come out ascending within
+        // each group, except in the groups it lists as unsorted); if a stack
+        // walk overflows its buffer, everything again as stack walks with the
+        // larger buffer, whose far lists are all sorted afterwards
         int nunsorted = 0;
         bool big_stack = false;
         for (int attempt = 0; attempt < 4; ++attempt) {
-            fkeys = dalloc<uint64_t>(far_cap);
+            // a flush other than a class's last holds > kTravBuf - 32 entries
+            const int64_t chunk_cap = far_cap / (kTravBuf - 31) + 2 * (int64_t)ng + 64;
+            fpool = dalloc<int>(far_cap);
+            chunks = dalloc<int4>(chunk_cap);
             nkeys = dalloc<uint64_t>(near_cap);
             nvals = dalloc<uint32_t>(near_cap);
             WNNC_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
-            WNNC_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
+            WNNC_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s));
+            TravOut o;
+            o.far_pool = fpool;
+            o.far_cap = far_cap;
+            o.far_count = counts;
+            o.chunks = chunks;
+            o.chunk_cap = chunk_cap;
+            o.chunk_count = counts + 1;
+            o.gcount = gcount;
+            o.near_pool = nkeys;
+            o.near_vpool = nvals;
+            o.near_cap = near_cap;
+            o.near_count = counts + 2;
+            o.nsh = nsh;
+            o.err = err;
+            o.unsorted = unsorted;
+            o.unsorted_count = err + 1;
 #define WNNC_TRAVERSE(STK, FIFO)                                                                               \
     k_traverse<STK, FIFO><<<tgrid, 32 * kTravWarps, 0, s>>>(t.node_lo, t.node_hi, t.node_lof, t.node_hif,           \
                                                       t.node_depth, t.node_nchild, t.node_child0,            \
-                                                      t.node_start, ts.glo, ts.ghi, ng, theta, clocal, fkeys,\
-                                                      far_cap, counts, nkeys, nvals, near_cap, counts + 1,  \
-                                                      err, unsorted, err + 1)
+                                                      t.node_start, ts.glo, ts.ghi, ng, theta, clocal, o)
             if (big_stack) WNNC_TRAVERSE(kStackBig, false); else WNNC_TRAVERSE(kStackSmall, true);
 #undef WNNC_TRAVERSE
             WNNC_LAUNCH_CHECK();
-            unsigned long long hc[2] = {0, 0};
+            unsigned long long hc[3] = {0, 0, 0};
             int herr[2] = {0, 0};
             WNNC_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
             WNNC_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
             WNNC_CUDA(cudaStreamSynchronize(s));
             nunsorted = herr[1];
             if (herr[0]) {
-                pool_free(fkeys); pool_free(nkeys); pool_free(nvals);
+                pool_free(fpool); pool_free(chunks); pool_free(nkeys); pool_free(nvals);
                 if (!big_stack) {   // again with the larger stack
                     big_stack = true;
                     continue;
                 }
-                pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts); pool_free(near_off0);
+                pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts); pool_free(gcount);
+                pool_free(near_off0);
                 fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
             }
             nfar = (int64_t)hc[0];
-            nleafent = (int64_t)hc[1];
-            if (nfar <= far_cap && nleafent <= near_cap) break;
+            nchunk = (int64_t)hc[1];
+            nleafent = (int64_t)hc[2];
+            if (nfar <= far_cap && nchunk <= chunk_cap && nleafent <= near_cap) break;
+            pool_free(fpool); pool_free(chunks); pool_free(nkeys); pool_free(nvals);
             if (attempt == 3 || nfar > INT32_MAX || nleafent > INT32_MAX) {
-                pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(leaf_off); pool_free(err);
-                pool_free(unsorted); pool_free(counts); pool_free(near_off0);
+                pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts); pool_free(gcount);
+                pool_free(near_off0);
                 fail(WNNC_ECAPACITY, "interaction lists too long");
             }
-            pool_free(fkeys); pool_free(nkeys); pool_free(nvals);
             far_cap = std::max<int64_t>(nfar, 1);
             near_cap = std::max<int64_t>(nleafent, 1);
         }
-        int gbits = bits_for(ng);
-        // by group (and, with local expansions, by the flag in bit 31 next):
-        // the first-in first-out walk wrote each group's nodes ascending
-        radix_sort_pairs(fkeys, nullptr, nfar, 32 + gbits, s, big_stack ? 0 : (local ? 31 : 32));
-        radix_sort_pairs(nkeys, nvals, nleafent, 32 + gbits, s);
-        segment_offsets_hi32(fkeys, nfar, ts.far_off, ng, s);
-        if (!big_stack && nunsorted > 0)
-            sort_far_segments(fkeys, ts.far_off, unsorted, nunsorted, local ? 32 : bits_for(t.nnodes), s);
-        ts.walk_stack_groups = big_stack ? 0 : nunsorted;
-        ts.walk_big_stack = big_stack ? 1 : 0;
-        segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s);
+        const int gbits = bits_for(ng);
+        // far lists: offsets from the per-group counts, chunks to their places
+        {
+            int* tot = dalloc<int>(ng + 1);
+            k_gcount_tot<<<ceil_div(ng, kTB), kTB, 0, s>>>(gcount, ng, tot);
+            WNNC_LAUNCH_CHECK();
+            exclusive_scan_i32(tot, ts.far_off, ng, s);
+            wait_before_free(s);
+            pool_free(tot);
+        }
         ts.far_entries = nfar;
-        ts.far_id = dalloc<int>(nfar);
+        ts.far_id = dalloc<int>(std::max<int64_t>(nfar, 1));
+        if (nchunk) {
+            k_far_place<<<ceil_div(nchunk * 32, kTB), kTB, 0, s>>>(chunks, nchunk, fpool, ts.far_off, gcount,
+                                                                  ts.far_id);
+            WNNC_LAUNCH_CHECK();
+        }
         if (local) {
             ts.far_lsplit = dalloc<int>(ng);
-            k_lsplit_init<<<ceil_div(ng, kTB), kTB, 0, s>>>(ts.far_off, ng, ts.far_lsplit);
+            k_lsplit_from_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ts.far_off, gcount, ng, ts.far_lsplit);
             WNNC_LAUNCH_CHECK();
         }
-        if (nfar) {
-            k_far_ids<<<ceil_div(nfar, kTB), kTB, 0, s>>>(fkeys, nfar, ts.far_id, ts.far_lsplit);
+        if (big_stack) {
+            k_iota_u64<<<ceil_div(ng, kTB), kTB, 0, s>>>(unsorted, ng);
             WNNC_LAUNCH_CHECK();
+            nunsorted = ng;
         }
+        if (nunsorted > 0 && nfar > 0)
+            sort_far_segments(ts.far_id, ts.far_off, ts.far_lsplit, unsorted, nunsorted, bits_for(t.nnodes), s);
+        ts.walk_stack_groups = big_stack ? 0 : nunsorted;
+        ts.walk_big_stack = big_stack ? 1 : 0;
+        // near leaves by (group, first point)
+        radix_sort_pairs(nkeys, nvals, nleafent, nsh + gbits, s);
+        segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s, nsh);
         if (K) {
             // entries expanded about their cluster: flagged, then each group's expanded
             // part reordered into [group | cluster] (csplit)
@@ -1496,7 +1605,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         int* head = dalloc<int>(nleafent + 2);
         int* hscan = dalloc<int>(nleafent + 2);
         if (nleafent) {
-            k_near_heads<<<ceil_div(nleafent, kTB), kTB, 0, s>>>(nkeys, nvals, nleafent, t.node_count, head);
+            k_near_heads<<<ceil_div(nleafent, kTB), kTB, 0, s>>>(nkeys, nvals, nleafent, nsh, t.node_count, head);
             WNNC_LAUNCH_CHECK();
         }
         // sentinel head[n] = 1 so that the last entry closes its range
@@ -1506,16 +1615,16 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         nr0 = read_int(hscan + nleafent, s);   // heads among the real entries
         rng0 = dalloc<int2>(nr0);
         if (nleafent) {
-            k_near_ranges<<<ceil_div(nleafent, kTB), kTB, 0, s>>>(nkeys, nvals, nleafent, t.node_count, hscan,
-                                                                 rng0);
+            k_near_ranges<<<ceil_div(nleafent, kTB), kTB, 0, s>>>(nkeys, nvals, nleafent, nsh, t.node_count,
+                                                                 hscan, rng0);
             WNNC_LAUNCH_CHECK();
         }
         // range offsets per group = number of heads before the group's first leaf entry
         k_gather_i32<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(hscan, leaf_off, ng + 1, near_off0);
         WNNC_LAUNCH_CHECK();
         wait_before_free(s);
-        pool_free(fkeys); pool_free(nkeys); pool_free(nvals); pool_free(head); pool_free(hscan);
-        pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts);
+        pool_free(fpool); pool_free(chunks); pool_free(nkeys); pool_free(nvals); pool_free(head); pool_free(hscan);
+        pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts); pool_free(gcount);
     }
     // cut ranges to at most kMaxRange points
     {
@@ -1751,27 +1860,17 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             WNNC_LAUNCH_CHECK();
         }
         if (ne) {
-            k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, egrp, S.far_lsplit, S.far_csplit,
-                                                          S.cluster_k, t.nnodes, k);
+            k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, egrp, S.far_csplit, S.cluster_k, t.nnodes,
+                                                          k);
             WNNC_LAUNCH_CHECK();
         }
-        // entry indices already ascending; the class bits sort too
-        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes + 1), s, local ? 30 : 32);
+        // entry indices already ascending: the node bits only
+        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes + 1), s, 32);
         t.tfar_ent = dalloc<int>(ne);
         segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
-        if (local) {
-            t.tfar_lsplit = dalloc<int>(t.nnodes);
-            k_lsplit_init<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.tfar_off, t.nnodes, t.tfar_lsplit);
-            WNNC_LAUNCH_CHECK();
-            if (S.far_csplit) {
-                t.tfar_csplit = dalloc<int>(t.nnodes);
-                k_lsplit_init<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.tfar_off, t.nnodes, t.tfar_csplit);
-                WNNC_LAUNCH_CHECK();
-            }
-        }
         if (ne) {
-            k_tfar_ids<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, egrp, S.cluster_k, t.nnodes, t.tfar_ent,
-                                                         t.tfar_lsplit, t.tfar_csplit);
+            k_tfar_ids<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, egrp, S.far_lsplit, S.far_csplit, S.cluster_k,
+                                                         t.nnodes, t.tfar_ent);
             WNNC_LAUNCH_CHECK();
         }
         wait_before_free(s);
@@ -1855,7 +1954,7 @@ void free_tree(Tree& t) {
     dfree(t.mom_r); dfree(t.mom_x); dfree(t.dmom); dfree(t.mom_mid); dfree(t.mom_top); dfree(t.mom_top_rng); dfree(t.mom_front); dfree(t.node_rep); dfree(t.contrib);
     dfree(t.near_contrib); dfree(t.vnode); dfree(t.red_ticket);
     dfree(t.mom_dip); dfree(t.mom_dip_r); dfree(t.dip_corr); dfree(t.contrib_h0); dfree(t.contrib_h1);
-    dfree(t.node_abs); dfree(t.local_rec); dfree(t.tfar_lsplit); dfree(t.gadj); dfree(t.tfar_csplit);
+    dfree(t.node_abs); dfree(t.local_rec); dfree(t.gadj);
     dfree(t.gather_raw);
     dfree(t.cadj);
     dfree(t.hnode0); dfree(t.hnode1);
