@@ -59,7 +59,7 @@ typedef enum {
     WNNC_ECUDA = 3,       /* a CUDA runtime call failed */
     WNNC_ENONFINITE = 4,  /* the iteration produced a non-finite step length */
     WNNC_ECAPACITY = 5,   /* a traversal stack or list capacity was exceeded */
-    WNNC_ETIMEOUT = 6     /* reserved: a bounded device wait gave up */
+    WNNC_ETIMEOUT = 6     /* a bounded device wait gave up (single-pass scans and sorts of a build) */
 } wnnc_status;
 
 /* Tree parameters (Sec. 5.1.1 defaults: D = 15, c = 2 i.e. theta = 0.5). */

@@ -259,7 +259,10 @@ wnnc_status wnnc_build_tree(const float* pts, int64_t n, const wnnc_tree_params*
         AllocStream as(s);
         build_tree(*t, pts, s);
         alloc_workspace(*t);
+        unsigned timeouts = 0;
+        wait_timeouts_async(&timeouts, s);
         WNNC_CUDA(cudaStreamSynchronize(s));
+        check_wait_timeouts(timeouts, s);
     });
     if (st != WNNC_OK) {
         if (t) {

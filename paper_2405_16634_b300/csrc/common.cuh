@@ -124,7 +124,6 @@ struct WorkList {
     int* gsplit = nullptr;      // per group: its record in splits, or -1 (lists with partial sums)
     int nsplit = 0;
     int nslots = 0;
-    int cap = 0;                // the item cap of this list (lane-slots)
 };
 void free_work(WorkList& w);
 
@@ -320,6 +319,12 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
 // bits (e.g. an index appended in ascending order), stability makes the result
 // the same as a sort on all the low `bits` bits.
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s, int lo_bit = 0);
+// Single-pass scans and sorts count a bounded wait that gave up in a device
+// word: wait_timeouts_async queues its copy into *host (read it after a
+// synchronisation of s); check_wait_timeouts clears it and fails with
+// WNNC_ETIMEOUT when the value read is non-zero.
+void wait_timeouts_async(unsigned* host, cudaStream_t s);
+void check_wait_timeouts(unsigned seen, cudaStream_t s);
 // off[g] = first index i with (keys[i] >> shift) >= g, for g in [0, ng]; keys sorted.
 void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s, int shift = 32);
 

@@ -2729,10 +2729,13 @@ void eval_at(Tree& t, const float* mu, const float* q, int64_t m, float w, int g
     }
     if (grad) launch_gather<kOpG, kEpiStoreGrad>(t, a, s);
     else launch_gather<kOpA, kEpiStoreW>(t, a, s);
+    unsigned timeouts = 0;
+    wait_timeouts_async(&timeouts, s);
     WNNC_CUDA(cudaStreamSynchronize(s));
     pool_free(qcorr);
     pool_free(pacc);
     free_target_set(Q);
+    check_wait_timeouts(timeouts, s);
 }
 
 // Smoothing width of iteration `it` (Sec. 4.4): from w2 at the first

@@ -1094,82 +1094,113 @@ __global__ void k_tnear_merge(const uint64_t* keys, const uint32_t* idx, const u
 //           a quarter of a target group per lane)
 //   mode 2: far entries only (adjoint far)
 // ---------------------------------------------------------------------------
-struct ItemWalk {
-    int g, q0, f0, cost, k;
-    Item* out;
-    int base, pslot_base, nparts, split;
-    bool partials;
-    __device__ void emit(int q1, int f1) {
-        if (out) {
+// Work items of segment g: its units in order (near ranges, then the
+// pair-by-pair far entries in chunks of 32), cut greedily: a unit that would
+// take a non-empty item past the cap starts a new item.  One warp per
+// segment: the lanes take 32 consecutive units at a time, an inclusive prefix
+// sum of their costs gives each unit's cost within the current item, and the
+// cuts follow one at a time by ballot (the first unit past the cap after the
+// last cut), so the items are those of the walk unit by unit.  Far entries
+// expanded about the group centre (from lsplit[g] on) are not in the items:
+// the local-expansion kernels take them.  Returns the number of items; with
+// out set, lane 0 writes them.
+__device__ int walk_items(int mode, int g, const int* near_off, const int2* rng, const int* far_off,
+                          const int* lsplit, int cap, Item* out, int base, int pslot_base, int nparts, int split,
+                          bool partials, int lane) {
+    const int qb = near_off ? near_off[g] : 0, qe = near_off ? near_off[g + 1] : 0;
+    const int fb = far_off ? far_off[g] : 0;
+    const int fe = far_off ? (lsplit ? min(max(lsplit[g], fb), far_off[g + 1]) : far_off[g + 1]) : 0;
+    const int nq = qe - qb, nu = nq + (fe - fb + 31) / 32;
+    // unit u starts at near range q_at(u) and far entry f_at(u)
+    auto q_at = [&](int u) { return u < nq ? qb + u : qe; };
+    auto f_at = [&](int u) { return u < nq ? fb : fb + 32 * (u - nq); };
+    int k = 0, u_start = 0, carry = 0;    // items so far; the current item's first unit and cost before the batch
+    auto emit = [&](int u_end, int cost) {
+        if (out && lane == 0) {
             Item it;
-            it.g = g; it.q0 = q0; it.q1 = q1; it.f0 = f0; it.f1 = f1;
+            it.g = g;
+            it.q0 = q_at(u_start);
+            it.q1 = u_end < nu ? q_at(u_end) : qe;
+            it.f0 = f_at(u_start);
+            it.f1 = u_end < nu ? f_at(u_end) : fe;
             it.pslot = (partials && nparts > 1) ? pslot_base + k : -1;
             it.cost = cost;
             it.split = it.pslot >= 0 ? split : -1;
             out[base + k] = it;
         }
         ++k;
-        q0 = q1;
-        f0 = f1;
-        cost = 0;
+        u_start = u_end;
+    };
+    for (int u0 = 0; u0 < nu; u0 += 32) {
+        const int u = u0 + lane;
+        int c = 0;
+        if (u < nu) c = u < nq ? (mode == 1 ? 8 : rng[qb + u].y - rng[qb + u].x) : min(32, fe - f_at(u));
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = incl - c;
+        int s = 0, ex_s = 0;      // first pending lane of the batch and its exclusive prefix
+        for (;;) {
+            const int cur = carry + excl - ex_s;      // the item's cost before this unit
+            const unsigned cut = __ballot_sync(0xffffffffu, u < nu && lane >= s && cur > 0 && cur + c > cap);
+            if (!cut) break;
+            const int j = __ffs(cut) - 1;
+            emit(u0 + j, __shfl_sync(0xffffffffu, cur, j));
+            ex_s = __shfl_sync(0xffffffffu, excl, j);
+            s = j;
+            carry = 0;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        carry += tot - ex_s;
     }
-};
-
-// Far entries expanded about the group centre (from lsplit[g] on) are not in
-// the items: the local-expansion kernels take them.
-__device__ int walk_items(int mode, int g, const int* near_off, const int2* rng, const int* far_off,
-                          const int* lsplit, int cap, Item* out, int base, int pslot_base, int nparts, int split,
-                          bool partials) {
-    const int qb = near_off ? near_off[g] : 0, qe = near_off ? near_off[g + 1] : 0;
-    const int fb = far_off ? far_off[g] : 0;
-    const int fe = far_off ? (lsplit ? min(max(lsplit[g], fb), far_off[g + 1]) : far_off[g + 1]) : 0;
-    ItemWalk w{g, qb, fb, 0, 0, out, base, pslot_base, nparts, split, partials};
-    for (int q = qb; q < qe; ++q) {
-        int c = mode == 1 ? 8 : rng[q].y - rng[q].x;
-        if (w.cost > 0 && w.cost + c > cap) w.emit(q, fb);
-        w.cost += c;
-    }
-    for (int e = fb; e < fe; e += 32) {
-        int c = min(32, fe - e);
-        if (w.cost > 0 && w.cost + c > cap) w.emit(qe, e);
-        w.cost += c;
-    }
-    if (w.cost > 0 || w.k == 0) w.emit(qe, fe);
-    return w.k;
+    if (carry > 0 || k == 0) emit(nu, carry);
+    return k;
 }
 
-// Total cost of segment g (its walk without a cap).
+// Total cost of segment g (its walk without a cap); one warp per segment.
 __global__ void k_seg_cost(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
                            const int* lsplit, int64_t* cost) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (g >= nseg) return;
     int64_t c = 0;
     if (near_off)
-        for (int q = near_off[g]; q < near_off[g + 1]; ++q) c += mode == 1 ? 8 : rng[q].y - rng[q].x;
-    if (far_off) {
-        const int fb = far_off[g];
-        c += (lsplit ? min(max(lsplit[g], fb), far_off[g + 1]) : far_off[g + 1]) - fb;
+        for (int q = near_off[g] + lane; q < near_off[g + 1]; q += 32) c += mode == 1 ? 8 : rng[q].y - rng[q].x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+        if (far_off) {
+            const int fb = far_off[g];
+            c += (lsplit ? min(max(lsplit[g], fb), far_off[g + 1]) : far_off[g + 1]) - fb;
+        }
+        cost[g] = c;
     }
-    cost[g] = c;
 }
 
 __global__ void k_items_count(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
-                              const int* lsplit, int cap, int* cnt, int* slots) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
+                              const int* lsplit, const int* capp, int* cnt, int* slots) {
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (g >= nseg) return;
-    int c = walk_items(mode, g, near_off, rng, far_off, lsplit, cap, nullptr, 0, 0, 0, -1, false);
-    cnt[g] = c;
-    slots[g] = c > 1 ? c : 0;
+    const int c = walk_items(mode, g, near_off, rng, far_off, lsplit, *capp, nullptr, 0, 0, 0, -1, false, lane);
+    if (lane == 0) {
+        cnt[g] = c;
+        slots[g] = c > 1 ? c : 0;
+    }
 }
 
 __global__ void k_items_fill(int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
-                             const int* lsplit, int cap, const int* cnt, const int* item_off, const int* slot_off,
-                             bool partials, Item* items, int4* splits, const int* split_off) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
+                             const int* lsplit, const int* capp, const int* cnt, const int* item_off,
+                             const int* slot_off, bool partials, Item* items, int4* splits, const int* split_off) {
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (g >= nseg) return;
-    walk_items(mode, g, near_off, rng, far_off, lsplit, cap, items, item_off[g], slot_off[g], cnt[g],
-               (partials && cnt[g] > 1) ? split_off[g] : -1, partials);
-    if (partials && cnt[g] > 1) splits[split_off[g]] = make_int4(g, slot_off[g], cnt[g], 0);
+    walk_items(mode, g, near_off, rng, far_off, lsplit, *capp, items, item_off[g], slot_off[g], cnt[g],
+               (partials && cnt[g] > 1) ? split_off[g] : -1, partials, lane);
+    if (lane == 0 && partials && cnt[g] > 1) splits[split_off[g]] = make_int4(g, slot_off[g], cnt[g], 0);
 }
 
 __global__ void k_group_splits(const int* cnt, const int* split_off, int nseg, int* gsplit) {
@@ -1210,11 +1241,27 @@ static void wait_before_free(cudaStream_t s) {
     if (alloc_stream() != s) WNNC_CUDA(cudaStreamSynchronize(s));
 }
 
+// Page-locked host memory for the build's read-backs (one block per host
+// thread, kept for the thread's life): copies into it are asynchronous, so
+// several can share one synchronisation.
+struct PinnedScratch {
+    void* p = nullptr;
+    ~PinnedScratch() {
+        if (p) cudaFreeHost(p);
+    }
+};
+constexpr size_t kPinnedBytes = 4096;
+static char* pinned_scratch() {
+    thread_local PinnedScratch ps;
+    if (!ps.p) WNNC_CUDA(cudaMallocHost(&ps.p, kPinnedBytes));
+    return static_cast<char*>(ps.p);
+}
+
 static int read_int(const int* dptr, cudaStream_t s) {
-    int v = 0;
-    WNNC_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int* h = reinterpret_cast<int*>(pinned_scratch());
+    WNNC_CUDA(cudaMemcpyAsync(h, dptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     WNNC_CUDA(cudaStreamSynchronize(s));
-    return v;
+    return *h;
 }
 
 static int bits_for(int64_t v) {
@@ -1231,61 +1278,85 @@ void free_work(WorkList& w) {
     w.nitems = w.nsplit = w.nslots = 0;
 }
 
-// Build the work list of nseg segments (see walk_items), heaviest item first.
-static void build_work(WorkList& w, int mode, int nseg, const int* near_off, const int2* rng,
-                       const int* far_off, const int* lsplit, bool partials, cudaStream_t s) {
-    int* cnt = dalloc<int>(nseg + 1);
-    int* slots = dalloc<int>(nseg + 1);
-    int* item_off = dalloc<int>(nseg + 2);
-    int* slot_off = dalloc<int>(nseg + 2);
-    int* flag = dalloc<int>(nseg + 1);
-    int* split_off = dalloc<int>(nseg + 2);
-    // the item cap from the total cost of all segments
+// The item cap of a work list from the total cost of its segments: about
+// total / kItemsTarget, a power of two within [kItemCostMin, kItemCostMax].
+__global__ void k_item_cap(const int64_t* total, int* cap) {
+    int c = kItemCostMin;
+    while (c < kItemCostMax && (int64_t)c * 2 * kItemsTarget <= *total) c *= 2;
+    *cap = c;
+}
+
+// A work list of nseg segments (see walk_items), heaviest item first, built
+// in two phases so that several lists share one read-back of their sizes:
+// work_count queues the cap, the per-segment item counts and their scans, and
+// leaves the list's three totals (items, partial slots, cut groups) in tot;
+// work_fill, given those totals on the host, allocates and fills the list.
+struct WorkBuild {
+    int mode = 0, nseg = 0;
+    const int* near_off = nullptr;
+    const int2* rng = nullptr;
+    const int* far_off = nullptr;
+    const int* lsplit = nullptr;
+    bool partials = false;
+    int *cnt = nullptr, *slots = nullptr, *item_off = nullptr, *slot_off = nullptr, *flag = nullptr,
+        *split_off = nullptr, *cap = nullptr, *tot = nullptr;
+};
+
+static void work_count(WorkBuild& b, int mode, int nseg, const int* near_off, const int2* rng, const int* far_off,
+                       const int* lsplit, bool partials, cudaStream_t s) {
+    b.mode = mode;
+    b.nseg = nseg;
+    b.near_off = near_off;
+    b.rng = rng;
+    b.far_off = far_off;
+    b.lsplit = lsplit;
+    b.partials = partials;
+    b.cnt = dalloc<int>(nseg + 1);
+    b.slots = dalloc<int>(nseg + 1);
+    b.item_off = dalloc<int>(nseg + 2);
+    b.slot_off = dalloc<int>(nseg + 2);
+    b.flag = dalloc<int>(nseg + 1);
+    b.split_off = dalloc<int>(nseg + 2);
+    b.cap = dalloc<int>(1);
+    b.tot = dalloc<int>(3);
     int64_t* seg_cost = dalloc<int64_t>(nseg + 1);
     int64_t* cost_scan = dalloc<int64_t>(nseg + 2);
-    k_seg_cost<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit, seg_cost);
+    k_seg_cost<<<ceil_div((int64_t)nseg * 32, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit, seg_cost);
     WNNC_LAUNCH_CHECK();
     exclusive_scan_i64(seg_cost, cost_scan, nseg, s);
-    int64_t total = 0;
-    WNNC_CUDA(cudaMemcpyAsync(&total, cost_scan + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    WNNC_CUDA(cudaStreamSynchronize(s));
+    k_item_cap<<<1, 1, 0, s>>>(cost_scan + nseg, b.cap);
+    WNNC_LAUNCH_CHECK();
+    k_items_count<<<ceil_div((int64_t)nseg * 32, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit,
+                                                                   b.cap, b.cnt, b.slots);
+    WNNC_LAUNCH_CHECK();
+    exclusive_scan_i32(b.cnt, b.item_off, nseg, s);
+    exclusive_scan_i32(b.slots, b.slot_off, nseg, s);
+    k_split_flags<<<ceil_div(nseg, kTB), kTB, 0, s>>>(b.cnt, nseg, b.flag);
+    WNNC_LAUNCH_CHECK();
+    exclusive_scan_i32(b.flag, b.split_off, nseg, s);
+    k_gather_tot3<<<1, 32, 0, s>>>(b.item_off + nseg, b.slot_off + nseg, b.split_off + nseg, b.tot);
+    WNNC_LAUNCH_CHECK();
     pool_free(seg_cost);
     pool_free(cost_scan);
-    int cap = kItemCostMin;
-    while (cap < kItemCostMax && (int64_t)cap * 2 * kItemsTarget <= total) cap *= 2;
-    w.cap = cap;
-    k_items_count<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit, cap, cnt,
-                                                     slots);
-    WNNC_LAUNCH_CHECK();
-    exclusive_scan_i32(cnt, item_off, nseg, s);
-    exclusive_scan_i32(slots, slot_off, nseg, s);
-    k_split_flags<<<ceil_div(nseg, kTB), kTB, 0, s>>>(cnt, nseg, flag);
-    WNNC_LAUNCH_CHECK();
-    exclusive_scan_i32(flag, split_off, nseg, s);
-    {
-        // the three totals in one copy (one wait)
-        int* tot = dalloc<int>(3);
-        k_gather_tot3<<<1, 32, 0, s>>>(item_off + nseg, slot_off + nseg, split_off + nseg, tot);
-        WNNC_LAUNCH_CHECK();
-        int h[3] = {0, 0, 0};
-        WNNC_CUDA(cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, s));
-        WNNC_CUDA(cudaStreamSynchronize(s));
-        pool_free(tot);
-        w.nitems = h[0];
-        w.nslots = partials ? h[1] : 0;
-        w.nsplit = partials ? h[2] : 0;
-    }
+}
+
+static void work_fill(WorkList& w, WorkBuild& b, const int* htot, cudaStream_t s) {
+    const int nseg = b.nseg;
+    w.nitems = htot[0];
+    w.nslots = b.partials ? htot[1] : 0;
+    w.nsplit = b.partials ? htot[2] : 0;
     Item* tmp = dalloc<Item>(w.nitems);
     w.splits = dalloc<int4>(w.nsplit);
     w.split_cnt = dalloc<unsigned>(w.nsplit);
-    if (partials) {
+    if (b.partials) {
         w.gsplit = dalloc<int>(nseg);
-        k_group_splits<<<ceil_div(nseg, kTB), kTB, 0, s>>>(cnt, split_off, nseg, w.gsplit);
+        k_group_splits<<<ceil_div(nseg, kTB), kTB, 0, s>>>(b.cnt, b.split_off, nseg, w.gsplit);
         WNNC_LAUNCH_CHECK();
     }
     WNNC_CUDA(cudaMemsetAsync(w.split_cnt, 0, sizeof(unsigned) * (size_t)std::max(w.nsplit, 1), s));
-    k_items_fill<<<ceil_div(nseg, kTB), kTB, 0, s>>>(mode, nseg, near_off, rng, far_off, lsplit, cap, cnt,
-                                                    item_off, slot_off, partials, tmp, w.splits, split_off);
+    k_items_fill<<<ceil_div((int64_t)nseg * 32, kTB), kTB, 0, s>>>(b.mode, nseg, b.near_off, b.rng, b.far_off,
+                                                                  b.lsplit, b.cap, b.cnt, b.item_off, b.slot_off,
+                                                                  b.partials, tmp, w.splits, b.split_off);
     WNNC_LAUNCH_CHECK();
     uint64_t* keys = dalloc<uint64_t>(w.nitems);
     k_item_keys<<<ceil_div(w.nitems, kTB), kTB, 0, s>>>(tmp, w.nitems, keys);
@@ -1295,8 +1366,9 @@ static void build_work(WorkList& w, int mode, int nseg, const int* near_off, con
     k_item_permute<<<ceil_div(w.nitems, kTB), kTB, 0, s>>>(tmp, keys, w.nitems, w.items);
     WNNC_LAUNCH_CHECK();
     wait_before_free(s);
-    pool_free(cnt); pool_free(slots); pool_free(item_off); pool_free(slot_off); pool_free(flag);
-    pool_free(split_off); pool_free(tmp); pool_free(keys);
+    pool_free(b.cnt); pool_free(b.slots); pool_free(b.item_off); pool_free(b.slot_off); pool_free(b.flag);
+    pool_free(b.split_off); pool_free(b.cap); pool_free(b.tot); pool_free(tmp); pool_free(keys);
+    b = WorkBuild();
 }
 
 // Far lists of the groups that a first-in first-out walk finished as stack
@@ -1520,10 +1592,10 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             if (big_stack) WNNC_TRAVERSE(kStackBig, false); else WNNC_TRAVERSE(kStackSmall, true);
 #undef WNNC_TRAVERSE
             WNNC_LAUNCH_CHECK();
-            unsigned long long hc[3] = {0, 0, 0};
-            int herr[2] = {0, 0};
-            WNNC_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
-            WNNC_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+            unsigned long long* hc = reinterpret_cast<unsigned long long*>(pinned_scratch());
+            int* herr = reinterpret_cast<int*>(hc + 3);
+            WNNC_CUDA(cudaMemcpyAsync(hc, counts, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            WNNC_CUDA(cudaMemcpyAsync(herr, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
             WNNC_CUDA(cudaStreamSynchronize(s));
             nunsorted = herr[1];
             if (herr[0]) {
@@ -1656,8 +1728,12 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     k_pair_counts<<<ceil_div(ng, kTB), kTB, 0, s>>>(ng, ts.goff, ts.far_off, ts.far_lsplit, ts.far_csplit, K,
                                                     ts.near_off, ts.near_rng, pc);
     WNNC_LAUNCH_CHECK();
-    unsigned long long hc[6];
-    WNNC_CUDA(cudaMemcpyAsync(hc, pc, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    WorkBuild wb;
+    work_count(wb, 0, ng, ts.near_off, ts.near_rng, ts.far_off, ts.far_lsplit, true, s);
+    unsigned long long* hc = reinterpret_cast<unsigned long long*>(pinned_scratch());
+    int* wt = reinterpret_cast<int*>(hc + 6);
+    WNNC_CUDA(cudaMemcpyAsync(hc, pc, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    WNNC_CUDA(cudaMemcpyAsync(wt, wb.tot, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     WNNC_CUDA(cudaStreamSynchronize(s));
     pool_free(pc);
     ts.far_pairs = (int64_t)hc[0];
@@ -1666,7 +1742,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
     ts.local_pairs = (int64_t)hc[3];
     ts.cluster_entries = (int64_t)hc[4];
     ts.cluster_pairs = (int64_t)hc[5];
-    build_work(ts.work, 0, ng, ts.near_off, ts.near_rng, ts.far_off, ts.far_lsplit, true, s);
+    work_fill(ts.work, wb, wt, s);
 }
 
 void free_target_set(TargetSet& ts) {
@@ -1701,8 +1777,8 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     WNNC_LAUNCH_CHECK();
     k_bbox_final<<<1, 1024, 0, s>>>(part, nparts, cs);
     WNNC_LAUNCH_CHECK();
-    double hcs[4];
-    WNNC_CUDA(cudaMemcpyAsync(hcs, cs, sizeof(hcs), cudaMemcpyDeviceToHost, s));
+    double* hcs = reinterpret_cast<double*>(pinned_scratch());
+    WNNC_CUDA(cudaMemcpyAsync(hcs, cs, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     double* xn = dalloc<double>(3 * n);
     uint32_t* idx = dalloc<uint32_t>(n);
     t.keys = dalloc<uint64_t>(n);
@@ -1804,8 +1880,10 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         k_mom_totals<<<1, 32, 0, s>>>(fl, nn, tot);
         WNNC_LAUNCH_CHECK();
         int h[4];
-        WNNC_CUDA(cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, s));
+        int* hp = reinterpret_cast<int*>(pinned_scratch());
+        WNNC_CUDA(cudaMemcpyAsync(hp, tot, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
         WNNC_CUDA(cudaStreamSynchronize(s));
+        std::copy(hp, hp + 4, h);
         t.nmom_mid = h[0];
         t.nmom_top = h[1];
         t.nleaves = h[3];
@@ -1887,8 +1965,6 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             WNNC_LAUNCH_CHECK();
         }
         exclusive_scan_i32(len, t.rng_slot, nr, s);
-        t.near_slots = read_int(t.rng_slot + nr, s);
-        pool_free(len);
         int* cnt = dalloc<int>(nr + 1);
         int* coff = dalloc<int>(nr + 2);
         if (nr) {
@@ -1896,7 +1972,14 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             WNNC_LAUNCH_CHECK();
         }
         exclusive_scan_i32(cnt, coff, nr, s);
-        int ne = read_int(coff + nr, s);
+        // both totals with one read-back
+        int* hp = reinterpret_cast<int*>(pinned_scratch());
+        WNNC_CUDA(cudaMemcpyAsync(hp, t.rng_slot + nr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        WNNC_CUDA(cudaMemcpyAsync(hp + 1, coff + nr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        t.near_slots = hp[0];
+        const int ne = hp[1];
+        pool_free(len);
         uint64_t* k = dalloc<uint64_t>(ne);
         uint32_t* msk = dalloc<uint32_t>(ne);
         int* slt = dalloc<int>(ne);
@@ -1928,9 +2011,22 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         pool_free(cnt); pool_free(coff); pool_free(k); pool_free(msk); pool_free(slt); pool_free(idx);
         pool_free(head); pool_free(hscan); pool_free(uk);
     }
-    build_work(t.adj_far_work, 2, ng, nullptr, nullptr, S.far_off, S.far_lsplit, false, s);
-    build_work(t.adj_pair_work, 0, ng, S.near_off, S.near_rng, nullptr, nullptr, false, s);
-    build_work(t.adj_near_work, 1, nach, t.tnear_off, nullptr, nullptr, nullptr, true, s);
+    // the adjoint's three work lists, sized by one read-back
+    {
+        WorkBuild wb[3];
+        work_count(wb[0], 2, ng, nullptr, nullptr, S.far_off, S.far_lsplit, false, s);
+        work_count(wb[1], 0, ng, S.near_off, S.near_rng, nullptr, nullptr, false, s);
+        work_count(wb[2], 1, nach, t.tnear_off, nullptr, nullptr, nullptr, true, s);
+        int* ht = reinterpret_cast<int*>(pinned_scratch());
+        for (int k = 0; k < 3; ++k)
+            WNNC_CUDA(cudaMemcpyAsync(ht + 3 * k, wb[k].tot, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        WNNC_CUDA(cudaStreamSynchronize(s));
+        int wt[3][3];
+        std::copy(ht, ht + 9, &wt[0][0]);
+        work_fill(t.adj_far_work, wb[0], wt[0], s);
+        work_fill(t.adj_pair_work, wb[1], wt[1], s);
+        work_fill(t.adj_near_work, wb[2], wt[2], s);
+    }
 }
 
 void free_tree(Tree& t) {
