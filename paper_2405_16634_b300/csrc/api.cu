@@ -102,7 +102,7 @@ static void alloc_workspace(Tree& t) {
     WNNC_CUDA(cudaMemsetAsync(t.scalars, 0, 4 * sizeof(double), alloc_stream()));
     t.err_flag = dalloc<int>(1);
     WNNC_CUDA(cudaMemsetAsync(t.err_flag, 0, sizeof(int), alloc_stream()));
-    WNNC_CUDA(cudaStreamCreateWithFlags(&t.aux, cudaStreamNonBlocking));
+    if (!t.aux) WNNC_CUDA(cudaStreamCreateWithFlags(&t.aux, cudaStreamNonBlocking));
     WNNC_CUDA(cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming));
     WNNC_CUDA(cudaEventCreateWithFlags(&t.ev_join, cudaEventDisableTiming));
     if (t.params.far_order == 1) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -337,8 +338,12 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s);
 // centroids, computed once after the build.
 void local_setup(Tree& t, cudaStream_t s);
 
+// after_far (optional) runs on the host once the far lists are final (the
+// work queued on s before it has produced them): the tree build forks the
+// transposed lists onto a second stream there.
 void build_target_set(const Tree& t, TargetSet& ts, const double* yn_unsorted, int64_t m, bool self,
-                      cudaStream_t s, const int64_t* self_perm = nullptr);
+                      cudaStream_t s, const int64_t* self_perm = nullptr,
+                      const std::function<void()>& after_far = nullptr);
 void free_target_set(TargetSet& ts);
 void free_tree(Tree& t);
 

@@ -1434,7 +1434,7 @@ static void sort_far_segments(int* far_id, const int* far_off, const int* lsplit
 }
 
 void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m, bool self,
-                      cudaStream_t s, const int64_t* self_perm) {
+                      cudaStream_t s, const int64_t* self_perm, const std::function<void()>& after_far) {
     ts.m = m;
     ts.nchunks = ceil_div(m, kGroup);
     // Morton order of the targets: for the tree's own points it is the
@@ -1539,6 +1539,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         nr0 = ng;
         k_all_near<<<ceil_div(ng + 1, kTB), kTB, 0, s>>>(ng, (int)t.n, near_off0, rng0);
         WNNC_LAUNCH_CHECK();
+        if (after_far) after_far();
     } else {
         int* leaf_off = dalloc<int>(ng + 1);
         int* err = dalloc<int>(2);        // [0] error flags, [1] groups finished as stack walks
@@ -1673,6 +1674,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             ts.far_id = reordered;
             pool_free(moved);
         }
+        if (after_far) after_far();
         // merge consecutive near leaves into ranges
         int* head = dalloc<int>(nleafent + 2);
         int* hscan = dalloc<int>(nleafent + 2);
@@ -1764,6 +1766,40 @@ static void grow_nodes(Tree& t, int& cap, int need) {
     grow(t.node_start); grow(t.node_count); grow(t.node_parent);
     grow(t.node_child0); grow(t.node_nchild); grow(t.node_depth);
     cap = ncap;
+}
+
+// Transposed far lists (node -> the far entries that name it), on stream s.
+static void build_tfar(Tree& t, cudaStream_t s) {
+    const TargetSet& S = t.self;
+    const int ng = S.ngroups;
+    t.tfar_off = dalloc<int>(t.nnodes + 1);
+    const int64_t ne = S.far_entries;
+    const bool local = S.far_lsplit != nullptr;
+    if (local && ne >= (int64_t(1) << 30)) fail(WNNC_ECAPACITY, "too many far entries for local expansions");
+    uint64_t* k = dalloc<uint64_t>(ne);
+    // with local expansions: the group of every entry (it decides the entry's
+    // class and drops the copies of cluster expansions past the first member)
+    int* egrp = local ? dalloc<int>(ne) : nullptr;
+    if (local && ne) {
+        k_entry_groups<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(S.far_off, ng, egrp);
+        WNNC_LAUNCH_CHECK();
+    }
+    if (ne) {
+        k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, egrp, S.far_csplit, S.cluster_k, t.nnodes, k);
+        WNNC_LAUNCH_CHECK();
+    }
+    // entry indices already ascending: the node bits only
+    radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes + 1), s, 32);
+    t.tfar_ent = dalloc<int>(ne);
+    segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
+    if (ne) {
+        k_tfar_ids<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, egrp, S.far_lsplit, S.far_csplit, S.cluster_k,
+                                                     t.nnodes, t.tfar_ent);
+        WNNC_LAUNCH_CHECK();
+    }
+    wait_before_free(s);
+    pool_free(k);
+    pool_free(egrp);
 }
 
 void build_tree(Tree& t, const float* pts, cudaStream_t s) {
@@ -1911,8 +1947,20 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         pool_free(fkeys);
     }
 
-    // --- the points as targets: same Morton order as the sources ---
-    build_target_set(t, t.self, xn, n, true, s, perm_tmp);
+    // --- the points as targets: same Morton order as the sources; the
+    // transposed far lists, which only the adjoint reads, are built on the
+    // second stream once the far lists are final, beside the rest ---
+    if (!t.aux) WNNC_CUDA(cudaStreamCreateWithFlags(&t.aux, cudaStreamNonBlocking));
+    cudaEvent_t ev_far = nullptr, ev_tfar = nullptr;
+    WNNC_CUDA(cudaEventCreateWithFlags(&ev_far, cudaEventDisableTiming));
+    WNNC_CUDA(cudaEventCreateWithFlags(&ev_tfar, cudaEventDisableTiming));
+    build_target_set(t, t.self, xn, n, true, s, perm_tmp, [&] {
+        WNNC_CUDA(cudaEventRecord(ev_far, s));
+        WNNC_CUDA(cudaStreamWaitEvent(t.aux, ev_far, 0));
+        AllocStream as(t.aux);
+        build_tfar(t, t.aux);
+        WNNC_CUDA(cudaEventRecord(ev_tfar, t.aux));
+    });
     pool_free(xn);
     pool_free(idx);
     pool_free(perm_tmp);
@@ -1924,37 +1972,6 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     const int ng = S.ngroups;
     const int nach = ceil_div(t.n, kAdjChunk);
     t.nach = nach;
-    t.tfar_off = dalloc<int>(t.nnodes + 1);
-    {
-        int64_t ne = S.far_entries;
-        const bool local = S.far_lsplit != nullptr;
-        if (local && ne >= (int64_t(1) << 30)) fail(WNNC_ECAPACITY, "too many far entries for local expansions");
-        uint64_t* k = dalloc<uint64_t>(ne);
-        // with local expansions: the group of every entry, and bit 31 of the
-        // key set for an expanded entry (sorted after the node's others)
-        int* egrp = local ? dalloc<int>(ne) : nullptr;
-        if (local && ne) {
-            k_entry_groups<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(S.far_off, ng, egrp);
-            WNNC_LAUNCH_CHECK();
-        }
-        if (ne) {
-            k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, egrp, S.far_csplit, S.cluster_k, t.nnodes,
-                                                          k);
-            WNNC_LAUNCH_CHECK();
-        }
-        // entry indices already ascending: the node bits only
-        radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes + 1), s, 32);
-        t.tfar_ent = dalloc<int>(ne);
-        segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
-        if (ne) {
-            k_tfar_ids<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, egrp, S.far_lsplit, S.far_csplit, S.cluster_k,
-                                                         t.nnodes, t.tfar_ent);
-            WNNC_LAUNCH_CHECK();
-        }
-        wait_before_free(s);
-        pool_free(k);
-        pool_free(egrp);
-    }
     {
         int64_t nr = S.near_ranges;
         // near slots: lengths of the ranges, scanned (ranges are group-major)
@@ -2027,6 +2044,9 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
         work_fill(t.adj_pair_work, wb[1], wt[1], s);
         work_fill(t.adj_near_work, wb[2], wt[2], s);
     }
+    WNNC_CUDA(cudaStreamWaitEvent(s, ev_tfar, 0));
+    WNNC_CUDA(cudaEventDestroy(ev_far));
+    WNNC_CUDA(cudaEventDestroy(ev_tfar));
 }
 
 void free_tree(Tree& t) {
