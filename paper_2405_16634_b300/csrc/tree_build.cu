@@ -227,37 +227,251 @@ __global__ void k_split_write(int* start, int* count, int* parent, int* child0, 
     }
 }
 
-// Bounding box and point sum of the nodes of one level (deepest first).
-__global__ void k_node_boxes(const double* xs, const int* start, const int* count,
-                             const int* child0, const int* nchild, int base, int m, double* lo,
-                             double* hi, double* sum) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    int b = base + i;
-    double l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
-    double sm[3] = {0, 0, 0};
-    if (nchild[b] == 0) {
-        for (int j = start[b]; j < start[b] + count[b]; ++j)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                double v = xs[3 * (int64_t)j + k];
-                l[k] = fmin(l[k], v);
-                h[k] = fmax(h[k], v);
-                sm[k] += v;
-            }
-    } else {
-        for (int q = 0; q < nchild[b]; ++q) {
-            int c = child0[b] + q;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                l[k] = fmin(l[k], lo[3 * c + k]);
-                h[k] = fmax(h[k], hi[3 * c + k]);
-                sm[k] += sum[3 * c + k];
+// ---------------------------------------------------------------------------
+// The whole octree in one cooperative launch (every block resident): level by
+// level as k_split_count / k_split_write do, the blocks meeting at a grid
+// barrier after the child counts of a level (phase A) and after its children
+// are written (phase B).  Block k takes a contiguous slice of the level's
+// nodes; a node's children go after the children of every node before it
+// (the slices' totals, then a scan inside the slice), so the ids are those of
+// the launch-per-level build.  If the nodes would pass the capacity, no
+// children of that level are written and the caller builds by launches.
+// ---------------------------------------------------------------------------
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int err;            // a wait gave up
+};
+constexpr int kBarrierPolls = 1 << 22;
+
+// Barrier of all blocks of a cooperative launch: each block arrives on the
+// counter; the last to arrive resets it and bumps the generation, which the
+// others poll (at most kBarrierPolls times: then the error flag, and on).
+__device__ void grid_barrier(GridBar* gb) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &gb->gen;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            int polls = 0;
+            while (*gen == g) {
+                if (++polls > kBarrierPolls) {
+                    atomicOr(&gb->err, 1);
+                    break;
+                }
+                __nanosleep(64);
             }
         }
+        __threadfence();
     }
+    __syncthreads();
+}
+
+constexpr int kOctThreads = 256;
+constexpr int kOctMaxLevels = kMaxDepth + 2;
+
+struct OctArgs {
+    const uint64_t* keys;
+    int n, leaf_size, max_depth, cap;
+    int *start, *count, *parent, *child0, *nchild, *depth;
+    int* bnd;           // [8 x largest level]
+    int* nkids;         // [largest level]
+    int* block_tot;     // [gridDim.x]
+    int* lvl;           // [kOctMaxLevels] nodes per level
+    GridBar* bar;
+    int* status;        // [0] nodes, [1] capacity exceeded
+};
+
+// Sum over the block of one value per thread, and the exclusive scan.
+__device__ __forceinline__ int oct_block_scan(int v, int* total) {
+    __shared__ int ws[kOctThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) { lo[3 * b + k] = l[k]; hi[3 * b + k] = h[k]; sum[3 * b + k] = sm[k]; }
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    int before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kOctThreads / 32; ++w) {
+        if (w < warp) before += ws[w];
+        all += ws[w];
+    }
+    __syncthreads();
+    *total = all;
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kOctThreads) k_octree(OctArgs A) {
+    const int G = (int)gridDim.x, blk = (int)blockIdx.x, tid = (int)threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    if (blk == 0 && tid == 0) {
+        A.start[0] = 0;
+        A.count[0] = A.n;
+        A.parent[0] = -1;
+        A.depth[0] = 0;
+        A.lvl[0] = 1;
+    }
+    grid_barrier(A.bar);
+    int base = 0, m = 1, d = 0, total = 1;
+    for (;;) {
+        const int chunk = (m + G - 1) / G;
+        const int B0 = min(blk * chunk, m), B1 = min(B0 + chunk, m);
+        // phase A: eight threads per node, thread q finding the end of child q
+        int mine = 0;
+        for (int i0 = B0; i0 < B1; i0 += kOctThreads / 8) {
+            const int i = i0 + (tid >> 3), q = tid & 7;
+            const bool act = i < B1;
+            int s = 0, e = 0;
+            bool split = false;
+            if (act) {
+                const int b = base + i;
+                s = A.start[b];
+                e = s + A.count[b];
+                split = A.count[b] > A.leaf_size && d < A.max_depth;
+            }
+            int p = e;
+            if (split && q < 7) p = first_digit_ge(A.keys, s, e, d, q + 1);
+            int pp = __shfl_up_sync(0xffffffffu, p, 1, 8);
+            if (q == 0) pp = s;
+            const unsigned nonempty = __ballot_sync(0xffffffffu, split && p > pp);
+            if (act) {
+                A.bnd[(int64_t)8 * i + q] = p;
+                if (q == 0) {
+                    const int nk = __popc((nonempty >> (lane & ~7u)) & 0xffu);
+                    A.nkids[i] = nk;
+                    mine += nk;
+                }
+            }
+        }
+        int bsum = 0;
+        oct_block_scan(mine, &bsum);
+        if (tid == 0) A.block_tot[blk] = bsum;
+        grid_barrier(A.bar);
+        // phase B: this slice's first child id, then the children
+        int before = 0, all = 0;
+        for (int k = tid; k < G; k += kOctThreads) {
+            const int v = A.block_tot[k];
+            all += v;
+            if (k < blk) before += v;
+        }
+        int pre = 0, tot = 0;
+        oct_block_scan(before, &pre);
+        oct_block_scan(all, &tot);
+        const bool overflow = (int64_t)total + tot > (int64_t)A.cap;
+        if (!overflow) {
+            int carry = 0;
+            for (int i0 = B0; i0 < B1; i0 += kOctThreads) {
+                const int i = i0 + tid;
+                const int v = i < B1 ? A.nkids[i] : 0;
+                int tile = 0;
+                const int ex = oct_block_scan(v, &tile);
+                if (i < B1) {
+                    const int b = base + i;
+                    if (v == 0) {
+                        A.child0[b] = -1;
+                        A.nchild[b] = 0;
+                    } else {
+                        const int c0 = total + pre + carry + ex;
+                        A.child0[b] = c0;
+                        A.nchild[b] = v;
+                        int prev = A.start[b], w = 0;
+                        for (int q = 0; q < 8; ++q) {
+                            const int p = A.bnd[(int64_t)8 * i + q];
+                            if (p > prev) {
+                                const int c = c0 + w++;
+                                A.start[c] = prev;
+                                A.count[c] = p - prev;
+                                A.parent[c] = b;
+                                A.depth[c] = d + 1;
+                            }
+                            prev = p;
+                        }
+                    }
+                }
+                carry += tile;
+            }
+        }
+        if (blk == 0 && tid == 0) {
+            A.lvl[d + 1] = overflow ? 0 : tot;
+            if (overflow) A.status[1] = 1;
+        }
+        grid_barrier(A.bar);
+        if (overflow) break;
+        base = total;
+        total += tot;
+        m = tot;
+        ++d;
+        if (m == 0 || d + 1 >= kOctMaxLevels) break;
+    }
+    if (blk == 0 && tid == 0) A.status[0] = total;
+}
+
+// Bounding boxes and point sums of all nodes in one launch, from the leaves
+// up: a thread takes a leaf (its points in order), then climbs while it is
+// the last of its parent's children to finish (a counter per node); the last
+// child sums the parent from all its children in child order, so the sums
+// are those of a level-by-level pass.  Children's values are written before
+// the counter is raised (fence) and read by the last one past L1 (__ldcg).
+__device__ __forceinline__ void node_box_store(double* lo, double* hi, double* sum, int b, const double* l,
+                                               const double* h, const double* sm) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[3 * b + k] = l[k];
+        hi[3 * b + k] = h[k];
+        sum[3 * b + k] = sm[k];
+    }
+}
+
+__global__ void k_node_boxes(const double* xs, const int* start, const int* count, const int* child0,
+                             const int* nchild, const int* parent, int nn, double* lo, double* hi, double* sum,
+                             int* arrive) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nn || nchild[b] != 0) return;
+    double l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double sm[3] = {0, 0, 0};
+    for (int j = start[b]; j < start[b] + count[b]; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double v = xs[3 * (int64_t)j + k];
+            l[k] = fmin(l[k], v);
+            h[k] = fmax(h[k], v);
+            sm[k] += v;
+        }
+    node_box_store(lo, hi, sum, b, l, h, sm);
+    for (;;) {
+        const int p = parent[b];
+        if (p < 0) break;
+        __threadfence();
+        const int nc = nchild[p];
+        if (atomicAdd(&arrive[p], 1) != nc - 1) break;
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            l[k] = INFINITY;
+            h[k] = -INFINITY;
+            sm[k] = 0.0;
+        }
+        for (int q = 0; q < nc; ++q) {
+            const int c = child0[p] + q;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                l[k] = fmin(l[k], __ldcg(lo + 3 * c + k));
+                h[k] = fmax(h[k], __ldcg(hi + 3 * c + k));
+                sm[k] += __ldcg(sum + 3 * c + k);
+            }
+        }
+        node_box_store(lo, hi, sum, p, l, h, sm);
+        b = p;
+    }
 }
 
 // Cell centre (exact dyadic), width, centroid offset; leaf ownership of points.
@@ -979,50 +1193,46 @@ __global__ void k_cluster_partition(const int* far_off, const int* lsplit, const
     if (lane == 0) csplit[g] = l0 + nstay;
 }
 
-// Group of every far entry (warp per group over its range).
-__global__ void k_entry_groups(const int* far_off, int ng, int* egrp) {
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Transposed far lists: one key per far entry, (node << 32 | the entry's
+// value in the transposed list), written by one warp per group.  The value is
+// the entry index; with local expansions class << 30 | id: class 0 for an
+// entry summed pair by pair (id = the entry), 1 for one expanded about its
+// group (from lsplit on; id = the group), 2 for one expanded about its cluster
+// (from csplit on; id = the cluster), kept only in the first member's copy
+// (the other members' copies get node = nnodes and sort past every node).  A
+// stable sort on the node bits then leaves each node's values in entry order.
+__global__ void k_tfar_keys(const int* far_off, const int* far_id, int ng, const int* lsplit, const int* csplit,
+                            int K, int nnodes, uint64_t* keys) {
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= ng) return;
-    for (int e = far_off[g] + lane; e < far_off[g + 1]; e += 32) egrp[e] = g;
+    const int f0 = far_off[g], f1 = far_off[g + 1];
+    const int l0 = lsplit ? lsplit[g] : f1, c0 = csplit ? csplit[g] : f1;
+    for (int e = f0 + lane; e < f1; e += 32) {
+        uint32_t node = (uint32_t)far_id[e];
+        uint32_t v = (uint32_t)e;
+        if (e >= c0) {   // only with clusters (K >= 2)
+            v = (2u << 30) | (uint32_t)(g / K);
+            if (g % K != 0) node = (uint32_t)nnodes;
+        } else if (e >= l0) {
+            v = (1u << 30) | (uint32_t)g;
+        }
+        keys[e] = ((uint64_t)node << 32) | v;
+    }
 }
 
-// Transposed far lists: key (node << 32 | entry index).  With local
-// expansions, an entry expanded about a cluster is kept only in the first
-// member's copy: the other members' copies get node = nnodes and sort past
-// every node.
-__global__ void k_tfar_keys(const int* far_id, int64_t nent, const int* egrp, const int* csplit, int K, int nnodes,
-                            uint64_t* keys) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nent) return;
-    uint32_t node = (uint32_t)far_id[e];
-    if (csplit) {
-        const int g = egrp[e];
-        if (e >= csplit[g] && g % K != 0) node = (uint32_t)nnodes;
-    }
-    keys[e] = ((uint64_t)node << 32) | (uint32_t)e;
-}
-
-// Sorted transposed keys -> tfar_ent.  Without local expansions: the entry
-// index.  With them (egrp set): class << 30 | id, class 0 for an entry summed
-// pair by pair (id = the entry), 1 for one expanded about its group (before
-// csplit, from lsplit on; id = the group), 2 for one expanded about its
-// cluster (id = the cluster).
-__global__ void k_tfar_ids(const uint64_t* keys, int64_t n, const int* egrp, const int* lsplit, const int* csplit,
-                           int K, int nnodes, int* tfar_ent) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const uint64_t k = keys[q];
-    if ((int)(k >> 32) >= nnodes) return;
-    const int e = (int)(uint32_t)(k & 0xffffffffu);
-    if (!egrp) {
-        tfar_ent[q] = e;
-        return;
-    }
-    const int g = egrp[e];
-    if (csplit && e >= csplit[g]) tfar_ent[q] = (2 << 30) | (g / K);
-    else if (e >= lsplit[g]) tfar_ent[q] = (1 << 30) | g;
-    else tfar_ent[q] = e;
+// Sorted transposed keys -> tfar_ent (the low words, dropped copies
+// excluded) and the offsets of every node's run.
+__global__ void k_tfar_finish(const uint64_t* keys, int64_t n, int nnodes, int* tfar_ent, int* off) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k = keys[i];
+    const int64_t b = (int64_t)(k >> 32);
+    if (b < nnodes) tfar_ent[i] = (int)(uint32_t)(k & 0xffffffffu);
+    const int64_t bp = i > 0 ? (int64_t)(keys[i - 1] >> 32) : -1;
+    for (int64_t q = bp + 1; q <= b && q <= nnodes; ++q) off[q] = (int)i;
+    if (i == n - 1)
+        for (int64_t q = b + 1; q <= nnodes; ++q) off[q] = (int)n;
 }
 
 __global__ void k_tnear_count(const int2* rng, int64_t nr, int* cnt) {
@@ -1774,32 +1984,22 @@ static void build_tfar(Tree& t, cudaStream_t s) {
     const int ng = S.ngroups;
     t.tfar_off = dalloc<int>(t.nnodes + 1);
     const int64_t ne = S.far_entries;
-    const bool local = S.far_lsplit != nullptr;
-    if (local && ne >= (int64_t(1) << 30)) fail(WNNC_ECAPACITY, "too many far entries for local expansions");
+    if (S.far_lsplit && ne >= (int64_t(1) << 30)) fail(WNNC_ECAPACITY, "too many far entries for local expansions");
+    t.tfar_ent = dalloc<int>(std::max<int64_t>(ne, 1));
+    if (ne == 0) {
+        WNNC_CUDA(cudaMemsetAsync(t.tfar_off, 0, sizeof(int) * (t.nnodes + 1), s));
+        return;
+    }
     uint64_t* k = dalloc<uint64_t>(ne);
-    // with local expansions: the group of every entry (it decides the entry's
-    // class and drops the copies of cluster expansions past the first member)
-    int* egrp = local ? dalloc<int>(ne) : nullptr;
-    if (local && ne) {
-        k_entry_groups<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(S.far_off, ng, egrp);
-        WNNC_LAUNCH_CHECK();
-    }
-    if (ne) {
-        k_tfar_keys<<<ceil_div(ne, kTB), kTB, 0, s>>>(S.far_id, ne, egrp, S.far_csplit, S.cluster_k, t.nnodes, k);
-        WNNC_LAUNCH_CHECK();
-    }
-    // entry indices already ascending: the node bits only
+    k_tfar_keys<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(S.far_off, S.far_id, ng, S.far_lsplit, S.far_csplit,
+                                                               S.cluster_k, t.nnodes, k);
+    WNNC_LAUNCH_CHECK();
+    // entry order already ascending: the node bits only
     radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes + 1), s, 32);
-    t.tfar_ent = dalloc<int>(ne);
-    segment_offsets_hi32(k, ne, t.tfar_off, t.nnodes, s);
-    if (ne) {
-        k_tfar_ids<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, egrp, S.far_lsplit, S.far_csplit, S.cluster_k,
-                                                     t.nnodes, t.tfar_ent);
-        WNNC_LAUNCH_CHECK();
-    }
+    k_tfar_finish<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, t.nnodes, t.tfar_ent, t.tfar_off);
+    WNNC_LAUNCH_CHECK();
     wait_before_free(s);
     pool_free(k);
-    pool_free(egrp);
 }
 
 void build_tree(Tree& t, const float* pts, cudaStream_t s) {
@@ -1835,55 +2035,113 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
     int cap = (int)std::min<int64_t>(INT32_MAX / 2, 2 * n + 64);
     t.node_start = dalloc<int>(cap); t.node_count = dalloc<int>(cap); t.node_parent = dalloc<int>(cap);
     t.node_child0 = dalloc<int>(cap); t.node_nchild = dalloc<int>(cap); t.node_depth = dalloc<int>(cap);
-    {
-        int h0 = 0, hn = (int)n, hp = -1;
-        WNNC_CUDA(cudaMemcpyAsync(t.node_start, &h0, sizeof(int), cudaMemcpyHostToDevice, s));
-        WNNC_CUDA(cudaMemcpyAsync(t.node_count, &hn, sizeof(int), cudaMemcpyHostToDevice, s));
-        WNNC_CUDA(cudaMemcpyAsync(t.node_parent, &hp, sizeof(int), cudaMemcpyHostToDevice, s));
-        WNNC_CUDA(cudaMemcpyAsync(t.node_depth, &h0, sizeof(int), cudaMemcpyHostToDevice, s));
-    }
     std::vector<int> level_off = {0, 1};
-    int base = 0, m = 1, depth = 0, total_nodes = 1;
+    int total_nodes = 1;
     int* nkids = dalloc<int>(n + 1);
-    int* koff = dalloc<int>(n + 2);
     int* bnd = dalloc<int>(8 * (size_t)(n + 1));   // child range ends; a level holds at most n nodes
-    while (m > 0) {
-        k_split_count<<<ceil_div((int64_t)8 * m, kTB), kTB, 0, s>>>(t.keys, t.node_start, t.node_count, base, m,
-                                                                   depth, P.leaf_size, P.max_depth, nkids, bnd);
-        WNNC_LAUNCH_CHECK();
-        exclusive_scan_i32(nkids, koff, m, s);
-        int nnext = read_int(koff + m, s);
-        grow_nodes(t, cap, total_nodes + nnext);
-        k_split_write<<<ceil_div(m, kTB), kTB, 0, s>>>(t.node_start, t.node_count, t.node_parent, t.node_child0,
-                                                      t.node_nchild, t.node_depth, base, m, depth, total_nodes,
-                                                      koff, nkids, bnd);
-        WNNC_LAUNCH_CHECK();
-        base = total_nodes;
-        total_nodes += nnext;
-        m = nnext;
-        if (m > 0) {
-            level_off.push_back(total_nodes);
-            ++depth;
+    bool built = false;
+    {
+        // one cooperative launch, if the device takes one and the nodes fit
+        int dev = 0, coop = 0, sms = 0, per_sm = 0;
+        WNNC_CUDA(cudaGetDevice(&dev));
+        WNNC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        WNNC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        WNNC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_octree, kOctThreads, 0));
+        if (coop && per_sm > 0) {
+            const int G = std::min(per_sm, 2) * sms;
+            int* ctl = dalloc<int>(kOctMaxLevels + 8 + G);   // lvl, barrier, status, block totals
+            WNNC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * (kOctMaxLevels + 8 + G), s));
+            OctArgs A;
+            A.keys = t.keys;
+            A.n = (int)n;
+            A.leaf_size = P.leaf_size;
+            A.max_depth = P.max_depth;
+            A.cap = cap;
+            A.start = t.node_start;
+            A.count = t.node_count;
+            A.parent = t.node_parent;
+            A.child0 = t.node_child0;
+            A.nchild = t.node_nchild;
+            A.depth = t.node_depth;
+            A.bnd = bnd;
+            A.nkids = nkids;
+            A.lvl = ctl;
+            A.bar = reinterpret_cast<GridBar*>(ctl + kOctMaxLevels);
+            A.status = ctl + kOctMaxLevels + 4;
+            A.block_tot = ctl + kOctMaxLevels + 8;
+            void* args[] = {&A};
+            WNNC_CUDA(cudaLaunchCooperativeKernel((const void*)k_octree, dim3(G), dim3(kOctThreads), args, 0, s));
+            WNNC_LAUNCH_CHECK();
+            int* h = reinterpret_cast<int*>(pinned_scratch());
+            WNNC_CUDA(cudaMemcpyAsync(h, ctl, sizeof(int) * (kOctMaxLevels + 8), cudaMemcpyDeviceToHost, s));
+            WNNC_CUDA(cudaStreamSynchronize(s));
+            const int* hl = h;
+            const GridBar* hb = reinterpret_cast<const GridBar*>(h + kOctMaxLevels);
+            const int* hs = h + kOctMaxLevels + 4;
+            if (hb->err) {
+                pool_free(ctl);
+                fail(WNNC_ETIMEOUT, "a grid barrier of the octree build gave up");
+            }
+            if (!hs[1]) {
+                built = true;
+                total_nodes = hs[0];
+                for (int L = 1; L < kOctMaxLevels && hl[L] > 0; ++L) level_off.push_back(level_off.back() + hl[L]);
+            }
+            pool_free(ctl);
         }
+    }
+    if (!built) {
+        // level by level, one launch each, growing the node arrays as needed
+        {
+            int h0 = 0, hn = (int)n, hp = -1;
+            WNNC_CUDA(cudaMemcpyAsync(t.node_start, &h0, sizeof(int), cudaMemcpyHostToDevice, s));
+            WNNC_CUDA(cudaMemcpyAsync(t.node_count, &hn, sizeof(int), cudaMemcpyHostToDevice, s));
+            WNNC_CUDA(cudaMemcpyAsync(t.node_parent, &hp, sizeof(int), cudaMemcpyHostToDevice, s));
+            WNNC_CUDA(cudaMemcpyAsync(t.node_depth, &h0, sizeof(int), cudaMemcpyHostToDevice, s));
+        }
+        int* koff = dalloc<int>(n + 2);
+        int base = 0, m = 1, depth = 0;
+        while (m > 0) {
+            k_split_count<<<ceil_div((int64_t)8 * m, kTB), kTB, 0, s>>>(t.keys, t.node_start, t.node_count, base, m,
+                                                                       depth, P.leaf_size, P.max_depth, nkids, bnd);
+            WNNC_LAUNCH_CHECK();
+            exclusive_scan_i32(nkids, koff, m, s);
+            int nnext = read_int(koff + m, s);
+            grow_nodes(t, cap, total_nodes + nnext);
+            k_split_write<<<ceil_div(m, kTB), kTB, 0, s>>>(t.node_start, t.node_count, t.node_parent,
+                                                          t.node_child0, t.node_nchild, t.node_depth, base, m, depth,
+                                                          total_nodes, koff, nkids, bnd);
+            WNNC_LAUNCH_CHECK();
+            base = total_nodes;
+            total_nodes += nnext;
+            m = nnext;
+            if (m > 0) {
+                level_off.push_back(total_nodes);
+                ++depth;
+            }
+        }
+        pool_free(koff);
     }
     pool_free(nkids);
     pool_free(bnd);
-    pool_free(koff);
     t.nnodes = total_nodes;
     t.nlevels = (int)level_off.size() - 1;
     t.depth_reached = t.nlevels - 1;
     t.level_off = new int[level_off.size()];
     std::copy(level_off.begin(), level_off.end(), t.level_off);
 
-    // --- boxes and centroids, deepest level first ---
+    // --- boxes and centroids, from the leaves up ---
     t.node_lo = dalloc<double>(3 * (size_t)t.nnodes);
     t.node_hi = dalloc<double>(3 * (size_t)t.nnodes);
     double* sum = dalloc<double>(3 * (size_t)t.nnodes);
-    for (int L = t.nlevels - 1; L >= 0; --L) {
-        int b0 = t.level_off[L], mm = t.level_off[L + 1] - b0;
-        k_node_boxes<<<ceil_div(mm, kTB), kTB, 0, s>>>(t.xs, t.node_start, t.node_count, t.node_child0,
-                                                      t.node_nchild, b0, mm, t.node_lo, t.node_hi, sum);
+    {
+        int* arrive = dalloc<int>(t.nnodes);
+        WNNC_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (size_t)t.nnodes, s));
+        k_node_boxes<<<ceil_div(t.nnodes, kTB), kTB, 0, s>>>(t.xs, t.node_start, t.node_count, t.node_child0,
+                                                            t.node_nchild, t.node_parent, t.nnodes, t.node_lo,
+                                                            t.node_hi, sum, arrive);
         WNNC_LAUNCH_CHECK();
+        pool_free(arrive);
     }
     t.node_lof = dalloc<float4>(t.nnodes);
     t.node_hif = dalloc<float4>(t.nnodes);

@@ -609,6 +609,30 @@ def test_edge_sizes(n, leaf, depth):
         check_close(T, To * sc * sc, {k: v * sc * sc for k, v in bt.items()}, what="AT")
 
 
+def test_octree_past_the_node_capacity():
+    """Coincident pairs with leaf_size 1: every pair is a chain of single-child
+    nodes down to depth 15, more nodes than the one-launch octree build holds
+    (2n + 64), so the build runs level by level with growing arrays; the tree
+    and lists still equal the oracle's."""
+    W = _wnnc()
+    base = _uniform_cube(2000, 21)
+    pts = np.concatenate([base, base]).astype(np.float32)
+    n = len(pts)
+    t = W.Tree(torch.from_numpy(pts).cuda(), theta=0.5, leaf_size=1)
+    assert t.info()["nnodes"] > 2 * n + 64
+    e = t.export()
+    xn, _, _ = oracle.normalize(pts)
+    ot = oracle.Tree(xn, f32(0.5), leaf_size=1)
+    assert np.array_equal(e["perm"], ot.perm())
+    nd = ot.nodes()
+    for k in ("start", "count", "depth", "nchild"):
+        assert np.array_equal(e["node_" + k], nd[k]), k
+    fo, fi, _, _ = ot.lists()
+    assert np.array_equal(e["far_off"], fo)
+    for g in range(len(fo) - 1):
+        assert np.array_equal(e["far_id"][fo[g]:fo[g + 1]], np.sort(fi[fo[g]:fo[g + 1]]))
+
+
 def test_duplicate_points():
     """All points coincident except one: a depth-15 leaf with many points, and
     coincident pairs excluded even at w = 0."""
