@@ -504,7 +504,28 @@ __global__ void k_node_cells(const uint64_t* keys, const int* start, const int* 
 // Target groups and coordinate frames
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double dyadic12(double v) { return rint(v * 4096.0) / 4096.0; }
+__device__ __forceinline__ double dyadic12(double v) { return rint(v * 4096.0) * 0x1p-12; }   // exact scaling
+
+// Warp minimum and maximum of doubles without the (slow) FP64 pipe: finite
+// doubles and infinities map to signed 64-bit integers in the same order
+// (negative values with their magnitude bits flipped), an involution.
+__device__ __forceinline__ long long dord(double v) {
+    const long long k = __double_as_longlong(v);
+    return k ^ ((k >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dord_inv(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ void warp_minmax_d(double& l, double& h) {
+    long long a = dord(l), b = dord(h);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        a = min(a, __shfl_xor_sync(0xffffffffu, a, d));
+        b = max(b, __shfl_xor_sync(0xffffffffu, b, d));
+    }
+    l = dord_inv(a);
+    h = dord_inv(b);
+}
 
 // Number of leading 3-bit digits two 45-bit keys share (0..15).
 __device__ __forceinline__ int common_digits(uint64_t a, uint64_t b) {
@@ -571,10 +592,7 @@ __global__ void k_chunk_frames(const double* ys, int64_t m, int nchunks, float4*
     for (int k = 0; k < 3; ++k) {
         double v = valid ? ys[3 * i + k] : 0.0;
         double l = valid ? v : INFINITY, h = valid ? v : -INFINITY;
-        for (int d = 16; d > 0; d >>= 1) {
-            l = fmin(l, __shfl_xor_sync(0xffffffffu, l, d));
-            h = fmax(h, __shfl_xor_sync(0xffffffffu, h, d));
-        }
+        warp_minmax_d(l, h);
         o[k] = dyadic12(0.5 * (l + h));
     }
     if (lane == 0) corig[c] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
@@ -599,10 +617,7 @@ __global__ void k_group_boxes(const double* ys, const int* goff, int ng, double*
     for (int k = 0; k < 3; ++k) {
         v[k] = valid ? ys[3 * i + k] : 0.0;
         double l = valid ? v[k] : INFINITY, h = valid ? v[k] : -INFINITY;
-        for (int d = 16; d > 0; d >>= 1) {
-            l = fmin(l, __shfl_xor_sync(0xffffffffu, l, d));
-            h = fmax(h, __shfl_xor_sync(0xffffffffu, h, d));
-        }
+        warp_minmax_d(l, h);
         if (lane == 0) { glo[3 * g + k] = l; ghi[3 * g + k] = h; }
         c[k] = 0.5 * (l + h);
         o[k] = dyadic12(c[k]);
@@ -610,12 +625,16 @@ __global__ void k_group_boxes(const double* ys, const int* goff, int ng, double*
         bh[k] = h - o[k];
     }
     if (gctr) {
-        double r = 0.0;
+        // the largest distance from the centre: the square root of the largest
+        // square (the same value: sqrt is monotone and correctly rounded)
+        double r2 = 0.0;
         if (valid) {
             const double dx = v[0] - c[0], dy = v[1] - c[1], dz = v[2] - c[2];
-            r = sqrt(dx * dx + dy * dy + dz * dz);
+            r2 = dx * dx + dy * dy + dz * dz;
         }
-        for (int d = 16; d > 0; d >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, d));
+        double lo2 = r2;
+        warp_minmax_d(lo2, r2);
+        const double r = sqrt(r2);
         if (lane == 0)
             gctr[g] = make_float4((float)(c[0] - o[0]), (float)(c[1] - o[1]), (float)(c[2] - o[2]),
                                   __double2float_ru(r));
@@ -1100,21 +1119,23 @@ __global__ void k_cluster_frames(const double* ys, const int* goff, const double
     for (int k = 0; k < 3; ++k) {
         double l = INFINITY, h = -INFINITY;
         if (g0 + lane < g1) { l = glo[3 * (g0 + lane) + k]; h = ghi[3 * (g0 + lane) + k]; }
-        for (int d = 16; d > 0; d >>= 1) {
-            l = fmin(l, __shfl_xor_sync(0xffffffffu, l, d));
-            h = fmax(h, __shfl_xor_sync(0xffffffffu, h, d));
-        }
+        warp_minmax_d(l, h);
         lo[k] = l;
         hi[k] = h;
         c[k] = 0.5 * (l + h);
         o[k] = dyadic12(c[k]);
     }
-    double r = 0.0;
+    // the largest distance from the centre: the square root of the largest
+    // square (sqrt is monotone and correctly rounded; squares compare as their
+    // bit patterns)
+    long long r2k = 0;
     for (int i = goff[g0] + lane; i < goff[g1]; i += 32) {
         const double dx = ys[3 * (int64_t)i] - c[0], dy = ys[3 * (int64_t)i + 1] - c[1], dz = ys[3 * (int64_t)i + 2] - c[2];
-        r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+        r2k = max(r2k, __double_as_longlong(dx * dx + dy * dy + dz * dz));
     }
-    for (int d = 16; d > 0; d >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, d));
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) r2k = max(r2k, __shfl_xor_sync(0xffffffffu, r2k, d));
+    const double r = sqrt(__longlong_as_double(r2k));
     if (lane == 0) {
         double e = __dsub_rn(hi[0], lo[0]);
         if (__dsub_rn(hi[1], lo[1]) > e) e = __dsub_rn(hi[1], lo[1]);
@@ -1132,8 +1153,8 @@ __global__ void k_cluster_frames(const double* ys, const int* goff, const double
 // member's expanded part (each ascending: binary search) are flagged in every
 // member.
 __global__ void k_cluster_classes(const int* far_off, const int* lsplit, const int* far_id, int ng, int K,
-                                  const double* nlo, const double* nhi, const double* clo, const double* chi,
-                                  const double* cle, unsigned char* moved) {
+                                  const double* nlo, const double* nhi, const float4* nlof, const float4* nhif,
+                                  const double* clo, const double* chi, const double* cle, unsigned char* moved) {
     const int C = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int nc = (ng + K - 1) / K;
@@ -1143,9 +1164,18 @@ __global__ void k_cluster_classes(const int* far_off, const int* lsplit, const i
     double lo[3], hi[3];
     for (int k = 0; k < 3; ++k) { lo[k] = clo[3 * C + k]; hi[k] = chi[3 * C + k]; }
     const double c2 = __dmul_rn(cle[C], cle[C]);
+    // the traversal's FP32 pre-test on outward-rounded boxes; the exact FP64
+    // test only within its margin of the threshold
+    const float4 cl = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]), 0.f);
+    const float4 ch = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]), 0.f);
+    const float cs = fmaxf(fmaxf(fmaxf(fabsf(cl.x), fabsf(cl.y)), fmaxf(fabsf(cl.z), fabsf(ch.x))),
+                           fmaxf(fabsf(ch.y), fabsf(ch.z)));
+    const float mscale = 1e-6f * (1.f + fmaxf(cs, 1.f));
+    const float clef = (float)cle[C];
     for (int e = lsplit[g0] + lane; e < far_off[g0 + 1]; e += 32) {
         const int b = far_id[e];
-        if (!(box_gap2_d(nlo, nhi, b, lo, hi) > c2)) continue;
+        const int q = far_pretest(gap2_f(nlof[b], nhif[b], cl, ch), clef, mscale);
+        if (q == 0 || (q < 0 && !(box_gap2_d(nlo, nhi, b, lo, hi) > c2))) continue;
         int qm[kMaxCluster];
         bool all = true;
         for (int m = 1; m < g1 - g0 && all; ++m) {
@@ -1873,7 +1903,8 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             unsigned char* moved = dalloc<unsigned char>(std::max<int64_t>(nfar, 1));
             WNNC_CUDA(cudaMemsetAsync(moved, 0, std::max<int64_t>(nfar, 1), s));
             k_cluster_classes<<<ceil_div((int64_t)ts.nclusters * 32, kTB), kTB, 0, s>>>(
-                ts.far_off, ts.far_lsplit, ts.far_id, ng, K, t.node_lo, t.node_hi, cl_lo, cl_hi, cl_e, moved);
+                ts.far_off, ts.far_lsplit, ts.far_id, ng, K, t.node_lo, t.node_hi, t.node_lof, t.node_hif, cl_lo,
+                cl_hi, cl_e, moved);
             WNNC_LAUNCH_CHECK();
             int* reordered = dalloc<int>(std::max<int64_t>(nfar, 1));
             k_cluster_partition<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(
