@@ -238,6 +238,33 @@ wnnc_status wnnc_debug_fail_alloc(int64_t after) {
     return WNNC_OK;
 }
 
+// A stream of the highest priority for one build, ordered after the caller's
+// stream at creation (fork) and before it again at join().
+struct BuildStream {
+    cudaStream_t us, s = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    explicit BuildStream(cudaStream_t caller) : us(caller) {
+        int least = 0, greatest = 0;
+        WNNC_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        WNNC_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
+        WNNC_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        WNNC_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        WNNC_CUDA(cudaEventRecord(fork, us));
+        WNNC_CUDA(cudaStreamWaitEvent(s, fork, 0));
+    }
+    void join() {
+        WNNC_CUDA(cudaEventRecord(done, s));
+        WNNC_CUDA(cudaStreamWaitEvent(us, done, 0));
+    }
+    ~BuildStream() {
+        if (done) cudaEventDestroy(done);
+        if (fork) cudaEventDestroy(fork);
+        if (s) cudaStreamDestroy(s);
+    }
+    BuildStream(const BuildStream&) = delete;
+    BuildStream& operator=(const BuildStream&) = delete;
+};
+
 wnnc_status wnnc_build_tree(const float* pts, int64_t n, const wnnc_tree_params* params, void* stream,
                             wnnc_tree** out) {
     if (out) *out = nullptr;
@@ -255,14 +282,23 @@ wnnc_status wnnc_build_tree(const float* pts, int64_t n, const wnnc_tree_params*
         t->n = n;
         t->params = p;
         WNNC_CUDA(cudaGetDevice(&t->device));
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        AllocStream as(s);
-        build_tree(*t, pts, s);
-        alloc_workspace(*t);
+        cudaStream_t us = static_cast<cudaStream_t>(stream);
+        // the build runs on a stream of the highest priority, after the work
+        // queued on the caller's stream and before what follows there: its
+        // short kernels then go ahead of the transposed lists' sorts on the
+        // second stream
+        BuildStream bs(us);
+        cudaStream_t s = bs.s;
+        {
+            AllocStream as(s);
+            build_tree(*t, pts, s);
+            alloc_workspace(*t);
+        }
+        bs.join();
         unsigned timeouts = 0;
-        wait_timeouts_async(&timeouts, s);
-        WNNC_CUDA(cudaStreamSynchronize(s));
-        check_wait_timeouts(timeouts, s);
+        wait_timeouts_async(&timeouts, us);
+        WNNC_CUDA(cudaStreamSynchronize(us));
+        check_wait_timeouts(timeouts, us);
     });
     if (st != WNNC_OK) {
         if (t) {
