@@ -1421,7 +1421,8 @@ __device__ __noinline__ float4 local_entry_pairs(const AdjArgs& A, int i0, int i
 // shorter lists gain more from the extra resident warps of the smaller
 // register count).  Each list item carries its class in bits 30-31: an entry
 // summed pair by pair (its contrib), one expanded about a group (the group;
-// its record gadj) or one expanded about a cluster (the cluster; cadj).
+// its record gadj) or one expanded about a cluster (the cluster; cadj); a
+// node's list holds its items by class.
 constexpr int kNodeGathers = 16;
 
 // The transposed term of one expanded entry from its group's or cluster's

@@ -1230,7 +1230,8 @@ __global__ void k_cluster_partition(const int* far_off, const int* lsplit, const
 // group (from lsplit on; id = the group), 2 for one expanded about its cluster
 // (from csplit on; id = the cluster), kept only in the first member's copy
 // (the other members' copies get node = nnodes and sort past every node).  A
-// stable sort on the node bits then leaves each node's values in entry order.
+// stable sort on the node and class bits then leaves each node's values by
+// class, each class in entry order.
 __global__ void k_tfar_keys(const int* far_off, const int* far_id, int ng, const int* lsplit, const int* csplit,
                             int K, int nnodes, uint64_t* keys) {
     const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -1893,9 +1894,6 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             sort_far_segments(ts.far_id, ts.far_off, ts.far_lsplit, unsorted, nunsorted, bits_for(t.nnodes), s);
         ts.walk_stack_groups = big_stack ? 0 : nunsorted;
         ts.walk_big_stack = big_stack ? 1 : 0;
-        // near leaves by (group, first point)
-        radix_sort_pairs(nkeys, nvals, nleafent, nsh + gbits, s);
-        segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s, nsh);
         if (K) {
             // entries expanded about their cluster: flagged, then each group's expanded
             // part reordered into [group | cluster] (csplit)
@@ -1916,6 +1914,9 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             pool_free(moved);
         }
         if (after_far) after_far();
+        // near leaves by (group, first point)
+        radix_sort_pairs(nkeys, nvals, nleafent, nsh + gbits, s);
+        segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s, nsh);
         // merge consecutive near leaves into ranges
         int* head = dalloc<int>(nleafent + 2);
         int* hscan = dalloc<int>(nleafent + 2);
@@ -2025,8 +2026,10 @@ static void build_tfar(Tree& t, cudaStream_t s) {
     k_tfar_keys<<<ceil_div((int64_t)ng * 32, kTB), kTB, 0, s>>>(S.far_off, S.far_id, ng, S.far_lsplit, S.far_csplit,
                                                                S.cluster_k, t.nnodes, k);
     WNNC_LAUNCH_CHECK();
-    // entry order already ascending: the node bits only
-    radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes + 1), s, 32);
+    // entry order already ascending: the node bits and, with local
+    // expansions, the class bits (each node's list by class, so that the
+    // warps of the node gather mostly take one kind of entry at a time)
+    radix_sort_pairs(k, nullptr, ne, 32 + bits_for(t.nnodes + 1), s, S.far_lsplit ? 30 : 32);
     k_tfar_finish<<<ceil_div(ne, kTB), kTB, 0, s>>>(k, ne, t.nnodes, t.tfar_ent, t.tfar_off);
     WNNC_LAUNCH_CHECK();
     wait_before_free(s);
