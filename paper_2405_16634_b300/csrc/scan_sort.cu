@@ -113,15 +113,39 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chained(const T* in, T* o
     __shared__ T tot;
     T ex = block_exclusive_scan<T>(sum, &tot);
     unsigned long long* w = look + 1;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // the first warp publishes the tile's total, then looks back 32 tiles
+        // at a time: it waits for all 32 words, and adds them up to the
+        // nearest inclusive one (tiles before 0 count as an inclusive 0)
+        const int lane = threadIdx.x;
         const unsigned long long agg = (unsigned long long)tot & kLbVal;
-        if (tile == 0) {
-            lb_store(w, kLbIncl | agg);
-            s_excl = 0;
-        } else {
-            lb_store(w + tile, kLbAgg | agg);
-            const unsigned long long e = lb_prefix(w, tile, 1);
-            lb_store(w + tile, kLbIncl | ((e + agg) & kLbVal));
+        if (lane == 0) lb_store(w + tile, (tile == 0 ? kLbIncl : kLbAgg) | agg);
+        unsigned long long e = 0;
+        int p = tile - 1, polls = 0;
+        bool gave_up = false;
+        while (tile > 0 && !gave_up) {
+            const int q = p - lane;
+            unsigned long long v = q >= 0 ? lb_load(w + q) : kLbIncl;
+            while (__any_sync(0xffffffffu, (v >> 62) == 0)) {
+                if (++polls > kWaitPolls) {
+                    if (lane == 0) atomicAdd(&g_wait_timeouts, 1u);
+                    gave_up = true;
+                    break;
+                }
+                if (polls > 64) __nanosleep(64);
+                if ((v >> 62) == 0) v = lb_load(w + q);
+            }
+            const unsigned incl = __ballot_sync(0xffffffffu, (v & ~kLbVal) == kLbIncl);
+            const int j = incl ? __ffs(incl) - 1 : 31;
+            unsigned long long x = lane <= j ? (v & kLbVal) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            e += x;
+            if (incl) break;
+            p -= 32;
+        }
+        if (lane == 0) {
+            if (tile > 0) lb_store(w + tile, kLbIncl | ((e + agg) & kLbVal));
             s_excl = (T)e;
         }
     }
