@@ -407,6 +407,18 @@ int64_t wnnc_kernel_launches(void);
 wnnc_status wnnc_probe_fp32(double* tflops, void* stream);
 
 /*
+ * Diagnostic (no counterpart in the paper): runs one block of the build's
+ * single-pass scan on `stream` with the tile before its own never published
+ * (a look-back word that nothing sets), so that its bounded wait gives up,
+ * then synchronises and reads the device's timeout count.  Returns
+ * WNNC_ETIMEOUT when the wait gave up and was reported as the builds report
+ * it (the count is cleared and the context stays usable; the wait lasts about
+ * a second at most); any other status means that the bound or the report
+ * failed.  Used by the tests of the failure paths.
+ */
+wnnc_status wnnc_selftest_wait_timeout(void* stream);
+
+/*
  * F(q_k; mu) at m query points by direct summation over all n points, with no
  * tree and no device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc (a host application

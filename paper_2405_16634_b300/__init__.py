@@ -114,6 +114,8 @@ def lib():
     L.wnnc_debug_fail_alloc.restype = c_int
     L.wnnc_probe_fp32.argtypes = [P, P]
     L.wnnc_probe_fp32.restype = c_int
+    L.wnnc_selftest_wait_timeout.argtypes = [P]
+    L.wnnc_selftest_wait_timeout.restype = c_int
     for name in ("wnnc_tree_params_default", "wnnc_iter_params_default", "wnnc_build_tree",
                  "wnnc_tree_free", "wnnc_eval_w", "wnnc_eval_grad", "wnnc_eval_adjoint",
                  "wnnc_eval_at", "wnnc_iterate", "wnnc_get_stats", "wnnc_get_local_stats", "wnnc_tree_info",
@@ -198,6 +200,14 @@ def probe_fp32(device=None) -> float:
     with torch.cuda.device(dev):
         _check(lib().wnnc_probe_fp32(ctypes.byref(v), _stream_ptr(dev)))
     return v.value
+
+
+def selftest_wait_timeout(device=None) -> int:
+    """Run one scan block whose bounded look-back wait runs out; returns the
+    library status (WNNC_ETIMEOUT = 6 when the bound and its report work)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    with torch.cuda.device(dev):
+        return int(lib().wnnc_selftest_wait_timeout(_stream_ptr(dev)))
 
 
 def default_tree_params() -> TreeParams:

@@ -691,6 +691,14 @@ wnnc_status wnnc_probe_fp32(double* tflops, void* stream) {
     });
 }
 
+wnnc_status wnnc_selftest_wait_timeout(void* stream) {
+    return guarded([&] {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        AllocStream as(s);
+        selftest_wait_timeout(s);
+    });
+}
+
 const char* wnnc_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

@@ -326,6 +326,8 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
 // WNNC_ETIMEOUT when the value read is non-zero.
 void wait_timeouts_async(unsigned* host, cudaStream_t s);
 void check_wait_timeouts(unsigned seen, cudaStream_t s);
+// One block of the single-pass scan whose look-back wait runs out (diagnostic).
+void selftest_wait_timeout(cudaStream_t s);
 // off[g] = first index i with (keys[i] >> shift) >= g, for g in [0, ng]; keys sorted.
 void segment_offsets_hi32(const uint64_t* keys, int64_t n, int* off, int ng, cudaStream_t s, int shift = 32);
 

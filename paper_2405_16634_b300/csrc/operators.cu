@@ -1339,12 +1339,9 @@ __global__ void WNNC_ADJ_BOUNDS k_adj_far(AdjArgs A) {
 //   S E/r^3 + (3 E (E.D) - r^2 D)/r^5
 // (first order in x_i - c_g of sum_i s_i (x_B - x_i)/|x_B - x_i|^3), unless
 // its pairs may straddle the cut-off (|E| - rho_g < w): then its pairs.
-// k_local_groups writes each group's (c_g, rho_g), (D, S); the node gather
-// evaluates the expanded entries as it meets them.
-__global__ void k_local_groups(AdjArgs A) {
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (g >= A.ngroups) return;
+// k_local_records writes each group's (c_g, rho_g), (D, S) (and each
+// cluster's); the node gather evaluates the expanded entries as it meets them.
+__device__ __forceinline__ void local_group_record(const AdjArgs& A, int g, int lane) {
     const int i0 = A.goff[g], cnt_t = A.goff[g + 1] - i0;
     const float4 o = A.gorig[g];
     const float4 cg = A.gctr[g];
@@ -1367,10 +1364,7 @@ __global__ void k_local_groups(AdjArgs A) {
 
 // The same records per cluster of the second level (warp per cluster, its
 // up to 32 K targets in the cluster's frame).
-__global__ void k_local_clusters(AdjArgs A) {
-    const int C = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (C >= A.nclusters) return;
+__device__ __forceinline__ void local_cluster_record(const AdjArgs& A, int C, int lane) {
     const int g0 = C * A.cluster_k, g1 = min(g0 + A.cluster_k, A.ngroups);
     const float4 o = A.cctr[C];
     const float4 cg = A.cexp[C];
@@ -1394,6 +1388,15 @@ __global__ void k_local_clusters(AdjArgs A) {
         A.cadj[2 * C] = make_float4(o.x + cg.x, o.y + cg.y, o.z + cg.z, cg.w);
         A.cadj[2 * C + 1] = make_float4(sx, sy, sz, sS);
     }
+}
+
+// Both record sets in one launch: warps [0, ngroups) take the groups, the
+// next nclusters warps the clusters.
+__global__ void k_local_records(AdjArgs A) {
+    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w < A.ngroups) local_group_record(A, w, lane);
+    else if (w < A.ngroups + A.nclusters) local_cluster_record(A, w - A.ngroups, lane);
 }
 
 // The pairs of one expanded entry whose pairs may straddle the cut-off: node
@@ -2608,14 +2611,11 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
             WNNC_LAUNCH_CHECK();
         }
         if (a.lsplit) {
-            // each group's record for its expanded entries
+            // each group's and cluster's record for its expanded entries
             ProfScope ps(&t.prof, WNNC_PROF_LOCAL, s);
-            k_local_groups<<<ceil_div((int64_t)t.self.ngroups * 32, kTB), kTB, 0, s>>>(a);
+            const int64_t nrec = (int64_t)t.self.ngroups + (a.cadj ? t.self.nclusters : 0);
+            k_local_records<<<ceil_div(nrec * 32, kTB), kTB, 0, s>>>(a);
             WNNC_LAUNCH_CHECK();
-            if (a.cadj) {
-                k_local_clusters<<<ceil_div((int64_t)t.self.nclusters * 32, kTB), kTB, 0, s>>>(a);
-                WNNC_LAUNCH_CHECK();
-            }
         }
         ProfScope ps(&t.prof, WNNC_PROF_ADJ_NODE, s);
         if (a.lsplit && a.cadj) {

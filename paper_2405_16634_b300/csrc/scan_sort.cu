@@ -56,7 +56,7 @@ __device__ T block_exclusive_scan(T v, T* total) {
 // the host, which then fails the build) and goes on.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbVal = (1ull << 62) - 1;
-constexpr int kWaitPolls = 1 << 22;
+constexpr int kWaitPolls = 1 << 20;   // with back-off: well under a second of polling
 
 __device__ unsigned g_wait_timeouts;
 
@@ -507,6 +507,28 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
     if (v2) pool_free(v2);
     if (ws) pool_free(ws);
     if (hist) pool_free(hist);
+}
+
+void selftest_wait_timeout(cudaStream_t s) {
+    // two tiles of input, one block: it takes tile 1 (the counter starts at 1)
+    // and waits for tile 0's look-back word, which nothing sets
+    const int64_t n = 2 * (int64_t)kScanTile;
+    int* in = dalloc<int>(n);
+    int* out = dalloc<int>(n + 1);
+    unsigned long long* look = dalloc<unsigned long long>(3);
+    WNNC_CUDA(cudaMemsetAsync(in, 0, sizeof(int) * n, s));
+    WNNC_CUDA(cudaMemsetAsync(look, 0, sizeof(unsigned long long) * 3, s));
+    static const unsigned long long one = 1;
+    WNNC_CUDA(cudaMemcpyAsync(look, &one, sizeof(one), cudaMemcpyHostToDevice, s));
+    k_scan_chained<int><<<1, kScanThreads, 0, s>>>(in, out, n, look);
+    WNNC_LAUNCH_CHECK();
+    unsigned seen = 0;
+    wait_timeouts_async(&seen, s);
+    WNNC_CUDA(cudaStreamSynchronize(s));
+    pool_free(in);
+    pool_free(out);
+    pool_free(look);
+    check_wait_timeouts(seen, s);
 }
 
 void wait_timeouts_async(unsigned* host, cudaStream_t s) {

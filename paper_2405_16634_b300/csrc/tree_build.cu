@@ -242,7 +242,7 @@ struct GridBar {
     unsigned gen;
     int err;            // a wait gave up
 };
-constexpr int kBarrierPolls = 1 << 22;
+constexpr int kBarrierPolls = 1 << 20;   // with back-off: well under a second of polling
 
 // Barrier of all blocks of a cooperative launch: each block arrives on the
 // counter; the last to arrive resets it and bumps the generation, which the

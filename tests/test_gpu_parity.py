@@ -9,6 +9,7 @@ kernel's FP32 test may fall on the other side).  Integer work (sort order,
 octree, interaction lists, pair counts) must match exactly.
 """
 import math
+import time
 
 import numpy as np
 import pytest
@@ -745,6 +746,26 @@ def test_allocation_failures_are_reported_and_leave_the_library_usable():
     again = W.Tree(pts, theta=0.5).iterate(n_iter=3).cpu()
     assert torch.equal(again, ref)
     t.sync_status()
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """Failure detection on the GPU without a fault: one block of the build's
+    single-pass scan waits on a look-back word that nothing sets.  Its wait is
+    bounded, the give-up is counted on the device and reported as
+    WNNC_ETIMEOUT, and the context stays usable: a build and an iteration
+    afterwards give bit-identical results to ones made before."""
+    W = _wnnc()
+    c = synth.union_cloud(20000, 9, n_tori=1, n_ellipsoids=1)
+    pts = torch.from_numpy(c.points).cuda()
+    ref = W.Tree(pts, theta=0.5, local_theta=0.5, local_cluster=4).iterate(n_iter=2).cpu()
+    t0 = time.perf_counter()
+    st = W.selftest_wait_timeout()
+    took = time.perf_counter() - t0
+    assert st == 6, st
+    assert took < 10.0
+    assert "bounded wait" in W.lib().wnnc_last_error().decode()
+    again = W.Tree(pts, theta=0.5, local_theta=0.5, local_cluster=4).iterate(n_iter=2).cpu()
+    assert torch.equal(again, ref)
 
 
 def test_units_scale_invariance():
