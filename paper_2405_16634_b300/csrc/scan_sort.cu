@@ -47,9 +47,11 @@ __device__ T block_exclusive_scan(T v, T* total) {
 // Single-pass prefix sums across blocks (decoupled look-back).  A block takes
 // the next tile index from an atomic counter, so that every tile it waits on
 // belongs to a block that has started; it publishes its tile's total
-// (status "aggregate") at once, then walks back over the earlier tiles, adding
-// their totals until it meets one whose inclusive prefix is known (status
-// "inclusive"), and publishes its own inclusive prefix.  A look-back word
+// (status "aggregate") at once, then walks back over the earlier tiles (a
+// warp 32 tiles at a time in the scans, a thread one tile at a time per digit
+// column in the radix passes), adding their totals until it meets one whose
+// inclusive prefix is known (status "inclusive"), and publishes its own
+// inclusive prefix.  A look-back word
 // holds the status in bits 62-63 and the (non-negative) value below, so one
 // relaxed 64-bit load or store moves both.  Every wait is bounded: past
 // kWaitPolls polls the block counts a timeout in g_wait_timeouts (read by
