@@ -720,8 +720,9 @@ constexpr int kStackSmall = 2048;
 constexpr int kStackBig = 4096;
 
 // Warp-cooperative traversal of the octree for one target group, one pass:
-// it writes far node ids in chunks (below) and, for near leaves, keys
-// (group << nsh | first point) with the leaf id (sorted by key afterwards).
+// it writes far node ids and, for near leaves, keys (group << nsh | first
+// point) with the leaf id, both in chunks (below); the near lists are sorted
+// by first point afterwards.
 // Up to 32 nodes are tested at once; children of opened nodes go into a
 // per-warp shared buffer whose capacity is checked before a push.
 //
@@ -770,15 +771,22 @@ __device__ __forceinline__ void trav_flush_far(const int* buf, int cnt, int* poo
 
 __device__ __forceinline__ void trav_flush_near(const uint64_t* buf, const uint32_t* vbuf, int cnt, uint64_t* pool,
                                                 uint32_t* vpool, int64_t cap, unsigned long long* counter,
-                                                int lane) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(counter, (unsigned long long)cnt);
+                                                int4* chunks, int64_t chunk_cap, unsigned long long* chunk_counter,
+                                                int g, int prefix, int lane) {
+    unsigned long long base = 0, ck = 0;
+    if (lane == 0) {
+        base = atomicAdd(counter, (unsigned long long)cnt);
+        ck = atomicAdd(chunk_counter, 1ull);
+    }
     base = __shfl_sync(0xffffffffu, base, 0);
-    if ((int64_t)(base + cnt) <= cap)
+    ck = __shfl_sync(0xffffffffu, ck, 0);
+    if ((int64_t)(base + cnt) <= cap) {
         for (int k = lane; k < cnt; k += 32) {
             pool[base + k] = buf[k];
             vpool[base + k] = vbuf[k];
         }
+        if (lane == 0 && (int64_t)ck < chunk_cap) chunks[ck] = make_int4((int)base, cnt, g, prefix);
+    }
     __syncwarp();
 }
 
@@ -791,11 +799,15 @@ struct TravOut {
     unsigned long long* chunk_count;
     int2* gcount;                     // per group: class-0 and class-1 far entries
     uint64_t* near_pool;              // near keys (group << nsh | first point)
-    uint32_t* near_vpool;             //   and leaf ids
+    uint32_t* near_vpool;             //   and leaf ids, in chunks
     int64_t near_cap;
     unsigned long long* near_count;
+    int4* near_chunks;                // their chunk records (pool position, count, group, prefix)
+    int64_t near_chunk_cap;
+    unsigned long long* near_chunk_count;
+    int* ncount;                      // per group: near leaves
     int nsh;
-    int* err;
+    int* err;                         // [0] error flags, [1] stack-walk groups, [2] most near leaves of a group
     uint64_t* unsorted;               // groups whose walk was finished as a stack walk
     int* unsorted_count;
 };
@@ -842,7 +854,7 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
     __syncwarp();
     // live entries are [head, head + top) modulo STACK; pushes append at the
     // end; first-in first-out pops from head, the stack walk from the end
-    int head = 0, top = 1, fcnt = 0, lcnt = 0, ncnt = 0, fdone = 0, ldone = 0;
+    int head = 0, top = 1, fcnt = 0, lcnt = 0, ncnt = 0, fdone = 0, ldone = 0, ndone = 0;
     bool fifo = FIFO;
     while (top > 0) {
         if (fifo && top > STACK - 256) {
@@ -883,7 +895,9 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
             lcnt = 0;
         }
         if (ncnt + 32 > kTravBuf) {
-            trav_flush_near(nbuf, nvbuf, ncnt, out.near_pool, out.near_vpool, out.near_cap, out.near_count, lane);
+            trav_flush_near(nbuf, nvbuf, ncnt, out.near_pool, out.near_vpool, out.near_cap, out.near_count,
+                            out.near_chunks, out.near_chunk_cap, out.near_chunk_count, g, ndone, lane);
+            ndone += ncnt;
             ncnt = 0;
         }
         if (far && !loc) fbuf[fcnt + __popc(fm & lt)] = b;
@@ -922,8 +936,14 @@ k_traverse(const double* nlo, const double* nhi, const float4* nlof, const float
     if (lcnt)
         trav_flush_far(lbuf, lcnt, out.far_pool, out.far_cap, out.far_count, out.chunks, out.chunk_cap,
                        out.chunk_count, g, 1, ldone, lane);
-    if (ncnt) trav_flush_near(nbuf, nvbuf, ncnt, out.near_pool, out.near_vpool, out.near_cap, out.near_count, lane);
-    if (lane == 0) out.gcount[g] = make_int2(fdone + fcnt, ldone + lcnt);
+    if (ncnt)
+        trav_flush_near(nbuf, nvbuf, ncnt, out.near_pool, out.near_vpool, out.near_cap, out.near_count,
+                        out.near_chunks, out.near_chunk_cap, out.near_chunk_count, g, ndone, lane);
+    if (lane == 0) {
+        out.gcount[g] = make_int2(fdone + fcnt, ldone + lcnt);
+        out.ncount[g] = ndone + ncnt;
+        atomicMax(out.err + 2, ndone + ncnt);
+    }
 }
 
 // Far list offsets from the per-group counts: tot[g] = class 0 + class 1.
@@ -944,6 +964,61 @@ __global__ void k_far_place(const int4* chunks, int64_t nchunks, const int* pool
     const int dst = far_off[c.z] + (cls ? gcount[c.z].x : 0) + prefix;
     for (int i = lane; i < c.y; i += 32) far_id[dst + i] = pool[c.x + i];
 }
+// Each near chunk of the pool to its place in its group's list (warp per
+// chunk), in the walk's order.
+__global__ void k_near_place(const int4* chunks, int64_t nchunks, const uint64_t* pool, const uint32_t* vpool,
+                             const int* off, uint64_t* keys, uint32_t* vals) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= nchunks) return;
+    const int4 c = chunks[k];
+    const int dst = off[c.z] + c.w;
+    for (int i = lane; i < c.y; i += 32) {
+        keys[dst + i] = pool[c.x + i];
+        vals[dst + i] = vpool[c.x + i];
+    }
+}
+
+// Each group's near list sorted by first point in shared memory, one block
+// per group: (first point << 32 | leaf) keys, padded to a power of two, by a
+// bitonic network (first points are distinct within a group).  Lists longer
+// than kNearSortCap are left to the caller, which then sorts all near keys.
+constexpr int kNearSortCap = 2048;
+constexpr int kNearSortThreads = 256;
+__global__ void __launch_bounds__(kNearSortThreads) k_near_group_sort(const int* off, int nsh, uint64_t* keys,
+                                                                      uint32_t* vals) {
+    __shared__ uint64_t sk[kNearSortCap];
+    const int g = blockIdx.x, t = threadIdx.x;
+    const int e0 = off[g], n = off[g + 1] - e0;
+    if (n <= 1 || n > kNearSortCap) return;
+    int P = 2;
+    while (P < n) P <<= 1;
+    const uint64_t low = (uint64_t(1) << nsh) - 1;
+    for (int i = t; i < P; i += kNearSortThreads)
+        sk[i] = i < n ? ((keys[e0 + i] & low) << 32) | vals[e0 + i] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = t; i < P; i += kNearSortThreads) {
+                const int ij = i ^ j;
+                if (ij > i) {
+                    const uint64_t a = sk[i], b = sk[ij];
+                    if ((a > b) == ((i & k) == 0)) {
+                        sk[i] = b;
+                        sk[ij] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const uint64_t hi = (uint64_t)g << nsh;
+    for (int i = t; i < n; i += kNearSortThreads) {
+        keys[e0 + i] = hi | (sk[i] >> 32);
+        vals[e0 + i] = (uint32_t)(sk[i] & 0xffffffffu);
+    }
+}
+
 __global__ void k_lsplit_from_counts(const int* far_off, const int2* gcount, int ng, int* lsplit) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g < ng) lsplit[g] = far_off[g] + gcount[g].x;
@@ -1783,19 +1858,22 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         if (after_far) after_far();
     } else {
         int* leaf_off = dalloc<int>(ng + 1);
-        int* err = dalloc<int>(2);        // [0] error flags, [1] groups finished as stack walks
+        int* err = dalloc<int>(3);        // [0] error flags, [1] groups finished as stack walks, [2] longest near list
         uint64_t* unsorted = dalloc<uint64_t>(ng);
-        unsigned long long* counts = dalloc<unsigned long long>(3);   // far ids, chunks, near entries
+        unsigned long long* counts = dalloc<unsigned long long>(4);   // far ids, far chunks, near entries, near chunks
         int2* gcount = dalloc<int2>(ng);
+        int* ncount = dalloc<int>(ng + 1);
         const int tgrid = ceil_div(ng, kTravWarps);
         const int nsh = bits_for(t.n);    // near keys: group << nsh | first point
         // pool estimates (per target); a second pass runs with exact sizes if exceeded
         int64_t far_cap = std::min<int64_t>(48 * m + 4096, INT32_MAX), near_cap = 8 * m + 4096;
         int* fpool = nullptr;
         int4* chunks = nullptr;
+        int4* nchunks = nullptr;
         uint64_t* nkeys = nullptr;
         uint32_t* nvals = nullptr;
-        int64_t nfar = 0, nchunk = 0, nleafent = 0;
+        int64_t nfar = 0, nchunk = 0, nleafent = 0, nnchunk = 0;
+        int longest_near = 0;
         // first the first-in first-out walk (far ids come out ascending within
         // each group, except in the groups it lists as unsorted); if a stack
         // walk overflows its buffer, everything again as stack walks with the
@@ -1805,12 +1883,14 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         for (int attempt = 0; attempt < 4; ++attempt) {
             // a flush other than a class's last holds > kTravBuf - 32 entries
             const int64_t chunk_cap = far_cap / (kTravBuf - 31) + 2 * (int64_t)ng + 64;
+            const int64_t nchunk_cap = near_cap / (kTravBuf - 31) + (int64_t)ng + 64;
             fpool = dalloc<int>(far_cap);
             chunks = dalloc<int4>(chunk_cap);
             nkeys = dalloc<uint64_t>(near_cap);
             nvals = dalloc<uint32_t>(near_cap);
-            WNNC_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
-            WNNC_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s));
+            nchunks = dalloc<int4>(nchunk_cap);
+            WNNC_CUDA(cudaMemsetAsync(err, 0, 3 * sizeof(int), s));
+            WNNC_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s));
             TravOut o;
             o.far_pool = fpool;
             o.far_cap = far_cap;
@@ -1823,6 +1903,10 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             o.near_vpool = nvals;
             o.near_cap = near_cap;
             o.near_count = counts + 2;
+            o.near_chunks = nchunks;
+            o.near_chunk_cap = nchunk_cap;
+            o.near_chunk_count = counts + 3;
+            o.ncount = ncount;
             o.nsh = nsh;
             o.err = err;
             o.unsorted = unsorted;
@@ -1835,29 +1919,31 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
 #undef WNNC_TRAVERSE
             WNNC_LAUNCH_CHECK();
             unsigned long long* hc = reinterpret_cast<unsigned long long*>(pinned_scratch());
-            int* herr = reinterpret_cast<int*>(hc + 3);
-            WNNC_CUDA(cudaMemcpyAsync(hc, counts, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-            WNNC_CUDA(cudaMemcpyAsync(herr, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            int* herr = reinterpret_cast<int*>(hc + 4);
+            WNNC_CUDA(cudaMemcpyAsync(hc, counts, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            WNNC_CUDA(cudaMemcpyAsync(herr, err, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
             WNNC_CUDA(cudaStreamSynchronize(s));
             nunsorted = herr[1];
+            longest_near = herr[2];
             if (herr[0]) {
-                pool_free(fpool); pool_free(chunks); pool_free(nkeys); pool_free(nvals);
+                pool_free(fpool); pool_free(chunks); pool_free(nkeys); pool_free(nvals); pool_free(nchunks);
                 if (!big_stack) {   // again with the larger stack
                     big_stack = true;
                     continue;
                 }
                 pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts); pool_free(gcount);
-                pool_free(near_off0);
+                pool_free(ncount); pool_free(near_off0);
                 fail(WNNC_ECAPACITY, "interaction-list traversal stack overflow (theta too small)");
             }
             nfar = (int64_t)hc[0];
             nchunk = (int64_t)hc[1];
             nleafent = (int64_t)hc[2];
-            if (nfar <= far_cap && nchunk <= chunk_cap && nleafent <= near_cap) break;
-            pool_free(fpool); pool_free(chunks); pool_free(nkeys); pool_free(nvals);
+            nnchunk = (int64_t)hc[3];
+            if (nfar <= far_cap && nchunk <= chunk_cap && nleafent <= near_cap && nnchunk <= nchunk_cap) break;
+            pool_free(fpool); pool_free(chunks); pool_free(nkeys); pool_free(nvals); pool_free(nchunks);
             if (attempt == 3 || nfar > INT32_MAX || nleafent > INT32_MAX) {
                 pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts); pool_free(gcount);
-                pool_free(near_off0);
+                pool_free(ncount); pool_free(near_off0);
                 fail(WNNC_ECAPACITY, "interaction lists too long");
             }
             far_cap = std::max<int64_t>(nfar, 1);
@@ -1914,9 +2000,28 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
             pool_free(moved);
         }
         if (after_far) after_far();
-        // near leaves by (group, first point)
-        radix_sort_pairs(nkeys, nvals, nleafent, nsh + gbits, s);
-        segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s, nsh);
+        // near leaves by (group, first point): the chunks to their groups' lists and each
+        // list sorted in shared memory, or, if a list is longer than that holds, a radix
+        // sort of all near keys
+        if (longest_near <= kNearSortCap) {
+            exclusive_scan_i32(ncount, leaf_off, ng, s);
+            uint64_t* pk = dalloc<uint64_t>(std::max<int64_t>(nleafent, 1));
+            uint32_t* pv = dalloc<uint32_t>(std::max<int64_t>(nleafent, 1));
+            if (nnchunk) {
+                k_near_place<<<ceil_div(nnchunk * 32, kTB), kTB, 0, s>>>(nchunks, nnchunk, nkeys, nvals, leaf_off, pk,
+                                                                        pv);
+                WNNC_LAUNCH_CHECK();
+            }
+            k_near_group_sort<<<ng, kNearSortThreads, 0, s>>>(leaf_off, nsh, pk, pv);
+            WNNC_LAUNCH_CHECK();
+            pool_free(nkeys);
+            pool_free(nvals);
+            nkeys = pk;
+            nvals = pv;
+        } else {
+            radix_sort_pairs(nkeys, nvals, nleafent, nsh + gbits, s);
+            segment_offsets_hi32(nkeys, nleafent, leaf_off, ng, s, nsh);
+        }
         // merge consecutive near leaves into ranges
         int* head = dalloc<int>(nleafent + 2);
         int* hscan = dalloc<int>(nleafent + 2);
@@ -1941,6 +2046,7 @@ void build_target_set(const Tree& t, TargetSet& ts, const double* yn, int64_t m,
         wait_before_free(s);
         pool_free(fpool); pool_free(chunks); pool_free(nkeys); pool_free(nvals); pool_free(head); pool_free(hscan);
         pool_free(leaf_off); pool_free(err); pool_free(unsorted); pool_free(counts); pool_free(gcount);
+        pool_free(nchunks); pool_free(ncount);
     }
     // cut ranges to at most kMaxRange points
     {
