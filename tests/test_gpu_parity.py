@@ -86,7 +86,9 @@ def _uniform_cube(n, seed):
 # (cloud, theta, traversal path): "bfs" every group breadth first; "mixed"
 # some groups finish depth first and have their far lists sorted afterwards;
 # "big" every group again depth first with the larger buffer.  theta = 0.05
-# opens nearly every node; a uniform cube has large group boxes.
+# opens nearly every node (its longest near list, 3746 leaves, is past what
+# one block sorts in shared memory, so all near keys take the radix sort);
+# a uniform cube has large group boxes.
 LIST_CASES = [("union20k", 0.05, "mixed"), ("union20k", 0.3, "bfs"), ("union20k", 0.5, "bfs"),
               ("union20k", 0.8, "bfs"), ("cube100k", 0.3, "big")]
 
