@@ -2210,22 +2210,30 @@ void build_tree(Tree& t, const float* pts, cudaStream_t s) {
             A.status = ctl + kOctMaxLevels + 4;
             A.block_tot = ctl + kOctMaxLevels + 8;
             void* args[] = {&A};
-            WNNC_CUDA(cudaLaunchCooperativeKernel((const void*)k_octree, dim3(G), dim3(kOctThreads), args, 0, s));
-            WNNC_LAUNCH_CHECK();
-            int* h = reinterpret_cast<int*>(pinned_scratch());
-            WNNC_CUDA(cudaMemcpyAsync(h, ctl, sizeof(int) * (kOctMaxLevels + 8), cudaMemcpyDeviceToHost, s));
-            WNNC_CUDA(cudaStreamSynchronize(s));
-            const int* hl = h;
-            const GridBar* hb = reinterpret_cast<const GridBar*>(h + kOctMaxLevels);
-            const int* hs = h + kOctMaxLevels + 4;
-            if (hb->err) {
-                pool_free(ctl);
-                fail(WNNC_ETIMEOUT, "a grid barrier of the octree build gave up");
-            }
-            if (!hs[1]) {
-                built = true;
-                total_nodes = hs[0];
-                for (int L = 1; L < kOctMaxLevels && hl[L] > 0; ++L) level_off.push_back(level_off.back() + hl[L]);
+            const cudaError_t le =
+                cudaLaunchCooperativeKernel((const void*)k_octree, dim3(G), dim3(kOctThreads), args, 0, s);
+            if (le == cudaErrorCooperativeLaunchTooLarge) {
+                // fewer SMs than the device reports (a partitioned device): by launches
+                (void)cudaGetLastError();
+            } else {
+                WNNC_CUDA(le);
+                WNNC_LAUNCH_CHECK();
+                int* h = reinterpret_cast<int*>(pinned_scratch());
+                WNNC_CUDA(cudaMemcpyAsync(h, ctl, sizeof(int) * (kOctMaxLevels + 8), cudaMemcpyDeviceToHost, s));
+                WNNC_CUDA(cudaStreamSynchronize(s));
+                const int* hl = h;
+                const GridBar* hb = reinterpret_cast<const GridBar*>(h + kOctMaxLevels);
+                const int* hs = h + kOctMaxLevels + 4;
+                if (hb->err) {
+                    pool_free(ctl);
+                    fail(WNNC_ETIMEOUT, "a grid barrier of the octree build gave up");
+                }
+                if (!hs[1]) {
+                    built = true;
+                    total_nodes = hs[0];
+                    for (int L = 1; L < kOctMaxLevels && hl[L] > 0; ++L)
+                        level_off.push_back(level_off.back() + hl[L]);
+                }
             }
             pool_free(ctl);
         }
