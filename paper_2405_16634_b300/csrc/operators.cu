@@ -2026,8 +2026,12 @@ __global__ void WNNC_ADJ_BOUNDS k_adj_near_pairs(AdjArgs A) {
 // points).  Lane l handles source point 8C + (l & 7) and every fourth entry
 // (offset l >> 3): if the entry's mask holds the point, it adds the point's
 // near slot of that entry (the entry's slot plus the number of mask bits
-// below the point).  The four partial sums of a point are added at the end
-// (fixed order), into lanes 0..7, followed by the far part and the output.
+// below the point).  A lane reads kAdjNearReads entries, then their slots,
+// before it adds them in entry order.  The four partial sums of a point are
+// added at the end (fixed order), into lanes 0..7, followed by the far part
+// and the output.
+constexpr int kAdjNearReads = 8;
+
 template <int EPI>
 __global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2040,15 +2044,26 @@ __global__ void WNNC_GATHER_BOUNDS k_adj_near(AdjArgs A) {
     const bool valid = j < A.n;
     const unsigned below = (1u << sl) - 1u;
     float ax = 0.f, ay = 0.f, az = 0.f;
-#pragma unroll 4
-    for (int q = item.q0 + tq; q < item.q1; q += 32 / kAdjChunk) {
-        const int2 ent = A.tnear_ent[q];
-        const unsigned mask = (unsigned)ent.y;
-        if ((mask >> sl) & 1u) {
-            const float4 c = A.near_contrib[ent.x + __popc(mask & below)];
-            ax += c.x;
-            ay += c.y;
-            az += c.z;
+    constexpr int kStep = 32 / kAdjChunk;
+    for (int q = item.q0 + tq; q < item.q1; q += kStep * kAdjNearReads) {
+        int2 ent[kAdjNearReads];
+#pragma unroll
+        for (int u = 0; u < kAdjNearReads; ++u)
+            ent[u] = q + kStep * u < item.q1 ? A.tnear_ent[q + kStep * u] : make_int2(0, 0);
+        float4 c[kAdjNearReads];
+#pragma unroll
+        for (int u = 0; u < kAdjNearReads; ++u) {
+            const unsigned mask = (unsigned)ent[u].y;
+            c[u] = ((mask >> sl) & 1u) ? A.near_contrib[ent[u].x + __popc(mask & below)]
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kAdjNearReads; ++u) {
+            if (((unsigned)ent[u].y >> sl) & 1u) {
+                ax += c[u].x;
+                ay += c[u].y;
+                az += c[u].z;
+            }
         }
     }
 #pragma unroll
