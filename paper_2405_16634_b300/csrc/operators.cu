@@ -1420,9 +1420,9 @@ __device__ __noinline__ float4 local_entry_pairs(const AdjArgs& A, int i0, int i
 
 // The node gather with expanded entries: one warp per node, lanes over the
 // node's whole transposed list (U reads in flight per lane, then the sums:
-// 4 for the longer lists of one expansion level, 2 with clusters, whose
+// 4 for the longer lists of one expansion level, 1 with clusters, whose
 // shorter lists gain more from the extra resident warps of the smaller
-// register count).  Each list item carries its class in bits 30-31: an entry
+// register count: 130 us per launch at 2, 115 at 1, 164 at 3).  Each list item carries its class in bits 30-31: an entry
 // summed pair by pair (its contrib), one expanded about a group (the group;
 // its record gadj) or one expanded about a cluster (the cluster; cadj); a
 // node's list holds its items by class.
@@ -2634,7 +2634,7 @@ static void adjoint_exact(Tree& t, const float* s_sorted, float w, float* out, f
         }
         ProfScope ps(&t.prof, WNNC_PROF_ADJ_NODE, s);
         if (a.lsplit && a.cadj) {
-            k_adj_node_local<2><<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);
+            k_adj_node_local<1><<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);
         } else if (a.lsplit) {
             k_adj_node_local<4><<<ceil_div((int64_t)t.nnodes * 32, kTB), kTB, 0, s>>>(a, t.vnode);
         } else if (dip) {
